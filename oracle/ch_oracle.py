@@ -1,0 +1,368 @@
+"""Plain FP64 CPU oracle of the per-time-step solve of the ternary Cahn-Hilliard model.
+
+TEST INFRASTRUCTURE ONLY.  This module exists to check the CUDA library.  Only
+the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+leg of ``bench.py`` may import or run it; the library itself never does, and
+it shares no code with the CUDA sources.
+
+Everything here is written out from the paper's statement of the method in
+plain numpy / scipy, in float64, with no blocking or fusion:
+
+* mesh           -- uniform simplicial meshes of a box (Section 4, first paragraph)
+* element_matrices / assemble -- P1 mass M and stiffness K (Section 3, below Eq. (12))
+* load_vector    -- f^(k): the exact load of df/dphi for the polynomial
+                    potential Eq. (15), explicit in time (Section 3, Eq. (12))
+* boundary_load  -- the flux boundary conditions Eq. (10) on Gamma_b and Gamma_t
+* saddle_matrix / rhs -- the symmetric saddle-point system Eq. (14)
+* Solver.step    -- one semi-implicit step Eq. (12)/(13): the exact solution of
+                    Eq. (14) for both species by a direct factorisation
+* schur / schur_tilde -- S and its matching approximation (Section 3, Lemma 1)
+
+Readings of points the paper leaves open (each also listed in the design doc):
+  R1 the discrete coefficient of K phi in the mu equation is eps (Eq. (12)/(14)),
+     not eps^2 as in the strong form Eq. (9);
+  R2 mobilities are 1 unless given ("appropriate constants");
+  R3 df/dphi_p differentiates f(phi_p, phi_nfa, 1 - phi_p - phi_nfa) by the chain
+     rule: f_p' = 7 phi_p phi_nfa^2 - 0.2 phi_s ('poly'); 'poly_partial' drops the
+     solvent term, 'none' sets f' = 0 (used by closed-form tests);
+  R4 f^(k) is the exact load vector int f'(phi_h^k) lambda_i, not M f'(phi^k);
+  R5 the evaporation flux on Gamma_t enters with sign ``evap_sign`` (+1: inflow of
+     polymer and NFA as the text describes; -1: Eq. (10) read literally);
+  R6 the substrate flux on Gamma_b is +df_s/dphi (Eq. (10) literally), p(x) = 1;
+  R7 no extra boundary term in the mu equation (natural condition grad phi . n = 0);
+  R8 2D cells split along the lower-left/upper-right diagonal, 3D hexahedra into
+     the 6 Kuhn tetrahedra; Gamma_b = {y = 0}, Gamma_t = {y = L_y}.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+DENSE_LIMIT = 6000  # 2N at or below this: dense LU; above: sparse LU
+
+
+@dataclass
+class Params:
+    """Model and discretisation parameters; defaults are the paper's (Section 4)."""
+    dim: int = 2
+    nx: int = 32
+    ny: int = 32
+    nz: int = 0
+    Lx: float = 1.0
+    Ly: float = 1.0
+    Lz: float = 1.0
+    tau: float = 1e-4          # scaled time step (Fig. 1 caption)
+    eps: float = 1e-3          # eps_p = eps_nfa (Section 4)
+    mobility: float = 1.0      # reading R2
+    bc_mode: int = 1           # 0: zero flux everywhere, 1: fluxes of Eq. (10)
+    k_evap: float = 5e-3       # evaporation rate k (Section 4)
+    evap_sign: int = 1         # reading R5
+    g_p: float = 0.01          # substrate parameters g, h of Eq. (5) (Section 4)
+    g_nfa: float = 0.01
+    h_p: float = 0.0
+    h_nfa: float = 0.0
+    potential: str = "poly"    # reading R3
+
+
+# ----------------------------------------------------------------------------
+# Mesh (Section 4: uniform triangulations of a box; reading R8)
+# ----------------------------------------------------------------------------
+@dataclass
+class Mesh:
+    dim: int
+    coords: np.ndarray        # (N, d) float64
+    elems: np.ndarray         # (E, d+1) int64
+    bottom: np.ndarray        # (Fb, d) facets on y = 0
+    top: np.ndarray           # (Ft, d) facets on y = Ly
+    ijk: np.ndarray = field(repr=False, default=None)  # (N, d) integer grid index
+
+
+def mesh(p: Params) -> Mesh:
+    """Uniform P1 mesh of [0,Lx]x[0,Ly](x[0,Lz]); node index i + (nx+1)(j + (ny+1)k)."""
+    if p.dim == 2:
+        nx, ny = p.nx, p.ny
+        j, i = np.meshgrid(np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+        ijk = np.c_[i.ravel(), j.ravel()]
+        coords = np.c_[ijk[:, 0] * (p.Lx / nx), ijk[:, 1] * (p.Ly / ny)]
+        cj, ci = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+        v00 = (ci + (nx + 1) * cj).ravel()
+        v10, v01 = v00 + 1, v00 + nx + 1
+        v11 = v01 + 1
+        # cell c -> elements 2c (v00,v10,v11) and 2c+1 (v00,v11,v01)
+        elems = np.stack([np.c_[v00, v10, v11], np.c_[v00, v11, v01]], 1).reshape(-1, 3)
+    elif p.dim == 3:
+        nx, ny, nz = p.nx, p.ny, p.nz
+        k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+        ijk = np.c_[i.ravel(), j.ravel(), k.ravel()]
+        coords = np.c_[ijk[:, 0] * (p.Lx / nx), ijk[:, 1] * (p.Ly / ny), ijk[:, 2] * (p.Lz / nz)]
+        ck, cj, ci = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+
+        def node(off):
+            return (ci + off[0]) + (nx + 1) * ((cj + off[1]) + (ny + 1) * (ck + off[2]))
+
+        tets = []
+        for perm in itertools.permutations(range(3)):   # Kuhn: v000 -> +e_a -> +e_b -> v111
+            off = [0, 0, 0]
+            verts = [node(off)]
+            for a in perm:
+                off[a] = 1
+                verts.append(node(off))
+            tets.append(np.stack(verts, 1))
+        elems = np.stack(tets, 1).reshape(-1, 4)
+    else:
+        raise ValueError("dim must be 2 or 3")
+    # boundary facets: element faces whose vertices all lie on y = 0 (resp. y = Ly)
+    d = p.dim
+    faces = np.concatenate([np.delete(elems, a, axis=1) for a in range(d + 1)])
+    jy = ijk[:, 1][faces]
+    bottom = faces[(jy == 0).all(1)]
+    top = faces[(jy == p.ny).all(1)]
+    return Mesh(d, coords.astype(np.float64), elems.astype(np.int64), bottom, top, ijk)
+
+
+# ----------------------------------------------------------------------------
+# P1 element matrices and assembly (Section 3: "standard mass and stiffness matrices")
+# ----------------------------------------------------------------------------
+def simplex_measure_and_gradients(X: np.ndarray):
+    """|T| and the gradients of the barycentric coordinates, per simplex.
+
+    X: (E, d+1, d) vertex coordinates.  lambda_{1..d}(x) = J^{-1}(x - x_0) with
+    J = [x_1 - x_0, ..., x_d - x_0], so grad lambda_k is row k of J^{-1} and
+    grad lambda_0 = -sum_k grad lambda_k.
+    """
+    d = X.shape[2]
+    J = np.transpose(X[:, 1:, :] - X[:, :1, :], (0, 2, 1))
+    vol = np.abs(np.linalg.det(J)) / math.factorial(d)
+    Jinv = np.linalg.inv(J)
+    G = np.concatenate([-Jinv.sum(axis=1, keepdims=True), Jinv], axis=1)  # (E, d+1, d)
+    return vol, G
+
+
+def element_matrices(X: np.ndarray):
+    """M_e = |T|(1 + delta_ab)/((d+1)(d+2)),  K_e = |T| grad lambda_a . grad lambda_b."""
+    d = X.shape[2]
+    vol, G = simplex_measure_and_gradients(X)
+    Ke = vol[:, None, None] * np.einsum("ead,ebd->eab", G, G)
+    base = (np.ones((d + 1, d + 1)) + np.eye(d + 1)) / ((d + 1) * (d + 2))
+    Me = vol[:, None, None] * base[None]
+    return Me, Ke
+
+
+def assemble(m: Mesh):
+    """Global CSR M and K (sum over elements of the scattered element matrices)."""
+    N = m.coords.shape[0]
+    Me, Ke = element_matrices(m.coords[m.elems])
+    n = m.dim + 1
+    rows = np.repeat(m.elems, n, axis=1).ravel()
+    cols = np.tile(m.elems, (1, n)).ravel()
+    M = sp.csr_matrix((Me.ravel(), (rows, cols)), shape=(N, N))
+    K = sp.csr_matrix((Ke.ravel(), (rows, cols)), shape=(N, N))
+    for A in (M, K):
+        A.sum_duplicates()
+        A.sort_indices()
+    return M, K
+
+
+# ----------------------------------------------------------------------------
+# Exact integrals of barycentric monomials: int_T lambda^alpha = d! alpha! |T| / (d + |alpha|)!
+# ----------------------------------------------------------------------------
+def monomial_table(d: int, order: int) -> np.ndarray:
+    """T[a_1,...,a_order] = (1/|T|) int_T lambda_{a_1} ... lambda_{a_order} on a d-simplex."""
+    n = d + 1
+    T = np.empty((n,) * order)
+    for idx in itertools.product(range(n), repeat=order):
+        alpha = np.bincount(np.array(idx, dtype=np.int64), minlength=n)
+        num = math.factorial(d) * np.prod([math.factorial(a) for a in alpha])
+        T[idx] = num / math.factorial(d + order)
+    return T
+
+
+def dfdphi(pp: np.ndarray, pn: np.ndarray, potential: str):
+    """Nodal df/dphi_p, df/dphi_nfa for f = 3.5 phi_p^2 phi_nfa^2 + 0.1 phi_s^2, Eq. (15)."""
+    ps = 1.0 - pp - pn
+    if potential == "poly":
+        return 7.0 * pp * pn ** 2 - 0.2 * ps, 7.0 * pp ** 2 * pn - 0.2 * ps
+    if potential == "poly_partial":
+        return 7.0 * pp * pn ** 2, 7.0 * pp ** 2 * pn
+    if potential == "none":
+        return np.zeros_like(pp), np.zeros_like(pn)
+    raise ValueError(potential)
+
+
+def load_vector(m: Mesh, pp: np.ndarray, pn: np.ndarray, potential: str = "poly"):
+    """F_s[i] = int_Omega df/dphi_s(phi_h) lambda_i, exactly (reading R4).
+
+    f_p' = 7 phi_p phi_n^2 - c_s (1 - phi_p - phi_n) with c_s = 0.2 ('poly') or 0;
+    the integrand is a polynomial of degree 4 in the barycentric coordinates, so
+    the monomial formula integrates it exactly.
+    """
+    d = m.dim
+    N = m.coords.shape[0]
+    vol, _ = simplex_measure_and_gradients(m.coords[m.elems])
+    P, Q = pp[m.elems], pn[m.elems]                       # (E, d+1) vertex values
+    if potential == "none":
+        return np.zeros(N), np.zeros(N)
+    T4, T2, T1 = monomial_table(d, 4), monomial_table(d, 2), monomial_table(d, 1)
+    cubic_p = 7.0 * np.einsum("ea,eb,ec,abci->ei", P, Q, Q, T4)   # int phi_p phi_n^2 lambda_i / |T|
+    cubic_n = 7.0 * np.einsum("ea,eb,ec,abci->ei", P, P, Q, T4)   # int phi_p^2 phi_n lambda_i / |T|
+    if potential == "poly":
+        solv = T1[None, :] - np.einsum("ea,ai->ei", P + Q, T2)    # int phi_s lambda_i / |T|
+        cubic_p = cubic_p - 0.2 * solv
+        cubic_n = cubic_n - 0.2 * solv
+    Fp = np.zeros(N)
+    Fn = np.zeros(N)
+    np.add.at(Fp, m.elems, vol[:, None] * cubic_p)
+    np.add.at(Fn, m.elems, vol[:, None] * cubic_n)
+    return Fp, Fn
+
+
+def facet_measure(X: np.ndarray) -> np.ndarray:
+    """Length (d=2) or area (d=3) of boundary facets with vertex coordinates X (F, d, d)."""
+    if X.shape[1] == 2:
+        return np.linalg.norm(X[:, 1] - X[:, 0], axis=1)
+    return 0.5 * np.linalg.norm(np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]), axis=1)
+
+
+def boundary_load(m: Mesh, pp: np.ndarray, pn: np.ndarray, p: Params):
+    """g_s[i] = int_{Gamma_b} (g_s + 2 h_s phi_s) lambda_i + evap_sign k int_{Gamma_t} phi_s phi_solv lambda_i.
+
+    Flux boundary conditions of Eq. (10) with the substrate density of Eq. (5)
+    (p(x) = 1) and the evaporation flux k phi_i phi_s; readings R5, R6.
+    Returns zeros when bc_mode == 0.
+    """
+    N = m.coords.shape[0]
+    gp, gn = np.zeros(N), np.zeros(N)
+    if p.bc_mode == 0:
+        return gp, gn
+    dF = m.dim - 1
+    T1, T2, T3 = monomial_table(dF, 1), monomial_table(dF, 2), monomial_table(dF, 3)
+    # substrate, Gamma_b
+    Fb = m.bottom
+    ab = facet_measure(m.coords[Fb])
+    for g_s, h_s, phi, out in ((p.g_p, p.h_p, pp, gp), (p.g_nfa, p.h_nfa, pn, gn)):
+        val = g_s * T1[None, :] + 2.0 * h_s * np.einsum("fa,ai->fi", phi[Fb], T2)
+        np.add.at(out, Fb, ab[:, None] * val)
+    # evaporation, Gamma_t
+    Ft = m.top
+    at = facet_measure(m.coords[Ft])
+    solv = (1.0 - pp - pn)[Ft]
+    for phi, out in ((pp, gp), (pn, gn)):
+        val = p.evap_sign * p.k_evap * np.einsum("fa,fb,abi->fi", phi[Ft], solv, T3)
+        np.add.at(out, Ft, at[:, None] * val)
+    return gp, gn
+
+
+# ----------------------------------------------------------------------------
+# The saddle-point system of one species, Eq. (14)
+# ----------------------------------------------------------------------------
+def coefficients(p: Params):
+    """(a, c) with A = [[M, a K], [a K, -c M]]: a = tau*mob, c = tau*mob/eps (Eq. (14))."""
+    a = p.tau * p.mobility
+    return a, a / p.eps
+
+
+def saddle_matrix(M, K, p: Params):
+    a, c = coefficients(p)
+    return sp.bmat([[M, a * K], [a * K, -c * M]], format="csr")
+
+
+def rhs(M, phi_k, F, gbd, p: Params):
+    """b = [M phi^k + tau g_bd ; -(tau mob/eps) F^k] (Eq. (13) -> Eq. (14))."""
+    _, c = coefficients(p)
+    return np.concatenate([M @ phi_k + p.tau * gbd, -c * F])
+
+
+def schur(M, K, p: Params):
+    """Dense S = c M + a^2 K M^{-1} K, the Schur complement of A (Section 3)."""
+    a, c = coefficients(p)
+    Md, Kd = M.toarray(), K.toarray()
+    return c * Md + a * a * Kd @ np.linalg.solve(Md, Kd)
+
+
+def schur_tilde(M, K, p: Params):
+    """Dense S~ = (a K + sqrt(c) M) M^{-1} (a K + sqrt(c) M), the matching approximation."""
+    a, c = coefficients(p)
+    Md = M.toarray()
+    Hd = a * K.toarray() + math.sqrt(c) * Md
+    return Hd @ np.linalg.solve(Md, Hd)
+
+
+def mass(M, phi):
+    """int_Omega phi_h = 1^T M phi."""
+    return float(np.ones(M.shape[0]) @ (M @ phi))
+
+
+# ----------------------------------------------------------------------------
+# Time stepping (Eq. (12)/(13)), exact solve per step
+# ----------------------------------------------------------------------------
+@dataclass
+class State:
+    phi_p: np.ndarray
+    phi_nfa: np.ndarray
+    mu_p: np.ndarray
+    mu_nfa: np.ndarray
+
+    @property
+    def phi_s(self):
+        return 1.0 - self.phi_p - self.phi_nfa   # Eq. (2)
+
+
+class Solver:
+    """Mesh, matrices and a factorisation of A, reused across steps (A is constant)."""
+
+    def __init__(self, p: Params, m: Mesh | None = None):
+        self.p = p
+        self.m = m if m is not None else mesh(p)
+        self.M, self.K = assemble(self.m)
+        self.A = saddle_matrix(self.M, self.K, p)
+        self.N = self.M.shape[0]
+        if 2 * self.N <= DENSE_LIMIT:
+            self._dense = self.A.toarray()
+            self._lu = None
+        else:
+            self._dense = None
+            self._lu = spla.splu(self.A.tocsc())
+
+    def solve(self, B: np.ndarray) -> np.ndarray:
+        if self._dense is not None:
+            return np.linalg.solve(self._dense, B)     # LAPACK LU with partial pivoting
+        return self._lu.solve(B)
+
+    def rhs_pair(self, s: State):
+        Fp, Fn = load_vector(self.m, s.phi_p, s.phi_nfa, self.p.potential)
+        gp, gn = boundary_load(self.m, s.phi_p, s.phi_nfa, self.p)
+        return (rhs(self.M, s.phi_p, Fp, gp, self.p), rhs(self.M, s.phi_nfa, Fn, gn, self.p))
+
+    def step(self, s: State) -> State:
+        bp, bn = self.rhs_pair(s)
+        X = self.solve(np.stack([bp, bn], 1))
+        N = self.N
+        return State(X[:N, 0].copy(), X[:N, 1].copy(), X[N:, 0].copy(), X[N:, 1].copy())
+
+    def run(self, s: State, nsteps: int):
+        out = [s]
+        for _ in range(nsteps):
+            s = self.step(s)
+            out.append(s)
+        return out
+
+    def relres(self, s_old: State, s_new: State):
+        """True relative residuals ||b - A x|| / ||b|| of a candidate step solution, per species."""
+        bp, bn = self.rhs_pair(s_old)
+        out = []
+        for b, phi, mu in ((bp, s_new.phi_p, s_new.mu_p), (bn, s_new.phi_nfa, s_new.mu_nfa)):
+            r = b - self.A @ np.concatenate([phi, mu])
+            out.append(float(np.linalg.norm(r) / np.linalg.norm(b)))
+        return out
+
+
+def initial(n_nodes: int, phi_p: np.ndarray, phi_nfa: np.ndarray) -> State:
+    """Initial state from given nodal fractions; mu^0 = 0 (mu^0 never enters b)."""
+    return State(np.asarray(phi_p, float).copy(), np.asarray(phi_nfa, float).copy(),
+                 np.zeros(n_nodes), np.zeros(n_nodes))

@@ -1,0 +1,439 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these compare the oracle with itself: each expected value comes from a
+closed form, a brute-force computation by a different method, an invariant of
+the scheme, or a bound the paper proves (Lemma 1).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+from oracle import ch_oracle as o
+from paper_2204_03575_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------- input generator
+def test_splitmix64_published_sequence():
+    """SplitMix64 from seed 0 (state advanced by the golden gamma) gives the published outputs."""
+    rows = read_golden("splitmix64.txt")
+    gamma = 0x9E3779B97F4A7C15
+    for k, hexval in rows:
+        ctr = ((int(k) - 1) * gamma) % 2 ** 64   # the k-th output mixes state (k-1) gamma + gamma
+        assert int(inputs.splitmix64(np.uint64(ctr))) == int(hexval, 16)
+
+
+def test_initial_state_range_and_independence():
+    pp, pn = inputs.initial_state(10000, 0.33, 0.30, 0.01, seed=7)
+    assert pp.min() >= 0.32 and pp.max() < 0.34 and pn.min() >= 0.29 and pn.max() < 0.31
+    assert abs(pp.mean() - 0.33) < 5e-4 and abs(pn.mean() - 0.30) < 5e-4
+    assert abs(np.corrcoef(pp, pn)[0, 1]) < 0.05
+    pp2, _ = inputs.initial_state(10000, 0.33, 0.30, 0.01, seed=8)
+    assert not np.array_equal(pp, pp2)
+
+
+# ---------------------------------------------------------------- mesh
+def edge_count_2d(nx, ny):
+    # horizontal + vertical + one diagonal per cell
+    return nx * (ny + 1) + (nx + 1) * ny + nx * ny
+
+
+def edge_count_3d(nx, ny, nz):
+    # Kuhn tetrahedra connect v to v + e for every nonzero e in {0,1}^3
+    tot = 0
+    for e in [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)]:
+        tot += (nx + 1 - e[0]) * (ny + 1 - e[1]) * (nz + 1 - e[2])
+    return tot
+
+
+@pytest.mark.parametrize("nx,ny,N,nnz", [(32, 32, 1089, 7361), (256, 256, 66049, 460289)])
+def test_mesh_counts_2d(nx, ny, N, nnz):
+    p = o.Params(nx=nx, ny=ny)
+    m = o.mesh(p)
+    M, K = o.assemble(m)
+    assert m.coords.shape[0] == N == (nx + 1) * (ny + 1)
+    assert m.elems.shape[0] == 2 * nx * ny
+    assert M.nnz == K.nnz == nnz == N + 2 * edge_count_2d(nx, ny)
+    assert m.bottom.shape[0] == nx and m.top.shape[0] == nx
+
+
+def test_mesh_counts_3d():
+    p = o.Params(dim=3, nx=16, ny=16, nz=4, Lz=0.25)
+    m = o.mesh(p)
+    M, K = o.assemble(m)
+    assert m.coords.shape[0] == 1445 and m.elems.shape[0] == 6 * 16 * 16 * 4
+    assert M.nnz == 18157 == 1445 + 2 * edge_count_3d(16, 16, 4)
+    assert m.bottom.shape[0] == 2 * 16 * 4 and m.top.shape[0] == 2 * 16 * 4
+    # the 3D bench mesh: counts only
+    assert 129 * 129 * 33 == 549153 and 549153 + 2 * edge_count_3d(128, 128, 32) == 8037217
+
+
+def test_mesh_volume_and_conformity():
+    for p in (o.Params(nx=5, ny=3, Lx=10, Ly=2.5), o.Params(dim=3, nx=3, ny=2, nz=4, Lx=10, Ly=2.5, Lz=10)):
+        m = o.mesh(p)
+        vol, _ = o.simplex_measure_and_gradients(m.coords[m.elems])
+        box = p.Lx * p.Ly * (p.Lz if p.dim == 3 else 1.0)
+        assert np.all(vol > 0)
+        assert math.isclose(vol.sum(), box, rel_tol=1e-13)
+        # conforming: every interior facet is shared by exactly two elements
+        d = p.dim
+        faces = np.sort(np.concatenate([np.delete(m.elems, a, axis=1) for a in range(d + 1)]), axis=1)
+        _, counts = np.unique(faces, axis=0, return_counts=True)
+        assert set(counts.tolist()) <= {1, 2}
+
+
+# ---------------------------------------------------------------- element matrices
+def test_element_matrices_right_triangle():
+    h = 0.37
+    X = np.array([[[0, 0], [h, 0], [0, h]]], float)
+    Me, Ke = o.element_matrices(X)
+    Kref = 0.5 * np.array([[2, -1, -1], [-1, 1, 0], [-1, 0, 1]])
+    Mref = h * h / 24 * np.array([[2, 1, 1], [1, 2, 1], [1, 1, 2]])
+    np.testing.assert_allclose(Ke[0], Kref, atol=1e-15)
+    np.testing.assert_allclose(Me[0], Mref, rtol=1e-14)
+
+
+def test_element_stiffness_cotangent_formula():
+    """For any triangle, K_ij = -cot(theta_k)/2 for the angle opposite edge ij."""
+    rng = np.random.default_rng(3)
+    X = rng.random((20, 3, 2))
+    _, Ke = o.element_matrices(X)
+    for e in range(20):
+        for i, j in ((0, 1), (1, 2), (0, 2)):
+            k = 3 - i - j
+            u, v = X[e, i] - X[e, k], X[e, j] - X[e, k]
+            cot = (u @ v) / abs(u[0] * v[1] - u[1] * v[0])
+            assert math.isclose(Ke[e, i, j], -0.5 * cot, rel_tol=1e-10, abs_tol=1e-12)
+
+
+def test_element_matrices_reference_tet():
+    X = np.array([[[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]]], float)
+    Me, Ke = o.element_matrices(X)
+    Kref = np.array([[3, -1, -1, -1], [-1, 1, 0, 0], [-1, 0, 1, 0], [-1, 0, 0, 1]]) / 6
+    Mref = (np.ones((4, 4)) + np.eye(4)) / 120
+    np.testing.assert_allclose(Ke[0], Kref, atol=1e-15)
+    np.testing.assert_allclose(Me[0], Mref, rtol=1e-14)
+
+
+def test_assembled_stencils_2d():
+    """Interior rows: K is the 5-point Laplacian, M is h^2 (1/2 centre, 1/12 on 6 neighbours)."""
+    n = 8
+    h = 1.0 / n
+    m = o.mesh(o.Params(nx=n, ny=n))
+    M, K = o.assemble(m)
+    Kd, Md = K.toarray(), M.toarray()
+    i, j = 3, 4
+    c = i + (n + 1) * j
+    nb = {(1, 0): -1, (-1, 0): -1, (0, 1): -1, (0, -1): -1, (1, 1): 0, (-1, -1): 0}
+    assert math.isclose(Kd[c, c], 4.0, rel_tol=1e-14)
+    for (di, dj), v in nb.items():
+        cc = (i + di) + (n + 1) * (j + dj)
+        assert abs(Kd[c, cc] - v) < 1e-14
+        assert math.isclose(Md[c, cc], h * h / 12, rel_tol=1e-13)
+    assert math.isclose(Md[c, c], h * h / 2, rel_tol=1e-13)
+    assert np.count_nonzero(M.toarray()[c]) == 7
+
+
+def test_assembled_stencils_3d_kuhn():
+    """Interior rows: K = h * 7-point stencil, exact zeros on the 8 other pattern neighbours."""
+    n = 5
+    h = 1.0 / n
+    m = o.mesh(o.Params(dim=3, nx=n, ny=n, nz=n))
+    M, K = o.assemble(m)
+    c = 2 + (n + 1) * (2 + (n + 1) * 2)
+    row = K.getrow(c)
+    assert row.nnz == 15
+    axis = {c + 1, c - 1, c + (n + 1), c - (n + 1), c + (n + 1) ** 2, c - (n + 1) ** 2}
+    for col, v in zip(row.indices, row.data):
+        if col == c:
+            assert math.isclose(v, 6 * h, rel_tol=1e-13)
+        elif col in axis:
+            assert math.isclose(v, -h, rel_tol=1e-13)
+        else:
+            assert abs(v) < 1e-15
+    assert math.isclose(M.getrow(c).sum(), h ** 3, rel_tol=1e-13)
+
+
+@pytest.mark.parametrize("p", [o.Params(nx=7, ny=5, Lx=10, Ly=2.5),
+                               o.Params(dim=3, nx=3, ny=4, nz=2, Lx=1, Ly=2, Lz=0.5)])
+def test_exact_integrals_of_low_degree_polynomials(p):
+    m = o.mesh(p)
+    M, K = o.assemble(m)
+    one = np.ones(M.shape[0])
+    x = m.coords[:, 0]
+    box = p.Lx * p.Ly * (p.Lz if p.dim == 3 else 1.0)
+    np.testing.assert_allclose(K @ one, 0.0, atol=1e-12)          # K 1 = 0
+    assert math.isclose(one @ M @ one, box, rel_tol=1e-13)         # int 1
+    assert math.isclose(x @ M @ one, box * p.Lx / 2, rel_tol=1e-13)  # int x
+    assert math.isclose(x @ M @ x, box * p.Lx ** 2 / 3, rel_tol=1e-13)  # int x^2 (exact: P1 product)
+    assert math.isclose(x @ K @ x, box, rel_tol=1e-12)             # int |grad x|^2
+
+
+def test_wathen_bounds_on_mass_matrix():
+    """eig(D^-1 M) lies in [1/2, 2] for triangles and [1/2, 5/2] for tetrahedra (Wathen 1987)."""
+    for p, hi in ((o.Params(nx=6, ny=5), 2.0), (o.Params(dim=3, nx=3, ny=3, nz=2), 2.5)):
+        M, _ = o.assemble(o.mesh(p))
+        Md = M.toarray()
+        ev = sla.eigh(Md, np.diag(np.diag(Md)), eigvals_only=True)
+        assert ev.min() >= 0.5 - 1e-12 and ev.max() <= hi + 1e-12
+
+
+# ---------------------------------------------------------------- load vectors
+def collapsed_gauss(d, n):
+    """Brute-force rule on the reference simplex: Gauss-Legendre in collapsed (Duffy) coordinates."""
+    g, w = np.polynomial.legendre.leggauss(n)
+    g = 0.5 * (g + 1.0)
+    w = 0.5 * w
+    if d == 1:
+        return g[:, None], w
+    if d == 2:
+        u, v = np.meshgrid(g, g, indexing="ij")
+        wu, wv = np.meshgrid(w, w, indexing="ij")
+        pts = np.c_[u.ravel(), (v * (1 - u)).ravel()]
+        return pts, (wu * wv * (1 - u)).ravel()
+    u, v, t = np.meshgrid(g, g, g, indexing="ij")
+    wu, wv, wt = np.meshgrid(w, w, w, indexing="ij")
+    pts = np.c_[u.ravel(), (v * (1 - u)).ravel(), (t * (1 - u) * (1 - v)).ravel()]
+    return pts, (wu * wv * wt * (1 - u) ** 2 * (1 - v)).ravel()
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_monomial_table_against_quadrature(d):
+    pts, w = collapsed_gauss(d, 6)
+    lam = np.c_[1 - pts.sum(1), pts]                                   # barycentrics at points
+    ref_vol = 1.0 / math.factorial(d)
+    for order in (1, 2, 3, 4):
+        T = o.monomial_table(d, order)
+        for idx in np.ndindex(*T.shape):
+            val = (w * np.prod(lam[:, list(idx)], axis=1)).sum() / ref_vol
+            assert math.isclose(T[idx], val, rel_tol=1e-13)
+
+
+def potential_f(pp, pn):
+    """Eq. (15) written out: f = 3.5 phi_p^2 phi_n^2 + 0.1 phi_s^2 with phi_s = 1 - phi_p - phi_n."""
+    return 3.5 * pp ** 2 * pn ** 2 + 0.1 * (1 - pp - pn) ** 2
+
+
+def fd_derivatives(pp, pn, h=1e-5):
+    fp = (potential_f(pp + h, pn) - potential_f(pp - h, pn)) / (2 * h)
+    fn = (potential_f(pp, pn + h) - potential_f(pp, pn - h)) / (2 * h)
+    return fp, fn
+
+
+def test_dfdphi_is_chain_rule_derivative_of_eq15():
+    rng = np.random.default_rng(0)
+    pp, pn = rng.random(50), rng.random(50)
+    fp, fn = o.dfdphi(pp, pn, "poly")
+    efp, efn = fd_derivatives(pp, pn)
+    np.testing.assert_allclose(fp, efp, atol=1e-9)
+    np.testing.assert_allclose(fn, efn, atol=1e-9)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_load_vector_constant_state(dim):
+    """phi = c everywhere gives F = f'(c) M 1 exactly; f'(c) from finite differences of Eq. (15)."""
+    p = o.Params(dim=dim, nx=4, ny=3, nz=2 if dim == 3 else 0)
+    m = o.mesh(p)
+    M, _ = o.assemble(m)
+    N = M.shape[0]
+    cp, cn = 0.31, 0.27
+    Fp, Fn = o.load_vector(m, np.full(N, cp), np.full(N, cn))
+    efp, efn = fd_derivatives(np.array(cp), np.array(cn))
+    np.testing.assert_allclose(Fp, float(efp) * (M @ np.ones(N)), rtol=1e-8)
+    np.testing.assert_allclose(Fn, float(efn) * (M @ np.ones(N)), rtol=1e-8)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_load_vector_against_brute_force_quadrature(dim):
+    """F_i = int f'(phi_h) lambda_i, recomputed element by element with a high-order Gauss rule."""
+    p = o.Params(dim=dim, nx=3, ny=2, nz=2 if dim == 3 else 0, Lx=2.0, Ly=0.5)
+    m = o.mesh(p)
+    N = m.coords.shape[0]
+    rng = np.random.default_rng(1)
+    pp, pn = rng.random(N) * 0.6, rng.random(N) * 0.6
+    Fp, Fn = o.load_vector(m, pp, pn, "poly")
+    pts, w = collapsed_gauss(dim, 5)
+    lam = np.c_[1 - pts.sum(1), pts]
+    vol, _ = o.simplex_measure_and_gradients(m.coords[m.elems])
+    bp, bn = np.zeros(N), np.zeros(N)
+    for e, el in enumerate(m.elems):
+        php, phn = lam @ pp[el], lam @ pn[el]
+        ph_s = 1 - php - phn
+        gp = 7 * php * phn ** 2 - 0.2 * ph_s
+        gn = 7 * php ** 2 * phn - 0.2 * ph_s
+        jac = vol[e] * math.factorial(dim)
+        for a, node in enumerate(el):
+            bp[node] += jac * (w * gp * lam[:, a]).sum()
+            bn[node] += jac * (w * gn * lam[:, a]).sum()
+    np.testing.assert_allclose(Fp, bp, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(Fn, bn, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_boundary_load_against_brute_force(dim):
+    p = o.Params(dim=dim, nx=3, ny=2, nz=2 if dim == 3 else 0, Lx=2.0, Ly=0.5, Lz=1.5,
+                 h_p=0.3, h_nfa=-0.2, g_p=0.02, g_nfa=0.05)
+    m = o.mesh(p)
+    N = m.coords.shape[0]
+    rng = np.random.default_rng(2)
+    pp, pn = rng.random(N) * 0.6, rng.random(N) * 0.6
+    gp, gn = o.boundary_load(m, pp, pn, p)
+    pts, w = collapsed_gauss(dim - 1, 5)
+    lam = np.c_[1 - pts.sum(1), pts]
+    ep, en = np.zeros(N), np.zeros(N)
+    for facets, kind in ((m.bottom, "b"), (m.top, "t")):
+        for f in facets:
+            X = m.coords[f]
+            meas = np.linalg.norm(X[1] - X[0]) if dim == 2 else 0.5 * np.linalg.norm(np.cross(X[1] - X[0], X[2] - X[0]))
+            jac = meas * math.factorial(dim - 1)
+            php, phn = lam @ pp[f], lam @ pn[f]
+            if kind == "b":
+                vp, vn = p.g_p + 2 * p.h_p * php, p.g_nfa + 2 * p.h_nfa * phn
+            else:
+                solv = 1 - php - phn
+                vp, vn = p.k_evap * php * solv, p.k_evap * phn * solv
+            for a, node in enumerate(f):
+                ep[node] += jac * (w * vp * lam[:, a]).sum()
+                en[node] += jac * (w * vn * lam[:, a]).sum()
+    np.testing.assert_allclose(gp, ep, rtol=1e-12, atol=1e-16)
+    np.testing.assert_allclose(gn, en, rtol=1e-12, atol=1e-16)
+    assert np.all(gp[m.ijk[:, 1] == 1] == 0)   # interior nodes get no boundary load
+
+
+# ---------------------------------------------------------------- the linear system and the step
+def test_saddle_matrix_symmetric():
+    s = o.Solver(o.Params(nx=6, ny=4))
+    d = abs(s.A - s.A.T)
+    assert d.max() <= 1e-15 * abs(s.A).max()
+
+
+def test_dense_and_sparse_lu_agree(monkeypatch):
+    p = o.Params(nx=8, ny=6)
+    s_dense = o.Solver(p)
+    monkeypatch.setattr(o, "DENSE_LIMIT", 0)
+    s_sparse = o.Solver(p)
+    assert s_dense._dense is not None and s_sparse._lu is not None
+    pp, pn = inputs.initial_state(s_dense.N, 0.33, 0.33, seed=3)
+    st = o.initial(s_dense.N, pp, pn)
+    a, b = s_dense.step(st), s_sparse.step(st)
+    for u, v in ((a.phi_p, b.phi_p), (a.mu_p, b.mu_p), (a.phi_nfa, b.phi_nfa), (a.mu_nfa, b.mu_nfa)):
+        np.testing.assert_allclose(u, v, rtol=1e-11, atol=1e-13 * np.abs(v).max())
+
+
+@pytest.mark.parametrize("tau", [1e-7, 1e-5, 1e-4, 1e-2])
+@pytest.mark.parametrize("eps", [1e-4, 1e-3, 1e-1, 10.0])
+def test_lemma1_schur_eigenvalues(tau, eps):
+    """Lemma 1: eig(S~^-1 S) lies in [1/2, 1] for every tau, eps and mesh."""
+    p = o.Params(nx=6, ny=6, tau=tau, eps=eps)
+    M, K = o.assemble(o.mesh(p))
+    S, St = o.schur(M, K, p), o.schur_tilde(M, K, p)
+    S, St = 0.5 * (S + S.T), 0.5 * (St + St.T)
+    ev = sla.eigh(S, St, eigvals_only=True)
+    assert ev.min() >= 0.5 - 1e-9 and ev.max() <= 1.0 + 1e-9
+
+
+def test_lemma1_bound_is_attained_3d():
+    p = o.Params(dim=3, nx=3, ny=3, nz=3, tau=1e-4, eps=1e-3)
+    M, K = o.assemble(o.mesh(p))
+    S, St = o.schur(M, K, p), o.schur_tilde(M, K, p)
+    ev = sla.eigh(0.5 * (S + S.T), 0.5 * (St + St.T), eigvals_only=True)
+    assert ev.min() >= 0.5 - 1e-9 and ev.max() <= 1.0 + 1e-9
+    assert ev.max() > 0.99     # the constant vector (K v = 0) gives exactly 1
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_constant_state_is_fixed_point(dim):
+    p = o.Params(dim=dim, nx=5, ny=4, nz=3 if dim == 3 else 0, bc_mode=0)
+    s = o.Solver(p)
+    c_p, c_n = 0.35, 0.25
+    st = o.initial(s.N, np.full(s.N, c_p), np.full(s.N, c_n))
+    nxt = s.step(st)
+    efp, efn = fd_derivatives(np.array(c_p), np.array(c_n))
+    np.testing.assert_allclose(nxt.phi_p, c_p, rtol=1e-12)
+    np.testing.assert_allclose(nxt.phi_nfa, c_n, rtol=1e-12)
+    np.testing.assert_allclose(nxt.mu_p, float(efp), rtol=1e-7)
+    np.testing.assert_allclose(nxt.mu_nfa, float(efn), rtol=1e-7)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_linear_mode_closed_form(dim):
+    """f' = 0, zero flux: a generalized eigenvector K v = lam M v decays as 1/(1 + tau eps lam^2)."""
+    p = o.Params(dim=dim, nx=6, ny=5, nz=3 if dim == 3 else 0, bc_mode=0, potential="none",
+                 tau=3e-3, eps=2e-2, mobility=1.0)
+    s = o.Solver(p)
+    lam, V = sla.eigh(s.K.toarray(), s.M.toarray())
+    for k in (1, 5, len(lam) // 2, len(lam) - 1):
+        v = V[:, k]
+        st = o.initial(s.N, v, 0.5 * v)
+        nxt = s.step(st)
+        g = 1.0 / (1.0 + p.tau * p.eps * lam[k] ** 2)
+        np.testing.assert_allclose(nxt.phi_p, g * v, atol=1e-12 * np.abs(v).max())
+        np.testing.assert_allclose(nxt.mu_p, p.eps * lam[k] * g * v, atol=1e-10 * max(1.0, lam[k]) * np.abs(v).max())
+        np.testing.assert_allclose(nxt.phi_nfa, 0.5 * g * v, atol=1e-12 * np.abs(v).max())
+
+
+def test_mobility_scales_time():
+    """With mobility m the linear-mode factor is 1/(1 + tau m eps lam^2)."""
+    p = o.Params(nx=5, ny=5, bc_mode=0, potential="none", tau=1e-3, eps=1e-2, mobility=3.0)
+    s = o.Solver(p)
+    lam, V = sla.eigh(s.K.toarray(), s.M.toarray())
+    v = V[:, 4]
+    nxt = s.step(o.initial(s.N, v, v))
+    np.testing.assert_allclose(nxt.phi_p, v / (1 + p.tau * 3.0 * p.eps * lam[4] ** 2), atol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mass_balance(dim):
+    """1^T K = 0, so 1^T M phi^{k+1} - 1^T M phi^k = tau * (total boundary flux); zero with bc_mode=0."""
+    for bc in (0, 1):
+        p = o.Params(dim=dim, nx=6, ny=5, nz=3 if dim == 3 else 0, bc_mode=bc, tau=1e-3)
+        s = o.Solver(p)
+        pp, pn = inputs.initial_state(s.N, 0.35, 0.30, seed=1)
+        st = o.initial(s.N, pp, pn)
+        nxt = s.step(st)
+        gp, gn = o.boundary_load(s.m, pp, pn, p)
+        # total flux written out independently: g |Gamma_b| + k int_{Gamma_t} phi phi_s
+        for phi0, phi1, g in ((pp, nxt.phi_p, gp), (pn, nxt.phi_nfa, gn)):
+            dm = o.mass(s.M, phi1) - o.mass(s.M, phi0)
+            assert math.isclose(dm, p.tau * g.sum(), rel_tol=1e-9, abs_tol=1e-15)
+        if bc == 1:
+            # with constant phi the flux is g * area(Gamma_b) + k c (1 - c_p - c_n) area(Gamma_t)
+            c = o.initial(s.N, np.full(s.N, 0.35), np.full(s.N, 0.30))
+            gpc, _ = o.boundary_load(s.m, c.phi_p, c.phi_nfa, p)
+            area = p.Lx * (p.Lz if dim == 3 else 1.0)
+            assert math.isclose(gpc.sum(), 0.01 * area + 5e-3 * 0.35 * 0.35 * area, rel_tol=1e-13)
+
+
+def test_phi_s_identity():
+    st = o.initial(4, np.array([0.1, 0.2, 0.3, 0.4]), np.array([0.4, 0.3, 0.2, 0.1]))
+    np.testing.assert_array_equal(st.phi_s, 1.0 - st.phi_p - st.phi_nfa)
+
+
+def test_step_matches_eq12_unsplit_form():
+    """The saddle form (14) solves the original pair (12): both residuals vanish."""
+    p = o.Params(nx=6, ny=6)
+    s = o.Solver(p)
+    pp, pn = inputs.initial_state(s.N, 0.33, 0.33, seed=5)
+    st = o.initial(s.N, pp, pn)
+    nxt = s.step(st)
+    Fp, _ = o.load_vector(s.m, pp, pn)
+    gp, _ = o.boundary_load(s.m, pp, pn, p)
+    r1 = s.M @ (nxt.phi_p - pp) / p.tau + s.K @ nxt.mu_p - gp
+    r2 = s.M @ nxt.mu_p - Fp - p.eps * (s.K @ nxt.phi_p)
+    assert np.abs(r1).max() < 1e-9 * np.abs(s.M @ pp / p.tau).max()
+    assert np.abs(r2).max() < 1e-9 * np.abs(Fp).max()
