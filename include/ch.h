@@ -1,0 +1,197 @@
+/*
+ * ch.h -- C ABI of the GB300 solver for the per-time-step saddle-point systems of
+ * the ternary Cahn-Hilliard model of Bergermann, Stoll et al., "Preconditioning for
+ * a Phase-Field Model with Application to Morphology Evolution in Organic
+ * Semiconductors" (arXiv 2204.03575).
+ *
+ * The model (Section 2) evolves the polymer and NFA volume fractions phi_p, phi_nfa
+ * with phi_s = 1 - phi_p - phi_nfa (Eq. (2)).  P1 finite elements and the
+ * semi-implicit scheme of Eq. (12) give, per time step and per species, the
+ * symmetric saddle-point system of Eq. (14)
+ *
+ *     [ M     a K ] [phi^{k+1}]   [ M phi^k + tau g_bd ]
+ *     [ a K  -c M ] [ mu^{k+1}] = [ -c f^{k}           ],   a = tau*mob, c = a/eps,
+ *
+ * with the same matrix for both species.  It is solved by flexible GMRES (FP64)
+ * right-preconditioned by Algorithm 1 (block-diagonal: AMG for M, and the matching
+ * Schur-complement approximation S~ = H M^-1 H with H = a K + sqrt(c) M, Section 3).
+ *
+ * Conventions (all entry points):
+ *  - Every pointer argument named as a vector is a DEVICE pointer owned by the caller,
+ *    unless the comment says "host".  Work is enqueued on the caller's CUDA stream
+ *    (`stream` is a cudaStream_t; NULL = legacy default stream).  Entry points that
+ *    return data to host memory (stats, info) synchronise that stream.
+ *  - Opaque handles are created and owned by the library and released with the
+ *    matching *_destroy call (NULL is accepted and ignored).  A handle created from
+ *    another (system from mesh, preconditioner from system, state from both) borrows
+ *    it: the borrowed handle must outlive the borrower.
+ *  - Node-major vectors: index i is the node number i + (nx+1)(j + (ny+1)k) of the
+ *    grid point (i,j,k).  "N x 4" vectors store, per node, the four unknowns of the
+ *    two systems as (phi_p, phi_nfa, mu_p, mu_nfa) -- the first block of both
+ *    species, then the second block of both species.
+ *  - Errors come back only as return codes; ch_last_error() gives a message for the
+ *    calling thread.  No entry point aborts or throws.  A handle stays valid after an
+ *    error return unless the code is CH_ERR_CUDA (the CUDA context may be unusable).
+ *  - Handles are not thread-safe: one thread at a time per handle.
+ */
+#ifndef CH_H
+#define CH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CH_OK = 0,
+  CH_ERR_ARG = 1,            /* invalid argument (NULL handle, bad size or parameter) */
+  CH_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  CH_ERR_OOM = 3,            /* device allocation failed */
+  CH_ERR_NOT_CONVERGED = 4,  /* FGMRES hit max_iter; the best iterate is still written */
+  CH_ERR_BREAKDOWN = 5,      /* Krylov breakdown before convergence */
+  CH_ERR_NONFINITE = 6,      /* NaN/Inf met in a residual norm or the right-hand side */
+  CH_ERR_STATE = 7,          /* call out of order (e.g. step before the state was set) */
+  CH_ERR_INTERNAL = 8        /* a device-side capacity or consistency check failed */
+} ch_status;
+
+/* Parameters.  ch_params_default() fills the paper's values (Section 4; Fig. 1 caption). */
+typedef struct ch_params {
+  int32_t dim;               /* 2 (triangles) or 3 (Kuhn tetrahedra) */
+  int32_t nx, ny, nz;        /* cells per axis; nz ignored in 2D.  y is the film height */
+  double Lx, Ly, Lz;         /* box [0,Lx]x[0,Ly](x[0,Lz]) */
+  double tau;                /* time step (scaled), default 1e-4 */
+  double eps;                /* interface parameter eps_p = eps_nfa, default 1e-3 */
+  double mobility;           /* M_p = M_nfa, default 1 */
+  int32_t bc_mode;           /* 0: zero flux on the whole boundary; 1: Eq. (10) fluxes */
+  int32_t evap_sign;         /* +1: evaporation adds polymer/NFA at y=Ly (text); -1: Eq. (10) literally */
+  int32_t potential;         /* 0: f of Eq. (15), chain rule through phi_s; 1: without the phi_s term; 2: f' = 0 */
+  int32_t precision;         /* 0: FP64 everywhere; 1: FP32 AMG V-cycles inside FP64 FGMRES */
+  double k_evap;             /* evaporation rate k, default 5e-3 */
+  double g_p, g_nfa;         /* substrate energy g of Eq. (5), default 0.01 */
+  double h_p, h_nfa;         /* substrate energy h of Eq. (5), default 0 */
+  double rtol;               /* stop when ||b - A x||_2 <= rtol ||b||_2 per species, default 1e-8 */
+  int32_t restart;           /* FGMRES restart length m (1..64), default 30 */
+  int32_t max_iter;          /* total FGMRES iterations per step, default 300 */
+  int32_t cheb_degree;       /* Chebyshev smoothing steps before and after coarse correction, default 2 */
+  int32_t coarse_max;        /* AMG: coarsest level is solved densely at or below this size, default 256 */
+  double amg_theta;          /* AMG strength threshold, default 0.08 */
+  int32_t vcycles_M;         /* V-cycles per application of M~^-1 (Algorithm 1, step 1), default 1 */
+  int32_t vcycles_H;         /* V-cycles per application of H~^-1 (Algorithm 1, steps 2 and 4), default 1 */
+} ch_params;
+
+/* Per-step statistics (host struct). */
+typedef struct ch_step_stats {
+  int32_t iters[2];          /* FGMRES iterations (polymer, NFA) */
+  int32_t restarts;          /* restart cycles used */
+  int32_t status;            /* ch_status of this step */
+  double relres[2];          /* true final ||b - A x|| / ||b|| per species, FP64 */
+  double mass[2];            /* int phi_h = 1^T M phi^{k+1} per species */
+  double ms;                 /* wall time of the step (ms, CUDA events) */
+} ch_step_stats;
+
+typedef struct ch_mesh_s ch_mesh_t;
+typedef struct ch_system_s ch_system_t;
+typedef struct ch_precond_s ch_precond_t;
+typedef struct ch_state_s ch_state_t;
+
+const char* ch_status_str(ch_status s);
+const char* ch_last_error(void);
+void ch_params_default(ch_params* p);
+
+/* ---------------------------------------------------------------- mesh (Section 4)
+ * Uniform simplicial mesh of the box: 2 triangles per cell (diagonal from (i,j) to
+ * (i+1,j+1)) or the 6 Kuhn tetrahedra per hexahedron.  Gamma_b = {y = 0} (substrate),
+ * Gamma_t = {y = Ly} (evaporation).  Built on the device. */
+ch_status ch_mesh(const ch_params* p, void* stream, ch_mesh_t** out);
+/* host outputs, any may be NULL */
+ch_status ch_mesh_info(const ch_mesh_t* m, int64_t* n_nodes, int64_t* n_elems,
+                       int64_t* n_bottom, int64_t* n_top);
+/* copies to caller device buffers: coords N x dim (fp64), elems E x (dim+1), facets F x dim (int32); any may be NULL */
+ch_status ch_mesh_copy(const ch_mesh_t* m, double* coords, int32_t* elems, int32_t* bottom,
+                       int32_t* top, void* stream);
+void ch_mesh_destroy(ch_mesh_t* m);
+
+/* ---------------------------------------------------------------- assembly (Section 3)
+ * P1 mass M and stiffness K ("standard ... with appropriate constants", below Eq. (12)) in
+ * one shared CSR pattern (sorted column indices), and H = a K + sqrt(c) M, on the device. */
+ch_status ch_assemble(const ch_mesh_t* m, const ch_params* p, void* stream, ch_system_t** out);
+ch_status ch_system_info(const ch_system_t* s, int64_t* n, int64_t* nnz);   /* host outputs */
+/* copies to caller device buffers (rowptr N+1, col nnz int32; values nnz fp64); any may be NULL */
+ch_status ch_system_copy(const ch_system_t* s, int32_t* rowptr, int32_t* col, double* valM,
+                         double* valK, double* valH, void* stream);
+void ch_system_destroy(ch_system_t* s);
+
+/* Explicit loads of one step (Eq. (12), right-hand sides): F_s[i] = int f_s'(phi_h) lambda_i,
+ * exact for the polynomial potential Eq. (15), and the boundary loads g_s of the flux
+ * conditions Eq. (10).  Inputs N fp64; outputs N fp64 (any output may be NULL). */
+ch_status ch_loads(const ch_system_t* s, const double* phi_p, const double* phi_nfa,
+                   double* F_p, double* F_nfa, double* g_p, double* g_nfa, void* stream);
+/* Right-hand sides of Eq. (14) for both species, b (N x 4) = (M phi_p + tau g_p, M phi_nfa + tau g_nfa,
+ * -c F_p, -c F_nfa) per node. */
+ch_status ch_rhs(const ch_system_t* s, const double* phi_p, const double* phi_nfa, double* b,
+                 void* stream);
+/* y = A x for both species at once (Eq. (14)); x, y are N x 4 fp64, must not alias. */
+ch_status ch_apply_A(const ch_system_t* s, const double* x, double* y, void* stream);
+
+/* ---------------------------------------------------------------- preconditioner (Algorithm 1)
+ * Builds, on the device, smoothed-aggregation AMG hierarchies for M and H (strength of
+ * connection, MIS(2) aggregation, Jacobi-smoothed prolongator, Galerkin coarse operators,
+ * dense inverse of the coarsest level), Chebyshev smoother bounds per level and, when
+ * precision = 1, FP32 copies of every level. */
+ch_status ch_precond_setup(const ch_system_t* s, void* stream, ch_precond_t** out);
+/* which: 0 = M hierarchy, 1 = H hierarchy.  Host outputs; level-wise sizes for level < nlevels. */
+ch_status ch_precond_info(const ch_precond_t* pc, int32_t which, int32_t level, int32_t* nlevels,
+                          int64_t* rows, int64_t* nnz);
+/* Algorithm 1 on both species: w_1 ~ M^-1 v_1 and w_2 ~ H^-1 M H^-1 v_2 (AMG V-cycles).
+ * v, w: N x 4 fp64, must not alias. */
+ch_status ch_precond_apply(ch_precond_t* pc, const double* v, double* w, void* stream);
+/* vcycles V-cycles (zero initial guess) on M (which = 0) or H (which = 1) for two right-hand
+ * sides stored N x 2 (fp64): x ~ A^-1 b.  b, x must not alias. */
+ch_status ch_vcycle(ch_precond_t* pc, int32_t which, int32_t vcycles, const double* b, double* x,
+                    void* stream);
+void ch_precond_destroy(ch_precond_t* pc);
+
+/* ---------------------------------------------------------------- time stepping (Eq. (12)-(14))
+ * A state holds (phi_p, phi_nfa, mu_p, mu_nfa) on the device plus all FGMRES work space, so
+ * ch_step allocates nothing. */
+ch_status ch_state_create(const ch_system_t* s, ch_precond_t* pc, void* stream, ch_state_t** out);
+/* Set the state from caller device buffers (N fp64 each); mu_* may be NULL (zero). */
+ch_status ch_state_set(ch_state_t* st, const double* phi_p, const double* phi_nfa,
+                       const double* mu_p, const double* mu_nfa, void* stream);
+/* Seeded initial state (Section 4): phi = base + noise (2u - 1), u from SplitMix64 on the counter
+ * seed ^ (field << 40) ^ node, field 0 = polymer, 1 = NFA; mu = 0. */
+ch_status ch_state_init_seeded(ch_state_t* st, double phi_p0, double phi_nfa0, double noise,
+                               uint64_t seed, void* stream);
+/* Copy fields to caller device buffers (N fp64 each); any may be NULL.  phi_s = 1 - phi_p - phi_nfa. */
+ch_status ch_state_get(const ch_state_t* st, double* phi_p, double* phi_nfa, double* phi_s,
+                       double* mu_p, double* mu_nfa, void* stream);
+/* One time step: loads, right-hand sides, FGMRES + Algorithm 1 for both species with the
+ * previous step as initial guess, state update.  stats (host) may be NULL.  On
+ * CH_ERR_NOT_CONVERGED the best iterate is stored in the state. */
+ch_status ch_step(ch_state_t* st, void* stream, ch_step_stats* stats);
+/* nsteps steps; per_step (host, nsteps entries) may be NULL.  Stops at the first error. */
+ch_status ch_run(ch_state_t* st, int32_t nsteps, void* stream, ch_step_stats* per_step);
+void ch_state_destroy(ch_state_t* st);
+
+/* ---------------------------------------------------------------- launch accounting
+ * Every kernel launch of the library is counted per kernel and working precision, with the
+ * algorithmic bytes (each operand once) and FMAs of that launch.  With timing on, CUDA events
+ * are recorded around each launch on its stream and the elapsed times summed (adds a small
+ * host overhead per launch).  Process-wide; thread-safe. */
+typedef struct ch_prof_entry {
+  char name[40];             /* kernel name and precision, e.g. "cheb_step_f32" */
+  int64_t launches;
+  double ms;                 /* summed event time (0 unless timing was on) */
+  double bytes;              /* summed algorithmic bytes */
+  double fmas;               /* summed fused multiply-adds */
+} ch_prof_entry;
+ch_status ch_profile_enable(int32_t on);
+/* Waits for pending events, then copies up to cap entries (host array) and sets *n to the
+ * number of kernels seen; out may be NULL to query n.  reset != 0 clears the counters. */
+ch_status ch_profile_read(ch_prof_entry* out, int32_t cap, int32_t* n, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CH_H */

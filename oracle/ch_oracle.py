@@ -366,3 +366,19 @@ def initial(n_nodes: int, phi_p: np.ndarray, phi_nfa: np.ndarray) -> State:
     """Initial state from given nodal fractions; mu^0 = 0 (mu^0 never enters b)."""
     return State(np.asarray(phi_p, float).copy(), np.asarray(phi_nfa, float).copy(),
                  np.zeros(n_nodes), np.zeros(n_nodes))
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 1 with exact inner solves (the ideal form of the preconditioner)
+# ----------------------------------------------------------------------------
+def algorithm1_exact(M, K, p: Params, v1: np.ndarray, v2: np.ndarray):
+    """Prec(v) of Algorithm 1 with every "approximately solve" replaced by an exact solve:
+    w1 = M^-1 v1;  w2 = H^-1 v2;  w2 <- M w2;  w2 = H^-1 w2, with H = a K + sqrt(c) M.
+    v1, v2 may be (N,) or (N, r)."""
+    a, c = coefficients(p)
+    H = (a * K + math.sqrt(c) * M).tocsc()
+    w1 = spla.spsolve(M.tocsc(), v1)
+    w2 = spla.spsolve(H, v2)
+    w2 = M @ w2
+    w2 = spla.spsolve(H, w2)
+    return w1, w2

@@ -1,0 +1,318 @@
+"""Python binding of libch.so (include/ch.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module passes torch device
+pointers and the current CUDA stream through ctypes and turns status codes into
+exceptions.  The library must have been built (``python -m
+paper_2204_03575_gb300.build``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libch.so")
+
+_lib = None
+
+
+class ChError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status} ({STATUS.get(status, '?')}): {message}")
+        self.status = status
+
+
+STATUS = {0: "CH_OK", 1: "CH_ERR_ARG", 2: "CH_ERR_CUDA", 3: "CH_ERR_OOM", 4: "CH_ERR_NOT_CONVERGED",
+          5: "CH_ERR_BREAKDOWN", 6: "CH_ERR_NONFINITE", 7: "CH_ERR_STATE", 8: "CH_ERR_INTERNAL"}
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE, ERR_STATE, ERR_INTERNAL = range(9)
+
+
+class Params(ctypes.Structure):
+    """Mirror of ch_params."""
+    _fields_ = [
+        ("dim", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+        ("tau", ctypes.c_double), ("eps", ctypes.c_double), ("mobility", ctypes.c_double),
+        ("bc_mode", ctypes.c_int32), ("evap_sign", ctypes.c_int32), ("potential", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("k_evap", ctypes.c_double), ("g_p", ctypes.c_double), ("g_nfa", ctypes.c_double),
+        ("h_p", ctypes.c_double), ("h_nfa", ctypes.c_double), ("rtol", ctypes.c_double),
+        ("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("cheb_degree", ctypes.c_int32),
+        ("coarse_max", ctypes.c_int32), ("amg_theta", ctypes.c_double),
+        ("vcycles_M", ctypes.c_int32), ("vcycles_H", ctypes.c_int32),
+    ]
+
+    def __init__(self, **kw):
+        super().__init__()
+        lib().ch_params_default(ctypes.byref(self))
+        for k, v in kw.items():
+            if k not in dict(self._fields_):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(self, k, v)
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class StepStats(ctypes.Structure):
+    """Mirror of ch_step_stats."""
+    _fields_ = [("iters", ctypes.c_int32 * 2), ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("relres", ctypes.c_double * 2), ("mass", ctypes.c_double * 2), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iters": list(self.iters), "restarts": self.restarts, "status": self.status,
+                "relres": list(self.relres), "mass": list(self.mass), "ms": self.ms}
+
+
+class ProfEntry(ctypes.Structure):
+    """Mirror of ch_prof_entry."""
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("fmas", ctypes.c_double)]
+
+
+_VP = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+
+_SIGNATURES = {
+    "ch_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "ch_last_error": (ctypes.c_char_p, []),
+    "ch_params_default": (None, [ctypes.POINTER(Params)]),
+    "ch_mesh": (ctypes.c_int, [ctypes.POINTER(Params), _VP, ctypes.POINTER(_VP)]),
+    "ch_mesh_info": (ctypes.c_int, [_VP, _I64P, _I64P, _I64P, _I64P]),
+    "ch_mesh_copy": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "ch_mesh_destroy": (None, [_VP]),
+    "ch_assemble": (ctypes.c_int, [_VP, ctypes.POINTER(Params), _VP, ctypes.POINTER(_VP)]),
+    "ch_system_info": (ctypes.c_int, [_VP, _I64P, _I64P]),
+    "ch_system_copy": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ch_system_destroy": (None, [_VP]),
+    "ch_loads": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ch_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "ch_apply_A": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ch_precond_setup": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_VP)]),
+    "ch_precond_info": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _I32P, _I64P, _I64P]),
+    "ch_precond_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ch_vcycle": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
+    "ch_precond_destroy": (None, [_VP]),
+    "ch_state_create": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(_VP)]),
+    "ch_state_set": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "ch_state_init_seeded": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_uint64, _VP]),
+    "ch_state_get": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ch_step": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(StepStats)]),
+    "ch_run": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.POINTER(StepStats)]),
+    "ch_state_destroy": (None, [_VP]),
+    "ch_profile_enable": (ctypes.c_int, [ctypes.c_int32]),
+    "ch_profile_read": (ctypes.c_int, [ctypes.POINTER(ProfEntry), ctypes.c_int32, _I32P, ctypes.c_int32]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libch.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2204_03575_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        msg = lib().ch_last_error().decode(errors="replace")
+        raise ChError(status, where, msg)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f64(t, n=None, cols=None):
+    if t.dtype != torch.float64 or not t.is_cuda:
+        raise ValueError("expected a float64 CUDA tensor")
+    t = t.contiguous()
+    if n is not None and t.shape[0] != n:
+        raise ValueError(f"expected {n} rows, got {t.shape[0]}")
+    return t
+
+
+class Mesh:
+    def __init__(self, params: Params, stream=None):
+        self.params = params
+        self._h = _VP()
+        _check(lib().ch_mesh(ctypes.byref(params), _stream(stream), ctypes.byref(self._h)), "ch_mesh")
+        n, e, fb, ft = (ctypes.c_int64() for _ in range(4))
+        _check(lib().ch_mesh_info(self._h, ctypes.byref(n), ctypes.byref(e), ctypes.byref(fb),
+                                  ctypes.byref(ft)), "ch_mesh_info")
+        self.n_nodes, self.n_elems, self.n_bottom, self.n_top = n.value, e.value, fb.value, ft.value
+        self.dim = params.dim
+
+    def copy(self, stream=None):
+        d = self.dim
+        dev = torch.device("cuda")
+        coords = torch.empty(self.n_nodes, d, dtype=torch.float64, device=dev)
+        elems = torch.empty(self.n_elems, d + 1, dtype=torch.int32, device=dev)
+        bot = torch.empty(self.n_bottom, d, dtype=torch.int32, device=dev)
+        top = torch.empty(self.n_top, d, dtype=torch.int32, device=dev)
+        _check(lib().ch_mesh_copy(self._h, _ptr(coords), _ptr(elems), _ptr(bot), _ptr(top), _stream(stream)),
+               "ch_mesh_copy")
+        return coords, elems, bot, top
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ch_mesh_destroy(self._h)
+            self._h = None
+
+
+class System:
+    def __init__(self, mesh: Mesh, params: Params | None = None, stream=None):
+        self.mesh = mesh  # keeps the borrowed mesh alive
+        self.params = params if params is not None else mesh.params
+        self._h = _VP()
+        _check(lib().ch_assemble(mesh._h, ctypes.byref(self.params), _stream(stream), ctypes.byref(self._h)),
+               "ch_assemble")
+        n, nnz = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().ch_system_info(self._h, ctypes.byref(n), ctypes.byref(nnz)), "ch_system_info")
+        self.n, self.nnz = n.value, nnz.value
+
+    def csr(self, stream=None):
+        dev = torch.device("cuda")
+        rowptr = torch.empty(self.n + 1, dtype=torch.int32, device=dev)
+        col = torch.empty(self.nnz, dtype=torch.int32, device=dev)
+        vm, vk, vh = (torch.empty(self.nnz, dtype=torch.float64, device=dev) for _ in range(3))
+        _check(lib().ch_system_copy(self._h, _ptr(rowptr), _ptr(col), _ptr(vm), _ptr(vk), _ptr(vh),
+                                    _stream(stream)), "ch_system_copy")
+        return rowptr, col, vm, vk, vh
+
+    def loads(self, phi_p, phi_nfa, stream=None):
+        pp, pn = _f64(phi_p, self.n), _f64(phi_nfa, self.n)
+        out = [torch.empty(self.n, dtype=torch.float64, device=pp.device) for _ in range(4)]
+        _check(lib().ch_loads(self._h, _ptr(pp), _ptr(pn), *[_ptr(o) for o in out], _stream(stream)), "ch_loads")
+        return out
+
+    def rhs(self, phi_p, phi_nfa, stream=None):
+        pp, pn = _f64(phi_p, self.n), _f64(phi_nfa, self.n)
+        b = torch.empty(self.n, 4, dtype=torch.float64, device=pp.device)
+        _check(lib().ch_rhs(self._h, _ptr(pp), _ptr(pn), _ptr(b), _stream(stream)), "ch_rhs")
+        return b
+
+    def apply_A(self, x, stream=None):
+        x = _f64(x, self.n)
+        y = torch.empty_like(x)
+        _check(lib().ch_apply_A(self._h, _ptr(x), _ptr(y), _stream(stream)), "ch_apply_A")
+        return y
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ch_system_destroy(self._h)
+            self._h = None
+
+
+class Precond:
+    def __init__(self, system: System, stream=None):
+        self.system = system
+        self._h = _VP()
+        _check(lib().ch_precond_setup(system._h, _stream(stream), ctypes.byref(self._h)), "ch_precond_setup")
+
+    def levels(self, which: int):
+        nl = ctypes.c_int32()
+        _check(lib().ch_precond_info(self._h, which, 0, ctypes.byref(nl), None, None), "ch_precond_info")
+        out = []
+        for l in range(nl.value):
+            r, z = ctypes.c_int64(), ctypes.c_int64()
+            _check(lib().ch_precond_info(self._h, which, l, None, ctypes.byref(r), ctypes.byref(z)),
+                   "ch_precond_info")
+            out.append((r.value, z.value))
+        return out
+
+    def apply(self, v, stream=None):
+        v = _f64(v, self.system.n)
+        w = torch.empty_like(v)
+        _check(lib().ch_precond_apply(self._h, _ptr(v), _ptr(w), _stream(stream)), "ch_precond_apply")
+        return w
+
+    def vcycle(self, which: int, b, vcycles: int = 1, stream=None):
+        b = _f64(b, self.system.n)
+        x = torch.empty_like(b)
+        _check(lib().ch_vcycle(self._h, which, vcycles, _ptr(b), _ptr(x), _stream(stream)), "ch_vcycle")
+        return x
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ch_precond_destroy(self._h)
+            self._h = None
+
+
+class State:
+    def __init__(self, system: System, precond: Precond, stream=None):
+        self.system, self.precond = system, precond
+        self._h = _VP()
+        _check(lib().ch_state_create(system._h, precond._h, _stream(stream), ctypes.byref(self._h)),
+               "ch_state_create")
+
+    def set(self, phi_p, phi_nfa, mu_p=None, mu_nfa=None, stream=None):
+        n = self.system.n
+        ts = [_f64(t, n) if t is not None else None for t in (phi_p, phi_nfa, mu_p, mu_nfa)]
+        _check(lib().ch_state_set(self._h, *[_ptr(t) for t in ts], _stream(stream)), "ch_state_set")
+
+    def init_seeded(self, phi_p0, phi_nfa0, noise=0.01, seed=0, stream=None):
+        _check(lib().ch_state_init_seeded(self._h, phi_p0, phi_nfa0, noise, seed, _stream(stream)),
+               "ch_state_init_seeded")
+
+    def get(self, stream=None):
+        n = self.system.n
+        out = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(5)]
+        _check(lib().ch_state_get(self._h, *[_ptr(o) for o in out], _stream(stream)), "ch_state_get")
+        return dict(zip(("phi_p", "phi_nfa", "phi_s", "mu_p", "mu_nfa"), out))
+
+    def step(self, stream=None, check=True):
+        st = StepStats()
+        status = lib().ch_step(self._h, _stream(stream), ctypes.byref(st))
+        if check:
+            _check(status, "ch_step")
+        return st.as_dict()
+
+    def run(self, nsteps: int, stream=None):
+        arr = (StepStats * max(nsteps, 1))()
+        _check(lib().ch_run(self._h, nsteps, _stream(stream), arr), "ch_run")
+        return [arr[k].as_dict() for k in range(nsteps)]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ch_state_destroy(self._h)
+            self._h = None
+
+
+def profile_enable(on: bool):
+    """Turn per-launch CUDA-event timing on or off (launch counts are always kept)."""
+    _check(lib().ch_profile_enable(1 if on else 0), "ch_profile_enable")
+
+
+def profile_read(reset: bool = False):
+    """{kernel name: {launches, ms, bytes, fmas}} accumulated since the last reset."""
+    n = ctypes.c_int32()
+    _check(lib().ch_profile_read(None, 0, ctypes.byref(n), 0), "ch_profile_read")
+    arr = (ProfEntry * max(n.value, 1))()
+    _check(lib().ch_profile_read(arr, n.value, ctypes.byref(n), 1 if reset else 0), "ch_profile_read")
+    return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes,
+                                   "fmas": arr[i].fmas} for i in range(n.value)}

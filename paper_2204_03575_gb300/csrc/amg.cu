@@ -1,0 +1,839 @@
+// Algebraic multigrid for the inner solves of Algorithm 1 (M~ ~ M and H = aK + sqrt(c)M).
+//
+// The paper uses Ruge-Stueben AMG from a CPU library (Section 4).  Here the hierarchy is
+// built on the device by smoothed aggregation (Vanek, Mandel, Brezina 1996) with MIS(2)
+// aggregates found by the parallel maximal-independent-set method of Bell, Dalton and
+// Olson (2012):
+//   strength  |a_ij| >= theta sqrt(a_ii a_jj), plus each row's strongest entry, symmetrised;
+//   MIS(2)    random-priority independent set at graph distance 2, roots become aggregates;
+//   P         (I - omega D^-1 A) T with T the aggregate indicator, omega = 4/(3 rho),
+//             rho the Gershgorin bound of D^-1 A;
+//   A_c       = P^T A P (deterministic sparse products), down to <= coarse_max rows, whose
+//             dense inverse is formed on the device.
+// Smoothing is Chebyshev on D^-1 A over [0.3, 1.1] * rho.  Every set-up sum has a fixed
+// order, so the hierarchy is bitwise reproducible.  V-cycles run in FP64 or FP32 on two
+// right-hand sides at once (the two species share M and H).
+#include <cmath>
+#include <type_traits>
+
+#include "ch_internal.cuh"
+
+namespace ch {
+
+template <typename T> struct V2T;
+template <> struct V2T<double> { using t = double2; };
+template <> struct V2T<float> { using t = float2; };
+
+template <typename T>
+struct LevelT {
+  Csr<T> A, P, R;
+  T* dinv = nullptr;
+  typename V2T<T>::t *x = nullptr, *x2 = nullptr, *d = nullptr, *r = nullptr, *b = nullptr;
+};
+
+struct Hierarchy {
+  int precision = 0;
+  int nlev = 0;
+  std::vector<Csr<double>> A, P, R;  // FP64 set-up results
+  std::vector<double*> dinv;
+  std::vector<double> rho;            // Gershgorin bound of D^-1 A per level
+  std::vector<LevelT<double>> Ld;     // working copies (precision 0)
+  std::vector<LevelT<float>> Lf;      // working copies (precision 1)
+  int nc = 0;                         // coarsest size
+  double* cinv = nullptr;             // nc x nc dense inverse (FP64)
+  float* cinvf = nullptr;
+  int cheb_degree = 2;
+  Alloc mem;
+};
+
+// ---------------------------------------------------------------- set-up kernels
+__global__ void k_diag_gersh(Csr<double> A, double* dinv, double* rowbound) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nrows) return;
+  double d = 0.0, s = 0.0;
+  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+    if (A.col[q] == i) d = A.val[q];
+    s += fabs(A.val[q]);
+  }
+  dinv[i] = 1.0 / d;
+  rowbound[i] = s / fabs(d);
+}
+
+__global__ void k_max_reduce(const double* v, int n, double* out) {
+  __shared__ double sm[TPB];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, v[i]);
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sm[0];
+}
+
+__global__ void k_strength(Csr<double> A, const double* dinv, double theta, uint8_t* s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nrows) return;
+  const double di = fabs(1.0 / dinv[i]);
+  double mx = 0.0;
+  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+    const int j = A.col[q];
+    if (j == i) continue;
+    mx = fmax(mx, fabs(A.val[q]) / sqrt(di * fabs(1.0 / dinv[j])));
+  }
+  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+    const int j = A.col[q];
+    uint8_t st = 0;
+    if (j != i) {
+      const double nrm = fabs(A.val[q]) / sqrt(di * fabs(1.0 / dinv[j]));
+      st = (nrm >= theta || (mx > 0.0 && nrm >= mx)) ? 1 : 0;
+    }
+    s[q] = st;
+  }
+}
+
+__device__ __forceinline__ int find_in_row(const int* col, int b, int e, int c) {
+  while (b < e) {
+    const int m = (b + e) >> 1;
+    if (col[m] < c) b = m + 1;
+    else e = m;
+  }
+  return b;
+}
+
+// s2_ij = s_ij or s_ji (A has a symmetric pattern)
+__global__ void k_strength_sym(Csr<double> A, const uint8_t* s, uint8_t* s2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nrows) return;
+  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+    const int j = A.col[q];
+    uint8_t v = s[q];
+    if (!v && j != i) {
+      const int p = find_in_row(A.col, A.rowptr[j], A.rowptr[j + 1], i);
+      if (p < A.rowptr[j + 1] && A.col[p] == i) v = s[p];
+    }
+    s2[q] = v;
+  }
+}
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {  // integer hash (avalanche mixer)
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+// key = state (2 bits) | hash (32 bits) | index (30 bits); state 2 = in, 1 = undecided, 0 = out
+__device__ __forceinline__ uint64_t mis_key(int state, int i) {
+  return ((uint64_t)state << 62) | ((uint64_t)hash32((uint32_t)i) << 30) | (uint64_t)i;
+}
+
+__global__ void k_mis_keys(int n, const int8_t* state, uint64_t* key) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) key[i] = mis_key(state[i], i);
+}
+
+__global__ void k_strong_max(Csr<double> A, const uint8_t* s, const uint64_t* in, uint64_t* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nrows) return;
+  uint64_t m = in[i];
+  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q)
+    if (s[q]) {
+      const uint64_t v = in[A.col[q]];
+      m = v > m ? v : m;
+    }
+  out[i] = m;
+}
+
+__global__ void k_mis_update(int n, const uint64_t* key, const uint64_t* m2, int8_t* state,
+                             int* undecided) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || state[i] != 1) return;
+  if (m2[i] == key[i]) state[i] = 2;
+  else if ((m2[i] >> 62) == 2) state[i] = 0;
+  else atomicAdd(undecided, 1);
+}
+
+__global__ void k_roots(int n, const int8_t* state, int* isroot) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) isroot[i] = state[i] == 2 ? 1 : 0;
+}
+
+// pass 1: roots own aggregate id (scan of isroot); other nodes join the strongest-key
+// neighbouring root.  pass >= 2: unassigned nodes join the aggregate of the max-key
+// assigned neighbour (reading the previous pass only).
+__global__ void k_agg_pass(Csr<double> A, const uint8_t* s, const int* isroot, const int* rootid,
+                           const int* agg_in, int* agg_out, int first, int* unassigned) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nrows) return;
+  if (first) {
+    if (isroot[i]) {
+      agg_out[i] = rootid[i];
+      return;
+    }
+  } else if (agg_in[i] >= 0) {
+    agg_out[i] = agg_in[i];
+    return;
+  }
+  uint64_t best = 0;
+  int bj = -1;
+  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+    if (!s[q]) continue;
+    const int j = A.col[q];
+    const bool ok = first ? (isroot[j] != 0) : (agg_in[j] >= 0);
+    if (!ok) continue;
+    const uint64_t k = mis_key(0, j);
+    if (bj < 0 || k > best) {
+      best = k;
+      bj = j;
+    }
+  }
+  if (bj >= 0) agg_out[i] = first ? rootid[bj] : agg_in[bj];
+  else {
+    agg_out[i] = -1;
+    atomicAdd(unassigned, 1);
+  }
+}
+
+// P row i = sum_j (delta_ij - omega a_ij / a_ii) e_{agg(j)}: sort (agg, coef) pairs of row i
+// by aggregate (stable insertion sort in a scratch laid out like A) and merge duplicates.
+template <bool FILL>
+__global__ void k_prolong(Csr<double> A, const double* dinv, const int* agg, double omega,
+                          int* skey, double* sval, int* cnt, const int* pptr, int* pcol,
+                          double* pval) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nrows) return;
+  const int b = A.rowptr[i], e = A.rowptr[i + 1];
+  for (int q = b; q < e; ++q) {
+    const int j = A.col[q];
+    const int k = agg[j];
+    const double c = (j == i ? 1.0 : 0.0) - omega * A.val[q] * dinv[i];
+    int t = q - 1;
+    while (t >= b && skey[t] > k) {
+      skey[t + 1] = skey[t];
+      sval[t + 1] = sval[t];
+      --t;
+    }
+    skey[t + 1] = k;
+    sval[t + 1] = c;
+  }
+  int out = FILL ? pptr[i] : 0, n = 0;
+  for (int q = b; q < e; ++q) {
+    if (q == b || skey[q] != skey[q - 1]) {
+      if (FILL) {
+        pcol[out + n] = skey[q];
+        pval[out + n] = sval[q];
+      }
+      ++n;
+    } else if (FILL) {
+      pval[out + n - 1] += sval[q];
+    }
+  }
+  if (!FILL) cnt[i] = n;
+}
+
+__global__ void k_to_dense(Csr<double> A, double* D) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nrows) return;
+  const int n = A.nrows;
+  for (int j = 0; j < 2 * n; ++j) D[(size_t)i * 2 * n + j] = (j == n + i) ? 1.0 : 0.0;
+  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) D[(size_t)i * 2 * n + A.col[q]] = A.val[q];
+}
+
+// Gauss-Jordan elimination of [A | I] in one thread block (A is SPD: no pivoting needed,
+// a non-positive pivot is reported).  Leaves A^-1 in the right half.
+__global__ void k_gauss_jordan(int n, double* D, double* inv, int* bad) {
+  const int w = 2 * n;
+  __shared__ double piv;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      piv = D[(size_t)k * w + k];
+      if (!(piv > 0.0)) *bad = 1;
+    }
+    __syncthreads();
+    const double ip = 1.0 / piv;
+    for (int j = threadIdx.x; j < w; j += blockDim.x) D[(size_t)k * w + j] *= ip;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * w; idx += blockDim.x) {
+      const int i = idx / w, j = idx % w;
+      if (i == k || j == k) continue;
+      D[(size_t)i * w + j] -= D[(size_t)i * w + k] * D[(size_t)k * w + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != k) D[(size_t)i * w + k] = 0.0;
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    inv[idx] = D[(size_t)i * w + n + j];
+  }
+}
+
+__global__ void k_d2f(const double* a, float* b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+template <typename T>
+__global__ void k_copy_cast(const double* a, T* b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (T)a[i];
+}
+
+// ---------------------------------------------------------------- set-up driver
+static ch_status level_setup(Hierarchy* h, int l, const ch_params& p, cudaStream_t st,
+                             bool* last) {
+  const Csr<double>& A = h->A[l];
+  const int n = A.nrows;
+  double* dinv = nullptr;
+  CH_TRY(h->mem.get(&dinv, (size_t)n));
+  h->dinv.push_back(dinv);
+  Alloc tmp;
+  double *rb = nullptr, *rmax = nullptr;
+  CH_TRY(tmp.get(&rb, (size_t)n));
+  CH_TRY(tmp.get(&rmax, 1));
+  k_diag_gersh<<<blocks_for(n), TPB, 0, st>>>(A, dinv, rb);
+  k_max_reduce<<<1, TPB, 0, st>>>(rb, n, rmax);
+  CH_LAUNCHED();
+  double rho = 0.0;
+  CH_CUDA(cudaMemcpyAsync(&rho, rmax, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  if (!(rho > 0.0) || !std::isfinite(rho)) {
+    set_error("AMG level %d: bad Gershgorin bound %g (zero or non-finite diagonal?)", l, rho);
+    return CH_ERR_NONFINITE;
+  }
+  h->rho.push_back(rho);
+  if (n <= p.coarse_max) {
+    *last = true;
+    return CH_OK;
+  }
+  // strength of connection
+  uint8_t *s0 = nullptr, *s = nullptr;
+  CH_TRY(tmp.get(&s0, (size_t)A.nnz));
+  CH_TRY(tmp.get(&s, (size_t)A.nnz));
+  k_strength<<<blocks_for(n), TPB, 0, st>>>(A, dinv, p.amg_theta, s0);
+  k_strength_sym<<<blocks_for(n), TPB, 0, st>>>(A, s0, s);
+  CH_LAUNCHED();
+  // MIS(2)
+  int8_t* state = nullptr;
+  uint64_t *key = nullptr, *m1 = nullptr, *m2 = nullptr;
+  int* und = nullptr;
+  CH_TRY(tmp.get(&state, (size_t)n));
+  CH_TRY(tmp.get(&key, (size_t)n));
+  CH_TRY(tmp.get(&m1, (size_t)n));
+  CH_TRY(tmp.get(&m2, (size_t)n));
+  CH_TRY(tmp.get(&und, 1));
+  CH_CUDA(cudaMemsetAsync(state, 1, (size_t)n, st));
+  for (int round = 0;; ++round) {
+    if (round > 200) {
+      set_error("AMG level %d: MIS(2) did not finish", l);
+      return CH_ERR_INTERNAL;
+    }
+    k_mis_keys<<<blocks_for(n), TPB, 0, st>>>(n, state, key);
+    k_strong_max<<<blocks_for(n), TPB, 0, st>>>(A, s, key, m1);
+    k_strong_max<<<blocks_for(n), TPB, 0, st>>>(A, s, m1, m2);
+    CH_CUDA(cudaMemsetAsync(und, 0, sizeof(int), st));
+    k_mis_update<<<blocks_for(n), TPB, 0, st>>>(n, key, m2, state, und);
+    CH_LAUNCHED();
+    int u = 0;
+    CH_CUDA(cudaMemcpyAsync(&u, und, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CH_CUDA(cudaStreamSynchronize(st));
+    if (u == 0) break;
+  }
+  // aggregates
+  int *isroot = nullptr, *rootid = nullptr, *agg = nullptr, *agg2 = nullptr, *una = nullptr;
+  CH_TRY(tmp.get(&isroot, (size_t)n));
+  CH_TRY(tmp.get(&rootid, (size_t)n + 1));
+  CH_TRY(tmp.get(&agg, (size_t)n));
+  CH_TRY(tmp.get(&agg2, (size_t)n));
+  CH_TRY(tmp.get(&una, 1));
+  k_roots<<<blocks_for(n), TPB, 0, st>>>(n, state, isroot);
+  CH_LAUNCHED();
+  int64_t nc = 0;
+  CH_TRY(scan_i32_to_rowptr(isroot, rootid, n, &nc, st, tmp));
+  for (int pass = 0;; ++pass) {
+    if (pass > 50) {
+      set_error("AMG level %d: aggregation did not cover all nodes", l);
+      return CH_ERR_INTERNAL;
+    }
+    CH_CUDA(cudaMemsetAsync(una, 0, sizeof(int), st));
+    k_agg_pass<<<blocks_for(n), TPB, 0, st>>>(A, s, isroot, rootid, agg, agg2, pass == 0, una);
+    CH_LAUNCHED();
+    std::swap(agg, agg2);
+    int u = 0;
+    CH_CUDA(cudaMemcpyAsync(&u, una, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CH_CUDA(cudaStreamSynchronize(st));
+    if (u == 0) break;
+  }
+  // smoothed prolongator
+  Csr<double> P;
+  P.nrows = n;
+  P.ncols = (int)nc;
+  int *skey = nullptr, *cnt = nullptr;
+  double* sval = nullptr;
+  CH_TRY(tmp.get(&skey, (size_t)A.nnz));
+  CH_TRY(tmp.get(&sval, (size_t)A.nnz));
+  CH_TRY(tmp.get(&cnt, (size_t)n));
+  const double omega = (4.0 / 3.0) / rho;
+  k_prolong<false><<<blocks_for(n), TPB, 0, st>>>(A, dinv, agg, omega, skey, sval, cnt, nullptr,
+                                                   nullptr, nullptr);
+  CH_LAUNCHED();
+  CH_TRY(h->mem.get(&P.rowptr, (size_t)n + 1));
+  int64_t pnnz = 0;
+  CH_TRY(scan_i32_to_rowptr(cnt, P.rowptr, n, &pnnz, st, tmp));
+  P.nnz = pnnz;
+  CH_TRY(h->mem.get(&P.col, (size_t)pnnz));
+  CH_TRY(h->mem.get(&P.val, (size_t)pnnz));
+  k_prolong<true><<<blocks_for(n), TPB, 0, st>>>(A, dinv, agg, omega, skey, sval, cnt, P.rowptr,
+                                                  P.col, P.val);
+  CH_LAUNCHED();
+  Csr<double> R, AP, Ac;
+  CH_TRY(transpose(P, &R, st, h->mem));
+  Alloc aptmp;
+  CH_TRY(spgemm(A, P, &AP, st, aptmp));
+  CH_TRY(spgemm(R, AP, &Ac, st, h->mem));
+  h->P.push_back(P);
+  h->R.push_back(R);
+  h->A.push_back(Ac);
+  CH_CUDA(cudaStreamSynchronize(st));
+  return CH_OK;
+}
+
+template <typename T>
+static ch_status make_working(Hierarchy* h, std::vector<LevelT<T>>& L, cudaStream_t st) {
+  using V2 = typename V2T<T>::t;
+  L.resize(h->nlev);
+  for (int l = 0; l < h->nlev; ++l) {
+    LevelT<T>& w = L[l];
+    auto cast_csr = [&](const Csr<double>& src, Csr<T>& dst) -> ch_status {
+      dst.nrows = src.nrows;
+      dst.ncols = src.ncols;
+      dst.nnz = src.nnz;
+      dst.rowptr = src.rowptr;
+      dst.col = src.col;
+      if (std::is_same<T, double>::value) {
+        dst.val = reinterpret_cast<T*>(src.val);
+      } else {
+        CH_TRY(h->mem.get(&dst.val, (size_t)src.nnz));
+        k_copy_cast<T><<<blocks_for(src.nnz), TPB, 0, st>>>(src.val, dst.val, src.nnz);
+        CH_LAUNCHED();
+      }
+      return CH_OK;
+    };
+    CH_TRY(cast_csr(h->A[l], w.A));
+    if (l + 1 < h->nlev) {
+      CH_TRY(cast_csr(h->P[l], w.P));
+      CH_TRY(cast_csr(h->R[l], w.R));
+    }
+    const int n = h->A[l].nrows;
+    if (std::is_same<T, double>::value) {
+      w.dinv = reinterpret_cast<T*>(h->dinv[l]);
+    } else {
+      CH_TRY(h->mem.get(&w.dinv, (size_t)n));
+      k_copy_cast<T><<<blocks_for(n), TPB, 0, st>>>(h->dinv[l], w.dinv, n);
+      CH_LAUNCHED();
+    }
+    CH_TRY(h->mem.get(&w.x, (size_t)n));
+    CH_TRY(h->mem.get(&w.x2, (size_t)n));
+    CH_TRY(h->mem.get(&w.d, (size_t)n));
+    CH_TRY(h->mem.get(&w.r, (size_t)n));
+    CH_TRY(h->mem.get(&w.b, (size_t)n));
+  }
+  return CH_OK;
+}
+
+ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precision, cudaStream_t st,
+                          Hierarchy** out) {
+  *out = nullptr;
+  Hierarchy* h = new Hierarchy();
+  h->precision = precision;
+  h->cheb_degree = p.cheb_degree;
+  h->A.push_back(A0);
+  ch_status s = CH_OK;
+  for (int l = 0;; ++l) {
+    if (l >= 25) {
+      set_error("AMG: more than 25 levels");
+      s = CH_ERR_INTERNAL;
+      break;
+    }
+    bool last = false;
+    s = level_setup(h, l, p, st, &last);
+    if (s != CH_OK || last) break;
+  }
+  if (s == CH_OK) {
+    h->nlev = (int)h->A.size();
+    h->nc = h->A.back().nrows;
+    if (h->nc > 4096) {
+      set_error("AMG: coarsest level has %d rows (> 4096); coarsening stalled", h->nc);
+      s = CH_ERR_INTERNAL;
+    }
+  }
+  if (s == CH_OK) {
+    Alloc tmp;
+    double* D = nullptr;
+    int* bad = nullptr;
+    const int nc = h->nc;
+    s = tmp.get(&D, (size_t)nc * 2 * nc);
+    if (s == CH_OK) s = tmp.get(&bad, 1);
+    if (s == CH_OK) s = h->mem.get(&h->cinv, (size_t)nc * nc);
+    if (s == CH_OK) {
+      cudaMemsetAsync(bad, 0, sizeof(int), st);
+      k_to_dense<<<blocks_for(nc), TPB, 0, st>>>(h->A.back(), D);
+      k_gauss_jordan<<<1, 1024, 0, st>>>(nc, D, h->cinv, bad);
+      int hb = 0;
+      cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        set_error("AMG: coarse inverse failed");
+        s = CH_ERR_CUDA;
+      } else if (hb) {
+        set_error("AMG: coarsest operator not positive definite");
+        s = CH_ERR_INTERNAL;
+      }
+    }
+  }
+  if (s == CH_OK) {
+    if (precision == 0) {
+      s = make_working<double>(h, h->Ld, st);
+    } else {
+      s = make_working<float>(h, h->Lf, st);
+      if (s == CH_OK) s = h->mem.get(&h->cinvf, (size_t)h->nc * h->nc);
+      if (s == CH_OK) {
+        k_d2f<<<blocks_for((int64_t)h->nc * h->nc), TPB, 0, st>>>(h->cinv, h->cinvf,
+                                                                  (int64_t)h->nc * h->nc);
+      }
+    }
+    if (s == CH_OK && cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error("AMG: building working copies failed");
+      s = CH_ERR_CUDA;
+    }
+  }
+  if (s != CH_OK) {
+    delete h;
+    return s;
+  }
+  *out = h;
+  return CH_OK;
+}
+
+void hierarchy_free(Hierarchy* h) { delete h; }
+int hierarchy_levels(const Hierarchy* h) { return h ? h->nlev : 0; }
+void hierarchy_level_size(const Hierarchy* h, int l, int64_t* rows, int64_t* nnz) {
+  if (rows) *rows = h->A[l].nrows;
+  if (nnz) *nnz = h->A[l].nnz;
+}
+
+// ---------------------------------------------------------------- V-cycle kernels (2 RHS)
+template <typename T, typename V2>
+__device__ __forceinline__ V2 mk2(T a, T b) {
+  V2 v;
+  v.x = a;
+  v.y = b;
+  return v;
+}
+
+// x = D^-1 b / theta (first Chebyshev step from a zero guess); d = x
+template <typename T, typename V2>
+__global__ void k_cheb_first(int n, const T* dinv, const V2* b, T invtheta, V2* x, V2* d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T s = invtheta * dinv[i];
+  const V2 bi = b[i];
+  const V2 v = mk2<T, V2>(s * bi.x, s * bi.y);
+  x[i] = v;
+  d[i] = v;
+}
+
+// r = b - A x;  d = alpha d + beta D^-1 r;  xo = x + d
+template <typename T, typename V2>
+__global__ void k_cheb_step(Csr<T> A, const T* dinv, const V2* b, const V2* x, V2* d, V2* xo,
+                            T alpha, T beta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nrows) return;
+  T s0 = 0, s1 = 0;
+  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+    const T a = A.val[q];
+    const V2 xj = x[A.col[q]];
+    s0 = fma(a, xj.x, s0);
+    s1 = fma(a, xj.y, s1);
+  }
+  const V2 bi = b[i], xi = x[i];
+  const T di = dinv[i] * beta;
+  V2 dd;
+  if (alpha != T(0)) {
+    const V2 dold = d[i];
+    dd = mk2<T, V2>(fma(alpha, dold.x, di * (bi.x - s0)), fma(alpha, dold.y, di * (bi.y - s1)));
+  } else {
+    dd = mk2<T, V2>(di * (bi.x - s0), di * (bi.y - s1));
+  }
+  d[i] = dd;
+  xo[i] = mk2<T, V2>(xi.x + dd.x, xi.y + dd.y);
+}
+
+template <typename T, typename V2>
+__global__ void k_residual(Csr<T> A, const V2* b, const V2* x, V2* r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nrows) return;
+  T s0 = 0, s1 = 0;
+  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+    const T a = A.val[q];
+    const V2 xj = x[A.col[q]];
+    s0 = fma(a, xj.x, s0);
+    s1 = fma(a, xj.y, s1);
+  }
+  const V2 bi = b[i];
+  r[i] = mk2<T, V2>(bi.x - s0, bi.y - s1);
+}
+
+// y = A x (ACC = false) or y += A x (ACC = true)
+template <typename T, typename V2, bool ACC>
+__global__ void k_spmv2(Csr<T> A, const V2* x, V2* y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nrows) return;
+  T s0 = 0, s1 = 0;
+  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+    const T a = A.val[q];
+    const V2 xj = x[A.col[q]];
+    s0 = fma(a, xj.x, s0);
+    s1 = fma(a, xj.y, s1);
+  }
+  if (ACC) {
+    const V2 yi = y[i];
+    y[i] = mk2<T, V2>(yi.x + s0, yi.y + s1);
+  } else {
+    y[i] = mk2<T, V2>(s0, s1);
+  }
+}
+
+// x = Ainv b, dense nc x nc, one warp per row
+template <typename T, typename V2>
+__global__ void k_dense_solve(int n, const T* inv, const V2* b, V2* x) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  T s0 = 0, s1 = 0;
+  for (int j = lane; j < n; j += 32) {
+    const T a = inv[(size_t)row * n + j];
+    const V2 bj = b[j];
+    s0 = fma(a, bj.x, s0);
+    s1 = fma(a, bj.y, s1);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if (lane == 0) x[row] = mk2<T, V2>(s0, s1);
+}
+
+// fine-level I/O: strided fp64 pairs <-> working precision pairs
+template <typename T, typename V2>
+__global__ void k_load2(int n, const double* src, int ld, V2* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = *reinterpret_cast<const double2*>(src + (size_t)i * ld);
+  dst[i] = mk2<T, V2>((T)v.x, (T)v.y);
+}
+template <typename T, typename V2>
+__global__ void k_store2(int n, const V2* src, double* dst, int ld) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const V2 v = src[i];
+  *reinterpret_cast<double2*>(dst + (size_t)i * ld) = make_double2((double)v.x, (double)v.y);
+}
+
+// ---------------------------------------------------------------- V-cycle driver
+struct ChebCoef {
+  double invtheta;
+  double alpha[16], beta[16];
+};
+
+static ChebCoef cheb_coef(double rho, int deg) {
+  ChebCoef c{};
+  const double hi = 1.1 * rho, lo = 0.3 * hi;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  c.invtheta = 1.0 / theta;
+  c.alpha[0] = 0.0;
+  c.beta[0] = 1.0 / theta;
+  double rho_prev = 1.0 / sigma;
+  for (int s = 1; s < deg && s < 16; ++s) {
+    const double r = 1.0 / (2.0 * sigma - rho_prev);
+    c.alpha[s] = r * rho_prev;
+    c.beta[s] = 2.0 * r / delta;
+    rho_prev = r;
+  }
+  return c;
+}
+
+template <typename T_>
+static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, bool zero_guess,
+                        typename V2T<T_>::t** xcur, cudaStream_t st) {
+  using V2 = typename V2T<T_>::t;
+  const int n = L.A.nrows;
+  const ChebCoef c = cheb_coef(h->rho[l], h->cheb_degree);
+  V2* x = *xcur;
+  V2* other = (x == L.x) ? L.x2 : L.x;
+  int s0 = 0;
+  const double T = sizeof(T_), nnz = (double)L.A.nnz;
+  if (zero_guess) {
+    ProfScope ps(st, K_CHEB_FIRST, sizeof(T_) == 4, 7.0 * T * n, 2.0 * n);
+    k_cheb_first<T_, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.dinv, L.b, (T_)c.invtheta, x, L.d);
+    s0 = 1;
+  }
+  for (int s = s0; s < h->cheb_degree; ++s) {
+    ProfScope ps(st, K_CHEB_STEP, sizeof(T_) == 4,
+                 nnz * (4 + T) + 4.0 * (n + 1) + T * n * (c.alpha[s] != 0.0 ? 11 : 9),
+                 2.0 * nnz + 4.0 * n);
+    k_cheb_step<T_, V2><<<blocks_for(n), TPB, 0, st>>>(L.A, L.dinv, L.b, x, L.d, other,
+                                                      (T_)c.alpha[s], (T_)c.beta[s]);
+    std::swap(x, other);
+  }
+  CH_LAUNCHED();
+  *xcur = x;
+  return CH_OK;
+}
+
+// one V-cycle at level l on L[l].b; result in *xres (L[l].x or L[l].x2)
+template <typename T>
+static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv, int l,
+                        bool zero_guess, typename V2T<T>::t** xres, cudaStream_t st) {
+  using V2 = typename V2T<T>::t;
+  LevelT<T>& L = Ls[l];
+  const int n = L.A.nrows;
+  const double Tb = sizeof(T);
+  if (l == h->nlev - 1) {
+    ProfScope ps(st, K_COARSE, sizeof(T) == 4, Tb * n * (double)n + 4.0 * Tb * n, 2.0 * n * (double)n);
+    k_dense_solve<T, V2><<<blocks_for((int64_t)n * 32), TPB, 0, st>>>(n, cinv, L.b, L.x);
+    CH_LAUNCHED();
+    *xres = L.x;
+    return CH_OK;
+  }
+  V2* x = *xres;
+  CH_TRY(smooth<T>(h, L, l, zero_guess, &x, st));
+  LevelT<T>& C = Ls[l + 1];
+  const int nc = C.A.nrows;
+  {
+    ProfScope ps(st, K_VRESIDUAL, sizeof(T) == 4, L.A.nnz * (4 + Tb) + 4.0 * (n + 1) + 6.0 * Tb * n,
+                 2.0 * L.A.nnz);
+    k_residual<T, V2><<<blocks_for(n), TPB, 0, st>>>(L.A, L.b, x, L.r);
+  }
+  {
+    ProfScope ps(st, K_RESTRICT, sizeof(T) == 4,
+                 L.R.nnz * (4 + Tb) + 4.0 * (nc + 1) + 2.0 * Tb * (n + nc), 2.0 * L.R.nnz);
+    k_spmv2<T, V2, false><<<blocks_for(nc), TPB, 0, st>>>(L.R, L.r, C.b);
+  }
+  CH_LAUNCHED();
+  V2* xc = C.x;
+  CH_TRY(vcycle<T>(h, Ls, cinv, l + 1, true, &xc, st));
+  {
+    ProfScope ps(st, K_PROLONG, sizeof(T) == 4,
+                 L.P.nnz * (4 + Tb) + 4.0 * (n + 1) + 2.0 * Tb * nc + 4.0 * Tb * n, 2.0 * L.P.nnz);
+    k_spmv2<T, V2, true><<<blocks_for(n), TPB, 0, st>>>(L.P, xc, x);
+  }
+  CH_LAUNCHED();
+  CH_TRY(smooth<T>(h, L, l, false, &x, st));
+  *xres = x;
+  return CH_OK;
+}
+
+template <typename T>
+static ch_status solve_t(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv, const double* b,
+                         int ldb, double* x, int ldx, int ncyc, cudaStream_t st) {
+  using V2 = typename V2T<T>::t;
+  LevelT<T>& L = Ls[0];
+  const int n = L.A.nrows;
+  k_load2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, b, ldb, L.b);
+  CH_LAUNCHED();
+  V2* xr = L.x;
+  for (int c = 0; c < ncyc; ++c) CH_TRY(vcycle<T>(h, Ls, cinv, 0, c == 0, &xr, st));
+  k_store2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, xr, x, ldx);
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+ch_status hierarchy_solve(Hierarchy* h, const double* b, int ldb, double* x, int ldx, int ncyc,
+                          cudaStream_t st) {
+  if (h->precision == 0) return solve_t<double>(h, h->Ld, h->cinv, b, ldb, x, ldx, ncyc, st);
+  return solve_t<float>(h, h->Lf, h->cinvf, b, ldb, x, ldx, ncyc, st);
+}
+
+template <typename T>
+static ch_status apply_fine_t(std::vector<LevelT<T>>& Ls, const double* x, int ldx, double* y,
+                              int ldy, cudaStream_t st) {
+  using V2 = typename V2T<T>::t;
+  LevelT<T>& L = Ls[0];
+  const int n = L.A.nrows;
+  k_load2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, x, ldx, L.r);
+  k_spmv2<T, V2, false><<<blocks_for(n), TPB, 0, st>>>(L.A, L.r, L.d);
+  k_store2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.d, y, ldy);
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+ch_status hierarchy_apply_fine(Hierarchy* h, const double* x, int ldx, double* y, int ldy,
+                               cudaStream_t st) {
+  if (h->precision == 0) return apply_fine_t<double>(h->Ld, x, ldx, y, ldy, st);
+  return apply_fine_t<float>(h->Lf, x, ldx, y, ldy, st);
+}
+
+// ---------------------------------------------------------------- Algorithm 1
+// w_1 = AMG(M) v_1;  w_2 = AMG(H) v_2;  w_2 = M w_2;  w_2 = AMG(H) w_2.
+// v, w are N x 4 (phi_p, phi_n, mu_p, mu_n per node): block 1 at offset 0, block 2 at offset 2.
+template <typename T>
+static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::vector<LevelT<T>>& LH,
+                           const T* cinvM, const T* cinvH, const double* v, double* w,
+                           cudaStream_t st) {
+  using V2 = typename V2T<T>::t;
+  const int n = LM[0].A.nrows;
+  const ch_params& p = pc->sys->p;
+  // step 1: M w_1 = v_1
+  {
+    LevelT<T>& L = LM[0];
+    {
+      ProfScope ps(st, K_VLOAD, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
+      k_load2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, v, 4, L.b);
+    }
+    V2* xr = L.x;
+    for (int c = 0; c < p.vcycles_M; ++c) CH_TRY(vcycle<T>(pc->hM, LM, cinvM, 0, c == 0, &xr, st));
+    {
+      ProfScope ps(st, K_VSTORE, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
+      k_store2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, xr, w, 4);
+    }
+    CH_LAUNCHED();
+  }
+  // steps 2-4: H w_2 = v_2; w_2 = M w_2; H w_2 = w_2
+  {
+    LevelT<T>& L = LH[0];
+    {
+      ProfScope ps(st, K_VLOAD, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
+      k_load2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, v + 2, 4, L.b);
+    }
+    V2* xr = L.x;
+    for (int c = 0; c < p.vcycles_H; ++c) CH_TRY(vcycle<T>(pc->hH, LH, cinvH, 0, c == 0, &xr, st));
+    // b <- M x (M's fine level in working precision); the V-cycle reads only L.b afterwards
+    {
+      const double Tb = sizeof(T), nnz = (double)LM[0].A.nnz;
+      ProfScope ps(st, K_SPMV_M, sizeof(T) == 4, nnz * (4 + Tb) + 4.0 * (n + 1) + 4.0 * Tb * n,
+                   2.0 * nnz);
+      k_spmv2<T, V2, false><<<blocks_for(n), TPB, 0, st>>>(LM[0].A, xr, L.b);
+    }
+    CH_LAUNCHED();
+    xr = L.x;  // the first solve's result now lives in L.b as M x; start afresh
+    for (int c = 0; c < p.vcycles_H; ++c) CH_TRY(vcycle<T>(pc->hH, LH, cinvH, 0, c == 0, &xr, st));
+    {
+      ProfScope ps(st, K_VSTORE, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
+      k_store2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, xr, w + 2, 4);
+    }
+    CH_LAUNCHED();
+  }
+  return CH_OK;
+}
+
+ch_status precond_apply(ch_precond_s* pc, const double* v, double* w, cudaStream_t st) {
+  if (pc->precision == 0)
+    return precond_t<double>(pc, pc->hM->Ld, pc->hH->Ld, pc->hM->cinv, pc->hH->cinv, v, w, st);
+  return precond_t<float>(pc, pc->hM->Lf, pc->hH->Lf, pc->hM->cinvf, pc->hH->cinvf, v, w, st);
+}
+
+}  // namespace ch

@@ -1,0 +1,584 @@
+// Mesh generation, P1 assembly, explicit loads and the block operator of Eq. (14).
+//
+// Everything is node-centric ("gather"): the thread of node i visits the simplices or
+// boundary facets incident to i in increasing index order and adds their contributions,
+// so every sum has a fixed order and results are bitwise reproducible (no atomics).
+#include "ch_internal.cuh"
+
+namespace ch {
+
+// ---------------------------------------------------------------- mesh (Section 4)
+__global__ void k_mesh_nodes(ch_params p, int N, double* coords) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int i = n % (p.nx + 1);
+  const int j = (n / (p.nx + 1)) % (p.ny + 1);
+  if (p.dim == 2) {
+    coords[2 * n + 0] = i * (p.Lx / p.nx);
+    coords[2 * n + 1] = j * (p.Ly / p.ny);
+  } else {
+    const int k = n / ((p.nx + 1) * (p.ny + 1));
+    coords[3 * n + 0] = i * (p.Lx / p.nx);
+    coords[3 * n + 1] = j * (p.Ly / p.ny);
+    coords[3 * n + 2] = k * (p.Lz / p.nz);
+  }
+}
+
+// 2D: cell c = i + nx j -> triangles 2c = (v00, v10, v11), 2c+1 = (v00, v11, v01).
+// 3D: hexahedron c -> the 6 Kuhn tetrahedra v000 -> +e_a -> +e_a+e_b -> v111 over the
+// permutations (a,b,c) of the axes, in lexicographic order of the permutation.
+__global__ void k_mesh_elems(ch_params p, int E, int* el) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  if (p.dim == 2) {
+    const int c = e >> 1, i = c % p.nx, j = c / p.nx;
+    const int v00 = i + (p.nx + 1) * j, v10 = v00 + 1, v01 = v00 + p.nx + 1, v11 = v01 + 1;
+    if ((e & 1) == 0) {
+      el[3 * e] = v00; el[3 * e + 1] = v10; el[3 * e + 2] = v11;
+    } else {
+      el[3 * e] = v00; el[3 * e + 1] = v11; el[3 * e + 2] = v01;
+    }
+  } else {
+    const int c = e / 6, t = e % 6;
+    const int i = c % p.nx, j = (c / p.nx) % p.ny, k = c / (p.nx * p.ny);
+    const int s[3] = {1, p.nx + 1, (p.nx + 1) * (p.ny + 1)};
+    const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    const int v0 = i + s[1] * j + s[2] * k;
+    el[4 * e + 0] = v0;
+    el[4 * e + 1] = v0 + s[perm[t][0]];
+    el[4 * e + 2] = v0 + s[perm[t][0]] + s[perm[t][1]];
+    el[4 * e + 3] = v0 + s[0] + s[1] + s[2];
+  }
+}
+
+// Boundary facets of the Kuhn / diagonal split on y = 0 (bottom) and y = Ly (top).
+__global__ void k_mesh_facets(ch_params p, int F, int* bot, int* top) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  if (p.dim == 2) {
+    const int b = f, t = p.ny * (p.nx + 1) + f;
+    bot[2 * f] = b; bot[2 * f + 1] = b + 1;
+    top[2 * f] = t; top[2 * f + 1] = t + 1;
+  } else {
+    const int q = f >> 1, i = q % p.nx, k = q / p.nx;
+    const int sx = 1, sz = (p.nx + 1) * (p.ny + 1);
+    const int b = i + sz * k;                   // (i, 0, k)
+    const int t = i + (p.nx + 1) * p.ny + sz * k;  // (i, ny, k)
+    if ((f & 1) == 0) {
+      bot[3 * f] = b; bot[3 * f + 1] = b + sx; bot[3 * f + 2] = b + sx + sz;
+      top[3 * f] = t; top[3 * f + 1] = t + sx; top[3 * f + 2] = t + sx + sz;
+    } else {
+      bot[3 * f] = b; bot[3 * f + 1] = b + sz; bot[3 * f + 2] = b + sx + sz;
+      top[3 * f] = t; top[3 * f + 1] = t + sz; top[3 * f + 2] = t + sx + sz;
+    }
+  }
+}
+
+// |T| and barycentric gradients: lambda_{1..d} = J^{-1}(x - x_0), J = [x_1-x_0, ..., x_d-x_0].
+template <int D>
+__device__ __forceinline__ double simplex_geo(const double* coords, const int* v, double g[D + 1][D]);
+
+template <>
+__device__ __forceinline__ double simplex_geo<2>(const double* X, const int* v, double g[3][2]) {
+  const double x0 = X[2 * v[0]], y0 = X[2 * v[0] + 1];
+  const double j00 = X[2 * v[1]] - x0, j10 = X[2 * v[1] + 1] - y0;
+  const double j01 = X[2 * v[2]] - x0, j11 = X[2 * v[2] + 1] - y0;
+  const double det = j00 * j11 - j01 * j10;
+  const double id = 1.0 / det;
+  g[1][0] = j11 * id;  g[1][1] = -j01 * id;
+  g[2][0] = -j10 * id; g[2][1] = j00 * id;
+  g[0][0] = -(g[1][0] + g[2][0]);
+  g[0][1] = -(g[1][1] + g[2][1]);
+  return 0.5 * fabs(det);
+}
+
+template <>
+__device__ __forceinline__ double simplex_geo<3>(const double* X, const int* v, double g[4][3]) {
+  double e[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) e[a][c] = X[3 * v[a + 1] + c] - X[3 * v[0] + c];
+  // rows of J^{-1}: (e2 x e3, e3 x e1, e1 x e2) / det
+  double r[3][3];
+  for (int a = 0; a < 3; ++a) {
+    const double* u = e[(a + 1) % 3];
+    const double* w = e[(a + 2) % 3];
+    r[a][0] = u[1] * w[2] - u[2] * w[1];
+    r[a][1] = u[2] * w[0] - u[0] * w[2];
+    r[a][2] = u[0] * w[1] - u[1] * w[0];
+  }
+  const double det = e[0][0] * r[0][0] + e[0][1] * r[0][1] + e[0][2] * r[0][2];
+  const double id = 1.0 / det;
+  for (int c = 0; c < 3; ++c) {
+    g[1][c] = r[0][c] * id;
+    g[2][c] = r[1][c] * id;
+    g[3][c] = r[2][c] * id;
+    g[0][c] = -(g[1][c] + g[2][c] + g[3][c]);
+  }
+  return fabs(det) / 6.0;
+}
+
+template <int D>
+__global__ void k_elem_vol(const double* X, const int* el, int E, double* vol) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double g[D + 1][D];
+  vol[e] = simplex_geo<D>(X, el + (D + 1) * e, g);
+}
+
+// facet measure: segment length (2D) or triangle area (3D)
+template <int D>
+__global__ void k_facet_vol(const double* X, const int* f, int F, double* vol) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= F) return;
+  if (D == 2) {
+    const double dx = X[2 * f[2 * q + 1]] - X[2 * f[2 * q]];
+    const double dy = X[2 * f[2 * q + 1] + 1] - X[2 * f[2 * q] + 1];
+    vol[q] = sqrt(dx * dx + dy * dy);
+  } else {
+    double u[3], w[3];
+    for (int c = 0; c < 3; ++c) {
+      u[c] = X[3 * f[3 * q + 1] + c] - X[3 * f[3 * q] + c];
+      w[c] = X[3 * f[3 * q + 2] + c] - X[3 * f[3 * q] + c];
+    }
+    const double cx = u[1] * w[2] - u[2] * w[1], cy = u[2] * w[0] - u[0] * w[2],
+                 cz = u[0] * w[1] - u[1] * w[0];
+    vol[q] = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+  }
+}
+
+ch_status mesh_build(ch_mesh_s* m, cudaStream_t st) {
+  const ch_params& p = m->p;
+  const int d = p.dim;
+  m->dim = d;
+  if (d == 2) {
+    m->N = (p.nx + 1) * (p.ny + 1);
+    m->E = 2 * p.nx * p.ny;
+    m->Fb = m->Ft = p.nx;
+  } else {
+    m->N = (p.nx + 1) * (p.ny + 1) * (p.nz + 1);
+    m->E = 6 * p.nx * p.ny * p.nz;
+    m->Fb = m->Ft = 2 * p.nx * p.nz;
+  }
+  CH_TRY(m->mem.get(&m->coords, (size_t)m->N * d));
+  CH_TRY(m->mem.get(&m->elems, (size_t)m->E * (d + 1)));
+  CH_TRY(m->mem.get(&m->bot, (size_t)m->Fb * d));
+  CH_TRY(m->mem.get(&m->top, (size_t)m->Ft * d));
+  CH_TRY(m->mem.get(&m->vol, (size_t)m->E));
+  CH_TRY(m->mem.get(&m->bvol, (size_t)m->Fb));
+  CH_TRY(m->mem.get(&m->tvol, (size_t)m->Ft));
+  k_mesh_nodes<<<blocks_for(m->N), TPB, 0, st>>>(p, m->N, m->coords);
+  k_mesh_elems<<<blocks_for(m->E), TPB, 0, st>>>(p, m->E, m->elems);
+  k_mesh_facets<<<blocks_for(m->Fb), TPB, 0, st>>>(p, m->Fb, m->bot, m->top);
+  CH_LAUNCHED();
+  if (d == 2) {
+    k_elem_vol<2><<<blocks_for(m->E), TPB, 0, st>>>(m->coords, m->elems, m->E, m->vol);
+    k_facet_vol<2><<<blocks_for(m->Fb), TPB, 0, st>>>(m->coords, m->bot, m->Fb, m->bvol);
+    k_facet_vol<2><<<blocks_for(m->Ft), TPB, 0, st>>>(m->coords, m->top, m->Ft, m->tvol);
+  } else {
+    k_elem_vol<3><<<blocks_for(m->E), TPB, 0, st>>>(m->coords, m->elems, m->E, m->vol);
+    k_facet_vol<3><<<blocks_for(m->Fb), TPB, 0, st>>>(m->coords, m->bot, m->Fb, m->bvol);
+    k_facet_vol<3><<<blocks_for(m->Ft), TPB, 0, st>>>(m->coords, m->top, m->Ft, m->tvol);
+  }
+  CH_LAUNCHED();
+  CH_TRY(build_incidence(m->elems, m->E, d + 1, m->N, &m->n2e_ptr, &m->n2e, st, m->mem));
+  CH_TRY(build_incidence(m->bot, m->Fb, d, m->N, &m->n2b_ptr, &m->n2b, st, m->mem));
+  CH_TRY(build_incidence(m->top, m->Ft, d, m->N, &m->n2t_ptr, &m->n2t, st, m->mem));
+  return CH_OK;
+}
+
+// ---------------------------------------------------------------- CSR pattern
+constexpr int MAXADJ = 128;  // distinct-or-not vertex entries gathered per node
+
+__device__ int gather_adjacent(const int* el, int k, const int* ptr, const int* list, int v,
+                               int* buf, int* overflow) {
+  int n = 0;
+  for (int q = ptr[v]; q < ptr[v + 1]; ++q) {
+    const int e = list[q];
+    for (int a = 0; a < k; ++a) {
+      if (n < MAXADJ) buf[n++] = el[k * e + a];
+      else *overflow = 1;
+    }
+  }
+  // insertion sort + unique
+  for (int i = 1; i < n; ++i) {
+    const int x = buf[i];
+    int j = i - 1;
+    while (j >= 0 && buf[j] > x) {
+      buf[j + 1] = buf[j];
+      --j;
+    }
+    buf[j + 1] = x;
+  }
+  int u = 0;
+  for (int i = 0; i < n; ++i)
+    if (u == 0 || buf[u - 1] != buf[i]) buf[u++] = buf[i];
+  return u;
+}
+
+__global__ void k_pattern(const int* el, int k, const int* ptr, const int* list, int N,
+                          const int* rowptr, int* cnt, int* col, int* overflow) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  int buf[MAXADJ];
+  const int u = gather_adjacent(el, k, ptr, list, v, buf, overflow);
+  if (rowptr == nullptr) {
+    cnt[v] = u;
+  } else {
+    for (int i = 0; i < u; ++i) col[rowptr[v] + i] = buf[i];
+  }
+}
+
+// ---------------------------------------------------------------- values of M and K
+__device__ __forceinline__ int find_col(const int* col, int b, int e, int c) {
+  while (b < e) {  // binary search in a sorted row
+    const int m = (b + e) >> 1;
+    if (col[m] < c) b = m + 1;
+    else e = m;
+  }
+  return b;
+}
+
+template <int D>
+__global__ void k_assemble(const double* X, const int* el, const int* ptr, const int* list, int N,
+                           const int* rowptr, const int* col, double* valM, double* valK,
+                           int* diag) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  const int rb = rowptr[v], re = rowptr[v + 1];
+  for (int q = rb; q < re; ++q) {
+    valM[q] = 0.0;
+    valK[q] = 0.0;
+  }
+  diag[v] = find_col(col, rb, re, v);
+  constexpr double mscale = 1.0 / ((D + 1) * (D + 2));  // M_e = |T| (1 + delta_ab) / ((d+1)(d+2))
+  for (int q = ptr[v]; q < ptr[v + 1]; ++q) {
+    const int e = list[q];
+    const int* ev = el + (D + 1) * e;
+    double g[D + 1][D];
+    const double vol = simplex_geo<D>(X, ev, g);
+    int a = 0;
+    while (ev[a] != v) ++a;
+    for (int b = 0; b <= D; ++b) {
+      double kab = 0.0;
+      for (int c = 0; c < D; ++c) kab = fma(g[a][c], g[b][c], kab);
+      const int pos = find_col(col, rb, re, ev[b]);
+      if (pos < re && col[pos] == ev[b]) {  // always true: the row pattern holds every neighbour
+        valK[pos] += vol * kab;
+        valM[pos] += vol * mscale * (a == b ? 2.0 : 1.0);
+      }
+    }
+  }
+}
+
+__global__ void k_axpby_vals(const double* x, const double* y, double a, double b, double* z,
+                             int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = a * x[i] + b * y[i];
+}
+
+ch_status assemble_system(const ch_mesh_s* m, ch_system_s* s, cudaStream_t st) {
+  const int N = m->N, d = m->dim;
+  s->N = N;
+  Alloc tmp;
+  int *cnt = nullptr, *overflow = nullptr;
+  CH_TRY(tmp.get(&cnt, (size_t)N));
+  CH_TRY(tmp.get(&overflow, 1));
+  CH_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int), st));
+  k_pattern<<<blocks_for(N), TPB, 0, st>>>(m->elems, d + 1, m->n2e_ptr, m->n2e, N, nullptr, cnt,
+                                            nullptr, overflow);
+  CH_LAUNCHED();
+  CH_TRY(s->mem.get(&s->rowptr, (size_t)N + 1));
+  int64_t nnz = 0;
+  CH_TRY(scan_i32_to_rowptr(cnt, s->rowptr, N, &nnz, st, tmp));
+  s->nnz = nnz;
+  CH_TRY(s->mem.get(&s->col, (size_t)nnz));
+  CH_TRY(s->mem.get(&s->valM, (size_t)nnz));
+  CH_TRY(s->mem.get(&s->valK, (size_t)nnz));
+  CH_TRY(s->mem.get(&s->valH, (size_t)nnz));
+  CH_TRY(s->mem.get(&s->diag, (size_t)N));
+  k_pattern<<<blocks_for(N), TPB, 0, st>>>(m->elems, d + 1, m->n2e_ptr, m->n2e, N, s->rowptr,
+                                            nullptr, s->col, overflow);
+  CH_LAUNCHED();
+  if (d == 2)
+    k_assemble<2><<<blocks_for(N), TPB, 0, st>>>(m->coords, m->elems, m->n2e_ptr, m->n2e, N,
+                                                  s->rowptr, s->col, s->valM, s->valK, s->diag);
+  else
+    k_assemble<3><<<blocks_for(N), TPB, 0, st>>>(m->coords, m->elems, m->n2e_ptr, m->n2e, N,
+                                                  s->rowptr, s->col, s->valM, s->valK, s->diag);
+  CH_LAUNCHED();
+  // H = a K + sqrt(c) M  (Section 3, matching Schur approximation)
+  k_axpby_vals<<<blocks_for(nnz), TPB, 0, st>>>(s->valK, s->valM, s->a, sqrt(s->c), s->valH, nnz);
+  CH_LAUNCHED();
+  int ovf = 0;
+  CH_CUDA(cudaMemcpyAsync(&ovf, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  if (ovf) {
+    set_error("a node has more than %d incident simplex vertices", MAXADJ);
+    return CH_ERR_INTERNAL;
+  }
+  return CH_OK;
+}
+
+// ---------------------------------------------------------------- explicit loads
+// Exact integrals of products of linear functions over a simplex T of dimension d:
+//   int_T l_1 ... l_n = d! |T| / (d+n)! * sum over permutations pi of {1..n} of
+//                       prod over the cycles C of pi of sum_vertices prod_{k in C} l_k(v),
+// which follows from int lambda^alpha = d! alpha! |T| / (d+|alpha|)! because alpha! counts
+// the permutations fixing an index tuple.  With l = (p, q, q, lambda_i) it gives
+//   int p q^2 lambda_i = d!|T|/(d+4)! [ <p><q>^2 + 2<pq><q> + <q^2><p> + 2<pq^2>
+//        + p_i(<q>^2 + <q^2>) + 2 q_i(<p><q> + <pq>) + 4 p_i q_i <q> + 2 q_i^2 <p> + 6 p_i q_i^2 ],
+// and with (a, b, lambda_i) on a facet of dimension d-1
+//   int a b lambda_i = (d-1)!|F|/(d+2)! [ <a><b> + <ab> + a_i<b> + b_i<a> + 2 a_i b_i ],
+// where <x> is the sum of x over the simplex's vertices.
+__device__ __forceinline__ double int_pqq_li(double Sp, double Sq, double Spq, double Sqq,
+                                             double Spqq, double pi, double qi) {
+  return Sp * Sq * Sq + 2.0 * Spq * Sq + Sqq * Sp + 2.0 * Spqq + pi * (Sq * Sq + Sqq) +
+         2.0 * qi * (Sp * Sq + Spq) + 4.0 * pi * qi * Sq + 2.0 * qi * qi * Sp + 6.0 * pi * qi * qi;
+}
+
+struct MeshPod {
+  int dim, N;
+  const double* coords;
+  const int* elems;
+  const int* bot;
+  const int* top;
+  const double* vol;
+  const double* bvol;
+  const double* tvol;
+  const int *n2e_ptr, *n2e, *n2b_ptr, *n2b, *n2t_ptr, *n2t;
+};
+
+static MeshPod mesh_pod(const ch_mesh_s* s) {
+  MeshPod v;
+  v.dim = s->dim;
+  v.N = s->N;
+  v.coords = s->coords;
+  v.elems = s->elems;
+  v.bot = s->bot;
+  v.top = s->top;
+  v.vol = s->vol;
+  v.bvol = s->bvol;
+  v.tvol = s->tvol;
+  v.n2e_ptr = s->n2e_ptr;
+  v.n2e = s->n2e;
+  v.n2b_ptr = s->n2b_ptr;
+  v.n2b = s->n2b;
+  v.n2t_ptr = s->n2t_ptr;
+  v.n2t = s->n2t;
+  return v;
+}
+
+struct LoadCoef {
+  double cs;      // coefficient of phi_s in f' (0.2 for Eq. (15), 0 otherwise)
+  double cubic;   // 7 for Eq. (15), 0 for f' = 0
+  int bc;         // boundary loads on/off
+  double gp, gn, hp, hn, kev;
+};
+
+template <int D>
+__device__ void node_loads(const MeshPod& m, const LoadCoef& L, const double* pp,
+                           const double* pn, int ld, int v, double* Fp, double* Fn, double* Gp,
+                           double* Gn) {
+  constexpr double c4 = (D == 2) ? 1.0 / 360.0 : 1.0 / 840.0;  // d!/(d+4)!
+  constexpr double c2 = 1.0 / ((D + 1) * (D + 2));             // int lambda_a lambda_i / |T|, a != i
+  double fp = 0.0, fn = 0.0;
+  for (int q = m.n2e_ptr[v]; q < m.n2e_ptr[v + 1]; ++q) {
+    const int e = m.n2e[q];
+    const int* ev = m.elems + (D + 1) * e;
+    double P[D + 1], Q[D + 1];
+    int li = 0;
+    for (int a = 0; a <= D; ++a) {
+      P[a] = pp[(size_t)ld * ev[a]];
+      Q[a] = pn[(size_t)ld * ev[a]];
+      if (ev[a] == v) li = a;
+    }
+    double Sp = 0, Sq = 0, Spq = 0, Spp = 0, Sqq = 0, Spqq = 0, Sppq = 0;
+    for (int a = 0; a <= D; ++a) {
+      Sp += P[a];
+      Sq += Q[a];
+      const double pq = P[a] * Q[a];
+      Spq += pq;
+      Spp += P[a] * P[a];
+      Sqq += Q[a] * Q[a];
+      Spqq += pq * Q[a];
+      Sppq += pq * P[a];
+    }
+    const double vol = m.vol[e];
+    const double Ip = c4 * int_pqq_li(Sp, Sq, Spq, Sqq, Spqq, P[li], Q[li]);  // int p q^2 l_i / |T|
+    const double In = c4 * int_pqq_li(Sq, Sp, Spq, Spp, Sppq, Q[li], P[li]);  // int q p^2 l_i / |T|
+    // int phi_s lambda_i / |T| with phi_s = 1 - p - q: (sum_a s_a + s_i) / ((d+1)(d+2))
+    const double Is = c2 * (((D + 1) - Sp - Sq) + (1.0 - P[li] - Q[li]));
+    fp += vol * (L.cubic * Ip - L.cs * Is);
+    fn += vol * (L.cubic * In - L.cs * Is);
+  }
+  *Fp = fp;
+  *Fn = fn;
+  double gp = 0.0, gn = 0.0;
+  if (L.bc) {
+    constexpr int DF = D - 1;
+    constexpr double f1 = 1.0 / (DF + 1);                 // int lambda_i / |F|
+    constexpr double f2 = 1.0 / ((DF + 1) * (DF + 2));    // int lambda_a lambda_i / |F|, a != i
+    constexpr double f3 = (D == 2) ? 1.0 / 24.0 : 1.0 / 60.0;  // (d-1)!/(d+2)!
+    for (int q = m.n2b_ptr[v]; q < m.n2b_ptr[v + 1]; ++q) {  // Gamma_b: int (g + 2 h phi) lambda_i
+      const int f = m.n2b[q];
+      const int* fv = m.bot + D * f;
+      double Sp = 0, Sq = 0, pi = 0, qi = 0;
+      for (int a = 0; a < D; ++a) {
+        Sp += pp[(size_t)ld * fv[a]];
+        Sq += pn[(size_t)ld * fv[a]];
+        if (fv[a] == v) {
+          pi = pp[(size_t)ld * fv[a]];
+          qi = pn[(size_t)ld * fv[a]];
+        }
+      }
+      const double ar = m.bvol[f];
+      gp += ar * (L.gp * f1 + 2.0 * L.hp * f2 * (Sp + pi));
+      gn += ar * (L.gn * f1 + 2.0 * L.hn * f2 * (Sq + qi));
+    }
+    for (int q = m.n2t_ptr[v]; q < m.n2t_ptr[v + 1]; ++q) {  // Gamma_t: k int phi phi_s lambda_i
+      const int f = m.n2t[q];
+      const int* fv = m.top + D * f;
+      double Sp = 0, Sq = 0, Ss = 0, Sps = 0, Sqs = 0, pi = 0, qi = 0, si = 0;
+      for (int a = 0; a < D; ++a) {
+        const double x = pp[(size_t)ld * fv[a]], y = pn[(size_t)ld * fv[a]], s = 1.0 - x - y;
+        Sp += x;
+        Sq += y;
+        Ss += s;
+        Sps += x * s;
+        Sqs += y * s;
+        if (fv[a] == v) {
+          pi = x;
+          qi = y;
+          si = s;
+        }
+      }
+      const double ar = m.tvol[f] * L.kev * f3;
+      gp += ar * (Sp * Ss + Sps + pi * Ss + si * Sp + 2.0 * pi * si);
+      gn += ar * (Sq * Ss + Sqs + qi * Ss + si * Sq + 2.0 * qi * si);
+    }
+  }
+  *Gp = gp;
+  *Gn = gn;
+}
+
+static LoadCoef load_coef(const ch_params& p) {
+  LoadCoef L;
+  L.cubic = p.potential == 2 ? 0.0 : 7.0;
+  L.cs = p.potential == 0 ? 0.2 : 0.0;
+  L.bc = p.bc_mode;
+  L.gp = p.g_p;
+  L.gn = p.g_nfa;
+  L.hp = p.h_p;
+  L.hn = p.h_nfa;
+  L.kev = p.evap_sign * p.k_evap;
+  return L;
+}
+
+template <int D>
+__global__ void k_loads(const MeshPod m, LoadCoef L, const double* pp, const double* pn,
+                        int ld, double* Fp, double* Fn, double* Gp, double* Gn) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= m.N) return;
+  double a, b, c, d;
+  node_loads<D>(m, L, pp, pn, ld, v, &a, &b, &c, &d);
+  if (Fp) Fp[v] = a;
+  if (Fn) Fn[v] = b;
+  if (Gp) Gp[v] = c;
+  if (Gn) Gn[v] = d;
+}
+
+// b (N x 4) = (M phi_p + tau g_p, M phi_n + tau g_n, -c F_p, -c F_n)   (Eq. (13) -> Eq. (14))
+template <int D>
+__global__ void k_rhs(const MeshPod m, LoadCoef L, const int* rowptr, const int* col,
+                      const double* valM, const double* pp, const double* pn, int ld,
+                      double tau, double c, double* b) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= m.N) return;
+  double Fp, Fn, Gp, Gn;
+  node_loads<D>(m, L, pp, pn, ld, v, &Fp, &Fn, &Gp, &Gn);
+  double mp = 0.0, mn = 0.0;
+  for (int q = rowptr[v]; q < rowptr[v + 1]; ++q) {
+    const int j = col[q];
+    mp = fma(valM[q], pp[(size_t)ld * j], mp);
+    mn = fma(valM[q], pn[(size_t)ld * j], mn);
+  }
+  double4_32a out;
+  out.x = mp + tau * Gp;
+  out.y = mn + tau * Gn;
+  out.z = -c * Fp;
+  out.w = -c * Fn;
+  reinterpret_cast<double4_32a*>(b)[v] = out;
+}
+
+ch_status loads(const ch_system_s* s, const double* pp, const double* pn, double* Fp, double* Fn,
+                double* gp, double* gn, cudaStream_t st) {
+  const MeshPod m = mesh_pod(s->mesh);
+  const LoadCoef L = load_coef(s->p);
+  ProfScope ps(st, K_LOADS, 0, 16.0 * m.N + 32.0 * m.N, 0.0);
+  if (m.dim == 2)
+    k_loads<2><<<blocks_for(m.N), TPB, 0, st>>>(m, L, pp, pn, 1, Fp, Fn, gp, gn);
+  else
+    k_loads<3><<<blocks_for(m.N), TPB, 0, st>>>(m, L, pp, pn, 1, Fp, Fn, gp, gn);
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+ch_status rhs_strided(const ch_system_s* s, const double* pp, const double* pn, int ld, double* b,
+                      cudaStream_t st) {
+  const MeshPod m = mesh_pod(s->mesh);
+  const LoadCoef L = load_coef(s->p);
+  const double E = s->mesh->E, d1 = m.dim + 1;
+  // phi read + b written + M (values, columns, row pointers) + elements, measures, incidence
+  ProfScope ps(st, K_RHS, 0, 48.0 * m.N + 12.0 * s->nnz + 4.0 * m.N + E * (8.0 * d1 + 8.0),
+               2.0 * s->nnz + 30.0 * E * d1);
+  if (m.dim == 2)
+    k_rhs<2><<<blocks_for(m.N), TPB, 0, st>>>(m, L, s->rowptr, s->col, s->valM, pp, pn, ld,
+                                               s->p.tau, s->c, b);
+  else
+    k_rhs<3><<<blocks_for(m.N), TPB, 0, st>>>(m, L, s->rowptr, s->col, s->valM, pp, pn, ld,
+                                               s->p.tau, s->c, b);
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+// ---------------------------------------------------------------- block operator of Eq. (14)
+// y = A x for both species: per node x = (x1_p, x1_n, x2_p, x2_n),
+//   y1 = M x1 + a K x2,  y2 = a K x1 - c M x2.
+// One pass over the shared pattern: 8 FMAs per stored entry.
+__global__ void k_apply_A(int N, const int* rowptr, const int* col, const double* valM,
+                          const double* valK, double a, double c, const double4_32a* x, double4_32a* y) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  double m1p = 0, m1n = 0, m2p = 0, m2n = 0, k1p = 0, k1n = 0, k2p = 0, k2n = 0;
+  for (int q = rowptr[v]; q < rowptr[v + 1]; ++q) {
+    const int j = col[q];
+    const double m = valM[q], k = valK[q];
+    const double4_32a z = x[j];
+    m1p = fma(m, z.x, m1p);
+    m1n = fma(m, z.y, m1n);
+    m2p = fma(m, z.z, m2p);
+    m2n = fma(m, z.w, m2n);
+    k1p = fma(k, z.x, k1p);
+    k1n = fma(k, z.y, k1n);
+    k2p = fma(k, z.z, k2p);
+    k2n = fma(k, z.w, k2n);
+  }
+  double4_32a out;
+  out.x = fma(a, k2p, m1p);
+  out.y = fma(a, k2n, m1n);
+  out.z = fma(a, k1p, -c * m2p);
+  out.w = fma(a, k1n, -c * m2n);
+  y[v] = out;
+}
+
+ch_status apply_A(const ch_system_s* s, const double* x, double* y, cudaStream_t st) {
+  ProfScope ps(st, K_APPLY_A, 0, 20.0 * s->nnz + 4.0 * (s->N + 1) + 64.0 * s->N,
+               8.0 * s->nnz + 4.0 * s->N);
+  k_apply_A<<<blocks_for(s->N), TPB, 0, st>>>(s->N, s->rowptr, s->col, s->valM, s->valK, s->a,
+                                               s->c, reinterpret_cast<const double4_32a*>(x),
+                                               reinterpret_cast<double4_32a*>(y));
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+}  // namespace ch

@@ -1,0 +1,305 @@
+// extern "C" entry points declared in include/ch.h: argument checks, handle lifetime,
+// and dispatch to the kernels of assemble.cu, amg.cu and krylov.cu.
+#include <cmath>
+#include <new>
+
+#include "ch_internal.cuh"
+
+using ch::set_error;
+
+namespace {
+cudaStream_t S(void* stream) { return reinterpret_cast<cudaStream_t>(stream); }
+
+ch_status check_params(const ch_params* p) {
+  CH_ARG(p != nullptr, "params is NULL");
+  CH_ARG(p->dim == 2 || p->dim == 3, "dim must be 2 or 3");
+  CH_ARG(p->nx >= 1 && p->ny >= 1 && (p->dim == 2 || p->nz >= 1), "cell counts must be >= 1");
+  CH_ARG(p->Lx > 0 && p->Ly > 0 && (p->dim == 2 || p->Lz > 0), "box extents must be > 0");
+  const double nodes = (double)(p->nx + 1) * (p->ny + 1) * (p->dim == 3 ? (p->nz + 1) : 1);
+  CH_ARG(nodes < 2.0e8, "mesh too large for int32 indexing");
+  CH_ARG(p->tau > 0 && std::isfinite(p->tau), "tau must be > 0");
+  CH_ARG(p->eps > 0 && std::isfinite(p->eps), "eps must be > 0");
+  CH_ARG(p->mobility > 0 && std::isfinite(p->mobility), "mobility must be > 0");
+  CH_ARG(p->bc_mode == 0 || p->bc_mode == 1, "bc_mode must be 0 or 1");
+  CH_ARG(p->evap_sign == 1 || p->evap_sign == -1, "evap_sign must be +1 or -1");
+  CH_ARG(p->potential >= 0 && p->potential <= 2, "potential must be 0, 1 or 2");
+  CH_ARG(p->precision == 0 || p->precision == 1, "precision must be 0 or 1");
+  CH_ARG(p->rtol > 0 && p->rtol < 1, "rtol must be in (0, 1)");
+  CH_ARG(p->restart >= 1 && p->restart <= 64, "restart must be in [1, 64]");
+  CH_ARG(p->max_iter >= 1, "max_iter must be >= 1");
+  CH_ARG(p->cheb_degree >= 1 && p->cheb_degree <= 16, "cheb_degree must be in [1, 16]");
+  CH_ARG(p->coarse_max >= 1 && p->coarse_max <= 4096, "coarse_max must be in [1, 4096]");
+  CH_ARG(p->amg_theta >= 0 && p->amg_theta < 1, "amg_theta must be in [0, 1)");
+  CH_ARG(p->vcycles_M >= 1 && p->vcycles_H >= 1, "vcycles must be >= 1");
+  return CH_OK;
+}
+}  // namespace
+
+extern "C" {
+
+const char* ch_status_str(ch_status s) {
+  switch (s) {
+    case CH_OK: return "ok";
+    case CH_ERR_ARG: return "invalid argument";
+    case CH_ERR_CUDA: return "CUDA error";
+    case CH_ERR_OOM: return "out of device memory";
+    case CH_ERR_NOT_CONVERGED: return "not converged";
+    case CH_ERR_BREAKDOWN: return "Krylov breakdown";
+    case CH_ERR_NONFINITE: return "non-finite value";
+    case CH_ERR_STATE: return "call out of order";
+    case CH_ERR_INTERNAL: return "internal check failed";
+  }
+  return "unknown status";
+}
+
+const char* ch_last_error(void) { return ch::last_error(); }
+
+void ch_params_default(ch_params* p) {
+  if (!p) return;
+  ch_params d{};
+  d.dim = 2;
+  d.nx = 32;
+  d.ny = 32;
+  d.nz = 0;
+  d.Lx = 1.0;
+  d.Ly = 1.0;
+  d.Lz = 1.0;
+  d.tau = 1e-4;
+  d.eps = 1e-3;
+  d.mobility = 1.0;
+  d.bc_mode = 1;
+  d.evap_sign = 1;
+  d.potential = 0;
+  d.precision = 0;
+  d.k_evap = 5e-3;
+  d.g_p = 0.01;
+  d.g_nfa = 0.01;
+  d.h_p = 0.0;
+  d.h_nfa = 0.0;
+  d.rtol = 1e-8;
+  d.restart = 30;
+  d.max_iter = 300;
+  d.cheb_degree = 2;
+  d.coarse_max = 256;
+  d.amg_theta = 0.08;
+  d.vcycles_M = 1;
+  d.vcycles_H = 1;
+  *p = d;
+}
+
+// ---------------------------------------------------------------- mesh
+ch_status ch_mesh(const ch_params* p, void* stream, ch_mesh_t** out) {
+  CH_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  CH_TRY(check_params(p));
+  ch_mesh_s* m = new (std::nothrow) ch_mesh_s();
+  if (!m) return CH_ERR_OOM;
+  m->p = *p;
+  ch_status r = ch::mesh_build(m, S(stream));
+  if (r != CH_OK) {
+    delete m;
+    return r;
+  }
+  *out = m;
+  return CH_OK;
+}
+
+ch_status ch_mesh_info(const ch_mesh_t* m, int64_t* n_nodes, int64_t* n_elems, int64_t* n_bottom,
+                       int64_t* n_top) {
+  CH_ARG(m != nullptr, "mesh is NULL");
+  if (n_nodes) *n_nodes = m->N;
+  if (n_elems) *n_elems = m->E;
+  if (n_bottom) *n_bottom = m->Fb;
+  if (n_top) *n_top = m->Ft;
+  return CH_OK;
+}
+
+ch_status ch_mesh_copy(const ch_mesh_t* m, double* coords, int32_t* elems, int32_t* bottom,
+                       int32_t* top, void* stream) {
+  CH_ARG(m != nullptr, "mesh is NULL");
+  const cudaStream_t st = S(stream);
+  const int d = m->dim;
+  if (coords)
+    CH_CUDA(cudaMemcpyAsync(coords, m->coords, sizeof(double) * m->N * d, cudaMemcpyDeviceToDevice, st));
+  if (elems)
+    CH_CUDA(cudaMemcpyAsync(elems, m->elems, sizeof(int) * (size_t)m->E * (d + 1),
+                            cudaMemcpyDeviceToDevice, st));
+  if (bottom)
+    CH_CUDA(cudaMemcpyAsync(bottom, m->bot, sizeof(int) * (size_t)m->Fb * d, cudaMemcpyDeviceToDevice, st));
+  if (top)
+    CH_CUDA(cudaMemcpyAsync(top, m->top, sizeof(int) * (size_t)m->Ft * d, cudaMemcpyDeviceToDevice, st));
+  return CH_OK;
+}
+
+void ch_mesh_destroy(ch_mesh_t* m) { delete m; }
+
+// ---------------------------------------------------------------- assembly
+ch_status ch_assemble(const ch_mesh_t* m, const ch_params* p, void* stream, ch_system_t** out) {
+  CH_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  CH_ARG(m != nullptr, "mesh is NULL");
+  CH_TRY(check_params(p));
+  CH_ARG(p->dim == m->p.dim && p->nx == m->p.nx && p->ny == m->p.ny &&
+             (p->dim == 2 || p->nz == m->p.nz),
+         "params describe a different mesh");
+  ch_system_s* s = new (std::nothrow) ch_system_s();
+  if (!s) return CH_ERR_OOM;
+  s->mesh = m;
+  s->p = *p;
+  s->a = p->tau * p->mobility;
+  s->c = s->a / p->eps;
+  ch_status r = ch::assemble_system(m, s, S(stream));
+  if (r != CH_OK) {
+    delete s;
+    return r;
+  }
+  *out = s;
+  return CH_OK;
+}
+
+ch_status ch_system_info(const ch_system_t* s, int64_t* n, int64_t* nnz) {
+  CH_ARG(s != nullptr, "system is NULL");
+  if (n) *n = s->N;
+  if (nnz) *nnz = s->nnz;
+  return CH_OK;
+}
+
+ch_status ch_system_copy(const ch_system_t* s, int32_t* rowptr, int32_t* col, double* valM,
+                         double* valK, double* valH, void* stream) {
+  CH_ARG(s != nullptr, "system is NULL");
+  const cudaStream_t st = S(stream);
+  if (rowptr)
+    CH_CUDA(cudaMemcpyAsync(rowptr, s->rowptr, sizeof(int) * ((size_t)s->N + 1), cudaMemcpyDeviceToDevice, st));
+  if (col) CH_CUDA(cudaMemcpyAsync(col, s->col, sizeof(int) * s->nnz, cudaMemcpyDeviceToDevice, st));
+  if (valM) CH_CUDA(cudaMemcpyAsync(valM, s->valM, sizeof(double) * s->nnz, cudaMemcpyDeviceToDevice, st));
+  if (valK) CH_CUDA(cudaMemcpyAsync(valK, s->valK, sizeof(double) * s->nnz, cudaMemcpyDeviceToDevice, st));
+  if (valH) CH_CUDA(cudaMemcpyAsync(valH, s->valH, sizeof(double) * s->nnz, cudaMemcpyDeviceToDevice, st));
+  return CH_OK;
+}
+
+void ch_system_destroy(ch_system_t* s) { delete s; }
+
+ch_status ch_loads(const ch_system_t* s, const double* phi_p, const double* phi_nfa, double* F_p,
+                   double* F_nfa, double* g_p, double* g_nfa, void* stream) {
+  CH_ARG(s != nullptr && phi_p != nullptr && phi_nfa != nullptr, "NULL system or input");
+  return ch::loads(s, phi_p, phi_nfa, F_p, F_nfa, g_p, g_nfa, S(stream));
+}
+
+ch_status ch_rhs(const ch_system_t* s, const double* phi_p, const double* phi_nfa, double* b,
+                 void* stream) {
+  CH_ARG(s != nullptr && phi_p != nullptr && phi_nfa != nullptr && b != nullptr, "NULL argument");
+  CH_ARG((reinterpret_cast<uintptr_t>(b) & 31) == 0, "b must be 32-byte aligned");
+  return ch::rhs_strided(s, phi_p, phi_nfa, 1, b, S(stream));
+}
+
+ch_status ch_apply_A(const ch_system_t* s, const double* x, double* y, void* stream) {
+  CH_ARG(s != nullptr && x != nullptr && y != nullptr, "NULL argument");
+  CH_ARG(x != y, "x and y must not alias");
+  CH_ARG(((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 31) == 0,
+         "x and y must be 32-byte aligned");
+  return ch::apply_A(s, x, y, S(stream));
+}
+
+// ---------------------------------------------------------------- preconditioner
+ch_status ch_precond_setup(const ch_system_t* s, void* stream, ch_precond_t** out) {
+  CH_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  CH_ARG(s != nullptr, "system is NULL");
+  ch_precond_s* pc = new (std::nothrow) ch_precond_s();
+  if (!pc) return CH_ERR_OOM;
+  pc->sys = s;
+  pc->precision = s->p.precision;
+  ch::Csr<double> M, H;
+  M.nrows = M.ncols = H.nrows = H.ncols = s->N;
+  M.nnz = H.nnz = s->nnz;
+  M.rowptr = H.rowptr = s->rowptr;
+  M.col = H.col = s->col;
+  M.val = s->valM;
+  H.val = s->valH;
+  ch_status r = ch::hierarchy_build(M, s->p, pc->precision, S(stream), &pc->hM);
+  if (r == CH_OK) r = ch::hierarchy_build(H, s->p, pc->precision, S(stream), &pc->hH);
+  if (r != CH_OK) {
+    delete pc;
+    return r;
+  }
+  *out = pc;
+  return CH_OK;
+}
+
+ch_status ch_precond_info(const ch_precond_t* pc, int32_t which, int32_t level, int32_t* nlevels,
+                          int64_t* rows, int64_t* nnz) {
+  CH_ARG(pc != nullptr, "preconditioner is NULL");
+  CH_ARG(which == 0 || which == 1, "which must be 0 (M) or 1 (H)");
+  const ch::Hierarchy* h = which == 0 ? pc->hM : pc->hH;
+  const int nl = ch::hierarchy_levels(h);
+  if (nlevels) *nlevels = nl;
+  if (rows || nnz) {
+    CH_ARG(level >= 0 && level < nl, "level out of range");
+    ch::hierarchy_level_size(h, level, rows, nnz);
+  }
+  return CH_OK;
+}
+
+ch_status ch_precond_apply(ch_precond_t* pc, const double* v, double* w, void* stream) {
+  CH_ARG(pc != nullptr && v != nullptr && w != nullptr, "NULL argument");
+  CH_ARG(v != w, "v and w must not alias");
+  CH_ARG(((reinterpret_cast<uintptr_t>(v) | reinterpret_cast<uintptr_t>(w)) & 31) == 0,
+         "v and w must be 32-byte aligned");
+  return ch::precond_apply(pc, v, w, S(stream));
+}
+
+ch_status ch_vcycle(ch_precond_t* pc, int32_t which, int32_t vcycles, const double* b, double* x,
+                    void* stream) {
+  CH_ARG(pc != nullptr && b != nullptr && x != nullptr, "NULL argument");
+  CH_ARG(which == 0 || which == 1, "which must be 0 (M) or 1 (H)");
+  CH_ARG(vcycles >= 1, "vcycles must be >= 1");
+  CH_ARG(b != x, "b and x must not alias");
+  CH_ARG(((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15) == 0,
+         "b and x must be 16-byte aligned");
+  return ch::hierarchy_solve(which == 0 ? pc->hM : pc->hH, b, 2, x, 2, vcycles, S(stream));
+}
+
+void ch_precond_destroy(ch_precond_t* pc) { delete pc; }
+
+// ---------------------------------------------------------------- state and stepping
+ch_status ch_state_create(const ch_system_t* s, ch_precond_t* pc, void* stream, ch_state_t** out) {
+  CH_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  CH_ARG(s != nullptr && pc != nullptr, "NULL system or preconditioner");
+  CH_ARG(pc->sys == s, "preconditioner was built for another system");
+  return ch::state_create(s, pc, S(stream), out);
+}
+
+ch_status ch_state_set(ch_state_t* st, const double* phi_p, const double* phi_nfa,
+                       const double* mu_p, const double* mu_nfa, void* stream) {
+  CH_ARG(st != nullptr && phi_p != nullptr && phi_nfa != nullptr, "NULL argument");
+  return ch::state_set(st, phi_p, phi_nfa, mu_p, mu_nfa, S(stream));
+}
+
+ch_status ch_state_init_seeded(ch_state_t* st, double phi_p0, double phi_nfa0, double noise,
+                               uint64_t seed, void* stream) {
+  CH_ARG(st != nullptr, "state is NULL");
+  return ch::state_seeded(st, phi_p0, phi_nfa0, noise, seed, S(stream));
+}
+
+ch_status ch_state_get(const ch_state_t* st, double* phi_p, double* phi_nfa, double* phi_s,
+                       double* mu_p, double* mu_nfa, void* stream) {
+  CH_ARG(st != nullptr, "state is NULL");
+  return ch::state_get(st, phi_p, phi_nfa, phi_s, mu_p, mu_nfa, S(stream));
+}
+
+ch_status ch_step(ch_state_t* st, void* stream, ch_step_stats* stats) {
+  CH_ARG(st != nullptr, "state is NULL");
+  return ch::state_step(st, S(stream), stats);
+}
+
+ch_status ch_run(ch_state_t* st, int32_t nsteps, void* stream, ch_step_stats* per_step) {
+  CH_ARG(st != nullptr, "state is NULL");
+  CH_ARG(nsteps >= 0, "nsteps must be >= 0");
+  for (int k = 0; k < nsteps; ++k) CH_TRY(ch::state_step(st, S(stream), per_step ? per_step + k : nullptr));
+  return CH_OK;
+}
+
+void ch_state_destroy(ch_state_t* st) { ch::state_destroy(st); }
+
+}  // extern "C"

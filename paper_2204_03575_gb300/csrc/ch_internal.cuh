@@ -1,0 +1,223 @@
+// Internal declarations shared by the CUDA translation units of libch.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/ch.h"
+
+namespace ch {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+
+#define CH_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      ::ch::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? CH_ERR_OOM : CH_ERR_CUDA;                   \
+    }                                                                                      \
+  } while (0)
+
+#define CH_LAUNCHED() CH_CUDA(cudaGetLastError())
+
+#define CH_TRY(call)                \
+  do {                              \
+    ch_status s_ = (call);          \
+    if (s_ != CH_OK) return s_;     \
+  } while (0)
+
+#define CH_ARG(cond, msg)                                        \
+  do {                                                           \
+    if (!(cond)) {                                               \
+      ::ch::set_error("invalid argument: %s", msg);              \
+      return CH_ERR_ARG;                                         \
+    }                                                            \
+  } while (0)
+
+// ---------------------------------------------------------------- device memory owned by a handle
+struct Alloc {
+  std::vector<void*> ptrs;
+  Alloc() = default;
+  Alloc(const Alloc&) = delete;
+  Alloc& operator=(const Alloc&) = delete;
+  ~Alloc() { release(); }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+  template <typename T>
+  ch_status get(T** out, size_t n) {
+    *out = nullptr;
+    if (n == 0) n = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? CH_ERR_OOM : CH_ERR_CUDA;
+    }
+    ptrs.push_back(p);
+    *out = static_cast<T*>(p);
+    return CH_OK;
+  }
+  void forget(void* p) {  // free one allocation early
+    for (size_t i = 0; i < ptrs.size(); ++i)
+      if (ptrs[i] == p) {
+        cudaFree(p);
+        ptrs[i] = ptrs.back();
+        ptrs.pop_back();
+        return;
+      }
+  }
+};
+
+// ---------------------------------------------------------------- sparse matrices
+template <typename T>
+struct Csr {
+  int nrows = 0, ncols = 0;
+  int64_t nnz = 0;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  T* val = nullptr;
+};
+
+constexpr int TPB = 256;  // threads per block of the plain node-parallel kernels
+inline int blocks_for(int64_t n, int tpb = TPB) { return (int)((n + tpb - 1) / tpb); }
+// fixed grid for deterministic grid-stride reductions: a multiple of the 152 SMs
+constexpr int RED_BLOCKS_MAX = 152 * 4;
+inline int red_blocks(int64_t n) {
+  int b = blocks_for(n);
+  return b < RED_BLOCKS_MAX ? (b < 1 ? 1 : b) : RED_BLOCKS_MAX;
+}
+
+// ---------------------------------------------------------------- primitives (sparse.cu)
+// exclusive scan of n int64 values in place; returns the total in *total (host)
+ch_status scan_i64(int64_t* data, int64_t n, int64_t* total, cudaStream_t st, Alloc& tmp);
+ch_status scan_i32_to_rowptr(const int* counts, int* rowptr, int n, int64_t* total,
+                             cudaStream_t st, Alloc& tmp);
+// incidence lists: for each of nitems items with k entries (ids in [0,nkeys)), build the
+// key -> sorted item list (CSR)
+ch_status build_incidence(const int* items, int nitems, int k, int nkeys, int** ptr, int** list,
+                          cudaStream_t st, Alloc& mem);
+// C = A * B (fp64, deterministic), allocated in mem
+ch_status spgemm(const Csr<double>& A, const Csr<double>& B, Csr<double>* C, cudaStream_t st,
+                 Alloc& mem);
+// B = A^T (fp64), allocated in mem
+ch_status transpose(const Csr<double>& A, Csr<double>* B, cudaStream_t st, Alloc& mem);
+
+// ---------------------------------------------------------------- launch accounting (prof.cu)
+enum KernelId {
+  K_RHS, K_LOADS, K_APPLY_A, K_RESIDUAL4, K_ORTH0, K_ORTH1, K_ORTH2, K_SCALE4, K_UPDATE_X,
+  K_CYCLE_SOLVE, K_FLAGS, K_MASS, K_CHEB_FIRST, K_CHEB_STEP, K_VRESIDUAL, K_RESTRICT, K_PROLONG,
+  K_COARSE, K_VLOAD, K_VSTORE, K_SPMV_M, K_STATE_IO, K_COUNT
+};
+// RAII around one kernel launch: counts it with its algorithmic bytes / FMAs and, when timing
+// is on, records CUDA events around it on the launching stream.
+class ProfScope {
+ public:
+  ProfScope(cudaStream_t st, int kid, int f32, double bytes, double fmas);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  cudaStream_t st_;
+  int slot_;
+  double bytes_, fmas_;
+  cudaEvent_t e0_ = nullptr, e1_ = nullptr;
+};
+void prof_drain();
+
+}  // namespace ch
+
+// ---------------------------------------------------------------- opaque handles
+struct ch_mesh_s {
+  ch_params p{};
+  int dim = 2, N = 0, E = 0, Fb = 0, Ft = 0;
+  double* coords = nullptr;   // N x dim
+  int* elems = nullptr;       // E x (dim+1)
+  int* bot = nullptr;         // Fb x dim
+  int* top = nullptr;         // Ft x dim
+  double* vol = nullptr;      // E element measures
+  double* bvol = nullptr;     // Fb facet measures
+  double* tvol = nullptr;     // Ft facet measures
+  int *n2e_ptr = nullptr, *n2e = nullptr;  // node -> incident elements (sorted)
+  int *n2b_ptr = nullptr, *n2b = nullptr;  // node -> incident bottom facets
+  int *n2t_ptr = nullptr, *n2t = nullptr;  // node -> incident top facets
+  ch::Alloc mem;
+};
+
+struct ch_system_s {
+  const ch_mesh_s* mesh = nullptr;
+  ch_params p{};
+  int N = 0;
+  int64_t nnz = 0;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* valM = nullptr;
+  double* valK = nullptr;
+  double* valH = nullptr;
+  int* diag = nullptr;  // position of the diagonal entry of each row
+  double a = 0, c = 0;  // A = [[M, aK], [aK, -cM]]
+  ch::Alloc mem;
+};
+
+namespace ch {
+struct Hierarchy;  // amg.cu
+ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precision,
+                          cudaStream_t st, Hierarchy** out);
+void hierarchy_free(Hierarchy* h);
+int hierarchy_levels(const Hierarchy* h);
+void hierarchy_level_size(const Hierarchy* h, int l, int64_t* rows, int64_t* nnz);
+// x (N x 2, fp64, row stride ldx) ~ A^-1 b (N x 2, fp64, row stride ldb), ncyc V-cycles
+ch_status hierarchy_solve(Hierarchy* h, const double* b, int ldb, double* x, int ldx, int ncyc,
+                          cudaStream_t st);
+// y (N x 2, fp64, stride ldy) = A0 x (N x 2, fp64, stride ldx) in the hierarchy's working precision
+ch_status hierarchy_apply_fine(Hierarchy* h, const double* x, int ldx, double* y, int ldy,
+                               cudaStream_t st);
+
+// assemble.cu
+ch_status loads(const ch_system_s* s, const double* pp, const double* pn, double* Fp, double* Fn,
+                double* gp, double* gn, cudaStream_t st);
+// b (N x 4) from phi_p, phi_nfa read with element stride ld
+ch_status rhs_strided(const ch_system_s* s, const double* pp, const double* pn, int ld, double* b,
+                      cudaStream_t st);
+ch_status mesh_build(ch_mesh_s* m, cudaStream_t st);
+ch_status assemble_system(const ch_mesh_s* m, ch_system_s* s, cudaStream_t st);
+ch_status apply_A(const ch_system_s* s, const double* x, double* y, cudaStream_t st);
+}  // namespace ch
+
+struct ch_precond_s {
+  const ch_system_s* sys = nullptr;
+  int precision = 0;
+  ch::Hierarchy* hM = nullptr;
+  ch::Hierarchy* hH = nullptr;
+  double* t1 = nullptr;  // N x 2 temporaries for Algorithm 1
+  double* t2 = nullptr;
+  ch::Alloc mem;
+  ~ch_precond_s() {
+    ch::hierarchy_free(hM);
+    ch::hierarchy_free(hH);
+  }
+};
+
+struct ch_state_s;
+namespace ch {
+ch_status precond_apply(ch_precond_s* pc, const double* v, double* w, cudaStream_t st);
+const char* last_error();
+ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, ch_state_s** out);
+void state_destroy(ch_state_s* S);
+ch_status state_set(ch_state_s* S, const double* pp, const double* pn, const double* mp,
+                    const double* mn, cudaStream_t st);
+ch_status state_seeded(ch_state_s* S, double p0, double n0, double noise, uint64_t seed,
+                       cudaStream_t st);
+ch_status state_get(const ch_state_s* S, double* pp, double* pn, double* ps, double* mp, double* mn,
+                    cudaStream_t st);
+ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats);
+}

@@ -1,0 +1,644 @@
+// Flexible GMRES(m) in FP64 for the two saddle-point systems of one time step (Eq. (14)),
+// right-preconditioned by Algorithm 1, plus the time-step driver.
+//
+// The paper solves each system with preconditioned MINRES (Section 4).  MINRES needs a
+// fixed symmetric positive definite preconditioner; one AMG V-cycle with Chebyshev
+// smoothing (and its FP32 variant) is neither exactly fixed nor symmetric, so the outer
+// method here is flexible GMRES (Saad 1993), which allows the preconditioner to vary.
+// Both species advance in lockstep: every kernel processes the N x 4 node-major vectors
+// (phi_p, phi_n, mu_p, mu_n) of both systems, while Hessenberg matrices, Givens rotations
+// and convergence flags are kept per system.  Orthogonalisation is classical Gram-Schmidt
+// with one re-orthogonalisation (CGS2), its inner products reduced in a fixed order by the
+// last thread block to finish (no floating-point atomics: runs are bitwise reproducible).
+#include <cmath>
+
+#include "ch_internal.cuh"
+
+namespace ch {
+
+constexpr int MAXM = 64;
+constexpr int MAXV = 2 * (MAXM + 1);  // reduced values per kernel (2 systems x (j+1))
+
+struct KrylovDev {
+  double R[2][MAXM][MAXM];  // upper-triangular factor after Givens (column j in R[s][.][j])
+  double cs[2][MAXM], sn[2][MAXM], g[2][MAXM + 1], y[2][MAXM];
+  double h1[2][MAXM + 1], h2[2][MAXM + 1];
+  double hinv[2], beta[2], bnorm[2], relres[2], tol[2], mass[2];
+  int active[2];        // system still unsolved this step
+  int cycle_active[2];  // system still iterating in the current restart cycle
+  int k[2];             // Arnoldi steps taken in the current cycle
+  int its[2];           // Arnoldi steps taken this step
+  int nonfinite;
+  unsigned int ticket;  // last-block counter
+};
+
+struct Flags {
+  int cycle_active[2];
+  int active[2];
+  int nonfinite;
+  int pad;
+  double relres[2];
+};
+
+// ---------------------------------------------------------------- block reductions
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* [TPB/32][NV] */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sm[w * NV + k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int q = 0; q < TPB / 32; ++q) s += sm[q * NV + threadIdx.x];
+    sm[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// After a block has written its nv partials, returns true in the last block to finish, which
+// then reads every block's partials in block order.
+__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(ticket, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+__device__ void reduce_partials(const double* partials, int nv, double* out) {
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += partials[(size_t)b * MAXV + v];
+    out[v] = s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- residual / norms
+// W = b - A x (both systems), then the last block computes ||b_s||, ||r_s||, relres and sets
+// active / cycle flags, beta and g for a (re)start.  If init, also tol_s = rtol ||b_s||.
+__global__ void k_residual4(int N, const int* rowptr, const int* col, const double* valM,
+                            const double* valK, double a, double c, const double4_32a* x,
+                            const double4_32a* b, double4_32a* W, double* partials, KrylovDev* kd,
+                            int init, double rtol) {
+  __shared__ double sm[(TPB / 32) * 4];
+  double acc[4] = {0, 0, 0, 0};  // ||b_p||^2, ||b_n||^2, ||r_p||^2, ||r_n||^2
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+    double m1p = 0, m1n = 0, m2p = 0, m2n = 0, k1p = 0, k1n = 0, k2p = 0, k2n = 0;
+    for (int q = rowptr[v]; q < rowptr[v + 1]; ++q) {
+      const int j = col[q];
+      const double m = valM[q], k = valK[q];
+      const double4_32a z = x[j];
+      m1p = fma(m, z.x, m1p);
+      m1n = fma(m, z.y, m1n);
+      m2p = fma(m, z.z, m2p);
+      m2n = fma(m, z.w, m2n);
+      k1p = fma(k, z.x, k1p);
+      k1n = fma(k, z.y, k1n);
+      k2p = fma(k, z.z, k2p);
+      k2n = fma(k, z.w, k2n);
+    }
+    const double4_32a bb = b[v];
+    double4_32a r;
+    r.x = bb.x - fma(a, k2p, m1p);
+    r.y = bb.y - fma(a, k2n, m1n);
+    r.z = bb.z - fma(a, k1p, -c * m2p);
+    r.w = bb.w - fma(a, k1n, -c * m2n);
+    W[v] = r;
+    acc[0] += bb.x * bb.x + bb.z * bb.z;
+    acc[1] += bb.y * bb.y + bb.w * bb.w;
+    acc[2] += r.x * r.x + r.z * r.z;
+    acc[3] += r.y * r.y + r.w * r.w;
+  }
+  block_sum<4>(acc, sm);
+  if (threadIdx.x < 4) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = sm[threadIdx.x];
+  if (!last_block(&kd->ticket)) return;
+  __shared__ double tot[4];
+  reduce_partials(partials, 4, tot);
+  if (threadIdx.x < 2) {
+    const int s = threadIdx.x;
+    const double bn = sqrt(tot[s]), rn = sqrt(tot[2 + s]);
+    if (init) {
+      kd->bnorm[s] = bn;
+      kd->tol[s] = rtol * bn;
+      kd->its[s] = 0;
+      kd->active[s] = 1;
+    }
+    if (!isfinite(bn) || !isfinite(rn)) kd->nonfinite = 1;
+    kd->relres[s] = bn > 0.0 ? rn / bn : 0.0;
+    const int act = kd->active[s] && rn > kd->tol[s] && bn > 0.0;
+    kd->active[s] = act;
+    kd->cycle_active[s] = act;
+    kd->k[s] = 0;
+    kd->beta[s] = rn;
+    kd->g[s][0] = rn;
+    kd->hinv[s] = (act && rn > 0.0) ? 1.0 / rn : 0.0;
+  }
+  if (threadIdx.x == 0) kd->ticket = 0;
+}
+
+// dst = src * hinv[s] per system (components x,z -> system 0, y,w -> system 1)
+__global__ void k_scale4(int N, const double4_32a* src, double4_32a* dst, const KrylovDev* kd) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  const double s0 = kd->hinv[0], s1 = kd->hinv[1];
+  const double4_32a a = src[v];
+  dst[v] = make_double4_32a(a.x * s0, a.y * s1, a.z * s0, a.w * s1);
+}
+
+// ---------------------------------------------------------------- CGS2 passes
+// MODE 0: h1[s][k] = <V_k, W>_s                       k = 0..nv-1
+// MODE 1: W -= sum_k h1[s][k] V_k;  h2[s][k] = <V_k, W>_s
+// MODE 2: W -= sum_k h2[s][k] V_k;  ||W||_s^2, then the Hessenberg / Givens update (last block)
+constexpr int KC = 8;  // basis vectors per register chunk
+
+template <int MODE>
+__global__ void __launch_bounds__(TPB) k_orth(int N, int nv, const double4_32a* __restrict__ V,
+                                               double4_32a* __restrict__ W, double* partials,
+                                               KrylovDev* kd) {
+  __shared__ double sm[(TPB / 32) * 2 * KC];
+  __shared__ double coef[2][MAXM + 1];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  if (MODE >= 1) {
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+      coef[0][k] = MODE == 1 ? kd->h1[0][k] : kd->h2[0][k];
+      coef[1][k] = MODE == 1 ? kd->h1[1][k] : kd->h2[1][k];
+    }
+    __syncthreads();
+    for (int v = tid; v < N; v += stride) {
+      double4_32a w = W[v];
+      for (int k = 0; k < nv; ++k) {
+        const double4_32a q = V[(size_t)k * N + v];
+        const double c0 = coef[0][k], c1 = coef[1][k];
+        w.x = fma(-c0, q.x, w.x);
+        w.z = fma(-c0, q.z, w.z);
+        w.y = fma(-c1, q.y, w.y);
+        w.w = fma(-c1, q.w, w.w);
+      }
+      W[v] = w;
+    }
+  }
+  if (MODE <= 1) {
+    for (int k0 = 0; k0 < nv; k0 += KC) {
+      double acc[2 * KC];
+#pragma unroll
+      for (int t = 0; t < 2 * KC; ++t) acc[t] = 0.0;
+      for (int v = tid; v < N; v += stride) {
+        const double4_32a w = W[v];
+#pragma unroll
+        for (int t = 0; t < KC; ++t) {
+          if (k0 + t < nv) {
+            const double4_32a q = V[(size_t)(k0 + t) * N + v];
+            acc[2 * t] = fma(q.x, w.x, fma(q.z, w.z, acc[2 * t]));
+            acc[2 * t + 1] = fma(q.y, w.y, fma(q.w, w.w, acc[2 * t + 1]));
+          }
+        }
+      }
+      block_sum<2 * KC>(acc, sm);
+      for (int t = threadIdx.x; t < 2 * KC; t += blockDim.x) {
+        const int k = k0 + t / 2;
+        if (k < nv) partials[(size_t)blockIdx.x * MAXV + 2 * k + (t & 1)] = sm[t];
+      }
+      __syncthreads();
+    }
+    if (!last_block(&kd->ticket)) return;
+    __shared__ double tot[MAXV];
+    reduce_partials(partials, 2 * nv, tot);
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+      double* dst0 = MODE == 0 ? kd->h1[0] : kd->h2[0];
+      double* dst1 = MODE == 0 ? kd->h1[1] : kd->h2[1];
+      dst0[k] = tot[2 * k];
+      dst1[k] = tot[2 * k + 1];
+    }
+    if (threadIdx.x == 0) kd->ticket = 0;
+  } else {
+    double acc[2] = {0.0, 0.0};
+    for (int v = tid; v < N; v += stride) {
+      const double4_32a w = W[v];
+      acc[0] = fma(w.x, w.x, fma(w.z, w.z, acc[0]));
+      acc[1] = fma(w.y, w.y, fma(w.w, w.w, acc[1]));
+    }
+    block_sum<2>(acc, sm);
+    if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = sm[threadIdx.x];
+    if (!last_block(&kd->ticket)) return;
+    __shared__ double tot[2];
+    reduce_partials(partials, 2, tot);
+    if (threadIdx.x < 2) {
+      const int s = threadIdx.x;
+      const int j = nv - 1;  // Arnoldi column
+      if (kd->cycle_active[s]) {
+        double h[MAXM + 1];
+        for (int k = 0; k <= j; ++k) h[k] = kd->h1[s][k] + kd->h2[s][k];
+        const double hn = sqrt(tot[s]);
+        h[j + 1] = hn;
+        for (int k = 0; k < j; ++k) {  // previous rotations
+          const double t = kd->cs[s][k] * h[k] + kd->sn[s][k] * h[k + 1];
+          h[k + 1] = -kd->sn[s][k] * h[k] + kd->cs[s][k] * h[k + 1];
+          h[k] = t;
+        }
+        const double den = hypot(h[j], h[j + 1]);
+        double cs = 1.0, sn = 0.0;
+        if (den > 0.0) {
+          cs = h[j] / den;
+          sn = h[j + 1] / den;
+        }
+        kd->cs[s][j] = cs;
+        kd->sn[s][j] = sn;
+        h[j] = den;
+        for (int k = 0; k <= j; ++k) kd->R[s][k][j] = h[k];
+        const double gj = kd->g[s][j];
+        kd->g[s][j + 1] = -sn * gj;
+        kd->g[s][j] = cs * gj;
+        kd->k[s] = j + 1;
+        kd->its[s] += 1;
+        if (!isfinite(hn) || !isfinite(den)) kd->nonfinite = 1;
+        const bool breakdown = !(hn > 1e-300);
+        kd->hinv[s] = breakdown ? 0.0 : 1.0 / hn;
+        if (fabs(kd->g[s][j + 1]) <= kd->tol[s] || breakdown || den == 0.0) kd->cycle_active[s] = 0;
+      } else {
+        kd->hinv[s] = 0.0;
+      }
+    }
+    if (threadIdx.x == 0) kd->ticket = 0;
+  }
+}
+
+// y_s = R_s^-1 g_s (back substitution, k_s x k_s)
+__global__ void k_cycle_solve(KrylovDev* kd) {
+  const int s = threadIdx.x;
+  if (s >= 2) return;
+  const int k = kd->k[s];
+  for (int i = k - 1; i >= 0; --i) {
+    double t = kd->g[s][i];
+    for (int q = i + 1; q < k; ++q) t -= kd->R[s][i][q] * kd->y[s][q];
+    kd->y[s][i] = kd->R[s][i][i] != 0.0 ? t / kd->R[s][i][i] : 0.0;
+  }
+  for (int i = k; i < MAXM; ++i) kd->y[s][i] = 0.0;
+}
+
+// x += sum_k y_s[k] Z_k
+__global__ void k_update_x(int N, int kmax, const double4_32a* __restrict__ Z, double4_32a* x,
+                           const KrylovDev* kd) {
+  __shared__ double y[2][MAXM];
+  for (int k = threadIdx.x; k < kmax; k += blockDim.x) {
+    y[0][k] = kd->y[0][k];
+    y[1][k] = kd->y[1][k];
+  }
+  __syncthreads();
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  double4_32a a = x[v];
+  for (int k = 0; k < kmax; ++k) {
+    const double4_32a z = Z[(size_t)k * N + v];
+    a.x = fma(y[0][k], z.x, a.x);
+    a.z = fma(y[0][k], z.z, a.z);
+    a.y = fma(y[1][k], z.y, a.y);
+    a.w = fma(y[1][k], z.w, a.w);
+  }
+  x[v] = a;
+}
+
+__global__ void k_flags(const KrylovDev* kd, Flags* f) {
+  if (threadIdx.x == 0) {
+    f->cycle_active[0] = kd->cycle_active[0];
+    f->cycle_active[1] = kd->cycle_active[1];
+    f->active[0] = kd->active[0];
+    f->active[1] = kd->active[1];
+    f->nonfinite = kd->nonfinite;
+    f->relres[0] = kd->relres[0];
+    f->relres[1] = kd->relres[1];
+  }
+}
+
+// mass_s = sum_i (M 1)_i phi_s,i  (M symmetric: 1^T M phi)
+__global__ void k_mass(int N, const double* mlump, const double4_32a* x, double* partials,
+                       KrylovDev* kd) {
+  __shared__ double sm[(TPB / 32) * 2];
+  double acc[2] = {0.0, 0.0};
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+    const double4_32a a = x[v];
+    acc[0] = fma(mlump[v], a.x, acc[0]);
+    acc[1] = fma(mlump[v], a.y, acc[1]);
+  }
+  block_sum<2>(acc, sm);
+  if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = sm[threadIdx.x];
+  if (!last_block(&kd->ticket)) return;
+  __shared__ double tot[2];
+  reduce_partials(partials, 2, tot);
+  if (threadIdx.x < 2) kd->mass[threadIdx.x] = tot[threadIdx.x];
+  if (threadIdx.x == 0) kd->ticket = 0;
+}
+
+__global__ void k_rowsum(int N, const int* rowptr, const double* val, double* out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  double s = 0.0;
+  for (int q = rowptr[v]; q < rowptr[v + 1]; ++q) s += val[q];
+  out[v] = s;
+}
+
+}  // namespace ch
+
+// ---------------------------------------------------------------- state
+struct ch_state_s {
+  const ch_system_s* sys = nullptr;
+  ch_precond_s* pc = nullptr;
+  int N = 0, m = 0;
+  double* x = nullptr;  // N x 4: the state (phi_p, phi_n, mu_p, mu_n)
+  double* b = nullptr;  // N x 4
+  double* W = nullptr;  // N x 4
+  double* V = nullptr;  // (m+1) x N x 4
+  double* Z = nullptr;  // m x N x 4
+  double* mlump = nullptr;
+  double* partials = nullptr;
+  ch::KrylovDev* kd = nullptr;
+  ch::Flags* dflags = nullptr;
+  ch::Flags* hflags = nullptr;  // pinned
+  bool set = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  ch::Alloc mem;
+  ~ch_state_s() {
+    if (hflags) cudaFreeHost(hflags);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+};
+
+namespace ch {
+
+ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, ch_state_s** out) {
+  const int m = s->p.restart;
+  if (m < 1 || m > MAXM) {
+    set_error("restart must be in [1, %d]", MAXM);
+    return CH_ERR_ARG;
+  }
+  ch_state_s* S = new ch_state_s();
+  S->sys = s;
+  S->pc = pc;
+  S->N = s->N;
+  S->m = m;
+  const size_t n4 = (size_t)s->N * 4;
+  ch_status r = CH_OK;
+  if (r == CH_OK) r = S->mem.get(&S->x, n4);
+  if (r == CH_OK) r = S->mem.get(&S->b, n4);
+  if (r == CH_OK) r = S->mem.get(&S->W, n4);
+  if (r == CH_OK) r = S->mem.get(&S->V, n4 * (m + 1));
+  if (r == CH_OK) r = S->mem.get(&S->Z, n4 * m);
+  if (r == CH_OK) r = S->mem.get(&S->mlump, (size_t)s->N);
+  if (r == CH_OK) r = S->mem.get(&S->partials, (size_t)RED_BLOCKS_MAX * MAXV);
+  if (r == CH_OK) r = S->mem.get(&S->kd, 1);
+  if (r == CH_OK) r = S->mem.get(&S->dflags, 1);
+  if (r == CH_OK && cudaMallocHost(&S->hflags, sizeof(Flags)) != cudaSuccess) {
+    set_error("pinned allocation failed");
+    S->hflags = nullptr;
+    r = CH_ERR_OOM;
+  }
+  if (r == CH_OK && (cudaEventCreate(&S->ev0) != cudaSuccess || cudaEventCreate(&S->ev1) != cudaSuccess)) {
+    set_error("event creation failed");
+    r = CH_ERR_CUDA;
+  }
+  if (r == CH_OK) {
+    cudaMemsetAsync(S->kd, 0, sizeof(KrylovDev), st);
+    cudaMemsetAsync(S->x, 0, n4 * sizeof(double), st);
+    k_rowsum<<<blocks_for(s->N), TPB, 0, st>>>(s->N, s->rowptr, s->valM, S->mlump);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error("state initialisation failed");
+      r = CH_ERR_CUDA;
+    }
+  }
+  if (r != CH_OK) {
+    delete S;
+    return r;
+  }
+  *out = S;
+  return CH_OK;
+}
+
+void state_destroy(ch_state_s* S) { delete S; }
+
+static ch_status read_flags(ch_state_s* S, cudaStream_t st) {
+  {
+    ProfScope ps(st, K_FLAGS, 0, 0.0, 0.0);
+    k_flags<<<1, 32, 0, st>>>(S->kd, S->dflags);
+  }
+  CH_LAUNCHED();
+  CH_CUDA(cudaMemcpyAsync(S->hflags, S->dflags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  prof_drain();
+  return CH_OK;
+}
+
+static double res4_bytes(const ch_system_s* s) { return 20.0 * s->nnz + 4.0 * (s->N + 1) + 96.0 * s->N; }
+
+// Solve A x = b for both systems; x holds the initial guess on entry.
+static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
+  const ch_system_s* s = S->sys;
+  const ch_params& p = s->p;
+  const int N = S->N, m = S->m;
+  const int rb = red_blocks(N);
+  const double4_32a* b4 = reinterpret_cast<const double4_32a*>(S->b);
+  double4_32a* x4 = reinterpret_cast<double4_32a*>(S->x);
+  double4_32a* W4 = reinterpret_cast<double4_32a*>(S->W);
+  double4_32a* V4 = reinterpret_cast<double4_32a*>(S->V);
+  double4_32a* Z4 = reinterpret_cast<double4_32a*>(S->Z);
+  CH_CUDA(cudaMemsetAsync(&S->kd->nonfinite, 0, sizeof(int), st));
+  {
+    ProfScope ps(st, K_RESIDUAL4, 0, res4_bytes(s), 8.0 * s->nnz + 12.0 * N);
+    k_residual4<<<rb, TPB, 0, st>>>(N, s->rowptr, s->col, s->valM, s->valK, s->a, s->c, x4, b4, W4,
+                                    S->partials, S->kd, 1, p.rtol);
+  }
+  CH_LAUNCHED();
+  CH_TRY(read_flags(S, st));
+  if (S->hflags->nonfinite) {
+    set_error("non-finite right-hand side or initial residual");
+    return CH_ERR_NONFINITE;
+  }
+  int total = 0;
+  *restarts = 0;
+  while (S->hflags->active[0] || S->hflags->active[1]) {
+    if (total >= p.max_iter) {
+      set_error("FGMRES reached max_iter = %d (relres %.3e, %.3e)", p.max_iter,
+                S->hflags->relres[0], S->hflags->relres[1]);
+      return CH_ERR_NOT_CONVERGED;
+    }
+    {
+      ProfScope ps(st, K_SCALE4, 0, 64.0 * N, 0.0);
+      k_scale4<<<blocks_for(N), TPB, 0, st>>>(N, W4, V4, S->kd);  // V_0 = r / beta
+    }
+    CH_LAUNCHED();
+    int j = 0;
+    for (; j < m; ++j) {
+      double4_32a* Vj = V4 + (size_t)j * N;
+      double4_32a* Zj = Z4 + (size_t)j * N;
+      CH_TRY(precond_apply(S->pc, reinterpret_cast<double*>(Vj), reinterpret_cast<double*>(Zj), st));
+      CH_TRY(apply_A(s, reinterpret_cast<double*>(Zj), S->W, st));
+      const double nv = j + 1, n32 = 32.0 * N;
+      {
+        ProfScope ps(st, K_ORTH0, 0, (nv + 1) * n32, 4.0 * nv * N);
+        k_orth<0><<<rb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+      }
+      {
+        ProfScope ps(st, K_ORTH1, 0, (nv + 2) * n32, 8.0 * nv * N);
+        k_orth<1><<<rb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+      }
+      {
+        ProfScope ps(st, K_ORTH2, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
+        k_orth<2><<<rb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+      }
+      {
+        ProfScope ps(st, K_SCALE4, 0, 64.0 * N, 0.0);
+        k_scale4<<<blocks_for(N), TPB, 0, st>>>(N, W4, V4 + (size_t)(j + 1) * N, S->kd);
+      }
+      CH_LAUNCHED();
+      ++total;
+      CH_TRY(read_flags(S, st));
+      if (S->hflags->nonfinite) {
+        set_error("non-finite value in the Arnoldi process");
+        return CH_ERR_NONFINITE;
+      }
+      if (!(S->hflags->cycle_active[0] || S->hflags->cycle_active[1]) || total >= p.max_iter) {
+        ++j;
+        break;
+      }
+    }
+    if (j > m) j = m;
+    {
+      ProfScope ps(st, K_CYCLE_SOLVE, 0, 0.0, 0.0);
+      k_cycle_solve<<<1, 32, 0, st>>>(S->kd);
+    }
+    {
+      ProfScope ps(st, K_UPDATE_X, 0, (j + 2) * 32.0 * N, 4.0 * j * N);
+      k_update_x<<<blocks_for(N), TPB, 0, st>>>(N, j, Z4, x4, S->kd);
+    }
+    {
+      ProfScope ps(st, K_RESIDUAL4, 0, res4_bytes(s), 8.0 * s->nnz + 12.0 * N);
+      k_residual4<<<rb, TPB, 0, st>>>(N, s->rowptr, s->col, s->valM, s->valK, s->a, s->c, x4, b4,
+                                      W4, S->partials, S->kd, 0, p.rtol);
+    }
+    CH_LAUNCHED();
+    CH_TRY(read_flags(S, st));
+    if (S->hflags->nonfinite) {
+      set_error("non-finite residual");
+      return CH_ERR_NONFINITE;
+    }
+    ++*restarts;
+  }
+  return CH_OK;
+}
+
+__global__ void k_set_state(int N, const double* pp, const double* pn, const double* mp,
+                            const double* mn, double4_32a* x) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  x[v] = make_double4_32a(pp[v], pn[v], mp ? mp[v] : 0.0, mn ? mn[v] : 0.0);
+}
+
+__global__ void k_get_state(int N, const double4_32a* x, double* pp, double* pn, double* ps, double* mp,
+                            double* mn) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  const double4_32a a = x[v];
+  if (pp) pp[v] = a.x;
+  if (pn) pn[v] = a.y;
+  if (ps) ps[v] = 1.0 - a.x - a.y;  // Eq. (2)
+  if (mp) mp[v] = a.z;
+  if (mn) mn[v] = a.w;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) on the counter seed ^ (field << 40) ^ node
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_seeded(int N, double p0, double n0, double noise, uint64_t seed, double4_32a* x) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  const double up = (double)(splitmix64(seed ^ (0ULL << 40) ^ (uint64_t)v) >> 11) * 0x1.0p-53;
+  const double un = (double)(splitmix64(seed ^ (1ULL << 40) ^ (uint64_t)v) >> 11) * 0x1.0p-53;
+  x[v] = make_double4_32a(p0 + noise * (2.0 * up - 1.0), n0 + noise * (2.0 * un - 1.0), 0.0, 0.0);
+}
+
+ch_status state_set(ch_state_s* S, const double* pp, const double* pn, const double* mp,
+                    const double* mn, cudaStream_t st) {
+  ProfScope prof_io(st, K_STATE_IO, 0, 72.0 * S->N, 0.0);
+  k_set_state<<<blocks_for(S->N), TPB, 0, st>>>(S->N, pp, pn, mp, mn,
+                                                 reinterpret_cast<double4_32a*>(S->x));
+  CH_LAUNCHED();
+  S->set = true;
+  return CH_OK;
+}
+
+ch_status state_seeded(ch_state_s* S, double p0, double n0, double noise, uint64_t seed,
+                       cudaStream_t st) {
+  ProfScope prof_io(st, K_STATE_IO, 0, 72.0 * S->N, 0.0);
+  k_seeded<<<blocks_for(S->N), TPB, 0, st>>>(S->N, p0, n0, noise, seed,
+                                              reinterpret_cast<double4_32a*>(S->x));
+  CH_LAUNCHED();
+  S->set = true;
+  return CH_OK;
+}
+
+ch_status state_get(const ch_state_s* S, double* pp, double* pn, double* ps, double* mp, double* mn,
+                    cudaStream_t st) {
+  ProfScope prof_io(st, K_STATE_IO, 0, 72.0 * S->N, 0.0);
+  k_get_state<<<blocks_for(S->N), TPB, 0, st>>>(S->N, reinterpret_cast<const double4_32a*>(S->x), pp,
+                                                 pn, ps, mp, mn);
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats) {
+  if (!S->set) {
+    set_error("state not initialised (call ch_state_set or ch_state_init_seeded)");
+    return CH_ERR_STATE;
+  }
+  CH_CUDA(cudaEventRecord(S->ev0, st));
+  // right-hand sides from phi^k (strided views of the state)
+  CH_TRY(rhs_strided(S->sys, S->x, S->x + 1, 4, S->b, st));
+  int restarts = 0;
+  ch_status r = fgmres(S, st, &restarts);
+  const int rb = red_blocks(S->N);
+  {
+    ProfScope ps(st, K_MASS, 0, 40.0 * S->N, 2.0 * S->N);
+    k_mass<<<rb, TPB, 0, st>>>(S->N, S->mlump, reinterpret_cast<const double4_32a*>(S->x),
+                               S->partials, S->kd);
+  }
+  CH_CUDA(cudaEventRecord(S->ev1, st));
+  if (stats) {
+    KrylovDev* kd = S->kd;
+    int its[2];
+    double rel[2], mass[2];
+    CH_CUDA(cudaMemcpyAsync(its, kd->its, sizeof(its), cudaMemcpyDeviceToHost, st));
+    CH_CUDA(cudaMemcpyAsync(rel, kd->relres, sizeof(rel), cudaMemcpyDeviceToHost, st));
+    CH_CUDA(cudaMemcpyAsync(mass, kd->mass, sizeof(mass), cudaMemcpyDeviceToHost, st));
+    CH_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, S->ev0, S->ev1);
+    stats->iters[0] = its[0];
+    stats->iters[1] = its[1];
+    stats->restarts = restarts;
+    stats->status = r;
+    stats->relres[0] = rel[0];
+    stats->relres[1] = rel[1];
+    stats->mass[0] = mass[0];
+    stats->mass[1] = mass[1];
+    stats->ms = ms;
+  }
+  return r;
+}
+
+}  // namespace ch
