@@ -152,6 +152,26 @@ ch_status ch_vcycle(ch_precond_t* pc, int32_t which, int32_t vcycles, const doub
                     void* stream);
 void ch_precond_destroy(ch_precond_t* pc);
 
+/* Allocation-free V-cycles.  The paper has no counterpart to this call: it exists for callers
+ * that must not allocate device memory while they run -- for example code recorded into a CUDA
+ * graph by stream capture (where cudaMalloc is not allowed), applications whose device memory is
+ * owned by a framework's caching allocator with a fixed budget, or latency-critical loops that
+ * cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * It computes exactly what ch_vcycle computes (same kernels, same order; strides 2), but every
+ * per-level work vector lives in one static device array of 8 MiB that each GPU loading the
+ * library reserves until the process exits.  The only other device memory it touches is the
+ * caller's b and x and the hierarchy built earlier by ch_precond_setup (read only).
+ *  - Limit: 5 work vectors x 2 right-hand sides per level must fit in 8 MiB, i.e. the level
+ *    sizes summed over the hierarchy may not exceed about 104,000 rows with precision 0 (FP64)
+ *    or 209,000 with precision 1 (FP32); larger hierarchies return CH_ERR_ARG with a message.
+ *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream capture on the device.
+ *  - All calls share the one array and keep the last call's contents (nothing in it needs to
+ *    start at zero).  Calls that overlap on the GPU -- different streams or threads at the same
+ *    time -- race and give wrong results: issue them in order on one stream. */
+ch_status ch_vcycle_noalloc(ch_precond_t* pc, int32_t which, int32_t vcycles, const double* b,
+                            double* x, void* stream);
+
 /* ---------------------------------------------------------------- time stepping (Eq. (12)-(14))
  * A state holds (phi_p, phi_nfa, mu_p, mu_nfa) on the device plus all FGMRES work space, so
  * ch_step allocates nothing. */

@@ -96,6 +96,7 @@ _SIGNATURES = {
     "ch_precond_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "ch_vcycle": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
     "ch_precond_destroy": (None, [_VP]),
+    "ch_vcycle_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
     "ch_state_create": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(_VP)]),
     "ch_state_set": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "ch_state_init_seeded": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -255,6 +256,14 @@ class Precond:
         b = _f64(b, self.system.n)
         x = torch.empty_like(b)
         _check(lib().ch_vcycle(self._h, which, vcycles, _ptr(b), _ptr(x), _stream(stream)), "ch_vcycle")
+        return x
+
+    def vcycle_noalloc(self, which: int, b, vcycles: int = 1, stream=None):
+        """ch_vcycle_noalloc: the same V-cycles with work space in the library's static array."""
+        b = _f64(b, self.system.n)
+        x = torch.empty_like(b)
+        _check(lib().ch_vcycle_noalloc(self._h, which, vcycles, _ptr(b), _ptr(x), _stream(stream)),
+               "ch_vcycle_noalloc")
         return x
 
     def __del__(self):

@@ -14,6 +14,7 @@
 // order, so the hierarchy is bitwise reproducible.  V-cycles run in FP64 or FP32 on two
 // right-hand sides at once (the two species share M and H).
 #include <cmath>
+#include <mutex>
 #include <type_traits>
 
 #include "ch_internal.cuh"
@@ -834,6 +835,141 @@ ch_status precond_apply(ch_precond_s* pc, const double* v, double* w, cudaStream
   if (pc->precision == 0)
     return precond_t<double>(pc, pc->hM->Ld, pc->hH->Ld, pc->hM->cinv, pc->hH->cinv, v, w, st);
   return precond_t<float>(pc, pc->hM->Lf, pc->hH->Lf, pc->hM->cinvf, pc->hH->cinvf, v, w, st);
+}
+
+}  // namespace ch
+
+// ---------------------------------------------------------------- allocation-free V-cycles
+// ch_vcycle_noalloc runs the same V-cycles as ch_vcycle, but the per-level work vectors
+// (x, x2, d, r, b for every level, two right-hand sides each) are carved out of one
+// file-scope device array instead of the preconditioner's own buffers, so a call needs no
+// device memory beyond the caller's b and x and the already-built hierarchy.  The array is
+// reserved in every GPU that loads the library for the life of the process.
+namespace ch {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(8) << 20;  // 8 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// The array's device address for the current device.  In host code the symbol names a host
+// stand-in, so the address is looked up once per device (with that device current) and cached.
+ch_status noalloc_scratch(void** out) {
+  int dev = -1;
+  CH_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    set_error("ch_vcycle_noalloc: device ordinal %d not supported (max %d)", dev, NOALLOC_MAX_DEVICES);
+    return CH_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      set_error("ch_vcycle_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return CH_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CH_OK;
+}
+}  // namespace
+
+template <typename T>
+static ch_status vcycle_static(Hierarchy* h, LevelT<T>* Ls, const T* cinv, int l, bool zero_guess,
+                               typename V2T<T>::t** xres, cudaStream_t st) {
+  using V2 = typename V2T<T>::t;
+  LevelT<T>& L = Ls[l];
+  const int n = L.A.nrows;
+  if (l == h->nlev - 1) {
+    k_dense_solve<T, V2><<<blocks_for((int64_t)n * 32), TPB, 0, st>>>(n, cinv, L.b, L.x);
+    CH_LAUNCHED();
+    *xres = L.x;
+    return CH_OK;
+  }
+  const ChebCoef c = cheb_coef(h->rho[l], h->cheb_degree);
+  V2* x = *xres;
+  auto smooth_static = [&](bool zg) {
+    V2* other = (x == L.x) ? L.x2 : L.x;
+    int s0 = 0;
+    if (zg) {
+      k_cheb_first<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.dinv, L.b, (T)c.invtheta, x, L.d);
+      s0 = 1;
+    }
+    for (int s = s0; s < h->cheb_degree; ++s) {
+      k_cheb_step<T, V2><<<blocks_for(n), TPB, 0, st>>>(L.A, L.dinv, L.b, x, L.d, other,
+                                                        (T)c.alpha[s], (T)c.beta[s]);
+      std::swap(x, other);
+    }
+  };
+  smooth_static(zero_guess);
+  LevelT<T>& C = Ls[l + 1];
+  k_residual<T, V2><<<blocks_for(n), TPB, 0, st>>>(L.A, L.b, x, L.r);
+  k_spmv2<T, V2, false><<<blocks_for(C.A.nrows), TPB, 0, st>>>(L.R, L.r, C.b);
+  CH_LAUNCHED();
+  V2* xc = C.x;
+  CH_TRY(vcycle_static<T>(h, Ls, cinv, l + 1, true, &xc, st));
+  k_spmv2<T, V2, true><<<blocks_for(n), TPB, 0, st>>>(L.P, xc, x);
+  smooth_static(false);
+  CH_LAUNCHED();
+  *xres = x;
+  return CH_OK;
+}
+
+template <typename T>
+static ch_status solve_static(Hierarchy* h, const std::vector<LevelT<T>>& src, const T* cinv,
+                              const double* b, double* x, int ncyc, cudaStream_t st) {
+  using V2 = typename V2T<T>::t;
+  constexpr int MAXLEV = 32;
+  if (h->nlev > MAXLEV) {
+    set_error("ch_vcycle_noalloc: hierarchy has %d levels (max %d)", h->nlev, MAXLEV);
+    return CH_ERR_ARG;
+  }
+  // 5 vectors of n_l pairs per level, each rounded up to 256 bytes
+  size_t need = 0;
+  for (int l = 0; l < h->nlev; ++l) need += 5 * ((src[l].A.nrows * sizeof(V2) + 255) / 256 * 256);
+  if (need > NOALLOC_SCRATCH_BYTES) {
+    set_error("ch_vcycle_noalloc: hierarchy needs %zu bytes of work space, the static array holds %zu "
+              "(use ch_vcycle for this size)", need, NOALLOC_SCRATCH_BYTES);
+    return CH_ERR_ARG;
+  }
+  void* base = nullptr;
+  CH_TRY(noalloc_scratch(&base));
+  LevelT<T> Ls[MAXLEV];
+  unsigned char* cur = static_cast<unsigned char*>(base);
+  auto carve = [&](int n) {
+    V2* p = reinterpret_cast<V2*>(cur);
+    cur += (n * sizeof(V2) + 255) / 256 * 256;
+    return p;
+  };
+  for (int l = 0; l < h->nlev; ++l) {
+    Ls[l] = src[l];  // matrices, diagonal inverses: the hierarchy's own
+    const int n = src[l].A.nrows;
+    Ls[l].x = carve(n);
+    Ls[l].x2 = carve(n);
+    Ls[l].d = carve(n);
+    Ls[l].r = carve(n);
+    Ls[l].b = carve(n);
+  }
+  // Every work vector is written before it is read (zero initial guesses are applied by the
+  // first Chebyshev step), so nothing in the array needs clearing between calls.
+  const int n0 = Ls[0].A.nrows;
+  k_load2<T, V2><<<blocks_for(n0), TPB, 0, st>>>(n0, b, 2, Ls[0].b);
+  CH_LAUNCHED();
+  V2* xr = Ls[0].x;
+  for (int c = 0; c < ncyc; ++c) CH_TRY(vcycle_static<T>(h, Ls, cinv, 0, c == 0, &xr, st));
+  k_store2<T, V2><<<blocks_for(n0), TPB, 0, st>>>(n0, xr, x, 2);
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+ch_status hierarchy_solve_noalloc(Hierarchy* h, const double* b, double* x, int ncyc, cudaStream_t st) {
+  if (h->precision == 0) return solve_static<double>(h, h->Ld, h->cinv, b, x, ncyc, st);
+  return solve_static<float>(h, h->Lf, h->cinvf, b, x, ncyc, st);
 }
 
 }  // namespace ch

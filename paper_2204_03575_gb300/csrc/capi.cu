@@ -261,6 +261,17 @@ ch_status ch_vcycle(ch_precond_t* pc, int32_t which, int32_t vcycles, const doub
 
 void ch_precond_destroy(ch_precond_t* pc) { delete pc; }
 
+ch_status ch_vcycle_noalloc(ch_precond_t* pc, int32_t which, int32_t vcycles, const double* b,
+                            double* x, void* stream) {
+  CH_ARG(pc != nullptr && b != nullptr && x != nullptr, "NULL argument");
+  CH_ARG(which == 0 || which == 1, "which must be 0 (M) or 1 (H)");
+  CH_ARG(vcycles >= 1, "vcycles must be >= 1");
+  CH_ARG(b != x, "b and x must not alias");
+  CH_ARG(((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15) == 0,
+         "b and x must be 16-byte aligned");
+  return ch::hierarchy_solve_noalloc(which == 0 ? pc->hM : pc->hH, b, x, vcycles, S(stream));
+}
+
 // ---------------------------------------------------------------- state and stepping
 ch_status ch_state_create(const ch_system_t* s, ch_precond_t* pc, void* stream, ch_state_t** out) {
   CH_ARG(out != nullptr, "out is NULL");

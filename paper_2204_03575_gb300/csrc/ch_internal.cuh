@@ -178,6 +178,8 @@ void hierarchy_level_size(const Hierarchy* h, int l, int64_t* rows, int64_t* nnz
 // x (N x 2, fp64, row stride ldx) ~ A^-1 b (N x 2, fp64, row stride ldb), ncyc V-cycles
 ch_status hierarchy_solve(Hierarchy* h, const double* b, int ldb, double* x, int ldx, int ncyc,
                           cudaStream_t st);
+// as hierarchy_solve (strides 2), work vectors in a static device array: no device allocation
+ch_status hierarchy_solve_noalloc(Hierarchy* h, const double* b, double* x, int ncyc, cudaStream_t st);
 // y (N x 2, fp64, stride ldy) = A0 x (N x 2, fp64, stride ldx) in the hierarchy's working precision
 ch_status hierarchy_apply_fine(Hierarchy* h, const double* x, int ldx, double* y, int ldy,
                                cudaStream_t st);
