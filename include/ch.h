@@ -73,11 +73,13 @@ typedef struct ch_params {
   double rtol;               /* stop when ||b - A x||_2 <= rtol ||b||_2 per species, default 1e-8 */
   int32_t restart;           /* FGMRES restart length m (1..64), default 30 */
   int32_t max_iter;          /* total FGMRES iterations per step, default 300 */
-  int32_t cheb_degree;       /* Chebyshev smoothing steps before and after coarse correction, default 2 */
+  int32_t cheb_degree;       /* Chebyshev smoothing steps before and after coarse correction, default 3 */
   int32_t coarse_max;        /* AMG: coarsest level is solved densely at or below this size, default 256 */
   double amg_theta;          /* AMG strength threshold, default 0.08 */
   int32_t vcycles_M;         /* V-cycles per application of M~^-1 (Algorithm 1, step 1), default 1 */
-  int32_t vcycles_H;         /* V-cycles per application of H~^-1 (Algorithm 1, steps 2 and 4), default 1 */
+  int32_t vcycles_H;         /* V-cycles per application of H~^-1 (Algorithm 1, steps 2 and 4), default 2 */
+  int32_t autotune;          /* SpMV lanes per row: 0 = fixed rule, 1 = timed at set-up (cached per process), default 1 */
+  double cheb_lower;         /* Chebyshev interval [cheb_lower, 1] x 1.1 lambda_max(D^-1 A), default 0.3 */
 } ch_params;
 
 /* Per-step statistics (host struct). */
@@ -143,6 +145,10 @@ ch_status ch_precond_setup(const ch_system_t* s, void* stream, ch_precond_t** ou
 /* which: 0 = M hierarchy, 1 = H hierarchy.  Host outputs; level-wise sizes for level < nlevels. */
 ch_status ch_precond_info(const ch_precond_t* pc, int32_t which, int32_t level, int32_t* nlevels,
                           int64_t* rows, int64_t* nnz);
+/* Lanes per row chosen for the level's A (smoothing, residual), R (restriction) and P
+ * (prolongation) SpMVs (host outputs; R and P are 0 on the coarsest level). */
+ch_status ch_precond_tiles(const ch_precond_t* pc, int32_t which, int32_t level, int32_t* tpr_A,
+                           int32_t* tpr_R, int32_t* tpr_P);
 /* Algorithm 1 on both species: w_1 ~ M^-1 v_1 and w_2 ~ H^-1 M H^-1 v_2 (AMG V-cycles).
  * v, w: N x 4 fp64, must not alias. */
 ch_status ch_precond_apply(ch_precond_t* pc, const double* v, double* w, void* stream);

@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
         ("h_p", ctypes.c_double), ("h_nfa", ctypes.c_double), ("rtol", ctypes.c_double),
         ("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("cheb_degree", ctypes.c_int32),
         ("coarse_max", ctypes.c_int32), ("amg_theta", ctypes.c_double),
-        ("vcycles_M", ctypes.c_int32), ("vcycles_H", ctypes.c_int32),
+        ("vcycles_M", ctypes.c_int32), ("vcycles_H", ctypes.c_int32), ("autotune", ctypes.c_int32),
+        ("cheb_lower", ctypes.c_double),
     ]
 
     def __init__(self, **kw):
@@ -94,6 +95,7 @@ _SIGNATURES = {
     "ch_precond_setup": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_VP)]),
     "ch_precond_info": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _I32P, _I64P, _I64P]),
     "ch_precond_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ch_precond_tiles": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _I32P, _I32P, _I32P]),
     "ch_vcycle": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
     "ch_precond_destroy": (None, [_VP]),
     "ch_vcycle_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
@@ -244,6 +246,16 @@ class Precond:
             _check(lib().ch_precond_info(self._h, which, l, None, ctypes.byref(r), ctypes.byref(z)),
                    "ch_precond_info")
             out.append((r.value, z.value))
+        return out
+
+    def tiles(self, which: int):
+        """[(lanes per row for A, R, P) per level] chosen by the SpMV autotuner."""
+        out = []
+        for l in range(len(self.levels(which))):
+            a, r, q = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+            _check(lib().ch_precond_tiles(self._h, which, l, ctypes.byref(a), ctypes.byref(r), ctypes.byref(q)),
+                   "ch_precond_tiles")
+            out.append((a.value, r.value, q.value))
         return out
 
     def apply(self, v, stream=None):

@@ -10,11 +10,13 @@
 //             rho the Gershgorin bound of D^-1 A;
 //   A_c       = P^T A P (deterministic sparse products), down to <= coarse_max rows, whose
 //             dense inverse is formed on the device.
-// Smoothing is Chebyshev on D^-1 A over [0.3, 1.1] * rho.  Every set-up sum has a fixed
+// Smoothing is Chebyshev on D^-1 A over [cheb_lower, 1] * 1.1 rho, rho a power-iteration estimate.  Every set-up sum has a fixed
 // order, so the hierarchy is bitwise reproducible.  V-cycles run in FP64 or FP32 on two
 // right-hand sides at once (the two species share M and H).
 #include <cmath>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "ch_internal.cuh"
@@ -28,6 +30,7 @@ template <> struct V2T<float> { using t = float2; };
 template <typename T>
 struct LevelT {
   Csr<T> A, P, R;
+  int tprA = 1, tprP = 1, tprR = 1;  // lanes per row of the SpMV-type kernels (autotuned)
   T* dinv = nullptr;
   typename V2T<T>::t *x = nullptr, *x2 = nullptr, *d = nullptr, *r = nullptr, *b = nullptr;
 };
@@ -44,6 +47,8 @@ struct Hierarchy {
   double* cinv = nullptr;             // nc x nc dense inverse (FP64)
   float* cinvf = nullptr;
   int cheb_degree = 2;
+  double cheb_lower = 0.3;
+  int autotune = 1;
   Alloc mem;
 };
 
@@ -284,6 +289,85 @@ __global__ void k_copy_cast(const double* a, T* b, int64_t n) {
   if (i < n) b[i] = (T)a[i];
 }
 
+// ---------------------------------------------------------------- spectral radius of D^-1 A
+// Power iteration with the D-weighted Rayleigh quotient lambda = (x, A x) / (x, D x), which for
+// symmetric A converges twice as fast as the norm ratio.  One launch computes y = D^-1 A x and
+// the block partials of (x, A x), (x, D x) and (y, D y); a one-block launch sums them in block
+// order and stores lambda and the D-norm scaling of y for the next iterate.
+constexpr int POW_BLOCKS = 152 * 2;
+
+__global__ void k_pow_init(int n, double* x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = 0.5 + (double)(hash32((uint32_t)i * 2654435761u + 12345u) >> 8) * 0x1.0p-24;
+}
+
+__global__ void k_pow_step(Csr<double> A, const double* __restrict__ dinv, const double* __restrict__ x,
+                           double* __restrict__ y, double* partials) {
+  __shared__ double sm[3][TPB];
+  double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nrows; i += gridDim.x * blockDim.x) {
+    double ax = 0.0;
+    for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) ax = fma(A.val[q], x[A.col[q]], ax);
+    const double di = dinv[i];
+    p0 = fma(x[i], ax, p0);
+    p1 = fma(x[i] * x[i], 1.0 / di, p1);
+    p2 = fma(ax * ax, di, p2);
+    y[i] = di * ax;
+  }
+  sm[0][threadIdx.x] = p0;
+  sm[1][threadIdx.x] = p1;
+  sm[2][threadIdx.x] = p2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int c = 0; c < 3; ++c) sm[c][threadIdx.x] += sm[c][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) partials[3 * blockIdx.x + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void k_pow_reduce(int nb, const double* partials, double* out /* lambda, scale */) {
+  if (threadIdx.x != 0) return;
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    t0 += partials[3 * b];
+    t1 += partials[3 * b + 1];
+    t2 += partials[3 * b + 2];
+  }
+  out[0] = t1 > 0.0 ? t0 / t1 : 0.0;
+  out[1] = t2 > 0.0 ? 1.0 / sqrt(t2) : 0.0;
+}
+
+__global__ void k_pow_scale(int n, const double* y, const double* out, double* x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = y[i] * out[1];
+}
+
+// lambda_max(D^-1 A) estimate (20 iterations); the caller caps it by the Gershgorin bound
+static ch_status power_estimate(const Csr<double>& A, const double* dinv, cudaStream_t st,
+                                double* lambda) {
+  const int n = A.nrows;
+  Alloc tmp;
+  double *x = nullptr, *y = nullptr, *part = nullptr, *out = nullptr;
+  CH_TRY(tmp.get(&x, (size_t)n));
+  CH_TRY(tmp.get(&y, (size_t)n));
+  CH_TRY(tmp.get(&part, (size_t)3 * POW_BLOCKS));
+  CH_TRY(tmp.get(&out, 2));
+  const int nb = blocks_for(n) < POW_BLOCKS ? blocks_for(n) : POW_BLOCKS;
+  k_pow_init<<<blocks_for(n), TPB, 0, st>>>(n, x);
+  for (int it = 0; it < 20; ++it) {
+    k_pow_step<<<nb, TPB, 0, st>>>(A, dinv, x, y, part);
+    k_pow_reduce<<<1, 32, 0, st>>>(nb, part, out);
+    k_pow_scale<<<blocks_for(n), TPB, 0, st>>>(n, y, out, x);
+  }
+  CH_LAUNCHED();
+  double h_out[2] = {0.0, 0.0};
+  CH_CUDA(cudaMemcpyAsync(h_out, out, sizeof(h_out), cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  *lambda = h_out[0];
+  return CH_OK;
+}
+
 // ---------------------------------------------------------------- set-up driver
 static ch_status level_setup(Hierarchy* h, int l, const ch_params& p, cudaStream_t st,
                              bool* last) {
@@ -306,6 +390,12 @@ static ch_status level_setup(Hierarchy* h, int l, const ch_params& p, cudaStream
     set_error("AMG level %d: bad Gershgorin bound %g (zero or non-finite diagonal?)", l, rho);
     return CH_ERR_NONFINITE;
   }
+  // Gershgorin overestimates lambda_max(D^-1 A) on coarse aggregation levels (by 30-150% on the
+  // meshes here), which would misplace the Chebyshev interval: use a power-iteration estimate
+  // with a 5% margin, never above the Gershgorin bound.
+  double lam = 0.0;
+  CH_TRY(power_estimate(A, dinv, st, &lam));
+  if (lam > 0.0 && std::isfinite(lam)) rho = std::min(rho, 1.05 * lam);
   h->rho.push_back(rho);
   if (n <= p.coarse_max) {
     *last = true;
@@ -403,6 +493,94 @@ static ch_status level_setup(Hierarchy* h, int l, const ch_params& p, cudaStream
   return CH_OK;
 }
 
+template <typename T, typename V2>
+static void launch_residual(int tpr, const Csr<T>& A, const V2* b, const V2* x, V2* r, cudaStream_t st);
+template <typename T, typename V2, bool ACC>
+static void launch_spmv2(int tpr, const Csr<T>& A, const V2* x, V2* y, cudaStream_t st);
+
+// ---------------------------------------------------------------- SpMV tile autotuner
+// Lanes per row (1..32) for each matrix the V-cycle multiplies by: A (smoother steps and
+// residuals), R (restriction), P (prolongation).  autotune = 0 takes the rule below; 1 times
+// every candidate on the matrix itself (one warm-up, three timed launches) and keeps the rule's
+// choice unless another is more than 5% faster.  Decisions are cached per process by matrix
+// shape (kind, rows, columns, entries, value size), so rebuilding a hierarchy of the same shape
+// reproduces its choices -- and its floating-point summation order -- exactly.
+static int tpr_rule(int64_t nnz, int rows) {
+  const double avg = rows > 0 ? (double)nnz / rows : 1.0;
+  int t = 1;
+  while (t < 32 && 4.0 * t <= avg) t *= 2;
+  return t;
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int64_t, int>, int> g_tune_cache;
+
+template <typename Launch>
+static int tune_tpr(int kind, int rows, int cols, int64_t nnz, int tsize, int mode, Launch&& launch,
+                    cudaStream_t st) {
+  const int rule = tpr_rule(nnz, rows);
+  if (mode == 0 || rows == 0) return rule;
+  const auto key = std::make_tuple(kind, rows, cols, nnz, tsize);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) return it->second;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return rule;
+  }
+  float best = 1e30f, t_rule = 1e30f;
+  int pick = rule;
+  for (int tpr = 1; tpr <= 32; tpr *= 2) {
+    launch(tpr);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) launch(tpr);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 1e30f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (tpr == rule) t_rule = ms;
+    if (ms < best) {
+      best = ms;
+      pick = tpr;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  if (t_rule <= 1.05f * best) pick = rule;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = pick;
+  return pick;
+}
+
+template <typename T>
+static ch_status autotune_levels(Hierarchy* h, std::vector<LevelT<T>>& L, int mode, cudaStream_t st) {
+  using V2 = typename V2T<T>::t;
+  for (int l = 0; l < h->nlev; ++l) {
+    const int n = L[l].A.nrows;
+    V2* vecs[5] = {L[l].x, L[l].x2, L[l].d, L[l].r, L[l].b};
+    for (int k = 0; k < 5; ++k) CH_CUDA(cudaMemsetAsync(vecs[k], 0, sizeof(V2) * n, st));
+  }
+  for (int l = 0; l < h->nlev; ++l) {
+    LevelT<T>& W = L[l];
+    W.tprA = tune_tpr(0, W.A.nrows, W.A.ncols, W.A.nnz, sizeof(T), mode,
+                      [&](int t) { launch_residual<T, V2>(t, W.A, W.b, W.x, W.r, st); }, st);
+    if (l + 1 < h->nlev) {
+      LevelT<T>& C = L[l + 1];
+      W.tprR = tune_tpr(1, W.R.nrows, W.R.ncols, W.R.nnz, sizeof(T), mode,
+                        [&](int t) { launch_spmv2<T, V2, false>(t, W.R, W.r, C.b, st); }, st);
+      W.tprP = tune_tpr(2, W.P.nrows, W.P.ncols, W.P.nnz, sizeof(T), mode,
+                        [&](int t) { launch_spmv2<T, V2, true>(t, W.P, C.x, W.x, st); }, st);
+    }
+  }
+  CH_LAUNCHED();
+  CH_CUDA(cudaStreamSynchronize(st));
+  return CH_OK;
+}
+
 template <typename T>
 static ch_status make_working(Hierarchy* h, std::vector<LevelT<T>>& L, cudaStream_t st) {
   using V2 = typename V2T<T>::t;
@@ -443,7 +621,7 @@ static ch_status make_working(Hierarchy* h, std::vector<LevelT<T>>& L, cudaStrea
     CH_TRY(h->mem.get(&w.r, (size_t)n));
     CH_TRY(h->mem.get(&w.b, (size_t)n));
   }
-  return CH_OK;
+  return autotune_levels<T>(h, L, h->autotune, st);
 }
 
 ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precision, cudaStream_t st,
@@ -452,6 +630,8 @@ ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precisi
   Hierarchy* h = new Hierarchy();
   h->precision = precision;
   h->cheb_degree = p.cheb_degree;
+  h->autotune = p.autotune;
+  h->cheb_lower = p.cheb_lower;
   h->A.push_back(A0);
   ch_status s = CH_OK;
   for (int l = 0;; ++l) {
@@ -521,6 +701,15 @@ ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precisi
 
 void hierarchy_free(Hierarchy* h) { delete h; }
 int hierarchy_levels(const Hierarchy* h) { return h ? h->nlev : 0; }
+void hierarchy_level_tiles(const Hierarchy* h, int l, int* tA, int* tR, int* tP) {
+  const int a = h->precision == 0 ? h->Ld[l].tprA : h->Lf[l].tprA;
+  const int r = h->precision == 0 ? h->Ld[l].tprR : h->Lf[l].tprR;
+  const int q = h->precision == 0 ? h->Ld[l].tprP : h->Lf[l].tprP;
+  if (tA) *tA = a;
+  if (tR) *tR = l + 1 < h->nlev ? r : 0;
+  if (tP) *tP = l + 1 < h->nlev ? q : 0;
+}
+
 void hierarchy_level_size(const Hierarchy* h, int l, int64_t* rows, int64_t* nnz) {
   if (rows) *rows = h->A[l].nrows;
   if (nnz) *nnz = h->A[l].nnz;
@@ -547,19 +736,42 @@ __global__ void k_cheb_first(int n, const T* dinv, const V2* b, T invtheta, V2* 
   d[i] = v;
 }
 
-// r = b - A x;  d = alpha d + beta D^-1 r;  xo = x + d
-template <typename T, typename V2>
-__global__ void k_cheb_step(Csr<T> A, const T* dinv, const V2* b, const V2* x, V2* d, V2* xo,
-                            T alpha, T beta) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.nrows) return;
-  T s0 = 0, s1 = 0;
-  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
-    const T a = A.val[q];
-    const V2 xj = x[A.col[q]];
-    s0 = fma(a, xj.x, s0);
-    s1 = fma(a, xj.y, s1);
+// Row sums of A x for both right-hand sides with TPR lanes per row: lane `sub` takes entries
+// sub, sub+TPR, ... of the row and a butterfly of shuffles adds the lanes' partial sums, so the
+// summation order is fixed for a given TPR.  Threads past the last row contribute zeros (no
+// early return before the shuffles).
+template <typename T, typename V2, int TPR>
+__device__ __forceinline__ void row_sum(const Csr<T>& A, int row, int sub, const V2* __restrict__ x,
+                                        T& s0, T& s1) {
+  s0 = 0;
+  s1 = 0;
+  if (row < A.nrows) {
+    const int e = A.rowptr[row + 1];
+    for (int q = A.rowptr[row] + sub; q < e; q += TPR) {
+      const T a = A.val[q];
+      const V2 xj = x[A.col[q]];
+      s0 = fma(a, xj.x, s0);
+      s1 = fma(a, xj.y, s1);
+    }
   }
+#pragma unroll
+  for (int o = TPR / 2; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+}
+
+// r = b - A x;  d = alpha d + beta D^-1 r;  xo = x + d
+template <typename T, typename V2, int TPR>
+__global__ void __launch_bounds__(TPB) k_cheb_step(Csr<T> A, const T* __restrict__ dinv,
+                                                   const V2* __restrict__ b, const V2* __restrict__ x,
+                                                   V2* __restrict__ d, V2* __restrict__ xo, T alpha,
+                                                   T beta) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / TPR, sub = t % TPR;
+  T s0, s1;
+  row_sum<T, V2, TPR>(A, i, sub, x, s0, s1);
+  if (i >= A.nrows || sub != 0) return;
   const V2 bi = b[i], xi = x[i];
   const T di = dinv[i] * beta;
   V2 dd;
@@ -573,39 +785,59 @@ __global__ void k_cheb_step(Csr<T> A, const T* dinv, const V2* b, const V2* x, V
   xo[i] = mk2<T, V2>(xi.x + dd.x, xi.y + dd.y);
 }
 
-template <typename T, typename V2>
-__global__ void k_residual(Csr<T> A, const V2* b, const V2* x, V2* r) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.nrows) return;
-  T s0 = 0, s1 = 0;
-  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
-    const T a = A.val[q];
-    const V2 xj = x[A.col[q]];
-    s0 = fma(a, xj.x, s0);
-    s1 = fma(a, xj.y, s1);
-  }
+template <typename T, typename V2, int TPR>
+__global__ void __launch_bounds__(TPB) k_residual(Csr<T> A, const V2* __restrict__ b,
+                                                  const V2* __restrict__ x, V2* __restrict__ r) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / TPR, sub = t % TPR;
+  T s0, s1;
+  row_sum<T, V2, TPR>(A, i, sub, x, s0, s1);
+  if (i >= A.nrows || sub != 0) return;
   const V2 bi = b[i];
   r[i] = mk2<T, V2>(bi.x - s0, bi.y - s1);
 }
 
 // y = A x (ACC = false) or y += A x (ACC = true)
-template <typename T, typename V2, bool ACC>
-__global__ void k_spmv2(Csr<T> A, const V2* x, V2* y) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.nrows) return;
-  T s0 = 0, s1 = 0;
-  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
-    const T a = A.val[q];
-    const V2 xj = x[A.col[q]];
-    s0 = fma(a, xj.x, s0);
-    s1 = fma(a, xj.y, s1);
-  }
+template <typename T, typename V2, int TPR, bool ACC>
+__global__ void __launch_bounds__(TPB) k_spmv2(Csr<T> A, const V2* __restrict__ x, V2* __restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / TPR, sub = t % TPR;
+  T s0, s1;
+  row_sum<T, V2, TPR>(A, i, sub, x, s0, s1);
+  if (i >= A.nrows || sub != 0) return;
   if (ACC) {
     const V2 yi = y[i];
     y[i] = mk2<T, V2>(yi.x + s0, yi.y + s1);
   } else {
     y[i] = mk2<T, V2>(s0, s1);
   }
+}
+
+#define CH_TPR_DISPATCH(tpr, KCALL)                      \
+  switch (tpr) {                                         \
+    case 1: { constexpr int TPRC = 1; KCALL; } break;    \
+    case 2: { constexpr int TPRC = 2; KCALL; } break;    \
+    case 4: { constexpr int TPRC = 4; KCALL; } break;    \
+    case 8: { constexpr int TPRC = 8; KCALL; } break;    \
+    case 16: { constexpr int TPRC = 16; KCALL; } break;  \
+    default: { constexpr int TPRC = 32; KCALL; } break;  \
+  }
+
+template <typename T, typename V2>
+static void launch_cheb_step(int tpr, const Csr<T>& A, const T* dinv, const V2* b, const V2* x, V2* d,
+                             V2* xo, T alpha, T beta, cudaStream_t st) {
+  const int g = blocks_for((int64_t)A.nrows * tpr);
+  CH_TPR_DISPATCH(tpr, (k_cheb_step<T, V2, TPRC><<<g, TPB, 0, st>>>(A, dinv, b, x, d, xo, alpha, beta)));
+}
+template <typename T, typename V2>
+static void launch_residual(int tpr, const Csr<T>& A, const V2* b, const V2* x, V2* r, cudaStream_t st) {
+  const int g = blocks_for((int64_t)A.nrows * tpr);
+  CH_TPR_DISPATCH(tpr, (k_residual<T, V2, TPRC><<<g, TPB, 0, st>>>(A, b, x, r)));
+}
+template <typename T, typename V2, bool ACC>
+static void launch_spmv2(int tpr, const Csr<T>& A, const V2* x, V2* y, cudaStream_t st) {
+  const int g = blocks_for((int64_t)A.nrows * tpr);
+  CH_TPR_DISPATCH(tpr, (k_spmv2<T, V2, TPRC, ACC><<<g, TPB, 0, st>>>(A, x, y)));
 }
 
 // x = Ainv b, dense nc x nc, one warp per row
@@ -650,9 +882,9 @@ struct ChebCoef {
   double alpha[16], beta[16];
 };
 
-static ChebCoef cheb_coef(double rho, int deg) {
+static ChebCoef cheb_coef(double rho, int deg, double lower) {
   ChebCoef c{};
-  const double hi = 1.1 * rho, lo = 0.3 * hi;
+  const double hi = 1.1 * rho, lo = lower * hi;
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
   c.invtheta = 1.0 / theta;
   c.alpha[0] = 0.0;
@@ -672,7 +904,7 @@ static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, bool zero_guess,
                         typename V2T<T_>::t** xcur, cudaStream_t st) {
   using V2 = typename V2T<T_>::t;
   const int n = L.A.nrows;
-  const ChebCoef c = cheb_coef(h->rho[l], h->cheb_degree);
+  const ChebCoef c = cheb_coef(h->rho[l], h->cheb_degree, h->cheb_lower);
   V2* x = *xcur;
   V2* other = (x == L.x) ? L.x2 : L.x;
   int s0 = 0;
@@ -686,8 +918,7 @@ static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, bool zero_guess,
     ProfScope ps(st, K_CHEB_STEP, sizeof(T_) == 4,
                  nnz * (4 + T) + 4.0 * (n + 1) + T * n * (c.alpha[s] != 0.0 ? 11 : 9),
                  2.0 * nnz + 4.0 * n);
-    k_cheb_step<T_, V2><<<blocks_for(n), TPB, 0, st>>>(L.A, L.dinv, L.b, x, L.d, other,
-                                                      (T_)c.alpha[s], (T_)c.beta[s]);
+    launch_cheb_step<T_, V2>(L.tprA, L.A, L.dinv, L.b, x, L.d, other, (T_)c.alpha[s], (T_)c.beta[s], st);
     std::swap(x, other);
   }
   CH_LAUNCHED();
@@ -717,12 +948,12 @@ static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv,
   {
     ProfScope ps(st, K_VRESIDUAL, sizeof(T) == 4, L.A.nnz * (4 + Tb) + 4.0 * (n + 1) + 6.0 * Tb * n,
                  2.0 * L.A.nnz);
-    k_residual<T, V2><<<blocks_for(n), TPB, 0, st>>>(L.A, L.b, x, L.r);
+    launch_residual<T, V2>(L.tprA, L.A, L.b, x, L.r, st);
   }
   {
     ProfScope ps(st, K_RESTRICT, sizeof(T) == 4,
                  L.R.nnz * (4 + Tb) + 4.0 * (nc + 1) + 2.0 * Tb * (n + nc), 2.0 * L.R.nnz);
-    k_spmv2<T, V2, false><<<blocks_for(nc), TPB, 0, st>>>(L.R, L.r, C.b);
+    launch_spmv2<T, V2, false>(L.tprR, L.R, L.r, C.b, st);
   }
   CH_LAUNCHED();
   V2* xc = C.x;
@@ -730,7 +961,7 @@ static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv,
   {
     ProfScope ps(st, K_PROLONG, sizeof(T) == 4,
                  L.P.nnz * (4 + Tb) + 4.0 * (n + 1) + 2.0 * Tb * nc + 4.0 * Tb * n, 2.0 * L.P.nnz);
-    k_spmv2<T, V2, true><<<blocks_for(n), TPB, 0, st>>>(L.P, xc, x);
+    launch_spmv2<T, V2, true>(L.tprP, L.P, xc, x, st);
   }
   CH_LAUNCHED();
   CH_TRY(smooth<T>(h, L, l, false, &x, st));
@@ -766,7 +997,7 @@ static ch_status apply_fine_t(std::vector<LevelT<T>>& Ls, const double* x, int l
   LevelT<T>& L = Ls[0];
   const int n = L.A.nrows;
   k_load2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, x, ldx, L.r);
-  k_spmv2<T, V2, false><<<blocks_for(n), TPB, 0, st>>>(L.A, L.r, L.d);
+  launch_spmv2<T, V2, false>(L.tprA, L.A, L.r, L.d, st);
   k_store2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.d, y, ldy);
   CH_LAUNCHED();
   return CH_OK;
@@ -817,7 +1048,7 @@ static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::ve
       const double Tb = sizeof(T), nnz = (double)LM[0].A.nnz;
       ProfScope ps(st, K_SPMV_M, sizeof(T) == 4, nnz * (4 + Tb) + 4.0 * (n + 1) + 4.0 * Tb * n,
                    2.0 * nnz);
-      k_spmv2<T, V2, false><<<blocks_for(n), TPB, 0, st>>>(LM[0].A, xr, L.b);
+      launch_spmv2<T, V2, false>(LM[0].tprA, LM[0].A, xr, L.b, st);
     }
     CH_LAUNCHED();
     xr = L.x;  // the first solve's result now lives in L.b as M x; start afresh
@@ -891,7 +1122,7 @@ static ch_status vcycle_static(Hierarchy* h, LevelT<T>* Ls, const T* cinv, int l
     *xres = L.x;
     return CH_OK;
   }
-  const ChebCoef c = cheb_coef(h->rho[l], h->cheb_degree);
+  const ChebCoef c = cheb_coef(h->rho[l], h->cheb_degree, h->cheb_lower);
   V2* x = *xres;
   auto smooth_static = [&](bool zg) {
     V2* other = (x == L.x) ? L.x2 : L.x;
@@ -901,19 +1132,18 @@ static ch_status vcycle_static(Hierarchy* h, LevelT<T>* Ls, const T* cinv, int l
       s0 = 1;
     }
     for (int s = s0; s < h->cheb_degree; ++s) {
-      k_cheb_step<T, V2><<<blocks_for(n), TPB, 0, st>>>(L.A, L.dinv, L.b, x, L.d, other,
-                                                        (T)c.alpha[s], (T)c.beta[s]);
+      launch_cheb_step<T, V2>(L.tprA, L.A, L.dinv, L.b, x, L.d, other, (T)c.alpha[s], (T)c.beta[s], st);
       std::swap(x, other);
     }
   };
   smooth_static(zero_guess);
   LevelT<T>& C = Ls[l + 1];
-  k_residual<T, V2><<<blocks_for(n), TPB, 0, st>>>(L.A, L.b, x, L.r);
-  k_spmv2<T, V2, false><<<blocks_for(C.A.nrows), TPB, 0, st>>>(L.R, L.r, C.b);
+  launch_residual<T, V2>(L.tprA, L.A, L.b, x, L.r, st);
+  launch_spmv2<T, V2, false>(L.tprR, L.R, L.r, C.b, st);
   CH_LAUNCHED();
   V2* xc = C.x;
   CH_TRY(vcycle_static<T>(h, Ls, cinv, l + 1, true, &xc, st));
-  k_spmv2<T, V2, true><<<blocks_for(n), TPB, 0, st>>>(L.P, xc, x);
+  launch_spmv2<T, V2, true>(L.tprP, L.P, xc, x, st);
   smooth_static(false);
   CH_LAUNCHED();
   *xres = x;

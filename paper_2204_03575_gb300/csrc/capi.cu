@@ -31,6 +31,8 @@ ch_status check_params(const ch_params* p) {
   CH_ARG(p->coarse_max >= 1 && p->coarse_max <= 4096, "coarse_max must be in [1, 4096]");
   CH_ARG(p->amg_theta >= 0 && p->amg_theta < 1, "amg_theta must be in [0, 1)");
   CH_ARG(p->vcycles_M >= 1 && p->vcycles_H >= 1, "vcycles must be >= 1");
+  CH_ARG(p->autotune == 0 || p->autotune == 1, "autotune must be 0 or 1");
+  CH_ARG(p->cheb_lower > 0 && p->cheb_lower < 1, "cheb_lower must be in (0, 1)");
   return CH_OK;
 }
 }  // namespace
@@ -79,11 +81,13 @@ void ch_params_default(ch_params* p) {
   d.rtol = 1e-8;
   d.restart = 30;
   d.max_iter = 300;
-  d.cheb_degree = 2;
+  d.cheb_degree = 3;
   d.coarse_max = 256;
   d.amg_theta = 0.08;
   d.vcycles_M = 1;
-  d.vcycles_H = 1;
+  d.vcycles_H = 2;
+  d.autotune = 1;
+  d.cheb_lower = 0.3;
   *p = d;
 }
 
@@ -237,6 +241,20 @@ ch_status ch_precond_info(const ch_precond_t* pc, int32_t which, int32_t level, 
     CH_ARG(level >= 0 && level < nl, "level out of range");
     ch::hierarchy_level_size(h, level, rows, nnz);
   }
+  return CH_OK;
+}
+
+ch_status ch_precond_tiles(const ch_precond_t* pc, int32_t which, int32_t level, int32_t* tpr_A,
+                           int32_t* tpr_R, int32_t* tpr_P) {
+  CH_ARG(pc != nullptr, "preconditioner is NULL");
+  CH_ARG(which == 0 || which == 1, "which must be 0 (M) or 1 (H)");
+  const ch::Hierarchy* h = which == 0 ? pc->hM : pc->hH;
+  CH_ARG(level >= 0 && level < ch::hierarchy_levels(h), "level out of range");
+  int a = 0, r = 0, q = 0;
+  ch::hierarchy_level_tiles(h, level, &a, &r, &q);
+  if (tpr_A) *tpr_A = a;
+  if (tpr_R) *tpr_R = r;
+  if (tpr_P) *tpr_P = q;
   return CH_OK;
 }
 

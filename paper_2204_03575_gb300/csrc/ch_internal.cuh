@@ -175,6 +175,7 @@ ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precisi
 void hierarchy_free(Hierarchy* h);
 int hierarchy_levels(const Hierarchy* h);
 void hierarchy_level_size(const Hierarchy* h, int l, int64_t* rows, int64_t* nnz);
+void hierarchy_level_tiles(const Hierarchy* h, int l, int* tA, int* tR, int* tP);
 // x (N x 2, fp64, row stride ldx) ~ A^-1 b (N x 2, fp64, row stride ldb), ncyc V-cycles
 ch_status hierarchy_solve(Hierarchy* h, const double* b, int ldb, double* x, int ldx, int ncyc,
                           cudaStream_t st);

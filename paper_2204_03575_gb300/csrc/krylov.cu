@@ -160,13 +160,47 @@ __global__ void k_scale4(int N, const double4_32a* src, double4_32a* dst, const 
 // MODE 0: h1[s][k] = <V_k, W>_s                       k = 0..nv-1
 // MODE 1: W -= sum_k h1[s][k] V_k;  h2[s][k] = <V_k, W>_s
 // MODE 2: W -= sum_k h2[s][k] V_k;  ||W||_s^2, then the Hessenberg / Givens update (last block)
-constexpr int KC = 8;  // basis vectors per register chunk
+// <a, b>_s sums components (x, z) for system 0 and (y, w) for system 1.
+constexpr int KC = 16;                 // basis vectors per chunk: 2 KC = 32 values, one per lane
+constexpr int ORTH_BLOCKS = 152 * 2;   // fixed grid (2 blocks per SM): fixed reduction order
+
+// Sum 32 per-lane values over the warp by recursive halving: at each step a lane keeps half of
+// its values and adds the partner's copy of that half.  On return lane l holds the warp sum of
+// value l (31 shuffles instead of 32 x 5).
+__device__ __forceinline__ double warp_transpose_sum32(double (&a)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int step = 0; step < 5; ++step) {
+    const int o = 16 >> step, h = 16 >> step;  // partner offset, values kept
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const double send = up ? a[k] : a[k + h];
+      const double keep = up ? a[k + h] : a[k];
+      a[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return a[0];
+}
+
+// Block sum of the 32 per-thread values: returns, in threads 0..31, the block total of value t.
+__device__ __forceinline__ double block_sum32(double (&a)[32], double* sm /* [TPB/32][32] */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double r = warp_transpose_sum32(a);
+  sm[w * 32 + lane] = r;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32)
+    for (int q = 0; q < TPB / 32; ++q) t += sm[q * 32 + threadIdx.x];
+  __syncthreads();
+  return t;
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(TPB) k_orth(int N, int nv, const double4_32a* __restrict__ V,
                                                double4_32a* __restrict__ W, double* partials,
                                                KrylovDev* kd) {
-  __shared__ double sm[(TPB / 32) * 2 * KC];
+  __shared__ double sm[(TPB / 32) * 32];
   __shared__ double coef[2][MAXM + 1];
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
@@ -177,23 +211,34 @@ __global__ void __launch_bounds__(TPB) k_orth(int N, int nv, const double4_32a* 
     }
     __syncthreads();
     for (int v = tid; v < N; v += stride) {
-      double4_32a w = W[v];
-      for (int k = 0; k < nv; ++k) {
-        const double4_32a q = V[(size_t)k * N + v];
-        const double c0 = coef[0][k], c1 = coef[1][k];
-        w.x = fma(-c0, q.x, w.x);
-        w.z = fma(-c0, q.z, w.z);
-        w.y = fma(-c1, q.y, w.y);
-        w.w = fma(-c1, q.w, w.w);
+      // two partial sums (even / odd k) halve the FP64 dependency chains
+      double ax = 0, ay = 0, az = 0, aw = 0, bx = 0, by = 0, bz = 0, bw = 0;
+      int k = 0;
+      for (; k + 1 < nv; k += 2) {
+        const double4_32a q0 = V[(size_t)k * N + v];
+        const double4_32a q1 = V[(size_t)(k + 1) * N + v];
+        const double c00 = coef[0][k], c10 = coef[1][k], c01 = coef[0][k + 1], c11 = coef[1][k + 1];
+        ax = fma(c00, q0.x, ax); az = fma(c00, q0.z, az); ay = fma(c10, q0.y, ay); aw = fma(c10, q0.w, aw);
+        bx = fma(c01, q1.x, bx); bz = fma(c01, q1.z, bz); by = fma(c11, q1.y, by); bw = fma(c11, q1.w, bw);
       }
+      if (k < nv) {
+        const double4_32a q0 = V[(size_t)k * N + v];
+        ax = fma(coef[0][k], q0.x, ax); az = fma(coef[0][k], q0.z, az);
+        ay = fma(coef[1][k], q0.y, ay); aw = fma(coef[1][k], q0.w, aw);
+      }
+      double4_32a w = W[v];
+      w.x -= ax + bx;
+      w.y -= ay + by;
+      w.z -= az + bz;
+      w.w -= aw + bw;
       W[v] = w;
     }
   }
   if (MODE <= 1) {
     for (int k0 = 0; k0 < nv; k0 += KC) {
-      double acc[2 * KC];
+      double acc[32];
 #pragma unroll
-      for (int t = 0; t < 2 * KC; ++t) acc[t] = 0.0;
+      for (int t = 0; t < 32; ++t) acc[t] = 0.0;
       for (int v = tid; v < N; v += stride) {
         const double4_32a w = W[v];
 #pragma unroll
@@ -205,12 +250,9 @@ __global__ void __launch_bounds__(TPB) k_orth(int N, int nv, const double4_32a* 
           }
         }
       }
-      block_sum<2 * KC>(acc, sm);
-      for (int t = threadIdx.x; t < 2 * KC; t += blockDim.x) {
-        const int k = k0 + t / 2;
-        if (k < nv) partials[(size_t)blockIdx.x * MAXV + 2 * k + (t & 1)] = sm[t];
-      }
-      __syncthreads();
+      const double tot = block_sum32(acc, sm);
+      const int nval = 2 * (nv - k0 < KC ? nv - k0 : KC);
+      if (threadIdx.x < nval) partials[(size_t)blockIdx.x * MAXV + 2 * k0 + threadIdx.x] = tot;
     }
     if (!last_block(&kd->ticket)) return;
     __shared__ double tot[MAXV];
@@ -223,14 +265,16 @@ __global__ void __launch_bounds__(TPB) k_orth(int N, int nv, const double4_32a* 
     }
     if (threadIdx.x == 0) kd->ticket = 0;
   } else {
-    double acc[2] = {0.0, 0.0};
+    double acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0.0;
     for (int v = tid; v < N; v += stride) {
       const double4_32a w = W[v];
       acc[0] = fma(w.x, w.x, fma(w.z, w.z, acc[0]));
       acc[1] = fma(w.y, w.y, fma(w.w, w.w, acc[1]));
     }
-    block_sum<2>(acc, sm);
-    if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = sm[threadIdx.x];
+    const double bt = block_sum32(acc, sm);
+    if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = bt;
     if (!last_block(&kd->ticket)) return;
     __shared__ double tot[2];
     reduce_partials(partials, 2, tot);
@@ -447,6 +491,7 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
   const ch_params& p = s->p;
   const int N = S->N, m = S->m;
   const int rb = red_blocks(N);
+  const int orb = blocks_for(N) < ORTH_BLOCKS ? blocks_for(N) : ORTH_BLOCKS;
   const double4_32a* b4 = reinterpret_cast<const double4_32a*>(S->b);
   double4_32a* x4 = reinterpret_cast<double4_32a*>(S->x);
   double4_32a* W4 = reinterpret_cast<double4_32a*>(S->W);
@@ -486,15 +531,15 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
       const double nv = j + 1, n32 = 32.0 * N;
       {
         ProfScope ps(st, K_ORTH0, 0, (nv + 1) * n32, 4.0 * nv * N);
-        k_orth<0><<<rb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+        k_orth<0><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
       }
       {
         ProfScope ps(st, K_ORTH1, 0, (nv + 2) * n32, 8.0 * nv * N);
-        k_orth<1><<<rb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+        k_orth<1><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
       }
       {
         ProfScope ps(st, K_ORTH2, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
-        k_orth<2><<<rb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+        k_orth<2><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
       }
       {
         ProfScope ps(st, K_SCALE4, 0, 64.0 * N, 0.0);

@@ -210,8 +210,10 @@ def test_trajectory_parity_2d_config1(lib):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_step_parity_3d_subsize(lib, precision):
-    """16x16x4 Kuhn mesh on [0,1]^2 x [0,0.25], 0.30 +/- 0.01: 3 steps."""
-    _, out = run_pair(lib, 3, base=(0.30, 0.30), dim=3, nx=16, ny=16, nz=4, Lz=0.25, rtol=1e-12,
+    """16x16x4 Kuhn mesh on [0,1]^2 x [0,0.25], 0.30 +/- 0.01: 3 steps.  The 3D saddle system is
+    worse conditioned than config 1 (mu errors reach ~1.2e-10 at rtol 1e-12), so parity mode
+    solves to 1e-13."""
+    _, out = run_pair(lib, 3, base=(0.30, 0.30), dim=3, nx=16, ny=16, nz=4, Lz=0.25, rtol=1e-13,
                       precision=precision)
     for k, (stats, g, _, nxt) in enumerate(out):
         for gk, ok in FIELDS:
