@@ -910,12 +910,12 @@ static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, bool zero_guess,
   int s0 = 0;
   const double T = sizeof(T_), nnz = (double)L.A.nnz;
   if (zero_guess) {
-    ProfScope ps(st, K_CHEB_FIRST, sizeof(T_) == 4, 7.0 * T * n, 2.0 * n);
+    ProfScope ps(st, l == 0 ? K_CHEB_FIRST : K_CHEB_FIRST_C, sizeof(T_) == 4, 7.0 * T * n, 2.0 * n);
     k_cheb_first<T_, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.dinv, L.b, (T_)c.invtheta, x, L.d);
     s0 = 1;
   }
   for (int s = s0; s < h->cheb_degree; ++s) {
-    ProfScope ps(st, K_CHEB_STEP, sizeof(T_) == 4,
+    ProfScope ps(st, l == 0 ? K_CHEB_STEP : K_CHEB_STEP_C, sizeof(T_) == 4,
                  nnz * (4 + T) + 4.0 * (n + 1) + T * n * (c.alpha[s] != 0.0 ? 11 : 9),
                  2.0 * nnz + 4.0 * n);
     launch_cheb_step<T_, V2>(L.tprA, L.A, L.dinv, L.b, x, L.d, other, (T_)c.alpha[s], (T_)c.beta[s], st);
@@ -946,12 +946,12 @@ static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv,
   LevelT<T>& C = Ls[l + 1];
   const int nc = C.A.nrows;
   {
-    ProfScope ps(st, K_VRESIDUAL, sizeof(T) == 4, L.A.nnz * (4 + Tb) + 4.0 * (n + 1) + 6.0 * Tb * n,
+    ProfScope ps(st, l == 0 ? K_VRESIDUAL : K_VRESIDUAL_C, sizeof(T) == 4, L.A.nnz * (4 + Tb) + 4.0 * (n + 1) + 6.0 * Tb * n,
                  2.0 * L.A.nnz);
     launch_residual<T, V2>(L.tprA, L.A, L.b, x, L.r, st);
   }
   {
-    ProfScope ps(st, K_RESTRICT, sizeof(T) == 4,
+    ProfScope ps(st, l == 0 ? K_RESTRICT : K_RESTRICT_C, sizeof(T) == 4,
                  L.R.nnz * (4 + Tb) + 4.0 * (nc + 1) + 2.0 * Tb * (n + nc), 2.0 * L.R.nnz);
     launch_spmv2<T, V2, false>(L.tprR, L.R, L.r, C.b, st);
   }
@@ -959,7 +959,7 @@ static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv,
   V2* xc = C.x;
   CH_TRY(vcycle<T>(h, Ls, cinv, l + 1, true, &xc, st));
   {
-    ProfScope ps(st, K_PROLONG, sizeof(T) == 4,
+    ProfScope ps(st, l == 0 ? K_PROLONG : K_PROLONG_C, sizeof(T) == 4,
                  L.P.nnz * (4 + Tb) + 4.0 * (n + 1) + 2.0 * Tb * nc + 4.0 * Tb * n, 2.0 * L.P.nnz);
     launch_spmv2<T, V2, true>(L.tprP, L.P, xc, x, st);
   }

@@ -33,6 +33,7 @@ ch_status check_params(const ch_params* p) {
   CH_ARG(p->vcycles_M >= 1 && p->vcycles_H >= 1, "vcycles must be >= 1");
   CH_ARG(p->autotune == 0 || p->autotune == 1, "autotune must be 0 or 1");
   CH_ARG(p->cheb_lower > 0 && p->cheb_lower < 1, "cheb_lower must be in (0, 1)");
+  CH_ARG(p->graphs == 0 || p->graphs == 1, "graphs must be 0 or 1");
   return CH_OK;
 }
 }  // namespace
@@ -88,6 +89,7 @@ void ch_params_default(ch_params* p) {
   d.vcycles_H = 2;
   d.autotune = 1;
   d.cheb_lower = 0.3;
+  d.graphs = 1;
   *p = d;
 }
 

@@ -115,7 +115,9 @@ ch_status transpose(const Csr<double>& A, Csr<double>* B, cudaStream_t st, Alloc
 enum KernelId {
   K_RHS, K_LOADS, K_APPLY_A, K_RESIDUAL4, K_ORTH0, K_ORTH1, K_ORTH2, K_SCALE4, K_UPDATE_X,
   K_CYCLE_SOLVE, K_FLAGS, K_MASS, K_CHEB_FIRST, K_CHEB_STEP, K_VRESIDUAL, K_RESTRICT, K_PROLONG,
-  K_COARSE, K_VLOAD, K_VSTORE, K_SPMV_M, K_STATE_IO, K_COUNT
+  K_COARSE, K_VLOAD, K_VSTORE, K_SPMV_M, K_STATE_IO,
+  // the same V-cycle kernels on levels below the finest (accounted separately)
+  K_CHEB_FIRST_C, K_CHEB_STEP_C, K_VRESIDUAL_C, K_RESTRICT_C, K_PROLONG_C, K_COUNT
 };
 // RAII around one kernel launch: counts it with its algorithmic bytes / FMAs and, when timing
 // is on, records CUDA events around it on the launching stream.
@@ -133,6 +135,16 @@ class ProfScope {
   cudaEvent_t e0_ = nullptr, e1_ = nullptr;
 };
 void prof_drain();
+bool prof_timing();
+// launch accounting of kernels recorded into a CUDA graph, replayed at each graph launch
+struct ProfTally {
+  int64_t launches[K_COUNT * 2] = {};
+  double bytes[K_COUNT * 2] = {};
+  double fmas[K_COUNT * 2] = {};
+};
+void prof_capture_begin();
+ProfTally prof_capture_end();
+void prof_add(const ProfTally& t);
 
 }  // namespace ch
 

@@ -410,9 +410,16 @@ struct ch_state_s {
   ch::Flags* dflags = nullptr;
   ch::Flags* hflags = nullptr;  // pinned
   bool set = false;
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;            // private stream for graph capture
+  cudaGraphExec_t graph[64] = {};               // Arnoldi step j, captured on first use
+  ch::ProfTally tally[64];                      // launch accounting of each graph
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   ch::Alloc mem;
   ~ch_state_s() {
+    for (auto& g : graph)
+      if (g) cudaGraphExecDestroy(g);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     if (hflags) cudaFreeHost(hflags);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -447,6 +454,11 @@ ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, 
     set_error("pinned allocation failed");
     S->hflags = nullptr;
     r = CH_ERR_OOM;
+  }
+  S->use_graphs = s->p.graphs != 0;
+  if (r == CH_OK && cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("stream creation failed");
+    r = CH_ERR_CUDA;
   }
   if (r == CH_OK && (cudaEventCreate(&S->ev0) != cudaSuccess || cudaEventCreate(&S->ev1) != cudaSuccess)) {
     set_error("event creation failed");
@@ -485,13 +497,84 @@ static ch_status read_flags(ch_state_s* S, cudaStream_t st) {
 
 static double res4_bytes(const ch_system_s* s) { return 20.0 * s->nnz + 4.0 * (s->N + 1) + 96.0 * s->N; }
 
+// One Arnoldi step j for both systems: Z_j = Prec(V_j) (Algorithm 1), W = A Z_j, CGS2 against
+// V_0..V_j with the Givens update, V_{j+1} = W / h_{j+1,j}, and the convergence flags copied to
+// dflags.  Everything is enqueued on `st` with no host synchronisation, so it can be captured.
+static ch_status arnoldi_step(ch_state_s* S, int j, cudaStream_t st) {
+  const ch_system_s* s = S->sys;
+  const int N = S->N;
+  const int orb = blocks_for(N) < ORTH_BLOCKS ? blocks_for(N) : ORTH_BLOCKS;
+  double4_32a* W4 = reinterpret_cast<double4_32a*>(S->W);
+  double4_32a* V4 = reinterpret_cast<double4_32a*>(S->V);
+  double4_32a* Z4 = reinterpret_cast<double4_32a*>(S->Z);
+  double4_32a* Vj = V4 + (size_t)j * N;
+  double4_32a* Zj = Z4 + (size_t)j * N;
+  CH_TRY(precond_apply(S->pc, reinterpret_cast<double*>(Vj), reinterpret_cast<double*>(Zj), st));
+  CH_TRY(apply_A(s, reinterpret_cast<double*>(Zj), S->W, st));
+  const double nv = j + 1, n32 = 32.0 * N;
+  {
+    ProfScope ps(st, K_ORTH0, 0, (nv + 1) * n32, 4.0 * nv * N);
+    k_orth<0><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+  }
+  {
+    ProfScope ps(st, K_ORTH1, 0, (nv + 2) * n32, 8.0 * nv * N);
+    k_orth<1><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+  }
+  {
+    ProfScope ps(st, K_ORTH2, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
+    k_orth<2><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+  }
+  {
+    ProfScope ps(st, K_SCALE4, 0, 64.0 * N, 0.0);
+    k_scale4<<<blocks_for(N), TPB, 0, st>>>(N, W4, V4 + (size_t)(j + 1) * N, S->kd);
+  }
+  CH_LAUNCHED();
+  {
+    ProfScope ps(st, K_FLAGS, 0, 0.0, 0.0);
+    k_flags<<<1, 32, 0, st>>>(S->kd, S->dflags);
+  }
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+// Launch Arnoldi step j: replay its captured CUDA graph (captured on first use on the state's
+// private stream, since the legacy default stream cannot be captured), or enqueue the kernels
+// directly when graphs are off or per-launch event timing is on.  Then read the flags.
+static ch_status arnoldi_launch(ch_state_s* S, int j, cudaStream_t st) {
+  if (!S->use_graphs || prof_timing()) {
+    CH_TRY(arnoldi_step(S, j, st));
+  } else {
+    if (!S->graph[j]) {
+      cudaGraph_t g = nullptr;
+      CH_CUDA(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
+      prof_capture_begin();
+      const ch_status r = arnoldi_step(S, j, S->cap_stream);
+      const cudaError_t e = cudaStreamEndCapture(S->cap_stream, &g);
+      S->tally[j] = prof_capture_end();
+      if (r != CH_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      CH_CUDA(e);
+      const cudaError_t ei = cudaGraphInstantiate(&S->graph[j], g, 0);
+      cudaGraphDestroy(g);
+      CH_CUDA(ei);
+    }
+    CH_CUDA(cudaGraphLaunch(S->graph[j], st));
+    prof_add(S->tally[j]);
+  }
+  CH_CUDA(cudaMemcpyAsync(S->hflags, S->dflags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  prof_drain();
+  return CH_OK;
+}
+
 // Solve A x = b for both systems; x holds the initial guess on entry.
 static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
   const ch_system_s* s = S->sys;
   const ch_params& p = s->p;
   const int N = S->N, m = S->m;
   const int rb = red_blocks(N);
-  const int orb = blocks_for(N) < ORTH_BLOCKS ? blocks_for(N) : ORTH_BLOCKS;
   const double4_32a* b4 = reinterpret_cast<const double4_32a*>(S->b);
   double4_32a* x4 = reinterpret_cast<double4_32a*>(S->x);
   double4_32a* W4 = reinterpret_cast<double4_32a*>(S->W);
@@ -524,30 +607,8 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
     CH_LAUNCHED();
     int j = 0;
     for (; j < m; ++j) {
-      double4_32a* Vj = V4 + (size_t)j * N;
-      double4_32a* Zj = Z4 + (size_t)j * N;
-      CH_TRY(precond_apply(S->pc, reinterpret_cast<double*>(Vj), reinterpret_cast<double*>(Zj), st));
-      CH_TRY(apply_A(s, reinterpret_cast<double*>(Zj), S->W, st));
-      const double nv = j + 1, n32 = 32.0 * N;
-      {
-        ProfScope ps(st, K_ORTH0, 0, (nv + 1) * n32, 4.0 * nv * N);
-        k_orth<0><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
-      }
-      {
-        ProfScope ps(st, K_ORTH1, 0, (nv + 2) * n32, 8.0 * nv * N);
-        k_orth<1><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
-      }
-      {
-        ProfScope ps(st, K_ORTH2, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
-        k_orth<2><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
-      }
-      {
-        ProfScope ps(st, K_SCALE4, 0, 64.0 * N, 0.0);
-        k_scale4<<<blocks_for(N), TPB, 0, st>>>(N, W4, V4 + (size_t)(j + 1) * N, S->kd);
-      }
-      CH_LAUNCHED();
       ++total;
-      CH_TRY(read_flags(S, st));
+      CH_TRY(arnoldi_launch(S, j, st));
       if (S->hflags->nonfinite) {
         set_error("non-finite value in the Arnoldi process");
         return CH_ERR_NONFINITE;

@@ -16,7 +16,8 @@ static const char* const kNames[K_COUNT] = {
     "rhs",          "loads",         "apply_A",     "residual4",  "orth_dots",  "orth_update_dots",
     "orth_update_norm", "scale4",    "update_x",    "cycle_solve", "flags",     "mass",
     "cheb_first",   "cheb_step",     "vresidual",   "restrict",    "prolong",   "coarse_solve",
-    "vload",        "vstore",        "spmv_M",      "state_io"};
+    "vload",        "vstore",        "spmv_M",      "state_io",    "cheb_first_coarse",
+    "cheb_step_coarse", "vresidual_coarse", "restrict_coarse", "prolong_coarse"};
 
 struct Acc {
   int64_t launches = 0;
@@ -28,6 +29,8 @@ struct Pending {
   int slot;
   double bytes, fmas;
 };
+
+static thread_local ProfTally* t_capture = nullptr;  // set while a graph is being captured
 
 static struct {
   std::mutex mu;
@@ -65,6 +68,12 @@ static void drain_locked(bool wait) {
 
 ProfScope::ProfScope(cudaStream_t st, int kid, int f32, double bytes, double fmas)
     : st_(st), slot_(kid * 2 + (f32 ? 1 : 0)), bytes_(bytes), fmas_(fmas) {
+  if (t_capture) {  // counted each time the captured graph is launched
+    t_capture->launches[slot_] += 1;
+    t_capture->bytes[slot_] += bytes;
+    t_capture->fmas[slot_] += fmas;
+    return;
+  }
   std::lock_guard<std::mutex> lk(g.mu);
   Acc& a = g.acc[slot_];
   a.launches += 1;
@@ -83,6 +92,33 @@ ProfScope::~ProfScope() {
   cudaEventRecord(e1_, st_);
   g.pending.push_back({e0_, e1_, slot_, bytes_, fmas_});
   if (g.pending.size() > 2048) drain_locked(true);
+}
+
+bool prof_timing() {
+  std::lock_guard<std::mutex> lk(g.mu);
+  return g.timing;
+}
+
+void prof_capture_begin() {
+  static thread_local ProfTally tally;
+  tally = ProfTally();
+  t_capture = &tally;
+}
+
+ProfTally prof_capture_end() {
+  ProfTally out = t_capture ? *t_capture : ProfTally();
+  t_capture = nullptr;
+  return out;
+}
+
+void prof_add(const ProfTally& t) {
+  std::lock_guard<std::mutex> lk(g.mu);
+  for (int s = 0; s < K_COUNT * 2; ++s) {
+    if (!t.launches[s]) continue;
+    g.acc[s].launches += t.launches[s];
+    g.acc[s].bytes += t.bytes[s];
+    g.acc[s].fmas += t.fmas[s];
+  }
 }
 
 void prof_drain() {

@@ -1,0 +1,45 @@
+"""A bounded solver run for profilers: one mesh, one state, a few time steps.
+
+    python -m paper_2204_03575_gb300.profile_case --nx 1024 --ny 1024 --steps 1 --restart 10
+
+Builds the mesh, system, preconditioner and state on cuda:0 (seeded initial state, paper
+parameters), runs the warm-up and timed steps and prints per-step statistics.  Used as the
+target of ncu captures, where the full benchmark would hold too much device memory.
+"""
+import argparse
+import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=1024)
+    ap.add_argument("--nz", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--restart", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    a = ap.parse_args()
+    import torch
+    from paper_2204_03575_gb300 import ch
+    torch.cuda.set_device(0)
+    kw = dict(nx=a.nx, ny=a.ny, precision=a.precision, restart=a.restart)
+    if a.nz:
+        kw.update(dim=3, nz=a.nz, Lz=a.nz / a.nx)
+    p = ch.Params(**kw)
+    system = ch.System(ch.Mesh(p), p)
+    pc = ch.Precond(system)
+    state = ch.State(system, pc)
+    state.init_seeded(0.33, 0.33, 0.01, seed=0)
+    for _ in range(a.warmup):
+        state.step()
+    for k in range(a.steps):
+        print(json.dumps({"step": k, **state.step()}), flush=True)
+
+
+if __name__ == "__main__":
+    main()
