@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -335,6 +336,30 @@ def main():
                  "roofline": roofline(profm, peaks, sustained=True), "top_kernels": top_kernels(profm)}
         del sysM, pcM, stateM
 
+    # ---- batched workload: 64 independent runs of uneven size in one state (FP32 V-cycles)
+    batch = None
+    if not args.no_batch:
+        from paper_2204_03575_gb300 import inputs
+        spec = inputs.batch_runs(64, seed=0)
+        pb = ch.Params(precision=1)
+        bmesh = ch.Mesh(pb, runs=[ch.Params(nx=nx, ny=ny) for nx, ny, _, _ in spec])
+        bsys = ch.System(bmesh, pb)
+        bstate = ch.State(bsys, ch.Precond(bsys))
+        bstate.init_seeded_batch([x[2] for x in spec], [x[3] for x in spec], 0.01, seed=0)
+        for _ in range(W):
+            bstate.step()
+        KB = min(K, 20)
+        ch.profile_read(reset=True)
+        ms_b, iters_b = timed_steps(torch, ch, bstate, KB, flush, barrier)
+        blaunch = sum(v["launches"] for v in ch.profile_read(reset=True).values())
+        worst = max(max(bstate.run_stats(r)["relres"]) for r in range(len(spec)))
+        batch = {"workload": "64 runs, nx, ny drawn from {64,96,128,192,256}, bases U[0.20,0.45), "
+                             "noise +/-0.01, FP32 V-cycles in FP64 FGMRES, one state (disjoint union)",
+                 "runs": len(spec), "nodes": bsys.n, "steps": KB,
+                 "run_steps_per_s": world * len(spec) * KB / (ms_b * 1e-3), "ms_per_step": ms_b / KB,
+                 "launches_per_step": blaunch / KB, "max_relres_last_step": worst}
+        del bstate, bsys, bmesh
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, sample, _, _ = oracle_rate(args.nx, args.ny, 2)
@@ -352,7 +377,7 @@ def main():
         "top_kernels": top_kernels(prof64),
         "iters_per_step_mean": float(np.mean(iters)), "iters_per_step_max": int(np.max(iters)),
         "amg_levels": {k: [r for r, _ in v] for k, v in levels.items()},
-        "mixed": mixed, "cpu_baseline": cpu,
+        "mixed": mixed, "batch": batch, "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

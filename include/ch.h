@@ -107,6 +107,15 @@ void ch_params_default(ch_params* p);
  * (i+1,j+1)) or the 6 Kuhn tetrahedra per hexahedron.  Gamma_b = {y = 0} (substrate),
  * Gamma_t = {y = Ly} (evaporation).  Built on the device. */
 ch_status ch_mesh(const ch_params* p, void* stream, ch_mesh_t** out);
+/* Batched runs: the disjoint union of nruns box meshes (runs[r] gives run r's dim, nx, ny, nz,
+ * Lx, Ly, Lz; all runs share dim).  Run r owns the node range [off[r], off[r+1]) (ch_mesh_runs),
+ * its own boundaries Gamma_b, Gamma_t and its own initial state; the model parameters come from
+ * the params given to ch_assemble (whose cell counts are then ignored) and are the same for every run.  Every later call (assembly,
+ * AMG set-up, V-cycles, FGMRES steps) then advances all runs together, with the Krylov scalars
+ * and convergence tests kept per run and species. */
+ch_status ch_mesh_batch(int32_t nruns, const ch_params* runs, void* stream, ch_mesh_t** out);
+/* host outputs: number of runs and (if run_offsets != NULL) nruns+1 node offsets */
+ch_status ch_mesh_runs(const ch_mesh_t* m, int32_t* nruns, int32_t* run_offsets);
 /* host outputs, any may be NULL */
 ch_status ch_mesh_info(const ch_mesh_t* m, int64_t* n_nodes, int64_t* n_elems,
                        int64_t* n_bottom, int64_t* n_top);
@@ -187,9 +196,16 @@ ch_status ch_state_create(const ch_system_t* s, ch_precond_t* pc, void* stream, 
 ch_status ch_state_set(ch_state_t* st, const double* phi_p, const double* phi_nfa,
                        const double* mu_p, const double* mu_nfa, void* stream);
 /* Seeded initial state (Section 4): phi = base + noise (2u - 1), u from SplitMix64 on the counter
- * seed ^ (field << 40) ^ node, field 0 = polymer, 1 = NFA; mu = 0. */
+ * seed ^ (field << 40) ^ node, field 0 = polymer, 1 = NFA; mu = 0.  For a batch, every run uses
+ * these bases and run r the stream seed + r over its local node index. */
 ch_status ch_state_init_seeded(ch_state_t* st, double phi_p0, double phi_nfa0, double noise,
                                uint64_t seed, void* stream);
+/* Seeded initial state of a batch: run r gets bases phi_p0[r], phi_nfa0[r] (host arrays of nruns)
+ * and the generator stream seed + r over its local node index. */
+ch_status ch_state_init_seeded_batch(ch_state_t* st, const double* phi_p0, const double* phi_nfa0,
+                                     double noise, uint64_t seed, void* stream);
+/* Statistics of run `run` for the last ch_step (host output); ch_step itself reports run 0. */
+ch_status ch_state_run_stats(const ch_state_t* st, int32_t run, ch_step_stats* out);
 /* Copy fields to caller device buffers (N fp64 each); any may be NULL.  phi_s = 1 - phi_p - phi_nfa. */
 ch_status ch_state_get(const ch_state_t* st, double* phi_p, double* phi_nfa, double* phi_s,
                        double* mu_p, double* mu_nfa, void* stream);

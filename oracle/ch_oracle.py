@@ -316,12 +316,15 @@ class State:
 class Solver:
     """Mesh, matrices and a factorisation of A, reused across steps (A is constant)."""
 
-    def __init__(self, p: Params, m: Mesh | None = None):
+    def __init__(self, p: Params, m: Mesh | None = None, factor: bool = True):
         self.p = p
         self.m = m if m is not None else mesh(p)
         self.M, self.K = assemble(self.m)
         self.A = saddle_matrix(self.M, self.K, p)
         self.N = self.M.shape[0]
+        self._dense = self._lu = None
+        if not factor:          # residual checks only (relres, rhs_pair); step() unavailable
+            return
         if 2 * self.N <= DENSE_LIMIT:
             self._dense = self.A.toarray()
             self._lu = None
@@ -330,6 +333,8 @@ class Solver:
             self._lu = spla.splu(self.A.tocsc())
 
     def solve(self, B: np.ndarray) -> np.ndarray:
+        if self._dense is None and self._lu is None:
+            raise RuntimeError("Solver built with factor=False")
         if self._dense is not None:
             return np.linalg.solve(self._dense, B)     # LAPACK LU with partial pivoting
         return self._lu.solve(B)

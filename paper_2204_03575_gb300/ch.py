@@ -83,6 +83,8 @@ _SIGNATURES = {
     "ch_params_default": (None, [ctypes.POINTER(Params)]),
     "ch_mesh": (ctypes.c_int, [ctypes.POINTER(Params), _VP, ctypes.POINTER(_VP)]),
     "ch_mesh_info": (ctypes.c_int, [_VP, _I64P, _I64P, _I64P, _I64P]),
+    "ch_mesh_batch": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Params), _VP, ctypes.POINTER(_VP)]),
+    "ch_mesh_runs": (ctypes.c_int, [_VP, _I32P, _I32P]),
     "ch_mesh_copy": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "ch_mesh_destroy": (None, [_VP]),
     "ch_assemble": (ctypes.c_int, [_VP, ctypes.POINTER(Params), _VP, ctypes.POINTER(_VP)]),
@@ -104,6 +106,9 @@ _SIGNATURES = {
     "ch_state_init_seeded": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_uint64, _VP]),
     "ch_state_get": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ch_state_init_seeded_batch": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.c_double, ctypes.c_uint64, _VP]),
+    "ch_state_run_stats": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(StepStats)]),
     "ch_step": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(StepStats)]),
     "ch_run": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.POINTER(StepStats)]),
     "ch_state_destroy": (None, [_VP]),
@@ -160,10 +165,20 @@ def _f64(t, n=None, cols=None):
 
 
 class Mesh:
-    def __init__(self, params: Params, stream=None):
+    def __init__(self, params: Params, stream=None, runs=None):
+        """One box mesh from params, or (runs = list of Params) the disjoint union of run meshes."""
         self.params = params
         self._h = _VP()
-        _check(lib().ch_mesh(ctypes.byref(params), _stream(stream), ctypes.byref(self._h)), "ch_mesh")
+        if runs is None:
+            _check(lib().ch_mesh(ctypes.byref(params), _stream(stream), ctypes.byref(self._h)), "ch_mesh")
+        else:
+            arr = (Params * len(runs))(*runs)
+            _check(lib().ch_mesh_batch(len(runs), arr, _stream(stream), ctypes.byref(self._h)), "ch_mesh_batch")
+        nr = ctypes.c_int32()
+        _check(lib().ch_mesh_runs(self._h, ctypes.byref(nr), None), "ch_mesh_runs")
+        offs = (ctypes.c_int32 * (nr.value + 1))()
+        _check(lib().ch_mesh_runs(self._h, None, offs), "ch_mesh_runs")
+        self.nruns, self.run_offsets = nr.value, list(offs)
         n, e, fb, ft = (ctypes.c_int64() for _ in range(4))
         _check(lib().ch_mesh_info(self._h, ctypes.byref(n), ctypes.byref(e), ctypes.byref(fb),
                                   ctypes.byref(ft)), "ch_mesh_info")
@@ -299,6 +314,18 @@ class State:
     def init_seeded(self, phi_p0, phi_nfa0, noise=0.01, seed=0, stream=None):
         _check(lib().ch_state_init_seeded(self._h, phi_p0, phi_nfa0, noise, seed, _stream(stream)),
                "ch_state_init_seeded")
+
+    def init_seeded_batch(self, phi_p0, phi_nfa0, noise=0.01, seed=0, stream=None):
+        R = len(phi_p0)
+        bp = (ctypes.c_double * R)(*phi_p0)
+        bn = (ctypes.c_double * R)(*phi_nfa0)
+        _check(lib().ch_state_init_seeded_batch(self._h, bp, bn, noise, seed, _stream(stream)),
+               "ch_state_init_seeded_batch")
+
+    def run_stats(self, run: int):
+        st = StepStats()
+        _check(lib().ch_state_run_stats(self._h, run, ctypes.byref(st)), "ch_state_run_stats")
+        return st.as_dict()
 
     def get(self, stream=None):
         n = self.system.n

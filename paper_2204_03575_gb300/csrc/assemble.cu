@@ -8,31 +8,37 @@
 namespace ch {
 
 // ---------------------------------------------------------------- mesh (Section 4)
-__global__ void k_mesh_nodes(ch_params p, int N, double* coords) {
+__global__ void k_fill_int(int* a, int n, int v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+__global__ void k_mesh_nodes(ch_params p, int N, int node_off, double* coords) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int i = n % (p.nx + 1);
   const int j = (n / (p.nx + 1)) % (p.ny + 1);
+  const int g = node_off + n;
   if (p.dim == 2) {
-    coords[2 * n + 0] = i * (p.Lx / p.nx);
-    coords[2 * n + 1] = j * (p.Ly / p.ny);
+    coords[2 * g + 0] = i * (p.Lx / p.nx);
+    coords[2 * g + 1] = j * (p.Ly / p.ny);
   } else {
     const int k = n / ((p.nx + 1) * (p.ny + 1));
-    coords[3 * n + 0] = i * (p.Lx / p.nx);
-    coords[3 * n + 1] = j * (p.Ly / p.ny);
-    coords[3 * n + 2] = k * (p.Lz / p.nz);
+    coords[3 * g + 0] = i * (p.Lx / p.nx);
+    coords[3 * g + 1] = j * (p.Ly / p.ny);
+    coords[3 * g + 2] = k * (p.Lz / p.nz);
   }
 }
 
 // 2D: cell c = i + nx j -> triangles 2c = (v00, v10, v11), 2c+1 = (v00, v11, v01).
 // 3D: hexahedron c -> the 6 Kuhn tetrahedra v000 -> +e_a -> +e_a+e_b -> v111 over the
 // permutations (a,b,c) of the axes, in lexicographic order of the permutation.
-__global__ void k_mesh_elems(ch_params p, int E, int* el) {
+__global__ void k_mesh_elems(ch_params p, int E, int node_off, int* el) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   if (p.dim == 2) {
     const int c = e >> 1, i = c % p.nx, j = c / p.nx;
-    const int v00 = i + (p.nx + 1) * j, v10 = v00 + 1, v01 = v00 + p.nx + 1, v11 = v01 + 1;
+    const int v00 = node_off + i + (p.nx + 1) * j, v10 = v00 + 1, v01 = v00 + p.nx + 1, v11 = v01 + 1;
     if ((e & 1) == 0) {
       el[3 * e] = v00; el[3 * e + 1] = v10; el[3 * e + 2] = v11;
     } else {
@@ -43,7 +49,7 @@ __global__ void k_mesh_elems(ch_params p, int E, int* el) {
     const int i = c % p.nx, j = (c / p.nx) % p.ny, k = c / (p.nx * p.ny);
     const int s[3] = {1, p.nx + 1, (p.nx + 1) * (p.ny + 1)};
     const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-    const int v0 = i + s[1] * j + s[2] * k;
+    const int v0 = node_off + i + s[1] * j + s[2] * k;
     el[4 * e + 0] = v0;
     el[4 * e + 1] = v0 + s[perm[t][0]];
     el[4 * e + 2] = v0 + s[perm[t][0]] + s[perm[t][1]];
@@ -52,18 +58,18 @@ __global__ void k_mesh_elems(ch_params p, int E, int* el) {
 }
 
 // Boundary facets of the Kuhn / diagonal split on y = 0 (bottom) and y = Ly (top).
-__global__ void k_mesh_facets(ch_params p, int F, int* bot, int* top) {
+__global__ void k_mesh_facets(ch_params p, int F, int node_off, int* bot, int* top) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
   if (p.dim == 2) {
-    const int b = f, t = p.ny * (p.nx + 1) + f;
+    const int b = node_off + f, t = node_off + p.ny * (p.nx + 1) + f;
     bot[2 * f] = b; bot[2 * f + 1] = b + 1;
     top[2 * f] = t; top[2 * f + 1] = t + 1;
   } else {
     const int q = f >> 1, i = q % p.nx, k = q / p.nx;
     const int sx = 1, sz = (p.nx + 1) * (p.ny + 1);
-    const int b = i + sz * k;                   // (i, 0, k)
-    const int t = i + (p.nx + 1) * p.ny + sz * k;  // (i, ny, k)
+    const int b = node_off + i + sz * k;                      // (i, 0, k)
+    const int t = node_off + i + (p.nx + 1) * p.ny + sz * k;  // (i, ny, k)
     if ((f & 1) == 0) {
       bot[3 * f] = b; bot[3 * f + 1] = b + sx; bot[3 * f + 2] = b + sx + sz;
       top[3 * f] = t; top[3 * f + 1] = t + sx; top[3 * f + 2] = t + sx + sz;
@@ -146,19 +152,43 @@ __global__ void k_facet_vol(const double* X, const int* f, int F, double* vol) {
   }
 }
 
-ch_status mesh_build(ch_mesh_s* m, cudaStream_t st) {
-  const ch_params& p = m->p;
-  const int d = p.dim;
-  m->dim = d;
-  if (d == 2) {
-    m->N = (p.nx + 1) * (p.ny + 1);
-    m->E = 2 * p.nx * p.ny;
-    m->Fb = m->Ft = p.nx;
+// counts of one box mesh
+static void box_counts(const ch_params& p, int* N, int* E, int* F) {
+  if (p.dim == 2) {
+    *N = (p.nx + 1) * (p.ny + 1);
+    *E = 2 * p.nx * p.ny;
+    *F = p.nx;
   } else {
-    m->N = (p.nx + 1) * (p.ny + 1) * (p.nz + 1);
-    m->E = 6 * p.nx * p.ny * p.nz;
-    m->Fb = m->Ft = 2 * p.nx * p.nz;
+    *N = (p.nx + 1) * (p.ny + 1) * (p.nz + 1);
+    *E = 6 * p.nx * p.ny * p.nz;
+    *F = 2 * p.nx * p.nz;
   }
+}
+
+// The mesh of every run, laid out one after another: run r owns nodes [run_off[r], run_off[r+1]),
+// its elements and boundary facets follow those of run r-1 and reference only its own nodes, so
+// the union is a disjoint set of box meshes (one run: the plain mesh).
+ch_status mesh_build(ch_mesh_s* m, cudaStream_t st) {
+  const int R = (int)m->runs.size();
+  const int d = m->runs[0].dim;
+  m->dim = d;
+  m->p = m->runs[0];
+  m->run_off.assign(R + 1, 0);
+  std::vector<int> eoff(R + 1, 0), foff(R + 1, 0);
+  for (int r = 0; r < R; ++r) {
+    int n, e, f;
+    box_counts(m->runs[r], &n, &e, &f);
+    if ((int64_t)m->run_off[r] + n > 2000000000LL) {
+      set_error("batched mesh too large for int32 indexing");
+      return CH_ERR_ARG;
+    }
+    m->run_off[r + 1] = m->run_off[r] + n;
+    eoff[r + 1] = eoff[r] + e;
+    foff[r + 1] = foff[r] + f;
+  }
+  m->N = m->run_off[R];
+  m->E = eoff[R];
+  m->Fb = m->Ft = foff[R];
   CH_TRY(m->mem.get(&m->coords, (size_t)m->N * d));
   CH_TRY(m->mem.get(&m->elems, (size_t)m->E * (d + 1)));
   CH_TRY(m->mem.get(&m->bot, (size_t)m->Fb * d));
@@ -166,10 +196,19 @@ ch_status mesh_build(ch_mesh_s* m, cudaStream_t st) {
   CH_TRY(m->mem.get(&m->vol, (size_t)m->E));
   CH_TRY(m->mem.get(&m->bvol, (size_t)m->Fb));
   CH_TRY(m->mem.get(&m->tvol, (size_t)m->Ft));
-  k_mesh_nodes<<<blocks_for(m->N), TPB, 0, st>>>(p, m->N, m->coords);
-  k_mesh_elems<<<blocks_for(m->E), TPB, 0, st>>>(p, m->E, m->elems);
-  k_mesh_facets<<<blocks_for(m->Fb), TPB, 0, st>>>(p, m->Fb, m->bot, m->top);
+  CH_TRY(m->mem.get(&m->node_run, (size_t)m->N));
+  CH_TRY(m->mem.get(&m->run_off_d, (size_t)R + 1));
+  for (int r = 0; r < R; ++r) {
+    const ch_params& p = m->runs[r];
+    const int n = m->run_off[r + 1] - m->run_off[r], e = eoff[r + 1] - eoff[r], f = foff[r + 1] - foff[r];
+    k_mesh_nodes<<<blocks_for(n), TPB, 0, st>>>(p, n, m->run_off[r], m->coords);
+    k_mesh_elems<<<blocks_for(e), TPB, 0, st>>>(p, e, m->run_off[r], m->elems + (size_t)eoff[r] * (d + 1));
+    k_mesh_facets<<<blocks_for(f), TPB, 0, st>>>(p, f, m->run_off[r], m->bot + (size_t)foff[r] * d,
+                                                  m->top + (size_t)foff[r] * d);
+    k_fill_int<<<blocks_for(n), TPB, 0, st>>>(m->node_run + m->run_off[r], n, r);
+  }
   CH_LAUNCHED();
+  CH_CUDA(cudaMemcpyAsync(m->run_off_d, m->run_off.data(), sizeof(int) * (R + 1), cudaMemcpyHostToDevice, st));
   if (d == 2) {
     k_elem_vol<2><<<blocks_for(m->E), TPB, 0, st>>>(m->coords, m->elems, m->E, m->vol);
     k_facet_vol<2><<<blocks_for(m->Fb), TPB, 0, st>>>(m->coords, m->bot, m->Fb, m->bvol);

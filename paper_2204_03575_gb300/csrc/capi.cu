@@ -101,12 +101,43 @@ ch_status ch_mesh(const ch_params* p, void* stream, ch_mesh_t** out) {
   ch_mesh_s* m = new (std::nothrow) ch_mesh_s();
   if (!m) return CH_ERR_OOM;
   m->p = *p;
+  m->runs.assign(1, *p);
   ch_status r = ch::mesh_build(m, S(stream));
   if (r != CH_OK) {
     delete m;
     return r;
   }
   *out = m;
+  return CH_OK;
+}
+
+ch_status ch_mesh_batch(int32_t nruns, const ch_params* runs, void* stream, ch_mesh_t** out) {
+  CH_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  CH_ARG(nruns >= 1 && runs != nullptr, "need at least one run");
+  for (int r = 0; r < nruns; ++r) {
+    CH_TRY(check_params(&runs[r]));
+    CH_ARG(runs[r].dim == runs[0].dim, "all runs of a batch must have the same dim");
+  }
+  ch_mesh_s* m = new (std::nothrow) ch_mesh_s();
+  if (!m) return CH_ERR_OOM;
+  m->p = runs[0];
+  m->runs.assign(runs, runs + nruns);
+  m->batch = true;
+  ch_status r = ch::mesh_build(m, S(stream));
+  if (r != CH_OK) {
+    delete m;
+    return r;
+  }
+  *out = m;
+  return CH_OK;
+}
+
+ch_status ch_mesh_runs(const ch_mesh_t* m, int32_t* nruns, int32_t* run_offsets) {
+  CH_ARG(m != nullptr, "mesh is NULL");
+  if (nruns) *nruns = (int32_t)m->runs.size();
+  if (run_offsets)
+    for (size_t r = 0; r < m->run_off.size(); ++r) run_offsets[r] = m->run_off[r];
   return CH_OK;
 }
 
@@ -145,8 +176,8 @@ ch_status ch_assemble(const ch_mesh_t* m, const ch_params* p, void* stream, ch_s
   *out = nullptr;
   CH_ARG(m != nullptr, "mesh is NULL");
   CH_TRY(check_params(p));
-  CH_ARG(p->dim == m->p.dim && p->nx == m->p.nx && p->ny == m->p.ny &&
-             (p->dim == 2 || p->nz == m->p.nz),
+  CH_ARG(p->dim == m->p.dim, "params describe a mesh of another dimension");
+  CH_ARG(m->batch || (p->nx == m->p.nx && p->ny == m->p.ny && (p->dim == 2 || p->nz == m->p.nz)),
          "params describe a different mesh");
   ch_system_s* s = new (std::nothrow) ch_system_s();
   if (!s) return CH_ERR_OOM;
@@ -311,6 +342,17 @@ ch_status ch_state_init_seeded(ch_state_t* st, double phi_p0, double phi_nfa0, d
                                uint64_t seed, void* stream) {
   CH_ARG(st != nullptr, "state is NULL");
   return ch::state_seeded(st, phi_p0, phi_nfa0, noise, seed, S(stream));
+}
+
+ch_status ch_state_init_seeded_batch(ch_state_t* st, const double* phi_p0, const double* phi_nfa0,
+                                     double noise, uint64_t seed, void* stream) {
+  CH_ARG(st != nullptr && phi_p0 != nullptr && phi_nfa0 != nullptr, "NULL argument");
+  return ch::state_seeded_batch(st, phi_p0, phi_nfa0, noise, seed, S(stream));
+}
+
+ch_status ch_state_run_stats(const ch_state_t* st, int32_t run, ch_step_stats* out) {
+  CH_ARG(st != nullptr && out != nullptr, "NULL argument");
+  return ch::state_run_stats(st, run, out);
 }
 
 ch_status ch_state_get(const ch_state_t* st, double* phi_p, double* phi_nfa, double* phi_s,

@@ -150,7 +150,12 @@ void prof_add(const ProfTally& t);
 
 // ---------------------------------------------------------------- opaque handles
 struct ch_mesh_s {
-  ch_params p{};
+  ch_params p{};                 // parameters of run 0 (the only run of a plain mesh)
+  std::vector<ch_params> runs;   // per-run parameters (box, cells)
+  bool batch = false;            // built by ch_mesh_batch
+  std::vector<int> run_off;      // host: first node of each run, run_off[R] = N
+  int* run_off_d = nullptr;      // device copy
+  int* node_run = nullptr;       // run of each node
   int dim = 2, N = 0, E = 0, Fb = 0, Ft = 0;
   double* coords = nullptr;   // N x dim
   int* elems = nullptr;       // E x (dim+1)
@@ -234,5 +239,9 @@ ch_status state_seeded(ch_state_s* S, double p0, double n0, double noise, uint64
                        cudaStream_t st);
 ch_status state_get(const ch_state_s* S, double* pp, double* pn, double* ps, double* mp, double* mn,
                     cudaStream_t st);
+ch_status state_seeded_batch(ch_state_s* S, const double* base_p, const double* base_n, double noise,
+                             uint64_t seed, cudaStream_t st);
+ch_status state_run_stats(const ch_state_s* S, int run, ch_step_stats* out);
+int state_runs(const ch_state_s* S);
 ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats);
 }

@@ -1,15 +1,21 @@
-// Flexible GMRES(m) in FP64 for the two saddle-point systems of one time step (Eq. (14)),
+// Flexible GMRES(m) in FP64 for the saddle-point systems of one time step (Eq. (14)),
 // right-preconditioned by Algorithm 1, plus the time-step driver.
 //
 // The paper solves each system with preconditioned MINRES (Section 4).  MINRES needs a
 // fixed symmetric positive definite preconditioner; one AMG V-cycle with Chebyshev
 // smoothing (and its FP32 variant) is neither exactly fixed nor symmetric, so the outer
 // method here is flexible GMRES (Saad 1993), which allows the preconditioner to vary.
-// Both species advance in lockstep: every kernel processes the N x 4 node-major vectors
-// (phi_p, phi_n, mu_p, mu_n) of both systems, while Hessenberg matrices, Givens rotations
-// and convergence flags are kept per system.  Orthogonalisation is classical Gram-Schmidt
-// with one re-orthogonalisation (CGS2), its inner products reduced in a fixed order by the
-// last thread block to finish (no floating-point atomics: runs are bitwise reproducible).
+//
+// A state holds R independent runs (R = 1 for a plain mesh; a batched mesh is the disjoint
+// union of R run meshes) and two species per run, i.e. 2R independent systems.  Every kernel
+// processes the N x 4 node-major vectors (phi_p, phi_n, mu_p, mu_n) of all systems at once;
+// the Krylov scalars -- Hessenberg matrix, Givens rotations, convergence flags -- are kept per
+// (run, species).  Inner products and norms are segmented: the grid is split so that each
+// thread block owns a contiguous node range of exactly one run, and the last block of a run to
+// finish (a per-run ticket) sums that run's block partials in block order.  There are no
+// floating-point atomics, so runs are bitwise reproducible.  Orthogonalisation is classical
+// Gram-Schmidt with one re-orthogonalisation (CGS2).
+#include <algorithm>
 #include <cmath>
 
 #include "ch_internal.cuh"
@@ -17,8 +23,9 @@
 namespace ch {
 
 constexpr int MAXM = 64;
-constexpr int MAXV = 2 * (MAXM + 1);  // reduced values per kernel (2 systems x (j+1))
+constexpr int MAXV = 2 * (MAXM + 1);  // reduced values per block (2 species x (j+1))
 
+// Krylov scalars of one run (two species)
 struct KrylovDev {
   double R[2][MAXM][MAXM];  // upper-triangular factor after Givens (column j in R[s][.][j])
   double cs[2][MAXM], sn[2][MAXM], g[2][MAXM + 1], y[2][MAXM];
@@ -29,15 +36,23 @@ struct KrylovDev {
   int k[2];             // Arnoldi steps taken in the current cycle
   int its[2];           // Arnoldi steps taken this step
   int nonfinite;
-  unsigned int ticket;  // last-block counter
+  unsigned int ticket;  // last-block counter of this run
 };
 
-struct Flags {
-  int cycle_active[2];
-  int active[2];
+struct Flags {  // summary over all runs
+  int cycle_active;  // systems still iterating in the cycle
+  int active;        // systems not yet converged
   int nonfinite;
   int pad;
-  double relres[2];
+};
+
+// Block decomposition: block b works on nodes [lo[b], hi[b]) of run run[b]; the blocks of run r
+// are first[r] .. first[r+1]-1.
+struct Seg {
+  const int* run;
+  const int* lo;
+  const int* hi;
+  const int* first;
 };
 
 // ---------------------------------------------------------------- block reductions
@@ -60,40 +75,41 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* [TPB/32
   __syncthreads();
 }
 
-// After a block has written its nv partials, returns true in the last block to finish, which
-// then reads every block's partials in block order.
-__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+// After a block has written its partials, returns true in the last block of its run to finish,
+// which then reads the run's block partials in block order.
+__device__ __forceinline__ bool last_block_of_run(unsigned int* ticket, int nblocks) {
   __shared__ bool am_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int t = atomicAdd(ticket, 1u);
-    am_last = (t == gridDim.x - 1);
+    am_last = (t == (unsigned)nblocks - 1u);
   }
   __syncthreads();
   if (am_last) __threadfence();
   return am_last;
 }
 
-__device__ void reduce_partials(const double* partials, int nv, double* out) {
+__device__ void reduce_partials(const double* partials, int b0, int b1, int nv, double* out) {
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += partials[(size_t)b * MAXV + v];
+    for (int b = b0; b < b1; ++b) s += partials[(size_t)b * MAXV + v];
     out[v] = s;
   }
   __syncthreads();
 }
 
 // ---------------------------------------------------------------- residual / norms
-// W = b - A x (both systems), then the last block computes ||b_s||, ||r_s||, relres and sets
-// active / cycle flags, beta and g for a (re)start.  If init, also tol_s = rtol ||b_s||.
-__global__ void k_residual4(int N, const int* rowptr, const int* col, const double* valM,
+// W = b - A x (all systems), then per run the last block computes ||b_s||, ||r_s||, relres and
+// sets active / cycle flags, beta and g for a (re)start.  If init, also tol_s = rtol ||b_s||.
+__global__ void k_residual4(Seg sg, const int* rowptr, const int* col, const double* valM,
                             const double* valK, double a, double c, const double4_32a* x,
-                            const double4_32a* b, double4_32a* W, double* partials, KrylovDev* kd,
+                            const double4_32a* b, double4_32a* W, double* partials, KrylovDev* kds,
                             int init, double rtol) {
   __shared__ double sm[(TPB / 32) * 4];
+  const int run = sg.run[blockIdx.x];
   double acc[4] = {0, 0, 0, 0};  // ||b_p||^2, ||b_n||^2, ||r_p||^2, ||r_n||^2
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+  for (int v = sg.lo[blockIdx.x] + threadIdx.x; v < sg.hi[blockIdx.x]; v += blockDim.x) {
     double m1p = 0, m1n = 0, m2p = 0, m2n = 0, k1p = 0, k1n = 0, k2p = 0, k2n = 0;
     for (int q = rowptr[v]; q < rowptr[v + 1]; ++q) {
       const int j = col[q];
@@ -122,9 +138,11 @@ __global__ void k_residual4(int N, const int* rowptr, const int* col, const doub
   }
   block_sum<4>(acc, sm);
   if (threadIdx.x < 4) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = sm[threadIdx.x];
-  if (!last_block(&kd->ticket)) return;
+  KrylovDev* kd = kds + run;
+  const int b0 = sg.first[run], b1 = sg.first[run + 1];
+  if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
   __shared__ double tot[4];
-  reduce_partials(partials, 4, tot);
+  reduce_partials(partials, b0, b1, 4, tot);
   if (threadIdx.x < 2) {
     const int s = threadIdx.x;
     const double bn = sqrt(tot[s]), rn = sqrt(tot[2 + s]);
@@ -133,7 +151,9 @@ __global__ void k_residual4(int N, const int* rowptr, const int* col, const doub
       kd->tol[s] = rtol * bn;
       kd->its[s] = 0;
       kd->active[s] = 1;
+      if (s == 0) kd->nonfinite = 0;
     }
+    __syncwarp(0x3u);
     if (!isfinite(bn) || !isfinite(rn)) kd->nonfinite = 1;
     kd->relres[s] = bn > 0.0 ? rn / bn : 0.0;
     const int act = kd->active[s] && rn > kd->tol[s] && bn > 0.0;
@@ -147,22 +167,23 @@ __global__ void k_residual4(int N, const int* rowptr, const int* col, const doub
   if (threadIdx.x == 0) kd->ticket = 0;
 }
 
-// dst = src * hinv[s] per system (components x,z -> system 0, y,w -> system 1)
-__global__ void k_scale4(int N, const double4_32a* src, double4_32a* dst, const KrylovDev* kd) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= N) return;
+// dst = src * hinv[s] per system of the block's run (components x,z: polymer; y,w: NFA)
+__global__ void k_scale4(Seg sg, const double4_32a* src, double4_32a* dst, const KrylovDev* kds) {
+  const KrylovDev* kd = kds + sg.run[blockIdx.x];
   const double s0 = kd->hinv[0], s1 = kd->hinv[1];
-  const double4_32a a = src[v];
-  dst[v] = make_double4_32a(a.x * s0, a.y * s1, a.z * s0, a.w * s1);
+  for (int v = sg.lo[blockIdx.x] + threadIdx.x; v < sg.hi[blockIdx.x]; v += blockDim.x) {
+    const double4_32a a = src[v];
+    dst[v] = make_double4_32a(a.x * s0, a.y * s1, a.z * s0, a.w * s1);
+  }
 }
 
 // ---------------------------------------------------------------- CGS2 passes
 // MODE 0: h1[s][k] = <V_k, W>_s                       k = 0..nv-1
 // MODE 1: W -= sum_k h1[s][k] V_k;  h2[s][k] = <V_k, W>_s
 // MODE 2: W -= sum_k h2[s][k] V_k;  ||W||_s^2, then the Hessenberg / Givens update (last block)
-// <a, b>_s sums components (x, z) for system 0 and (y, w) for system 1.
-constexpr int KC = 16;                 // basis vectors per chunk: 2 KC = 32 values, one per lane
-constexpr int ORTH_BLOCKS = 152 * 2;   // fixed grid (2 blocks per SM): fixed reduction order
+// <a, b>_s sums components (x, z) for species 0 and (y, w) for species 1 over the run's nodes.
+constexpr int KC = 16;                // basis vectors per chunk: 2 KC = 32 values, one per lane
+constexpr int ORTH_BLOCKS = 152 * 2;  // target grid of the segmented kernels (2 blocks per SM)
 
 // Sum 32 per-lane values over the warp by recursive halving: at each step a lane keeps half of
 // its values and adds the partner's copy of that half.  On return lane l holds the warp sum of
@@ -197,20 +218,21 @@ __device__ __forceinline__ double block_sum32(double (&a)[32], double* sm /* [TP
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(TPB) k_orth(int N, int nv, const double4_32a* __restrict__ V,
+__global__ void __launch_bounds__(TPB) k_orth(Seg sg, int N, int nv, const double4_32a* __restrict__ V,
                                                double4_32a* __restrict__ W, double* partials,
-                                               KrylovDev* kd) {
+                                               KrylovDev* kds) {
   __shared__ double sm[(TPB / 32) * 32];
   __shared__ double coef[2][MAXM + 1];
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int stride = gridDim.x * blockDim.x;
+  const int run = sg.run[blockIdx.x];
+  KrylovDev* kd = kds + run;
+  const int v0 = sg.lo[blockIdx.x] + threadIdx.x, v1 = sg.hi[blockIdx.x];
   if (MODE >= 1) {
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
       coef[0][k] = MODE == 1 ? kd->h1[0][k] : kd->h2[0][k];
       coef[1][k] = MODE == 1 ? kd->h1[1][k] : kd->h2[1][k];
     }
     __syncthreads();
-    for (int v = tid; v < N; v += stride) {
+    for (int v = v0; v < v1; v += blockDim.x) {
       // two partial sums (even / odd k) halve the FP64 dependency chains
       double ax = 0, ay = 0, az = 0, aw = 0, bx = 0, by = 0, bz = 0, bw = 0;
       int k = 0;
@@ -234,12 +256,13 @@ __global__ void __launch_bounds__(TPB) k_orth(int N, int nv, const double4_32a* 
       W[v] = w;
     }
   }
+  const int b0 = sg.first[run], b1 = sg.first[run + 1];
   if (MODE <= 1) {
     for (int k0 = 0; k0 < nv; k0 += KC) {
       double acc[32];
 #pragma unroll
       for (int t = 0; t < 32; ++t) acc[t] = 0.0;
-      for (int v = tid; v < N; v += stride) {
+      for (int v = v0; v < v1; v += blockDim.x) {
         const double4_32a w = W[v];
 #pragma unroll
         for (int t = 0; t < KC; ++t) {
@@ -254,9 +277,9 @@ __global__ void __launch_bounds__(TPB) k_orth(int N, int nv, const double4_32a* 
       const int nval = 2 * (nv - k0 < KC ? nv - k0 : KC);
       if (threadIdx.x < nval) partials[(size_t)blockIdx.x * MAXV + 2 * k0 + threadIdx.x] = tot;
     }
-    if (!last_block(&kd->ticket)) return;
+    if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
     __shared__ double tot[MAXV];
-    reduce_partials(partials, 2 * nv, tot);
+    reduce_partials(partials, b0, b1, 2 * nv, tot);
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
       double* dst0 = MODE == 0 ? kd->h1[0] : kd->h2[0];
       double* dst1 = MODE == 0 ? kd->h1[1] : kd->h2[1];
@@ -268,16 +291,16 @@ __global__ void __launch_bounds__(TPB) k_orth(int N, int nv, const double4_32a* 
     double acc[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) acc[t] = 0.0;
-    for (int v = tid; v < N; v += stride) {
+    for (int v = v0; v < v1; v += blockDim.x) {
       const double4_32a w = W[v];
       acc[0] = fma(w.x, w.x, fma(w.z, w.z, acc[0]));
       acc[1] = fma(w.y, w.y, fma(w.w, w.w, acc[1]));
     }
     const double bt = block_sum32(acc, sm);
     if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = bt;
-    if (!last_block(&kd->ticket)) return;
+    if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
     __shared__ double tot[2];
-    reduce_partials(partials, 2, tot);
+    reduce_partials(partials, b0, b1, 2, tot);
     if (threadIdx.x < 2) {
       const int s = threadIdx.x;
       const int j = nv - 1;  // Arnoldi column
@@ -318,68 +341,81 @@ __global__ void __launch_bounds__(TPB) k_orth(int N, int nv, const double4_32a* 
   }
 }
 
-// y_s = R_s^-1 g_s (back substitution, k_s x k_s)
-__global__ void k_cycle_solve(KrylovDev* kd) {
-  const int s = threadIdx.x;
-  if (s >= 2) return;
+// y_s = R_s^-1 g_s (back substitution, k_s x k_s), one thread per (run, species)
+__global__ void k_cycle_solve(int nruns, KrylovDev* kds) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * nruns) return;
+  KrylovDev* kd = kds + t / 2;
+  const int s = t % 2;
   const int k = kd->k[s];
   for (int i = k - 1; i >= 0; --i) {
-    double t = kd->g[s][i];
-    for (int q = i + 1; q < k; ++q) t -= kd->R[s][i][q] * kd->y[s][q];
-    kd->y[s][i] = kd->R[s][i][i] != 0.0 ? t / kd->R[s][i][i] : 0.0;
+    double v = kd->g[s][i];
+    for (int q = i + 1; q < k; ++q) v -= kd->R[s][i][q] * kd->y[s][q];
+    kd->y[s][i] = kd->R[s][i][i] != 0.0 ? v / kd->R[s][i][i] : 0.0;
   }
   for (int i = k; i < MAXM; ++i) kd->y[s][i] = 0.0;
 }
 
-// x += sum_k y_s[k] Z_k
-__global__ void k_update_x(int N, int kmax, const double4_32a* __restrict__ Z, double4_32a* x,
-                           const KrylovDev* kd) {
+// x += sum_k y_s[k] Z_k with the coefficients of the block's run
+__global__ void k_update_x(Seg sg, int N, int kmax, const double4_32a* __restrict__ Z, double4_32a* x,
+                           const KrylovDev* kds) {
   __shared__ double y[2][MAXM];
+  const KrylovDev* kd = kds + sg.run[blockIdx.x];
   for (int k = threadIdx.x; k < kmax; k += blockDim.x) {
     y[0][k] = kd->y[0][k];
     y[1][k] = kd->y[1][k];
   }
   __syncthreads();
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= N) return;
-  double4_32a a = x[v];
-  for (int k = 0; k < kmax; ++k) {
-    const double4_32a z = Z[(size_t)k * N + v];
-    a.x = fma(y[0][k], z.x, a.x);
-    a.z = fma(y[0][k], z.z, a.z);
-    a.y = fma(y[1][k], z.y, a.y);
-    a.w = fma(y[1][k], z.w, a.w);
+  for (int v = sg.lo[blockIdx.x] + threadIdx.x; v < sg.hi[blockIdx.x]; v += blockDim.x) {
+    double4_32a a = x[v];
+    for (int k = 0; k < kmax; ++k) {
+      const double4_32a z = Z[(size_t)k * N + v];
+      a.x = fma(y[0][k], z.x, a.x);
+      a.z = fma(y[0][k], z.z, a.z);
+      a.y = fma(y[1][k], z.y, a.y);
+      a.w = fma(y[1][k], z.w, a.w);
+    }
+    x[v] = a;
   }
-  x[v] = a;
 }
 
-__global__ void k_flags(const KrylovDev* kd, Flags* f) {
+// summary flags over all runs (one block)
+__global__ void k_flags(int nruns, const KrylovDev* kds, Flags* f) {
+  __shared__ int c[3];
+  if (threadIdx.x < 3) c[threadIdx.x] = 0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < nruns; r += blockDim.x) {
+    const KrylovDev* kd = kds + r;
+    atomicAdd(&c[0], kd->cycle_active[0] + kd->cycle_active[1]);
+    atomicAdd(&c[1], kd->active[0] + kd->active[1]);
+    atomicAdd(&c[2], kd->nonfinite);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    f->cycle_active[0] = kd->cycle_active[0];
-    f->cycle_active[1] = kd->cycle_active[1];
-    f->active[0] = kd->active[0];
-    f->active[1] = kd->active[1];
-    f->nonfinite = kd->nonfinite;
-    f->relres[0] = kd->relres[0];
-    f->relres[1] = kd->relres[1];
+    f->cycle_active = c[0];
+    f->active = c[1];
+    f->nonfinite = c[2];
   }
 }
 
-// mass_s = sum_i (M 1)_i phi_s,i  (M symmetric: 1^T M phi)
-__global__ void k_mass(int N, const double* mlump, const double4_32a* x, double* partials,
-                       KrylovDev* kd) {
+// mass_s = sum_i (M 1)_i phi_s,i  (M symmetric: 1^T M phi), per run
+__global__ void k_mass(Seg sg, const double* mlump, const double4_32a* x, double* partials,
+                       KrylovDev* kds) {
   __shared__ double sm[(TPB / 32) * 2];
+  const int run = sg.run[blockIdx.x];
   double acc[2] = {0.0, 0.0};
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+  for (int v = sg.lo[blockIdx.x] + threadIdx.x; v < sg.hi[blockIdx.x]; v += blockDim.x) {
     const double4_32a a = x[v];
     acc[0] = fma(mlump[v], a.x, acc[0]);
     acc[1] = fma(mlump[v], a.y, acc[1]);
   }
   block_sum<2>(acc, sm);
   if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = sm[threadIdx.x];
-  if (!last_block(&kd->ticket)) return;
+  KrylovDev* kd = kds + run;
+  const int b0 = sg.first[run], b1 = sg.first[run + 1];
+  if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
   __shared__ double tot[2];
-  reduce_partials(partials, 2, tot);
+  reduce_partials(partials, b0, b1, 2, tot);
   if (threadIdx.x < 2) kd->mass[threadIdx.x] = tot[threadIdx.x];
   if (threadIdx.x == 0) kd->ticket = 0;
 }
@@ -392,13 +428,31 @@ __global__ void k_rowsum(int N, const int* rowptr, const double* val, double* ou
   out[v] = s;
 }
 
+// per-run statistics gathered for the host after a step
+struct RunStats {
+  int its[2];
+  double relres[2];
+  double mass[2];
+};
+
+__global__ void k_run_stats(int nruns, const KrylovDev* kds, RunStats* out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nruns) return;
+  const KrylovDev* kd = kds + r;
+  for (int s = 0; s < 2; ++s) {
+    out[r].its[s] = kd->its[s];
+    out[r].relres[s] = kd->relres[s];
+    out[r].mass[s] = kd->mass[s];
+  }
+}
+
 }  // namespace ch
 
 // ---------------------------------------------------------------- state
 struct ch_state_s {
   const ch_system_s* sys = nullptr;
   ch_precond_s* pc = nullptr;
-  int N = 0, m = 0;
+  int N = 0, m = 0, R = 1;
   double* x = nullptr;  // N x 4: the state (phi_p, phi_n, mu_p, mu_n)
   double* b = nullptr;  // N x 4
   double* W = nullptr;  // N x 4
@@ -406,9 +460,15 @@ struct ch_state_s {
   double* Z = nullptr;  // m x N x 4
   double* mlump = nullptr;
   double* partials = nullptr;
-  ch::KrylovDev* kd = nullptr;
+  ch::KrylovDev* kd = nullptr;  // R runs
+  ch::Seg seg{};
+  int nblocks = 0;
   ch::Flags* dflags = nullptr;
   ch::Flags* hflags = nullptr;  // pinned
+  ch::RunStats* dstats = nullptr;
+  std::vector<ch::RunStats> hstats;
+  int last_status = 0, last_restarts = 0;
+  float last_ms = 0.f;
   bool set = false;
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;            // private stream for graph capture
@@ -428,6 +488,41 @@ struct ch_state_s {
 
 namespace ch {
 
+// Split every run into blocks of about the same node count (at least one block per run); a
+// single mesh gets about ORTH_BLOCKS blocks.
+static ch_status make_segments(ch_state_s* S, cudaStream_t st) {
+  const std::vector<int>& off = S->sys->mesh->run_off;
+  const int R = S->R;
+  const int64_t N = S->N;
+  const int64_t npb = std::max<int64_t>(TPB, (N + ORTH_BLOCKS - 1) / ORTH_BLOCKS);
+  std::vector<int> run, lo, hi, first(R + 1, 0);
+  for (int r = 0; r < R; ++r) {
+    const int64_t n = off[r + 1] - off[r];
+    const int nb = (int)std::max<int64_t>(1, (n + npb - 1) / npb);
+    const int64_t chunk = (n + nb - 1) / nb;
+    first[r] = (int)run.size();
+    for (int b = 0; b < nb; ++b) {
+      run.push_back(r);
+      lo.push_back((int)std::min<int64_t>(off[r] + b * chunk, off[r + 1]));
+      hi.push_back((int)std::min<int64_t>(off[r] + (b + 1) * chunk, off[r + 1]));
+    }
+  }
+  first[R] = (int)run.size();
+  S->nblocks = (int)run.size();
+  int *d_run = nullptr, *d_lo = nullptr, *d_hi = nullptr, *d_first = nullptr;
+  CH_TRY(S->mem.get(&d_run, run.size()));
+  CH_TRY(S->mem.get(&d_lo, lo.size()));
+  CH_TRY(S->mem.get(&d_hi, hi.size()));
+  CH_TRY(S->mem.get(&d_first, first.size()));
+  CH_CUDA(cudaMemcpyAsync(d_run, run.data(), sizeof(int) * run.size(), cudaMemcpyHostToDevice, st));
+  CH_CUDA(cudaMemcpyAsync(d_lo, lo.data(), sizeof(int) * lo.size(), cudaMemcpyHostToDevice, st));
+  CH_CUDA(cudaMemcpyAsync(d_hi, hi.data(), sizeof(int) * hi.size(), cudaMemcpyHostToDevice, st));
+  CH_CUDA(cudaMemcpyAsync(d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  S->seg = Seg{d_run, d_lo, d_hi, d_first};
+  return CH_OK;
+}
+
 ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, ch_state_s** out) {
   const int m = s->p.restart;
   if (m < 1 || m > MAXM) {
@@ -439,6 +534,8 @@ ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, 
   S->pc = pc;
   S->N = s->N;
   S->m = m;
+  S->R = (int)s->mesh->runs.size();
+  S->hstats.resize(S->R);
   const size_t n4 = (size_t)s->N * 4;
   ch_status r = CH_OK;
   if (r == CH_OK) r = S->mem.get(&S->x, n4);
@@ -447,9 +544,11 @@ ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, 
   if (r == CH_OK) r = S->mem.get(&S->V, n4 * (m + 1));
   if (r == CH_OK) r = S->mem.get(&S->Z, n4 * m);
   if (r == CH_OK) r = S->mem.get(&S->mlump, (size_t)s->N);
-  if (r == CH_OK) r = S->mem.get(&S->partials, (size_t)RED_BLOCKS_MAX * MAXV);
-  if (r == CH_OK) r = S->mem.get(&S->kd, 1);
+  if (r == CH_OK) r = S->mem.get(&S->kd, (size_t)S->R);
   if (r == CH_OK) r = S->mem.get(&S->dflags, 1);
+  if (r == CH_OK) r = S->mem.get(&S->dstats, (size_t)S->R);
+  if (r == CH_OK) r = make_segments(S, st);
+  if (r == CH_OK) r = S->mem.get(&S->partials, (size_t)S->nblocks * MAXV);
   if (r == CH_OK && cudaMallocHost(&S->hflags, sizeof(Flags)) != cudaSuccess) {
     set_error("pinned allocation failed");
     S->hflags = nullptr;
@@ -465,7 +564,7 @@ ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, 
     r = CH_ERR_CUDA;
   }
   if (r == CH_OK) {
-    cudaMemsetAsync(S->kd, 0, sizeof(KrylovDev), st);
+    cudaMemsetAsync(S->kd, 0, sizeof(KrylovDev) * S->R, st);
     cudaMemsetAsync(S->x, 0, n4 * sizeof(double), st);
     k_rowsum<<<blocks_for(s->N), TPB, 0, st>>>(s->N, s->rowptr, s->valM, S->mlump);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
@@ -486,7 +585,7 @@ void state_destroy(ch_state_s* S) { delete S; }
 static ch_status read_flags(ch_state_s* S, cudaStream_t st) {
   {
     ProfScope ps(st, K_FLAGS, 0, 0.0, 0.0);
-    k_flags<<<1, 32, 0, st>>>(S->kd, S->dflags);
+    k_flags<<<1, 256, 0, st>>>(S->R, S->kd, S->dflags);
   }
   CH_LAUNCHED();
   CH_CUDA(cudaMemcpyAsync(S->hflags, S->dflags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
@@ -497,13 +596,12 @@ static ch_status read_flags(ch_state_s* S, cudaStream_t st) {
 
 static double res4_bytes(const ch_system_s* s) { return 20.0 * s->nnz + 4.0 * (s->N + 1) + 96.0 * s->N; }
 
-// One Arnoldi step j for both systems: Z_j = Prec(V_j) (Algorithm 1), W = A Z_j, CGS2 against
-// V_0..V_j with the Givens update, V_{j+1} = W / h_{j+1,j}, and the convergence flags copied to
+// One Arnoldi step j for all systems: Z_j = Prec(V_j) (Algorithm 1), W = A Z_j, CGS2 against
+// V_0..V_j with the Givens update, V_{j+1} = W / h_{j+1,j}, and the summary flags written to
 // dflags.  Everything is enqueued on `st` with no host synchronisation, so it can be captured.
 static ch_status arnoldi_step(ch_state_s* S, int j, cudaStream_t st) {
   const ch_system_s* s = S->sys;
-  const int N = S->N;
-  const int orb = blocks_for(N) < ORTH_BLOCKS ? blocks_for(N) : ORTH_BLOCKS;
+  const int N = S->N, nb = S->nblocks;
   double4_32a* W4 = reinterpret_cast<double4_32a*>(S->W);
   double4_32a* V4 = reinterpret_cast<double4_32a*>(S->V);
   double4_32a* Z4 = reinterpret_cast<double4_32a*>(S->Z);
@@ -514,24 +612,24 @@ static ch_status arnoldi_step(ch_state_s* S, int j, cudaStream_t st) {
   const double nv = j + 1, n32 = 32.0 * N;
   {
     ProfScope ps(st, K_ORTH0, 0, (nv + 1) * n32, 4.0 * nv * N);
-    k_orth<0><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+    k_orth<0><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
   }
   {
     ProfScope ps(st, K_ORTH1, 0, (nv + 2) * n32, 8.0 * nv * N);
-    k_orth<1><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+    k_orth<1><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
   }
   {
     ProfScope ps(st, K_ORTH2, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
-    k_orth<2><<<orb, TPB, 0, st>>>(N, j + 1, V4, W4, S->partials, S->kd);
+    k_orth<2><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
   }
   {
     ProfScope ps(st, K_SCALE4, 0, 64.0 * N, 0.0);
-    k_scale4<<<blocks_for(N), TPB, 0, st>>>(N, W4, V4 + (size_t)(j + 1) * N, S->kd);
+    k_scale4<<<nb, TPB, 0, st>>>(S->seg, W4, V4 + (size_t)(j + 1) * N, S->kd);
   }
   CH_LAUNCHED();
   {
     ProfScope ps(st, K_FLAGS, 0, 0.0, 0.0);
-    k_flags<<<1, 32, 0, st>>>(S->kd, S->dflags);
+    k_flags<<<1, 256, 0, st>>>(S->R, S->kd, S->dflags);
   }
   CH_LAUNCHED();
   return CH_OK;
@@ -569,24 +667,27 @@ static ch_status arnoldi_launch(ch_state_s* S, int j, cudaStream_t st) {
   return CH_OK;
 }
 
-// Solve A x = b for both systems; x holds the initial guess on entry.
-static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
+static ch_status residual_launch(ch_state_s* S, int init, cudaStream_t st) {
   const ch_system_s* s = S->sys;
-  const ch_params& p = s->p;
-  const int N = S->N, m = S->m;
-  const int rb = red_blocks(N);
-  const double4_32a* b4 = reinterpret_cast<const double4_32a*>(S->b);
+  ProfScope ps(st, K_RESIDUAL4, 0, res4_bytes(s), 8.0 * s->nnz + 12.0 * S->N);
+  k_residual4<<<S->nblocks, TPB, 0, st>>>(S->seg, s->rowptr, s->col, s->valM, s->valK, s->a, s->c,
+                                           reinterpret_cast<const double4_32a*>(S->x),
+                                           reinterpret_cast<const double4_32a*>(S->b),
+                                           reinterpret_cast<double4_32a*>(S->W), S->partials, S->kd,
+                                           init, s->p.rtol);
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+// Solve A x = b for all systems; x holds the initial guess on entry.
+static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
+  const ch_params& p = S->sys->p;
+  const int N = S->N, m = S->m, nb = S->nblocks;
   double4_32a* x4 = reinterpret_cast<double4_32a*>(S->x);
   double4_32a* W4 = reinterpret_cast<double4_32a*>(S->W);
   double4_32a* V4 = reinterpret_cast<double4_32a*>(S->V);
   double4_32a* Z4 = reinterpret_cast<double4_32a*>(S->Z);
-  CH_CUDA(cudaMemsetAsync(&S->kd->nonfinite, 0, sizeof(int), st));
-  {
-    ProfScope ps(st, K_RESIDUAL4, 0, res4_bytes(s), 8.0 * s->nnz + 12.0 * N);
-    k_residual4<<<rb, TPB, 0, st>>>(N, s->rowptr, s->col, s->valM, s->valK, s->a, s->c, x4, b4, W4,
-                                    S->partials, S->kd, 1, p.rtol);
-  }
-  CH_LAUNCHED();
+  CH_TRY(residual_launch(S, 1, st));
   CH_TRY(read_flags(S, st));
   if (S->hflags->nonfinite) {
     set_error("non-finite right-hand side or initial residual");
@@ -594,15 +695,15 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
   }
   int total = 0;
   *restarts = 0;
-  while (S->hflags->active[0] || S->hflags->active[1]) {
+  while (S->hflags->active > 0) {
     if (total >= p.max_iter) {
-      set_error("FGMRES reached max_iter = %d (relres %.3e, %.3e)", p.max_iter,
-                S->hflags->relres[0], S->hflags->relres[1]);
+      set_error("FGMRES reached max_iter = %d with %d of %d systems unconverged", p.max_iter,
+                S->hflags->active, 2 * S->R);
       return CH_ERR_NOT_CONVERGED;
     }
     {
       ProfScope ps(st, K_SCALE4, 0, 64.0 * N, 0.0);
-      k_scale4<<<blocks_for(N), TPB, 0, st>>>(N, W4, V4, S->kd);  // V_0 = r / beta
+      k_scale4<<<nb, TPB, 0, st>>>(S->seg, W4, V4, S->kd);  // V_0 = r / beta
     }
     CH_LAUNCHED();
     int j = 0;
@@ -613,7 +714,7 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
         set_error("non-finite value in the Arnoldi process");
         return CH_ERR_NONFINITE;
       }
-      if (!(S->hflags->cycle_active[0] || S->hflags->cycle_active[1]) || total >= p.max_iter) {
+      if (S->hflags->cycle_active == 0 || total >= p.max_iter) {
         ++j;
         break;
       }
@@ -621,18 +722,14 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
     if (j > m) j = m;
     {
       ProfScope ps(st, K_CYCLE_SOLVE, 0, 0.0, 0.0);
-      k_cycle_solve<<<1, 32, 0, st>>>(S->kd);
+      k_cycle_solve<<<blocks_for(2 * S->R, 64), 64, 0, st>>>(S->R, S->kd);
     }
     {
       ProfScope ps(st, K_UPDATE_X, 0, (j + 2) * 32.0 * N, 4.0 * j * N);
-      k_update_x<<<blocks_for(N), TPB, 0, st>>>(N, j, Z4, x4, S->kd);
-    }
-    {
-      ProfScope ps(st, K_RESIDUAL4, 0, res4_bytes(s), 8.0 * s->nnz + 12.0 * N);
-      k_residual4<<<rb, TPB, 0, st>>>(N, s->rowptr, s->col, s->valM, s->valK, s->a, s->c, x4, b4,
-                                      W4, S->partials, S->kd, 0, p.rtol);
+      k_update_x<<<nb, TPB, 0, st>>>(S->seg, N, j, Z4, x4, S->kd);
     }
     CH_LAUNCHED();
+    CH_TRY(residual_launch(S, 0, st));
     CH_TRY(read_flags(S, st));
     if (S->hflags->nonfinite) {
       set_error("non-finite residual");
@@ -662,7 +759,8 @@ __global__ void k_get_state(int N, const double4_32a* x, double* pp, double* pn,
   if (mn) mn[v] = a.w;
 }
 
-// SplitMix64 (Steele, Lea, Flood 2014) on the counter seed ^ (field << 40) ^ node
+// SplitMix64 (Steele, Lea, Flood 2014) on the counter seed_r ^ (field << 40) ^ local node index,
+// seed_r = seed + r for run r
 __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
   z += 0x9E3779B97F4A7C15ULL;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -670,12 +768,19 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-__global__ void k_seeded(int N, double p0, double n0, double noise, uint64_t seed, double4_32a* x) {
+__global__ void k_seeded(int N, const int* node_run, const int* run_off, const double* base_p,
+                         const double* base_n, double noise, uint64_t seed, double4_32a* x) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= N) return;
-  const double up = (double)(splitmix64(seed ^ (0ULL << 40) ^ (uint64_t)v) >> 11) * 0x1.0p-53;
-  const double un = (double)(splitmix64(seed ^ (1ULL << 40) ^ (uint64_t)v) >> 11) * 0x1.0p-53;
-  x[v] = make_double4_32a(p0 + noise * (2.0 * up - 1.0), n0 + noise * (2.0 * un - 1.0), 0.0, 0.0);
+  const int r = node_run[v];
+  const uint64_t sr = seed + (uint64_t)r, loc = (uint64_t)(v - run_off[r]);
+  const double up = (double)(splitmix64(sr ^ (0ULL << 40) ^ loc) >> 11) * 0x1.0p-53;
+  const double un = (double)(splitmix64(sr ^ (1ULL << 40) ^ loc) >> 11) * 0x1.0p-53;
+  // base + noise (2u - 1) with every operation rounded on its own (no FMA contraction), as the
+  // host generator computes it
+  const double tp = __dmul_rn(noise, __dsub_rn(__dmul_rn(2.0, up), 1.0));
+  const double tn = __dmul_rn(noise, __dsub_rn(__dmul_rn(2.0, un), 1.0));
+  x[v] = make_double4_32a(__dadd_rn(base_p[r], tp), __dadd_rn(base_n[r], tn), 0.0, 0.0);
 }
 
 ch_status state_set(ch_state_s* S, const double* pp, const double* pn, const double* mp,
@@ -688,14 +793,30 @@ ch_status state_set(ch_state_s* S, const double* pp, const double* pn, const dou
   return CH_OK;
 }
 
-ch_status state_seeded(ch_state_s* S, double p0, double n0, double noise, uint64_t seed,
-                       cudaStream_t st) {
-  ProfScope prof_io(st, K_STATE_IO, 0, 72.0 * S->N, 0.0);
-  k_seeded<<<blocks_for(S->N), TPB, 0, st>>>(S->N, p0, n0, noise, seed,
-                                              reinterpret_cast<double4_32a*>(S->x));
+ch_status state_seeded_batch(ch_state_s* S, const double* base_p, const double* base_n, double noise,
+                             uint64_t seed, cudaStream_t st) {
+  const int R = S->R;
+  double* d = nullptr;
+  Alloc tmp;
+  CH_TRY(tmp.get(&d, 2 * (size_t)R));
+  CH_CUDA(cudaMemcpyAsync(d, base_p, sizeof(double) * R, cudaMemcpyHostToDevice, st));
+  CH_CUDA(cudaMemcpyAsync(d + R, base_n, sizeof(double) * R, cudaMemcpyHostToDevice, st));
+  {
+    ProfScope prof_io(st, K_STATE_IO, 0, 72.0 * S->N, 0.0);
+    k_seeded<<<blocks_for(S->N), TPB, 0, st>>>(S->N, S->sys->mesh->node_run, S->sys->mesh->run_off_d,
+                                                d, d + R, noise, seed,
+                                                reinterpret_cast<double4_32a*>(S->x));
+  }
   CH_LAUNCHED();
+  CH_CUDA(cudaStreamSynchronize(st));
   S->set = true;
   return CH_OK;
+}
+
+ch_status state_seeded(ch_state_s* S, double p0, double n0, double noise, uint64_t seed,
+                       cudaStream_t st) {
+  std::vector<double> bp(S->R, p0), bn(S->R, n0);
+  return state_seeded_batch(S, bp.data(), bn.data(), noise, seed, st);
 }
 
 ch_status state_get(const ch_state_s* S, double* pp, double* pn, double* ps, double* mp, double* mn,
@@ -705,6 +826,19 @@ ch_status state_get(const ch_state_s* S, double* pp, double* pn, double* ps, dou
                                                  pn, ps, mp, mn);
   CH_LAUNCHED();
   return CH_OK;
+}
+
+static void fill_stats(const ch_state_s* S, int run, ch_step_stats* o) {
+  const RunStats& rs = S->hstats[run];
+  o->iters[0] = rs.its[0];
+  o->iters[1] = rs.its[1];
+  o->restarts = S->last_restarts;
+  o->status = S->last_status;
+  o->relres[0] = rs.relres[0];
+  o->relres[1] = rs.relres[1];
+  o->mass[0] = rs.mass[0];
+  o->mass[1] = rs.mass[1];
+  o->ms = S->last_ms;
 }
 
 ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats) {
@@ -717,34 +851,32 @@ ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats) {
   CH_TRY(rhs_strided(S->sys, S->x, S->x + 1, 4, S->b, st));
   int restarts = 0;
   ch_status r = fgmres(S, st, &restarts);
-  const int rb = red_blocks(S->N);
   {
     ProfScope ps(st, K_MASS, 0, 40.0 * S->N, 2.0 * S->N);
-    k_mass<<<rb, TPB, 0, st>>>(S->N, S->mlump, reinterpret_cast<const double4_32a*>(S->x),
-                               S->partials, S->kd);
+    k_mass<<<S->nblocks, TPB, 0, st>>>(S->seg, S->mlump, reinterpret_cast<const double4_32a*>(S->x),
+                                        S->partials, S->kd);
   }
+  k_run_stats<<<blocks_for(S->R, 64), 64, 0, st>>>(S->R, S->kd, S->dstats);
+  CH_LAUNCHED();
   CH_CUDA(cudaEventRecord(S->ev1, st));
-  if (stats) {
-    KrylovDev* kd = S->kd;
-    int its[2];
-    double rel[2], mass[2];
-    CH_CUDA(cudaMemcpyAsync(its, kd->its, sizeof(its), cudaMemcpyDeviceToHost, st));
-    CH_CUDA(cudaMemcpyAsync(rel, kd->relres, sizeof(rel), cudaMemcpyDeviceToHost, st));
-    CH_CUDA(cudaMemcpyAsync(mass, kd->mass, sizeof(mass), cudaMemcpyDeviceToHost, st));
-    CH_CUDA(cudaStreamSynchronize(st));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, S->ev0, S->ev1);
-    stats->iters[0] = its[0];
-    stats->iters[1] = its[1];
-    stats->restarts = restarts;
-    stats->status = r;
-    stats->relres[0] = rel[0];
-    stats->relres[1] = rel[1];
-    stats->mass[0] = mass[0];
-    stats->mass[1] = mass[1];
-    stats->ms = ms;
-  }
+  CH_CUDA(cudaMemcpyAsync(S->hstats.data(), S->dstats, sizeof(RunStats) * S->R, cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  cudaEventElapsedTime(&S->last_ms, S->ev0, S->ev1);
+  S->last_status = r;
+  S->last_restarts = restarts;
+  if (stats) fill_stats(S, 0, stats);
   return r;
 }
+
+ch_status state_run_stats(const ch_state_s* S, int run, ch_step_stats* out) {
+  if (run < 0 || run >= S->R) {
+    set_error("run %d out of range [0, %d)", run, S->R);
+    return CH_ERR_ARG;
+  }
+  fill_stats(S, run, out);
+  return CH_OK;
+}
+
+int state_runs(const ch_state_s* S) { return S->R; }
 
 }  // namespace ch
