@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-nx", type=int, default=256)
     return ap.parse_args()
 
 
@@ -154,7 +156,8 @@ def make_solver(ch, nx, ny, precision):
     return system, pc, state
 
 
-def timed_steps(torch, ch, state, K, flush, barrier):
+def timed_steps(torch, ch, state, K, flush, barrier, net=None):
+    """K steps timed with CUDA events (ch_step, or ch_step_learned with `net`)."""
     iters = []
     torch.cuda.synchronize()
     barrier()
@@ -162,7 +165,7 @@ def timed_steps(torch, ch, state, K, flush, barrier):
     e0.record()
     for _ in range(K):
         flush.zero_()  # 256 MiB write: evicts L2 between steps
-        st = state.step()
+        st = state.step() if net is None else state.step_learned(net)
         if st["status"] != 0 or max(st["relres"]) > 1e-8:
             raise RuntimeError(f"step did not reach 1e-8: {st}")
         iters.append(st["iters"])
@@ -170,6 +173,51 @@ def timed_steps(torch, ch, state, K, flush, barrier):
     torch.cuda.synchronize()
     barrier()
     return e0.elapsed_time(e1), iters
+
+
+def learned_section(torch, ch, nx, K, flush, barrier, world):
+    """The learned warm start on an nx x nx grid: 2000 (s_{k-1}, s_k, s_{k+1}) triples from the
+    plain FP64 solver (20 seeded runs x 100 steps), residual-loss training by the library's
+    kernels, then K timed steps of a held-out run per form: previous-state guess, the network,
+    and linear extrapolation (the zero network), in FP64 and mixed precision."""
+    import time
+    import numpy as np
+    from paper_2204_03575_gb300 import warmstart as ws
+    t0 = time.time()
+    data = ws.generate_pairs(nx, nx, seeds=range(20), steps=100, dtype=torch.float64)
+    torch.cuda.synchronize()
+    t_gen = time.time() - t0
+    system = ws.make_system(nx, nx)
+    net = ch.WarmStartNet(nx + 1, nx + 1, max_batch=8)
+    t0 = time.time()
+    net, info = ws.train_residual(data, net, system, epochs=8, batch=8, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    del data
+    zero = ws.zero_net(nx, nx)
+    out = {"workload": f"2D {nx}x{nx} P1 triangles ({(nx + 1) ** 2} nodes), held-out seed 1000, bases from "
+                       f"SplitMix64 in [0.20, 0.45), noise +/-0.01; timed steps 3..{K + 2} of the run",
+           "pairs": info["pairs"], "generate_s": round(t_gen, 2), "train_s": round(t_train, 2),
+           "train_loss_first_last_epoch": [info["loss_per_epoch"][0], info["loss_per_epoch"][-1]],
+           "loss_meaning": "mean |r|^2 / |r_extrapolation|^2 of the step residual"}
+    for prec, tag in ((0, "fp64"), (1, "mixed")):
+        res = {}
+        for form, n in (("previous_state", None), ("learned", net), ("extrapolation", zero)):
+            state = ws.make_state(nx, nx, prec)
+            b0, b1 = ws.seed_bases(1000)
+            state.init_seeded(b0, b1, 0.01, seed=1000)
+            for _ in range(2):  # ch_step_learned starts from the previous state for two steps
+                if n is None:
+                    state.step()
+                else:
+                    state.step_learned(n)
+            ms, iters = timed_steps(torch, ch, state, K, flush, barrier, net=n)
+            res[form] = {"steps_per_s": world * K / (ms * 1e-3), "ms_per_step": ms / K,
+                         "iters_per_step_mean": float(np.mean(iters))}
+        out[tag] = res
+    out["mixed_learned_over_fp64_previous_state"] = (out["mixed"]["learned"]["steps_per_s"]
+                                                     / out["fp64"]["previous_state"]["steps_per_s"])
+    return out
 
 
 def roofline(prof, peaks, sustained):
@@ -360,6 +408,11 @@ def main():
                  "launches_per_step": blaunch / KB, "max_relres_last_step": worst}
         del bstate, bsys, bmesh
 
+    # ---- learned warm start (256 x 256 grid): training, then FP64 / mixed with and without it
+    learned = None
+    if not args.no_learned:
+        learned = learned_section(torch, ch, args.learned_nx, min(K, 40), flush, barrier, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, sample, _, _ = oracle_rate(args.nx, args.ny, 2)
@@ -377,7 +430,7 @@ def main():
         "top_kernels": top_kernels(prof64),
         "iters_per_step_mean": float(np.mean(iters)), "iters_per_step_max": int(np.max(iters)),
         "amg_levels": {k: [r for r, _ in v] for k, v in levels.items()},
-        "mixed": mixed, "batch": batch, "cpu_baseline": cpu,
+        "mixed": mixed, "batch": batch, "learned": learned, "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -91,12 +91,14 @@ typedef struct ch_step_stats {
   double relres[2];          /* true final ||b - A x|| / ||b|| per species, FP64 */
   double mass[2];            /* int phi_h = 1^T M phi^{k+1} per species */
   double ms;                 /* wall time of the step (ms, CUDA events) */
+  int32_t warm[2];           /* ch_step_guess: 1 if the caller's guess was used as initial iterate */
 } ch_step_stats;
 
 typedef struct ch_mesh_s ch_mesh_t;
 typedef struct ch_system_s ch_system_t;
 typedef struct ch_precond_s ch_precond_t;
 typedef struct ch_state_s ch_state_t;
+typedef struct ch_ws_s ch_ws_t;
 
 const char* ch_status_str(ch_status s);
 const char* ch_last_error(void);
@@ -213,9 +215,70 @@ ch_status ch_state_get(const ch_state_t* st, double* phi_p, double* phi_nfa, dou
  * previous step as initial guess, state update.  stats (host) may be NULL.  On
  * CH_ERR_NOT_CONVERGED the best iterate is stored in the state. */
 ch_status ch_step(ch_state_t* st, void* stream, ch_step_stats* stats);
+/* One time step as ch_step, but with a candidate initial iterate `guess` (N x 4 fp64 device, the
+ * state layout): for each run and species FGMRES starts from the guess if its true FP64 residual
+ * ||b - A guess|| is smaller than that of the previous step's state, else from the previous state
+ * (stats->warm records which).  The right-hand side is always built from the previous state. */
+ch_status ch_step_guess(ch_state_t* st, const double* guess, void* stream, ch_step_stats* stats);
 /* nsteps steps; per_step (host, nsteps entries) may be NULL.  Stops at the first error. */
 ch_status ch_run(ch_state_t* st, int32_t nsteps, void* stream, ch_step_stats* per_step);
 void ch_state_destroy(ch_state_t* st);
+
+/* ---------------------------------------------------------------- learned warm start
+ * A 3-layer convolutional network on the nodal image of a 2D structured mesh (H = ny+1 rows,
+ * W = nx+1 columns, node i + W j = pixel (j, i)) that predicts the next step's state, used as the
+ * guess of ch_step_guess.  The paper has no counterpart (this extension is one of the build's own).
+ * Layers: 3x3 convolutions with zero padding, 8 -> 32 (ReLU) -> 32 (ReLU) -> 4; BF16 weights and
+ * activations, FP32 accumulation on the tensor cores, FP32 master weights with Adam.
+ * Input: the state s_k = (phi_p, phi_nfa, mu_p, mu_nfa) and its change d_k = s_k - s_{k-1};
+ * r_k[c] = RMS over the image of channel c of d_k.  Channels (s_k - mean[0:4]) * inv_std[0:4] and
+ * (d_k / r_k - mean[4:8]) * inv_std[4:8]; output y: the correction to the linear extrapolation,
+ * pred = s_k + d_k + y * out_scale * r_k.
+ * Parameters (ch_ws_nparams() floats, host arrays), in order: w1[9][16][32] (tap = 3 ky + kx,
+ * input channel padded to 16, output channel), b1[32], w2[9][32][32], b2[32], w3[9][32][8]
+ * (output channel padded to 8), b3[8]; padded entries are ignored. */
+int32_t ch_ws_nparams(void);
+ch_status ch_ws_create(int32_t H, int32_t W, int32_t max_batch, ch_ws_t** out);
+void ch_ws_destroy(ch_ws_t* w);
+ch_status ch_ws_set_params(ch_ws_t* w, const float* params, void* stream);     /* host; resets Adam */
+/* host outputs, either may be NULL; grads are those of the last ch_ws_train_step */
+ch_status ch_ws_get_params(const ch_ws_t* w, float* params, float* grads, void* stream);
+/* host: mean[8], inv_std[8], out_scale[4] */
+ch_status ch_ws_set_norm(ch_ws_t* w, const float* norm20, void* stream);
+/* pred (N x 4 fp64 device): the prediction of the next state from the state s and its predecessor */
+ch_status ch_ws_predict(ch_ws_t* w, const double* state, const double* prev, double* pred, void* stream);
+/* One training step on B <= max_batch samples (device fp32, B x N x 4 each): states x = s_k, their
+ * predecessors q = s_{k-1} and successors n = s_{k+1}; the target of y is
+ * t = ((n - x) - (x - q)) / (out_scale * r_k).  With E = y - t and G the graph Laplacian of the
+ * pixel grid ((G E)_p = sum over the 4-neighbours q of p in the image of E_q - E_p), the loss is
+ * (sum E^2 + lap * sum (G E)^2) / (4 B N): lap >= 0 weighs rough errors, which dominate the step's
+ * residual through its stiffness rows.  Computes the gradients (ch_ws_get_params); lr > 0 also
+ * takes an Adam step.  *loss (host) may be NULL.  CH_ERR_ARG: B outside [1, max_batch], lap < 0
+ * or not finite. */
+ch_status ch_ws_train_step(ch_ws_t* w, const float* x, const float* q, const float* n, int32_t B,
+                           float lap, float lr, float* loss, void* stream);
+
+/* One training step against the residual of Eq. (14) (the quantity FGMRES's stopping test
+ * measures), on B <= max_batch samples of consecutive states (device fp64, B x N x 4 each:
+ * x = s_k, q = s_{k-1}) of the 2D single-run mesh of `sys` (N = H W).  Per sample and species,
+ * with b the right-hand side of the step from s_k and c the network's correction,
+ * r_ex = b - A (2 s_k - s_{k-1}) and r = r_ex - A c, measured in the norm of the preconditioner
+ * `pc` (<r, P^-1 r>, Algorithm 1 built on `sys`) or, if pc is NULL, the Euclidean norm.  The loss
+ * is the mean over samples and species of |r|^2 / |r_ex|^2, so a loss below 1 means the
+ * prediction beats linear extrapolation.  Computes the gradients; lr > 0 also takes an Adam step.
+ * *loss (host) may be NULL.  CH_ERR_ARG: B outside [1, max_batch], a system that is not a
+ * single-run 2D mesh of H x W nodes, or a preconditioner of another system. */
+ch_status ch_ws_train_residual(ch_ws_t* w, const ch_system_t* sys, ch_precond_t* pc, const double* x,
+                               const double* q, int32_t B, float lr, float* loss, void* stream);
+
+/* One time step whose candidate guess is the network's prediction from the state and its
+ * predecessor, which the state keeps on the device across consecutive ch_step_learned calls; the
+ * choice between guess and previous state is that of ch_step_guess.  Until two steps have been
+ * taken since the state was set (the first sets up the chemical potentials), and on the first
+ * learned step after a step of another kind, the step starts from the previous state.
+ * stats->ms includes the prediction.  CH_ERR_ARG: a network sized for another mesh, or a state
+ * of several runs. */
+ch_status ch_step_learned(ch_state_t* st, ch_ws_t* w, void* stream, ch_step_stats* stats);
 
 /* ---------------------------------------------------------------- launch accounting
  * Every kernel launch of the library is counted per kernel and working precision, with the

@@ -60,11 +60,12 @@ class Params(ctypes.Structure):
 class StepStats(ctypes.Structure):
     """Mirror of ch_step_stats."""
     _fields_ = [("iters", ctypes.c_int32 * 2), ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("relres", ctypes.c_double * 2), ("mass", ctypes.c_double * 2), ("ms", ctypes.c_double)]
+                ("relres", ctypes.c_double * 2), ("mass", ctypes.c_double * 2), ("ms", ctypes.c_double),
+                ("warm", ctypes.c_int32 * 2)]
 
     def as_dict(self):
         return {"iters": list(self.iters), "restarts": self.restarts, "status": self.status,
-                "relres": list(self.relres), "mass": list(self.mass), "ms": self.ms}
+                "relres": list(self.relres), "mass": list(self.mass), "ms": self.ms, "warm": list(self.warm)}
 
 
 class ProfEntry(ctypes.Structure):
@@ -112,6 +113,19 @@ _SIGNATURES = {
     "ch_step": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(StepStats)]),
     "ch_run": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.POINTER(StepStats)]),
     "ch_state_destroy": (None, [_VP]),
+    "ch_step_learned": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(StepStats)]),
+    "ch_step_guess": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(StepStats)]),
+    "ch_ws_nparams": (ctypes.c_int32, []),
+    "ch_ws_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_VP)]),
+    "ch_ws_destroy": (None, [_VP]),
+    "ch_ws_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), _VP]),
+    "ch_ws_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _VP]),
+    "ch_ws_set_norm": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), _VP]),
+    "ch_ws_predict": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "ch_ws_train_residual": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_float,
+                                            ctypes.POINTER(ctypes.c_float), _VP]),
+    "ch_ws_train_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                        ctypes.POINTER(ctypes.c_float), _VP]),
     "ch_profile_enable": (ctypes.c_int, [ctypes.c_int32]),
     "ch_profile_read": (ctypes.c_int, [ctypes.POINTER(ProfEntry), ctypes.c_int32, _I32P, ctypes.c_int32]),
 }
@@ -340,6 +354,29 @@ class State:
             _check(status, "ch_step")
         return st.as_dict()
 
+    def step_guess(self, guess, stream=None, check=True):
+        """One step starting from `guess` (N x 4 fp64: phi_p, phi_nfa, mu_p, mu_nfa) where it beats
+        the previous state's residual."""
+        g = _f64(guess, self.system.n)
+        st = StepStats()
+        status = lib().ch_step_guess(self._h, _ptr(g), _stream(stream), ctypes.byref(st))
+        if check:
+            _check(status, "ch_step_guess")
+        return st.as_dict()
+
+    def step_learned(self, net, stream=None, check=True):
+        """One step from the warm-start network's prediction (ch_step_learned)."""
+        st = StepStats()
+        status = lib().ch_step_learned(self._h, net._h, _stream(stream), ctypes.byref(st))
+        if check:
+            _check(status, "ch_step_learned")
+        return st.as_dict()
+
+    def state4(self, stream=None):
+        """The state as one N x 4 fp64 tensor (phi_p, phi_nfa, mu_p, mu_nfa)."""
+        g = self.get(stream)
+        return torch.stack([g["phi_p"], g["phi_nfa"], g["mu_p"], g["mu_nfa"]], 1).contiguous()
+
     def run(self, nsteps: int, stream=None):
         arr = (StepStats * max(nsteps, 1))()
         _check(lib().ch_run(self._h, nsteps, _stream(stream), arr), "ch_run")
@@ -364,3 +401,71 @@ def profile_read(reset: bool = False):
     _check(lib().ch_profile_read(arr, n.value, ctypes.byref(n), 1 if reset else 0), "ch_profile_read")
     return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes,
                                    "fmas": arr[i].fmas} for i in range(n.value)}
+
+
+class WarmStartNet:
+    """The learned warm-start network (ch_ws_*): BF16 convolutional net on the nodal image."""
+
+    def __init__(self, H: int, W: int, max_batch: int = 8):
+        self.H, self.W, self.max_batch = H, W, max_batch
+        self._h = _VP()
+        _check(lib().ch_ws_create(H, W, max_batch, ctypes.byref(self._h)), "ch_ws_create")
+        self.nparams = lib().ch_ws_nparams()
+
+    def set_params(self, params, stream=None):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == self.nparams
+        _check(lib().ch_ws_set_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream(stream)),
+               "ch_ws_set_params")
+
+    def get_params(self, stream=None):
+        import numpy as np
+        p = np.empty(self.nparams, np.float32)
+        g = np.empty(self.nparams, np.float32)
+        _check(lib().ch_ws_get_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                      g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream(stream)),
+               "ch_ws_get_params")
+        return p, g
+
+    def set_norm(self, mean, inv_std, out_scale, stream=None):
+        """mean, inv_std: 8 values (the 4 fields, then their change); out_scale: 4."""
+        import numpy as np
+        a = np.ascontiguousarray(np.concatenate([mean, inv_std, out_scale]), dtype=np.float32)
+        assert a.size == 20
+        _check(lib().ch_ws_set_norm(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream(stream)),
+               "ch_ws_set_norm")
+
+    def predict(self, state4, prev4, stream=None):
+        s, q = _f64(state4), _f64(prev4)
+        pred = torch.empty_like(s)
+        _check(lib().ch_ws_predict(self._h, _ptr(s), _ptr(q), _ptr(pred), _stream(stream)), "ch_ws_predict")
+        return pred
+
+    def train_residual(self, system, x, q, lr: float, precond=None, stream=None):
+        """One step against the residual of the time step (x = s_k, q = s_{k-1}: B x N x 4 fp64
+        CUDA), in the norm of `precond` if given; returns the loss (mean |r|^2 / |r_extrap|^2)."""
+        for a in (x, q):
+            if a.dtype != torch.float64 or not a.is_contiguous() or not a.is_cuda:
+                raise ValueError("expected contiguous float64 CUDA tensors")
+        loss = ctypes.c_float()
+        pc = precond._h if precond is not None else None
+        _check(lib().ch_ws_train_residual(self._h, system._h, pc, _ptr(x), _ptr(q), x.shape[0], lr, ctypes.byref(loss),
+                                          _stream(stream)), "ch_ws_train_residual")
+        return loss.value
+
+    def train_step(self, x, q, n, lr: float, lap: float = 0.0, stream=None):
+        """One step on states x, predecessors q and successors n (B x N x 4 fp32 CUDA); `lap`
+        weighs the grid-Laplacian term of the loss."""
+        for a in (x, q, n):
+            if a.dtype != torch.float32 or not a.is_contiguous() or not a.is_cuda:
+                raise ValueError("expected contiguous float32 CUDA tensors")
+        loss = ctypes.c_float()
+        _check(lib().ch_ws_train_step(self._h, _ptr(x), _ptr(q), _ptr(n), x.shape[0], lap, lr, ctypes.byref(loss),
+                                      _stream(stream)), "ch_ws_train_step")
+        return loss.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ch_ws_destroy(self._h)
+            self._h = None

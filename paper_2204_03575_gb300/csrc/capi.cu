@@ -375,4 +375,61 @@ ch_status ch_run(ch_state_t* st, int32_t nsteps, void* stream, ch_step_stats* pe
 
 void ch_state_destroy(ch_state_t* st) { ch::state_destroy(st); }
 
+ch_status ch_step_guess(ch_state_t* st, const double* guess, void* stream, ch_step_stats* stats) {
+  CH_ARG(st != nullptr && guess != nullptr, "NULL argument");
+  CH_ARG((reinterpret_cast<uintptr_t>(guess) & 31) == 0, "guess must be 32-byte aligned");
+  return ch::state_step_guess(st, guess, S(stream), stats);
+}
+
+ch_status ch_step_learned(ch_state_t* state, ch_ws_t* w, void* stream, ch_step_stats* stats) {
+  CH_ARG(state != nullptr && w != nullptr, "NULL argument");
+  return ch::state_step_learned(state, w, S(stream), stats);
+}
+
+// ---------------------------------------------------------------- learned warm start
+int32_t ch_ws_nparams(void) { return ch::ws_nparam(); }
+
+ch_status ch_ws_create(int32_t H, int32_t W, int32_t max_batch, ch_ws_t** out) {
+  CH_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  CH_ARG(H >= 1 && W >= 1 && (double)H * W < 1.0e8, "image size out of range");
+  CH_ARG(max_batch >= 1 && max_batch <= 256, "max_batch must be in [1, 256]");
+  return ch::ws_create(H, W, max_batch, out);
+}
+
+void ch_ws_destroy(ch_ws_t* w) { ch::ws_destroy(w); }
+
+ch_status ch_ws_set_params(ch_ws_t* w, const float* params, void* stream) {
+  CH_ARG(w != nullptr && params != nullptr, "NULL argument");
+  return ch::ws_set_params(w, params, S(stream));
+}
+
+ch_status ch_ws_get_params(const ch_ws_t* w, float* params, float* grads, void* stream) {
+  CH_ARG(w != nullptr, "NULL argument");
+  return ch::ws_get_params(w, params, grads, S(stream));
+}
+
+ch_status ch_ws_set_norm(ch_ws_t* w, const float* norm20, void* stream) {
+  CH_ARG(w != nullptr && norm20 != nullptr, "NULL argument");
+  return ch::ws_set_norm(w, norm20, S(stream));
+}
+
+ch_status ch_ws_predict(ch_ws_t* w, const double* state, const double* prev, double* pred, void* stream) {
+  CH_ARG(w != nullptr && state != nullptr && prev != nullptr && pred != nullptr, "NULL argument");
+  CH_ARG(state != pred && prev != pred, "pred must not alias the inputs");
+  return ch::ws_predict(w, state, prev, pred, S(stream));
+}
+
+ch_status ch_ws_train_step(ch_ws_t* w, const float* x, const float* q, const float* n, int32_t B,
+                           float lap, float lr, float* loss, void* stream) {
+  CH_ARG(w != nullptr && x != nullptr && q != nullptr && n != nullptr, "NULL argument");
+  return ch::ws_train_step(w, x, q, n, B, lap, lr, loss, S(stream));
+}
+
+ch_status ch_ws_train_residual(ch_ws_t* w, const ch_system_t* sys, ch_precond_t* pc, const double* x,
+                               const double* q, int32_t B, float lr, float* loss, void* stream) {
+  CH_ARG(w != nullptr && sys != nullptr && x != nullptr && q != nullptr, "NULL argument");
+  return ch::ws_train_residual(w, sys, pc, x, q, B, lr, loss, S(stream));
+}
+
 }  // extern "C"

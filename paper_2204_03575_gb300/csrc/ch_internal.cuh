@@ -117,7 +117,8 @@ enum KernelId {
   K_CYCLE_SOLVE, K_FLAGS, K_MASS, K_CHEB_FIRST, K_CHEB_STEP, K_VRESIDUAL, K_RESTRICT, K_PROLONG,
   K_COARSE, K_VLOAD, K_VSTORE, K_SPMV_M, K_STATE_IO,
   // the same V-cycle kernels on levels below the finest (accounted separately)
-  K_CHEB_FIRST_C, K_CHEB_STEP_C, K_VRESIDUAL_C, K_RESTRICT_C, K_PROLONG_C, K_COUNT
+  K_CHEB_FIRST_C, K_CHEB_STEP_C, K_VRESIDUAL_C, K_RESTRICT_C, K_PROLONG_C,
+  K_WS_CONV, K_WS_IO, K_GUESS, K_COUNT
 };
 // RAII around one kernel launch: counts it with its algorithmic bytes / FMAs and, when timing
 // is on, records CUDA events around it on the launching stream.
@@ -245,3 +246,22 @@ ch_status state_run_stats(const ch_state_s* S, int run, ch_step_stats* out);
 int state_runs(const ch_state_s* S);
 ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats);
 }
+
+// warmstart.cu
+struct ch_ws_s;
+namespace ch {
+ch_status ws_create(int H, int W, int Bmax, ch_ws_s** out);
+void ws_destroy(ch_ws_s* w);
+ch_status ws_set_params(ch_ws_s* w, const float* host, cudaStream_t st);
+ch_status ws_get_params(const ch_ws_s* w, float* host, float* host_grads, cudaStream_t st);
+ch_status ws_set_norm(ch_ws_s* w, const float* host20, cudaStream_t st);
+ch_status ws_predict(ch_ws_s* w, const double* state, const double* prev, double* pred, cudaStream_t st);
+ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float* n, int B, float lap,
+                        float lr, float* loss, cudaStream_t st);
+ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc, const double* x,
+                            const double* q, int B, float lr, float* loss, cudaStream_t st);
+int ws_nparam();
+int ws_pixels(const ch_ws_s* w);
+ch_status state_step_learned(ch_state_s* S, ch_ws_s* w, cudaStream_t st, ch_step_stats* stats);
+ch_status state_step_guess(ch_state_s* S, const double* guess, cudaStream_t st, ch_step_stats* stats);
+}  // namespace ch

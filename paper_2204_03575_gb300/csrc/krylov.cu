@@ -37,6 +37,8 @@ struct KrylovDev {
   int its[2];           // Arnoldi steps taken this step
   int nonfinite;
   unsigned int ticket;  // last-block counter of this run
+  double relres_prev[2];  // initial-guess selection: residual of the previous step's state
+  int warm[2];            // the caller's guess was taken for this species
 };
 
 struct Flags {  // summary over all runs
@@ -433,6 +435,7 @@ struct RunStats {
   int its[2];
   double relres[2];
   double mass[2];
+  int warm[2];
 };
 
 __global__ void k_run_stats(int nruns, const KrylovDev* kds, RunStats* out) {
@@ -443,6 +446,43 @@ __global__ void k_run_stats(int nruns, const KrylovDev* kds, RunStats* out) {
     out[r].its[s] = kd->its[s];
     out[r].relres[s] = kd->relres[s];
     out[r].mass[s] = kd->mass[s];
+    out[r].warm[s] = kd->warm[s];
+  }
+}
+
+__global__ void k_clear_warm(int nruns, KrylovDev* kds) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nruns) kds[r].warm[0] = kds[r].warm[1] = 0;
+}
+
+// initial-guess selection: remember the residual of the previous state, then take the guess
+// per (run, species) where its residual is smaller
+__global__ void k_save_relres(int nruns, KrylovDev* kds) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nruns) return;
+  kds[r].relres_prev[0] = kds[r].relres[0];
+  kds[r].relres_prev[1] = kds[r].relres[1];
+}
+
+__global__ void k_pick_guess(Seg sg, const double4_32a* __restrict__ guess, double4_32a* x, KrylovDev* kds) {
+  KrylovDev* kd = kds + sg.run[blockIdx.x];
+  const bool tp = kd->relres[0] < kd->relres_prev[0], tn = kd->relres[1] < kd->relres_prev[1];
+  if (blockIdx.x == sg.first[sg.run[blockIdx.x]] && threadIdx.x == 0) {
+    kd->warm[0] = tp;
+    kd->warm[1] = tn;
+  }
+  for (int v = sg.lo[blockIdx.x] + threadIdx.x; v < sg.hi[blockIdx.x]; v += blockDim.x) {
+    const double4_32a g = guess[v];
+    double4_32a a = x[v];
+    if (tp) {
+      a.x = g.x;
+      a.z = g.z;
+    }
+    if (tn) {
+      a.y = g.y;
+      a.w = g.w;
+    }
+    x[v] = a;
   }
 }
 
@@ -471,6 +511,10 @@ struct ch_state_s {
   float last_ms = 0.f;
   bool set = false;
   bool use_graphs = true;
+  int since_set = 0;                // steps taken since the state was last set
+  int learn_k = 0;                  // consecutive learned steps (x_prev valid when >= 1)
+  double* x_prev = nullptr;         // N x 4: the state before the last learned step
+  double* guess = nullptr;          // N x 4: the network's prediction
   cudaStream_t cap_stream = nullptr;            // private stream for graph capture
   cudaGraphExec_t graph[64] = {};               // Arnoldi step j, captured on first use
   ch::ProfTally tally[64];                      // launch accounting of each graph
@@ -667,11 +711,11 @@ static ch_status arnoldi_launch(ch_state_s* S, int j, cudaStream_t st) {
   return CH_OK;
 }
 
-static ch_status residual_launch(ch_state_s* S, int init, cudaStream_t st) {
+static ch_status residual_launch(ch_state_s* S, int init, cudaStream_t st, const double* x = nullptr) {
   const ch_system_s* s = S->sys;
   ProfScope ps(st, K_RESIDUAL4, 0, res4_bytes(s), 8.0 * s->nnz + 12.0 * S->N);
   k_residual4<<<S->nblocks, TPB, 0, st>>>(S->seg, s->rowptr, s->col, s->valM, s->valK, s->a, s->c,
-                                           reinterpret_cast<const double4_32a*>(S->x),
+                                           reinterpret_cast<const double4_32a*>(x ? x : S->x),
                                            reinterpret_cast<const double4_32a*>(S->b),
                                            reinterpret_cast<double4_32a*>(S->W), S->partials, S->kd,
                                            init, s->p.rtol);
@@ -790,6 +834,7 @@ ch_status state_set(ch_state_s* S, const double* pp, const double* pn, const dou
                                                  reinterpret_cast<double4_32a*>(S->x));
   CH_LAUNCHED();
   S->set = true;
+  S->since_set = S->learn_k = 0;
   return CH_OK;
 }
 
@@ -810,6 +855,7 @@ ch_status state_seeded_batch(ch_state_s* S, const double* base_p, const double* 
   CH_LAUNCHED();
   CH_CUDA(cudaStreamSynchronize(st));
   S->set = true;
+  S->since_set = S->learn_k = 0;
   return CH_OK;
 }
 
@@ -839,16 +885,16 @@ static void fill_stats(const ch_state_s* S, int run, ch_step_stats* o) {
   o->mass[0] = rs.mass[0];
   o->mass[1] = rs.mass[1];
   o->ms = S->last_ms;
+  o->warm[0] = rs.warm[0];
+  o->warm[1] = rs.warm[1];
 }
 
-ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats) {
-  if (!S->set) {
-    set_error("state not initialised (call ch_state_set or ch_state_init_seeded)");
-    return CH_ERR_STATE;
-  }
-  CH_CUDA(cudaEventRecord(S->ev0, st));
+// One step from the previous state; rec0: record the start event here (else the caller did).
+static ch_status step_plain_core(ch_state_s* S, cudaStream_t st, ch_step_stats* stats, bool rec0) {
+  if (rec0) CH_CUDA(cudaEventRecord(S->ev0, st));
   // right-hand sides from phi^k (strided views of the state)
   CH_TRY(rhs_strided(S->sys, S->x, S->x + 1, 4, S->b, st));
+  k_clear_warm<<<blocks_for(S->R, 64), 64, 0, st>>>(S->R, S->kd);
   int restarts = 0;
   ch_status r = fgmres(S, st, &restarts);
   {
@@ -864,9 +910,100 @@ ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats) {
   cudaEventElapsedTime(&S->last_ms, S->ev0, S->ev1);
   S->last_status = r;
   S->last_restarts = restarts;
+  S->since_set += 1;
   if (stats) fill_stats(S, 0, stats);
   return r;
 }
+
+ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats) {
+  if (!S->set) {
+    set_error("state not initialised (call ch_state_set or ch_state_init_seeded)");
+    return CH_ERR_STATE;
+  }
+  S->learn_k = 0;
+  return step_plain_core(S, st, stats, true);
+}
+
+// A step whose initial guess is, per (run, species), the caller's guess when its true residual
+// ||b - A guess|| is smaller than that of the previous state, else the previous state.
+static ch_status step_guess_core(ch_state_s* S, const double* guess, cudaStream_t st, ch_step_stats* stats,
+                                 bool rec0) {
+  if (rec0) CH_CUDA(cudaEventRecord(S->ev0, st));
+  CH_TRY(rhs_strided(S->sys, S->x, S->x + 1, 4, S->b, st));
+  CH_TRY(residual_launch(S, 1, st));  // previous state
+  {
+    ProfScope ps(st, K_GUESS, 0, 0.0, 0.0);
+    k_save_relres<<<blocks_for(S->R, 64), 64, 0, st>>>(S->R, S->kd);
+  }
+  CH_TRY(residual_launch(S, 1, st, guess));
+  {
+    ProfScope ps(st, K_GUESS, 0, 96.0 * S->N, 0.0);
+    k_pick_guess<<<S->nblocks, TPB, 0, st>>>(S->seg, reinterpret_cast<const double4_32a*>(guess),
+                                              reinterpret_cast<double4_32a*>(S->x), S->kd);
+  }
+  CH_LAUNCHED();
+  int restarts = 0;
+  ch_status r = fgmres(S, st, &restarts);
+  {
+    ProfScope ps(st, K_MASS, 0, 40.0 * S->N, 2.0 * S->N);
+    k_mass<<<S->nblocks, TPB, 0, st>>>(S->seg, S->mlump, reinterpret_cast<const double4_32a*>(S->x),
+                                        S->partials, S->kd);
+  }
+  k_run_stats<<<blocks_for(S->R, 64), 64, 0, st>>>(S->R, S->kd, S->dstats);
+  CH_LAUNCHED();
+  CH_CUDA(cudaEventRecord(S->ev1, st));
+  CH_CUDA(cudaMemcpyAsync(S->hstats.data(), S->dstats, sizeof(RunStats) * S->R, cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  cudaEventElapsedTime(&S->last_ms, S->ev0, S->ev1);
+  S->last_status = r;
+  S->last_restarts = restarts;
+  S->since_set += 1;
+  if (stats) fill_stats(S, 0, stats);
+  return r;
+}
+
+ch_status state_step_guess(ch_state_s* S, const double* guess, cudaStream_t st, ch_step_stats* stats) {
+  if (!S->set) {
+    set_error("state not initialised (call ch_state_set or ch_state_init_seeded)");
+    return CH_ERR_STATE;
+  }
+  S->learn_k = 0;
+  return step_guess_core(S, guess, st, stats, true);
+}
+
+// A step whose guess is the warm-start network's prediction from the state and its predecessor
+// (kept on the device across consecutive learned steps).  The network needs a predecessor that
+// is not the initial state (whose chemical potentials the first step sets up): until two steps
+// have been taken since the state was set, and after any step of another kind, the step starts
+// from the previous state.  ms in the statistics includes the prediction.
+ch_status state_step_learned(ch_state_s* S, ch_ws_s* w, cudaStream_t st, ch_step_stats* stats) {
+  if (!S->set) {
+    set_error("state not initialised (call ch_state_set or ch_state_init_seeded)");
+    return CH_ERR_STATE;
+  }
+  if (S->R != 1 || ws_pixels(w) != S->N) {
+    set_error("the warm-start network is sized for %d nodes, the state has %d (and must be one run)",
+              ws_pixels(w), S->N);
+    return CH_ERR_ARG;
+  }
+  if (!S->x_prev) {
+    CH_TRY(S->mem.get(&S->x_prev, (size_t)S->N * 4));
+    CH_TRY(S->mem.get(&S->guess, (size_t)S->N * 4));
+  }
+  const bool use_net = S->learn_k >= 1 && S->since_set >= 2;
+  CH_CUDA(cudaEventRecord(S->ev0, st));
+  if (use_net) CH_TRY(ws_predict(w, S->x, S->x_prev, S->guess, st));
+  {
+    ProfScope ps(st, K_STATE_IO, 0, 64.0 * S->N, 0.0);
+    CH_CUDA(cudaMemcpyAsync(S->x_prev, S->x, sizeof(double) * 4 * S->N, cudaMemcpyDeviceToDevice, st));
+  }
+  const ch_status r = use_net ? step_guess_core(S, S->guess, st, stats, false)
+                              : step_plain_core(S, st, stats, false);
+  S->learn_k += 1;
+  return r;
+}
+
+
 
 ch_status state_run_stats(const ch_state_s* S, int run, ch_step_stats* out) {
   if (run < 0 || run >= S->R) {

@@ -17,7 +17,8 @@ static const char* const kNames[K_COUNT] = {
     "orth_update_norm", "scale4",    "update_x",    "cycle_solve", "flags",     "mass",
     "cheb_first",   "cheb_step",     "vresidual",   "restrict",    "prolong",   "coarse_solve",
     "vload",        "vstore",        "spmv_M",      "state_io",    "cheb_first_coarse",
-    "cheb_step_coarse", "vresidual_coarse", "restrict_coarse", "prolong_coarse"};
+    "cheb_step_coarse", "vresidual_coarse", "restrict_coarse", "prolong_coarse", "ws_conv",
+    "ws_io",        "guess_select"};
 
 struct Acc {
   int64_t launches = 0;

@@ -1,0 +1,788 @@
+// Learned warm start: a small convolutional network on the nodal image of a 2D structured mesh
+// that predicts the next time step's state, used as the initial guess of FGMRES.
+//
+// Network (3 layers, 3x3 convolutions, "same" zero padding, stride 1):
+//   z1 = W1 * x + b1 (8 -> C),  a1 = relu(z1)
+//   z2 = W2 * a1 + b2 (C -> C), a2 = relu(z2)
+//   y  = W3 * a2 + b3 (C -> 4)
+// x holds the state s_k = (phi_p, phi_n, mu_p, mu_n) at step k, normalised per channel, and its
+// change d_k = s_k - s_{k-1} in units of its RMS over the image (8 of 16 input channels); y is the
+// correction to the linearly extrapolated next state in the same units,
+// pred = s_k + d_k + y * out_scale * rms(d_k).  Scaling by the sample's own rms(d_k) makes the
+// map independent of how fast the state is moving (early steps change it by orders of magnitude
+// more than later ones).  Activations are NHWC BF16
+// with FP32 accumulation; weights are kept as FP32 master copies (Adam) and BF16 copies for the
+// tensor cores, the latter also in tap-flipped, channel-transposed form for the backward pass
+// through the data.
+//
+// Convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16, BF16 in, FP32
+// accumulate): M = pixels (16 per warp), N = output channels (8 per tile), K = 9 taps x input
+// channels (16 per step); each lane gathers its A-fragment elements straight from the shifted
+// input (zero outside the image), the B fragments come from the weights staged in shared memory.
+// Weight gradients are reduced over pixels by FP32 FMAs in fixed-size pixel chunks and summed in
+// chunk order (deterministic).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <vector>
+
+#include "ch_internal.cuh"
+
+namespace ch {
+
+constexpr int WS_C = 32;       // hidden channels
+constexpr int WS_CIN = 16;     // input channels padded for the k16 MMA (8 used)
+constexpr int WS_COUT = 8;     // output channels padded for the n8 MMA (4 used)
+constexpr int WS_CHUNK = 1024; // pixels per weight-gradient partial
+
+struct WsParams {  // FP32 master parameters, contiguous
+  float* w1;  // [9][WS_CIN][WS_C]
+  float* b1;  // [WS_C]
+  float* w2;  // [9][WS_C][WS_C]
+  float* b2;  // [WS_C]
+  float* w3;  // [9][WS_C][WS_COUT]
+  float* b3;  // [WS_COUT]
+};
+
+constexpr int WS_N1 = 9 * WS_CIN * WS_C, WS_N2 = 9 * WS_C * WS_C, WS_N3 = 9 * WS_C * WS_COUT;
+constexpr int WS_NPARAM = WS_N1 + WS_C + WS_N2 + WS_C + WS_N3 + WS_COUT;
+
+// ---------------------------------------------------------------- BF16 helpers
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// D = A (16x16, row) * B (16x8, col) + C, BF16 inputs, FP32 accumulate
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// two consecutive BF16 channels (c, c+1) of pixel (r, q) of an NHWC image, zero outside
+__device__ __forceinline__ uint32_t load_pair(const __nv_bfloat16* X, int H, int W, int C, int r, int q,
+                                              int c) {
+  if (r < 0 || r >= H || q < 0 || q >= W) return 0u;
+  return *reinterpret_cast<const uint32_t*>(X + ((size_t)r * W + q) * C + c);
+}
+
+// ---------------------------------------------------------------- 3x3 convolution (implicit GEMM)
+// Y[p][co] = sum_{tap, ci} X[p + off(tap)][ci] Wt[tap][ci][co] (+ bias[co]), p = r W + q, then
+//   MODE 0: Yb = bf16(relu(.))                          (hidden layer forward)
+//   MODE 1: Yf = float(.)                               (output layer forward)
+//   MODE 2: Yb = bf16(. * (mask[p][co] > 0))            (backward through the data: mask = a)
+// One warp computes 16 pixels x COUT; 8 warps per block; blockIdx.y = sample.
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict__ X,
+                                                 const __nv_bfloat16* __restrict__ Wt,
+                                                 const float* __restrict__ bias, int H, int W,
+                                                 __nv_bfloat16* __restrict__ Yb, float* __restrict__ Yf,
+                                                 const __nv_bfloat16* __restrict__ mask) {
+  __shared__ __nv_bfloat16 ws[9 * CIN * COUT];
+  const int P = H * W;
+  const size_t xo = (size_t)blockIdx.y * P * CIN, yo = (size_t)blockIdx.y * P * COUT;
+  X += xo;
+  for (int i = threadIdx.x; i < 9 * CIN * COUT; i += blockDim.x) ws[i] = Wt[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int p0 = (blockIdx.x * 8 + warp) * 16;
+  if (p0 >= P) return;  // whole warp leaves together
+  const int pa = p0 + g, pb = p0 + g + 8;  // the two pixel rows this lane feeds
+  const int ra = pa / W, qa = pa % W, rb = pb / W, qb = pb % W;
+  const bool va = pa < P, vb = pb < P;
+  float acc[COUT / 8][4];
+#pragma unroll
+  for (int n = 0; n < COUT / 8; ++n)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[n][e] = 0.f;
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+    for (int c0 = 0; c0 < CIN; c0 += 16) {
+      uint32_t a[4];
+      a[0] = va ? load_pair(X, H, W, CIN, ra + dy, qa + dx, c0 + 2 * t) : 0u;
+      a[1] = vb ? load_pair(X, H, W, CIN, rb + dy, qb + dx, c0 + 2 * t) : 0u;
+      a[2] = va ? load_pair(X, H, W, CIN, ra + dy, qa + dx, c0 + 2 * t + 8) : 0u;
+      a[3] = vb ? load_pair(X, H, W, CIN, rb + dy, qb + dx, c0 + 2 * t + 8) : 0u;
+      const __nv_bfloat16* wk = ws + (tap * CIN + c0) * COUT;
+#pragma unroll
+      for (int n = 0; n < COUT / 8; ++n) {
+        const int co = n * 8 + g;
+        uint32_t b[2];
+        b[0] = pack_bf16(wk[(2 * t) * COUT + co], wk[(2 * t + 1) * COUT + co]);
+        b[1] = pack_bf16(wk[(2 * t + 8) * COUT + co], wk[(2 * t + 9) * COUT + co]);
+        mma_bf16(acc[n], a, b);
+      }
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < COUT / 8; ++n) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int p = (e < 2) ? pa : pb;
+      if (p >= P) continue;
+      const int co = n * 8 + 2 * t + (e & 1);
+      float v = acc[n][e] + (bias ? bias[co] : 0.f);
+      if (MODE == 0) {
+        Yb[yo + (size_t)p * COUT + co] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+      } else if (MODE == 1) {
+        Yf[yo + (size_t)p * COUT + co] = v;
+      } else {
+        const float m = __bfloat162float(mask[yo + (size_t)p * COUT + co]);
+        Yb[yo + (size_t)p * COUT + co] = __float2bfloat16_rn(m > 0.f ? v : 0.f);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- data movement
+// Per-sample scale of the last change: dscale[smp][c] = sqrt(mean_i (s_ic - q_ic)^2), the RMS over
+// the image of channel c of d = s - q (at least 1e-30).  One block per sample; FP64 sums reduced in
+// a fixed order (deterministic).
+template <typename T>
+__global__ void k_ws_dscale(const T* __restrict__ s, const T* __restrict__ q, int P, float* __restrict__ dscale) {
+  __shared__ double red[4][256];
+  const int smp = blockIdx.x;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (size_t i = threadIdx.x; i < (size_t)P; i += blockDim.x) {
+    const size_t o = ((size_t)smp * P + i) * 4;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double d = (double)s[o + c] - (double)q[o + c];
+      acc[c] = fma(d, d, acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) dscale[smp * 4 + threadIdx.x] = (float)fmax(sqrt(red[threadIdx.x][0] / (double)P), 1e-30);
+}
+
+// Input image of the network from the state s and the previous state q (N x 4 each, fp64 node
+// major or fp32 sample-major): channels 0-3 = (s - mean[0:4]) * inv_std[0:4] (the fields at step
+// k), channels 4-7 = ((s - q) / dscale - mean[4:8]) * inv_std[4:8] (their change over the last
+// step in units of its RMS), channels 8-15 zero.
+template <typename T>
+__global__ void k_ws_pack(const T* __restrict__ s, const T* __restrict__ q, int P,
+                          const float* __restrict__ mean, const float* __restrict__ inv_std,
+                          const float* __restrict__ dscale, __nv_bfloat16* __restrict__ x) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // pixel; blockIdx.y = sample
+  const int smp = blockIdx.y;
+  if (i >= (size_t)P) return;
+  const T* a = s + ((size_t)smp * P + i) * 4;
+  const T* b = q + ((size_t)smp * P + i) * 4;
+  __nv_bfloat16* dst = x + ((size_t)smp * P + i) * WS_CIN;
+#pragma unroll
+  for (int c = 0; c < WS_CIN; ++c) {
+    float v = 0.f;
+    if (c < 4) {
+      v = ((float)a[c] - mean[c]) * inv_std[c];
+    } else if (c < 8) {
+      const double d = ((double)a[c - 4] - (double)b[c - 4]) / (double)dscale[smp * 4 + c - 4];
+      v = ((float)d - mean[c]) * inv_std[c];
+    }
+    dst[c] = __float2bfloat16_rn(v);
+  }
+}
+
+// Training target: t = ((n - s) - (s - q)) / (dscale * out_scale), the normalised correction to
+// the linear extrapolation (fp32 inputs, sample-major B x N x 4).
+__global__ void k_ws_target(const float* __restrict__ s, const float* __restrict__ q,
+                            const float* __restrict__ n, int P, const float* __restrict__ dscale,
+                            const float* __restrict__ out_scale, float* __restrict__ t) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int smp = blockIdx.y;
+  if (i >= (size_t)P) return;
+  const size_t o = ((size_t)smp * P + i) * 4;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double a = s[o + c], e = ((double)n[o + c] - a) - (a - (double)q[o + c]);
+    t[o + c] = (float)(e / ((double)dscale[smp * 4 + c] * (double)out_scale[c]));
+  }
+}
+
+// pred = s + (s - q) + y * out_scale * dscale (fp64, N x 4): linear extrapolation plus the
+// learned correction
+__global__ void k_ws_unpack(const double* __restrict__ s, const double* __restrict__ q,
+                            const float* __restrict__ y, int P, const float* __restrict__ out_scale,
+                            const float* __restrict__ dscale, double* __restrict__ pred) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double a = s[(size_t)i * 4 + c], b = q[(size_t)i * 4 + c];
+    const double corr = (double)y[(size_t)i * WS_COUT + c] * ((double)out_scale[c] * (double)dscale[c]);
+    pred[(size_t)i * 4 + c] = a + (a - b) + corr;
+  }
+}
+
+// Loss on the 4 used output channels, L = (sum E^2 + lap * sum (G E)^2) / count with E = y - t and
+// G the graph Laplacian of the pixel grid, (G E)_p = sum over the 4-neighbours q of p inside the
+// image of (E_q - E_p).  The second term weighs errors the way the stiffness rows of the step's
+// residual do.  Three passes: E, then G E with the per-block partial losses (summed in block
+// order), then dy = 2 (E + lap G (G E)) / count as a bf16 NHWC image with 16 channels.
+__global__ void k_ws_err(const float* __restrict__ y, const float* __restrict__ tgt, size_t total,
+                         float* __restrict__ e) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) e[i * 4 + c] = y[i * WS_COUT + c] - tgt[i * 4 + c];
+  }
+}
+
+__device__ __forceinline__ float4 grid_laplacian(const float* __restrict__ e, int H, int W, size_t base, int r, int q) {
+  const float4 c = *reinterpret_cast<const float4*>(e + (base + (size_t)r * W + q) * 4);
+  float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int dr[4] = {-1, 1, 0, 0}, dq[4] = {0, 0, -1, 1};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int rr = r + dr[k], qq = q + dq[k];
+    if (rr < 0 || rr >= H || qq < 0 || qq >= W) continue;
+    const float4 n = *reinterpret_cast<const float4*>(e + (base + (size_t)rr * W + qq) * 4);
+    g.x += n.x - c.x;
+    g.y += n.y - c.y;
+    g.z += n.z - c.z;
+    g.w += n.w - c.w;
+  }
+  return g;
+}
+
+__global__ void k_ws_lap_loss(const float* __restrict__ e, int H, int W, int B, float lap,
+                              float* __restrict__ ge, float* __restrict__ loss_part) {
+  __shared__ float sm[256];
+  const size_t P = (size_t)H * W, total = (size_t)B * P;
+  float acc = 0.f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t smp = i / P, p = i % P;
+    const float4 c = *reinterpret_cast<const float4*>(e + i * 4);
+    acc = fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, fmaf(c.w, c.w, acc))));
+    if (lap != 0.f) {
+      const float4 g = grid_laplacian(e, H, W, smp * P, (int)(p / W), (int)(p % W));
+      *reinterpret_cast<float4*>(ge + i * 4) = g;
+      acc = fmaf(lap, g.x * g.x + g.y * g.y + g.z * g.z + g.w * g.w, acc);
+    }
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = sm[0];
+}
+
+__global__ void k_ws_dy(const float* __restrict__ e, const float* __restrict__ ge, int H, int W, int B,
+                        float lap, __nv_bfloat16* __restrict__ dy) {
+  const size_t P = (size_t)H * W, total = (size_t)B * P;
+  const float scale = 2.f / (float)(total * 4);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t smp = i / P, p = i % P;
+    float4 v = *reinterpret_cast<const float4*>(e + i * 4);
+    if (lap != 0.f) {
+      const float4 g = grid_laplacian(ge, H, W, smp * P, (int)(p / W), (int)(p % W));
+      v.x = fmaf(lap, g.x, v.x);
+      v.y = fmaf(lap, g.y, v.y);
+      v.z = fmaf(lap, g.z, v.z);
+      v.w = fmaf(lap, g.w, v.w);
+    }
+    const float vals[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int c = 0; c < 16; ++c) dy[i * 16 + c] = __float2bfloat16_rn(c < 4 ? scale * vals[c] : 0.f);
+  }
+}
+
+// ---------------------------------------------------------------- weight gradients
+// dW[tap][ci][co] = sum_p X[p + off(tap)][ci] dY[p][co], db[co] = sum_p dY[p][co], over a chunk
+// of WS_CHUNK pixels of one sample per block (partials[(sample * nchunk + chunk)][...]).
+// One thread per (tap, ci) pair keeps COUT accumulators; dY of 64 pixels is staged in shared memory.
+template <int CIN, int COUTG, int COUTW>  // COUTG: channels stored in dY; COUTW: channels of dW
+__global__ void __launch_bounds__(256) k_ws_wgrad(const __nv_bfloat16* __restrict__ X,
+                                                  const __nv_bfloat16* __restrict__ dY, int H, int W,
+                                                  int nchunk, float* __restrict__ partials) {
+  constexpr int NP = 9 * CIN;  // (tap, ci) pairs
+  constexpr int TILE = 64;
+  __shared__ float dys[TILE][COUTW];
+  const int P = H * W;
+  const int smp = blockIdx.y, chunk = blockIdx.x;
+  const __nv_bfloat16* Xs = X + (size_t)smp * P * CIN;
+  const __nv_bfloat16* Ds = dY + (size_t)smp * P * COUTG;
+  float* out = partials + ((size_t)smp * nchunk + chunk) * (NP * COUTW + COUTW);
+  for (int pair0 = 0; pair0 < NP; pair0 += blockDim.x) {
+    const int pair = pair0 + threadIdx.x;
+    const int tap = pair / CIN, ci = pair % CIN;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    float acc[COUTW];
+#pragma unroll
+    for (int c = 0; c < COUTW; ++c) acc[c] = 0.f;
+    float bacc = 0.f;  // bias gradient (thread 0 of the first pass only)
+    const int pbeg = chunk * WS_CHUNK, pend = min(P, pbeg + WS_CHUNK);
+    for (int pt = pbeg; pt < pend; pt += TILE) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < TILE * COUTW; i += blockDim.x) {
+        const int pp = pt + i / COUTW, c = i % COUTW;
+        dys[i / COUTW][c] = pp < pend ? __bfloat162float(Ds[(size_t)pp * COUTG + c]) : 0.f;
+      }
+      __syncthreads();
+      if (pair < NP) {
+        for (int k = 0; k < TILE && pt + k < pend; ++k) {
+          const int p = pt + k, r = p / W + dy, q = p % W + dx;
+          const float xv = (r >= 0 && r < H && q >= 0 && q < W)
+                               ? __bfloat162float(Xs[((size_t)r * W + q) * CIN + ci]) : 0.f;
+#pragma unroll
+          for (int c = 0; c < COUTW; ++c) acc[c] = fmaf(xv, dys[k][c], acc[c]);
+        }
+      }
+      if (pair0 == 0 && threadIdx.x < COUTW)
+        for (int k = 0; k < TILE && pt + k < pend; ++k) bacc += dys[k][threadIdx.x];
+    }
+    if (pair < NP)
+#pragma unroll
+      for (int c = 0; c < COUTW; ++c) out[pair * COUTW + c] = acc[c];
+    if (pair0 == 0 && threadIdx.x < COUTW) out[NP * COUTW + threadIdx.x] = bacc;
+  }
+}
+
+// sum of nparts partial gradient vectors of length len, in part order
+__global__ void k_ws_reduce(const float* __restrict__ partials, int nparts, int len, float* __restrict__ g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  float s = 0.f;
+  for (int k = 0; k < nparts; ++k) s += partials[(size_t)k * len + i];
+  g[i] = s;
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 master parameters
+__global__ void k_ws_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                          float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
+                          float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 copies of the weights: forward [tap][ci][co] and, for the backward pass through the data,
+// flipped [8 - tap][co][ci] with the channel counts of that pass (co padded to CPAD rows).
+__global__ void k_ws_bf16(const float* __restrict__ w, int cin, int cout, int cout_used, int cpad,
+                          __nv_bfloat16* __restrict__ fwd, __nv_bfloat16* __restrict__ flip) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 9 * cin * cout) {
+    const int co = i % cout;
+    fwd[i] = __float2bfloat16_rn(co < cout_used ? w[i] : 0.f);
+  }
+  if (flip && i < 9 * cpad * cin) {  // flip[tap'][c][ci], c < cpad
+    const int ci = i % cin, c = (i / cin) % cpad, tp = i / (cin * cpad);
+    const float val = c < cout_used ? w[((8 - tp) * cin + ci) * cout + c] : 0.f;
+    flip[i] = __float2bfloat16_rn(val);
+  }
+}
+
+}  // namespace ch
+
+// ---------------------------------------------------------------- handle
+struct ch_ws_s {
+  int H = 0, W = 0, P = 0, Bmax = 0;
+  float* params = nullptr;  // FP32 master, WS_NPARAM
+  float* grads = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  int adam_t = 0;
+  __nv_bfloat16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr;     // forward copies
+  __nv_bfloat16 *w2f = nullptr, *w3f = nullptr;                    // flipped copies (backward)
+  float* norm = nullptr;  // mean[8], inv_std[8], out_scale[4]
+  float* dscale = nullptr;  // Bmax x 4: RMS of the last change per sample and channel
+  float* t = nullptr;       // Bmax x P x 4 training targets
+  float* e = nullptr;       // Bmax x P x 4 output errors y - t
+  float* ge = nullptr;      // Bmax x P x 4 their grid Laplacian
+  double* rex = nullptr;    // Bmax x P x 4 residuals of the extrapolation (residual loss)
+  double* rres = nullptr;   // Bmax x P x 4 residuals of the prediction
+  double *tmp1 = nullptr, *tmp2 = nullptr;  // P x 4
+  double* nrm = nullptr;    // Bmax x 8 squared residual norms per channel
+  double *zex = nullptr, *zr = nullptr;  // preconditioned residuals: P x 4, Bmax x P x 4
+  __nv_bfloat16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr;      // Bmax x P x {16, 32, 32}
+  __nv_bfloat16 *dy = nullptr, *dz2 = nullptr, *dz1 = nullptr;    // Bmax x P x {16, 32, 32}
+  float* y = nullptr;                                              // Bmax x P x 8
+  float* part = nullptr;                                           // weight-gradient partials
+  float* loss_part = nullptr;
+  bool fresh = false;  // bf16 copies up to date
+  ch::Alloc mem;
+};
+
+namespace ch {
+
+static WsParams ws_views(float* base) {
+  WsParams v;
+  v.w1 = base;
+  v.b1 = v.w1 + WS_N1;
+  v.w2 = v.b1 + WS_C;
+  v.b2 = v.w2 + WS_N2;
+  v.w3 = v.b2 + WS_C;
+  v.b3 = v.w3 + WS_N3;
+  return v;
+}
+
+static ch_status ws_refresh(ch_ws_s* w, cudaStream_t st) {
+  const WsParams p = ws_views(w->params);
+  k_ws_bf16<<<blocks_for(9 * WS_CIN * WS_C), TPB, 0, st>>>(p.w1, WS_CIN, WS_C, WS_C, 0, w->w1, nullptr);
+  k_ws_bf16<<<blocks_for(9 * WS_C * WS_C), TPB, 0, st>>>(p.w2, WS_C, WS_C, WS_C, WS_C, w->w2, w->w2f);
+  k_ws_bf16<<<blocks_for(9 * 16 * WS_C), TPB, 0, st>>>(p.w3, WS_C, WS_COUT, 4, 16, w->w3, w->w3f);
+  CH_LAUNCHED();
+  w->fresh = true;
+  return CH_OK;
+}
+
+// forward pass of B samples whose inputs are already packed in w->x0
+static ch_status ws_forward_packed(ch_ws_s* w, int B, cudaStream_t st) {
+  if (!w->fresh) CH_TRY(ws_refresh(w, st));
+  const WsParams p = ws_views(w->params);
+  const dim3 grid(blocks_for(w->P, 128), B);
+  {
+    ProfScope ps(st, K_WS_CONV, 1, (double)B * w->P * (16 + 32) * 2, (double)B * w->P * 9 * 16 * 32);
+    k_conv3x3<WS_CIN, WS_C, 0><<<grid, 256, 0, st>>>(w->x0, w->w1, p.b1, w->H, w->W, w->a1, nullptr, nullptr);
+  }
+  {
+    ProfScope ps(st, K_WS_CONV, 1, (double)B * w->P * (32 + 32) * 2, (double)B * w->P * 9 * 32 * 32);
+    k_conv3x3<WS_C, WS_C, 0><<<grid, 256, 0, st>>>(w->a1, w->w2, p.b2, w->H, w->W, w->a2, nullptr, nullptr);
+  }
+  {
+    ProfScope ps(st, K_WS_CONV, 1, (double)B * w->P * (32 * 2 + 8 * 4), (double)B * w->P * 9 * 32 * 8);
+    k_conv3x3<WS_C, WS_COUT, 1><<<grid, 256, 0, st>>>(w->a2, w->w3, p.b3, w->H, w->W, nullptr, w->y, nullptr);
+  }
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+ch_status ws_create(int H, int W, int Bmax, ch_ws_s** out) {
+  ch_ws_s* w = new ch_ws_s();
+  w->H = H;
+  w->W = W;
+  w->P = H * W;
+  w->Bmax = Bmax;
+  const size_t P = (size_t)w->P * Bmax;
+  const int nchunk = (w->P + WS_CHUNK - 1) / WS_CHUNK;
+  ch_status r = CH_OK;
+  if (r == CH_OK) r = w->mem.get(&w->params, WS_NPARAM);
+  if (r == CH_OK) r = w->mem.get(&w->grads, WS_NPARAM);
+  if (r == CH_OK) r = w->mem.get(&w->adam_m, WS_NPARAM);
+  if (r == CH_OK) r = w->mem.get(&w->adam_v, WS_NPARAM);
+  if (r == CH_OK) r = w->mem.get(&w->w1, 9 * WS_CIN * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->w2, 9 * WS_C * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->w3, 9 * WS_C * WS_COUT);
+  if (r == CH_OK) r = w->mem.get(&w->w2f, 9 * WS_C * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->w3f, 9 * 16 * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->norm, 20);
+  if (r == CH_OK) r = w->mem.get(&w->dscale, (size_t)Bmax * 4);
+  if (r == CH_OK) r = w->mem.get(&w->t, P * 4);
+  if (r == CH_OK) r = w->mem.get(&w->e, P * 4);
+  if (r == CH_OK) r = w->mem.get(&w->ge, P * 4);
+  if (r == CH_OK) r = w->mem.get(&w->x0, P * WS_CIN);
+  if (r == CH_OK) r = w->mem.get(&w->a1, P * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->a2, P * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->dy, P * 16);
+  if (r == CH_OK) r = w->mem.get(&w->dz2, P * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->dz1, P * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->y, P * WS_COUT);
+  if (r == CH_OK) r = w->mem.get(&w->part, (size_t)Bmax * nchunk * (9 * WS_C * WS_C + WS_C));
+  if (r == CH_OK) r = w->mem.get(&w->loss_part, 1024);
+  if (r == CH_OK) {
+    cudaMemset(w->params, 0, sizeof(float) * WS_NPARAM);
+    cudaMemset(w->adam_m, 0, sizeof(float) * WS_NPARAM);
+    cudaMemset(w->adam_v, 0, sizeof(float) * WS_NPARAM);
+    const float nrm[20] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+    if (cudaMemcpy(w->norm, nrm, sizeof(nrm), cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error("warm-start initialisation failed");
+      r = CH_ERR_CUDA;
+    }
+  }
+  if (r != CH_OK) {
+    delete w;
+    return r;
+  }
+  *out = w;
+  return CH_OK;
+}
+
+void ws_destroy(ch_ws_s* w) { delete w; }
+
+ch_status ws_set_params(ch_ws_s* w, const float* host, cudaStream_t st) {
+  CH_CUDA(cudaMemcpyAsync(w->params, host, sizeof(float) * WS_NPARAM, cudaMemcpyHostToDevice, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  w->fresh = false;
+  w->adam_t = 0;
+  CH_CUDA(cudaMemsetAsync(w->adam_m, 0, sizeof(float) * WS_NPARAM, st));
+  CH_CUDA(cudaMemsetAsync(w->adam_v, 0, sizeof(float) * WS_NPARAM, st));
+  return CH_OK;
+}
+
+ch_status ws_get_params(const ch_ws_s* w, float* host, float* host_grads, cudaStream_t st) {
+  if (host) CH_CUDA(cudaMemcpyAsync(host, w->params, sizeof(float) * WS_NPARAM, cudaMemcpyDeviceToHost, st));
+  if (host_grads)
+    CH_CUDA(cudaMemcpyAsync(host_grads, w->grads, sizeof(float) * WS_NPARAM, cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  return CH_OK;
+}
+
+ch_status ws_set_norm(ch_ws_s* w, const float* host20, cudaStream_t st) {
+  CH_CUDA(cudaMemcpyAsync(w->norm, host20, sizeof(float) * 20, cudaMemcpyHostToDevice, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  return CH_OK;
+}
+
+// Backward pass from dy (already in w->dy) and, if lr > 0, an Adam step.
+static ch_status ws_backward_update(ch_ws_s* w, int B, float lr, cudaStream_t st) {
+  const int P = w->P;
+  // backward through the data: dz2 = (W3 flipped * dy) . [a2 > 0];  dz1 = (W2 flipped * dz2) . [a1 > 0]
+  const dim3 grid(blocks_for(P, 128), B);
+  k_conv3x3<16, WS_C, 2><<<grid, 256, 0, st>>>(w->dy, w->w3f, nullptr, w->H, w->W, w->dz2, nullptr, w->a2);
+  k_conv3x3<WS_C, WS_C, 2><<<grid, 256, 0, st>>>(w->dz2, w->w2f, nullptr, w->H, w->W, w->dz1, nullptr, w->a1);
+  CH_LAUNCHED();
+  // weight gradients, per sample and pixel chunk, then summed in order
+  const int nchunk = (P + WS_CHUNK - 1) / WS_CHUNK;
+  WsParams g = ws_views(w->grads);
+  const dim3 wg(nchunk, B);
+  k_ws_wgrad<WS_C, 16, WS_COUT><<<wg, 256, 0, st>>>(w->a2, w->dy, w->H, w->W, nchunk, w->part);
+  k_ws_reduce<<<blocks_for(WS_N3 + WS_COUT), TPB, 0, st>>>(w->part, B * nchunk, WS_N3 + WS_COUT, g.w3);
+  k_ws_wgrad<WS_C, WS_C, WS_C><<<wg, 256, 0, st>>>(w->a1, w->dz2, w->H, w->W, nchunk, w->part);
+  k_ws_reduce<<<blocks_for(WS_N2 + WS_C), TPB, 0, st>>>(w->part, B * nchunk, WS_N2 + WS_C, g.w2);
+  k_ws_wgrad<WS_CIN, WS_C, WS_C><<<wg, 256, 0, st>>>(w->x0, w->dz1, w->H, w->W, nchunk, w->part);
+  k_ws_reduce<<<blocks_for(WS_N1 + WS_C), TPB, 0, st>>>(w->part, B * nchunk, WS_N1 + WS_C, g.w1);
+  CH_LAUNCHED();
+  if (lr > 0.f) {
+    w->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)w->adam_t), c2 = 1.f - powf(b2, (float)w->adam_t);
+    k_ws_adam<<<blocks_for(WS_NPARAM), TPB, 0, st>>>(w->params, w->grads, w->adam_m, w->adam_v, WS_NPARAM,
+                                                      lr, b1, b2, 1e-8f, c1, c2);
+    CH_LAUNCHED();
+    w->fresh = false;
+  }
+  return CH_OK;
+}
+
+// inference: pred = s + d + net(s, d / dscale) * out_scale * dscale for one state s, its
+// predecessor q and d = s - q
+ch_status ws_predict(ch_ws_s* w, const double* state, const double* prev, double* pred, cudaStream_t st) {
+  {
+    ProfScope ps(st, K_WS_IO, 0, w->P * (32.0 + 32.0 + 32.0 + 32.0), 0.0);
+    k_ws_dscale<double><<<1, 256, 0, st>>>(state, prev, w->P, w->dscale);
+    k_ws_pack<double><<<dim3(blocks_for(w->P), 1), TPB, 0, st>>>(state, prev, w->P, w->norm, w->norm + 8,
+                                                                  w->dscale, w->x0);
+  }
+  CH_LAUNCHED();
+  CH_TRY(ws_forward_packed(w, 1, st));
+  {
+    ProfScope ps(st, K_WS_IO, 0, w->P * (32.0 + 32.0 + 32.0 + 32.0), 0.0);
+    k_ws_unpack<<<blocks_for(w->P), TPB, 0, st>>>(state, prev, w->y, w->P, w->norm + 16, w->dscale, pred);
+  }
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+// one training step on B samples (fp32, B x N x 4 each): states x, their predecessors q and
+// successors n.  Computes the loss (with the grid-Laplacian term weighted by lap) and the
+// gradients; if lr > 0 also takes an Adam step.
+ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float* n, int B, float lap,
+                        float lr, float* loss, cudaStream_t st) {
+  if (B < 1 || B > w->Bmax) {
+    set_error("batch of %d samples outside [1, %d]", B, w->Bmax);
+    return CH_ERR_ARG;
+  }
+  if (!(lap >= 0.f) || !std::isfinite(lap)) {
+    set_error("Laplacian loss weight %g must be finite and >= 0", (double)lap);
+    return CH_ERR_ARG;
+  }
+  const int P = w->P;
+  k_ws_dscale<float><<<B, 256, 0, st>>>(x, q, P, w->dscale);
+  k_ws_pack<float><<<dim3(blocks_for(P), B), TPB, 0, st>>>(x, q, P, w->norm, w->norm + 8, w->dscale, w->x0);
+  k_ws_target<<<dim3(blocks_for(P), B), TPB, 0, st>>>(x, q, n, P, w->dscale, w->norm + 16, w->t);
+  CH_LAUNCHED();
+  CH_TRY(ws_forward_packed(w, B, st));
+  const int lb = 304;
+  k_ws_err<<<lb, 256, 0, st>>>(w->y, w->t, (size_t)B * P, w->e);
+  k_ws_lap_loss<<<lb, 256, 0, st>>>(w->e, w->H, w->W, B, lap, w->ge, w->loss_part);
+  k_ws_dy<<<lb, 256, 0, st>>>(w->e, w->ge, w->H, w->W, B, lap, w->dy);
+  CH_TRY(ws_backward_update(w, B, lr, st));
+  if (loss) {
+    float parts[lb];
+    CH_CUDA(cudaMemcpyAsync(parts, w->loss_part, sizeof(parts), cudaMemcpyDeviceToHost, st));
+    CH_CUDA(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (int i = 0; i < lb; ++i) s += parts[i];
+    *loss = (float)(s / ((double)B * P * 4));
+  }
+  return CH_OK;
+}
+
+// ---------------------------------------------------------------- residual-loss training
+// The correction c = y * out_scale * dscale (fp64, N x 4) of one sample, or the extrapolation
+// 2 s - q (mode 0).
+__global__ void k_ws_guess_part(int P, int mode, const double* __restrict__ s, const double* __restrict__ q,
+                                const float* __restrict__ y, const float* __restrict__ out_scale,
+                                const float* __restrict__ dscale, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const size_t o = (size_t)i * 4 + c;
+    out[o] = mode == 0 ? 2.0 * s[o] - q[o]
+                       : (double)y[(size_t)i * WS_COUT + c] * ((double)out_scale[c] * (double)dscale[c]);
+  }
+}
+
+// out = a - b (N x 4)
+__global__ void k_ws_sub(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] - b[i];
+}
+
+// nrm[0..3] = per channel sum of rex * zex, nrm[4..7] = per channel sum of r * z, where z = P^-1 r
+// (or z = r for the plain norm); one block, fixed order
+__global__ void k_ws_resnorm(int P, const double* __restrict__ rex, const double* __restrict__ zex,
+                             const double* __restrict__ r, const double* __restrict__ z, double* __restrict__ nrm) {
+  __shared__ double red[8][256];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const size_t o = (size_t)i * 4 + c;
+      acc[c] = fma(rex[o], zex[o], acc[c]);
+      acc[4 + c] = fma(r[o], z[o], acc[4 + c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) red[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) nrm[threadIdx.x] = red[threadIdx.x][0];
+}
+
+// dy of one sample from g = A z: L = sum_species <r, z>_sp / <rex, zex>_sp / (2B) with z = P^-1 r
+// (P^-1 symmetric, or the identity), r = rex - A c, so dL/dc = -2 A z / <rex, zex>_sp / (2B) and
+// dL/dy_c = dL/dc_c * out_scale_c * dscale_c.
+// Channel c belongs to species c % 2 (channels phi_p, phi_n, mu_p, mu_n).
+__global__ void k_ws_res_dy(int P, int B, const double* __restrict__ g, const double* __restrict__ nrm,
+                            const float* __restrict__ out_scale, const float* __restrict__ dscale,
+                            __nv_bfloat16* __restrict__ dy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  double wsp[2];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    const double den = nrm[sp] + nrm[sp + 2];
+    wsp[sp] = den > 0.0 ? 1.0 / (den * (double)B) : 0.0;
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    float v = 0.f;
+    if (c < 4)
+      v = (float)(-g[(size_t)i * 4 + c] * wsp[c % 2] * ((double)out_scale[c] * (double)dscale[c]));
+    dy[(size_t)i * 16 + c] = __float2bfloat16_rn(v);
+  }
+}
+
+ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc, const double* x,
+                            const double* q, int B, float lr, float* loss, cudaStream_t st) {
+  if (B < 1 || B > w->Bmax) {
+    set_error("batch of %d samples outside [1, %d]", B, w->Bmax);
+    return CH_ERR_ARG;
+  }
+  const ch_params& mp = sys->mesh->p;
+  if (mp.dim != 2 || sys->mesh->runs.size() != 1 || mp.nx + 1 != w->W || mp.ny + 1 != w->H) {
+    set_error("the system must be a single-run 2D mesh of %d x %d nodes", w->W, w->H);
+    return CH_ERR_ARG;
+  }
+  if (pc != nullptr && pc->sys != sys) {
+    set_error("the preconditioner was built for another system");
+    return CH_ERR_ARG;
+  }
+  const int P = w->P;
+  if (pc != nullptr && !w->zex) {
+    CH_TRY(w->mem.get(&w->zex, (size_t)P * 4));
+    CH_TRY(w->mem.get(&w->zr, (size_t)w->Bmax * P * 4));
+  }
+  if (!w->rex) {
+    CH_TRY(w->mem.get(&w->rex, (size_t)w->Bmax * P * 4));
+    CH_TRY(w->mem.get(&w->rres, (size_t)w->Bmax * P * 4));
+    CH_TRY(w->mem.get(&w->tmp1, (size_t)P * 4));
+    CH_TRY(w->mem.get(&w->tmp2, (size_t)P * 4));
+    CH_TRY(w->mem.get(&w->nrm, (size_t)w->Bmax * 8));
+  }
+  k_ws_dscale<double><<<B, 256, 0, st>>>(x, q, P, w->dscale);
+  k_ws_pack<double><<<dim3(blocks_for(P), B), TPB, 0, st>>>(x, q, P, w->norm, w->norm + 8, w->dscale, w->x0);
+  CH_LAUNCHED();
+  CH_TRY(ws_forward_packed(w, B, st));
+  const int nb = blocks_for(P), nb4 = blocks_for(4 * P);
+  for (int b = 0; b < B; ++b) {
+    const double* xs = x + (size_t)b * P * 4;
+    const double* qs = q + (size_t)b * P * 4;
+    double* rex = w->rex + (size_t)b * P * 4;
+    double* r = w->rres + (size_t)b * P * 4;
+    // rex = b(s) - A (2 s - q)
+    CH_TRY(rhs_strided(sys, xs, xs + 1, 4, w->tmp1, st));
+    k_ws_guess_part<<<nb, TPB, 0, st>>>(P, 0, xs, qs, nullptr, nullptr, nullptr, w->tmp2);
+    CH_LAUNCHED();
+    CH_TRY(apply_A(sys, w->tmp2, rex, st));
+    k_ws_sub<<<nb4, TPB, 0, st>>>(4 * P, w->tmp1, rex, rex);
+    // r = rex - A c
+    k_ws_guess_part<<<nb, TPB, 0, st>>>(P, 1, nullptr, nullptr, w->y + (size_t)b * P * WS_COUT, w->norm + 16,
+                                        w->dscale + 4 * b, w->tmp2);
+    CH_LAUNCHED();
+    CH_TRY(apply_A(sys, w->tmp2, w->tmp1, st));
+    k_ws_sub<<<nb4, TPB, 0, st>>>(4 * P, rex, w->tmp1, r);
+    // z = P^-1 r, zex = P^-1 rex (Algorithm 1), or the residuals themselves
+    const double* zex = rex;
+    const double* z = r;
+    if (pc != nullptr) {
+      CH_TRY(precond_apply(pc, rex, w->zex, st));
+      CH_TRY(precond_apply(pc, r, w->zr + (size_t)b * P * 4, st));
+      zex = w->zex;
+      z = w->zr + (size_t)b * P * 4;
+    }
+    k_ws_resnorm<<<1, 256, 0, st>>>(P, rex, zex, r, z, w->nrm + 8 * b);
+    // g = A z (A is symmetric) -> dy of this sample
+    CH_TRY(apply_A(sys, z, w->tmp1, st));
+    k_ws_res_dy<<<nb, TPB, 0, st>>>(P, B, w->tmp1, w->nrm + 8 * b, w->norm + 16, w->dscale + 4 * b,
+                                    w->dy + (size_t)b * P * 16);
+    CH_LAUNCHED();
+  }
+  CH_TRY(ws_backward_update(w, B, lr, st));
+  if (loss) {
+    std::vector<double> h((size_t)B * 8);
+    CH_CUDA(cudaMemcpyAsync(h.data(), w->nrm, sizeof(double) * 8 * B, cudaMemcpyDeviceToHost, st));
+    CH_CUDA(cudaStreamSynchronize(st));
+    double L = 0.0;
+    for (int b = 0; b < B; ++b)
+      for (int sp = 0; sp < 2; ++sp) {
+        const double den = h[8 * b + sp] + h[8 * b + sp + 2];
+        if (den > 0.0) L += (h[8 * b + 4 + sp] + h[8 * b + 6 + sp]) / den;
+      }
+    *loss = (float)(L / (2.0 * B));
+  }
+  return CH_OK;
+}
+
+int ws_nparam() { return WS_NPARAM; }
+
+int ws_pixels(const ch_ws_s* w) { return w->P; }
+
+}  // namespace ch

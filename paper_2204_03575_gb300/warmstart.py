@@ -1,0 +1,173 @@
+"""Learned warm start: training data from the solver, training and use of the network.
+
+The network (``ch.WarmStartNet``, kernels in ``csrc/warmstart.cu``) predicts the state at step k+1
+from the states at steps k and k-1 on the nodal image of a 2D structured mesh, as a learned
+correction to the linear extrapolation 2 s_k - s_{k-1}; ``ch_step_guess`` takes the prediction as
+FGMRES's initial iterate wherever its true FP64 residual beats that of the previous state, so the
+FP64 residual remains the judge and the previous step the fallback.
+
+    data = generate_pairs(nx, ny, seeds=range(20), steps=100, dtype=torch.float64)  # plain solver
+    net = ch.WarmStartNet(ny + 1, nx + 1, 8)
+    net, info = train_residual(data, net, make_system(nx, ny))   # library kernels, Adam
+    stats = run_steps(nx, ny, seed, 20, net=net)                  # ch_step_learned per step
+
+PyTorch holds the tensors (state stacks, shuffling indices) and computes the normalisation
+statistics once before training; every layer, loss, gradient and optimiser update, and every
+prediction during stepping, runs in the library.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import ch, inputs
+
+
+def seed_bases(seed: int, lo: float = 0.20, hi: float = 0.45):
+    """Initial bases (phi_p0, phi_nfa0) of a training run, uniform in [lo, hi) from SplitMix64."""
+    u = (inputs.splitmix64(np.uint64(seed) ^ (np.uint64(0x5EED) << np.uint64(40)) ^ np.arange(2, dtype=np.uint64))
+         >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return lo + (hi - lo) * u[0], lo + (hi - lo) * u[1]
+
+
+def make_state(nx: int, ny: int, precision: int = 0, **kw):
+    p = ch.Params(nx=nx, ny=ny, precision=precision, **kw)
+    system = ch.System(ch.Mesh(p), p)
+    return ch.State(system, ch.Precond(system))
+
+
+def make_system(nx: int, ny: int, **kw):
+    """The time-step system of the nx x ny mesh (for the residual loss)."""
+    p = ch.Params(nx=nx, ny=ny, **kw)
+    return ch.System(ch.Mesh(p), p)
+
+
+def generate_pairs(nx: int, ny: int, seeds, steps: int, precision: int = 0, burn_in: int = 1,
+                   dtype=torch.float32):
+    """(Q, X, Y): CUDA tensors (S, N, 4) of `dtype` holding consecutive states s_{k-1}, s_k,
+    s_{k+1} along the solver's own trajectories, `steps` triples per seed.  The first triple starts
+    `burn_in` steps after the initial state (whose chemical potentials the first step sets up)."""
+    qs, xs, ys = [], [], []
+    state = make_state(nx, ny, precision)
+    for seed in seeds:
+        b0, b1 = seed_bases(seed)
+        state.init_seeded(b0, b1, 0.01, seed=int(seed))
+        for _ in range(burn_in):
+            state.step()
+        prev = state.state4()
+        state.step()
+        cur = state.state4()
+        for _ in range(steps):
+            state.step()
+            nxt = state.state4()
+            qs.append(prev.to(dtype))
+            xs.append(cur.to(dtype))
+            ys.append(nxt.to(dtype))
+            prev, cur = cur, nxt
+    return torch.stack(qs), torch.stack(xs), torch.stack(ys)
+
+
+def normalisation(Q: torch.Tensor, X: torch.Tensor, Y: torch.Tensor):
+    """Input mean and 1/std per channel (the fields; the change channels are already in units of
+    their RMS and keep mean 0, scale 1) and the output scale: the std of the correction to the
+    linear extrapolation in those units."""
+    x = X.reshape(-1, 4).double()
+    d = X.double() - Q.double()
+    r = d.pow(2).mean(1, keepdim=True).sqrt().clamp_min(1e-30)          # (S, 1, 4)
+    e = ((Y.double() - X.double()) - d) / r
+    mean = torch.cat([x.mean(0), torch.zeros(4, dtype=torch.float64, device=x.device)])
+    inv_std = torch.cat([1.0 / x.std(0).clamp_min(1e-30), torch.ones(4, dtype=torch.float64, device=x.device)])
+    out = e.reshape(-1, 4).std(0).clamp_min(1e-30)
+    return mean.cpu().numpy(), inv_std.cpu().numpy(), out.cpu().numpy()
+
+
+def init_params(nparams: int, seed: int = 0):
+    """He-uniform initial weights (zero biases) in the library's parameter layout."""
+    rng = np.random.default_rng(seed)
+    layers = [(9 * 16 * 32, 9 * 8, 32), (9 * 32 * 32, 9 * 32, 32), (9 * 32 * 8, 9 * 32, 8)]
+    out = []
+    for i, (n, fan_in, nb) in enumerate(layers):
+        lim = np.sqrt(6.0 / fan_in) * (0.1 if i == 2 else 1.0)  # start close to pure extrapolation
+        out.append(rng.uniform(-lim, lim, n))
+        out.append(np.zeros(nb))
+    theta = np.concatenate(out).astype(np.float32)
+    assert theta.size == nparams
+    return theta
+
+
+def train(data, net, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: int = 0,
+          use_fields: bool = True, lap: float = 0.0):
+    """Fit `net` (a ch.WarmStartNet sized for the mesh) to the correction of the linear
+    extrapolation on `data` = (Q, X, Y) from generate_pairs.  With use_fields=False the field
+    channels are switched off (scale 0) and the network sees only the change; `lap` weighs the
+    grid-Laplacian term of the loss.  Returns (net, info)."""
+    Q, X, Y = data
+    S, N = X.shape[0], X.shape[1]
+    mean, inv_std, out_scale = normalisation(Q, X, Y)
+    if not use_fields:
+        mean[:4], inv_std[:4] = 0.0, 0.0
+    net.set_norm(mean, inv_std, out_scale)
+    net.set_params(init_params(net.nparams, seed))
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    losses = []
+    for ep in range(epochs):
+        perm = torch.randperm(S, generator=g)
+        lr_ep = lr * (0.5 ** (ep // max(1, epochs // 3)))
+        tot, nb = 0.0, 0
+        for i in range(0, S - batch + 1, batch):
+            idx = perm[i:i + batch].to(X.device)
+            tot += net.train_step(X[idx].contiguous(), Q[idx].contiguous(), Y[idx].contiguous(), lr_ep, lap=lap)
+            nb += 1
+        losses.append(tot / max(nb, 1))
+    return net, {"loss_per_epoch": losses, "mean": mean.tolist(), "inv_std": inv_std.tolist(),
+                 "out_scale": out_scale.tolist(), "pairs": S, "nodes": N}
+
+
+def train_residual(data, net, system, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: int = 0,
+                   use_fields: bool = True, precond=None):
+    """Fit `net` against the residual of the time step (ch_ws_train_residual) on fp64 `data` =
+    (Q, X, Y) from generate_pairs(..., dtype=torch.float64); Y only sets the normalisation.
+    With `precond` (a ch.Precond of `system`) the residual is measured in its norm.  The per-epoch
+    loss is the mean |r|^2 / |r_extrapolation|^2: below 1 beats extrapolation."""
+    Q, X, Y = data
+    S, N = X.shape[0], X.shape[1]
+    mean, inv_std, out_scale = normalisation(Q, X, Y)
+    if not use_fields:
+        mean[:4], inv_std[:4] = 0.0, 0.0
+    net.set_norm(mean, inv_std, out_scale)
+    net.set_params(init_params(net.nparams, seed))
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    losses = []
+    for ep in range(epochs):
+        perm = torch.randperm(S, generator=g)
+        lr_ep = lr * (0.5 ** (ep // max(1, epochs // 3)))
+        tot, nb = 0.0, 0
+        for i in range(0, S - batch + 1, batch):
+            idx = perm[i:i + batch].to(X.device)
+            tot += net.train_residual(system, X[idx].contiguous(), Q[idx].contiguous(), lr_ep, precond=precond)
+            nb += 1
+        losses.append(tot / max(nb, 1))
+    return net, {"loss_per_epoch": losses, "mean": mean.tolist(), "inv_std": inv_std.tolist(),
+                 "out_scale": out_scale.tolist(), "pairs": S, "nodes": N}
+
+
+def zero_net(nx: int, ny: int):
+    """A network whose correction is zero: its prediction is the linear extrapolation 2 s_k - s_{k-1}."""
+    net = ch.WarmStartNet(ny + 1, nx + 1, max_batch=1)
+    net.set_params(np.zeros(net.nparams, np.float32))
+    return net
+
+
+def run_steps(nx: int, ny: int, seed: int, steps: int, net=None, extrapolate: bool = False,
+              precision: int = 0, warm_up: int = 0):
+    """Advance a seeded run; return per-step stats.  With `net`, every step is ch_step_learned
+    (the network's prediction where it beats the previous state, from the third step on); with
+    `extrapolate`, the same with the zero network, i.e. the guess 2 s_k - s_{k-1}."""
+    state = make_state(nx, ny, precision)
+    b0, b1 = seed_bases(seed)
+    state.init_seeded(b0, b1, 0.01, seed=int(seed))
+    for _ in range(warm_up):
+        state.step()
+    if extrapolate and net is None:
+        net = zero_net(nx, ny)
+    return [state.step_learned(net) if net is not None else state.step() for _ in range(steps)]

@@ -1,0 +1,197 @@
+"""Pins of the warm-start network oracle: its convolution against scipy's 2D correlation, its
+gradients against central finite differences of its own float64 loss, and its bfloat16 rounding
+against exactly representable values and the round-to-nearest-even rule."""
+import numpy as np
+import pytest
+import scipy.signal
+
+from oracle import warmstart_oracle as wo
+
+
+def rand_theta(rng, scale=0.3):
+    return rng.standard_normal(wo.NPARAM) * scale
+
+
+def test_conv_matches_scipy_correlate():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((7, 9, 3))
+    w = rng.standard_normal((9, 3, 5))
+    got = wo.conv(x, w)
+    for o in range(5):
+        ref = np.zeros((7, 9))
+        for c in range(3):
+            ref += scipy.signal.correlate2d(x[:, :, c], w[:, c, o].reshape(3, 3), mode="same", boundary="fill")
+        np.testing.assert_allclose(got[:, :, o], ref, atol=1e-12)
+
+
+def test_conv_backward_is_the_adjoint():
+    """<conv(x, w), z> = <x, conv_back_data(z, w)> = <w, conv_back_weight(x, z)>."""
+    rng = np.random.default_rng(1)
+    x, w, z = rng.standard_normal((6, 8, 4)), rng.standard_normal((9, 4, 3)), rng.standard_normal((6, 8, 3))
+    lhs = (wo.conv(x, w) * z).sum()
+    assert abs(lhs - (x * wo.conv_back_data(z, w)).sum()) < 1e-10 * abs(lhs)
+    assert abs(lhs - (w * wo.conv_back_weight(x, z)).sum()) < 1e-10 * abs(lhs)
+
+
+@pytest.mark.parametrize("lap", [0.0, 0.7])
+def test_gradient_matches_finite_differences(lap):
+    rng = np.random.default_rng(2)
+    theta = rand_theta(rng)
+    xs, ts = rng.standard_normal((2, 5, 6, wo.NIN)), rng.standard_normal((2, 5, 6, wo.NOUT))
+    _, g = wo.loss_and_grads(theta, xs, ts, lap=lap)
+    # parameters that exist in the network (the rest pad the library's layout and get zero)
+    mask = np.ones(wo.NPARAM, bool)
+    mask[:9 * 16 * 32] = np.tile(np.r_[np.ones(wo.NIN * 32), np.zeros((16 - wo.NIN) * 32)], 9).astype(bool)
+    off3 = 9 * 16 * 32 + 32 + 9 * 32 * 32 + 32
+    m3 = np.zeros((9, 32, 8), bool)
+    m3[:, :, :wo.NOUT] = True
+    mask[off3:off3 + 9 * 32 * 8] = m3.ravel()
+    mask[off3 + 9 * 32 * 8 + wo.NOUT:] = False
+    idx = rng.choice(np.flatnonzero(mask), 40, replace=False)
+    h = 1e-6
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (wo.loss_and_grads(tp, xs, ts, lap=lap)[0] - wo.loss_and_grads(tm, xs, ts, lap=lap)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+    assert np.all(g[~mask] == 0)
+
+
+def test_grid_laplacian():
+    """Zero on constants and on linear ramps away from the border; symmetric (<G a, b> = <a, G b>);
+    -4 at a lone interior spike, -2 at a lone corner spike; matches the dense graph Laplacian."""
+    rng = np.random.default_rng(9)
+    H, W = 6, 7
+    r, q = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    np.testing.assert_allclose(wo.grid_laplacian(np.ones((H, W, 2))), 0.0, atol=1e-15)
+    ramp = (2.0 * r - 3.0 * q)[..., None]
+    np.testing.assert_allclose(wo.grid_laplacian(ramp)[1:-1, 1:-1], 0.0, atol=1e-12)
+    a, b = rng.standard_normal((H, W, 3)), rng.standard_normal((H, W, 3))
+    assert abs((wo.grid_laplacian(a) * b).sum() - (a * wo.grid_laplacian(b)).sum()) < 1e-10
+    spike = np.zeros((H, W, 1))
+    spike[2, 3] = 1.0
+    assert wo.grid_laplacian(spike)[2, 3, 0] == -4.0
+    spike[:] = 0
+    spike[0, 0] = 1.0
+    assert wo.grid_laplacian(spike)[0, 0, 0] == -2.0
+    # dense graph Laplacian of the H x W grid graph: A - D
+    n = H * W
+    Lg = np.zeros((n, n))
+    for i in range(H):
+        for j in range(W):
+            for di, dj in ((1, 0), (0, 1)):
+                if i + di < H and j + dj < W:
+                    u, v = i * W + j, (i + di) * W + j + dj
+                    Lg[u, v] = Lg[v, u] = 1.0
+    Lg -= np.diag(Lg.sum(1))
+    np.testing.assert_allclose(wo.grid_laplacian(a).reshape(n, 3), Lg @ a.reshape(n, 3), atol=1e-12)
+
+
+def test_zero_network_predicts_linear_extrapolation():
+    """With all weights and biases zero the correction vanishes: pred = 2 s_k - s_{k-1}; with only
+    the output bias set, every pixel moves by bias * out_scale * r."""
+    rng = np.random.default_rng(4)
+    s, q = rng.standard_normal((5, 7, 4)), rng.standard_normal((5, 7, 4))
+    p = wo.unpack(np.zeros(wo.NPARAM))
+    np.testing.assert_allclose(wo.predict(p, s, q), 2 * s - q, rtol=0, atol=1e-15)
+    p["b3"] = np.array([1.0, -2.0, 0.5, 0.0])
+    scale = np.array([1e-3, 2e-3, 3e-3, 4e-3])
+    r = np.sqrt(((s - q) ** 2).reshape(-1, 4).mean(0))
+    np.testing.assert_allclose(wo.predict(p, s, q, (None, None, scale)), 2 * s - q + p["b3"] * scale * r,
+                               rtol=1e-7, atol=1e-15)
+
+
+def test_inputs_normalise_fields_and_change():
+    rng = np.random.default_rng(5)
+    s, q = rng.standard_normal((3, 4, 4)), rng.standard_normal((3, 4, 4))
+    mean, inv = rng.standard_normal(8), rng.uniform(0.5, 2, 8)
+    x = wo.inputs(s, q, mean, inv)
+    np.testing.assert_allclose(x[..., :4], (s - mean[:4]) * inv[:4], rtol=1e-6, atol=1e-6)
+    unit = wo.inputs(s, q)[..., 4:]  # the change in units of its RMS has unit RMS per channel
+    np.testing.assert_allclose(np.sqrt((unit.reshape(-1, 4) ** 2).mean(0)), 1.0, rtol=1e-6)
+    np.testing.assert_allclose(x[..., 4:], (unit - mean[4:]) * inv[4:], rtol=1e-5, atol=1e-5)
+
+
+@pytest.mark.parametrize("lam", [1e-4, 0.5, 3.0])
+def test_prediction_is_equivariant_to_the_pace(lam):
+    """Scaling the last change by lam leaves the network input unchanged and scales the predicted
+    change (pred - s) by lam: the map does not depend on how fast the state moves."""
+    rng = np.random.default_rng(6)
+    p = wo.unpack(rand_theta(rng))
+    s, d = rng.standard_normal((6, 5, 4)), rng.standard_normal((6, 5, 4)) * 1e-2
+    base = wo.predict(p, s, s - d, (None, None, np.full(4, 0.1))) - s
+    scaled = wo.predict(p, s, s - lam * d, (None, None, np.full(4, 0.1))) - s
+    np.testing.assert_allclose(scaled, lam * base, rtol=1e-4, atol=1e-12 * lam)
+
+
+def test_targets_recover_a_known_correction():
+    rng = np.random.default_rng(8)
+    s, d, y = rng.standard_normal((4, 6, 4)), rng.standard_normal((4, 6, 4)), rng.standard_normal((4, 6, 4))
+    out = np.array([0.5, 1.0, 2.0, 0.25])
+    r = np.sqrt((d.reshape(-1, 4) ** 2).mean(0))
+    n = s + d + y * out * r
+    np.testing.assert_allclose(wo.targets(s, s - d, n, out), y, rtol=1e-5, atol=1e-5)
+
+
+def test_bf16_rounding():
+    exact = np.array([1.0, -2.5, 0.15625, 3.0 * 2 ** -20, 0.0])
+    np.testing.assert_array_equal(wo.bf16(exact), exact)
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties to even -> 1; 1 + 3*2^-8 -> 1 + 2^-6
+    assert wo.bf16(np.array([1 + 2 ** -8]))[0] == 1.0
+    assert wo.bf16(np.array([1 + 3 * 2 ** -8]))[0] == 1 + 2 ** -6
+    x = np.random.default_rng(3).standard_normal(1000)
+    assert np.all(np.abs(wo.bf16(x) - x) <= np.abs(x) * 2 ** -8)
+
+
+def _random_symmetric_operator(rng, H, W):
+    """A symmetric block operator on H x W x 4 images: [[Mb, Kb], [Kb, -Mb]] per species, with Mb
+    diagonal positive and Kb a grid Laplacian weight (the structure of the step's saddle matrix)."""
+    m = rng.uniform(0.5, 1.5, (H, W, 1))
+    k = 0.3
+
+    def apply(x):
+        out = np.empty_like(x)
+        for sp in (0, 1):
+            u, v = x[..., sp:sp + 1], x[..., sp + 2:sp + 3]
+            out[..., sp:sp + 1] = m * u - k * wo.grid_laplacian(v)
+            out[..., sp + 2:sp + 3] = -k * wo.grid_laplacian(u) - m * v
+        return out
+    return apply
+
+
+def test_residual_loss_zero_network_is_one_and_symmetric_operator():
+    rng = np.random.default_rng(10)
+    H, W = 5, 6
+    A = _random_symmetric_operator(rng, H, W)
+    a, b = rng.standard_normal((H, W, 4)), rng.standard_normal((H, W, 4))
+    assert abs((A(a) * b).sum() - (a * A(b)).sum()) < 1e-10
+    s, q, rhs = (rng.standard_normal((2, H, W, 4)) for _ in range(3))
+    L, g = wo.residual_loss_and_grads(np.zeros(wo.NPARAM), s, q, rhs, A)
+    assert L == 1.0
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_residual_loss_gradient_matches_finite_differences(precond):
+    rng = np.random.default_rng(11)
+    H, W = 5, 6
+    A = _random_symmetric_operator(rng, H, W)
+    Pinv = None
+    if precond:  # a symmetric positive definite operator: diagonal scaling plus a smoothing term
+        dscale = rng.uniform(0.5, 2.0, (H, W, 4))
+        Pinv = lambda v: dscale * v - 0.1 * wo.grid_laplacian(v)
+    theta = rand_theta(rng, 0.2)
+    s = rng.standard_normal((2, H, W, 4))
+    q = s - 0.1 * rng.standard_normal((2, H, W, 4))
+    rhs = rng.standard_normal((2, H, W, 4))
+    norm = (None, None, np.array([0.3, 0.5, 0.2, 0.4]))
+    L, g = wo.residual_loss_and_grads(theta, s, q, rhs, A, norm, apply_Pinv=Pinv)
+    h = 1e-6
+    idx = rng.choice(np.flatnonzero(g != 0), 30, replace=False)
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (wo.residual_loss_and_grads(tp, s, q, rhs, A, norm, apply_Pinv=Pinv)[0]
+              - wo.residual_loss_and_grads(tm, s, q, rhs, A, norm, apply_Pinv=Pinv)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
