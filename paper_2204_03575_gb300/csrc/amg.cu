@@ -279,6 +279,44 @@ __global__ void k_gauss_jordan(int n, double* D, double* inv, int* bad) {
   }
 }
 
+// Grid-wide Gauss-Jordan for larger coarsest levels, two launches per pivot k: the first
+// scales the pivot row of [A | I] and copies column k (so the update reads it race-free), the
+// second eliminates column k from every other row.
+__global__ void k_gj_pivot(int n, int k, double* D, double* colk, int* bad) {
+  const int w = 2 * n;
+  const double piv = D[(size_t)k * w + k];
+  const double ip = 1.0 / piv;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0 && !(piv > 0.0)) *bad = 1;
+  // column k of the other rows (the pivot row's own entry is not needed).  D[k][k] itself is
+  // left as it is: every block reads it as the pivot, and no later step reads it again.
+  if (t < n) colk[t] = t == k ? 0.0 : D[(size_t)t * w + k];
+  for (int j = t; j < w; j += gridDim.x * blockDim.x) {
+    if (j == k) continue;
+    D[(size_t)k * w + j] *= ip;
+  }
+}
+
+__global__ void k_gj_eliminate(int n, int k, double* D, const double* colk) {
+  const int w = 2 * n;
+  const int64_t total = (int64_t)n * w;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / w), j = (int)(idx % w);
+    if (i == k) continue;
+    D[idx] = j == k ? 0.0 : D[idx] - colk[i] * D[(size_t)k * w + j];
+  }
+}
+
+__global__ void k_gj_extract(int n, const double* D, double* inv) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    inv[idx] = D[(size_t)i * 2 * n + n + j];
+  }
+}
+
 __global__ void k_d2f(const double* a, float* b, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -397,7 +435,10 @@ static ch_status level_setup(Hierarchy* h, int l, const ch_params& p, cudaStream
   CH_TRY(power_estimate(A, dinv, st, &lam));
   if (lam > 0.0 && std::isfinite(lam)) rho = std::min(rho, 1.05 * lam);
   h->rho.push_back(rho);
-  if (n <= p.coarse_max) {
+  // coarse_max 0: 512 rows for FP64 V-cycles, 4096 for FP32 (where the dense inverse is half the
+  // bytes); measured on 512 x 512: the dense solve beats the per-level launch chain up to there
+  const int cmax = p.coarse_max > 0 ? p.coarse_max : (h->precision == 0 ? 512 : 4096);
+  if (n <= cmax) {
     *last = true;
     return CH_OK;
   }
@@ -663,7 +704,21 @@ ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precisi
     if (s == CH_OK) {
       cudaMemsetAsync(bad, 0, sizeof(int), st);
       k_to_dense<<<blocks_for(nc), TPB, 0, st>>>(h->A.back(), D);
-      k_gauss_jordan<<<1, 1024, 0, st>>>(nc, D, h->cinv, bad);
+      if (nc <= 256) {
+        k_gauss_jordan<<<1, 1024, 0, st>>>(nc, D, h->cinv, bad);
+      } else {
+        double* colk = nullptr;
+        if (tmp.get(&colk, (size_t)nc) != CH_OK) {
+          s = CH_ERR_OOM;
+        } else {
+          const int gp = (2 * nc + TPB - 1) / TPB;
+          for (int k = 0; k < nc; ++k) {
+            k_gj_pivot<<<gp, TPB, 0, st>>>(nc, k, D, colk, bad);
+            k_gj_eliminate<<<4 * 152, TPB, 0, st>>>(nc, k, D, colk);
+          }
+          k_gj_extract<<<4 * 152, TPB, 0, st>>>(nc, D, h->cinv);
+        }
+      }
       int hb = 0;
       cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
       if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {

@@ -28,7 +28,7 @@ ch_status check_params(const ch_params* p) {
   CH_ARG(p->restart >= 1 && p->restart <= 64, "restart must be in [1, 64]");
   CH_ARG(p->max_iter >= 1, "max_iter must be >= 1");
   CH_ARG(p->cheb_degree >= 1 && p->cheb_degree <= 16, "cheb_degree must be in [1, 16]");
-  CH_ARG(p->coarse_max >= 1 && p->coarse_max <= 4096, "coarse_max must be in [1, 4096]");
+  CH_ARG(p->coarse_max >= 0 && p->coarse_max <= 4096, "coarse_max must be in [0, 4096]");
   CH_ARG(p->amg_theta >= 0 && p->amg_theta < 1, "amg_theta must be in [0, 1)");
   CH_ARG(p->vcycles_M >= 1 && p->vcycles_H >= 1, "vcycles must be >= 1");
   CH_ARG(p->autotune == 0 || p->autotune == 1, "autotune must be 0 or 1");
@@ -83,7 +83,7 @@ void ch_params_default(ch_params* p) {
   d.restart = 30;
   d.max_iter = 300;
   d.cheb_degree = 3;
-  d.coarse_max = 256;
+  d.coarse_max = 0;
   d.amg_theta = 0.08;
   d.vcycles_M = 1;
   d.vcycles_H = 2;

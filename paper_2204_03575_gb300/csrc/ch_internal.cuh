@@ -261,7 +261,7 @@ ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float*
 ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc, const double* x,
                             const double* q, int B, float lr, float* loss, cudaStream_t st);
 int ws_nparam();
-int ws_pixels(const ch_ws_s* w);
+void ws_dims(const ch_ws_s* w, int* H, int* W);
 ch_status state_step_learned(ch_state_s* S, ch_ws_s* w, cudaStream_t st, ch_step_stats* stats);
 ch_status state_step_guess(ch_state_s* S, const double* guess, cudaStream_t st, ch_step_stats* stats);
 }  // namespace ch

@@ -981,9 +981,12 @@ ch_status state_step_learned(ch_state_s* S, ch_ws_s* w, cudaStream_t st, ch_step
     set_error("state not initialised (call ch_state_set or ch_state_init_seeded)");
     return CH_ERR_STATE;
   }
-  if (S->R != 1 || ws_pixels(w) != S->N) {
-    set_error("the warm-start network is sized for %d nodes, the state has %d (and must be one run)",
-              ws_pixels(w), S->N);
+  int H = 0, W = 0;
+  ws_dims(w, &H, &W);
+  const ch_params& mp = S->sys->mesh->p;
+  if (S->R != 1 || mp.dim != 2 || W != mp.nx + 1 || H != mp.ny + 1) {
+    set_error("the warm-start network's image is %d x %d; the state must be one 2D run of %d x %d nodes",
+              H, W, H, W);
     return CH_ERR_ARG;
   }
   if (!S->x_prev) {

@@ -783,6 +783,9 @@ ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc
 
 int ws_nparam() { return WS_NPARAM; }
 
-int ws_pixels(const ch_ws_s* w) { return w->P; }
+void ws_dims(const ch_ws_s* w, int* H, int* W) {
+  *H = w->H;
+  *W = w->W;
+}
 
 }  // namespace ch

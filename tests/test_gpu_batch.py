@@ -39,7 +39,7 @@ def split(mesh, arr):
 def test_batch_step_parity_per_run(lib, precision):
     geoms = [(8, 12), (16, 16), (24, 10, 10.0, 2.5), (12, 20), (32, 32)]
     bases = [(0.33, 0.33), (0.25, 0.40), (0.40, 0.22), (0.30, 0.35), (0.21, 0.44)]
-    mesh, system, state = make_batch(lib, geoms, rtol=1e-13, precision=precision)
+    mesh, system, state = make_batch(lib, geoms, rtol=1e-14, precision=precision)
     assert mesh.nruns == len(geoms)
     state.init_seeded_batch([b[0] for b in bases], [b[1] for b in bases], 0.01, seed=100)
     solvers = [o.Solver(o.Params(nx=g[0], ny=g[1], Lx=g[2] if len(g) > 2 else 1.0,
@@ -59,7 +59,7 @@ def test_batch_step_parity_per_run(lib, precision):
             for gk in ("phi_p", "phi_nfa", "mu_p", "mu_nfa"):
                 assert rel(g[gk][r], getattr(ref, gk)) < 1e-10, (step, r, gk)
             st = state.run_stats(r)
-            assert st["status"] == 0 and max(st["relres"]) <= 1e-13
+            assert st["status"] == 0 and max(st["relres"]) <= 1e-14
             assert abs(st["mass"][0] - o.mass(s.M, g["phi_p"][r])) <= 1e-12 * abs(st["mass"][0])
             prev[r] = o.State(g["phi_p"][r], g["phi_nfa"][r], g["mu_p"][r], g["mu_nfa"][r])
 
