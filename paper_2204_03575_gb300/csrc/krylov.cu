@@ -219,8 +219,68 @@ __device__ __forceinline__ double block_sum32(double (&a)[32], double* sm /* [TP
   return t;
 }
 
+// W[v] -= sum_{k < nv} c[s][k] V_k[v] for one node (two partial sums, even / odd k, halve the
+// FP64 dependency chains)
+__device__ __forceinline__ void orth_update_node(const double4_32a* __restrict__ V, double4_32a* __restrict__ W,
+                                                 size_t N, int nv, const double (*coef)[MAXM + 1], int v) {
+  double ax = 0, ay = 0, az = 0, aw = 0, bx = 0, by = 0, bz = 0, bw = 0;
+  int k = 0;
+  for (; k + 1 < nv; k += 2) {
+    const double4_32a q0 = V[(size_t)k * N + v];
+    const double4_32a q1 = V[(size_t)(k + 1) * N + v];
+    const double c00 = coef[0][k], c10 = coef[1][k], c01 = coef[0][k + 1], c11 = coef[1][k + 1];
+    ax = fma(c00, q0.x, ax); az = fma(c00, q0.z, az); ay = fma(c10, q0.y, ay); aw = fma(c10, q0.w, aw);
+    bx = fma(c01, q1.x, bx); bz = fma(c01, q1.z, bz); by = fma(c11, q1.y, by); bw = fma(c11, q1.w, bw);
+  }
+  if (k < nv) {
+    const double4_32a q0 = V[(size_t)k * N + v];
+    ax = fma(coef[0][k], q0.x, ax); az = fma(coef[0][k], q0.z, az);
+    ay = fma(coef[1][k], q0.y, ay); aw = fma(coef[1][k], q0.w, aw);
+  }
+  double4_32a w = W[v];
+  w.x -= ax + bx;
+  w.y -= ay + by;
+  w.z -= az + bz;
+  w.w -= aw + bw;
+  W[v] = w;
+}
+
+// Dots of W with the KW basis vectors k0 .. k0+KW-1 over this thread's nodes, into acc[2t] (species
+// 0) and acc[2t+1] (species 1).  KW is exact, so no FP64 slot is spent on absent vectors.  With
+// UPD the node is first updated with all nv vectors (the same vectors are then re-read from L1).
+template <int KW, bool UPD>
+__device__ __forceinline__ void orth_dots_chunk(const double4_32a* __restrict__ V, double4_32a* __restrict__ W,
+                                                size_t N, int k0, int nv, const double (*coef)[MAXM + 1],
+                                                int v0, int v1, double (&acc)[32]) {
+  for (int v = v0; v < v1; v += blockDim.x) {
+    if (UPD) orth_update_node(V, W, N, nv, coef, v);
+    const double4_32a w = W[v];
+#pragma unroll
+    for (int t = 0; t < KW; ++t) {
+      const double4_32a q = V[(size_t)(k0 + t) * N + v];
+      acc[2 * t] = fma(q.x, w.x, fma(q.z, w.z, acc[2 * t]));
+      acc[2 * t + 1] = fma(q.y, w.y, fma(q.w, w.w, acc[2 * t + 1]));
+    }
+  }
+}
+
+template <bool UPD>
+__device__ __forceinline__ void orth_dots_dispatch(int kw, const double4_32a* __restrict__ V,
+                                                   double4_32a* __restrict__ W, size_t N, int k0, int nv,
+                                                   const double (*coef)[MAXM + 1], int v0, int v1,
+                                                   double (&acc)[32]) {
+#define CH_ORTH_CASE(n) \
+  case n: orth_dots_chunk<n, UPD>(V, W, N, k0, nv, coef, v0, v1, acc); break;
+  switch (kw) {
+    CH_ORTH_CASE(1) CH_ORTH_CASE(2) CH_ORTH_CASE(3) CH_ORTH_CASE(4) CH_ORTH_CASE(5) CH_ORTH_CASE(6)
+    CH_ORTH_CASE(7) CH_ORTH_CASE(8) CH_ORTH_CASE(9) CH_ORTH_CASE(10) CH_ORTH_CASE(11) CH_ORTH_CASE(12)
+    CH_ORTH_CASE(13) CH_ORTH_CASE(14) CH_ORTH_CASE(15) default: orth_dots_chunk<16, UPD>(V, W, N, k0, nv, coef, v0, v1, acc);
+  }
+#undef CH_ORTH_CASE
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(TPB) k_orth(Seg sg, int N, int nv, const double4_32a* __restrict__ V,
+__global__ void __launch_bounds__(TPB, 2) k_orth(Seg sg, int N, int nv, const double4_32a* __restrict__ V,
                                                double4_32a* __restrict__ W, double* partials,
                                                KrylovDev* kds) {
   __shared__ double sm[(TPB / 32) * 32];
@@ -234,29 +294,9 @@ __global__ void __launch_bounds__(TPB) k_orth(Seg sg, int N, int nv, const doubl
       coef[1][k] = MODE == 1 ? kd->h1[1][k] : kd->h2[1][k];
     }
     __syncthreads();
-    for (int v = v0; v < v1; v += blockDim.x) {
-      // two partial sums (even / odd k) halve the FP64 dependency chains
-      double ax = 0, ay = 0, az = 0, aw = 0, bx = 0, by = 0, bz = 0, bw = 0;
-      int k = 0;
-      for (; k + 1 < nv; k += 2) {
-        const double4_32a q0 = V[(size_t)k * N + v];
-        const double4_32a q1 = V[(size_t)(k + 1) * N + v];
-        const double c00 = coef[0][k], c10 = coef[1][k], c01 = coef[0][k + 1], c11 = coef[1][k + 1];
-        ax = fma(c00, q0.x, ax); az = fma(c00, q0.z, az); ay = fma(c10, q0.y, ay); aw = fma(c10, q0.w, aw);
-        bx = fma(c01, q1.x, bx); bz = fma(c01, q1.z, bz); by = fma(c11, q1.y, by); bw = fma(c11, q1.w, bw);
-      }
-      if (k < nv) {
-        const double4_32a q0 = V[(size_t)k * N + v];
-        ax = fma(coef[0][k], q0.x, ax); az = fma(coef[0][k], q0.z, az);
-        ay = fma(coef[1][k], q0.y, ay); aw = fma(coef[1][k], q0.w, aw);
-      }
-      double4_32a w = W[v];
-      w.x -= ax + bx;
-      w.y -= ay + by;
-      w.z -= az + bz;
-      w.w -= aw + bw;
-      W[v] = w;
-    }
+  }
+  if (MODE == 2) {
+    for (int v = v0; v < v1; v += blockDim.x) orth_update_node(V, W, (size_t)N, nv, coef, v);
   }
   const int b0 = sg.first[run], b1 = sg.first[run + 1];
   if (MODE <= 1) {
@@ -264,20 +304,14 @@ __global__ void __launch_bounds__(TPB) k_orth(Seg sg, int N, int nv, const doubl
       double acc[32];
 #pragma unroll
       for (int t = 0; t < 32; ++t) acc[t] = 0.0;
-      for (int v = v0; v < v1; v += blockDim.x) {
-        const double4_32a w = W[v];
-#pragma unroll
-        for (int t = 0; t < KC; ++t) {
-          if (k0 + t < nv) {
-            const double4_32a q = V[(size_t)(k0 + t) * N + v];
-            acc[2 * t] = fma(q.x, w.x, fma(q.z, w.z, acc[2 * t]));
-            acc[2 * t + 1] = fma(q.y, w.y, fma(q.w, w.w, acc[2 * t + 1]));
-          }
-        }
-      }
+      const int kw = nv - k0 < KC ? nv - k0 : KC;
+      // MODE 1: the update of each node is fused into the first chunk's dots
+      if (MODE == 1 && k0 == 0)
+        orth_dots_dispatch<true>(kw, V, W, (size_t)N, k0, nv, coef, v0, v1, acc);
+      else
+        orth_dots_dispatch<false>(kw, V, W, (size_t)N, k0, nv, coef, v0, v1, acc);
       const double tot = block_sum32(acc, sm);
-      const int nval = 2 * (nv - k0 < KC ? nv - k0 : KC);
-      if (threadIdx.x < nval) partials[(size_t)blockIdx.x * MAXV + 2 * k0 + threadIdx.x] = tot;
+      if (threadIdx.x < 2 * kw) partials[(size_t)blockIdx.x * MAXV + 2 * k0 + threadIdx.x] = tot;
     }
     if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
     __shared__ double tot[MAXV];
