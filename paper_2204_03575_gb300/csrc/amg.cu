@@ -16,6 +16,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <set>
 #include <tuple>
 #include <type_traits>
 
@@ -27,9 +28,21 @@ template <typename T> struct V2T;
 template <> struct V2T<double> { using t = double2; };
 template <> struct V2T<float> { using t = float2; };
 
+// Fine-level operator of a structured mesh as diagonals: row i's neighbours sit at i + off[d]
+// (offsets ascending); val[d * n + i] is zero where row i has no such neighbour (the clamped
+// column index is then read but multiplied by zero).
+constexpr int kDiaSlots = 16;
+template <typename T>
+struct Dia {
+  int nd = 0;  // 0: not structured, use the CSR form
+  int off[kDiaSlots] = {};
+  T* val = nullptr;
+};
+
 template <typename T>
 struct LevelT {
   Csr<T> A, P, R;
+  Dia<T> dia;                          // level 0 of a structured mesh
   int tprA = 1, tprP = 1, tprR = 1;  // lanes per row of the SpMV-type kernels (autotuned)
   T* dinv = nullptr;
   typename V2T<T>::t *x = nullptr, *x2 = nullptr, *d = nullptr, *r = nullptr, *b = nullptr;
@@ -535,7 +548,8 @@ static ch_status level_setup(Hierarchy* h, int l, const ch_params& p, cudaStream
 }
 
 template <typename T, typename V2>
-static void launch_residual(int tpr, const Csr<T>& A, const V2* b, const V2* x, V2* r, cudaStream_t st);
+static void launch_residual(int tpr, const Csr<T>& A, const V2* b, const V2* x, V2* r, cudaStream_t st,
+                            const Dia<T>* dia = nullptr);
 template <typename T, typename V2, bool ACC>
 static void launch_spmv2(int tpr, const Csr<T>& A, const V2* x, V2* y, cudaStream_t st);
 
@@ -607,8 +621,9 @@ static ch_status autotune_levels(Hierarchy* h, std::vector<LevelT<T>>& L, int mo
   }
   for (int l = 0; l < h->nlev; ++l) {
     LevelT<T>& W = L[l];
-    W.tprA = tune_tpr(0, W.A.nrows, W.A.ncols, W.A.nnz, sizeof(T), mode,
-                      [&](int t) { launch_residual<T, V2>(t, W.A, W.b, W.x, W.r, st); }, st);
+    W.tprA = W.dia.nd ? 1
+                      : tune_tpr(0, W.A.nrows, W.A.ncols, W.A.nnz, sizeof(T), mode,
+                                 [&](int t) { launch_residual<T, V2>(t, W.A, W.b, W.x, W.r, st); }, st);
     if (l + 1 < h->nlev) {
       LevelT<T>& C = L[l + 1];
       W.tprR = tune_tpr(1, W.R.nrows, W.R.ncols, W.R.nnz, sizeof(T), mode,
@@ -619,6 +634,41 @@ static ch_status autotune_levels(Hierarchy* h, std::vector<LevelT<T>>& L, int mo
   }
   CH_LAUNCHED();
   CH_CUDA(cudaStreamSynchronize(st));
+  return CH_OK;
+}
+
+__global__ void k_csr_to_dia(Csr<double> A, Dia<double> D) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nrows) return;
+  for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+    const int o = A.col[q] - i;
+    for (int d = 0; d < D.nd; ++d)
+      if (D.off[d] == o) D.val[(size_t)d * A.nrows + i] = A.val[q];
+  }
+}
+
+// The diagonal form of A when its pattern has exactly 7 (uniform 2D triangles) or 15 (uniform 3D
+// Kuhn tetrahedra) distinct column offsets (a host scan of the pattern at set-up); else nd = 0.
+static ch_status dia_build(const Csr<double>& A, Alloc& mem, Dia<double>* out, cudaStream_t st) {
+  out->nd = 0;
+  const int n = A.nrows;
+  std::vector<int> rp(n + 1), col((size_t)A.nnz);
+  CH_CUDA(cudaMemcpyAsync(rp.data(), A.rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaMemcpyAsync(col.data(), A.col, sizeof(int) * (size_t)A.nnz, cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  std::set<int> offs;
+  for (int i = 0; i < n && (int)offs.size() <= kDiaSlots; ++i)
+    for (int q = rp[i]; q < rp[i + 1]; ++q) offs.insert(col[q] - i);
+  if (offs.size() != 7 && offs.size() != 15) return CH_OK;
+  Dia<double> D;
+  D.nd = (int)offs.size();
+  int k = 0;
+  for (int o : offs) D.off[k++] = o;  // ascending: the CSR column order of every row
+  CH_TRY(mem.get(&D.val, (size_t)D.nd * n));
+  CH_CUDA(cudaMemsetAsync(D.val, 0, sizeof(double) * (size_t)D.nd * n, st));
+  k_csr_to_dia<<<blocks_for(n), TPB, 0, st>>>(A, D);
+  CH_LAUNCHED();
+  *out = D;
   return CH_OK;
 }
 
@@ -661,6 +711,22 @@ static ch_status make_working(Hierarchy* h, std::vector<LevelT<T>>& L, cudaStrea
     CH_TRY(h->mem.get(&w.d, (size_t)n));
     CH_TRY(h->mem.get(&w.r, (size_t)n));
     CH_TRY(h->mem.get(&w.b, (size_t)n));
+  }
+  // the fine level of a uniform mesh in diagonal form
+  Dia<double> d64;
+  CH_TRY(dia_build(h->A[0], h->mem, &d64, st));
+  if (d64.nd) {
+    Dia<T>& d = L[0].dia;
+    d.nd = d64.nd;
+    for (int k = 0; k < kDiaSlots; ++k) d.off[k] = d64.off[k];
+    const size_t cnt = (size_t)d64.nd * h->A[0].nrows;
+    if (std::is_same<T, double>::value) {
+      d.val = reinterpret_cast<T*>(d64.val);
+    } else {
+      CH_TRY(h->mem.get(&d.val, cnt));
+      k_copy_cast<T><<<blocks_for((int64_t)cnt), TPB, 0, st>>>(d64.val, d.val, (int64_t)cnt);
+      CH_LAUNCHED();
+    }
   }
   return autotune_levels<T>(h, L, h->autotune, st);
 }
@@ -868,6 +934,70 @@ __global__ void __launch_bounds__(TPB) k_spmv2(Csr<T> A, const V2* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------- structured (diagonal) fine level
+template <typename T, typename V2, int ND>
+__device__ __forceinline__ void dia_row_sum(const Dia<T>& D, int n, int i, const V2* __restrict__ x, T& s0,
+                                            T& s1) {
+  s0 = 0;
+  s1 = 0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    int j = i + D.off[d];
+    j = j < 0 ? 0 : (j >= n ? n - 1 : j);
+    const T a = D.val[(size_t)d * n + i];
+    const V2 xj = x[j];
+    s0 = fma(a, xj.x, s0);
+    s1 = fma(a, xj.y, s1);
+  }
+}
+
+template <typename T, typename V2, int ND>
+__global__ void __launch_bounds__(TPB) k_cheb_step_dia(Dia<T> D, int n, const T* __restrict__ dinv,
+                                                       const V2* __restrict__ b, const V2* __restrict__ x,
+                                                       V2* __restrict__ d, V2* __restrict__ xo, T alpha, T beta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s0, s1;
+  dia_row_sum<T, V2, ND>(D, n, i, x, s0, s1);
+  const V2 bi = b[i], xi = x[i];
+  const T di = dinv[i] * beta;
+  V2 dd;
+  if (alpha != T(0)) {
+    const V2 dold = d[i];
+    dd = mk2<T, V2>(fma(alpha, dold.x, di * (bi.x - s0)), fma(alpha, dold.y, di * (bi.y - s1)));
+  } else {
+    dd = mk2<T, V2>(di * (bi.x - s0), di * (bi.y - s1));
+  }
+  d[i] = dd;
+  xo[i] = mk2<T, V2>(xi.x + dd.x, xi.y + dd.y);
+}
+
+template <typename T, typename V2, int ND>
+__global__ void __launch_bounds__(TPB) k_residual_dia(Dia<T> D, int n, const V2* __restrict__ b,
+                                                      const V2* __restrict__ x, V2* __restrict__ r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s0, s1;
+  dia_row_sum<T, V2, ND>(D, n, i, x, s0, s1);
+  const V2 bi = b[i];
+  r[i] = mk2<T, V2>(bi.x - s0, bi.y - s1);
+}
+
+template <typename T, typename V2, int ND>
+__global__ void __launch_bounds__(TPB) k_spmv2_dia(Dia<T> D, int n, const V2* __restrict__ x, V2* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s0, s1;
+  dia_row_sum<T, V2, ND>(D, n, i, x, s0, s1);
+  y[i] = mk2<T, V2>(s0, s1);
+}
+
+#define CH_DIA_DISPATCH(nd, KCALL)                    \
+  switch (nd) {                                       \
+    case 7: { constexpr int NDC = 7; KCALL; } break;  \
+    default: { constexpr int NDC = 15; KCALL; } break; \
+  }
+
 #define CH_TPR_DISPATCH(tpr, KCALL)                      \
   switch (tpr) {                                         \
     case 1: { constexpr int TPRC = 1; KCALL; } break;    \
@@ -880,14 +1010,36 @@ __global__ void __launch_bounds__(TPB) k_spmv2(Csr<T> A, const V2* __restrict__ 
 
 template <typename T, typename V2>
 static void launch_cheb_step(int tpr, const Csr<T>& A, const T* dinv, const V2* b, const V2* x, V2* d,
-                             V2* xo, T alpha, T beta, cudaStream_t st) {
+                             V2* xo, T alpha, T beta, cudaStream_t st, const Dia<T>* dia = nullptr) {
+  if (dia && dia->nd) {
+    const int g = blocks_for(A.nrows);
+    CH_DIA_DISPATCH(dia->nd, (k_cheb_step_dia<T, V2, NDC><<<g, TPB, 0, st>>>(*dia, A.nrows, dinv, b, x, d, xo,
+                                                                              alpha, beta)));
+    return;
+  }
   const int g = blocks_for((int64_t)A.nrows * tpr);
   CH_TPR_DISPATCH(tpr, (k_cheb_step<T, V2, TPRC><<<g, TPB, 0, st>>>(A, dinv, b, x, d, xo, alpha, beta)));
 }
 template <typename T, typename V2>
-static void launch_residual(int tpr, const Csr<T>& A, const V2* b, const V2* x, V2* r, cudaStream_t st) {
+static void launch_residual(int tpr, const Csr<T>& A, const V2* b, const V2* x, V2* r, cudaStream_t st,
+                            const Dia<T>* dia) {
+  if (dia && dia->nd) {
+    const int g = blocks_for(A.nrows);
+    CH_DIA_DISPATCH(dia->nd, (k_residual_dia<T, V2, NDC><<<g, TPB, 0, st>>>(*dia, A.nrows, b, x, r)));
+    return;
+  }
   const int g = blocks_for((int64_t)A.nrows * tpr);
   CH_TPR_DISPATCH(tpr, (k_residual<T, V2, TPRC><<<g, TPB, 0, st>>>(A, b, x, r)));
+}
+// y = A x with the level's operator (the diagonal form where there is one)
+template <typename T, typename V2>
+static void launch_apply_level(const LevelT<T>& L, const V2* x, V2* y, cudaStream_t st) {
+  if (L.dia.nd) {
+    const int g = blocks_for(L.A.nrows);
+    CH_DIA_DISPATCH(L.dia.nd, (k_spmv2_dia<T, V2, NDC><<<g, TPB, 0, st>>>(L.dia, L.A.nrows, x, y)));
+    return;
+  }
+  launch_spmv2<T, V2, false>(L.tprA, L.A, x, y, st);
 }
 template <typename T, typename V2, bool ACC>
 static void launch_spmv2(int tpr, const Csr<T>& A, const V2* x, V2* y, cudaStream_t st) {
@@ -969,11 +1121,13 @@ static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, bool zero_guess,
     k_cheb_first<T_, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.dinv, L.b, (T_)c.invtheta, x, L.d);
     s0 = 1;
   }
+  // operator bytes: CSR values + column indices + row pointers, or the diagonals' values
+  const double opb = L.dia.nd ? T * L.dia.nd * (double)n : nnz * (4 + T) + 4.0 * (n + 1);
   for (int s = s0; s < h->cheb_degree; ++s) {
     ProfScope ps(st, l == 0 ? K_CHEB_STEP : K_CHEB_STEP_C, sizeof(T_) == 4,
-                 nnz * (4 + T) + 4.0 * (n + 1) + T * n * (c.alpha[s] != 0.0 ? 11 : 9),
-                 2.0 * nnz + 4.0 * n);
-    launch_cheb_step<T_, V2>(L.tprA, L.A, L.dinv, L.b, x, L.d, other, (T_)c.alpha[s], (T_)c.beta[s], st);
+                 opb + T * n * (c.alpha[s] != 0.0 ? 11 : 9), 2.0 * nnz + 4.0 * n);
+    launch_cheb_step<T_, V2>(L.tprA, L.A, L.dinv, L.b, x, L.d, other, (T_)c.alpha[s], (T_)c.beta[s], st,
+                             &L.dia);
     std::swap(x, other);
   }
   CH_LAUNCHED();
@@ -1001,9 +1155,9 @@ static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv,
   LevelT<T>& C = Ls[l + 1];
   const int nc = C.A.nrows;
   {
-    ProfScope ps(st, l == 0 ? K_VRESIDUAL : K_VRESIDUAL_C, sizeof(T) == 4, L.A.nnz * (4 + Tb) + 4.0 * (n + 1) + 6.0 * Tb * n,
-                 2.0 * L.A.nnz);
-    launch_residual<T, V2>(L.tprA, L.A, L.b, x, L.r, st);
+    const double opb = L.dia.nd ? Tb * L.dia.nd * (double)n : L.A.nnz * (4 + Tb) + 4.0 * (n + 1);
+    ProfScope ps(st, l == 0 ? K_VRESIDUAL : K_VRESIDUAL_C, sizeof(T) == 4, opb + 6.0 * Tb * n, 2.0 * L.A.nnz);
+    launch_residual<T, V2>(L.tprA, L.A, L.b, x, L.r, st, &L.dia);
   }
   {
     ProfScope ps(st, l == 0 ? K_RESTRICT : K_RESTRICT_C, sizeof(T) == 4,
@@ -1052,7 +1206,7 @@ static ch_status apply_fine_t(std::vector<LevelT<T>>& Ls, const double* x, int l
   LevelT<T>& L = Ls[0];
   const int n = L.A.nrows;
   k_load2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, x, ldx, L.r);
-  launch_spmv2<T, V2, false>(L.tprA, L.A, L.r, L.d, st);
+  launch_apply_level<T, V2>(L, L.r, L.d, st);
   k_store2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.d, y, ldy);
   CH_LAUNCHED();
   return CH_OK;
@@ -1101,9 +1255,9 @@ static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::ve
     // b <- M x (M's fine level in working precision); the V-cycle reads only L.b afterwards
     {
       const double Tb = sizeof(T), nnz = (double)LM[0].A.nnz;
-      ProfScope ps(st, K_SPMV_M, sizeof(T) == 4, nnz * (4 + Tb) + 4.0 * (n + 1) + 4.0 * Tb * n,
-                   2.0 * nnz);
-      launch_spmv2<T, V2, false>(LM[0].tprA, LM[0].A, xr, L.b, st);
+      const double opb = LM[0].dia.nd ? Tb * LM[0].dia.nd * (double)n : nnz * (4 + Tb) + 4.0 * (n + 1);
+      ProfScope ps(st, K_SPMV_M, sizeof(T) == 4, opb + 4.0 * Tb * n, 2.0 * nnz);
+      launch_apply_level<T, V2>(LM[0], xr, L.b, st);
     }
     CH_LAUNCHED();
     xr = L.x;  // the first solve's result now lives in L.b as M x; start afresh
@@ -1187,13 +1341,14 @@ static ch_status vcycle_static(Hierarchy* h, LevelT<T>* Ls, const T* cinv, int l
       s0 = 1;
     }
     for (int s = s0; s < h->cheb_degree; ++s) {
-      launch_cheb_step<T, V2>(L.tprA, L.A, L.dinv, L.b, x, L.d, other, (T)c.alpha[s], (T)c.beta[s], st);
+      launch_cheb_step<T, V2>(L.tprA, L.A, L.dinv, L.b, x, L.d, other, (T)c.alpha[s], (T)c.beta[s], st,
+                              &L.dia);
       std::swap(x, other);
     }
   };
   smooth_static(zero_guess);
   LevelT<T>& C = Ls[l + 1];
-  launch_residual<T, V2>(L.tprA, L.A, L.b, x, L.r, st);
+  launch_residual<T, V2>(L.tprA, L.A, L.b, x, L.r, st, &L.dia);
   launch_spmv2<T, V2, false>(L.tprR, L.R, L.r, C.b, st);
   CH_LAUNCHED();
   V2* xc = C.x;
