@@ -1228,21 +1228,33 @@ static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::ve
   using V2 = typename V2T<T>::t;
   const int n = LM[0].A.nrows;
   const ch_params& p = pc->sys->p;
-  // step 1: M w_1 = v_1
+  // Step 1 does not depend on steps 2-4: it runs on the preconditioner's side stream, forked
+  // from and joined back into st (inside a stream capture this becomes two parallel graph
+  // branches).  Both chains are mostly latency-bound coarse-level launches, so they overlap.
+  // With per-launch event timing on, everything stays on st so that kernel times do not overlap.
+  const bool fork = pc->side != nullptr && !prof_timing();
+  cudaStream_t sm = st;
+  if (fork) {
+    CH_CUDA(cudaEventRecord(pc->ev_fork, st));
+    CH_CUDA(cudaStreamWaitEvent(pc->side, pc->ev_fork, 0));
+    sm = pc->side;
+  }
+  // step 1: M w_1 = v_1 (w_1 in columns 0-1 of w; steps 2-4 write columns 2-3)
   {
     LevelT<T>& L = LM[0];
     {
-      ProfScope ps(st, K_VLOAD, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
-      k_load2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, v, 4, L.b);
+      ProfScope ps(sm, K_VLOAD, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
+      k_load2<T, V2><<<blocks_for(n), TPB, 0, sm>>>(n, v, 4, L.b);
     }
     V2* xr = L.x;
-    for (int c = 0; c < p.vcycles_M; ++c) CH_TRY(vcycle<T>(pc->hM, LM, cinvM, 0, c == 0, &xr, st));
+    for (int c = 0; c < p.vcycles_M; ++c) CH_TRY(vcycle<T>(pc->hM, LM, cinvM, 0, c == 0, &xr, sm));
     {
-      ProfScope ps(st, K_VSTORE, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
-      k_store2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, xr, w, 4);
+      ProfScope ps(sm, K_VSTORE, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
+      k_store2<T, V2><<<blocks_for(n), TPB, 0, sm>>>(n, xr, w, 4);
     }
     CH_LAUNCHED();
   }
+  if (fork) CH_CUDA(cudaEventRecord(pc->ev_join, sm));
   // steps 2-4: H w_2 = v_2; w_2 = M w_2; H w_2 = w_2
   {
     LevelT<T>& L = LH[0];
@@ -1268,6 +1280,7 @@ static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::ve
     }
     CH_LAUNCHED();
   }
+  if (fork) CH_CUDA(cudaStreamWaitEvent(st, pc->ev_join, 0));
   return CH_OK;
 }
 

@@ -255,6 +255,13 @@ ch_status ch_precond_setup(const ch_system_t* s, void* stream, ch_precond_t** ou
   H.val = s->valH;
   ch_status r = ch::hierarchy_build(M, s->p, pc->precision, S(stream), &pc->hM);
   if (r == CH_OK) r = ch::hierarchy_build(H, s->p, pc->precision, S(stream), &pc->hH);
+  if (r == CH_OK && (cudaStreamCreateWithFlags(&pc->side, cudaStreamNonBlocking) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&pc->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&pc->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    ch::set_error("preconditioner: creating its side stream or events failed");
+    r = CH_ERR_CUDA;
+  }
   if (r != CH_OK) {
     delete pc;
     return r;

@@ -221,10 +221,15 @@ struct ch_precond_s {
   ch::Hierarchy* hH = nullptr;
   double* t1 = nullptr;  // N x 2 temporaries for Algorithm 1
   double* t2 = nullptr;
+  cudaStream_t side = nullptr;  // Algorithm 1's M-solve branch (non-blocking)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   ch::Alloc mem;
   ~ch_precond_s() {
     ch::hierarchy_free(hM);
     ch::hierarchy_free(hH);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
   }
 };
 
