@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
         ("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("cheb_degree", ctypes.c_int32),
         ("coarse_max", ctypes.c_int32), ("amg_theta", ctypes.c_double),
         ("vcycles_M", ctypes.c_int32), ("vcycles_H", ctypes.c_int32), ("autotune", ctypes.c_int32),
-        ("cheb_lower", ctypes.c_double), ("graphs", ctypes.c_int32),
+        ("cheb_lower", ctypes.c_double), ("graphs", ctypes.c_int32), ("cheb_degree_coarse", ctypes.c_int32),
     ]
 
     def __init__(self, **kw):

@@ -60,6 +60,7 @@ struct Hierarchy {
   double* cinv = nullptr;             // nc x nc dense inverse (FP64)
   float* cinvf = nullptr;
   int cheb_degree = 2;
+  int cheb_degree_coarse = 2;         // on the levels below the finest
   double cheb_lower = 0.3;
   int autotune = 1;
   Alloc mem;
@@ -737,6 +738,7 @@ ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precisi
   Hierarchy* h = new Hierarchy();
   h->precision = precision;
   h->cheb_degree = p.cheb_degree;
+  h->cheb_degree_coarse = p.cheb_degree_coarse > 0 ? p.cheb_degree_coarse : p.cheb_degree;
   h->autotune = p.autotune;
   h->cheb_lower = p.cheb_lower;
   h->A.push_back(A0);
@@ -1111,7 +1113,8 @@ static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, bool zero_guess,
                         typename V2T<T_>::t** xcur, cudaStream_t st) {
   using V2 = typename V2T<T_>::t;
   const int n = L.A.nrows;
-  const ChebCoef c = cheb_coef(h->rho[l], h->cheb_degree, h->cheb_lower);
+  const int deg = l == 0 ? h->cheb_degree : h->cheb_degree_coarse;
+  const ChebCoef c = cheb_coef(h->rho[l], deg, h->cheb_lower);
   V2* x = *xcur;
   V2* other = (x == L.x) ? L.x2 : L.x;
   int s0 = 0;
@@ -1123,7 +1126,7 @@ static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, bool zero_guess,
   }
   // operator bytes: CSR values + column indices + row pointers, or the diagonals' values
   const double opb = L.dia.nd ? T * L.dia.nd * (double)n : nnz * (4 + T) + 4.0 * (n + 1);
-  for (int s = s0; s < h->cheb_degree; ++s) {
+  for (int s = s0; s < deg; ++s) {
     ProfScope ps(st, l == 0 ? K_CHEB_STEP : K_CHEB_STEP_C, sizeof(T_) == 4,
                  opb + T * n * (c.alpha[s] != 0.0 ? 11 : 9), 2.0 * nnz + 4.0 * n);
     launch_cheb_step<T_, V2>(L.tprA, L.A, L.dinv, L.b, x, L.d, other, (T_)c.alpha[s], (T_)c.beta[s], st,
@@ -1344,7 +1347,8 @@ static ch_status vcycle_static(Hierarchy* h, LevelT<T>* Ls, const T* cinv, int l
     *xres = L.x;
     return CH_OK;
   }
-  const ChebCoef c = cheb_coef(h->rho[l], h->cheb_degree, h->cheb_lower);
+  const int deg = l == 0 ? h->cheb_degree : h->cheb_degree_coarse;
+  const ChebCoef c = cheb_coef(h->rho[l], deg, h->cheb_lower);
   V2* x = *xres;
   auto smooth_static = [&](bool zg) {
     V2* other = (x == L.x) ? L.x2 : L.x;
@@ -1353,7 +1357,7 @@ static ch_status vcycle_static(Hierarchy* h, LevelT<T>* Ls, const T* cinv, int l
       k_cheb_first<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.dinv, L.b, (T)c.invtheta, x, L.d);
       s0 = 1;
     }
-    for (int s = s0; s < h->cheb_degree; ++s) {
+    for (int s = s0; s < deg; ++s) {
       launch_cheb_step<T, V2>(L.tprA, L.A, L.dinv, L.b, x, L.d, other, (T)c.alpha[s], (T)c.beta[s], st,
                               &L.dia);
       std::swap(x, other);

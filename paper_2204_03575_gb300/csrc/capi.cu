@@ -34,6 +34,7 @@ ch_status check_params(const ch_params* p) {
   CH_ARG(p->autotune == 0 || p->autotune == 1, "autotune must be 0 or 1");
   CH_ARG(p->cheb_lower > 0 && p->cheb_lower < 1, "cheb_lower must be in (0, 1)");
   CH_ARG(p->graphs == 0 || p->graphs == 1, "graphs must be 0 or 1");
+  CH_ARG(p->cheb_degree_coarse >= 0 && p->cheb_degree_coarse <= 16, "cheb_degree_coarse must be in [0, 16]");
   return CH_OK;
 }
 }  // namespace
@@ -90,6 +91,7 @@ void ch_params_default(ch_params* p) {
   d.autotune = 1;
   d.cheb_lower = 0.3;
   d.graphs = 1;
+  d.cheb_degree_coarse = 0;
   *p = d;
 }
 
