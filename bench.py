@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the C1, mesh-size and 3D sections")
     ap.add_argument("--prewarm-s", type=float, default=2.0,
                     help="seconds of untimed steps on a throwaway state before the timed state exists")
     ap.add_argument("--learned-nx", type=int, default=256)
@@ -175,6 +176,55 @@ def timed_steps(torch, ch, state, K, flush, barrier, net=None):
     torch.cuda.synchronize()
     barrier()
     return e0.elapsed_time(e1), iters
+
+
+def extra_sections(torch, ch, np, K, W, flush, barrier, world):
+    """32x32 steps/s (10 steps), FGMRES iterations per step for 32^2 .. 512^2 (first 10 steps of
+    the same seeded run), and 3D 128x128x32 Kuhn tetrahedra on [0,1]^2 x [0,0.25], bases
+    0.30/0.30 +/- 0.01 seed 0, FP32 V-cycles in FP64 FGMRES, up to 50 timed steps."""
+    out = {}
+    _, _, st1 = make_solver(ch, 32, 32, precision=0)
+    for _ in range(W):
+        st1.step()
+    ms1, it1 = timed_steps(torch, ch, st1, 10, flush, barrier)
+    out["2d_32x32_fp64"] = {"steps": 10, "steps_per_s": world * 10 / (ms1 * 1e-3),
+                            "iters_per_step_mean": float(np.mean(it1)),
+                            "note": "launch-bound: a roofline is not meaningful at 1089 nodes"}
+    del st1
+    scaling = {}
+    for n in (32, 64, 128, 256, 512):
+        _, pcn, stn = make_solver(ch, n, n, precision=0)
+        its = [max(stn.step()["iters"]) for _ in range(10)]
+        scaling[f"{n}x{n}"] = {"iters_per_step_mean_first10": float(np.mean(its)),
+                               "amg_levels_H": [r for r, _ in pcn.levels(1)]}
+        del pcn, stn
+    out["fp64_iters_vs_mesh"] = scaling
+    p3 = ch.Params(dim=3, nx=128, ny=128, nz=32, Lz=0.25, precision=1)
+    sys3 = ch.System(ch.Mesh(p3), p3)
+    pc3 = ch.Precond(sys3)
+    st3 = ch.State(sys3, pc3)
+    st3.init_seeded(0.30, 0.30, 0.01, seed=0)
+    for _ in range(W):
+        st3.step()
+    K3 = min(K, 50)
+    ms3, it3 = timed_steps(torch, ch, st3, K3, flush, barrier)
+    ch.profile_enable(True)
+    ch.profile_read(reset=True)
+    for _ in range(5):
+        flush.zero_()
+        st3.step()
+    torch.cuda.synchronize()
+    prof3 = ch.profile_read(reset=True)
+    ch.profile_enable(False)
+    out["3d_128x128x32_mixed"] = {
+        "workload": "3D [0,1]^2 x [0,0.25], 128x128x32 hexes x 6 Kuhn tetrahedra, phi_p=phi_nfa=0.30+/-0.01 "
+                    "seed 0, FP32 V-cycles in FP64 FGMRES to 1e-8", "nodes": sys3.n, "nnz": sys3.nnz,
+        "steps": K3, "steps_per_s": world * K3 / (ms3 * 1e-3), "ms_per_step": ms3 / K3,
+        "iters_per_step_mean": float(np.mean(it3)), "amg_levels": {"M": [r for r, _ in pc3.levels(0)],
+                                                                    "H": [r for r, _ in pc3.levels(1)]},
+        "top_kernels": top_kernels(prof3)}
+    del st3, pc3, sys3
+    return out
 
 
 def learned_section(torch, ch, nx, K, flush, barrier, world):
@@ -414,12 +464,22 @@ def main():
         ms_b, iters_b = timed_steps(torch, ch, bstate, KB, flush, barrier)
         blaunch = sum(v["launches"] for v in ch.profile_read(reset=True).values())
         worst = max(max(bstate.run_stats(r)["relres"]) for r in range(len(spec)))
+        by_size = {}
+        for r, (nx_r, ny_r, _, _) in enumerate(spec):
+            by_size.setdefault(f"{nx_r}x{ny_r}", []).append(max(bstate.run_stats(r)["iters"]))
+        per_size = {k: {"runs": len(v), "iters_last_step_mean": float(np.mean(v))} for k, v in sorted(by_size.items())}
         batch = {"workload": "64 runs, nx, ny drawn from {64,96,128,192,256}, bases U[0.20,0.45), "
                              "noise +/-0.01, FP32 V-cycles in FP64 FGMRES, one state (disjoint union)",
                  "runs": len(spec), "nodes": bsys.n, "steps": KB,
                  "run_steps_per_s": world * len(spec) * KB / (ms_b * 1e-3), "ms_per_step": ms_b / KB,
-                 "launches_per_step": blaunch / KB, "max_relres_last_step": worst}
+                 "launches_per_step": blaunch / KB, "max_relres_last_step": worst, "per_size": per_size}
         del bstate, bsys, bmesh
+
+    # ---- the other configurations' throughput lines: 32x32 (launch-bound), FGMRES iterations per
+    # step against the mesh size, and the 3D Kuhn-tetrahedra box in the mixed form
+    extra = None
+    if not args.no_extra:
+        extra = extra_sections(torch, ch, np, K, W, flush, barrier, world)
 
     # ---- learned warm start (256 x 256 grid): training, then FP64 / mixed with and without it
     learned = None
@@ -444,7 +504,7 @@ def main():
         "top_kernels": top_kernels(prof64),
         "iters_per_step_mean": float(np.mean(iters)), "iters_per_step_max": int(np.max(iters)),
         "amg_levels": {k: [r for r, _ in v] for k, v in levels.items()},
-        "mixed": mixed, "batch": batch, "learned": learned, "cpu_baseline": cpu,
+        "mixed": mixed, "batch": batch, "learned": learned, "configs": extra, "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

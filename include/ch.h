@@ -213,6 +213,15 @@ ch_status ch_state_run_stats(const ch_state_t* st, int32_t run, ch_step_stats* o
 /* Copy fields to caller device buffers (N fp64 each); any may be NULL.  phi_s = 1 - phi_p - phi_nfa. */
 ch_status ch_state_get(const ch_state_t* st, double* phi_p, double* phi_nfa, double* phi_s,
                        double* mu_p, double* mu_nfa, void* stream);
+/* Checkpoint / resume.  ch_state_save writes the state (phi_p, phi_nfa, mu_p, mu_nfa of every
+ * node, FP64) to a file at `path`: an 8-byte tag "CHSTATE1", the node count and the run count
+ * (int64 each), then the N x 4 values node by node, in the host's byte order.  ch_state_load reads
+ * such a file into a state built on a system of the same node and run counts (CH_ERR_ARG
+ * otherwise, or when the file is missing, truncated or not a state file); the loaded state then
+ * steps exactly as the saved one would (the learned-step history starts afresh).  Both block the
+ * stream; save needs a set state (CH_ERR_STATE). */
+ch_status ch_state_save(const ch_state_t* st, const char* path, void* stream);
+ch_status ch_state_load(ch_state_t* st, const char* path, void* stream);
 /* One time step: loads, right-hand sides, FGMRES + Algorithm 1 for both species with the
  * previous step as initial guess, state update.  stats (host) may be NULL.  On
  * CH_ERR_NOT_CONVERGED the best iterate is stored in the state. */

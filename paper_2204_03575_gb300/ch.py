@@ -114,6 +114,8 @@ _SIGNATURES = {
     "ch_run": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.POINTER(StepStats)]),
     "ch_state_destroy": (None, [_VP]),
     "ch_step_learned": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(StepStats)]),
+    "ch_state_save": (ctypes.c_int, [_VP, ctypes.c_char_p, _VP]),
+    "ch_state_load": (ctypes.c_int, [_VP, ctypes.c_char_p, _VP]),
     "ch_step_guess": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(StepStats)]),
     "ch_ws_nparams": (ctypes.c_int32, []),
     "ch_ws_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_VP)]),
@@ -371,6 +373,14 @@ class State:
         if check:
             _check(status, "ch_step_learned")
         return st.as_dict()
+
+    def save(self, path, stream=None):
+        """Write the state to `path` (ch_state_save)."""
+        _check(lib().ch_state_save(self._h, str(path).encode(), _stream(stream)), "ch_state_save")
+
+    def load(self, path, stream=None):
+        """Read a state written by save() (ch_state_load)."""
+        _check(lib().ch_state_load(self._h, str(path).encode(), _stream(stream)), "ch_state_load")
 
     def state4(self, stream=None):
         """The state as one N x 4 fp64 tensor (phi_p, phi_nfa, mu_p, mu_nfa)."""

@@ -370,6 +370,16 @@ ch_status ch_state_get(const ch_state_t* st, double* phi_p, double* phi_nfa, dou
   return ch::state_get(st, phi_p, phi_nfa, phi_s, mu_p, mu_nfa, S(stream));
 }
 
+ch_status ch_state_save(const ch_state_t* st, const char* path, void* stream) {
+  CH_ARG(st != nullptr && path != nullptr, "NULL argument");
+  return ch::state_save(st, path, S(stream));
+}
+
+ch_status ch_state_load(ch_state_t* st, const char* path, void* stream) {
+  CH_ARG(st != nullptr && path != nullptr, "NULL argument");
+  return ch::state_load(st, path, S(stream));
+}
+
 ch_status ch_step(ch_state_t* st, void* stream, ch_step_stats* stats) {
   CH_ARG(st != nullptr, "state is NULL");
   return ch::state_step(st, S(stream), stats);

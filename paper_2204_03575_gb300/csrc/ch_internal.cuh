@@ -249,6 +249,8 @@ ch_status state_seeded_batch(ch_state_s* S, const double* base_p, const double* 
                              uint64_t seed, cudaStream_t st);
 ch_status state_run_stats(const ch_state_s* S, int run, ch_step_stats* out);
 int state_runs(const ch_state_s* S);
+ch_status state_save(const ch_state_s* S, const char* path, cudaStream_t st);
+ch_status state_load(ch_state_s* S, const char* path, cudaStream_t st);
 ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats);
 }
 

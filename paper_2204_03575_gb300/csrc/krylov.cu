@@ -18,6 +18,9 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cstdio>
+#include <cstring>
+
 #include "ch_internal.cuh"
 
 namespace ch {
@@ -897,6 +900,69 @@ ch_status state_seeded(ch_state_s* S, double p0, double n0, double noise, uint64
                        cudaStream_t st) {
   std::vector<double> bp(S->R, p0), bn(S->R, n0);
   return state_seeded_batch(S, bp.data(), bn.data(), noise, seed, st);
+}
+
+// ---------------------------------------------------------------- checkpoint / resume
+// File: 8-byte magic "CHSTATE1", int64 N, int64 runs, then the N x 4 FP64 state (phi_p, phi_n,
+// mu_p, mu_n per node, node-major), little-endian as the host writes it.
+static const char kStateMagic[8] = {'C', 'H', 'S', 'T', 'A', 'T', 'E', '1'};
+
+ch_status state_save(const ch_state_s* S, const char* path, cudaStream_t st) {
+  if (!S->set) {
+    set_error("state not initialised: nothing to save");
+    return CH_ERR_STATE;
+  }
+  std::vector<double> h((size_t)S->N * 4);
+  CH_CUDA(cudaMemcpyAsync(h.data(), S->x, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  FILE* f = fopen(path, "wb");
+  if (!f) {
+    set_error("cannot open %s for writing", path);
+    return CH_ERR_ARG;
+  }
+  const int64_t hdr[2] = {S->N, S->R};
+  bool ok = fwrite(kStateMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(int64_t), 2, f) == 2 &&
+            fwrite(h.data(), sizeof(double), h.size(), f) == h.size();
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) {
+    set_error("writing %s failed", path);
+    return CH_ERR_ARG;
+  }
+  return CH_OK;
+}
+
+ch_status state_load(ch_state_s* S, const char* path, cudaStream_t st) {
+  FILE* f = fopen(path, "rb");
+  if (!f) {
+    set_error("cannot open %s", path);
+    return CH_ERR_ARG;
+  }
+  char magic[8] = {};
+  int64_t hdr[2] = {0, 0};
+  std::vector<double> h((size_t)S->N * 4);
+  const bool head = fread(magic, 1, 8, f) == 8 && fread(hdr, sizeof(int64_t), 2, f) == 2;
+  if (!head || memcmp(magic, kStateMagic, 8) != 0) {
+    fclose(f);
+    set_error("%s is not a state file", path);
+    return CH_ERR_ARG;
+  }
+  if (hdr[0] != S->N || hdr[1] != S->R) {
+    fclose(f);
+    set_error("%s holds %lld nodes in %lld runs; this state has %d nodes in %d runs", path, (long long)hdr[0],
+              (long long)hdr[1], S->N, S->R);
+    return CH_ERR_ARG;
+  }
+  const bool body = fread(h.data(), sizeof(double), h.size(), f) == h.size();
+  fclose(f);
+  if (!body) {
+    set_error("%s is truncated", path);
+    return CH_ERR_ARG;
+  }
+  CH_CUDA(cudaMemcpyAsync(S->x, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  S->set = true;
+  S->since_set = S->learn_k = 0;
+  return CH_OK;
 }
 
 ch_status state_get(const ch_state_s* S, double* pp, double* pn, double* ps, double* mp, double* mn,
