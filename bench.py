@@ -109,12 +109,29 @@ class Clocks:
         self.p = None
 
     def __enter__(self):
+        # The sampler's start-up (driver / NVML initialisation) must not overlap the timed region:
+        # wait, up to 15 s, for its first sample before returning.
+        import threading
+        self.lines = []
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                                        "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+            return self
+        first = threading.Event()
+
+        def read():
+            for line in self.p.stdout:
+                self.lines.append(line)
+                first.set()
+            first.set()
+
+        self.reader = threading.Thread(target=read, daemon=True)
+        self.reader.start()
+        first.wait(timeout=15.0)
+        self.skip = len(self.lines)  # samples taken before the timed region are not kept
         return self
 
     def __exit__(self, *a):
@@ -122,10 +139,12 @@ class Clocks:
         if self.p is not None:
             self.p.terminate()
             try:
-                self.out, _ = self.p.communicate(timeout=5)
+                self.p.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.p.kill()
-                self.out, _ = self.p.communicate()
+                self.p.wait()
+            self.reader.join(timeout=5)
+            self.out = "".join(self.lines[self.skip:])
 
     def summary(self):
         sm, mx, reasons = [], [], set()
@@ -348,13 +367,23 @@ def main():
         peaks = json.load(open(pk))
     dev = torch.device("cuda", local)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # the first zero_() loads PyTorch's fill kernel (lazy module loading: ~0.25 s on a fresh box);
+    # do it before any timed region, which runs one flush per step
+    flush.zero_()
+    torch.cuda.synchronize()
     K, W = args.steps, max(args.warmup, 0)
 
-    # ---- GPU pre-warm: an idle GPU's first seconds of work ran up to 25% slower on this
-    # pool; steps of a throwaway solver of the same workload bring it to its working state
+    # ---- GPU pre-warm: an idle GPU ramps its clocks over the first fraction of a second; steps of
+    # a throwaway solver of the same workload bring it to its working state before any timing
     if args.prewarm_s > 0:
         import time
-        sysW, pcW, stateW = make_solver(ch, args.nx, args.ny, precision=0)
+        # autotune = 0: the throwaway solver leaves the per-process tuning cache empty, so the timed
+        # solvers' SpMV widths are chosen on the warmed GPU
+        pW = ch.Params(nx=args.nx, ny=args.ny, autotune=0)
+        sysW = ch.System(ch.Mesh(pW), pW)
+        pcW = ch.Precond(sysW)
+        stateW = ch.State(sysW, pcW)
+        stateW.init_seeded(0.33, 0.33, 0.01, seed=0)
         t0 = time.time()
         while time.time() - t0 < args.prewarm_s:
             stateW.step()

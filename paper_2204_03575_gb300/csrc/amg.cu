@@ -13,6 +13,7 @@
 // Smoothing is Chebyshev on D^-1 A over [cheb_lower, 1] * 1.1 rho, rho a power-iteration estimate.  Every set-up sum has a fixed
 // order, so the hierarchy is bitwise reproducible.  V-cycles run in FP64 or FP32 on two
 // right-hand sides at once (the two species share M and H).
+#include <algorithm>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -560,7 +561,9 @@ static void launch_spmv2(int tpr, const Csr<T>& A, const V2* x, V2* y, cudaStrea
 // every candidate on the matrix itself (one warm-up, three timed launches) and keeps the rule's
 // choice unless another is more than 5% faster.  Decisions are cached per process by matrix
 // shape (kind, rows, columns, entries, value size), so rebuilding a hierarchy of the same shape
-// reproduces its choices -- and its floating-point summation order -- exactly.
+// reproduces its choices -- and its floating-point summation order -- exactly.  A process that
+// wants its choices made on a busy GPU builds its first solver with autotune = 0 (nothing is
+// cached then) and tunes afterwards.
 static int tpr_rule(int64_t nnz, int rows) {
   const double avg = rows > 0 ? (double)nnz / rows : 1.0;
   int t = 1;
@@ -587,19 +590,29 @@ static int tune_tpr(int kind, int rows, int cols, int64_t nnz, int tsize, int mo
     cudaGetLastError();
     return rule;
   }
+  // An idle GPU ramps its clocks over the first fraction of a second: warm up on the rule's width,
+  // then time every width in two passes and keep each width's faster pass.
+  for (int r = 0; r < 20; ++r) launch(rule);
+  float t[6];
+  for (int k = 0; k < 6; ++k) t[k] = 1e30f;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int k = 0, tpr = 1; k < 6; ++k, tpr *= 2) {
+      launch(tpr);
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 3; ++r) launch(tpr);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 1e30f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t[k] = std::min(t[k], ms);
+    }
+  }
   float best = 1e30f, t_rule = 1e30f;
   int pick = rule;
-  for (int tpr = 1; tpr <= 32; tpr *= 2) {
-    launch(tpr);
-    cudaEventRecord(e0, st);
-    for (int r = 0; r < 3; ++r) launch(tpr);
-    cudaEventRecord(e1, st);
-    cudaEventSynchronize(e1);
-    float ms = 1e30f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (tpr == rule) t_rule = ms;
-    if (ms < best) {
-      best = ms;
+  for (int k = 0, tpr = 1; k < 6; ++k, tpr *= 2) {
+    if (tpr == rule) t_rule = t[k];
+    if (t[k] < best) {
+      best = t[k];
       pick = tpr;
     }
   }
