@@ -82,7 +82,8 @@ typedef struct ch_params {
   int32_t autotune;          /* SpMV lanes per row: 0 = fixed rule, 1 = timed at set-up (cached per process), default 1 */
   double cheb_lower;         /* Chebyshev interval [cheb_lower, 1] x 1.1 lambda_max(D^-1 A), default 0.3 */
   int32_t graphs;            /* 1: replay each Arnoldi step as a captured CUDA graph; 0: direct launches; default 1 */
-  int32_t cheb_degree_coarse; /* Chebyshev steps on the levels below the finest; 0 (default): cheb_degree */
+  int32_t cheb_degree_coarse; /* Chebyshev steps on the levels below the finest; 0 (default): 2 for FP64
+                                V-cycles (at most cheb_degree), cheb_degree for FP32 */
 } ch_params;
 
 /* Per-step statistics (host struct). */

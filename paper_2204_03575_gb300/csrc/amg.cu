@@ -751,7 +751,12 @@ ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precisi
   Hierarchy* h = new Hierarchy();
   h->precision = precision;
   h->cheb_degree = p.cheb_degree;
-  h->cheb_degree_coarse = p.cheb_degree_coarse > 0 ? p.cheb_degree_coarse : p.cheb_degree;
+  // cheb_degree_coarse 0: degree 2 below the finest level for FP64 V-cycles (measured on 512 x 512:
+  // ~9 % less time per iteration, ~6 % more iterations: +4 % steps/s), cheb_degree for FP32 (there
+  // the same trade loses 1 %)
+  h->cheb_degree_coarse = p.cheb_degree_coarse > 0 ? p.cheb_degree_coarse
+                          : precision == 0          ? std::min(2, p.cheb_degree)
+                                                    : p.cheb_degree;
   h->autotune = p.autotune;
   h->cheb_lower = p.cheb_lower;
   h->A.push_back(A0);
