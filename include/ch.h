@@ -131,7 +131,10 @@ void ch_mesh_destroy(ch_mesh_t* m);
 
 /* ---------------------------------------------------------------- assembly (Section 3)
  * P1 mass M and stiffness K ("standard ... with appropriate constants", below Eq. (12)) in
- * one shared CSR pattern (sorted column indices), and H = a K + sqrt(c) M, on the device. */
+ * one shared CSR pattern (sorted column indices), and H = a K + sqrt(c) M, on the device.
+ * The system also holds a scratch for the explicit loads (one entry per element vertex):
+ * calls that use one system -- ch_loads, ch_rhs and the steps of states built on it -- must
+ * not overlap on the GPU. */
 ch_status ch_assemble(const ch_mesh_t* m, const ch_params* p, void* stream, ch_system_t** out);
 ch_status ch_system_info(const ch_system_t* s, int64_t* n, int64_t* nnz);   /* host outputs */
 /* copies to caller device buffers (rowptr N+1, col nnz int32; values nnz fp64); any may be NULL */

@@ -334,6 +334,7 @@ ch_status assemble_system(const ch_mesh_s* m, ch_system_s* s, cudaStream_t st) {
   CH_TRY(s->mem.get(&s->valM, (size_t)nnz));
   CH_TRY(s->mem.get(&s->valK, (size_t)nnz));
   CH_TRY(s->mem.get(&s->valH, (size_t)nnz));
+  CH_TRY(s->mem.get(&s->eload, (size_t)m->E * (d + 1) * 2));
   CH_TRY(s->mem.get(&s->diag, (size_t)N));
   k_pattern<<<blocks_for(N), TPB, 0, st>>>(m->elems, d + 1, m->n2e_ptr, m->n2e, N, s->rowptr,
                                             nullptr, s->col, overflow);
@@ -369,14 +370,9 @@ ch_status assemble_system(const ch_mesh_s* m, ch_system_s* s, cudaStream_t st) {
 // and with (a, b, lambda_i) on a facet of dimension d-1
 //   int a b lambda_i = (d-1)!|F|/(d+2)! [ <a><b> + <ab> + a_i<b> + b_i<a> + 2 a_i b_i ],
 // where <x> is the sum of x over the simplex's vertices.
-__device__ __forceinline__ double int_pqq_li(double Sp, double Sq, double Spq, double Sqq,
-                                             double Spqq, double pi, double qi) {
-  return Sp * Sq * Sq + 2.0 * Spq * Sq + Sqq * Sp + 2.0 * Spqq + pi * (Sq * Sq + Sqq) +
-         2.0 * qi * (Sp * Sq + Spq) + 4.0 * pi * qi * Sq + 2.0 * qi * qi * Sp + 6.0 * pi * qi * qi;
-}
 
 struct MeshPod {
-  int dim, N;
+  int dim, N, E;
   const double* coords;
   const int* elems;
   const int* bot;
@@ -391,6 +387,7 @@ static MeshPod mesh_pod(const ch_mesh_s* s) {
   MeshPod v;
   v.dim = s->dim;
   v.N = s->N;
+  v.E = s->E;
   v.coords = s->coords;
   v.elems = s->elems;
   v.bot = s->bot;
@@ -414,41 +411,71 @@ struct LoadCoef {
   double gp, gn, hp, hn, kev;
 };
 
+// Per element e and vertex a, eload[(e (D+1) + a) 2 + {0, 1}] = |T| (7 int p q^2 l_a - 0.2 int phi_s l_a)
+// / |T| and the same with p and q exchanged (Eq. (15)'s f' for polymer and NFA against the hat
+// function of vertex a).  The vertex sums are formed once per element; int_pqq_li's terms that do
+// not involve the vertex (A, B, C below) are element constants (the closed form above).
 template <int D>
-__device__ void node_loads(const MeshPod& m, const LoadCoef& L, const double* pp,
-                           const double* pn, int ld, int v, double* Fp, double* Fn, double* Gp,
-                           double* Gn) {
+__global__ void k_elem_loads(const MeshPod m, LoadCoef L, const double* pp, const double* pn, int ld,
+                             double* __restrict__ eload) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
   constexpr double c4 = (D == 2) ? 1.0 / 360.0 : 1.0 / 840.0;  // d!/(d+4)!
   constexpr double c2 = 1.0 / ((D + 1) * (D + 2));             // int lambda_a lambda_i / |T|, a != i
+  const int* ev = m.elems + (D + 1) * e;
+  double P[D + 1], Q[D + 1];
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    P[a] = pp[(size_t)ld * ev[a]];
+    Q[a] = pn[(size_t)ld * ev[a]];
+  }
+  double Sp = 0, Sq = 0, Spq = 0, Spp = 0, Sqq = 0, Spqq = 0, Sppq = 0;
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    Sp += P[a];
+    Sq += Q[a];
+    const double pq = P[a] * Q[a];
+    Spq += pq;
+    Spp += P[a] * P[a];
+    Sqq += Q[a] * Q[a];
+    Spqq += pq * Q[a];
+    Sppq += pq * P[a];
+  }
+  // int p q^2 l_i / (c4 |T|) = A + p_i B + q_i (C + 2 q_i Sp) + p_i q_i (4 Sq + 6 q_i), and the
+  // same with p and q exchanged (C is symmetric)
+  const double Ap = Sp * Sq * Sq + 2.0 * Spq * Sq + Sqq * Sp + 2.0 * Spqq, Bp = Sq * Sq + Sqq;
+  const double An = Sq * Sp * Sp + 2.0 * Spq * Sp + Spp * Sq + 2.0 * Sppq, Bn = Sp * Sp + Spp;
+  const double C = 2.0 * (Sp * Sq + Spq);
+  const double vol = m.vol[e];
+  const double ss = (D + 1) - Sp - Sq;  // sum of phi_s over the vertices
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    const double pi = P[a], qi = Q[a];
+    const double Ip = c4 * (Ap + pi * Bp + qi * (C + 2.0 * qi * Sp) + pi * qi * (4.0 * Sq + 6.0 * qi));
+    const double In = c4 * (An + qi * Bn + pi * (C + 2.0 * pi * Sq) + qi * pi * (4.0 * Sp + 6.0 * pi));
+    const double Is = c2 * (ss + (1.0 - pi - qi));  // int phi_s lambda_i / |T|
+    double2 out;
+    out.x = vol * (L.cubic * Ip - L.cs * Is);
+    out.y = vol * (L.cubic * In - L.cs * Is);
+    reinterpret_cast<double2*>(eload)[(size_t)e * (D + 1) + a] = out;
+  }
+}
+
+template <int D>
+__device__ void node_loads(const MeshPod& m, const LoadCoef& L, const double* __restrict__ eload,
+                           const double* pp, const double* pn, int ld, int v, double* Fp, double* Fn,
+                           double* Gp, double* Gn) {
   double fp = 0.0, fn = 0.0;
-  for (int q = m.n2e_ptr[v]; q < m.n2e_ptr[v + 1]; ++q) {
+  for (int q = m.n2e_ptr[v]; q < m.n2e_ptr[v + 1]; ++q) {  // incident elements in a fixed order
     const int e = m.n2e[q];
     const int* ev = m.elems + (D + 1) * e;
-    double P[D + 1], Q[D + 1];
     int li = 0;
-    for (int a = 0; a <= D; ++a) {
-      P[a] = pp[(size_t)ld * ev[a]];
-      Q[a] = pn[(size_t)ld * ev[a]];
+#pragma unroll
+    for (int a = 0; a <= D; ++a)
       if (ev[a] == v) li = a;
-    }
-    double Sp = 0, Sq = 0, Spq = 0, Spp = 0, Sqq = 0, Spqq = 0, Sppq = 0;
-    for (int a = 0; a <= D; ++a) {
-      Sp += P[a];
-      Sq += Q[a];
-      const double pq = P[a] * Q[a];
-      Spq += pq;
-      Spp += P[a] * P[a];
-      Sqq += Q[a] * Q[a];
-      Spqq += pq * Q[a];
-      Sppq += pq * P[a];
-    }
-    const double vol = m.vol[e];
-    const double Ip = c4 * int_pqq_li(Sp, Sq, Spq, Sqq, Spqq, P[li], Q[li]);  // int p q^2 l_i / |T|
-    const double In = c4 * int_pqq_li(Sq, Sp, Spq, Spp, Sppq, Q[li], P[li]);  // int q p^2 l_i / |T|
-    // int phi_s lambda_i / |T| with phi_s = 1 - p - q: (sum_a s_a + s_i) / ((d+1)(d+2))
-    const double Is = c2 * (((D + 1) - Sp - Sq) + (1.0 - P[li] - Q[li]));
-    fp += vol * (L.cubic * Ip - L.cs * Is);
-    fn += vol * (L.cubic * In - L.cs * Is);
+    const double2 c = reinterpret_cast<const double2*>(eload)[(size_t)e * (D + 1) + li];
+    fp += c.x;
+    fn += c.y;
   }
   *Fp = fp;
   *Fn = fn;
@@ -514,12 +541,12 @@ static LoadCoef load_coef(const ch_params& p) {
 }
 
 template <int D>
-__global__ void k_loads(const MeshPod m, LoadCoef L, const double* pp, const double* pn,
-                        int ld, double* Fp, double* Fn, double* Gp, double* Gn) {
+__global__ void k_loads(const MeshPod m, LoadCoef L, const double* eload, const double* pp,
+                        const double* pn, int ld, double* Fp, double* Fn, double* Gp, double* Gn) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= m.N) return;
   double a, b, c, d;
-  node_loads<D>(m, L, pp, pn, ld, v, &a, &b, &c, &d);
+  node_loads<D>(m, L, eload, pp, pn, ld, v, &a, &b, &c, &d);
   if (Fp) Fp[v] = a;
   if (Fn) Fn[v] = b;
   if (Gp) Gp[v] = c;
@@ -528,13 +555,13 @@ __global__ void k_loads(const MeshPod m, LoadCoef L, const double* pp, const dou
 
 // b (N x 4) = (M phi_p + tau g_p, M phi_n + tau g_n, -c F_p, -c F_n)   (Eq. (13) -> Eq. (14))
 template <int D>
-__global__ void k_rhs(const MeshPod m, LoadCoef L, const int* rowptr, const int* col,
-                      const double* valM, const double* pp, const double* pn, int ld,
+__global__ void k_rhs(const MeshPod m, LoadCoef L, const double* eload, const int* rowptr,
+                      const int* col, const double* valM, const double* pp, const double* pn, int ld,
                       double tau, double c, double* b) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= m.N) return;
   double Fp, Fn, Gp, Gn;
-  node_loads<D>(m, L, pp, pn, ld, v, &Fp, &Fn, &Gp, &Gn);
+  node_loads<D>(m, L, eload, pp, pn, ld, v, &Fp, &Fn, &Gp, &Gn);
   double mp = 0.0, mn = 0.0;
   for (int q = rowptr[v]; q < rowptr[v + 1]; ++q) {
     const int j = col[q];
@@ -549,15 +576,29 @@ __global__ void k_rhs(const MeshPod m, LoadCoef L, const int* rowptr, const int*
   reinterpret_cast<double4_32a*>(b)[v] = out;
 }
 
+// Per-element load contributions into s->eload (the system's scratch: calls on one system must
+// not overlap on the GPU).  Algorithmic bytes: the vertex values gathered, element indices and
+// measures, the contributions written.
+static void elem_loads(const ch_system_s* s, const MeshPod& m, const LoadCoef& L, const double* pp,
+                       const double* pn, int ld, cudaStream_t st) {
+  const double E = m.E, d1 = m.dim + 1;
+  ProfScope ps(st, K_ELEM_LOADS, 0, E * (d1 * (4.0 + 16.0) + 8.0 + 16.0 * d1), E * (22.0 + 12.0 * d1));
+  if (m.dim == 2)
+    k_elem_loads<2><<<blocks_for(m.E), TPB, 0, st>>>(m, L, pp, pn, ld, s->eload);
+  else
+    k_elem_loads<3><<<blocks_for(m.E), TPB, 0, st>>>(m, L, pp, pn, ld, s->eload);
+}
+
 ch_status loads(const ch_system_s* s, const double* pp, const double* pn, double* Fp, double* Fn,
                 double* gp, double* gn, cudaStream_t st) {
   const MeshPod m = mesh_pod(s->mesh);
   const LoadCoef L = load_coef(s->p);
+  elem_loads(s, m, L, pp, pn, 1, st);
   ProfScope ps(st, K_LOADS, 0, 16.0 * m.N + 32.0 * m.N, 0.0);
   if (m.dim == 2)
-    k_loads<2><<<blocks_for(m.N), TPB, 0, st>>>(m, L, pp, pn, 1, Fp, Fn, gp, gn);
+    k_loads<2><<<blocks_for(m.N), TPB, 0, st>>>(m, L, s->eload, pp, pn, 1, Fp, Fn, gp, gn);
   else
-    k_loads<3><<<blocks_for(m.N), TPB, 0, st>>>(m, L, pp, pn, 1, Fp, Fn, gp, gn);
+    k_loads<3><<<blocks_for(m.N), TPB, 0, st>>>(m, L, s->eload, pp, pn, 1, Fp, Fn, gp, gn);
   CH_LAUNCHED();
   return CH_OK;
 }
@@ -566,15 +607,17 @@ ch_status rhs_strided(const ch_system_s* s, const double* pp, const double* pn, 
                       cudaStream_t st) {
   const MeshPod m = mesh_pod(s->mesh);
   const LoadCoef L = load_coef(s->p);
+  elem_loads(s, m, L, pp, pn, ld, st);
   const double E = s->mesh->E, d1 = m.dim + 1;
-  // phi read + b written + M (values, columns, row pointers) + elements, measures, incidence
-  ProfScope ps(st, K_RHS, 0, 48.0 * m.N + 12.0 * s->nnz + 4.0 * m.N + E * (8.0 * d1 + 8.0),
-               2.0 * s->nnz + 30.0 * E * d1);
+  // phi read + b written + M (values, columns, row pointers) + incidence and the element
+  // contributions gathered
+  ProfScope ps(st, K_RHS, 0, 48.0 * m.N + 12.0 * s->nnz + 4.0 * m.N + E * d1 * (4.0 + 4.0 + 16.0),
+               2.0 * s->nnz);
   if (m.dim == 2)
-    k_rhs<2><<<blocks_for(m.N), TPB, 0, st>>>(m, L, s->rowptr, s->col, s->valM, pp, pn, ld,
+    k_rhs<2><<<blocks_for(m.N), TPB, 0, st>>>(m, L, s->eload, s->rowptr, s->col, s->valM, pp, pn, ld,
                                                s->p.tau, s->c, b);
   else
-    k_rhs<3><<<blocks_for(m.N), TPB, 0, st>>>(m, L, s->rowptr, s->col, s->valM, pp, pn, ld,
+    k_rhs<3><<<blocks_for(m.N), TPB, 0, st>>>(m, L, s->eload, s->rowptr, s->col, s->valM, pp, pn, ld,
                                                s->p.tau, s->c, b);
   CH_LAUNCHED();
   return CH_OK;

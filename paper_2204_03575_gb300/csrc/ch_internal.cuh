@@ -118,7 +118,7 @@ enum KernelId {
   K_COARSE, K_VLOAD, K_VSTORE, K_SPMV_M, K_STATE_IO,
   // the same V-cycle kernels on levels below the finest (accounted separately)
   K_CHEB_FIRST_C, K_CHEB_STEP_C, K_VRESIDUAL_C, K_RESTRICT_C, K_PROLONG_C,
-  K_WS_CONV, K_WS_IO, K_GUESS, K_COUNT
+  K_WS_CONV, K_WS_IO, K_GUESS, K_ELEM_LOADS, K_COUNT
 };
 // RAII around one kernel launch: counts it with its algorithmic bytes / FMAs and, when timing
 // is on, records CUDA events around it on the launching stream.
@@ -182,6 +182,7 @@ struct ch_system_s {
   double* valK = nullptr;
   double* valH = nullptr;
   int* diag = nullptr;  // position of the diagonal entry of each row
+  double* eload = nullptr;  // E x (dim+1) x 2: per element and vertex, the f-load contributions
   double a = 0, c = 0;  // A = [[M, aK], [aK, -cM]]
   ch::Alloc mem;
 };
