@@ -1018,6 +1018,24 @@ __global__ void __launch_bounds__(TPB) k_spmv2_dia(Dia<T> D, int n, const V2* __
     default: { constexpr int NDC = 15; KCALL; } break; \
   }
 
+// b_c = R r, fused with the coarse level's first Chebyshev step from a zero guess (pointwise:
+// x_c = d_c = invtheta D_c^-1 b_c, the arithmetic of k_cheb_first): one launch instead of two.
+template <typename T, typename V2, int TPR>
+__global__ void __launch_bounds__(TPB) k_restrict_first(Csr<T> R, const V2* __restrict__ r, V2* __restrict__ bc,
+                                                        const T* __restrict__ dinv_c, T invtheta,
+                                                        V2* __restrict__ xc, V2* __restrict__ dc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / TPR, sub = t % TPR;
+  T s0, s1;
+  row_sum<T, V2, TPR>(R, i, sub, r, s0, s1);
+  if (i >= R.nrows || sub != 0) return;
+  bc[i] = mk2<T, V2>(s0, s1);
+  const T s = invtheta * dinv_c[i];
+  const V2 v = mk2<T, V2>(s * s0, s * s1);
+  xc[i] = v;
+  dc[i] = v;
+}
+
 #define CH_TPR_DISPATCH(tpr, KCALL)                      \
   switch (tpr) {                                         \
     case 1: { constexpr int TPRC = 1; KCALL; } break;    \
@@ -1127,7 +1145,9 @@ static ChebCoef cheb_coef(double rho, int deg, double lower) {
 }
 
 template <typename T_>
-static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, bool zero_guess,
+// zero_guess: 0 continue from *xcur; 1 start from zero (the first step is pointwise); 2 start from
+// zero with that first step already taken by the caller (fused into the restriction)
+static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, int zero_guess,
                         typename V2T<T_>::t** xcur, cudaStream_t st) {
   using V2 = typename V2T<T_>::t;
   const int n = L.A.nrows;
@@ -1137,9 +1157,11 @@ static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, bool zero_guess,
   V2* other = (x == L.x) ? L.x2 : L.x;
   int s0 = 0;
   const double T = sizeof(T_), nnz = (double)L.A.nnz;
-  if (zero_guess) {
+  if (zero_guess == 1) {
     ProfScope ps(st, l == 0 ? K_CHEB_FIRST : K_CHEB_FIRST_C, sizeof(T_) == 4, 7.0 * T * n, 2.0 * n);
     k_cheb_first<T_, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.dinv, L.b, (T_)c.invtheta, x, L.d);
+    s0 = 1;
+  } else if (zero_guess == 2) {
     s0 = 1;
   }
   // operator bytes: CSR values + column indices + row pointers, or the diagonals' values
@@ -1159,7 +1181,7 @@ static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, bool zero_guess,
 // one V-cycle at level l on L[l].b; result in *xres (L[l].x or L[l].x2)
 template <typename T>
 static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv, int l,
-                        bool zero_guess, typename V2T<T>::t** xres, cudaStream_t st) {
+                        int zero_guess, typename V2T<T>::t** xres, cudaStream_t st) {
   using V2 = typename V2T<T>::t;
   LevelT<T>& L = Ls[l];
   const int n = L.A.nrows;
@@ -1180,21 +1202,31 @@ static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv,
     ProfScope ps(st, l == 0 ? K_VRESIDUAL : K_VRESIDUAL_C, sizeof(T) == 4, opb + 6.0 * Tb * n, 2.0 * L.A.nnz);
     launch_residual<T, V2>(L.tprA, L.A, L.b, x, L.r, st, &L.dia);
   }
+  const bool fuse = l + 1 < h->nlev - 1;  // the coarse level smooths: fuse its first step
   {
     ProfScope ps(st, l == 0 ? K_RESTRICT : K_RESTRICT_C, sizeof(T) == 4,
-                 L.R.nnz * (4 + Tb) + 4.0 * (nc + 1) + 2.0 * Tb * (n + nc), 2.0 * L.R.nnz);
-    launch_spmv2<T, V2, false>(L.tprR, L.R, L.r, C.b, st);
+                 L.R.nnz * (4 + Tb) + 4.0 * (nc + 1) + 2.0 * Tb * (n + nc) + (fuse ? 5.0 * Tb * nc : 0.0),
+                 2.0 * L.R.nnz + (fuse ? 2.0 * nc : 0.0));
+    if (fuse) {
+      const int degc = h->cheb_degree_coarse;
+      const ChebCoef cc = cheb_coef(h->rho[l + 1], degc, h->cheb_lower);
+      const int g = blocks_for((int64_t)L.R.nrows * L.tprR);
+      CH_TPR_DISPATCH(L.tprR, (k_restrict_first<T, V2, TPRC><<<g, TPB, 0, st>>>(
+                                  L.R, L.r, C.b, C.dinv, (T)cc.invtheta, C.x, C.d)));
+    } else {
+      launch_spmv2<T, V2, false>(L.tprR, L.R, L.r, C.b, st);
+    }
   }
   CH_LAUNCHED();
   V2* xc = C.x;
-  CH_TRY(vcycle<T>(h, Ls, cinv, l + 1, true, &xc, st));
+  CH_TRY(vcycle<T>(h, Ls, cinv, l + 1, fuse ? 2 : 1, &xc, st));
   {
     ProfScope ps(st, l == 0 ? K_PROLONG : K_PROLONG_C, sizeof(T) == 4,
                  L.P.nnz * (4 + Tb) + 4.0 * (n + 1) + 2.0 * Tb * nc + 4.0 * Tb * n, 2.0 * L.P.nnz);
     launch_spmv2<T, V2, true>(L.tprP, L.P, xc, x, st);
   }
   CH_LAUNCHED();
-  CH_TRY(smooth<T>(h, L, l, false, &x, st));
+  CH_TRY(smooth<T>(h, L, l, 0, &x, st));
   *xres = x;
   return CH_OK;
 }
