@@ -575,7 +575,25 @@ static ch_status make_segments(ch_state_s* S, cudaStream_t st) {
   const std::vector<int>& off = S->sys->mesh->run_off;
   const int R = S->R;
   const int64_t N = S->N;
-  const int64_t npb = std::max<int64_t>(TPB, (N + ORTH_BLOCKS - 1) / ORTH_BLOCKS);
+  // Nodes per block: every block owns nodes of one run, so each run's count rounds up.  Take the
+  // smallest size at which the rounded total still fits ORTH_BLOCKS (one wave of the segmented
+  // kernels at two blocks per SM; a few blocks more made a second, nearly empty wave that left the
+  // SMs ~30 % idle on the 64-run batch), or one block per run when there are more runs than that.
+  auto blocks_at = [&](int64_t npb) {
+    int64_t nb = 0;
+    for (int r = 0; r < R; ++r) nb += std::max<int64_t>(1, (off[r + 1] - off[r] + npb - 1) / npb);
+    return nb;
+  };
+  int64_t npb = std::max<int64_t>(TPB, (N + ORTH_BLOCKS - 1) / ORTH_BLOCKS);
+  if (blocks_at(npb) > ORTH_BLOCKS) {
+    int64_t lo_n = npb, hi_n = std::max<int64_t>(npb, N);  // blocks_at(hi_n) == R
+    while (lo_n < hi_n) {
+      const int64_t mid = lo_n + (hi_n - lo_n) / 2;
+      if (blocks_at(mid) <= ORTH_BLOCKS) hi_n = mid;
+      else lo_n = mid + 1;
+    }
+    npb = lo_n;
+  }
   std::vector<int> run, lo, hi, first(R + 1, 0);
   for (int r = 0; r < R; ++r) {
     const int64_t n = off[r + 1] - off[r];

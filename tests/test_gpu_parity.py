@@ -331,6 +331,23 @@ def test_graph_replay_matches_direct_launches(lib):
             np.testing.assert_array_equal(ga[k], gb[k])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_parallel_m_branch_matches_serial_algorithm1(lib, precision):
+    """Algorithm 1's M solve runs as a parallel branch of the H solves, except under per-launch
+    event timing, which keeps one stream: both give bitwise the same steps."""
+    a = run_pair(lib, 2, nx=48, ny=40, precision=precision)[1]
+    lib.profile_enable(True)
+    try:
+        b = run_pair(lib, 2, nx=48, ny=40, precision=precision)[1]
+    finally:
+        lib.profile_enable(False)
+        lib.profile_read(reset=True)
+    for (sa, ga, _, _), (sb, gb, _, _) in zip(a, b):
+        assert sa["iters"] == sb["iters"]
+        for k in ga:
+            np.testing.assert_array_equal(ga[k], gb[k])
+
+
 def test_bitwise_reproducible(lib):
     a = run_pair(lib, 2, nx=64, ny=64)[1]
     b = run_pair(lib, 2, nx=64, ny=64)[1]
