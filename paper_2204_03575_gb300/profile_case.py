@@ -1,6 +1,7 @@
 """A bounded solver run for profilers: one mesh, one state, a few time steps.
 
     python -m paper_2204_03575_gb300.profile_case --nx 1024 --ny 1024 --steps 1 --restart 10
+    python -m paper_2204_03575_gb300.profile_case --batch 64 --precision 1 --restart 30 --warmup 0 --steps 2
 
 Builds the mesh, system, preconditioner and state on cuda:0 (seeded initial state, paper
 parameters), runs the warm-up and timed steps and prints per-step statistics.  Used as the
@@ -23,6 +24,8 @@ def main():
     ap.add_argument("--restart", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead of one mesh: this many runs of inputs.batch_runs(n, seed=0)")
     a = ap.parse_args()
     import torch
     from paper_2204_03575_gb300 import ch
@@ -30,11 +33,21 @@ def main():
     kw = dict(nx=a.nx, ny=a.ny, precision=a.precision, restart=a.restart)
     if a.nz:
         kw.update(dim=3, nz=a.nz, Lz=a.nz / a.nx)
-    p = ch.Params(**kw)
-    system = ch.System(ch.Mesh(p), p)
-    pc = ch.Precond(system)
-    state = ch.State(system, pc)
-    state.init_seeded(0.33, 0.33, 0.01, seed=0)
+    if a.batch:
+        from paper_2204_03575_gb300 import inputs
+        spec = inputs.batch_runs(a.batch, seed=0)
+        p = ch.Params(precision=a.precision, restart=a.restart)
+        mesh = ch.Mesh(p, runs=[ch.Params(nx=nx, ny=ny) for nx, ny, _, _ in spec])
+        system = ch.System(mesh, p)
+        pc = ch.Precond(system)
+        state = ch.State(system, pc)
+        state.init_seeded_batch([x[2] for x in spec], [x[3] for x in spec], 0.01, seed=0)
+    else:
+        p = ch.Params(**kw)
+        system = ch.System(ch.Mesh(p), p)
+        pc = ch.Precond(system)
+        state = ch.State(system, pc)
+        state.init_seeded(0.33, 0.33, 0.01, seed=0)
     for _ in range(a.warmup):
         state.step()
     for k in range(a.steps):
