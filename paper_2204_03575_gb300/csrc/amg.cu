@@ -29,16 +29,27 @@ template <typename T> struct V2T;
 template <> struct V2T<double> { using t = double2; };
 template <> struct V2T<float> { using t = float2; };
 
-// Fine-level operator of a structured mesh as diagonals: row i's neighbours sit at i + off[d]
-// (offsets ascending); val[d * n + i] is zero where row i has no such neighbour (the clamped
-// column index is then read but multiplied by zero).
-constexpr int kDiaSlots = 16;
+// Fine-level operator of a uniform mesh as diagonals: row i's neighbours sit at i + lat_off(d),
+// the lattice directions a + b W + c WH (W, WH: the row's run's strides), ascending in d for any
+// W, H >= 2, i.e. in CSR column order; val[d * n + i] is zero where row i has no such neighbour
+// (the clamped column index is then read but multiplied by zero).
 template <typename T>
 struct Dia {
-  int nd = 0;  // 0: not structured, use the CSR form
-  int off[kDiaSlots] = {};
+  int nd = 0;                      // 7 (2D) or 15 (3D); 0: not structured, use the CSR form
+  int W = 0, WH = 0;               // strides of a single-run mesh
+  const int* node_run = nullptr;   // several runs: run of each row ...
+  const int2* run_wh = nullptr;    // ... and (W, WH) of each run
   T* val = nullptr;
 };
+
+// direction d of the 2D (7: uniform triangles) or 3D (15: Kuhn tetrahedra) lattice stencil
+__host__ __device__ __forceinline__ int lat_off(int nd, int d, int W, int WH) {
+  constexpr int a2[7] = {-1, 0, -1, 0, 1, 0, 1}, b2[7] = {-1, -1, 0, 0, 0, 1, 1};
+  constexpr int a3[15] = {-1, 0, -1, 0, -1, 0, -1, 0, 1, 0, 1, 0, 1, 0, 1};
+  constexpr int b3[15] = {-1, -1, 0, 0, -1, -1, 0, 0, 0, 1, 1, 0, 0, 1, 1};
+  constexpr int c3[15] = {-1, -1, -1, -1, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1};
+  return nd == 7 ? a2[d] + b2[d] * W : a3[d] + b3[d] * W + c3[d] * WH;
+}
 
 template <typename T>
 struct LevelT {
@@ -654,32 +665,62 @@ static ch_status autotune_levels(Hierarchy* h, std::vector<LevelT<T>>& L, int mo
 __global__ void k_csr_to_dia(Csr<double> A, Dia<double> D) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.nrows) return;
+  int W = D.W, WH = D.WH;
+  if (D.node_run) {
+    const int2 w = D.run_wh[D.node_run[i]];
+    W = w.x;
+    WH = w.y;
+  }
   for (int q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
     const int o = A.col[q] - i;
     for (int d = 0; d < D.nd; ++d)
-      if (D.off[d] == o) D.val[(size_t)d * A.nrows + i] = A.val[q];
+      if (lat_off(D.nd, d, W, WH) == o) D.val[(size_t)d * A.nrows + i] = A.val[q];
   }
 }
 
-// The diagonal form of A when its pattern has exactly 7 (uniform 2D triangles) or 15 (uniform 3D
-// Kuhn tetrahedra) distinct column offsets (a host scan of the pattern at set-up); else nd = 0.
-static ch_status dia_build(const Csr<double>& A, Alloc& mem, Dia<double>* out, cudaStream_t st) {
+// The diagonal form of A when every stored entry of every row lies on the lattice stencil of its
+// run (checked on the host from the pattern at set-up); else nd = 0 and the level stays CSR.
+static ch_status dia_build(const Csr<double>& A, const FineLattice* lat, Alloc& mem, Dia<double>* out,
+                           cudaStream_t st) {
   out->nd = 0;
-  const int n = A.nrows;
+  if (!lat || (lat->dim != 2 && lat->dim != 3)) return CH_OK;
+  const int n = A.nrows, R = (int)lat->W.size();
+  if (R < 1 || (int)lat->run_off.size() != R + 1 || lat->run_off[R] != n) return CH_OK;
+  const int nd = lat->dim == 2 ? 7 : 15;
   std::vector<int> rp(n + 1), col((size_t)A.nnz);
   CH_CUDA(cudaMemcpyAsync(rp.data(), A.rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, st));
   CH_CUDA(cudaMemcpyAsync(col.data(), A.col, sizeof(int) * (size_t)A.nnz, cudaMemcpyDeviceToHost, st));
   CH_CUDA(cudaStreamSynchronize(st));
-  std::set<int> offs;
-  for (int i = 0; i < n && (int)offs.size() <= kDiaSlots; ++i)
-    for (int q = rp[i]; q < rp[i + 1]; ++q) offs.insert(col[q] - i);
-  if (offs.size() != 7 && offs.size() != 15) return CH_OK;
+  for (int r = 0; r < R; ++r) {
+    const int W = lat->W[r], WH = lat->WH[r];
+    if (W < 2 || WH < 2 * W) return CH_OK;
+    int offs[15];
+    for (int d = 0; d < nd; ++d) offs[d] = lat_off(nd, d, W, WH);
+    for (int i = lat->run_off[r]; i < lat->run_off[r + 1]; ++i)
+      for (int q = rp[i]; q < rp[i + 1]; ++q) {
+        const int o = col[q] - i;
+        bool on = false;
+        for (int d = 0; d < nd && !on; ++d) on = offs[d] == o;
+        if (!on) return CH_OK;
+      }
+  }
   Dia<double> D;
-  D.nd = (int)offs.size();
-  int k = 0;
-  for (int o : offs) D.off[k++] = o;  // ascending: the CSR column order of every row
-  CH_TRY(mem.get(&D.val, (size_t)D.nd * n));
-  CH_CUDA(cudaMemsetAsync(D.val, 0, sizeof(double) * (size_t)D.nd * n, st));
+  D.nd = nd;
+  if (R == 1) {
+    D.W = lat->W[0];
+    D.WH = lat->WH[0];
+  } else {
+    std::vector<int2> wh(R);
+    for (int r = 0; r < R; ++r) wh[r] = make_int2(lat->W[r], lat->WH[r]);
+    int2* d_wh = nullptr;
+    CH_TRY(mem.get(&d_wh, (size_t)R));
+    CH_CUDA(cudaMemcpyAsync(d_wh, wh.data(), sizeof(int2) * R, cudaMemcpyHostToDevice, st));
+    CH_CUDA(cudaStreamSynchronize(st));  // wh is a host temporary
+    D.node_run = lat->node_run;
+    D.run_wh = d_wh;
+  }
+  CH_TRY(mem.get(&D.val, (size_t)nd * n));
+  CH_CUDA(cudaMemsetAsync(D.val, 0, sizeof(double) * (size_t)nd * n, st));
   k_csr_to_dia<<<blocks_for(n), TPB, 0, st>>>(A, D);
   CH_LAUNCHED();
   *out = D;
@@ -687,7 +728,7 @@ static ch_status dia_build(const Csr<double>& A, Alloc& mem, Dia<double>* out, c
 }
 
 template <typename T>
-static ch_status make_working(Hierarchy* h, std::vector<LevelT<T>>& L, cudaStream_t st) {
+static ch_status make_working(Hierarchy* h, const FineLattice* lat, std::vector<LevelT<T>>& L, cudaStream_t st) {
   using V2 = typename V2T<T>::t;
   L.resize(h->nlev);
   for (int l = 0; l < h->nlev; ++l) {
@@ -728,11 +769,14 @@ static ch_status make_working(Hierarchy* h, std::vector<LevelT<T>>& L, cudaStrea
   }
   // the fine level of a uniform mesh in diagonal form
   Dia<double> d64;
-  CH_TRY(dia_build(h->A[0], h->mem, &d64, st));
+  CH_TRY(dia_build(h->A[0], lat, h->mem, &d64, st));
   if (d64.nd) {
     Dia<T>& d = L[0].dia;
     d.nd = d64.nd;
-    for (int k = 0; k < kDiaSlots; ++k) d.off[k] = d64.off[k];
+    d.W = d64.W;
+    d.WH = d64.WH;
+    d.node_run = d64.node_run;
+    d.run_wh = d64.run_wh;
     const size_t cnt = (size_t)d64.nd * h->A[0].nrows;
     if (std::is_same<T, double>::value) {
       d.val = reinterpret_cast<T*>(d64.val);
@@ -745,7 +789,7 @@ static ch_status make_working(Hierarchy* h, std::vector<LevelT<T>>& L, cudaStrea
   return autotune_levels<T>(h, L, h->autotune, st);
 }
 
-ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precision, cudaStream_t st,
+ch_status hierarchy_build(const Csr<double>& A0, const FineLattice* lat, const ch_params& p, int precision, cudaStream_t st,
                           Hierarchy** out) {
   *out = nullptr;
   Hierarchy* h = new Hierarchy();
@@ -818,9 +862,9 @@ ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precisi
   }
   if (s == CH_OK) {
     if (precision == 0) {
-      s = make_working<double>(h, h->Ld, st);
+      s = make_working<double>(h, lat, h->Ld, st);
     } else {
-      s = make_working<float>(h, h->Lf, st);
+      s = make_working<float>(h, lat, h->Lf, st);
       if (s == CH_OK) s = h->mem.get(&h->cinvf, (size_t)h->nc * h->nc);
       if (s == CH_OK) {
         k_d2f<<<blocks_for((int64_t)h->nc * h->nc), TPB, 0, st>>>(h->cinv, h->cinvf,
@@ -960,9 +1004,15 @@ __device__ __forceinline__ void dia_row_sum(const Dia<T>& D, int n, int i, const
                                             T& s1) {
   s0 = 0;
   s1 = 0;
+  int W = D.W, WH = D.WH;
+  if (D.node_run) {
+    const int2 w = D.run_wh[D.node_run[i]];
+    W = w.x;
+    WH = w.y;
+  }
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    int j = i + D.off[d];
+    int j = i + lat_off(ND, d, W, WH);
     j = j < 0 ? 0 : (j >= n ? n - 1 : j);
     const T a = D.val[(size_t)d * n + i];
     const V2 xj = x[j];

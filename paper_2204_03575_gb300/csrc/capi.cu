@@ -255,8 +255,16 @@ ch_status ch_precond_setup(const ch_system_t* s, void* stream, ch_precond_t** ou
   M.col = H.col = s->col;
   M.val = s->valM;
   H.val = s->valH;
-  ch_status r = ch::hierarchy_build(M, s->p, pc->precision, S(stream), &pc->hM);
-  if (r == CH_OK) r = ch::hierarchy_build(H, s->p, pc->precision, S(stream), &pc->hH);
+  ch::FineLattice lat;
+  lat.dim = s->mesh->dim;
+  lat.run_off = s->mesh->run_off;
+  for (const ch_params& rp : s->mesh->runs) {
+    lat.W.push_back(rp.nx + 1);
+    lat.WH.push_back((rp.nx + 1) * (rp.ny + 1));
+  }
+  lat.node_run = s->mesh->node_run;
+  ch_status r = ch::hierarchy_build(M, &lat, s->p, pc->precision, S(stream), &pc->hM);
+  if (r == CH_OK) r = ch::hierarchy_build(H, &lat, s->p, pc->precision, S(stream), &pc->hH);
   if (r == CH_OK && (cudaStreamCreateWithFlags(&pc->side, cudaStreamNonBlocking) != cudaSuccess ||
                      cudaEventCreateWithFlags(&pc->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                      cudaEventCreateWithFlags(&pc->ev_join, cudaEventDisableTiming) != cudaSuccess)) {

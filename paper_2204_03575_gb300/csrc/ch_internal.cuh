@@ -189,7 +189,15 @@ struct ch_system_s {
 
 namespace ch {
 struct Hierarchy;  // amg.cu
-ch_status hierarchy_build(const Csr<double>& A0, const ch_params& p, int precision,
+// The fine level's mesh structure, for the structured (diagonal) form of level 0: node i of run r
+// has its neighbours at i + a + b W_r + c WH_r over the uniform mesh's lattice directions.
+struct FineLattice {
+  int dim = 0;                    // 2 or 3
+  std::vector<int> run_off;       // host, runs + 1
+  std::vector<int> W, WH;         // host, per run: nx + 1 and (nx + 1)(ny + 1)
+  const int* node_run = nullptr;  // device, N (used when there are several runs)
+};
+ch_status hierarchy_build(const Csr<double>& A0, const FineLattice* lat, const ch_params& p, int precision,
                           cudaStream_t st, Hierarchy** out);
 void hierarchy_free(Hierarchy* h);
 int hierarchy_levels(const Hierarchy* h);
