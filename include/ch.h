@@ -158,7 +158,10 @@ ch_status ch_apply_A(const ch_system_t* s, const double* x, double* y, void* str
  * Builds, on the device, smoothed-aggregation AMG hierarchies for M and H (strength of
  * connection, MIS(2) aggregation, Jacobi-smoothed prolongator, Galerkin coarse operators,
  * dense inverse of the coarsest level), Chebyshev smoother bounds per level and, when
- * precision = 1, FP32 copies of every level. */
+ * precision = 1, FP32 copies of every level.  On a uniform mesh (one run or a batch of them) the
+ * finest level is also stored by lattice diagonals.  The preconditioner owns a non-blocking
+ * CUDA stream and two events on the current device: ch_precond_apply runs step 1 of Algorithm 1
+ * on that stream, forked from and joined back into the caller's stream. */
 ch_status ch_precond_setup(const ch_system_t* s, void* stream, ch_precond_t** out);
 /* which: 0 = M hierarchy, 1 = H hierarchy.  Host outputs; level-wise sizes for level < nlevels. */
 ch_status ch_precond_info(const ch_precond_t* pc, int32_t which, int32_t level, int32_t* nlevels,
@@ -167,7 +170,9 @@ ch_status ch_precond_info(const ch_precond_t* pc, int32_t which, int32_t level, 
  * (prolongation) SpMVs (host outputs; R and P are 0 on the coarsest level). */
 ch_status ch_precond_tiles(const ch_precond_t* pc, int32_t which, int32_t level, int32_t* tpr_A,
                            int32_t* tpr_R, int32_t* tpr_P);
-/* Algorithm 1 on both species: w_1 ~ M^-1 v_1 and w_2 ~ H^-1 M H^-1 v_2 (AMG V-cycles).
+/* Algorithm 1 on both species: w_1 ~ M^-1 v_1 and w_2 ~ H^-1 M H^-1 v_2 (AMG V-cycles); the
+ * w_1 branch runs concurrently on the preconditioner's own stream and is joined back into
+ * `stream` before the call's work ends (stream order for the caller is unchanged).
  * v, w: N x 4 fp64, must not alias. */
 ch_status ch_precond_apply(ch_precond_t* pc, const double* v, double* w, void* stream);
 /* vcycles V-cycles (zero initial guess) on M (which = 0) or H (which = 1) for two right-hand
@@ -181,7 +186,8 @@ void ch_precond_destroy(ch_precond_t* pc);
  * graph by stream capture (where cudaMalloc is not allowed), applications whose device memory is
  * owned by a framework's caching allocator with a fixed budget, or latency-critical loops that
  * cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
- * It computes exactly what ch_vcycle computes (same kernels, same order; strides 2), but every
+ * It computes exactly what ch_vcycle computes (the same arithmetic in the same order; ch_vcycle
+ * merges some of these launches, which leaves the results unchanged; strides 2), but every
  * per-level work vector lives in one static device array of 8 MiB that each GPU loading the
  * library reserves until the process exits.  The only other device memory it touches is the
  * caller's b and x and the hierarchy built earlier by ch_precond_setup (read only).
