@@ -178,11 +178,36 @@ def make_solver(ch, nx, ny, precision):
     return system, pc, state
 
 
-def timed_steps(torch, ch, state, K, flush, barrier, net=None):
-    """K steps timed with CUDA events (ch_step, or ch_step_learned with `net`)."""
+class Ranks:
+    """The job's ranks (one process per GPU, replicas of the workload): a barrier around every timed
+    region and the slowest rank's time, which is the whole job's time.  `device` holds the
+    reduction tensor (cuda under NCCL, cpu under gloo)."""
+
+    def __init__(self, world=1, dist=None, device="cpu"):
+        self.world, self.dist, self.device = world, dist, device
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, ms):
+        import torch
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=self.device)
+        if self.world > 1:
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def rate(self, units_per_rank, ms_max):
+        """Whole-job units per second: every rank did units_per_rank in at most ms_max."""
+        return self.world * units_per_rank / (ms_max * 1e-3)
+
+
+def timed_steps(torch, ch, state, K, flush, ranks, net=None):
+    """K steps timed with CUDA events (ch_step, or ch_step_learned with `net`); returns the
+    slowest rank's milliseconds and this rank's iteration counts."""
     iters = []
     torch.cuda.synchronize()
-    barrier()
+    ranks.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(K):
@@ -193,11 +218,11 @@ def timed_steps(torch, ch, state, K, flush, barrier, net=None):
         iters.append(st["iters"])
     e1.record()
     torch.cuda.synchronize()
-    barrier()
-    return e0.elapsed_time(e1), iters
+    ranks.barrier()
+    return ranks.max(e0.elapsed_time(e1)), iters
 
 
-def extra_sections(torch, ch, np, K, W, flush, barrier, world):
+def extra_sections(torch, ch, np, K, W, flush, ranks):
     """32x32 steps/s (10 steps), FGMRES iterations per step for 32^2 .. 512^2 (first 10 steps of
     the same seeded run), and 3D 128x128x32 Kuhn tetrahedra on [0,1]^2 x [0,0.25], bases
     0.30/0.30 +/- 0.01 seed 0, FP32 V-cycles in FP64 FGMRES, up to 50 timed steps."""
@@ -205,8 +230,8 @@ def extra_sections(torch, ch, np, K, W, flush, barrier, world):
     _, _, st1 = make_solver(ch, 32, 32, precision=0)
     for _ in range(W):
         st1.step()
-    ms1, it1 = timed_steps(torch, ch, st1, 10, flush, barrier)
-    out["2d_32x32_fp64"] = {"steps": 10, "steps_per_s": world * 10 / (ms1 * 1e-3),
+    ms1, it1 = timed_steps(torch, ch, st1, 10, flush, ranks)
+    out["2d_32x32_fp64"] = {"steps": 10, "steps_per_s": ranks.rate(10, ms1),
                             "iters_per_step_mean": float(np.mean(it1)),
                             "note": "launch-bound: a roofline is not meaningful at 1089 nodes"}
     del st1
@@ -226,7 +251,7 @@ def extra_sections(torch, ch, np, K, W, flush, barrier, world):
     for _ in range(W):
         st3.step()
     K3 = min(K, 50)
-    ms3, it3 = timed_steps(torch, ch, st3, K3, flush, barrier)
+    ms3, it3 = timed_steps(torch, ch, st3, K3, flush, ranks)
     ch.profile_enable(True)
     ch.profile_read(reset=True)
     for _ in range(5):
@@ -238,7 +263,7 @@ def extra_sections(torch, ch, np, K, W, flush, barrier, world):
     out["3d_128x128x32_mixed"] = {
         "workload": "3D [0,1]^2 x [0,0.25], 128x128x32 hexes x 6 Kuhn tetrahedra, phi_p=phi_nfa=0.30+/-0.01 "
                     "seed 0, FP32 V-cycles in FP64 FGMRES to 1e-8", "nodes": sys3.n, "nnz": sys3.nnz,
-        "steps": K3, "steps_per_s": world * K3 / (ms3 * 1e-3), "ms_per_step": ms3 / K3,
+        "steps": K3, "steps_per_s": ranks.rate(K3, ms3), "ms_per_step": ms3 / K3,
         "iters_per_step_mean": float(np.mean(it3)), "amg_levels": {"M": [r for r, _ in pc3.levels(0)],
                                                                     "H": [r for r, _ in pc3.levels(1)]},
         "top_kernels": top_kernels(prof3)}
@@ -246,7 +271,7 @@ def extra_sections(torch, ch, np, K, W, flush, barrier, world):
     return out
 
 
-def learned_section(torch, ch, nx, K, flush, barrier, world):
+def learned_section(torch, ch, nx, K, flush, ranks):
     """The learned warm start on an nx x nx grid: 2000 (s_{k-1}, s_k, s_{k+1}) triples from the
     plain FP64 solver (20 seeded runs x 100 steps), residual-loss training by the library's
     kernels, then K timed steps of a held-out run per form: previous-state guess, the network,
@@ -282,8 +307,8 @@ def learned_section(torch, ch, nx, K, flush, barrier, world):
                     state.step()
                 else:
                     state.step_learned(n)
-            ms, iters = timed_steps(torch, ch, state, K, flush, barrier, net=n)
-            res[form] = {"steps_per_s": world * K / (ms * 1e-3), "ms_per_step": ms / K,
+            ms, iters = timed_steps(torch, ch, state, K, flush, ranks, net=n)
+            res[form] = {"steps_per_s": ranks.rate(K, ms), "ms_per_step": ms / K,
                          "iters_per_step_mean": float(np.mean(iters))}
         out[tag] = res
     out["mixed_learned_over_fp64_previous_state"] = (out["mixed"]["learned"]["steps_per_s"]
@@ -357,9 +382,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    ranks = Ranks(world, dist, torch.device("cuda", local))
+    barrier = ranks.barrier
 
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -397,13 +421,9 @@ def main():
         state.step()
     ch.profile_read(reset=True)
     with Clocks(local) as clk:
-        ms, iters = timed_steps(torch, ch, state, K, flush, barrier)
+        ms, iters = timed_steps(torch, ch, state, K, flush, ranks)
     launches = sum(v["launches"] for v in ch.profile_read(reset=True).values())
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = world * K / (ms * 1e-3)
+    value = ranks.rate(K, ms)  # ms is already the slowest rank's
     fields64 = {k: v.clone() for k, v in state.get().items()}
 
     # ---- per-kernel event timing of the same steps (separate pass: events add host overhead)
@@ -444,11 +464,8 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = e0.elapsed_time(e1)
-    t = torch.tensor([ms_e2e], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * K / (float(t.item()) * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * N,
+    ms_e2e = ranks.max(e0.elapsed_time(e1))
+    e2e = {"value": ranks.rate(K, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * N,
            "d2h_bytes_per_step": 5 * 8 * N,
            "api": "ch_state_set / ch_step / ch_state_get with pinned host copies each step"}
     del sysE, pcE, stateE
@@ -459,7 +476,7 @@ def main():
         sysM, pcM, stateM = make_solver(ch, args.nx, args.ny, precision=1)
         for _ in range(W):
             stateM.step()
-        ms_m, iters_m = timed_steps(torch, ch, stateM, K, flush, barrier)
+        ms_m, iters_m = timed_steps(torch, ch, stateM, K, flush, ranks)
         fm = stateM.get()
         diff = max(float((fm[k] - fields64[k]).abs().max() / fields64[k].abs().max()) for k in ("phi_p", "phi_nfa"))
         ch.profile_enable(True)
@@ -470,7 +487,7 @@ def main():
         torch.cuda.synchronize()
         profm = ch.profile_read(reset=True)
         ch.profile_enable(False)
-        mixed = {"value": world * K / (ms_m * 1e-3), "ms_per_step": ms_m / K,
+        mixed = {"value": ranks.rate(K, ms_m), "ms_per_step": ms_m / K,
                  "iters_per_step_mean": float(np.mean(iters_m)),
                  "max_rel_diff_phi_vs_fp64_form_after_run": diff,
                  "roofline": roofline(profm, peaks, sustained=True), "top_kernels": top_kernels(profm)}
@@ -490,7 +507,7 @@ def main():
             bstate.step()
         KB = min(K, 20)
         ch.profile_read(reset=True)
-        ms_b, iters_b = timed_steps(torch, ch, bstate, KB, flush, barrier)
+        ms_b, iters_b = timed_steps(torch, ch, bstate, KB, flush, ranks)
         blaunch = sum(v["launches"] for v in ch.profile_read(reset=True).values())
         worst = max(max(bstate.run_stats(r)["relres"]) for r in range(len(spec)))
         by_size = {}
@@ -500,7 +517,7 @@ def main():
         batch = {"workload": "64 runs, nx, ny drawn from {64,96,128,192,256}, bases U[0.20,0.45), "
                              "noise +/-0.01, FP32 V-cycles in FP64 FGMRES, one state (disjoint union)",
                  "runs": len(spec), "nodes": bsys.n, "steps": KB,
-                 "run_steps_per_s": world * len(spec) * KB / (ms_b * 1e-3), "ms_per_step": ms_b / KB,
+                 "run_steps_per_s": ranks.rate(len(spec) * KB, ms_b), "ms_per_step": ms_b / KB,
                  "launches_per_step": blaunch / KB, "max_relres_last_step": worst, "per_size": per_size}
         del bstate, bsys, bmesh
 
@@ -508,12 +525,12 @@ def main():
     # step against the mesh size, and the 3D Kuhn-tetrahedra box in the mixed form
     extra = None
     if not args.no_extra:
-        extra = extra_sections(torch, ch, np, K, W, flush, barrier, world)
+        extra = extra_sections(torch, ch, np, K, W, flush, ranks)
 
     # ---- learned warm start (256 x 256 grid): training, then FP64 / mixed with and without it
     learned = None
     if not args.no_learned:
-        learned = learned_section(torch, ch, args.learned_nx, min(K, 40), flush, barrier, world)
+        learned = learned_section(torch, ch, args.learned_nx, min(K, 40), flush, ranks)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
