@@ -73,7 +73,8 @@ typedef struct ch_params {
   double rtol;               /* stop when ||b - A x||_2 <= rtol ||b||_2 per species, default 1e-8 */
   int32_t restart;           /* FGMRES restart length m (1..64), default 30 */
   int32_t max_iter;          /* total FGMRES iterations per step, default 300 */
-  int32_t cheb_degree;       /* Chebyshev smoothing steps before and after coarse correction, default 3 */
+  int32_t cheb_degree;       /* Chebyshev smoothing steps before and after coarse correction on the
+                                finest level, default 5 */
   int32_t coarse_max;        /* AMG: coarsest level is solved densely at or below this size (<= 4096);
                                 0 (default): 512 rows for FP64 V-cycles, 4096 for FP32 */
   double amg_theta;          /* AMG strength threshold, default 0.08 */
@@ -82,8 +83,8 @@ typedef struct ch_params {
   int32_t autotune;          /* SpMV lanes per row: 0 = fixed rule, 1 = timed at set-up (cached per process), default 1 */
   double cheb_lower;         /* Chebyshev interval [cheb_lower, 1] x 1.1 lambda_max(D^-1 A), default 0.3 */
   int32_t graphs;            /* 1: replay each Arnoldi step as a captured CUDA graph; 0: direct launches; default 1 */
-  int32_t cheb_degree_coarse; /* Chebyshev steps on the levels below the finest; 0 (default): 2 for FP64
-                                V-cycles (at most cheb_degree), cheb_degree for FP32 */
+  int32_t cheb_degree_coarse; /* Chebyshev steps on the levels below the finest; 0 (default): 2 (at
+                                most cheb_degree) */
 } ch_params;
 
 /* Per-step statistics (host struct). */

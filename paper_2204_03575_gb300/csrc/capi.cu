@@ -83,7 +83,7 @@ void ch_params_default(ch_params* p) {
   d.rtol = 1e-8;
   d.restart = 30;
   d.max_iter = 300;
-  d.cheb_degree = 3;
+  d.cheb_degree = 5;
   d.coarse_max = 0;
   d.amg_theta = 0.08;
   d.vcycles_M = 1;

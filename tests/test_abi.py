@@ -69,7 +69,7 @@ def test_defaults_are_the_papers(L):
     p = ch.Params()
     assert (p.tau, p.eps, p.k_evap, p.g_p, p.g_nfa, p.h_p) == (1e-4, 1e-3, 5e-3, 0.01, 0.01, 0.0)
     assert p.rtol == 1e-8 and p.bc_mode == 1 and p.evap_sign == 1 and p.precision == 0
-    assert p.cheb_degree == 3 and p.vcycles_H == 2 and p.vcycles_M == 1 and p.autotune == 1
+    assert p.cheb_degree == 5 and p.vcycles_H == 2 and p.vcycles_M == 1 and p.autotune == 1
     assert p.coarse_max == 0 and p.cheb_degree_coarse == 0
 
 
