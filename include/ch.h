@@ -85,12 +85,15 @@ typedef struct ch_params {
   int32_t graphs;            /* 1: replay each Arnoldi step as a captured CUDA graph; 0: direct launches; default 1 */
   int32_t cheb_degree_coarse; /* Chebyshev steps on the levels below the finest; 0 (default): 2 (at
                                 most cheb_degree) */
+  int32_t krylov;            /* 0 (default): flexible GMRES(restart); 1: preconditioned MINRES, the
+                                paper's method (Algorithm 1 with fixed V-cycles is symmetric positive
+                                definite; work vectors use the basis storage, so restart >= 5) */
 } ch_params;
 
 /* Per-step statistics (host struct). */
 typedef struct ch_step_stats {
   int32_t iters[2];          /* FGMRES iterations (polymer, NFA) */
-  int32_t restarts;          /* restart cycles used */
+  int32_t restarts;          /* FGMRES: restart cycles used; MINRES: true-residual checks after the first */
   int32_t status;            /* ch_status of this step */
   double relres[2];          /* true final ||b - A x|| / ||b|| per species, FP64 */
   double mass[2];            /* int phi_h = 1^T M phi^{k+1} per species */

@@ -35,6 +35,7 @@ ch_status check_params(const ch_params* p) {
   CH_ARG(p->cheb_lower > 0 && p->cheb_lower < 1, "cheb_lower must be in (0, 1)");
   CH_ARG(p->graphs == 0 || p->graphs == 1, "graphs must be 0 or 1");
   CH_ARG(p->cheb_degree_coarse >= 0 && p->cheb_degree_coarse <= 16, "cheb_degree_coarse must be in [0, 16]");
+  CH_ARG(p->krylov == 0 || p->krylov == 1, "krylov must be 0 (FGMRES) or 1 (MINRES)");
   return CH_OK;
 }
 }  // namespace
@@ -92,6 +93,7 @@ void ch_params_default(ch_params* p) {
   d.cheb_lower = 0.3;
   d.graphs = 1;
   d.cheb_degree_coarse = 0;
+  d.krylov = 0;
   *p = d;
 }
 

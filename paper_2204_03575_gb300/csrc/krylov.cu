@@ -44,6 +44,20 @@ struct KrylovDev {
   int warm[2];            // the caller's guess was taken for this species
 };
 
+// Preconditioned MINRES scalars of one run, per species (the Lanczos process on P^-1 A in the
+// P inner product and the Givens QR of its tridiagonal matrix).
+struct MrDev {
+  double gam[2];           // gamma_j: the norm that normalised the current Lanczos vector
+  double c[2], cp[2];      // cosines c_j, c_{j-1}
+  double s[2], sp[2];      // sines s_j, s_{j-1}
+  double eta[2];           // |eta| estimates ||r||_{P^-1}
+  double est[2];           // target for |eta| at which the true residual is checked
+  double delta[2];         // delta_j = (A z_j) . z_j
+  double a1[2], a2[2], a3[2], cn[2], etao[2];  // this iteration's update coefficients
+  double scale[2];         // 1 / gamma_{j+1} (0 once the species stops)
+  int upd[2];              // the species took this iteration
+};
+
 struct Flags {  // summary over all runs
   int cycle_active;  // systems still iterating in the cycle
   int active;        // systems not yet converged
@@ -555,11 +569,15 @@ struct ch_state_s {
   cudaStream_t cap_stream = nullptr;            // private stream for graph capture
   cudaGraphExec_t graph[64] = {};               // Arnoldi step j, captured on first use
   ch::ProfTally tally[64];                      // launch accounting of each graph
+  ch::MrDev* mr = nullptr;                      // MINRES scalars, one per run
+  cudaGraphExec_t mr_graph = nullptr;           // one MINRES iteration, captured on first use
+  ch::ProfTally mr_tally;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   ch::Alloc mem;
   ~ch_state_s() {
     for (auto& g : graph)
       if (g) cudaGraphExecDestroy(g);
+    if (mr_graph) cudaGraphExecDestroy(mr_graph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (hflags) cudaFreeHost(hflags);
     if (ev0) cudaEventDestroy(ev0);
@@ -628,6 +646,10 @@ ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, 
     set_error("restart must be in [1, %d]", MAXM);
     return CH_ERR_ARG;
   }
+  if (s->p.krylov == 1 && m < 5) {
+    set_error("MINRES keeps its 8 work vectors in the Krylov basis storage: restart must be >= 5");
+    return CH_ERR_ARG;
+  }
   ch_state_s* S = new ch_state_s();
   S->sys = s;
   S->pc = pc;
@@ -644,6 +666,7 @@ ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, 
   if (r == CH_OK) r = S->mem.get(&S->Z, n4 * m);
   if (r == CH_OK) r = S->mem.get(&S->mlump, (size_t)s->N);
   if (r == CH_OK) r = S->mem.get(&S->kd, (size_t)S->R);
+  if (r == CH_OK) r = S->mem.get(&S->mr, (size_t)S->R);
   if (r == CH_OK) r = S->mem.get(&S->dflags, 1);
   if (r == CH_OK) r = S->mem.get(&S->dstats, (size_t)S->R);
   if (r == CH_OK) r = make_segments(S, st);
@@ -839,6 +862,309 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
   return CH_OK;
 }
 
+// ---------------------------------------------------------------- preconditioned MINRES
+// The paper's Krylov method (Section 3): Lanczos vectors v_j (A-space) and z_j = P^-1 v_j, both
+// normalised by gamma_j = sqrt(v_j . z_j); the tridiagonal matrix (delta_j on the diagonal,
+// gamma_j off it) is reduced by Givens rotations, and x is updated by the direction w_{j+1}.
+// MODE 0: gamma_1 from (v_1, z_1) and the start of the recurrence; 1: delta_j = (A z_j) . z_j;
+// 2: gamma_{j+1} from (v_{j+1}, z_{j+1}) and the Givens step.  Dots per species: components
+// (x, z) for species 0 and (y, w) for species 1, over the run's nodes, reduced in block order.
+template <int MODE>
+__global__ void __launch_bounds__(TPB) k_mr_dot(Seg sg, const double4_32a* __restrict__ A_,
+                                                const double4_32a* __restrict__ B_, double* partials,
+                                                KrylovDev* kds, MrDev* mrs) {
+  __shared__ double sm[(TPB / 32) * 2];
+  const int run = sg.run[blockIdx.x];
+  double acc[2] = {0.0, 0.0};
+  for (int v = sg.lo[blockIdx.x] + threadIdx.x; v < sg.hi[blockIdx.x]; v += blockDim.x) {
+    const double4_32a a = A_[v], b = B_[v];
+    acc[0] = fma(a.x, b.x, fma(a.z, b.z, acc[0]));
+    acc[1] = fma(a.y, b.y, fma(a.w, b.w, acc[1]));
+  }
+  block_sum<2>(acc, sm);
+  if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = sm[threadIdx.x];
+  KrylovDev* kd = kds + run;
+  MrDev* mr = mrs + run;
+  const int b0 = sg.first[run], b1 = sg.first[run + 1];
+  if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
+  __shared__ double tot[2];
+  reduce_partials(partials, b0, b1, 2, tot);
+  if (threadIdx.x < 2) {
+    const int sp = threadIdx.x;
+    const double d = tot[sp];
+    if (!isfinite(d)) kd->nonfinite = 1;
+    if (MODE == 0) {
+      const bool go = kd->active[sp] && d > 0.0;
+      const double g = go ? sqrt(d) : 0.0;
+      mr->gam[sp] = g;
+      mr->eta[sp] = g;
+      mr->c[sp] = mr->cp[sp] = 1.0;
+      mr->s[sp] = mr->sp[sp] = 0.0;
+      // the preconditioned residual is to fall by the factor the true one must fall by
+      mr->est[sp] = (go && kd->beta[sp] > 0.0) ? g * kd->tol[sp] / kd->beta[sp] : 0.0;
+      mr->scale[sp] = go ? 1.0 / g : 0.0;
+      kd->cycle_active[sp] = go;
+    } else if (MODE == 1) {
+      mr->delta[sp] = d;
+    } else {
+      mr->upd[sp] = kd->cycle_active[sp];
+      if (kd->cycle_active[sp]) {
+        const double gn = d > 0.0 ? sqrt(d) : 0.0;
+        const double g = mr->gam[sp], dl = mr->delta[sp];
+        const double a0 = mr->c[sp] * dl - mr->cp[sp] * mr->s[sp] * g;
+        const double a1 = hypot(a0, gn);
+        mr->a2[sp] = mr->s[sp] * dl + mr->cp[sp] * mr->c[sp] * g;
+        mr->a3[sp] = mr->sp[sp] * g;
+        mr->a1[sp] = a1;
+        const double cn = a1 > 0.0 ? a0 / a1 : 1.0, sn = a1 > 0.0 ? gn / a1 : 0.0;
+        mr->cn[sp] = cn;
+        mr->etao[sp] = mr->eta[sp];
+        mr->eta[sp] = -sn * mr->eta[sp];
+        mr->cp[sp] = mr->c[sp];
+        mr->c[sp] = cn;
+        mr->sp[sp] = mr->s[sp];
+        mr->s[sp] = sn;
+        mr->gam[sp] = gn;
+        const bool breakdown = !(gn > 1e-300) || !(a1 > 0.0);
+        mr->scale[sp] = breakdown ? 0.0 : 1.0 / gn;
+        if (!(a1 > 0.0)) mr->upd[sp] = 0;
+        kd->its[sp] += 1;
+        if (!isfinite(a1) || !isfinite(mr->eta[sp])) kd->nonfinite = 1;
+        kd->cycle_active[sp] = !breakdown && fabs(mr->eta[sp]) > mr->est[sp];
+      }
+    }
+  }
+  if (threadIdx.x == 0) kd->ticket = 0;
+}
+
+// v *= 1 / gamma_1, z *= 1 / gamma_1 (start of the recurrence)
+__global__ void k_mr_scale(Seg sg, double4_32a* v, double4_32a* z, const MrDev* mrs) {
+  const MrDev* mr = mrs + sg.run[blockIdx.x];
+  const double f0 = mr->scale[0], f1 = mr->scale[1];
+  for (int i = sg.lo[blockIdx.x] + threadIdx.x; i < sg.hi[blockIdx.x]; i += blockDim.x) {
+    double4_32a a = v[i], b = z[i];
+    a.x *= f0; a.z *= f0; a.y *= f1; a.w *= f1;
+    b.x *= f0; b.z *= f0; b.y *= f1; b.w *= f1;
+    v[i] = a;
+    z[i] = b;
+  }
+}
+
+// v_{j+1} = A z_j - delta_j v_j - gamma_j v_{j-1} (zero for a species that has stopped)
+__global__ void k_mr_lanczos(Seg sg, const double4_32a* __restrict__ q, const double4_32a* __restrict__ v,
+                             const double4_32a* __restrict__ vp, double4_32a* __restrict__ vn,
+                             const KrylovDev* kds, const MrDev* mrs) {
+  const int run = sg.run[blockIdx.x];
+  const KrylovDev* kd = kds + run;
+  const MrDev* mr = mrs + run;
+  const bool on0 = kd->cycle_active[0], on1 = kd->cycle_active[1];
+  const double d0 = mr->delta[0], d1 = mr->delta[1], g0 = mr->gam[0], g1 = mr->gam[1];
+  for (int i = sg.lo[blockIdx.x] + threadIdx.x; i < sg.hi[blockIdx.x]; i += blockDim.x) {
+    const double4_32a a = q[i], b = v[i], c = vp[i];
+    double4_32a o;
+    o.x = on0 ? a.x - d0 * b.x - g0 * c.x : 0.0;
+    o.z = on0 ? a.z - d0 * b.z - g0 * c.z : 0.0;
+    o.y = on1 ? a.y - d1 * b.y - g1 * c.y : 0.0;
+    o.w = on1 ? a.w - d1 * b.w - g1 * c.w : 0.0;
+    vn[i] = o;
+  }
+}
+
+// w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j) / a1;  x += c_{j+1} eta_j w_{j+1};  then the roles move on:
+// w_{j-1} <- w_j, w_j <- w_{j+1}, v_{j-1} <- v_j, v_j <- v_{j+1} / gamma_{j+1}, z_j <- z_{j+1} / gamma_{j+1}
+__global__ void k_mr_update(Seg sg, double4_32a* __restrict__ x, double4_32a* __restrict__ w,
+                            double4_32a* __restrict__ wp, double4_32a* __restrict__ z,
+                            const double4_32a* __restrict__ zn, double4_32a* __restrict__ v,
+                            double4_32a* __restrict__ vp, const double4_32a* __restrict__ vn,
+                            const MrDev* mrs) {
+  const MrDev* mr = mrs + sg.run[blockIdx.x];
+  const bool u0 = mr->upd[0], u1 = mr->upd[1];
+  const double i0 = u0 ? 1.0 / mr->a1[0] : 0.0, i1 = u1 ? 1.0 / mr->a1[1] : 0.0;
+  const double a20 = mr->a2[0], a21 = mr->a2[1], a30 = mr->a3[0], a31 = mr->a3[1];
+  const double f0 = mr->cn[0] * mr->etao[0], f1 = mr->cn[1] * mr->etao[1];
+  const double s0 = mr->scale[0], s1 = mr->scale[1];
+  for (int i = sg.lo[blockIdx.x] + threadIdx.x; i < sg.hi[blockIdx.x]; i += blockDim.x) {
+    // a species that did not take this iteration keeps its vectors (it may resume after a
+    // true-residual check)
+    const double4_32a zz = z[i], ww = w[i], wwp = wp[i], vv = v[i], vnn = vn[i], znn = zn[i];
+    double4_32a xx = x[i], wo = ww, wpo = wwp, vo = vv, vpo = vp[i], zo = zz;
+    if (u0) {
+      const double wx = (zz.x - a30 * wwp.x - a20 * ww.x) * i0;
+      const double wz = (zz.z - a30 * wwp.z - a20 * ww.z) * i0;
+      xx.x += f0 * wx;
+      xx.z += f0 * wz;
+      wpo.x = ww.x; wpo.z = ww.z;
+      wo.x = wx; wo.z = wz;
+      vpo.x = vv.x; vpo.z = vv.z;
+      vo.x = vnn.x * s0; vo.z = vnn.z * s0;
+      zo.x = znn.x * s0; zo.z = znn.z * s0;
+    }
+    if (u1) {
+      const double wy = (zz.y - a31 * wwp.y - a21 * ww.y) * i1;
+      const double ww_ = (zz.w - a31 * wwp.w - a21 * ww.w) * i1;
+      xx.y += f1 * wy;
+      xx.w += f1 * ww_;
+      wpo.y = ww.y; wpo.w = ww.w;
+      wo.y = wy; wo.w = ww_;
+      vpo.y = vv.y; vpo.w = vv.w;
+      vo.y = vnn.y * s1; vo.w = vnn.w * s1;
+      zo.y = znn.y * s1; zo.w = znn.w * s1;
+    }
+    x[i] = xx;
+    wp[i] = wpo;
+    w[i] = wo;
+    vp[i] = vpo;
+    v[i] = vo;
+    z[i] = zo;
+  }
+}
+
+// after a true-residual check, species still unconverged aim their estimate lower: by the
+// factor their true residual still has to fall (at least 2)
+__global__ void k_mr_retarget(int nruns, const KrylovDev* kds, MrDev* mrs) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * nruns) return;
+  const KrylovDev* kd = kds + t / 2;
+  MrDev* mr = mrs + t / 2;
+  const int sp = t % 2;
+  if (!kd->active[sp]) return;
+  const double rn = kd->relres[sp] * kd->bnorm[sp];
+  const double f = rn > 0.0 ? fmin(0.5, 0.9 * kd->tol[sp] / rn) : 0.5;
+  mr->est[sp] = fabs(mr->eta[sp]) * f;
+}
+
+// One MINRES iteration for all runs and species.  Work vectors (N x 4 each) live in the Krylov
+// basis storage: V_0 v_j, V_1 v_{j-1}, V_2 v_{j+1}, V_3 w_j, V_4 w_{j-1}, V_5 A z_j; Z_0 z_j, Z_1 z_{j+1}.
+static ch_status mr_iteration(ch_state_s* S, cudaStream_t st) {
+  const int N = S->N, nb = S->nblocks;
+  const size_t n4 = (size_t)N;
+  double4_32a* V4 = reinterpret_cast<double4_32a*>(S->V);
+  double4_32a* Z4 = reinterpret_cast<double4_32a*>(S->Z);
+  double4_32a *v = V4, *vp = V4 + n4, *vn = V4 + 2 * n4, *w = V4 + 3 * n4, *wp = V4 + 4 * n4, *q = V4 + 5 * n4;
+  double4_32a *z = Z4, *zn = Z4 + n4;
+  CH_TRY(apply_A(S->sys, reinterpret_cast<const double*>(z), reinterpret_cast<double*>(q), st));
+  {
+    ProfScope ps(st, K_MR_DOT, 0, 64.0 * N, 4.0 * N);
+    k_mr_dot<1><<<nb, TPB, 0, st>>>(S->seg, q, z, S->partials, S->kd, S->mr);
+  }
+  {
+    ProfScope ps(st, K_MR_VEC, 0, 128.0 * N, 8.0 * N);
+    k_mr_lanczos<<<nb, TPB, 0, st>>>(S->seg, q, v, vp, vn, S->kd, S->mr);
+  }
+  CH_LAUNCHED();
+  CH_TRY(precond_apply(S->pc, reinterpret_cast<const double*>(vn), reinterpret_cast<double*>(zn), st));
+  {
+    ProfScope ps(st, K_MR_DOT, 0, 64.0 * N, 4.0 * N);
+    k_mr_dot<2><<<nb, TPB, 0, st>>>(S->seg, vn, zn, S->partials, S->kd, S->mr);
+  }
+  {
+    ProfScope ps(st, K_MR_VEC, 0, 10.0 * 32.0 * N, 12.0 * N);
+    k_mr_update<<<nb, TPB, 0, st>>>(S->seg, reinterpret_cast<double4_32a*>(S->x), w, wp, z, zn, v, vp, vn, S->mr);
+  }
+  {
+    ProfScope ps(st, K_FLAGS, 0, 0.0, 0.0);
+    k_flags<<<1, 256, 0, st>>>(S->R, S->kd, S->dflags);
+  }
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+static ch_status mr_launch(ch_state_s* S, cudaStream_t st) {
+  if (!S->use_graphs || prof_timing()) {
+    CH_TRY(mr_iteration(S, st));
+  } else {
+    if (!S->mr_graph) {
+      cudaGraph_t g = nullptr;
+      CH_CUDA(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
+      prof_capture_begin();
+      const ch_status r = mr_iteration(S, S->cap_stream);
+      const cudaError_t e = cudaStreamEndCapture(S->cap_stream, &g);
+      S->mr_tally = prof_capture_end();
+      if (r != CH_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      CH_CUDA(e);
+      const cudaError_t ei = cudaGraphInstantiate(&S->mr_graph, g, 0);
+      cudaGraphDestroy(g);
+      CH_CUDA(ei);
+    }
+    CH_CUDA(cudaGraphLaunch(S->mr_graph, st));
+    prof_add(S->mr_tally);
+  }
+  return read_flags(S, st);
+}
+
+// Preconditioned MINRES (the paper's Krylov method, Section 3) with Algorithm 1 as the fixed
+// preconditioner; the stopping test is the true FP64 residual, checked whenever every system's
+// MINRES estimate has reached its target (checks[0] counts the checks after the first).
+static ch_status minres(ch_state_s* S, cudaStream_t st, int* checks) {
+  const ch_params& p = S->sys->p;
+  const int N = S->N, nb = S->nblocks;
+  const size_t n4 = (size_t)N;
+  double4_32a* V4 = reinterpret_cast<double4_32a*>(S->V);
+  double4_32a* Z4 = reinterpret_cast<double4_32a*>(S->Z);
+  *checks = 0;
+  CH_TRY(residual_launch(S, 1, st));
+  CH_TRY(read_flags(S, st));
+  if (S->hflags->nonfinite) {
+    set_error("non-finite right-hand side or initial residual");
+    return CH_ERR_NONFINITE;
+  }
+  if (S->hflags->active == 0) return CH_OK;
+  // v_1 = r_0, z_1 = P^-1 v_1, v_0 = w_0 = w_{-1} = 0
+  CH_CUDA(cudaMemcpyAsync(V4, S->W, sizeof(double4_32a) * n4, cudaMemcpyDeviceToDevice, st));
+  CH_CUDA(cudaMemsetAsync(V4 + n4, 0, sizeof(double4_32a) * n4, st));
+  CH_CUDA(cudaMemsetAsync(V4 + 3 * n4, 0, sizeof(double4_32a) * 2 * n4, st));
+  CH_TRY(precond_apply(S->pc, reinterpret_cast<const double*>(V4), reinterpret_cast<double*>(Z4), st));
+  {
+    ProfScope ps(st, K_MR_DOT, 0, 64.0 * N, 4.0 * N);
+    k_mr_dot<0><<<nb, TPB, 0, st>>>(S->seg, V4, Z4, S->partials, S->kd, S->mr);
+  }
+  {
+    ProfScope ps(st, K_MR_VEC, 0, 128.0 * N, 4.0 * N);
+    k_mr_scale<<<nb, TPB, 0, st>>>(S->seg, V4, Z4, S->mr);
+  }
+  k_flags<<<1, 256, 0, st>>>(S->R, S->kd, S->dflags);
+  CH_LAUNCHED();
+  CH_TRY(read_flags(S, st));
+  int total = 0;
+  for (;;) {
+    while (S->hflags->cycle_active > 0) {
+      if (total >= p.max_iter) {
+        set_error("MINRES reached max_iter = %d with %d of %d systems unconverged", p.max_iter,
+                  S->hflags->active, 2 * S->R);
+        return CH_ERR_NOT_CONVERGED;
+      }
+      CH_TRY(mr_launch(S, st));
+      ++total;
+      if (S->hflags->nonfinite) {
+        set_error("non-finite value in the MINRES recurrence");
+        return CH_ERR_NONFINITE;
+      }
+    }
+    CH_TRY(residual_launch(S, 0, st));
+    CH_TRY(read_flags(S, st));
+    if (S->hflags->nonfinite) {
+      set_error("non-finite residual");
+      return CH_ERR_NONFINITE;
+    }
+    if (S->hflags->active == 0) return CH_OK;
+    if (total >= p.max_iter) {
+      set_error("MINRES reached max_iter = %d with %d of %d systems unconverged", p.max_iter,
+                S->hflags->active, 2 * S->R);
+      return CH_ERR_NOT_CONVERGED;
+    }
+    k_mr_retarget<<<blocks_for(2 * S->R, 64), 64, 0, st>>>(S->R, S->kd, S->mr);
+    CH_LAUNCHED();
+    ++*checks;
+  }
+}
+
+static ch_status krylov_solve(ch_state_s* S, cudaStream_t st, int* restarts) {
+  return S->sys->p.krylov == 1 ? minres(S, st, restarts) : fgmres(S, st, restarts);
+}
+
 __global__ void k_set_state(int N, const double* pp, const double* pn, const double* mp,
                             const double* mn, double4_32a* x) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1014,7 +1340,7 @@ static ch_status step_plain_core(ch_state_s* S, cudaStream_t st, ch_step_stats* 
   CH_TRY(rhs_strided(S->sys, S->x, S->x + 1, 4, S->b, st));
   k_clear_warm<<<blocks_for(S->R, 64), 64, 0, st>>>(S->R, S->kd);
   int restarts = 0;
-  ch_status r = fgmres(S, st, &restarts);
+  ch_status r = krylov_solve(S, st, &restarts);
   {
     ProfScope ps(st, K_MASS, 0, 40.0 * S->N, 2.0 * S->N);
     k_mass<<<S->nblocks, TPB, 0, st>>>(S->seg, S->mlump, reinterpret_cast<const double4_32a*>(S->x),
@@ -1061,7 +1387,7 @@ static ch_status step_guess_core(ch_state_s* S, const double* guess, cudaStream_
   }
   CH_LAUNCHED();
   int restarts = 0;
-  ch_status r = fgmres(S, st, &restarts);
+  ch_status r = krylov_solve(S, st, &restarts);
   {
     ProfScope ps(st, K_MASS, 0, 40.0 * S->N, 2.0 * S->N);
     k_mass<<<S->nblocks, TPB, 0, st>>>(S->seg, S->mlump, reinterpret_cast<const double4_32a*>(S->x),

@@ -348,6 +348,39 @@ def test_parallel_m_branch_matches_serial_algorithm1(lib, precision):
             np.testing.assert_array_equal(ga[k], gb[k])
 
 
+def test_minres_step_parity(lib):
+    """krylov = 1 (preconditioned MINRES, the paper's Krylov method, with Algorithm 1's fixed
+    FP64 V-cycles): per-step fields match the oracle's direct solve like FGMRES's (rtol 1e-12)."""
+    out = run_pair(lib, 4, nx=32, ny=32, rtol=1e-12, krylov=1)[1]
+    for st, g, _, ref in out:
+        assert st["status"] == 0 and max(st["relres"]) <= 1e-12
+        for k in ("phi_p", "phi_nfa", "mu_p", "mu_nfa"):
+            assert rel(g[k], getattr(ref, k)) < 1e-10, k
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_minres_default_tolerance_and_batch(lib, precision):
+    """MINRES at the default rtol reaches the true 1e-8 residual on a 128 x 96 mesh and on a
+    batch of runs of different sizes (per-run scalars), in FP64 and with FP32 V-cycles."""
+    cp, _ = make(lib, nx=128, ny=96, krylov=1, precision=precision)
+    system = lib.System(lib.Mesh(cp), cp)
+    state = lib.State(system, lib.Precond(system))
+    state.init_seeded(0.33, 0.31, 0.01, seed=2)
+    for _ in range(3):
+        st = state.step()
+        assert st["status"] == 0 and max(st["relres"]) <= 1e-8
+    pb = lib.Params(precision=precision, krylov=1)
+    mesh = lib.Mesh(pb, runs=[lib.Params(nx=nx, ny=ny) for nx, ny in ((24, 16), (40, 40), (16, 48))])
+    bsys = lib.System(mesh, pb)
+    bstate = lib.State(bsys, lib.Precond(bsys))
+    bstate.init_seeded_batch([0.33, 0.25, 0.40], [0.31, 0.40, 0.22], 0.01, seed=4)
+    for _ in range(2):
+        bstate.step()
+        for r in range(3):
+            rs = bstate.run_stats(r)
+            assert rs["status"] == 0 and max(rs["relres"]) <= 1e-8
+
+
 def test_bitwise_reproducible(lib):
     a = run_pair(lib, 2, nx=64, ny=64)[1]
     b = run_pair(lib, 2, nx=64, ny=64)[1]
