@@ -1300,25 +1300,6 @@ ch_status hierarchy_solve(Hierarchy* h, const double* b, int ldb, double* x, int
   return solve_t<float>(h, h->Lf, h->cinvf, b, ldb, x, ldx, ncyc, st);
 }
 
-template <typename T>
-static ch_status apply_fine_t(std::vector<LevelT<T>>& Ls, const double* x, int ldx, double* y,
-                              int ldy, cudaStream_t st) {
-  using V2 = typename V2T<T>::t;
-  LevelT<T>& L = Ls[0];
-  const int n = L.A.nrows;
-  k_load2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, x, ldx, L.r);
-  launch_apply_level<T, V2>(L, L.r, L.d, st);
-  k_store2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.d, y, ldy);
-  CH_LAUNCHED();
-  return CH_OK;
-}
-
-ch_status hierarchy_apply_fine(Hierarchy* h, const double* x, int ldx, double* y, int ldy,
-                               cudaStream_t st) {
-  if (h->precision == 0) return apply_fine_t<double>(h->Ld, x, ldx, y, ldy, st);
-  return apply_fine_t<float>(h->Lf, x, ldx, y, ldy, st);
-}
-
 // ---------------------------------------------------------------- Algorithm 1
 // w_1 = AMG(M) v_1;  w_2 = AMG(H) v_2;  w_2 = M w_2;  w_2 = AMG(H) w_2.
 // v, w are N x 4 (phi_p, phi_n, mu_p, mu_n per node): block 1 at offset 0, block 2 at offset 2.

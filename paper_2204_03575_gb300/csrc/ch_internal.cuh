@@ -209,8 +209,6 @@ ch_status hierarchy_solve(Hierarchy* h, const double* b, int ldb, double* x, int
 // as hierarchy_solve (strides 2), work vectors in a static device array: no device allocation
 ch_status hierarchy_solve_noalloc(Hierarchy* h, const double* b, double* x, int ncyc, cudaStream_t st);
 // y (N x 2, fp64, stride ldy) = A0 x (N x 2, fp64, stride ldx) in the hierarchy's working precision
-ch_status hierarchy_apply_fine(Hierarchy* h, const double* x, int ldx, double* y, int ldy,
-                               cudaStream_t st);
 
 // assemble.cu
 ch_status loads(const ch_system_s* s, const double* pp, const double* pn, double* Fp, double* Fn,
@@ -257,7 +255,6 @@ ch_status state_get(const ch_state_s* S, double* pp, double* pn, double* ps, dou
 ch_status state_seeded_batch(ch_state_s* S, const double* base_p, const double* base_n, double noise,
                              uint64_t seed, cudaStream_t st);
 ch_status state_run_stats(const ch_state_s* S, int run, ch_step_stats* out);
-int state_runs(const ch_state_s* S);
 ch_status state_save(const ch_state_s* S, const char* path, cudaStream_t st);
 ch_status state_load(ch_state_s* S, const char* path, cudaStream_t st);
 ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats);

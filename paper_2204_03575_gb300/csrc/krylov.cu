@@ -1461,6 +1461,5 @@ ch_status state_run_stats(const ch_state_s* S, int run, ch_step_stats* out) {
   return CH_OK;
 }
 
-int state_runs(const ch_state_s* S) { return S->R; }
 
 }  // namespace ch
