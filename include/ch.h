@@ -85,6 +85,8 @@ typedef struct ch_params {
   int32_t graphs;            /* 1: replay each Arnoldi step as a captured CUDA graph; 0: direct launches; default 1 */
   int32_t cheb_degree_coarse; /* Chebyshev steps on the levels below the finest; 0 (default): 2 (at
                                 most cheb_degree) */
+  int32_t cheb_degree_M;     /* finest-level Chebyshev degree of M's hierarchy (Algorithm 1, step 1);
+                                0 (default): min(3, cheb_degree) -- M is close to its diagonal */
   int32_t krylov;            /* 0 (default): flexible GMRES(restart); 1: preconditioned MINRES, the
                                 paper's method (Algorithm 1 with fixed V-cycles is symmetric positive
                                 definite; work vectors use the basis storage, so restart >= 5) */
