@@ -298,8 +298,11 @@ def learned_section(torch, ch, nx, K, flush, ranks):
            "loss_meaning": "mean |r|^2 / |r_extrapolation|^2 of the step residual"}
     for prec, tag in ((0, "fp64"), (1, "mixed")):
         res = {}
+        # one solver per precision: the three forms share its hierarchy and autotuned launch shapes,
+        # so they differ only in the initial guess (a preconditioner per form would tune anew);
+        # re-seeding restarts the run and the learned step's history
+        state = ws.make_state(nx, nx, prec)
         for form, n in (("previous_state", None), ("learned", net), ("extrapolation", zero)):
-            state = ws.make_state(nx, nx, prec)
             b0, b1 = ws.seed_bases(1000)
             state.init_seeded(b0, b1, 0.01, seed=1000)
             for _ in range(2):  # ch_step_learned starts from the previous state for two steps
