@@ -28,7 +28,10 @@ Readings of points the paper leaves open (each also listed in the design doc):
   R4 f^(k) is the exact load vector int f'(phi_h^k) lambda_i, not M f'(phi^k);
   R5 the evaporation flux on Gamma_t enters with sign ``evap_sign`` (+1: inflow of
      polymer and NFA as the text describes; -1: Eq. (10) read literally);
-  R6 the substrate flux on Gamma_b is +df_s/dphi (Eq. (10) literally), p(x) = 1;
+  R6 the substrate flux on Gamma_b is +df_s/dphi (Eq. (10) literally), with
+     p_p = p_nfa = 1, or with ``pattern`` = 1 Section 4's alternating preference:
+     p_p = 1 on the 1st, 3rd and 5th sixth of [0, Lx], p_nfa = 1 on the others
+     (the shared endpoints of the closed subintervals have measure zero);
   R7 no extra boundary term in the mu equation (natural condition grad phi . n = 0);
   R8 2D cells split along the lower-left/upper-right diagonal, 3D hexahedra into
      the 6 Kuhn tetrahedra; Gamma_b = {y = 0}, Gamma_t = {y = L_y}.
@@ -67,6 +70,7 @@ class Params:
     h_p: float = 0.0
     h_nfa: float = 0.0
     potential: str = "poly"    # reading R3
+    pattern: int = 0           # substrate patterning p_p(x), p_nfa(x) of Section 4 (reading R6)
 
 
 # ----------------------------------------------------------------------------
@@ -229,11 +233,78 @@ def facet_measure(X: np.ndarray) -> np.ndarray:
     return 0.5 * np.linalg.norm(np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]), axis=1)
 
 
+def substrate_preference(x: np.ndarray, Lx: float):
+    """(p_p(x), p_nfa(x)) of Section 4's patterned substrate for points inside [0, Lx]: the
+    interval is cut into six equal parts, polymer preferred on the 1st, 3rd and 5th."""
+    k = np.clip(np.floor(6.0 * np.asarray(x, dtype=np.float64) / Lx), 0, 5).astype(np.int64)
+    pref_p = (k % 2 == 0).astype(np.float64)
+    return pref_p, 1.0 - pref_p
+
+
+GAUSS3 = np.polynomial.legendre.leggauss(3)  # exact for degree 5 on an interval
+
+
+def _gauss_on(a: float, b: float):
+    """3-point Gauss-Legendre nodes and weights on [a, b]."""
+    x, w = GAUSS3
+    return 0.5 * (a + b) + 0.5 * (b - a) * x, 0.5 * (b - a) * w
+
+
+def _patterned_substrate(m: Mesh, pp: np.ndarray, pn: np.ndarray, p: Params, gp, gn):
+    """Adds int_{Gamma_b} p_s(x) (g_s + 2 h_s phi_s) lambda_i to gp, gn (Eq. (5), Section 4).
+
+    p_s is piecewise constant in x, so each facet is cut at the breakpoints k Lx / 6 that cross
+    it (and, in 3D, at its own vertices' x, where the facet's cross-section changes edges).  On
+    each piece the integrand is a polynomial of degree <= 2 in the facet's coordinates; nested
+    3-point Gauss-Legendre rules (x outside, z inside for a 3D facet) integrate it exactly."""
+    breaks = np.arange(1, 6) * (p.Lx / 6.0)
+    for f in m.bottom:
+        X = m.coords[f]
+        if m.dim == 2:
+            x0, x1 = X[0, 0], X[1, 0]
+            lo, hi = min(x0, x1), max(x0, x1)
+            cuts = np.unique(np.r_[lo, hi, breaks[(breaks > lo) & (breaks < hi)]])
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                xq, wq = _gauss_on(a, b)
+                l1 = (xq - x0) / (x1 - x0)
+                lam = np.c_[1.0 - l1, l1]                    # (q, 2) hat functions on the facet
+                _accumulate(f, lam, wq, xq, pp, pn, p, gp, gn)
+        else:
+            P = X[:, [0, 2]]                                  # the facet lies in y = 0: (x, z)
+            T = np.c_[P[1] - P[0], P[2] - P[0]]               # x-z Jacobian of the facet
+            lo, hi = P[:, 0].min(), P[:, 0].max()
+            cuts = np.unique(np.r_[P[:, 0], breaks[(breaks > lo) & (breaks < hi)]])
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                xq, wq = _gauss_on(a, b)
+                for x, wx in zip(xq, wq):
+                    zs = []
+                    for u, v in ((0, 1), (1, 2), (2, 0)):     # the facet's edges met by the line at x
+                        xa, xb = P[u, 0], P[v, 0]
+                        if xa != xb and min(xa, xb) <= x <= max(xa, xb):
+                            zs.append(P[u, 1] + (x - xa) / (xb - xa) * (P[v, 1] - P[u, 1]))
+                    zq, wz = _gauss_on(min(zs), max(zs))
+                    pts = np.c_[np.full_like(zq, x), zq]
+                    l12 = np.linalg.solve(T, (pts - P[0]).T).T
+                    lam = np.c_[1.0 - l12.sum(1), l12]
+                    _accumulate(f, lam, wx * wz, pts[:, 0], pp, pn, p, gp, gn)
+
+
+def _accumulate(f, lam, w, x, pp, pn, p: Params, gp, gn):
+    """gp[f[i]] += sum_q w_q p_p(x_q) (g_p + 2 h_p phi_p(x_q)) lam[q, i], and the same for NFA."""
+    pref_p, pref_n = substrate_preference(x, p.Lx)
+    php, phn = lam @ pp[f], lam @ pn[f]
+    vp = w * pref_p * (p.g_p + 2.0 * p.h_p * php)
+    vn = w * pref_n * (p.g_nfa + 2.0 * p.h_nfa * phn)
+    np.add.at(gp, f, vp @ lam)
+    np.add.at(gn, f, vn @ lam)
+
+
 def boundary_load(m: Mesh, pp: np.ndarray, pn: np.ndarray, p: Params):
     """g_s[i] = int_{Gamma_b} (g_s + 2 h_s phi_s) lambda_i + evap_sign k int_{Gamma_t} phi_s phi_solv lambda_i.
 
     Flux boundary conditions of Eq. (10) with the substrate density of Eq. (5)
-    (p(x) = 1) and the evaporation flux k phi_i phi_s; readings R5, R6.
+    (p(x) = 1, or Section 4's pattern when ``p.pattern``) and the evaporation flux
+    k phi_i phi_s; readings R5, R6.
     Returns zeros when bc_mode == 0.
     """
     N = m.coords.shape[0]
@@ -243,11 +314,14 @@ def boundary_load(m: Mesh, pp: np.ndarray, pn: np.ndarray, p: Params):
     dF = m.dim - 1
     T1, T2, T3 = monomial_table(dF, 1), monomial_table(dF, 2), monomial_table(dF, 3)
     # substrate, Gamma_b
-    Fb = m.bottom
-    ab = facet_measure(m.coords[Fb])
-    for g_s, h_s, phi, out in ((p.g_p, p.h_p, pp, gp), (p.g_nfa, p.h_nfa, pn, gn)):
-        val = g_s * T1[None, :] + 2.0 * h_s * np.einsum("fa,ai->fi", phi[Fb], T2)
-        np.add.at(out, Fb, ab[:, None] * val)
+    if p.pattern:
+        _patterned_substrate(m, pp, pn, p, gp, gn)
+    else:
+        Fb = m.bottom
+        ab = facet_measure(m.coords[Fb])
+        for g_s, h_s, phi, out in ((p.g_p, p.h_p, pp, gp), (p.g_nfa, p.h_nfa, pn, gn)):
+            val = g_s * T1[None, :] + 2.0 * h_s * np.einsum("fa,ai->fi", phi[Fb], T2)
+            np.add.at(out, Fb, ab[:, None] * val)
     # evaporation, Gamma_t
     Ft = m.top
     at = facet_measure(m.coords[Ft])

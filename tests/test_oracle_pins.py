@@ -437,3 +437,100 @@ def test_step_matches_eq12_unsplit_form():
     r2 = s.M @ nxt.mu_p - Fp - p.eps * (s.K @ nxt.phi_p)
     assert np.abs(r1).max() < 1e-9 * np.abs(s.M @ pp / p.tau).max()
     assert np.abs(r2).max() < 1e-9 * np.abs(Fp).max()
+
+
+# ---------------------------------------------------------------- substrate patterning (Section 4)
+def test_substrate_preference_follows_the_six_subintervals():
+    Lx = 10.0
+    x = np.array([0.05, 0.25, 0.45, 0.55, 0.7, 0.95]) * Lx  # one point inside each sixth
+    pp, pn = o.substrate_preference(x, Lx)
+    np.testing.assert_array_equal(pp, [1, 0, 1, 0, 1, 0])
+    np.testing.assert_array_equal(pn, [0, 1, 0, 1, 0, 1])
+    xs = np.linspace(0.0, Lx, 1001)
+    a, b = o.substrate_preference(xs, Lx)
+    np.testing.assert_array_equal(a + b, 1.0)
+
+
+def _patterned(dim, nx, **kw):
+    base = dict(dim=dim, nx=nx, ny=2, nz=3 if dim == 3 else 0, Lx=10.0, Ly=2.5, Lz=1.5,
+                k_evap=0.0, pattern=1)
+    base.update(kw)
+    return o.Params(**base)
+
+
+@pytest.mark.parametrize("dim,nx", [(2, 7), (2, 5), (3, 7), (3, 4)])
+def test_patterned_substrate_total(dim, nx):
+    """Summed over the nodes, the hat functions add up to 1: the g part of the load is g times the
+    measure of the preferred half of Gamma_b, whatever the facets' alignment with the sixths."""
+    p = _patterned(dim, nx, g_p=0.02, g_nfa=0.05, h_p=0.0, h_nfa=0.0)
+    m = o.mesh(p)
+    N = m.coords.shape[0]
+    gp, gn = o.boundary_load(m, np.full(N, 0.3), np.full(N, 0.3), p)
+    depth = p.Lz if dim == 3 else 1.0
+    assert math.isclose(gp.sum(), 0.02 * 0.5 * p.Lx * depth, rel_tol=1e-13)
+    assert math.isclose(gn.sum(), 0.05 * 0.5 * p.Lx * depth, rel_tol=1e-13)
+
+
+@pytest.mark.parametrize("dim,nx", [(2, 7), (3, 5)])
+def test_patterned_substrate_linear_moment(dim, nx):
+    """phi = x + 2z is exact in P1; with g = 0 the summed load is 2h int_{preferred} (x + 2z)."""
+    p = _patterned(dim, nx, g_p=0.0, g_nfa=0.0, h_p=0.5, h_nfa=-0.25)
+    m = o.mesh(p)
+    X = m.coords
+    phi = X[:, 0] + (2.0 * X[:, 2] if dim == 3 else 0.0)
+    gp, gn = o.boundary_load(m, phi, phi, p)
+    w = p.Lx / 6.0
+    depth = p.Lz if dim == 3 else 1.0
+    for h, ks, g in ((p.h_p, (0, 2, 4), gp), (p.h_nfa, (1, 3, 5), gn)):
+        int_x = sum(((k + 1) * w) ** 2 - (k * w) ** 2 for k in ks) / 2.0 * depth
+        int_z = 3 * w * (depth ** 2 / 2.0) if dim == 3 else 0.0
+        assert math.isclose(g.sum(), 2.0 * h * (int_x + 2.0 * int_z), rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_patterned_substrate_on_aligned_mesh(dim):
+    """With nx a multiple of 6 no facet crosses a breakpoint: the patterned load is the unpatterned
+    one restricted to the facets whose midpoint lies in the preferred sixths."""
+    p = _patterned(dim, 12, g_p=0.02, g_nfa=0.05, h_p=0.3, h_nfa=-0.2)
+    m = o.mesh(p)
+    N = m.coords.shape[0]
+    rng = np.random.default_rng(7)
+    pp, pn = 0.2 + 0.4 * rng.random(N), 0.2 + 0.4 * rng.random(N)
+    gp, gn = o.boundary_load(m, pp, pn, p)
+    mid = m.coords[m.bottom][:, :, 0].mean(1)
+    pref_p = ((np.floor(6.0 * mid / p.Lx)).astype(int) % 2) == 0
+    flat = o.Params(**{**p.__dict__, "pattern": 0})
+    for keep, which in ((pref_p, 0), (~pref_p, 1)):
+        sub = o.Mesh(m.dim, m.coords, m.elems, m.bottom[keep], m.top[:0], m.ijk)
+        ref = o.boundary_load(sub, pp, pn, flat)[which]
+        np.testing.assert_allclose((gp, gn)[which], ref, rtol=1e-13, atol=1e-16)
+
+
+def test_patterned_substrate_brute_force_2d():
+    """Composite midpoint rule on a sub-grid that contains both the nodes and the breakpoints
+    (step Lx / (6 nx n)), so p is constant on every sub-interval: second-order convergence."""
+    p = _patterned(2, 7, g_p=0.02, g_nfa=0.05, h_p=0.3, h_nfa=-0.2)
+    m = o.mesh(p)
+    N = m.coords.shape[0]
+    rng = np.random.default_rng(3)
+    pp, pn = 0.2 + 0.4 * rng.random(N), 0.2 + 0.4 * rng.random(N)
+    gp, gn = o.boundary_load(m, pp, pn, p)
+    n_sub = 6 * p.nx * 60
+    xm = (np.arange(n_sub) + 0.5) * (p.Lx / n_sub)
+    dx = p.Lx / n_sub
+    bp, bn = np.zeros(N), np.zeros(N)
+    hx = p.Lx / p.nx
+    cell = np.minimum((xm / hx).astype(int), p.nx - 1)
+    t = xm / hx - cell
+    left, right = cell, cell + 1                     # bottom-row nodes i = 0..nx
+    php = (1 - t) * pp[left] + t * pp[right]
+    phn = (1 - t) * pn[left] + t * pn[right]
+    k = np.floor(6.0 * xm / p.Lx).astype(int)
+    vp = np.where(k % 2 == 0, p.g_p + 2 * p.h_p * php, 0.0) * dx
+    vn = np.where(k % 2 == 1, p.g_nfa + 2 * p.h_nfa * phn, 0.0) * dx
+    np.add.at(bp, left, vp * (1 - t))
+    np.add.at(bp, right, vp * t)
+    np.add.at(bn, left, vn * (1 - t))
+    np.add.at(bn, right, vn * t)
+    np.testing.assert_allclose(gp, bp, rtol=0, atol=2e-6 * np.abs(bp).max())
+    np.testing.assert_allclose(gn, bn, rtol=0, atol=2e-6 * np.abs(bn).max())
