@@ -90,6 +90,10 @@ typedef struct ch_params {
   int32_t krylov;            /* 0 (default): flexible GMRES(restart); 1: preconditioned MINRES, the
                                 paper's method (Algorithm 1 with fixed V-cycles is symmetric positive
                                 definite; work vectors use the basis storage, so restart >= 5) */
+  int32_t pattern;           /* substrate preference on y = 0 (Eq. (5), Section 4): 0 (default) p_p =
+                                p_nfa = 1; 1: p_p = 1 on the 1st, 3rd and 5th sixth of [0, Lx] (each
+                                run's own Lx), p_nfa = 1 on the others.  Integrated exactly: facets
+                                are cut where they cross a breakpoint */
 } ch_params;
 
 /* Per-step statistics (host struct). */

@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
         ("coarse_max", ctypes.c_int32), ("amg_theta", ctypes.c_double),
         ("vcycles_M", ctypes.c_int32), ("vcycles_H", ctypes.c_int32), ("autotune", ctypes.c_int32),
         ("cheb_lower", ctypes.c_double), ("graphs", ctypes.c_int32), ("cheb_degree_coarse", ctypes.c_int32),
-        ("cheb_degree_M", ctypes.c_int32), ("krylov", ctypes.c_int32),
+        ("cheb_degree_M", ctypes.c_int32), ("krylov", ctypes.c_int32), ("pattern", ctypes.c_int32),
     ]
 
     def __init__(self, **kw):

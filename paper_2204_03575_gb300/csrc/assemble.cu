@@ -315,6 +315,150 @@ __global__ void k_axpby_vals(const double* x, const double* y, double a, double 
   if (i < n) z[i] = a * x[i] + b * y[i];
 }
 
+// ---------------------------------------------------------------- patterned substrate (Section 4)
+// With pattern = 1 the substrate energy density of Eq. (5) carries p_p(x) = 1 on the 1st, 3rd and
+// 5th sixth of [0, Lx] and p_nfa(x) = 1 on the others (0 elsewhere).  Its boundary load needs, per
+// bottom facet F and species s, W1_i = int_F p_s lambda_i and W2_ai = int_F p_s lambda_a lambda_i.
+// p_s is constant between breakpoints, so F is clipped to each sixth [lo, hi] and the pieces are
+// integrated exactly with the vertex-value rules for linear u, v on a simplex S of dimension k:
+//   int_S u = |S| / (k+1) sum_j u_j,   int_S u v = |S| / ((k+1)(k+2)) (sum_j u_j v_j + sum u sum v).
+// A 3D facet (a triangle in the x-z plane y = 0) is clipped by Sutherland-Hodgman against the two
+// half-planes and fanned into triangles; a 2D facet is a segment of the x axis.
+template <int D>
+struct FacetHat {  // the facet's hat functions as affine functions of (x, z)
+  double X[D], Z[D], det;
+  __device__ void lam(double x, double z, double* l) const {
+    if constexpr (D == 2) {
+      l[1] = (x - X[0]) / (X[1] - X[0]);
+      l[0] = 1.0 - l[1];
+    } else {
+      const double dx = x - X[0], dz = z - Z[0];
+      l[1] = (dx * (Z[2] - Z[0]) - (X[2] - X[0]) * dz) / det;
+      l[2] = ((X[1] - X[0]) * dz - dx * (Z[1] - Z[0])) / det;
+      l[0] = 1.0 - l[1] - l[2];
+    }
+  }
+};
+
+// Adds the integrals over the simplex with vertices P (k + 1 = D of them, measure meas) to W.
+template <int D>
+__device__ void add_piece(const FacetHat<D>& F, const double (*P)[2], double meas, double* W1, double* W2) {
+  double L[D][D];  // L[j][i] = lambda_i at vertex j of the piece
+#pragma unroll
+  for (int j = 0; j < D; ++j) F.lam(P[j][0], P[j][1], L[j]);
+  const double c1 = meas / D, c2 = meas / (D * (D + 1));
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double si = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) si += L[j][i];
+    W1[i] += c1 * si;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      double sa = 0.0, sai = 0.0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        sa += L[j][a];
+        sai += L[j][a] * L[j][i];
+      }
+      W2[a * D + i] += c2 * (sai + sa * si);
+    }
+  }
+}
+
+// Clips the convex polygon (x, z)[n] to the half-plane sgn (x - c) >= 0; returns the new vertex
+// count.  Each clip adds at most one vertex (a triangle ends with at most 5); cap bounds the
+// output all the same.
+__device__ int clip_x(const double (*in)[2], int n, double c, double sgn, double (*out)[2], int cap) {
+  int k = 0;
+  for (int j = 0; j < n && k + 2 <= cap; ++j) {
+    const double* P = in[j];
+    const double* Q = in[(j + 1) % n];
+    const double dp = sgn * (P[0] - c), dq = sgn * (Q[0] - c);
+    if (dp >= 0.0) {
+      out[k][0] = P[0];
+      out[k][1] = P[1];
+      ++k;
+    }
+    if ((dp >= 0.0) != (dq >= 0.0)) {
+      const double t = dp / (dp - dq);
+      out[k][0] = c;
+      out[k][1] = P[1] + t * (Q[1] - P[1]);
+      ++k;
+    }
+  }
+  return k;
+}
+
+template <int D>
+__global__ void k_facet_pattern(const double* coords, const int* bot, int nf, double Lx, double* bw) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  constexpr int NW = D + D * D;
+  const int* fv = bot + D * f;
+  FacetHat<D> F;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    F.X[a] = coords[(size_t)D * fv[a]];
+    F.Z[a] = (D == 3) ? coords[(size_t)D * fv[a] + 2] : 0.0;
+  }
+  F.det = 0.0;
+  if constexpr (D == 3) F.det = (F.X[1] - F.X[0]) * (F.Z[2] - F.Z[0]) - (F.X[2] - F.X[0]) * (F.Z[1] - F.Z[0]);
+  double W[2][NW];
+#pragma unroll
+  for (int q = 0; q < 2 * NW; ++q) W[q / NW][q % NW] = 0.0;
+  for (int k = 0; k < 6; ++k) {
+    const double lo = k * (Lx / 6.0), hi = (k + 1) * (Lx / 6.0);
+    double* W1 = W[k & 1];  // species 0 (polymer) on k = 0, 2, 4; species 1 (NFA) on k = 1, 3, 5
+    double* W2 = W1 + D;
+    if constexpr (D == 2) {
+      const double xa = fmax(fmin(F.X[0], F.X[1]), lo), xb = fmin(fmax(F.X[0], F.X[1]), hi);
+      if (xb <= xa) continue;
+      const double P[2][2] = {{xa, 0.0}, {xb, 0.0}};
+      add_piece<D>(F, P, xb - xa, W1, W2);
+    } else {
+      double A[8][2], B[8][2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        A[a][0] = F.X[a];
+        A[a][1] = F.Z[a];
+      }
+      int n = clip_x(A, 3, lo, 1.0, B, 8);
+      n = clip_x(B, n, hi, -1.0, A, 8);
+      for (int j = 1; j + 1 < n; ++j) {
+        const double P[3][2] = {{A[0][0], A[0][1]}, {A[j][0], A[j][1]}, {A[j + 1][0], A[j + 1][1]}};
+        const double meas = 0.5 * fabs((P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) -
+                                       (P[2][0] - P[0][0]) * (P[1][1] - P[0][1]));
+        if (meas > 0.0) add_piece<D>(F, P, meas, W1, W2);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2 * NW; ++q) bw[(size_t)f * 2 * NW + q] = W[q / NW][q % NW];
+}
+
+// Weights of every run's bottom facets (each run's box is [0, Lx_r] in x).
+static ch_status substrate_weights(const ch_mesh_s* m, ch_system_s* s, cudaStream_t st) {
+  const int d = m->dim, R = (int)m->runs.size();
+  CH_TRY(s->mem.get(&s->bw, (size_t)m->Fb * 2 * (d + d * d)));
+  int f0 = 0;
+  for (int r = 0; r < R; ++r) {
+    int n, e, f;
+    box_counts(m->runs[r], &n, &e, &f);
+    const int* bot = m->bot + (size_t)f0 * d;
+    double* bw = s->bw + (size_t)f0 * 2 * (d + d * d);
+    if (f > 0) {
+      if (d == 2)
+        k_facet_pattern<2><<<blocks_for(f), TPB, 0, st>>>(m->coords, bot, f, m->runs[r].Lx, bw);
+      else
+        k_facet_pattern<3><<<blocks_for(f), TPB, 0, st>>>(m->coords, bot, f, m->runs[r].Lx, bw);
+    }
+    f0 += f;
+  }
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
 ch_status assemble_system(const ch_mesh_s* m, ch_system_s* s, cudaStream_t st) {
   const int N = m->N, d = m->dim;
   s->N = N;
@@ -349,6 +493,7 @@ ch_status assemble_system(const ch_mesh_s* m, ch_system_s* s, cudaStream_t st) {
   // H = a K + sqrt(c) M  (Section 3, matching Schur approximation)
   k_axpby_vals<<<blocks_for(nnz), TPB, 0, st>>>(s->valK, s->valM, s->a, sqrt(s->c), s->valH, nnz);
   CH_LAUNCHED();
+  if (s->p.pattern && s->p.bc_mode) CH_TRY(substrate_weights(m, s, st));
   int ovf = 0;
   CH_CUDA(cudaMemcpyAsync(&ovf, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
   CH_CUDA(cudaStreamSynchronize(st));
@@ -409,6 +554,7 @@ struct LoadCoef {
   double cubic;   // 7 for Eq. (15), 0 for f' = 0
   int bc;         // boundary loads on/off
   double gp, gn, hp, hn, kev;
+  const double* bw;  // patterned substrate weights (Fb x 2 x (D + D^2)), or null for p = 1
 };
 
 // Per element e and vertex a, eload[(e (D+1) + a) 2 + {0, 1}] = |T| (7 int p q^2 l_a - 0.2 int phi_s l_a)
@@ -485,21 +631,41 @@ __device__ void node_loads(const MeshPod& m, const LoadCoef& L, const double* __
     constexpr double f1 = 1.0 / (DF + 1);                 // int lambda_i / |F|
     constexpr double f2 = 1.0 / ((DF + 1) * (DF + 2));    // int lambda_a lambda_i / |F|, a != i
     constexpr double f3 = (D == 2) ? 1.0 / 24.0 : 1.0 / 60.0;  // (d-1)!/(d+2)!
-    for (int q = m.n2b_ptr[v]; q < m.n2b_ptr[v + 1]; ++q) {  // Gamma_b: int (g + 2 h phi) lambda_i
-      const int f = m.n2b[q];
-      const int* fv = m.bot + D * f;
-      double Sp = 0, Sq = 0, pi = 0, qi = 0;
-      for (int a = 0; a < D; ++a) {
-        Sp += pp[(size_t)ld * fv[a]];
-        Sq += pn[(size_t)ld * fv[a]];
-        if (fv[a] == v) {
-          pi = pp[(size_t)ld * fv[a]];
-          qi = pn[(size_t)ld * fv[a]];
+    if (L.bw) {
+      // Gamma_b, patterned: int p_s (g + 2 h phi) lambda_i = g W1_i + 2 h sum_a phi_a W2_ai
+      for (int q = m.n2b_ptr[v]; q < m.n2b_ptr[v + 1]; ++q) {
+        const int f = m.n2b[q];
+        const int* fv = m.bot + D * f;
+        const double* Wp = L.bw + (size_t)f * 2 * (D + D * D);
+        const double* Wn = Wp + D + D * D;
+        int li = 0;
+        for (int a = 0; a < D; ++a)
+          if (fv[a] == v) li = a;
+        double sp = 0.0, sn = 0.0;
+        for (int a = 0; a < D; ++a) {
+          sp += pp[(size_t)ld * fv[a]] * Wp[D + a * D + li];
+          sn += pn[(size_t)ld * fv[a]] * Wn[D + a * D + li];
         }
+        gp += L.gp * Wp[li] + 2.0 * L.hp * sp;
+        gn += L.gn * Wn[li] + 2.0 * L.hn * sn;
       }
-      const double ar = m.bvol[f];
-      gp += ar * (L.gp * f1 + 2.0 * L.hp * f2 * (Sp + pi));
-      gn += ar * (L.gn * f1 + 2.0 * L.hn * f2 * (Sq + qi));
+    } else {
+      for (int q = m.n2b_ptr[v]; q < m.n2b_ptr[v + 1]; ++q) {  // Gamma_b: int (g + 2 h phi) lambda_i
+        const int f = m.n2b[q];
+        const int* fv = m.bot + D * f;
+        double Sp = 0, Sq = 0, pi = 0, qi = 0;
+        for (int a = 0; a < D; ++a) {
+          Sp += pp[(size_t)ld * fv[a]];
+          Sq += pn[(size_t)ld * fv[a]];
+          if (fv[a] == v) {
+            pi = pp[(size_t)ld * fv[a]];
+            qi = pn[(size_t)ld * fv[a]];
+          }
+        }
+        const double ar = m.bvol[f];
+        gp += ar * (L.gp * f1 + 2.0 * L.hp * f2 * (Sp + pi));
+        gn += ar * (L.gn * f1 + 2.0 * L.hn * f2 * (Sq + qi));
+      }
     }
     for (int q = m.n2t_ptr[v]; q < m.n2t_ptr[v + 1]; ++q) {  // Gamma_t: k int phi phi_s lambda_i
       const int f = m.n2t[q];
@@ -537,6 +703,7 @@ static LoadCoef load_coef(const ch_params& p) {
   L.hp = p.h_p;
   L.hn = p.h_nfa;
   L.kev = p.evap_sign * p.k_evap;
+  L.bw = nullptr;
   return L;
 }
 
@@ -592,7 +759,8 @@ static void elem_loads(const ch_system_s* s, const MeshPod& m, const LoadCoef& L
 ch_status loads(const ch_system_s* s, const double* pp, const double* pn, double* Fp, double* Fn,
                 double* gp, double* gn, cudaStream_t st) {
   const MeshPod m = mesh_pod(s->mesh);
-  const LoadCoef L = load_coef(s->p);
+  LoadCoef L = load_coef(s->p);
+  L.bw = s->bw;
   elem_loads(s, m, L, pp, pn, 1, st);
   ProfScope ps(st, K_LOADS, 0, 16.0 * m.N + 32.0 * m.N, 0.0);
   if (m.dim == 2)
@@ -606,7 +774,8 @@ ch_status loads(const ch_system_s* s, const double* pp, const double* pn, double
 ch_status rhs_strided(const ch_system_s* s, const double* pp, const double* pn, int ld, double* b,
                       cudaStream_t st) {
   const MeshPod m = mesh_pod(s->mesh);
-  const LoadCoef L = load_coef(s->p);
+  LoadCoef L = load_coef(s->p);
+  L.bw = s->bw;
   elem_loads(s, m, L, pp, pn, ld, st);
   const double E = s->mesh->E, d1 = m.dim + 1;
   // phi read + b written + M (values, columns, row pointers) + incidence and the element

@@ -38,6 +38,7 @@ ch_status check_params(const ch_params* p) {
   CH_ARG(p->cheb_degree_coarse >= 0 && p->cheb_degree_coarse <= 16, "cheb_degree_coarse must be in [0, 16]");
   CH_ARG(p->krylov == 0 || p->krylov == 1, "krylov must be 0 (FGMRES) or 1 (MINRES)");
   CH_ARG(p->cheb_degree_M >= 0 && p->cheb_degree_M <= 16, "cheb_degree_M must be in [0, 16]");
+  CH_ARG(p->pattern == 0 || p->pattern == 1, "pattern must be 0 or 1");
   return CH_OK;
 }
 }  // namespace
@@ -97,6 +98,7 @@ void ch_params_default(ch_params* p) {
   d.cheb_degree_coarse = 0;
   d.cheb_degree_M = 0;
   d.krylov = 0;
+  d.pattern = 0;
   *p = d;
 }
 

@@ -183,6 +183,7 @@ struct ch_system_s {
   double* valH = nullptr;
   int* diag = nullptr;  // position of the diagonal entry of each row
   double* eload = nullptr;  // E x (dim+1) x 2: per element and vertex, the f-load contributions
+  double* bw = nullptr;     // pattern = 1: Fb x 2 species x (dim + dim^2) substrate weights, else null
   double a = 0, c = 0;  // A = [[M, aK], [aK, -cM]]
   ch::Alloc mem;
 };

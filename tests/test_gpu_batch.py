@@ -110,3 +110,23 @@ def test_batch_64_runs_full_size_residuals(lib):
         rr = s.relres(prev, new)
         assert max(rr) <= 1e-8, (r, nx, ny, rr)
         assert max(state.run_stats(r)["relres"]) <= 1e-8
+
+
+def test_batch_patterned_substrate_per_run(lib):
+    """With pattern = 1 each run's substrate sixths follow its own Lx: the batch's boundary loads
+    equal the oracle's on each run's mesh (unaligned and aligned runs)."""
+    geoms = [(8, 12), (24, 10, 10.0, 2.5), (13, 7, 3.0, 1.0)]
+    kw = dict(pattern=1, h_p=0.3, h_nfa=-0.2)
+    runs = [lib.Params(nx=g[0], ny=g[1], Lx=g[2] if len(g) > 2 else 1.0, Ly=g[3] if len(g) > 3 else 1.0)
+            for g in geoms]
+    p = lib.Params(**kw)
+    mesh = lib.Mesh(p, runs=runs)
+    system = lib.System(mesh, p)
+    rng = np.random.default_rng(5)
+    pp, pn = 0.2 + 0.3 * rng.random(system.n), 0.2 + 0.3 * rng.random(system.n)
+    out = system.loads(torch.from_numpy(pp).cuda(), torch.from_numpy(pn).cuda())
+    gp, gn = [split(mesh, t.cpu().numpy()) for t in out[2:]]
+    for r, g in enumerate(geoms):
+        op = o.Params(nx=g[0], ny=g[1], Lx=g[2] if len(g) > 2 else 1.0, Ly=g[3] if len(g) > 3 else 1.0, **kw)
+        egp, egn = o.boundary_load(o.mesh(op), split(mesh, pp)[r], split(mesh, pn)[r], op)
+        assert rel(gp[r], egp) < 1e-13 and rel(gn[r], egn) < 1e-13, r

@@ -87,6 +87,24 @@ def test_loads_parity(lib, kw, potential):
     assert rel(gp, egp) < 1e-13 and rel(gn, egn) < 1e-13
 
 
+@pytest.mark.parametrize("kw", CASES + [dict(nx=36, ny=12, Lx=10.0, Ly=2.5),
+                                 dict(dim=3, nx=12, ny=3, nz=5, Lx=10.0, Ly=2.5, Lz=10.0)])
+def test_patterned_substrate_loads_parity(lib, kw):
+    """Section 4's substrate patterning (p_p, p_nfa alternating on the sixths of [0, Lx]): facets
+    cut by a breakpoint (nx not a multiple of 6) and aligned meshes, h != 0 so that the
+    field-dependent part of the substrate load is exercised."""
+    cp, op = make(lib, pattern=1, h_p=0.3, h_nfa=-0.2, g_nfa=0.02, **kw)
+    system = lib.System(lib.Mesh(cp), cp)
+    om = o.mesh(op)
+    rng = np.random.default_rng(12)
+    pp, pn = 0.2 + 0.3 * rng.random(system.n), 0.2 + 0.3 * rng.random(system.n)
+    _, _, gp, gn = [t.cpu().numpy() for t in system.loads(cuda(pp), cuda(pn))]
+    egp, egn = o.boundary_load(om, pp, pn, op)
+    assert rel(gp, egp) < 1e-13 and rel(gn, egn) < 1e-13
+    flat = o.boundary_load(om, pp, pn, o.Params(**{**op.__dict__, "pattern": 0}))
+    assert rel(gp, flat[0]) > 1e-3  # the pattern changes the load
+
+
 @pytest.mark.parametrize("kw", CASES[:3])
 def test_rhs_and_operator_parity(lib, kw):
     cp, op = make(lib, **kw)
@@ -236,6 +254,16 @@ def test_step_parity_3d_subsize(lib, precision):
     _, out = run_pair(lib, 3, base=(0.30, 0.30), dim=3, nx=16, ny=16, nz=4, Lz=0.25, rtol=1e-13,
                       precision=precision)
     for k, (stats, g, _, nxt) in enumerate(out):
+        for gk, ok in FIELDS:
+            assert rel(g[gk], getattr(nxt, ok)) < 1e-10, (k, gk)
+
+
+def test_patterned_substrate_step_parity(lib):
+    """Two steps on Section 4's 10 x 2.5 box (37 x 23 cells: breakpoints inside facets) with the
+    patterned substrate against the oracle's steps from the same inputs."""
+    _, out = run_pair(lib, 2, nx=37, ny=23, Lx=10.0, Ly=2.5, pattern=1, rtol=1e-13, max_iter=1000)
+    for k, (stats, g, _, nxt) in enumerate(out):
+        assert stats["status"] == 0
         for gk, ok in FIELDS:
             assert rel(g[gk], getattr(nxt, ok)) < 1e-10, (k, gk)
 
