@@ -268,6 +268,45 @@ def extra_sections(torch, ch, np, K, W, flush, ranks):
                                                                     "H": [r for r, _ in pc3.levels(1)]},
         "top_kernels": top_kernels(prof3)}
     del st3, pc3, sys3
+    out["paper_2d_minres_fig1"] = paper_2d_section(torch, ch, np, flush, ranks)
+    return out
+
+
+def paper_2d_section(torch, ch, np, flush, ranks):
+    """The paper's 2D solver experiment (Section 4, Fig. 1): the 10 x 2.5 box with nx x ny grid
+    points, phi_p = phi_nfa = 0.35 +/- 0.01 (seed 0), tau 1e-4, eps 1e-3, preconditioned MINRES
+    (krylov = 1; Algorithm 1 with fixed FP64 V-cycles) to a 1e-7 relative residual.  Iterations:
+    the worst of the two species over the first 20 steps (the figure's measure); time: the next
+    10 steps.  800 x 400 also runs with Section 4's patterned substrate (pattern = 1)."""
+    out = {}
+    cases = [(100, 50, 0), (200, 100, 0), (400, 200, 0), (800, 400, 0), (1600, 800, 0), (800, 400, 1)]
+    for npx, npy, pattern in cases:
+        p = ch.Params(nx=npx - 1, ny=npy - 1, Lx=10.0, Ly=2.5, krylov=1, rtol=1e-7, pattern=pattern)
+        system = ch.System(ch.Mesh(p), p)
+        state = ch.State(system, ch.Precond(system))
+        state.init_seeded(0.35, 0.35, 0.01, seed=0)
+        its = [max(state.step()["iters"]) for _ in range(20)]
+        torch.cuda.synchronize()
+        ranks.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        worst, failed = 0.0, 0
+        for _ in range(10):
+            flush.zero_()
+            st = state.step()
+            failed += st["status"] != 0
+            worst = max(worst, max(st["relres"]))
+        e1.record()
+        torch.cuda.synchronize()
+        ranks.barrier()
+        ms = ranks.max(e0.elapsed_time(e1)) / 10
+        key = f"{npx}x{npy}" + ("_patterned" if pattern else "")
+        out[key] = {"points": system.n, "minres_iters_max_first20": int(max(its)),
+                    "minres_iters_min_first20": int(min(its)), "minres_iters_first20": [int(i) for i in its],
+                    "ms_per_step_both_species": ms,
+                    "steps_per_s": ranks.rate(10, 10 * ms), "max_relres_timed": worst,
+                    "failed_steps_timed": int(failed)}
+        del state, system
     return out
 
 
