@@ -268,45 +268,67 @@ def extra_sections(torch, ch, np, K, W, flush, ranks):
                                                                     "H": [r for r, _ in pc3.levels(1)]},
         "top_kernels": top_kernels(prof3)}
     del st3, pc3, sys3
-    out["paper_2d_minres_fig1"] = paper_2d_section(torch, ch, np, flush, ranks)
+    out["paper_minres"] = paper_section(torch, ch, flush, ranks)
     return out
 
 
-def paper_2d_section(torch, ch, np, flush, ranks):
-    """The paper's 2D solver experiment (Section 4, Fig. 1): the 10 x 2.5 box with nx x ny grid
-    points, phi_p = phi_nfa = 0.35 +/- 0.01 (seed 0), tau 1e-4, eps 1e-3, preconditioned MINRES
-    (krylov = 1; Algorithm 1 with fixed FP64 V-cycles) to a 1e-7 relative residual.  Iterations:
-    the worst of the two species over the first 20 steps (the figure's measure); time: the next
-    10 steps.  800 x 400 also runs with Section 4's patterned substrate (pattern = 1)."""
+def minres_case(torch, ch, flush, ranks, **kw):
+    """One of the paper's solver experiments (Section 4): phi_p = phi_nfa = 0.35 +/- 0.01 (seed 0),
+    preconditioned MINRES (krylov = 1; Algorithm 1 with fixed FP64 V-cycles) to a 1e-7 relative
+    residual.  Iterations: the worse species of each of the first 20 steps (the figures' measure);
+    time: the next 10 steps (CUDA events, L2 flushed between steps)."""
+    p = ch.Params(krylov=1, rtol=1e-7, **kw)
+    system = ch.System(ch.Mesh(p), p)
+    state = ch.State(system, ch.Precond(system))
+    state.init_seeded(0.35, 0.35, 0.01, seed=0)
+    its = [max(state.step()["iters"]) for _ in range(20)]
+    torch.cuda.synchronize()
+    ranks.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    worst, failed = 0.0, 0
+    for _ in range(10):
+        flush.zero_()
+        st = state.step()
+        failed += st["status"] != 0
+        worst = max(worst, max(st["relres"]))
+    e1.record()
+    torch.cuda.synchronize()
+    ranks.barrier()
+    ms = ranks.max(e0.elapsed_time(e1)) / 10
+    out = {"points": system.n, "minres_iters_max_first20": int(max(its)),
+           "minres_iters_min_first20": int(min(its)), "minres_iters_first20": [int(i) for i in its],
+           "ms_per_step_both_species": ms, "steps_per_s": ranks.rate(10, 10 * ms),
+           "max_relres_timed": worst, "failed_steps_timed": int(failed)}
+    del state, system
+    return out
+
+
+def paper_section(torch, ch, flush, ranks):
+    """The paper's solver experiments on its boxes (Section 4): 2D 10 x 2.5 with nx x ny grid
+    points (Fig. 1), 3D 10 x 2.5 x 10 with nx x ny x nz points (Fig. 3), and at 800 x 400 points
+    the interface parameter (Fig. 4) and time step (Fig. 5) sweeps and the patterned substrate.
+    tau 1e-4 and eps 1e-3 unless swept.  A case that raises is recorded, not fatal."""
+    box2 = dict(Lx=10.0, Ly=2.5)
+    box3 = dict(dim=3, Lx=10.0, Ly=2.5, Lz=10.0)
+    groups = {
+        "fig1_2d": {f"{a}x{b}": dict(nx=a - 1, ny=b - 1, **box2)
+                    for a, b in ((100, 50), (200, 100), (400, 200), (800, 400), (1600, 800))},
+        "fig3_3d": {f"{a}x{b}x{c}": dict(nx=a - 1, ny=b - 1, nz=c - 1, **box3)
+                    for a, b, c in ((30, 15, 30), (40, 20, 40), (60, 30, 60), (80, 40, 80),
+                                    (120, 60, 120), (160, 80, 160))},
+        "fig4_eps_800x400": {f"eps={e:g}": dict(nx=799, ny=399, eps=e, **box2) for e in (1e-2, 1e-1, 1.0, 10.0)},
+        "fig5_tau_800x400": {f"tau={t:g}": dict(nx=799, ny=399, tau=t, **box2) for t in (1e-7, 1e-6, 1e-5)},
+        "patterned_800x400": {"pattern=1": dict(nx=799, ny=399, pattern=1, **box2)},
+    }
     out = {}
-    cases = [(100, 50, 0), (200, 100, 0), (400, 200, 0), (800, 400, 0), (1600, 800, 0), (800, 400, 1)]
-    for npx, npy, pattern in cases:
-        p = ch.Params(nx=npx - 1, ny=npy - 1, Lx=10.0, Ly=2.5, krylov=1, rtol=1e-7, pattern=pattern)
-        system = ch.System(ch.Mesh(p), p)
-        state = ch.State(system, ch.Precond(system))
-        state.init_seeded(0.35, 0.35, 0.01, seed=0)
-        its = [max(state.step()["iters"]) for _ in range(20)]
-        torch.cuda.synchronize()
-        ranks.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        worst, failed = 0.0, 0
-        for _ in range(10):
-            flush.zero_()
-            st = state.step()
-            failed += st["status"] != 0
-            worst = max(worst, max(st["relres"]))
-        e1.record()
-        torch.cuda.synchronize()
-        ranks.barrier()
-        ms = ranks.max(e0.elapsed_time(e1)) / 10
-        key = f"{npx}x{npy}" + ("_patterned" if pattern else "")
-        out[key] = {"points": system.n, "minres_iters_max_first20": int(max(its)),
-                    "minres_iters_min_first20": int(min(its)), "minres_iters_first20": [int(i) for i in its],
-                    "ms_per_step_both_species": ms,
-                    "steps_per_s": ranks.rate(10, 10 * ms), "max_relres_timed": worst,
-                    "failed_steps_timed": int(failed)}
-        del state, system
+    for g, cases in groups.items():
+        out[g] = {}
+        for name, kw in cases.items():
+            try:
+                out[g][name] = minres_case(torch, ch, flush, ranks, **kw)
+            except ch.ChError as e:  # a library status (e.g. out of memory) raised by the binding
+                out[g][name] = {"error": str(e)[:200]}
     return out
 
 
