@@ -4,7 +4,7 @@ The network (``ch.WarmStartNet``, kernels in ``csrc/warmstart.cu``) predicts the
 from the states at steps k and k-1 on the nodal image of a 2D structured mesh, as a learned
 correction to the linear extrapolation 2 s_k - s_{k-1}; ``ch_step_guess`` takes the prediction as
 FGMRES's initial iterate wherever its true FP64 residual beats that of the previous state, so the
-FP64 residual remains the judge and the previous step the fallback.
+FP64 residual decides between it and the previous step, which stays the fallback.
 
     data = generate_pairs(nx, ny, seeds=range(20), steps=100, dtype=torch.float64)  # plain solver
     net = ch.WarmStartNet(ny + 1, nx + 1, 8)
