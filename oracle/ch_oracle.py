@@ -17,6 +17,8 @@ plain numpy / scipy, in float64, with no blocking or fusion:
 * Solver.step    -- one semi-implicit step Eq. (12)/(13): the exact solution of
                     Eq. (14) for both species by a direct factorisation
 * schur / schur_tilde -- S and its matching approximation (Section 3, Lemma 1)
+* chebyshev_semi_iteration -- M~ by the Chebyshev semi-iteration Section 3 names as the
+                    alternative to AMG (Jacobi-preconditioned, Wathen's eigenvalue bounds)
 
 Readings of points the paper leaves open (each also listed in the design doc):
   R1 the discrete coefficient of K phi in the mu equation is eps (Eq. (12)/(14)),
@@ -461,3 +463,40 @@ def algorithm1_exact(M, K, p: Params, v1: np.ndarray, v2: np.ndarray):
     w2 = M @ w2
     w2 = spla.spsolve(H, w2)
     return w1, w2
+
+
+# ----------------------------------------------------------------------------
+# M~ by a Chebyshev semi-iteration (Section 3: the alternative to AMG for the
+# mass matrix; Wathen & Rees 2008)
+# ----------------------------------------------------------------------------
+WATHEN_BOUNDS = {2: (0.5, 2.0), 3: (0.5, 2.5)}  # eig(D^-1 M) for P1 triangles / tetrahedra
+
+
+def chebyshev_semi_iteration(M, b: np.ndarray, steps: int, bounds=None, dim: int = 2):
+    """x_k ~ M^-1 b by k steps of the Chebyshev semi-iteration on the Jacobi-preconditioned system
+    D^-1 M x = D^-1 b (D = diag(M)), started from x_0 = 0, for eigenvalues of D^-1 M in
+    [lo, hi] (default: Wathen's bounds for the element type).
+
+    The iterate is x_k = q_k(D^-1 M) D^-1 b with 1 - t q_k(t) = T_k((th - t) / de) / T_k(th / de),
+    th = (hi + lo) / 2, de = (hi - lo) / 2: the residual polynomial of least maximum on
+    [lo, hi].  It is computed by the three-term recurrence of the Chebyshev polynomials
+    (x_{k+1} = x_k + d_k with d_k mixing d_{k-1} and the preconditioned residual)."""
+    lo, hi = bounds if bounds is not None else WATHEN_BOUNDS[dim]
+    th, de = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    sigma = th / de
+    dinv = 1.0 / M.diagonal()
+    x = np.zeros_like(b, dtype=np.float64)
+    if steps <= 0:
+        return x
+    dinv_b = dinv[:, None] * b if b.ndim == 2 else dinv * b
+    d = dinv_b / th                       # first step: Jacobi damped by 1 / th
+    rho = 1.0 / sigma
+    x = x + d
+    for _ in range(1, steps):
+        r = b - M @ x
+        z = dinv[:, None] * r if r.ndim == 2 else dinv * r
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        d = rho_new * rho * d + (2.0 * rho_new / de) * z
+        x = x + d
+        rho = rho_new
+    return x

@@ -534,3 +534,61 @@ def test_patterned_substrate_brute_force_2d():
     np.add.at(bn, right, vn * t)
     np.testing.assert_allclose(gp, bp, rtol=0, atol=2e-6 * np.abs(bp).max())
     np.testing.assert_allclose(gn, bn, rtol=0, atol=2e-6 * np.abs(bn).max())
+
+
+# ---------------------------------------------------------------- Chebyshev semi-iteration for M~
+def _cheb_T(k, x):
+    """Chebyshev polynomial of the first kind, from its closed form (|x| >= 1 here as well)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    inside = np.abs(x) <= 1.0
+    out[inside] = np.cos(k * np.arccos(x[inside]))
+    xo = x[~inside]
+    out[~inside] = np.sign(xo) ** k * np.cosh(k * np.arccosh(np.abs(xo)))
+    return out
+
+
+@pytest.mark.parametrize("dim,bounds", [(2, None), (3, None), (2, (0.4, 2.3))])
+def test_chebyshev_semi_iteration_is_the_chebyshev_polynomial(dim, bounds):
+    """x_k = sum_j q_k(l_j) (v_j . b) v_j over the D-orthonormal generalized eigenpairs M v = l D v,
+    with 1 - l q_k(l) = T_k((th - l) / de) / T_k(th / de): the definition, by eigendecomposition."""
+    p = o.Params(nx=5, ny=4) if dim == 2 else o.Params(dim=3, nx=3, ny=2, nz=2)
+    M, _ = o.assemble(o.mesh(p))
+    Md = M.toarray()
+    lam, V = sla.eigh(Md, np.diag(np.diag(Md)))      # V^T D V = I
+    lo, hi = bounds if bounds else o.WATHEN_BOUNDS[dim]
+    th, de = (hi + lo) / 2, (hi - lo) / 2
+    b = np.random.default_rng(4).standard_normal(M.shape[0])
+    for k in range(1, 7):
+        q = (1.0 - _cheb_T(k, (th - lam) / de) / _cheb_T(k, np.array([th / de]))[0]) / lam
+        ref = V @ (q * (V.T @ b))
+        got = o.chebyshev_semi_iteration(M, b, k, bounds=bounds, dim=dim)
+        np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_chebyshev_semi_iteration_error_bound(dim):
+    """With the spectrum inside [lo, hi]: ||M^-1 b - x_k||_M <= ||M^-1 b||_M / T_k(th / de)
+    = 2 c^k / (1 + c^2k) ||M^-1 b||_M, c = (sqrt(kappa) - 1) / (sqrt(kappa) + 1), kappa = hi / lo."""
+    p = o.Params(nx=12, ny=9) if dim == 2 else o.Params(dim=3, nx=5, ny=4, nz=3)
+    M, _ = o.assemble(o.mesh(p))
+    b = np.random.default_rng(5).standard_normal(M.shape[0])
+    x = spla.spsolve(M.tocsc(), b)
+    lo, hi = o.WATHEN_BOUNDS[dim]
+    c = (math.sqrt(hi / lo) - 1) / (math.sqrt(hi / lo) + 1)
+    nrm = math.sqrt(x @ (M @ x))
+    for k in range(1, 13):
+        e = x - o.chebyshev_semi_iteration(M, b, k, dim=dim)
+        assert math.sqrt(e @ (M @ e)) <= (2 * c ** k / (1 + c ** (2 * k))) * nrm * (1 + 1e-10), k
+
+
+def test_chebyshev_semi_iteration_is_a_fixed_spd_operator():
+    """A fixed number of steps is a fixed linear operator q_k(D^-1 M) D^-1: symmetric and positive
+    definite, so it can serve as M~ inside MINRES; it also acts column by column on a block."""
+    M, _ = o.assemble(o.mesh(o.Params(nx=6, ny=5)))
+    n = M.shape[0]
+    C = o.chebyshev_semi_iteration(M, np.eye(n), 4)
+    np.testing.assert_allclose(C, C.T, rtol=0, atol=1e-13 * np.abs(C).max())
+    assert np.linalg.eigvalsh(0.5 * (C + C.T)).min() > 0
+    col = o.chebyshev_semi_iteration(M, np.eye(n)[:, 3], 4)
+    np.testing.assert_allclose(C[:, 3], col, rtol=0, atol=1e-15 * np.abs(col).max() + 1e-300)
