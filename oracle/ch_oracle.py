@@ -19,6 +19,8 @@ plain numpy / scipy, in float64, with no blocking or fusion:
 * schur / schur_tilde -- S and its matching approximation (Section 3, Lemma 1)
 * chebyshev_semi_iteration -- M~ by the Chebyshev semi-iteration Section 3 names as the
                     alternative to AMG (Jacobi-preconditioned, Wathen's eigenvalue bounds)
+* flory_huggins / dfdphi_fh / load_vector_fh -- the logarithmic bulk energy of Section 2
+                    and its load (reading R9)
 
 Readings of points the paper leaves open (each also listed in the design doc):
   R1 the discrete coefficient of K phi in the mu equation is eps (Eq. (12)/(14)),
@@ -37,6 +39,11 @@ Readings of points the paper leaves open (each also listed in the design doc):
   R7 no extra boundary term in the mu equation (natural condition grad phi . n = 0);
   R8 2D cells split along the lower-left/upper-right diagonal, 3D hexahedra into
      the 6 Kuhn tetrahedra; Gamma_b = {y = 0}, Gamma_t = {y = L_y}.
+  R9 the Flory-Huggins f (Section 2) is differentiated through phi_s like Eq. (15)
+     (R3), with Section 4's chi and N; its logarithms are evaluated at max(phi, delta)
+     (the positivity guard the paper's polynomial replacement avoids needing); its load
+     is defined by the collapsed 3-point Gauss-Legendre rule on each simplex, the
+     integrand not being a polynomial.
 """
 from __future__ import annotations
 
@@ -73,6 +80,13 @@ class Params:
     h_nfa: float = 0.0
     potential: str = "poly"    # reading R3
     pattern: int = 0           # substrate patterning p_p(x), p_nfa(x) of Section 4 (reading R6)
+    chi_pn: float = 1.0        # Flory-Huggins interaction parameters (Section 4)
+    chi_ps: float = 0.3
+    chi_ns: float = 0.3
+    N_p: float = 20.0          # degrees of polymerisation (Section 4)
+    N_nfa: float = 20.0
+    N_s: float = 1.0
+    fh_delta: float = 1e-10    # positivity guard: each logarithm at max(phi, fh_delta)
 
 
 # ----------------------------------------------------------------------------
@@ -500,3 +514,72 @@ def chebyshev_semi_iteration(M, b: np.ndarray, steps: int, bounds=None, dim: int
         x = x + d
         rho = rho_new
     return x
+
+
+# ----------------------------------------------------------------------------
+# The Flory-Huggins bulk energy (the logarithmic potential of Section 2, which the
+# paper's experiments replace by Eq. (15)) and its load by a fixed quadrature rule
+# ----------------------------------------------------------------------------
+def _guarded_log(x, delta):
+    return np.log(np.maximum(x, delta))
+
+
+def flory_huggins(pp: np.ndarray, pn: np.ndarray, p: Params):
+    """f(phi_p, phi_nfa, phi_s) with phi_s = 1 - phi_p - phi_nfa: the entropic terms phi ln(phi) / N
+    and the pairwise interactions chi phi phi'; logarithms guarded at fh_delta."""
+    ps = 1.0 - pp - pn
+    dl = p.fh_delta
+    return (pp / p.N_p * _guarded_log(pp, dl) + pn / p.N_nfa * _guarded_log(pn, dl)
+            + ps / p.N_s * _guarded_log(ps, dl)
+            + p.chi_pn * pp * pn + p.chi_ps * pp * ps + p.chi_ns * pn * ps)
+
+
+def dfdphi_fh(pp: np.ndarray, pn: np.ndarray, p: Params):
+    """df/dphi_p and df/dphi_nfa of the Flory-Huggins f through phi_s = 1 - phi_p - phi_nfa
+    (the chain rule of reading R3):
+      f_p' = (ln phi_p + 1)/N_p - (ln phi_s + 1)/N_s + chi_pn phi_n + chi_ps (phi_s - phi_p) - chi_ns phi_n
+      f_n' = (ln phi_n + 1)/N_n - (ln phi_s + 1)/N_s + chi_pn phi_p - chi_ps phi_p + chi_ns (phi_s - phi_n)."""
+    ps = 1.0 - pp - pn
+    dl = p.fh_delta
+    ls = (_guarded_log(ps, dl) + 1.0) / p.N_s
+    fp = ((_guarded_log(pp, dl) + 1.0) / p.N_p - ls + p.chi_pn * pn + p.chi_ps * (ps - pp) - p.chi_ns * pn)
+    fn = ((_guarded_log(pn, dl) + 1.0) / p.N_nfa - ls + p.chi_pn * pp - p.chi_ps * pp + p.chi_ns * (ps - pn))
+    return fp, fn
+
+
+def simplex_gauss_rule(d: int, n: int = 3):
+    """Collapsed (Duffy) Gauss-Legendre product rule on a d-simplex with n points per direction:
+    barycentric points (n^d, d+1) and weights summing to 1, so int_T g = |T| sum_q w_q g(x_q).
+    Exact for polynomials of degree 2n - d (the collapse adds d - 1 to the degree in the first
+    direction): 4 in 2D, 3 in 3D for n = 3."""
+    g, w = np.polynomial.legendre.leggauss(n)
+    g, w = 0.5 * (g + 1.0), 0.5 * w
+    if d == 2:
+        u, v = np.meshgrid(g, g, indexing="ij")
+        wu, wv = np.meshgrid(w, w, indexing="ij")
+        xi = np.c_[u.ravel(), (v * (1 - u)).ravel()]
+        wt = 2.0 * (wu * wv * (1 - u)).ravel()
+    elif d == 3:
+        u, v, t = np.meshgrid(g, g, g, indexing="ij")
+        wu, wv, wt3 = np.meshgrid(w, w, w, indexing="ij")
+        xi = np.c_[u.ravel(), (v * (1 - u)).ravel(), (t * (1 - u) * (1 - v)).ravel()]
+        wt = 6.0 * (wu * wv * wt3 * (1 - u) ** 2 * (1 - v)).ravel()
+    else:
+        raise ValueError("d must be 2 or 3")
+    return np.c_[1.0 - xi.sum(1), xi], wt
+
+
+def load_vector_fh(m: Mesh, pp: np.ndarray, pn: np.ndarray, p: Params, n: int = 3):
+    """F_s[i] = int df/dphi_s(phi_h) lambda_i for the Flory-Huggins f, each simplex integrated by
+    simplex_gauss_rule(d, n) (the rule defines the load: the integrand is not a polynomial)."""
+    d = m.dim
+    N = m.coords.shape[0]
+    vol, _ = simplex_measure_and_gradients(m.coords[m.elems])
+    lam, w = simplex_gauss_rule(d, n)                           # (Q, d+1), (Q,)
+    php = pp[m.elems] @ lam.T                                   # (E, Q) phi_h at the points
+    phn = pn[m.elems] @ lam.T
+    fp, fn = dfdphi_fh(php, phn, p)
+    Fp, Fn = np.zeros(N), np.zeros(N)
+    np.add.at(Fp, m.elems, vol[:, None] * ((fp * w) @ lam))
+    np.add.at(Fn, m.elems, vol[:, None] * ((fn * w) @ lam))
+    return Fp, Fn

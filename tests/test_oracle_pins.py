@@ -4,6 +4,7 @@ None of these compare the oracle with itself: each expected value comes from a
 closed form, a brute-force computation by a different method, an invariant of
 the scheme, or a bound the paper proves (Lemma 1).
 """
+import itertools
 import math
 import os
 
@@ -592,3 +593,94 @@ def test_chebyshev_semi_iteration_is_a_fixed_spd_operator():
     assert np.linalg.eigvalsh(0.5 * (C + C.T)).min() > 0
     col = o.chebyshev_semi_iteration(M, np.eye(n)[:, 3], 4)
     np.testing.assert_allclose(C[:, 3], col, rtol=0, atol=1e-15 * np.abs(col).max() + 1e-300)
+
+
+# ---------------------------------------------------------------- Flory-Huggins bulk energy
+def test_flory_huggins_derivative_matches_finite_differences():
+    """f_p', f_n' are the derivatives of f(phi_p, phi_n, 1 - phi_p - phi_n) (chain rule, R3)."""
+    p = o.Params()
+    rng = np.random.default_rng(8)
+    pp, pn = 0.05 + 0.4 * rng.random(50), 0.05 + 0.4 * rng.random(50)
+    fp, fn = o.dfdphi_fh(pp, pn, p)
+    h = 1e-6
+    fd_p = (o.flory_huggins(pp + h, pn, p) - o.flory_huggins(pp - h, pn, p)) / (2 * h)
+    fd_n = (o.flory_huggins(pp, pn + h, p) - o.flory_huggins(pp, pn - h, p)) / (2 * h)
+    np.testing.assert_allclose(fp, fd_p, rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose(fn, fd_n, rtol=1e-7, atol=1e-9)
+
+
+def test_flory_huggins_exchange_symmetry():
+    """With N_p = N_n and chi_ps = chi_ns (Section 4's values) f is symmetric in phi_p, phi_n, so
+    f_n'(a, b) = f_p'(b, a)."""
+    p = o.Params()
+    rng = np.random.default_rng(9)
+    a, b = 0.05 + 0.4 * rng.random(20), 0.05 + 0.4 * rng.random(20)
+    np.testing.assert_allclose(o.dfdphi_fh(a, b, p)[1], o.dfdphi_fh(b, a, p)[0], rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("d,deg", [(2, 4), (3, 3)])
+def test_simplex_gauss_rule_exact_to_its_degree(d, deg):
+    """sum_q w_q lambda^alpha(x_q) = d! alpha! / (d + |alpha|)! for every |alpha| <= the rule's
+    degree (the closed form of the monomial integrals, divided by |T|), and not beyond."""
+    lam, w = o.simplex_gauss_rule(d, 3)
+    assert math.isclose(w.sum(), 1.0, rel_tol=1e-14)
+    worst_next = 0.0
+    for alpha in itertools.product(range(deg + 2), repeat=d + 1):
+        k = sum(alpha)
+        if k > deg + 1:
+            continue
+        exact = math.factorial(d) * np.prod([math.factorial(a) for a in alpha]) / math.factorial(d + k)
+        got = float(np.sum(w * np.prod(lam ** np.array(alpha), axis=1)))
+        if k <= deg:
+            assert math.isclose(got, exact, rel_tol=1e-13), alpha
+        else:
+            worst_next = max(worst_next, abs(got - exact) / exact)
+    assert worst_next > 1e-6  # degree deg + 1 is not integrated exactly
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_flory_huggins_load_of_a_constant_state(dim):
+    """For constant phi the integrand is f'(c) lambda_i: F_i = f'(c) sum_{T ni i} |T| / (d + 1)."""
+    p = o.Params(dim=dim, nx=4, ny=3, nz=2 if dim == 3 else 0, Lx=2.0, Ly=1.0, Lz=1.0)
+    m = o.mesh(p)
+    N = m.coords.shape[0]
+    Fp, Fn = o.load_vector_fh(m, np.full(N, 0.3), np.full(N, 0.25), p)
+    fp, fn = o.dfdphi_fh(np.array([0.3]), np.array([0.25]), p)
+    vol, _ = o.simplex_measure_and_gradients(m.coords[m.elems])
+    share = np.zeros(N)
+    np.add.at(share, m.elems, np.repeat(vol[:, None] / (dim + 1), dim + 1, axis=1))
+    np.testing.assert_allclose(Fp, fp[0] * share, rtol=1e-13)
+    np.testing.assert_allclose(Fn, fn[0] * share, rtol=1e-13)
+
+
+def test_flory_huggins_load_converges_to_the_integral():
+    """The 3-point rule's load approaches a 10-point rule's (the integral to round-off) at the
+    rule's order: halving h cuts the relative gap by > 8 (degree 4 exact in 2D: O(h^5) per element
+    against O(h^2) measure)."""
+    gaps = []
+    for n in (8, 16):
+        p = o.Params(nx=n, ny=n)
+        m = o.mesh(p)
+        x, y = m.coords[:, 0], m.coords[:, 1]
+        pp = 0.3 + 0.1 * np.sin(2 * np.pi * x) * np.cos(np.pi * y)
+        pn = 0.3 + 0.1 * np.cos(2 * np.pi * y)
+        a = o.load_vector_fh(m, pp, pn, p, n=3)[0]
+        b = o.load_vector_fh(m, pp, pn, p, n=10)[0]
+        gaps.append(np.abs(a - b).max() / np.abs(b).max())
+    assert gaps[0] < 1e-5 and gaps[1] < gaps[0] / 8, gaps
+
+
+def test_flory_huggins_guard():
+    """At or below zero the logarithms take max(phi, delta): the load stays finite; for phi above
+    delta everywhere the guard changes nothing."""
+    p = o.Params(nx=4, ny=4)
+    m = o.mesh(p)
+    N = m.coords.shape[0]
+    pp = np.full(N, 0.3)
+    pp[::3] = -0.01
+    pn = np.full(N, 0.3)
+    assert all(np.isfinite(F).all() for F in o.load_vector_fh(m, pp, pn, p))
+    q = np.full(N, 0.3)
+    a = o.load_vector_fh(m, q, q, p)
+    b = o.load_vector_fh(m, q, q, o.Params(**{**p.__dict__, "fh_delta": 1e-300}))
+    np.testing.assert_array_equal(a[0], b[0])
