@@ -20,7 +20,7 @@ plain numpy / scipy, in float64, with no blocking or fusion:
 * chebyshev_semi_iteration -- M~ by the Chebyshev semi-iteration Section 3 names as the
                     alternative to AMG (Jacobi-preconditioned, Wathen's eigenvalue bounds)
 * flory_huggins / dfdphi_fh / load_vector_fh -- the logarithmic bulk energy of Section 2
-                    and its load (reading R9)
+                    and its load (reading R14)
 
 Readings of points the paper leaves open (each also listed in the design doc):
   R1 the discrete coefficient of K phi in the mu equation is eps (Eq. (12)/(14)),
@@ -39,7 +39,7 @@ Readings of points the paper leaves open (each also listed in the design doc):
   R7 no extra boundary term in the mu equation (natural condition grad phi . n = 0);
   R8 2D cells split along the lower-left/upper-right diagonal, 3D hexahedra into
      the 6 Kuhn tetrahedra; Gamma_b = {y = 0}, Gamma_t = {y = L_y}.
-  R9 the Flory-Huggins f (Section 2) is differentiated through phi_s like Eq. (15)
+  R14 the Flory-Huggins f (Section 2) is differentiated through phi_s like Eq. (15)
      (R3), with Section 4's chi and N; its logarithms are evaluated at max(phi, delta)
      (the positivity guard the paper's polynomial replacement avoids needing); its load
      is defined by the collapsed 3-point Gauss-Legendre rule on each simplex, the
