@@ -154,7 +154,9 @@ void ch_system_destroy(ch_system_t* s);
 
 /* Explicit loads of one step (Eq. (12), right-hand sides): F_s[i] = int f_s'(phi_h) lambda_i,
  * exact for the polynomial potential Eq. (15), and the boundary loads g_s of the flux
- * conditions Eq. (10).  Inputs N fp64; outputs N fp64 (any output may be NULL). */
+ * conditions Eq. (10), with Section 4's substrate pattern when the system's pattern = 1 (its
+ * per-facet weights are formed once by ch_assemble).  Inputs N fp64; outputs N fp64 (any output
+ * may be NULL). */
 ch_status ch_loads(const ch_system_t* s, const double* phi_p, const double* phi_nfa,
                    double* F_p, double* F_nfa, double* g_p, double* g_nfa, void* stream);
 /* Right-hand sides of Eq. (14) for both species, b (N x 4) = (M phi_p + tau g_p, M phi_nfa + tau g_nfa,
