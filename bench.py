@@ -381,7 +381,7 @@ def learned_section(torch, ch, nx, K, flush, ranks):
     return out
 
 
-def roofline(prof, peaks, sustained):
+def roofline(prof, peaks):
     """Dominant kernel (largest summed event time) against its bound."""
     name, e = max(prof.items(), key=lambda kv: kv[1]["ms"])
     per_launch_ms = e["ms"] / e["launches"]
@@ -501,7 +501,7 @@ def main():
     torch.cuda.synchronize()
     prof64 = ch.profile_read(reset=True)
     ch.profile_enable(False)
-    roof = roofline(prof64, peaks, sustained=True)
+    roof = roofline(prof64, peaks)
 
     # ---- end to end through the public API with host buffers
     sysE, pcE, stateE = make_solver(ch, args.nx, args.ny, precision=0)
@@ -555,7 +555,7 @@ def main():
         mixed = {"value": ranks.rate(K, ms_m), "ms_per_step": ms_m / K,
                  "iters_per_step_mean": float(np.mean(iters_m)),
                  "max_rel_diff_phi_vs_fp64_form_after_run": diff,
-                 "roofline": roofline(profm, peaks, sustained=True), "top_kernels": top_kernels(profm)}
+                 "roofline": roofline(profm, peaks), "top_kernels": top_kernels(profm)}
         del sysM, pcM, stateM
 
     # ---- batched workload: 64 independent runs of uneven size in one state (FP32 V-cycles)
