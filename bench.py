@@ -560,7 +560,9 @@ def main():
 
     # ---- batched workload: 64 independent runs of uneven size in one state (FP32 V-cycles)
     batch = None
-    if not args.no_batch:
+    # the auxiliary sections below run at N = 1 only: N replicas would repeat them without adding
+    # information while holding all N GPUs for minutes
+    if not args.no_batch and world == 1:
         from paper_2204_03575_gb300 import inputs
         spec = inputs.batch_runs(64, seed=0)
         pb = ch.Params(precision=1)
@@ -589,12 +591,12 @@ def main():
     # ---- the other configurations' throughput lines: 32x32 (launch-bound), FGMRES iterations per
     # step against the mesh size, and the 3D Kuhn-tetrahedra box in the mixed form
     extra = None
-    if not args.no_extra:
+    if not args.no_extra and world == 1:
         extra = extra_sections(torch, ch, np, K, W, flush, ranks)
 
     # ---- learned warm start (256 x 256 grid): training, then FP64 / mixed with and without it
     learned = None
-    if not args.no_learned:
+    if not args.no_learned and world == 1:
         learned = learned_section(torch, ch, args.learned_nx, min(K, 40), flush, ranks)
 
     cpu = None
