@@ -718,3 +718,24 @@ def test_minres_with_exact_algorithm1_matches_the_papers_iteration_counts():
             k_true = next(k + 1 for k, r in enumerate(hist) if r <= 1e-7 * np.linalg.norm(b))
             assert 16 <= k_true <= 20, k_true
         st = s.step(st)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mass_balance_with_patterned_substrate(dim):
+    """Section 4's pattern halves each species' substrate inflow: over a step the total mass changes
+    by tau (g |Gamma_b| / 2 + k int_{Gamma_t} phi phi_s), and with constant phi the flux is
+    g area / 2 + k c_p (1 - c_p - c_n) area (unaligned mesh, nx = 7)."""
+    p = o.Params(dim=dim, nx=7, ny=4, nz=3 if dim == 3 else 0, Lx=10.0, Ly=2.5, Lz=2.0,
+                 tau=1e-3, pattern=1)
+    s = o.Solver(p)
+    pp, pn = inputs.initial_state(s.N, 0.35, 0.30, seed=2)
+    nxt = s.step(o.initial(s.N, pp, pn))
+    gp, gn = o.boundary_load(s.m, pp, pn, p)
+    for phi0, phi1, g in ((pp, nxt.phi_p, gp), (pn, nxt.phi_nfa, gn)):
+        dm = o.mass(s.M, phi1) - o.mass(s.M, phi0)
+        assert math.isclose(dm, p.tau * g.sum(), rel_tol=1e-9, abs_tol=1e-15)
+    c = o.initial(s.N, np.full(s.N, 0.35), np.full(s.N, 0.30))
+    gpc, gnc = o.boundary_load(s.m, c.phi_p, c.phi_nfa, p)
+    area = p.Lx * (p.Lz if dim == 3 else 1.0)
+    assert math.isclose(gpc.sum(), 0.01 * area / 2 + 5e-3 * 0.35 * 0.35 * area, rel_tol=1e-13)
+    assert math.isclose(gnc.sum(), 0.01 * area / 2 + 5e-3 * 0.30 * 0.35 * area, rel_tol=1e-13)
