@@ -21,6 +21,9 @@ plain numpy / scipy, in float64, with no blocking or fusion:
                     alternative to AMG (Jacobi-preconditioned, Wathen's eigenvalue bounds)
 * flory_huggins / dfdphi_fh / load_vector_fh -- the logarithmic bulk energy of Section 2
                     and its load (reading R14)
+* chebyshev_smooth / vcycle / galerkin_levels -- one multigrid V-cycle over a given
+                    hierarchy (Chebyshev smoothing, P^T restriction, exact coarsest solve): the
+                    inner solves of Algorithm 1 written from their definition
 
 Readings of points the paper leaves open (each also listed in the design doc):
   R1 the discrete coefficient of K phi in the mu equation is eps (Eq. (12)/(14)),
@@ -583,3 +586,39 @@ def load_vector_fh(m: Mesh, pp: np.ndarray, pn: np.ndarray, p: Params, n: int = 
     np.add.at(Fp, m.elems, vol[:, None] * ((fp * w) @ lam))
     np.add.at(Fn, m.elems, vol[:, None] * ((fn * w) @ lam))
     return Fp, Fn
+
+
+# ----------------------------------------------------------------------------
+# A multigrid V-cycle over a given hierarchy (the inner solves of Algorithm 1)
+# ----------------------------------------------------------------------------
+def chebyshev_smooth(A, b: np.ndarray, x0: np.ndarray, degree: int, bounds):
+    """`degree` Chebyshev steps on D^-1 A x = D^-1 b from x0 for eigenvalues of D^-1 A in
+    [lo, hi]: x = x0 + q(D^-1 A) D^-1 (b - A x0), q the semi-iteration's polynomial."""
+    return x0 + chebyshev_semi_iteration(A, b - A @ x0, degree, bounds=bounds)
+
+
+def vcycle(levels, b: np.ndarray, x0: np.ndarray | None = None, level: int = 0):
+    """One V-cycle for A_0 x = b.  levels[l] = dict(A=A_l, P=P_l (rows of level l x rows of
+    level l+1), bounds=(lo, hi), degree=k) for every level but the last, whose dict holds only A
+    (solved exactly).  Per level: pre-smooth, restrict the residual with P^T, recurse from zero,
+    prolongate the correction, post-smooth with the same polynomial."""
+    L = levels[level]
+    A = L["A"]
+    if level == len(levels) - 1:
+        return np.linalg.solve(A.toarray() if sp.issparse(A) else A, b)
+    x = np.zeros_like(b, dtype=np.float64) if x0 is None else x0
+    x = chebyshev_smooth(A, b, x, L["degree"], L["bounds"])
+    r_c = L["P"].T @ (b - A @ x)
+    e_c = vcycle(levels, r_c, None, level + 1)
+    x = x + L["P"] @ e_c
+    return chebyshev_smooth(A, b, x, L["degree"], L["bounds"])
+
+
+def galerkin_levels(A, Ps, bounds_list, degrees):
+    """levels for `vcycle` from the fine matrix and prolongators: A_{l+1} = P_l^T A_l P_l."""
+    levels = []
+    for P, bd, k in zip(Ps, bounds_list, degrees):
+        levels.append(dict(A=A, P=P, bounds=bd, degree=k))
+        A = (P.T @ A @ P).tocsr()
+    levels.append(dict(A=A))
+    return levels
