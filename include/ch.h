@@ -178,6 +178,18 @@ ch_status ch_precond_setup(const ch_system_t* s, void* stream, ch_precond_t** ou
 /* which: 0 = M hierarchy, 1 = H hierarchy.  Host outputs; level-wise sizes for level < nlevels. */
 ch_status ch_precond_info(const ch_precond_t* pc, int32_t which, int32_t level, int32_t* nlevels,
                           int64_t* rows, int64_t* nnz);
+/* Level `level` of hierarchy `which` as the V-cycle uses it, for checking the V-cycle against an
+ * independent implementation.  Host outputs (any may be NULL): rows and nnz of A_l, nnz of P_l,
+ * the Chebyshev interval [lo, hi] of D^-1 A_l and the level's smoothing degree (the coarsest
+ * level has nnz_P = 0, lo = hi = 0 and degree 0: it is solved by its dense inverse).  Device
+ * outputs (any may be NULL; caller-owned, sized from a first call's host outputs): the FP64
+ * set-up matrices A_l (rowptr rows + 1, col nnz, val nnz) and P_l (rowptr rows + 1, col and val
+ * nnz_P; columns index level l + 1), copied on `stream`.  Precision 1 smooths with FP32 copies of
+ * these matrices. */
+ch_status ch_precond_level(const ch_precond_t* pc, int32_t which, int32_t level, int64_t* rows,
+                           int64_t* nnz, int64_t* nnz_P, double* lo, double* hi, int32_t* degree,
+                           int32_t* A_rowptr, int32_t* A_col, double* A_val, int32_t* P_rowptr,
+                           int32_t* P_col, double* P_val, void* stream);
 /* Lanes per row chosen for the level's A (smoothing, residual), R (restriction) and P
  * (prolongation) SpMVs (host outputs; R and P are 0 on the coarsest level). */
 ch_status ch_precond_tiles(const ch_precond_t* pc, int32_t which, int32_t level, int32_t* tpr_A,

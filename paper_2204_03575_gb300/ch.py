@@ -100,6 +100,9 @@ _SIGNATURES = {
     "ch_precond_info": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _I32P, _I64P, _I64P]),
     "ch_precond_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "ch_precond_tiles": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _I32P, _I32P, _I32P]),
+    "ch_precond_level": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _I64P, _I64P, _I64P,
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        _I32P, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "ch_vcycle": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
     "ch_precond_destroy": (None, [_VP]),
     "ch_vcycle_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
@@ -289,6 +292,27 @@ class Precond:
                    "ch_precond_tiles")
             out.append((a.value, r.value, q.value))
         return out
+
+    def level(self, which: int, l: int, stream=None):
+        """Level l of hierarchy `which` (0: M, 1: H) as the V-cycle uses it: dict with the FP64
+        CSR arrays of A (and P below the coarsest level) as device tensors, the Chebyshev interval
+        (lo, hi) of D^-1 A and the smoothing degree."""
+        rows, nnz, nnz_p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        lo, hi, deg = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        args = [ctypes.byref(rows), ctypes.byref(nnz), ctypes.byref(nnz_p), ctypes.byref(lo),
+                ctypes.byref(hi), ctypes.byref(deg)]
+        _check(lib().ch_precond_level(self._h, which, l, *args, None, None, None, None, None, None,
+                                      _stream(stream)), "ch_precond_level")
+        dev = torch.device("cuda")
+        n, z, zp = rows.value, nnz.value, nnz_p.value
+        A = (torch.empty(n + 1, dtype=torch.int32, device=dev), torch.empty(z, dtype=torch.int32, device=dev),
+             torch.empty(z, dtype=torch.float64, device=dev))
+        P = ((torch.empty(n + 1, dtype=torch.int32, device=dev), torch.empty(zp, dtype=torch.int32, device=dev),
+              torch.empty(zp, dtype=torch.float64, device=dev)) if zp else (None, None, None))
+        _check(lib().ch_precond_level(self._h, which, l, None, None, None, None, None, None,
+                                      *[_ptr(t) if t is not None else None for t in A + P],
+                                      _stream(stream)), "ch_precond_level")
+        return {"rows": n, "A": A, "P": P if zp else None, "bounds": (lo.value, hi.value), "degree": deg.value}
 
     def apply(self, v, stream=None):
         v = _f64(v, self.system.n)

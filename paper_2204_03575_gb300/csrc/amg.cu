@@ -898,6 +898,38 @@ void hierarchy_level_size(const Hierarchy* h, int l, int64_t* rows, int64_t* nnz
   if (nnz) *nnz = h->A[l].nnz;
 }
 
+// Level l as the V-cycle uses it: the FP64 set-up matrices A_l and P_l (device to device copies
+// into caller buffers), the Chebyshev interval [cheb_lower, 1] x 1.1 rho_l of D^-1 A_l and the
+// smoothing degree; the coarsest level has no P and no smoothing (dense inverse).
+ch_status hierarchy_level_export(const Hierarchy* h, int l, int64_t* rows, int64_t* nnz, int64_t* nnz_P,
+                                 double* lo, double* hi, int* degree, int* A_rowptr, int* A_col,
+                                 double* A_val, int* P_rowptr, int* P_col, double* P_val, cudaStream_t st) {
+  const Csr<double>& A = h->A[l];
+  const bool coarsest = l + 1 == h->nlev;
+  const int64_t np = coarsest ? 0 : h->P[l].nnz;
+  if (rows) *rows = A.nrows;
+  if (nnz) *nnz = A.nnz;
+  if (nnz_P) *nnz_P = np;
+  const double top = coarsest ? 0.0 : 1.1 * h->rho[l];
+  if (hi) *hi = top;
+  if (lo) *lo = h->cheb_lower * top;
+  if (degree) *degree = coarsest ? 0 : (l == 0 ? h->cheb_degree : h->cheb_degree_coarse);
+  const auto copy = [&](void* dst, const void* src, size_t bytes) -> ch_status {
+    if (dst && bytes) CH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+    return CH_OK;
+  };
+  CH_TRY(copy(A_rowptr, A.rowptr, sizeof(int) * ((size_t)A.nrows + 1)));
+  CH_TRY(copy(A_col, A.col, sizeof(int) * (size_t)A.nnz));
+  CH_TRY(copy(A_val, A.val, sizeof(double) * (size_t)A.nnz));
+  if (!coarsest) {
+    const Csr<double>& P = h->P[l];
+    CH_TRY(copy(P_rowptr, P.rowptr, sizeof(int) * ((size_t)P.nrows + 1)));
+    CH_TRY(copy(P_col, P.col, sizeof(int) * (size_t)P.nnz));
+    CH_TRY(copy(P_val, P.val, sizeof(double) * (size_t)P.nnz));
+  }
+  return CH_OK;
+}
+
 // ---------------------------------------------------------------- V-cycle kernels (2 RHS)
 template <typename T, typename V2>
 __device__ __forceinline__ V2 mk2(T a, T b) {

@@ -305,6 +305,18 @@ ch_status ch_precond_info(const ch_precond_t* pc, int32_t which, int32_t level, 
   return CH_OK;
 }
 
+ch_status ch_precond_level(const ch_precond_t* pc, int32_t which, int32_t level, int64_t* rows,
+                           int64_t* nnz, int64_t* nnz_P, double* lo, double* hi, int32_t* degree,
+                           int32_t* A_rowptr, int32_t* A_col, double* A_val, int32_t* P_rowptr,
+                           int32_t* P_col, double* P_val, void* stream) {
+  CH_ARG(pc != nullptr, "preconditioner is NULL");
+  CH_ARG(which == 0 || which == 1, "which must be 0 (M) or 1 (H)");
+  const ch::Hierarchy* h = which == 0 ? pc->hM : pc->hH;
+  CH_ARG(level >= 0 && level < ch::hierarchy_levels(h), "level out of range");
+  return ch::hierarchy_level_export(h, level, rows, nnz, nnz_P, lo, hi, degree, A_rowptr, A_col, A_val,
+                                    P_rowptr, P_col, P_val, S(stream));
+}
+
 ch_status ch_precond_tiles(const ch_precond_t* pc, int32_t which, int32_t level, int32_t* tpr_A,
                            int32_t* tpr_R, int32_t* tpr_P) {
   CH_ARG(pc != nullptr, "preconditioner is NULL");

@@ -203,6 +203,9 @@ ch_status hierarchy_build(const Csr<double>& A0, const FineLattice* lat, const c
 void hierarchy_free(Hierarchy* h);
 int hierarchy_levels(const Hierarchy* h);
 void hierarchy_level_size(const Hierarchy* h, int l, int64_t* rows, int64_t* nnz);
+ch_status hierarchy_level_export(const Hierarchy* h, int l, int64_t* rows, int64_t* nnz, int64_t* nnz_P,
+                                 double* lo, double* hi, int* degree, int* A_rowptr, int* A_col,
+                                 double* A_val, int* P_rowptr, int* P_col, double* P_val, cudaStream_t st);
 void hierarchy_level_tiles(const Hierarchy* h, int l, int* tA, int* tR, int* tP);
 // x (N x 2, fp64, row stride ldx) ~ A^-1 b (N x 2, fp64, row stride ldb), ncyc V-cycles
 ch_status hierarchy_solve(Hierarchy* h, const double* b, int ldb, double* x, int ldx, int ncyc,

@@ -97,6 +97,7 @@ def test_null_handles_rejected(L):
     assert L.ch_step(None, None, None) == ch.ERR_ARG
     assert L.ch_precond_apply(None, None, None, None) == ch.ERR_ARG
     assert L.ch_apply_A(None, None, None, None) == ch.ERR_ARG
+    assert L.ch_precond_level(None, 0, 0, *([None] * 12), None) == ch.ERR_ARG
     L.ch_state_destroy(None)
     L.ch_mesh_destroy(None)
 
