@@ -58,9 +58,10 @@ def workload_name(nx, ny):
 
 
 # ---------------------------------------------------------------- oracle (CPU) timing
-def oracle_rate(nx, ny, steps, warmup=0):
+def oracle_rate(nx, ny, steps, warmup=0, keep=False):
     """Oracle steps/s on the same workload: assembly + LU once, amortised over the run length;
-    `warmup` untimed steps run between the factorisation and the timed steps."""
+    `warmup` untimed steps run between the factorisation and the timed steps.  With keep, also
+    returns the oracle's state after every step (warm-up steps included)."""
     import numpy as np
     from oracle import ch_oracle as o
     from paper_2204_03575_gb300 import inputs
@@ -69,18 +70,34 @@ def oracle_rate(nx, ny, steps, warmup=0):
     t_setup = time.perf_counter() - t0
     pp, pn = inputs.initial_state(s.N, 0.33, 0.33, 0.01, seed=0)
     st = o.initial(s.N, pp, pn)
+    states = []
     for _ in range(warmup):
         st = s.step(st)
+        states.append(st)
     t0 = time.perf_counter()
     for _ in range(steps):
         st = s.step(st)
+        if keep:
+            states.append(st)
     t_steps = (time.perf_counter() - t0) / steps
     per_step = t_steps + t_setup / WORKLOAD_STEPS
     assert np.isfinite(st.phi_p).all()
-    sample = (f"{nx}x{ny} oracle (numpy/scipy, SuperLU direct solve): assembly+factorisation "
-              f"{t_setup:.1f} s once, {warmup} untimed and {steps} timed steps at {t_steps:.2f} s/step; "
-              f"rate = 1/(step + setup/{WORKLOAD_STEPS})")
+    sample = (f"{nx}x{ny} oracle (numpy/scipy, SuperLU direct solve) on 1 of {os.cpu_count()} host cores: "
+              f"assembly+factorisation {t_setup:.1f} s once, {warmup} untimed and {steps} timed steps at "
+              f"{t_steps:.2f} s/step; rate = 1/(step + setup/{WORKLOAD_STEPS})")
+    if keep:
+        return 1.0 / per_step, sample, t_setup, t_steps, states
     return 1.0 / per_step, sample, t_setup, t_steps
+
+
+def error_vs_oracle(gpu_traj, oracle_states):
+    """Max over the four fields of ||x_gpu - x_oracle||_inf / ||x_oracle||_inf after each step of
+    two runs from the same seeded initial state."""
+    out = []
+    for g, r in zip(gpu_traj, oracle_states):
+        out.append(max(float(abs(g[k] - getattr(r, k)).max() / abs(getattr(r, k)).max())
+                       for k in ("phi_p", "phi_nfa", "mu_p", "mu_nfa")))
+    return out
 
 
 def reference_main(args, rank):
@@ -94,6 +111,7 @@ def reference_main(args, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.nx, args.ny), "parallelism": "rank 0 only"},
             "cpu_baseline": {"kind": "oracle", "value": rate, "unit": UNIT, "cores": 1,
+                             "host_cores": os.cpu_count(),
                              "sample": sample + "; steps capped at 10, warm-up at 5"},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -382,7 +400,10 @@ def learned_section(torch, ch, nx, K, flush, ranks):
 
 
 def roofline(prof, peaks):
-    """Dominant kernel (largest summed event time) against its bound."""
+    """Dominant kernel (largest summed event time) against its bound.  Both fractions are given:
+    frac_hbm (algorithmic bytes per launch / event time against the measured HBM copy rate: the
+    unit of the >= 60 % target for SpMV and V-cycle kernels) and, for FP64 kernels, frac_alu
+    (FMAs against the FP64 pipe's peak).  `bound`/`frac` name the one that binds the kernel."""
     name, e = max(prof.items(), key=lambda kv: kv[1]["ms"])
     per_launch_ms = e["ms"] / e["launches"]
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -391,15 +412,23 @@ def roofline(prof, peaks):
     alu_balance = fp64_peak * 1e12 / 2 / (hbm * 1e9)  # FP64 FMA per byte at which both bounds meet
     out = {"kernel": name, "launches": e["launches"], "avg_launch_us": 1e3 * per_launch_ms,
            "share_of_kernel_time": e["ms"] / sum(v["ms"] for v in prof.values())}
+    ach_gbs = e["bytes"] / e["launches"] / (per_launch_ms * 1e-3) / 1e9
+    out["achieved_GBps"] = ach_gbs
+    out["frac_hbm"] = ach_gbs / hbm
+    hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"
+    if name.endswith("f64"):
+        ach_tf = 2 * e["fmas"] / e["launches"] / (per_launch_ms * 1e-3) / 1e12
+        out["achieved_TFLOPs_fp64"] = ach_tf
+        out["frac_alu"] = ach_tf / fp64_peak
     if name.endswith("f64") and fmas_per_byte > alu_balance:
-        ach = 2 * e["fmas"] / e["launches"] / (per_launch_ms * 1e-3) / 1e12
-        out.update({"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": ach / fp64_peak, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x "
-                    "max SM clock (measured probe: 1.20 TFLOP/s)"})
+        out.update({"bound": "alu", "achieved": out["achieved_TFLOPs_fp64"], "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": out["frac_alu"],
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x max SM clock "
+                                   "(measured probe: 1.20 TFLOP/s); frac_hbm against " + hbm_src})
     else:
-        ach = e["bytes"] / e["launches"] / (per_launch_ms * 1e-3) / 1e9
-        out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"})
+        out.update({"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": out["frac_hbm"],
+                    "peak_source": hbm_src})
+    out["target"] = "frac_hbm >= 0.6 (HBM roofline of the SpMV / V-cycle kernels)"
     out["algorithmic_bytes_per_launch"] = e["bytes"] / e["launches"]
     out["fmas_per_launch"] = e["fmas"] / e["launches"]
     out["traffic"] = traffic_for(name)
@@ -601,8 +630,25 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, sample, _, _ = oracle_rate(args.nx, args.ny, 2)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        # the GPU's FP64 and mixed trajectories of the first steps from the seeded state, at the
+        # default 1e-8 tolerance, next to the oracle's (exact direct solves) of the same steps
+        CB_W, CB_K = 1, 5
+        traj = {}
+        for prec, tag in ((0, "fp64"), (1, "mixed")):
+            _, _, stT = make_solver(ch, args.nx, args.ny, precision=prec)
+            t = []
+            for _ in range(CB_W + CB_K):
+                stT.step()
+                t.append({k: v.cpu().numpy() for k, v in stT.get().items()})
+            traj[tag] = t
+            del stT
+        rate, sample, _, _, ostates = oracle_rate(args.nx, args.ny, CB_K, warmup=CB_W, keep=True)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+               "sample": sample,
+               "error_vs_oracle_per_step": {tag: error_vs_oracle(t, ostates) for tag, t in traj.items()},
+               "error_note": "max over phi_p, phi_nfa, mu_p, mu_nfa of the relative inf-norm difference "
+                             "between the GPU run (rtol 1e-8) and the oracle's run after each of the "
+                             f"first {CB_W + CB_K} steps from the same seeded state"}
 
     levels = {"M": pc.levels(0), "H": pc.levels(1)}
     line = {
@@ -613,7 +659,8 @@ def main():
                    "l2": "flushed between steps (256 MiB write inside the timed region)",
                    "gpu_prewarm_s": args.prewarm_s,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+        "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "launches_per_step": launches / K,
+        "roofline": roof,
         "top_kernels": top_kernels(prof64),
         "iters_per_step_mean": float(np.mean(iters)), "iters_per_step_max": int(np.max(iters)),
         "amg_levels": {k: [r for r, _ in v] for k, v in levels.items()},

@@ -25,7 +25,7 @@ plain numpy / scipy, in float64, with no blocking or fusion:
                     hierarchy (Chebyshev smoothing, P^T restriction, exact coarsest solve): the
                     inner solves of Algorithm 1 written from their definition
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
   R1 the discrete coefficient of K phi in the mu equation is eps (Eq. (12)/(14)),
      not eps^2 as in the strong form Eq. (9);
   R2 mobilities are 1 unless given ("appropriate constants");

@@ -7,10 +7,10 @@
 //   strength  |a_ij| >= theta sqrt(a_ii a_jj), plus each row's strongest entry, symmetrised;
 //   MIS(2)    random-priority independent set at graph distance 2, roots become aggregates;
 //   P         (I - omega D^-1 A) T with T the aggregate indicator, omega = 4/(3 rho),
-//             rho the Gershgorin bound of D^-1 A;
+//             rho = min(Gershgorin bound, 1.05 x power-iteration estimate) of lambda_max(D^-1 A);
 //   A_c       = P^T A P (deterministic sparse products), down to <= coarse_max rows, whose
 //             dense inverse is formed on the device.
-// Smoothing is Chebyshev on D^-1 A over [cheb_lower, 1] * 1.1 rho, rho a power-iteration estimate.  Every set-up sum has a fixed
+// Smoothing is Chebyshev on D^-1 A over [cheb_lower, 1] * 1.1 rho, with the same rho.  Every set-up sum has a fixed
 // order, so the hierarchy is bitwise reproducible.  V-cycles run in FP64 or FP32 on two
 // right-hand sides at once (the two species share M and H).
 #include <algorithm>
@@ -65,7 +65,8 @@ struct Hierarchy {
   int nlev = 0;
   std::vector<Csr<double>> A, P, R;  // FP64 set-up results
   std::vector<double*> dinv;
-  std::vector<double> rho;            // Gershgorin bound of D^-1 A per level
+  std::vector<double> rho;            // per level: min(Gershgorin bound, 1.05 x power estimate) of
+                                      // lambda_max(D^-1 A); Chebyshev interval [lower, 1] x 1.1 rho
   std::vector<LevelT<double>> Ld;     // working copies (precision 0)
   std::vector<LevelT<float>> Lf;      // working copies (precision 1)
   int nc = 0;                         // coarsest size
@@ -954,12 +955,11 @@ __global__ void k_cheb_first(int n, const T* dinv, const V2* b, T invtheta, V2* 
 // Row sums of A x for both right-hand sides with TPR lanes per row: lane `sub` takes entries
 // sub, sub+TPR, ... of the row and a butterfly of shuffles adds the lanes' partial sums, so the
 // summation order is fixed for a given TPR.  Threads past the last row contribute zeros (no
-// early return before the shuffles).
+// early return before the shuffles).  row_acc adds onto the caller's (s0, s1), which lane 0 of a
+// row may seed (with -b: the sum is then A x - b at no extra FP64 instruction).
 template <typename T, typename V2, int TPR>
-__device__ __forceinline__ void row_sum(const Csr<T>& A, int row, int sub, const V2* __restrict__ x,
+__device__ __forceinline__ void row_acc(const Csr<T>& A, int row, int sub, const V2* __restrict__ x,
                                         T& s0, T& s1) {
-  s0 = 0;
-  s1 = 0;
   if (row < A.nrows) {
     const int e = A.rowptr[row + 1];
     for (int q = A.rowptr[row] + sub; q < e; q += TPR) {
@@ -976,25 +976,40 @@ __device__ __forceinline__ void row_sum(const Csr<T>& A, int row, int sub, const
   }
 }
 
-// r = b - A x;  d = alpha d + beta D^-1 r;  xo = x + d
+template <typename T, typename V2, int TPR>
+__device__ __forceinline__ void row_sum(const Csr<T>& A, int row, int sub, const V2* __restrict__ x,
+                                        T& s0, T& s1) {
+  s0 = 0;
+  s1 = 0;
+  row_acc<T, V2, TPR>(A, row, sub, x, s0, s1);
+}
+
+// r = b - A x;  d = alpha d + beta D^-1 r;  xo = x + d.  The row sum starts from -b, so it is
+// -r, and nbeta = -beta turns it back: d = alpha d + (nbeta D^-1) (A x - b), three FP64
+// instructions per right-hand side after the sum (multiply, fused multiply-add, add).
 template <typename T, typename V2, int TPR>
 __global__ void __launch_bounds__(TPB) k_cheb_step(Csr<T> A, const T* __restrict__ dinv,
                                                    const V2* __restrict__ b, const V2* __restrict__ x,
                                                    V2* __restrict__ d, V2* __restrict__ xo, T alpha,
-                                                   T beta) {
+                                                   T nbeta) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / TPR, sub = t % TPR;
-  T s0, s1;
-  row_sum<T, V2, TPR>(A, i, sub, x, s0, s1);
+  T s0 = 0, s1 = 0;
+  if (sub == 0 && i < A.nrows) {
+    const V2 bi = b[i];
+    s0 = -bi.x;
+    s1 = -bi.y;
+  }
+  row_acc<T, V2, TPR>(A, i, sub, x, s0, s1);
   if (i >= A.nrows || sub != 0) return;
-  const V2 bi = b[i], xi = x[i];
-  const T di = dinv[i] * beta;
+  const V2 xi = x[i];
+  const T di = dinv[i] * nbeta;
   V2 dd;
   if (alpha != T(0)) {
     const V2 dold = d[i];
-    dd = mk2<T, V2>(fma(alpha, dold.x, di * (bi.x - s0)), fma(alpha, dold.y, di * (bi.y - s1)));
+    dd = mk2<T, V2>(fma(alpha, dold.x, di * s0), fma(alpha, dold.y, di * s1));
   } else {
-    dd = mk2<T, V2>(di * (bi.x - s0), di * (bi.y - s1));
+    dd = mk2<T, V2>(di * s0, di * s1);
   }
   d[i] = dd;
   xo[i] = mk2<T, V2>(xi.x + dd.x, xi.y + dd.y);
@@ -1029,11 +1044,10 @@ __global__ void __launch_bounds__(TPB) k_spmv2(Csr<T> A, const V2* __restrict__ 
 }
 
 // ---------------------------------------------------------------- structured (diagonal) fine level
+// Row sum of the lattice form onto the caller's (s0, s1) (zero, or -b for a residual's negative).
 template <typename T, typename V2, int ND>
-__device__ __forceinline__ void dia_row_sum(const Dia<T>& D, int n, int i, const V2* __restrict__ x, T& s0,
+__device__ __forceinline__ void dia_row_acc(const Dia<T>& D, int n, int i, const V2* __restrict__ x, T& s0,
                                             T& s1) {
-  s0 = 0;
-  s1 = 0;
   int W = D.W, WH = D.WH;
   if (D.node_run) {
     const int2 w = D.run_wh[D.node_run[i]];
@@ -1052,21 +1066,31 @@ __device__ __forceinline__ void dia_row_sum(const Dia<T>& D, int n, int i, const
 }
 
 template <typename T, typename V2, int ND>
+__device__ __forceinline__ void dia_row_sum(const Dia<T>& D, int n, int i, const V2* __restrict__ x, T& s0,
+                                            T& s1) {
+  s0 = 0;
+  s1 = 0;
+  dia_row_acc<T, V2, ND>(D, n, i, x, s0, s1);
+}
+
+// k_cheb_step on the lattice form (same arithmetic: the sum starts from -b, nbeta = -beta)
+template <typename T, typename V2, int ND>
 __global__ void __launch_bounds__(TPB) k_cheb_step_dia(Dia<T> D, int n, const T* __restrict__ dinv,
                                                        const V2* __restrict__ b, const V2* __restrict__ x,
-                                                       V2* __restrict__ d, V2* __restrict__ xo, T alpha, T beta) {
+                                                       V2* __restrict__ d, V2* __restrict__ xo, T alpha, T nbeta) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  T s0, s1;
-  dia_row_sum<T, V2, ND>(D, n, i, x, s0, s1);
-  const V2 bi = b[i], xi = x[i];
-  const T di = dinv[i] * beta;
+  const V2 bi = b[i];
+  T s0 = -bi.x, s1 = -bi.y;
+  dia_row_acc<T, V2, ND>(D, n, i, x, s0, s1);
+  const V2 xi = x[i];
+  const T di = dinv[i] * nbeta;
   V2 dd;
   if (alpha != T(0)) {
     const V2 dold = d[i];
-    dd = mk2<T, V2>(fma(alpha, dold.x, di * (bi.x - s0)), fma(alpha, dold.y, di * (bi.y - s1)));
+    dd = mk2<T, V2>(fma(alpha, dold.x, di * s0), fma(alpha, dold.y, di * s1));
   } else {
-    dd = mk2<T, V2>(di * (bi.x - s0), di * (bi.y - s1));
+    dd = mk2<T, V2>(di * s0, di * s1);
   }
   d[i] = dd;
   xo[i] = mk2<T, V2>(xi.x + dd.x, xi.y + dd.y);
@@ -1126,17 +1150,19 @@ __global__ void __launch_bounds__(TPB) k_restrict_first(Csr<T> R, const V2* __re
     default: { constexpr int TPRC = 32; KCALL; } break;  \
   }
 
+// one Chebyshev step d = alpha d + beta D^-1 (b - A x), xo = x + d (the kernels take -beta)
 template <typename T, typename V2>
 static void launch_cheb_step(int tpr, const Csr<T>& A, const T* dinv, const V2* b, const V2* x, V2* d,
                              V2* xo, T alpha, T beta, cudaStream_t st, const Dia<T>* dia = nullptr) {
+  const T nbeta = -beta;
   if (dia && dia->nd) {
     const int g = blocks_for(A.nrows);
     CH_DIA_DISPATCH(dia->nd, (k_cheb_step_dia<T, V2, NDC><<<g, TPB, 0, st>>>(*dia, A.nrows, dinv, b, x, d, xo,
-                                                                              alpha, beta)));
+                                                                              alpha, nbeta)));
     return;
   }
   const int g = blocks_for((int64_t)A.nrows * tpr);
-  CH_TPR_DISPATCH(tpr, (k_cheb_step<T, V2, TPRC><<<g, TPB, 0, st>>>(A, dinv, b, x, d, xo, alpha, beta)));
+  CH_TPR_DISPATCH(tpr, (k_cheb_step<T, V2, TPRC><<<g, TPB, 0, st>>>(A, dinv, b, x, d, xo, alpha, nbeta)));
 }
 template <typename T, typename V2>
 static void launch_residual(int tpr, const Csr<T>& A, const V2* b, const V2* x, V2* r, cudaStream_t st,

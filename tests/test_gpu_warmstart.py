@@ -19,7 +19,9 @@ def small_theta(rng, scale=0.25):
     return (rng.standard_normal(wo.NPARAM) * scale).astype(np.float32)
 
 
-@pytest.mark.parametrize("H,W", [(12, 20), (17, 9)])
+# small images, and the 129 x 129 and 257 x 257 images of the benchmark's meshes (many tiles per
+# row and many rows of blocks: the multi-block tiling at full size)
+@pytest.mark.parametrize("H,W", [(12, 20), (17, 9), (129, 129), (257, 257)])
 def test_forward_matches_oracle(lib, H, W):
     rng = np.random.default_rng(0)
     net = lib.WarmStartNet(H, W, max_batch=2)
@@ -50,10 +52,10 @@ def test_zero_network_is_linear_extrapolation(lib):
     np.testing.assert_array_equal(pred, s + (s - q))
 
 
-@pytest.mark.parametrize("lap", [0.0, 0.5])
-def test_gradients_match_oracle(lib, lap):
+@pytest.mark.parametrize("lap,H,W", [(0.0, 12, 20), (0.5, 12, 20), (0.0, 129, 129), (0.5, 129, 131)])
+def test_gradients_match_oracle(lib, lap, H, W):
     rng = np.random.default_rng(1)
-    B, H, W = 2, 12, 20
+    B = 2
     net = lib.WarmStartNet(H, W, max_batch=B)
     theta = small_theta(rng)
     net.set_params(theta)
