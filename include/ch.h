@@ -82,7 +82,14 @@ typedef struct ch_params {
   int32_t vcycles_H;         /* V-cycles per application of H~^-1 (Algorithm 1, steps 2 and 4), default 2 */
   int32_t autotune;          /* SpMV lanes per row: 0 = fixed rule, 1 = timed at set-up (cached per process), default 1 */
   double cheb_lower;         /* Chebyshev interval [cheb_lower, 1] x 1.1 lambda_max(D^-1 A), default 0.3 */
-  int32_t graphs;            /* 1: replay each Arnoldi step as a captured CUDA graph; 0: direct launches; default 1 */
+  int32_t graphs;            /* 1 (default): FGMRES's convergence loop runs on the device -- a plain
+                                step (ch_step) is one CUDA graph launch (conditional while / switch
+                                nodes: Arnoldi steps and restart cycles chosen by the flags of every
+                                run and species) and one host synchronisation, a step with a guess
+                                launches its solve as one graph; 0: the host drives the loop with
+                                direct launches, reading the flags after every Arnoldi step.  Both
+                                give bitwise the same steps.  Per-launch event timing
+                                (ch_profile_enable) and MINRES (krylov = 1) use the host loop */
   int32_t cheb_degree_coarse; /* Chebyshev steps on the levels below the finest; 0 (default): 2 (at
                                 most cheb_degree) */
   int32_t cheb_degree_M;     /* finest-level Chebyshev degree of M's hierarchy (Algorithm 1, step 1);
@@ -228,7 +235,8 @@ ch_status ch_vcycle_noalloc(ch_precond_t* pc, int32_t which, int32_t vcycles, co
 
 /* ---------------------------------------------------------------- time stepping (Eq. (12)-(14))
  * A state holds (phi_p, phi_nfa, mu_p, mu_nfa) on the device plus all FGMRES work space, so
- * ch_step allocates nothing. */
+ * ch_step allocates no work vectors; with graphs on, the first step of each kind captures and
+ * instantiates the state's CUDA graph (kept until ch_state_destroy). */
 ch_status ch_state_create(const ch_system_t* s, ch_precond_t* pc, void* stream, ch_state_t** out);
 /* Set the state from caller device buffers (N fp64 each); mu_* may be NULL (zero). */
 ch_status ch_state_set(ch_state_t* st, const double* phi_p, const double* phi_nfa,

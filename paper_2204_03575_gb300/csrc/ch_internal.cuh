@@ -145,7 +145,12 @@ struct ProfTally {
 };
 void prof_capture_begin();
 ProfTally prof_capture_end();
+// the tally that ProfScopes record into while capturing (nullptr: none); returns the previous one
+ProfTally* prof_capture_swap(ProfTally* t);
 void prof_add(const ProfTally& t);
+void prof_add_times(const ProfTally& t, int64_t times);
+// add to one kernel's counters directly (work whose size only the device knew)
+void prof_add_slot(int kid, int f32, int64_t launches, double bytes, double fmas);
 
 }  // namespace ch
 

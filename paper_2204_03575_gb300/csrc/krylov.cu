@@ -14,7 +14,8 @@
 // thread block owns a contiguous node range of exactly one run, and the last block of a run to
 // finish (a per-run ticket) sums that run's block partials in block order.  There are no
 // floating-point atomics, so runs are bitwise reproducible.  Orthogonalisation is classical
-// Gram-Schmidt with one re-orthogonalisation (CGS2).
+// Gram-Schmidt with one re-orthogonalisation (CGS2).  With CUDA graphs on, the convergence loop
+// itself runs on the device (conditional graph nodes, see Ctl): a step is one graph launch.
 #include <algorithm>
 #include <cmath>
 
@@ -409,10 +410,12 @@ __global__ void k_cycle_solve(int nruns, KrylovDev* kds) {
   for (int i = k; i < MAXM; ++i) kd->y[s][i] = 0.0;
 }
 
-// x += sum_k y_s[k] Z_k with the coefficients of the block's run
-__global__ void k_update_x(Seg sg, int N, int kmax, const double4_32a* __restrict__ Z, double4_32a* x,
-                           const KrylovDev* kds) {
+// x += sum_k y_s[k] Z_k with the coefficients of the block's run, k < kmax (read from kmax_dev
+// when it is given: the device-side loop knows the cycle's length only on the device)
+__global__ void k_update_x(Seg sg, int N, int kmax_arg, const int* kmax_dev, const double4_32a* __restrict__ Z,
+                           double4_32a* x, const KrylovDev* kds) {
   __shared__ double y[2][MAXM];
+  const int kmax = kmax_dev ? *kmax_dev : kmax_arg;
   const KrylovDev* kd = kds + sg.run[blockIdx.x];
   for (int k = threadIdx.x; k < kmax; k += blockDim.x) {
     y[0][k] = kd->y[0][k];
@@ -449,6 +452,106 @@ __global__ void k_flags(int nruns, const KrylovDev* kds, Flags* f) {
     f->active = c[1];
     f->nonfinite = c[2];
   }
+}
+
+// ---------------------------------------------------------------- device-side solve loop
+// With CUDA graphs on, FGMRES runs without the host: the step's graph holds a while node whose
+// body is a switch over m + 1 cases -- case j < m is Arnoldi step j (case 0 first forms V_0 from
+// the residual), case m ends a restart cycle (Givens solve, x update, true residual) -- followed
+// by k_ctl, which reduces the flags of every run, advances this state and picks the next case.
+// The loop ends when every system has converged, at max_iter, or at a non-finite value; its
+// passes are bounded (each Arnoldi pass raises `total`, a cycle end follows at most m of them).
+struct Ctl {
+  int sel;        // case of the next body pass
+  int total;      // Arnoldi steps taken in this solve
+  int restarts;   // restart cycles completed
+  int passes;     // body passes
+  int status;     // ch_status of the solve
+  int where;      // non-finite value met in: 0 the initial residual, 1 an Arnoldi step, 2 a cycle's residual
+  int active;     // systems not converged when the loop stopped
+  int jcycle;     // Arnoldi steps of the current cycle (the x update's length)
+  int sum_j;      // jcycle summed over the completed cycles (launch accounting)
+  int count[MAXM + 1];  // body passes per case
+};
+
+// init = 1: after the initial residual (resets the state); 0: after a body pass.  One block.
+__global__ void k_ctl(int nruns, const KrylovDev* kds, Ctl* c, int m, int max_iter, int init,
+                      cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hs) {
+  __shared__ int cnt[3];
+  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+  if (init)
+    for (int k = threadIdx.x; k <= m; k += blockDim.x) c->count[k] = 0;
+  __syncthreads();
+  int ca = 0, ac = 0, nf = 0;
+  for (int r = threadIdx.x; r < nruns; r += blockDim.x) {
+    const KrylovDev* kd = kds + r;
+    ca += kd->cycle_active[0] + kd->cycle_active[1];
+    ac += kd->active[0] + kd->active[1];
+    nf += kd->nonfinite;
+  }
+  if (ca) atomicAdd(&cnt[0], ca);
+  if (ac) atomicAdd(&cnt[1], ac);
+  if (nf) atomicAdd(&cnt[2], nf);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int cycle_active = cnt[0], active = cnt[1], nonfinite = cnt[2];
+  int go = 1, sel = 0;
+  if (init) {
+    c->total = 0;
+    c->restarts = 0;
+    c->passes = 0;
+    c->sum_j = 0;
+    c->jcycle = 0;
+    c->where = 0;
+    c->status = CH_OK;
+    if (nonfinite) {
+      c->status = CH_ERR_NONFINITE;
+      go = 0;
+    } else if (active == 0) {
+      go = 0;
+    } else if (max_iter <= 0) {
+      c->status = CH_ERR_NOT_CONVERGED;
+      go = 0;
+    }
+  } else {
+    const int cur = c->sel;
+    c->count[cur] += 1;
+    c->passes += 1;
+    if (cur < m) {  // Arnoldi step cur was taken
+      c->total += 1;
+      if (nonfinite) {
+        c->status = CH_ERR_NONFINITE;
+        c->where = 1;
+        go = 0;
+      } else if (cycle_active == 0 || c->total >= max_iter || cur + 1 == m) {
+        c->jcycle = cur + 1;
+        sel = m;
+      } else {
+        sel = cur + 1;
+      }
+    } else {  // a restart cycle ended with its true residual
+      c->restarts += 1;
+      c->sum_j += c->jcycle;
+      if (nonfinite) {
+        c->status = CH_ERR_NONFINITE;
+        c->where = 2;
+        go = 0;
+      } else if (active == 0) {
+        go = 0;
+      } else if (c->total >= max_iter) {
+        c->status = CH_ERR_NOT_CONVERGED;
+        go = 0;
+      }
+    }
+    if (go && c->passes > 2 * max_iter + 2) {  // cannot happen by the rules above; a backstop
+      c->status = CH_ERR_INTERNAL;
+      go = 0;
+    }
+  }
+  c->active = active;
+  c->sel = sel;
+  cudaGraphSetConditional(hs, (unsigned)sel);
+  cudaGraphSetConditional(hw, (unsigned)go);
 }
 
 // mass_s = sum_i (M 1)_i phi_s,i  (M symmetric: 1^T M phi), per run
@@ -567,19 +670,31 @@ struct ch_state_s {
   double* x_prev = nullptr;         // N x 4: the state before the last learned step
   double* guess = nullptr;          // N x 4: the network's prediction
   cudaStream_t cap_stream = nullptr;            // private stream for graph capture
-  cudaGraphExec_t graph[64] = {};               // Arnoldi step j, captured on first use
-  ch::ProfTally tally[64];                      // launch accounting of each graph
+  cudaStream_t body_stream = nullptr;           // nested captures of the device loop's body
   ch::MrDev* mr = nullptr;                      // MINRES scalars, one per run
   cudaGraphExec_t mr_graph = nullptr;           // one MINRES iteration, captured on first use
   ch::ProfTally mr_tally;
+  // device-side FGMRES loop (graphs on, per-launch timing off): one graph per plain step, and
+  // the solve alone for steps with a caller's guess; built on first use
+  ch::Ctl* dctl = nullptr;
+  ch::Ctl* hctl = nullptr;                      // pinned copy, written by the graphs
+  ch::RunStats* hstats_pin = nullptr;           // pinned, written by the step graph
+  cudaGraph_t step_g = nullptr, solve_g = nullptr;
+  cudaGraphExec_t step_graph = nullptr, solve_graph = nullptr;
+  ch::ProfTally tally_step, tally_solve, tally_ctl, tally_case[ch::MAXM + 1];
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   ch::Alloc mem;
   ~ch_state_s() {
-    for (auto& g : graph)
-      if (g) cudaGraphExecDestroy(g);
+    if (step_graph) cudaGraphExecDestroy(step_graph);
+    if (solve_graph) cudaGraphExecDestroy(solve_graph);
+    if (step_g) cudaGraphDestroy(step_g);
+    if (solve_g) cudaGraphDestroy(solve_g);
     if (mr_graph) cudaGraphExecDestroy(mr_graph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (body_stream) cudaStreamDestroy(body_stream);
     if (hflags) cudaFreeHost(hflags);
+    if (hctl) cudaFreeHost(hctl);
+    if (hstats_pin) cudaFreeHost(hstats_pin);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
   }
@@ -669,15 +784,24 @@ ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, 
   if (r == CH_OK) r = S->mem.get(&S->mr, (size_t)S->R);
   if (r == CH_OK) r = S->mem.get(&S->dflags, 1);
   if (r == CH_OK) r = S->mem.get(&S->dstats, (size_t)S->R);
+  if (r == CH_OK) r = S->mem.get(&S->dctl, 1);
   if (r == CH_OK) r = make_segments(S, st);
   if (r == CH_OK) r = S->mem.get(&S->partials, (size_t)S->nblocks * MAXV);
-  if (r == CH_OK && cudaMallocHost(&S->hflags, sizeof(Flags)) != cudaSuccess) {
-    set_error("pinned allocation failed");
-    S->hflags = nullptr;
-    r = CH_ERR_OOM;
-  }
+  auto pinned = [&](void** ptr, size_t bytes) {
+    if (r != CH_OK) return;
+    if (cudaMallocHost(ptr, bytes) != cudaSuccess) {
+      *ptr = nullptr;
+      cudaGetLastError();
+      set_error("pinned allocation of %zu bytes failed", bytes);
+      r = CH_ERR_OOM;
+    }
+  };
+  pinned(reinterpret_cast<void**>(&S->hflags), sizeof(Flags));
+  pinned(reinterpret_cast<void**>(&S->hctl), sizeof(Ctl));
+  pinned(reinterpret_cast<void**>(&S->hstats_pin), sizeof(RunStats) * S->R);
   S->use_graphs = s->p.graphs != 0;
-  if (r == CH_OK && cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (r == CH_OK && (cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                     cudaStreamCreateWithFlags(&S->body_stream, cudaStreamNonBlocking) != cudaSuccess)) {
     set_error("stream creation failed");
     r = CH_ERR_CUDA;
   }
@@ -719,8 +843,8 @@ static ch_status read_flags(ch_state_s* S, cudaStream_t st) {
 static double res4_bytes(const ch_system_s* s) { return 20.0 * s->nnz + 4.0 * (s->N + 1) + 96.0 * s->N; }
 
 // One Arnoldi step j for all systems: Z_j = Prec(V_j) (Algorithm 1), W = A Z_j, CGS2 against
-// V_0..V_j with the Givens update, V_{j+1} = W / h_{j+1,j}, and the summary flags written to
-// dflags.  Everything is enqueued on `st` with no host synchronisation, so it can be captured.
+// V_0..V_j with the Givens update and V_{j+1} = W / h_{j+1,j}.  Everything is enqueued on `st`
+// with no host synchronisation, so it can be captured.
 static ch_status arnoldi_step(ch_state_s* S, int j, cudaStream_t st) {
   const ch_system_s* s = S->sys;
   const int N = S->N, nb = S->nblocks;
@@ -749,44 +873,14 @@ static ch_status arnoldi_step(ch_state_s* S, int j, cudaStream_t st) {
     k_scale4<<<nb, TPB, 0, st>>>(S->seg, W4, V4 + (size_t)(j + 1) * N, S->kd);
   }
   CH_LAUNCHED();
-  {
-    ProfScope ps(st, K_FLAGS, 0, 0.0, 0.0);
-    k_flags<<<1, 256, 0, st>>>(S->R, S->kd, S->dflags);
-  }
-  CH_LAUNCHED();
   return CH_OK;
 }
 
-// Launch Arnoldi step j: replay its captured CUDA graph (captured on first use on the state's
-// private stream, since the legacy default stream cannot be captured), or enqueue the kernels
-// directly when graphs are off or per-launch event timing is on.  Then read the flags.
+// Host-driven Arnoldi step (graphs off, or per-launch event timing on): the step's kernels, the
+// summary flags, and a read of the flags.
 static ch_status arnoldi_launch(ch_state_s* S, int j, cudaStream_t st) {
-  if (!S->use_graphs || prof_timing()) {
-    CH_TRY(arnoldi_step(S, j, st));
-  } else {
-    if (!S->graph[j]) {
-      cudaGraph_t g = nullptr;
-      CH_CUDA(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
-      prof_capture_begin();
-      const ch_status r = arnoldi_step(S, j, S->cap_stream);
-      const cudaError_t e = cudaStreamEndCapture(S->cap_stream, &g);
-      S->tally[j] = prof_capture_end();
-      if (r != CH_OK) {
-        if (g) cudaGraphDestroy(g);
-        return r;
-      }
-      CH_CUDA(e);
-      const cudaError_t ei = cudaGraphInstantiate(&S->graph[j], g, 0);
-      cudaGraphDestroy(g);
-      CH_CUDA(ei);
-    }
-    CH_CUDA(cudaGraphLaunch(S->graph[j], st));
-    prof_add(S->tally[j]);
-  }
-  CH_CUDA(cudaMemcpyAsync(S->hflags, S->dflags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
-  CH_CUDA(cudaStreamSynchronize(st));
-  prof_drain();
-  return CH_OK;
+  CH_TRY(arnoldi_step(S, j, st));
+  return read_flags(S, st);
 }
 
 static ch_status residual_launch(ch_state_s* S, int init, cudaStream_t st, const double* x = nullptr) {
@@ -848,7 +942,7 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
     }
     {
       ProfScope ps(st, K_UPDATE_X, 0, (j + 2) * 32.0 * N, 4.0 * j * N);
-      k_update_x<<<nb, TPB, 0, st>>>(S->seg, N, j, Z4, x4, S->kd);
+      k_update_x<<<nb, TPB, 0, st>>>(S->seg, N, j, nullptr, Z4, x4, S->kd);
     }
     CH_LAUNCHED();
     CH_TRY(residual_launch(S, 0, st));
@@ -860,6 +954,202 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
     ++*restarts;
   }
   return CH_OK;
+}
+
+// ---------------------------------------------------------------- FGMRES on the device
+// The loop of `fgmres` as one CUDA graph (see Ctl): no host synchronisation inside a solve.
+static bool device_loop(const ch_state_s* S) {
+  return S->use_graphs && S->sys->p.krylov == 0 && !prof_timing();
+}
+
+// Case j < m of the loop body: Arnoldi step j (case 0 first forms V_0 = r / beta); case m: the
+// end of a restart cycle (y = R^-1 g, x += Z y over the cycle's steps, the true residual).
+static ch_status loop_case(ch_state_s* S, int j, cudaStream_t st) {
+  const int N = S->N, nb = S->nblocks;
+  double4_32a* W4 = reinterpret_cast<double4_32a*>(S->W);
+  double4_32a* V4 = reinterpret_cast<double4_32a*>(S->V);
+  if (j < S->m) {
+    if (j == 0) {
+      ProfScope ps(st, K_SCALE4, 0, 64.0 * N, 0.0);
+      k_scale4<<<nb, TPB, 0, st>>>(S->seg, W4, V4, S->kd);
+    }
+    CH_LAUNCHED();
+    return arnoldi_step(S, j, st);
+  }
+  {
+    ProfScope ps(st, K_CYCLE_SOLVE, 0, 0.0, 0.0);
+    k_cycle_solve<<<blocks_for(2 * S->R, 64), 64, 0, st>>>(S->R, S->kd);
+  }
+  {
+    // bytes of the x update beyond x itself (32 N per Krylov vector) are added per cycle from
+    // the loop's record (Ctl::sum_j), the length being known on the device only
+    ProfScope ps(st, K_UPDATE_X, 0, 2 * 32.0 * N, 0.0);
+    k_update_x<<<nb, TPB, 0, st>>>(S->seg, N, S->m, &S->dctl->jcycle, reinterpret_cast<const double4_32a*>(S->Z),
+                                    reinterpret_cast<double4_32a*>(S->x), S->kd);
+  }
+  CH_LAUNCHED();
+  return residual_launch(S, 0, st);
+}
+
+// Capture `fill` into the graph `g` on the body stream, after the nodes deps[0..nd).
+template <typename F>
+static ch_status capture_into(ch_state_s* S, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, F fill) {
+  cudaStream_t bs = S->body_stream;
+  CH_CUDA(cudaStreamBeginCaptureToGraph(bs, g, deps, nullptr, nd, cudaStreamCaptureModeThreadLocal));
+  const ch_status r = fill(bs);
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(bs, &out);
+  CH_TRY(r);
+  CH_CUDA(e);
+  return CH_OK;
+}
+
+// Enqueue the whole solve on the capturing stream cs: the initial residual, k_ctl, and the while
+// node with its body.  Launch accounting: the initial residual and k_ctl go to the tally that is
+// current on entry, case j to tally_case[j], the body's k_ctl to tally_ctl.
+static ch_status capture_solve(ch_state_s* S, cudaStream_t cs) {
+  const int m = S->m, max_iter = S->sys->p.max_iter;
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  CH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle hw, hs;
+  CH_CUDA(cudaGraphConditionalHandleCreate(&hw, g, 0, 0));
+  CH_CUDA(cudaGraphConditionalHandleCreate(&hs, g, 0, 0));
+  CH_TRY(residual_launch(S, 1, cs));
+  {
+    ProfScope ps(cs, K_FLAGS, 0, 0.0, 0.0);
+    k_ctl<<<1, 256, 0, cs>>>(S->R, S->kd, S->dctl, m, max_iter, 1, hw, hs);
+  }
+  CH_LAUNCHED();
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wn = nullptr;
+  CH_CUDA(cudaGraphAddNode(&wn, g, deps, nullptr, nd, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  cudaGraphNodeParams sp = {};
+  sp.type = cudaGraphNodeTypeConditional;
+  sp.conditional.handle = hs;
+  sp.conditional.type = cudaGraphCondTypeSwitch;
+  sp.conditional.size = (unsigned)(m + 1);
+  cudaGraphNode_t sn = nullptr;
+  CH_CUDA(cudaGraphAddNode(&sn, body, nullptr, nullptr, 0, &sp));
+  ProfTally* outer = prof_capture_swap(nullptr);
+  ch_status r = CH_OK;
+  for (int j = 0; j <= m && r == CH_OK; ++j) {
+    S->tally_case[j] = ProfTally();
+    prof_capture_swap(&S->tally_case[j]);
+    r = capture_into(S, sp.conditional.phGraph_out[j], nullptr, 0,
+                     [&](cudaStream_t bs) { return loop_case(S, j, bs); });
+  }
+  if (r == CH_OK) {
+    S->tally_ctl = ProfTally();
+    prof_capture_swap(&S->tally_ctl);
+    r = capture_into(S, body, &sn, 1, [&](cudaStream_t bs) -> ch_status {
+      ProfScope ps(bs, K_FLAGS, 0, 0.0, 0.0);
+      k_ctl<<<1, 256, 0, bs>>>(S->R, S->kd, S->dctl, m, max_iter, 0, hw, hs);
+      CH_LAUNCHED();
+      return CH_OK;
+    });
+  }
+  prof_capture_swap(outer);
+  CH_TRY(r);
+  CH_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return CH_OK;
+}
+
+// Build the graph of a whole plain step (whole = true: right-hand sides, solve, masses, run
+// statistics, and the copies of the statistics and the loop record to pinned host memory) or of
+// the solve alone (the loop record copied out).
+static ch_status build_loop_graph(ch_state_s* S, bool whole, cudaGraph_t* gout, cudaGraphExec_t* xout,
+                                  ProfTally* tally) {
+  cudaGraph_t G = nullptr;
+  CH_CUDA(cudaGraphCreate(&G, 0));
+  cudaStream_t cs = S->cap_stream;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(G);
+    CH_CUDA(e);
+  }
+  *tally = ProfTally();
+  ProfTally* prev = prof_capture_swap(tally);
+  ch_status r = CH_OK;
+  if (whole) {
+    r = rhs_strided(S->sys, S->x, S->x + 1, 4, S->b, cs);
+    if (r == CH_OK) {
+      k_clear_warm<<<blocks_for(S->R, 64), 64, 0, cs>>>(S->R, S->kd);
+      if (cudaGetLastError() != cudaSuccess) r = CH_ERR_CUDA;
+    }
+  }
+  if (r == CH_OK) r = capture_solve(S, cs);
+  if (r == CH_OK && whole) {
+    {
+      ProfScope ps(cs, K_MASS, 0, 40.0 * S->N, 2.0 * S->N);
+      k_mass<<<S->nblocks, TPB, 0, cs>>>(S->seg, S->mlump, reinterpret_cast<const double4_32a*>(S->x),
+                                          S->partials, S->kd);
+    }
+    k_run_stats<<<blocks_for(S->R, 64), 64, 0, cs>>>(S->R, S->kd, S->dstats);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(S->hstats_pin, S->dstats, sizeof(RunStats) * S->R, cudaMemcpyDeviceToHost, cs) !=
+            cudaSuccess)
+      r = CH_ERR_CUDA;
+  }
+  if (r == CH_OK && cudaMemcpyAsync(S->hctl, S->dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+    r = CH_ERR_CUDA;
+  prof_capture_swap(prev);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cs, &captured);
+  if (r == CH_ERR_CUDA) set_error("capturing the device-side FGMRES loop failed: %s", cudaGetErrorString(cudaGetLastError()));
+  if (r == CH_OK && e != cudaSuccess) {
+    set_error("capturing the device-side FGMRES loop failed: %s", cudaGetErrorString(e));
+    r = CH_ERR_CUDA;
+  }
+  if (r == CH_OK) {
+    e = cudaGraphInstantiate(xout, G, 0);
+    if (e != cudaSuccess) {
+      set_error("instantiating the device-side FGMRES loop failed: %s", cudaGetErrorString(e));
+      *xout = nullptr;
+      r = CH_ERR_CUDA;
+    }
+  }
+  if (r != CH_OK) {
+    cudaGetLastError();
+    cudaGraphDestroy(G);
+    return r;
+  }
+  *gout = G;  // kept until the state goes (a graph with conditional nodes has one instantiation)
+  return CH_OK;
+}
+
+// After the loop's graph has completed (stream synchronised): launch accounting of the passes
+// taken and the solve's status from the loop record.
+static ch_status finish_loop(ch_state_s* S, const ProfTally& pro, int* restarts) {
+  const Ctl& c = *S->hctl;
+  prof_add(pro);
+  for (int j = 0; j <= S->m; ++j) prof_add_times(S->tally_case[j], c.count[j]);
+  prof_add_times(S->tally_ctl, c.passes);
+  prof_add_slot(K_UPDATE_X, 0, 0, 32.0 * S->N * c.sum_j, 4.0 * S->N * c.sum_j);
+  *restarts = c.restarts;
+  switch (c.status) {
+    case CH_OK:
+      return CH_OK;
+    case CH_ERR_NONFINITE:
+      set_error(c.where == 0 ? "non-finite right-hand side or initial residual"
+                : c.where == 1 ? "non-finite value in the Arnoldi process" : "non-finite residual");
+      return CH_ERR_NONFINITE;
+    case CH_ERR_NOT_CONVERGED:
+      set_error("FGMRES reached max_iter = %d with %d of %d systems unconverged", S->sys->p.max_iter, c.active,
+                2 * S->R);
+      return CH_ERR_NOT_CONVERGED;
+    default:
+      set_error("the device-side FGMRES loop stopped at its pass limit (%d passes)", c.passes);
+      return CH_ERR_INTERNAL;
+  }
 }
 
 // ---------------------------------------------------------------- preconditioned MINRES
@@ -1333,9 +1623,29 @@ static void fill_stats(const ch_state_s* S, int run, ch_step_stats* o) {
   o->warm[1] = rs.warm[1];
 }
 
+// The end of a step: the run statistics are in the host copy, the CUDA events recorded.
+static ch_status step_done(ch_state_s* S, ch_status r, int restarts, ch_step_stats* stats) {
+  cudaEventElapsedTime(&S->last_ms, S->ev0, S->ev1);
+  S->last_status = r;
+  S->last_restarts = restarts;
+  S->since_set += 1;
+  if (stats) fill_stats(S, 0, stats);
+  return r;
+}
+
 // One step from the previous state; rec0: record the start event here (else the caller did).
 static ch_status step_plain_core(ch_state_s* S, cudaStream_t st, ch_step_stats* stats, bool rec0) {
   if (rec0) CH_CUDA(cudaEventRecord(S->ev0, st));
+  if (device_loop(S)) {  // the whole step is one graph launch and one synchronisation
+    if (!S->step_graph) CH_TRY(build_loop_graph(S, true, &S->step_g, &S->step_graph, &S->tally_step));
+    CH_CUDA(cudaGraphLaunch(S->step_graph, st));
+    CH_CUDA(cudaEventRecord(S->ev1, st));
+    CH_CUDA(cudaStreamSynchronize(st));
+    std::memcpy(S->hstats.data(), S->hstats_pin, sizeof(RunStats) * S->R);
+    int restarts = 0;
+    const ch_status r = finish_loop(S, S->tally_step, &restarts);
+    return step_done(S, r, restarts, stats);
+  }
   // right-hand sides from phi^k (strided views of the state)
   CH_TRY(rhs_strided(S->sys, S->x, S->x + 1, 4, S->b, st));
   k_clear_warm<<<blocks_for(S->R, 64), 64, 0, st>>>(S->R, S->kd);
@@ -1349,14 +1659,10 @@ static ch_status step_plain_core(ch_state_s* S, cudaStream_t st, ch_step_stats* 
   k_run_stats<<<blocks_for(S->R, 64), 64, 0, st>>>(S->R, S->kd, S->dstats);
   CH_LAUNCHED();
   CH_CUDA(cudaEventRecord(S->ev1, st));
-  CH_CUDA(cudaMemcpyAsync(S->hstats.data(), S->dstats, sizeof(RunStats) * S->R, cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaMemcpyAsync(S->hstats_pin, S->dstats, sizeof(RunStats) * S->R, cudaMemcpyDeviceToHost, st));
   CH_CUDA(cudaStreamSynchronize(st));
-  cudaEventElapsedTime(&S->last_ms, S->ev0, S->ev1);
-  S->last_status = r;
-  S->last_restarts = restarts;
-  S->since_set += 1;
-  if (stats) fill_stats(S, 0, stats);
-  return r;
+  std::memcpy(S->hstats.data(), S->hstats_pin, sizeof(RunStats) * S->R);
+  return step_done(S, r, restarts, stats);
 }
 
 ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats) {
@@ -1387,7 +1693,14 @@ static ch_status step_guess_core(ch_state_s* S, const double* guess, cudaStream_
   }
   CH_LAUNCHED();
   int restarts = 0;
-  ch_status r = krylov_solve(S, st, &restarts);
+  const bool dev = device_loop(S);
+  ch_status r = CH_OK;
+  if (dev) {  // the solve is one graph launch; its status is read after the synchronisation
+    if (!S->solve_graph) CH_TRY(build_loop_graph(S, false, &S->solve_g, &S->solve_graph, &S->tally_solve));
+    CH_CUDA(cudaGraphLaunch(S->solve_graph, st));
+  } else {
+    r = krylov_solve(S, st, &restarts);
+  }
   {
     ProfScope ps(st, K_MASS, 0, 40.0 * S->N, 2.0 * S->N);
     k_mass<<<S->nblocks, TPB, 0, st>>>(S->seg, S->mlump, reinterpret_cast<const double4_32a*>(S->x),
@@ -1396,14 +1709,11 @@ static ch_status step_guess_core(ch_state_s* S, const double* guess, cudaStream_
   k_run_stats<<<blocks_for(S->R, 64), 64, 0, st>>>(S->R, S->kd, S->dstats);
   CH_LAUNCHED();
   CH_CUDA(cudaEventRecord(S->ev1, st));
-  CH_CUDA(cudaMemcpyAsync(S->hstats.data(), S->dstats, sizeof(RunStats) * S->R, cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaMemcpyAsync(S->hstats_pin, S->dstats, sizeof(RunStats) * S->R, cudaMemcpyDeviceToHost, st));
   CH_CUDA(cudaStreamSynchronize(st));
-  cudaEventElapsedTime(&S->last_ms, S->ev0, S->ev1);
-  S->last_status = r;
-  S->last_restarts = restarts;
-  S->since_set += 1;
-  if (stats) fill_stats(S, 0, stats);
-  return r;
+  std::memcpy(S->hstats.data(), S->hstats_pin, sizeof(RunStats) * S->R);
+  if (dev) r = finish_loop(S, S->tally_solve, &restarts);
+  return step_done(S, r, restarts, stats);
 }
 
 ch_status state_step_guess(ch_state_s* S, const double* guess, cudaStream_t st, ch_step_stats* stats) {

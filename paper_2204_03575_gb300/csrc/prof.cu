@@ -112,14 +112,31 @@ ProfTally prof_capture_end() {
   return out;
 }
 
-void prof_add(const ProfTally& t) {
+ProfTally* prof_capture_swap(ProfTally* t) {
+  ProfTally* prev = t_capture;
+  t_capture = t;
+  return prev;
+}
+
+void prof_add_times(const ProfTally& t, int64_t times) {
+  if (times <= 0) return;
   std::lock_guard<std::mutex> lk(g.mu);
   for (int s = 0; s < K_COUNT * 2; ++s) {
     if (!t.launches[s]) continue;
-    g.acc[s].launches += t.launches[s];
-    g.acc[s].bytes += t.bytes[s];
-    g.acc[s].fmas += t.fmas[s];
+    g.acc[s].launches += t.launches[s] * times;
+    g.acc[s].bytes += t.bytes[s] * (double)times;
+    g.acc[s].fmas += t.fmas[s] * (double)times;
   }
+}
+
+void prof_add(const ProfTally& t) { prof_add_times(t, 1); }
+
+void prof_add_slot(int kid, int f32, int64_t launches, double bytes, double fmas) {
+  std::lock_guard<std::mutex> lk(g.mu);
+  Acc& a = g.acc[kid * 2 + (f32 ? 1 : 0)];
+  a.launches += launches;
+  a.bytes += bytes;
+  a.fmas += fmas;
 }
 
 void prof_drain() {
