@@ -351,6 +351,91 @@ def paper_section(torch, ch, flush, ranks):
     return out
 
 
+def variants_section(torch, ch, np, nx, K, W, flush, ranks):
+    """The solver's variants on the headline workload (nx x nx, seeded 0.33 +/- 0.01): M~ by the
+    Chebyshev semi-iteration (precond_M = 1, Section 3) in FP64 and mixed precision, and the
+    Flory-Huggins potential (potential = 3, Section 2) in FP64; K timed steps after W warm-up
+    steps each, every step at the true 1e-8 residual."""
+    out = {}
+    for tag, kw in (("chebyshev_M_fp64", dict(precond_M=1)), ("chebyshev_M_mixed", dict(precond_M=1, precision=1)),
+                    ("flory_huggins_fp64", dict(potential=3))):
+        p = ch.Params(nx=nx, ny=nx, **kw)
+        system = ch.System(ch.Mesh(p), p)
+        state = ch.State(system, ch.Precond(system))
+        state.init_seeded(0.33, 0.33, 0.01, seed=0)
+        for _ in range(W):
+            state.step()
+        ms, iters = timed_steps(torch, ch, state, K, flush, ranks)
+        out[tag] = {"steps": K, "steps_per_s": ranks.rate(K, ms), "ms_per_step": ms / K,
+                    "iters_per_step_mean": float(np.mean(iters)), "params": {k: int(v) for k, v in kw.items()}}
+        del state, system
+    return out
+
+
+def eoc_section(torch, ch, np):
+    """Section 4's convergence study in tau: five steps sizes 2e-4 .. 3.2e-3 against tau = 1e-5 on
+    the paper's 10 x 2.5 box with 100 x 50 grid points (its smallest 2D grid), 0.35 +/- 0.01
+    (seed 0), eps = 1e-3, Eq. (15), final time T = 3.2e-2 (ten steps of the largest tau; 3200 of the
+    reference); FP64 solves to a 1e-10 residual.  Errors in the discrete L2 norm sqrt(e^T M e);
+    orders pairwise (successive tau) and by a least-squares fit of log(error) on log(tau)."""
+    import math
+    T, taus = 3.2e-2, (2e-4, 4e-4, 8e-4, 1.6e-3, 3.2e-3)
+
+    def run(tau):
+        p = ch.Params(nx=99, ny=49, Lx=10.0, Ly=2.5, tau=tau, rtol=1e-10)
+        system = ch.System(ch.Mesh(p), p)
+        state = ch.State(system, ch.Precond(system))
+        state.init_seeded(0.35, 0.35, 0.01, seed=0)
+        n = int(round(T / tau))
+        for _ in range(n):
+            state.step()
+        g = state.get()
+        return g["phi_p"].cpu().numpy(), g["phi_nfa"].cpu().numpy(), system, n
+
+    import scipy.sparse as sp
+    t0 = time.time()
+    rp, rn, system, nref = run(1e-5)
+    rowptr, col, vm, _, _ = [t.cpu().numpy() for t in system.csr()]
+    M = sp.csr_matrix((vm, col, rowptr), shape=(system.n, system.n))
+
+    def mnorm(d):
+        return math.sqrt(float(d @ (M @ d)))
+
+    errs = {"polymer": [], "nfa": []}
+    for tau in taus:
+        pp, pn, _, _ = run(tau)
+        errs["polymer"].append(mnorm(pp - rp))
+        errs["nfa"].append(mnorm(pn - rn))
+    lt = np.log(np.array(taus))
+    out = {"final_time": T, "reference_tau": 1e-5, "reference_steps": nref, "taus": list(taus),
+           "grid_points": "100 x 50", "box": "10 x 2.5", "seconds": round(time.time() - t0, 1),
+           "paper_eoc": {"polymer": 0.789, "nfa": 0.788}}
+    for k, e in errs.items():
+        e = np.array(e)
+        out[k] = {"l2_error": e.tolist(), "eoc_pairwise": (np.log(e[1:] / e[:-1]) / np.log(2.0)).tolist(),
+                  "eoc_fit": float(np.polyfit(lt, np.log(e), 1)[0])}
+    return out
+
+
+def morphology_section(torch, ch, state_fields, nx, reps=20):
+    """Section 5's projection of the headline run's final morphology (nx x nx nodal image,
+    polymer where phi_p > phi_nfa) onto the centres of a 2nx x 2nx finite-difference grid,
+    upward ray-crossing parity per grid point; CUDA-event time over `reps` launches."""
+    pp, pn = state_fields["phi_p"], state_fields["phi_nfa"]
+    g = 2 * nx
+    ch.morphology_project(pp, pn, nx, nx, 1.0, 1.0, g, g)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        polymer, _, _ = ch.morphology_project(pp, pn, nx, nx, 1.0, 1.0, g, g)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"image": f"{nx + 1} x {nx + 1}", "grid": f"{g} x {g}", "ms_per_projection": ms,
+            "grid_points_per_s": g * g / (ms * 1e-3), "polymer_fraction": float(polymer.float().mean())}
+
+
 def learned_section(torch, ch, nx, K, flush, ranks):
     """The learned warm start on an nx x nx grid: 2000 (s_{k-1}, s_k, s_{k+1}) triples from the
     plain FP64 solver (20 seeded runs x 100 steps), residual-loss training by the library's
@@ -623,6 +708,14 @@ def main():
     if not args.no_extra and world == 1:
         extra = extra_sections(torch, ch, np, K, W, flush, ranks)
 
+    # ---- the solver's variants (Chebyshev M~, Flory-Huggins), Section 4's EOC study in tau and
+    # Section 5's morphology projection
+    variants = eoc = morph = None
+    if not args.no_extra and world == 1:
+        variants = variants_section(torch, ch, np, args.nx, min(K, 20), W, flush, ranks)
+        eoc = eoc_section(torch, ch, np)
+        morph = morphology_section(torch, ch, fields64, args.nx)
+
     # ---- learned warm start (256 x 256 grid): training, then FP64 / mixed with and without it
     learned = None
     if not args.no_learned and world == 1:
@@ -664,7 +757,8 @@ def main():
         "top_kernels": top_kernels(prof64),
         "iters_per_step_mean": float(np.mean(iters)), "iters_per_step_max": int(np.max(iters)),
         "amg_levels": {k: [r for r, _ in v] for k, v in levels.items()},
-        "mixed": mixed, "batch": batch, "learned": learned, "configs": extra, "cpu_baseline": cpu,
+        "mixed": mixed, "batch": batch, "learned": learned, "configs": extra, "variants": variants,
+        "eoc_tau": eoc, "morphology_projection": morph, "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

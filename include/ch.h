@@ -65,7 +65,10 @@ typedef struct ch_params {
   double mobility;           /* M_p = M_nfa, default 1 */
   int32_t bc_mode;           /* 0: zero flux on the whole boundary; 1: Eq. (10) fluxes */
   int32_t evap_sign;         /* +1: evaporation adds polymer/NFA at y=Ly (text); -1: Eq. (10) literally */
-  int32_t potential;         /* 0: f of Eq. (15), chain rule through phi_s; 1: without the phi_s term; 2: f' = 0 */
+  int32_t potential;         /* 0: f of Eq. (15), chain rule through phi_s; 1: without the phi_s term; 2: f' = 0;
+                                3: the Flory-Huggins f of Section 2 (logarithmic), also through phi_s, with
+                                the chi_* / N_* below; its load is defined by the collapsed 3-point
+                                Gauss-Legendre product rule on each simplex (9 points in 2D, 27 in 3D) */
   int32_t precision;         /* 0: FP64 everywhere; 1: FP32 AMG V-cycles inside FP64 FGMRES */
   double k_evap;             /* evaporation rate k, default 5e-3 */
   double g_p, g_nfa;         /* substrate energy g of Eq. (5), default 0.01 */
@@ -101,6 +104,16 @@ typedef struct ch_params {
                                 p_nfa = 1; 1: p_p = 1 on the 1st, 3rd and 5th sixth of [0, Lx] (each
                                 run's own Lx), p_nfa = 1 on the others.  Integrated exactly: facets
                                 are cut where they cross a breakpoint */
+  int32_t precond_M;         /* Algorithm 1, step 1 (M~^-1 v_1): 0 (default) AMG V-cycles of M's
+                                hierarchy; 1: the Chebyshev semi-iteration Section 3 names instead --
+                                cheb_M_steps steps on D^-1 M from a zero guess over Wathen's bounds of
+                                its eigenvalues, [1/2, 2] (triangles) or [1/2, 5/2] (tetrahedra) */
+  int32_t cheb_M_steps;      /* steps of that semi-iteration (1..16); 0 (default): 5 */
+  double chi_pn, chi_ps, chi_ns; /* Flory-Huggins interaction parameters (potential = 3); default
+                                1, 0.3, 0.3 (Section 4) */
+  double N_p, N_nfa, N_s;    /* degrees of polymerisation (potential = 3); default 20, 20, 1 (Section 4) */
+  double fh_delta;           /* potential = 3: each logarithm is taken at max(phi, fh_delta) (a
+                                positivity guard; concentrations may dip below 0), default 1e-10 */
 } ch_params;
 
 /* Per-step statistics (host struct). */
@@ -210,6 +223,12 @@ ch_status ch_precond_apply(ch_precond_t* pc, const double* v, double* w, void* s
  * sides stored N x 2 (fp64): x ~ A^-1 b.  b, x must not alias. */
 ch_status ch_vcycle(ch_precond_t* pc, int32_t which, int32_t vcycles, const double* b, double* x,
                     void* stream);
+/* Algorithm 1's step 1 alone (Section 3: "approximately solve M w_1 = v_1") for two right-hand
+ * sides stored N x 2 (fp64): x = M~^-1 b, by the vcycles_M V-cycles of M's hierarchy
+ * (precond_M = 0) or the Chebyshev semi-iteration (precond_M = 1: cheb_M_steps steps on D^-1 M
+ * from zero over Wathen's bounds [1/2, 2] for triangles, [1/2, 5/2] for tetrahedra), in the
+ * preconditioner's working precision.  b, x must not alias and must be 16-byte aligned. */
+ch_status ch_mass_solve(ch_precond_t* pc, const double* b, double* x, void* stream);
 void ch_precond_destroy(ch_precond_t* pc);
 
 /* Allocation-free V-cycles.  The paper has no counterpart to this call: it exists for callers
@@ -298,6 +317,17 @@ ch_status ch_ws_set_params(ch_ws_t* w, const float* params, void* stream);     /
 ch_status ch_ws_get_params(const ch_ws_t* w, float* params, float* grads, void* stream);
 /* host: mean[8], inv_std[8], out_scale[4] */
 ch_status ch_ws_set_norm(ch_ws_t* w, const float* norm20, void* stream);
+/* Normalisation of a training set, computed on the device and set on the network (as
+ * ch_ws_set_norm): nsamples consecutive-state triples, device arrays of nsamples x N x 4 (fp64, or
+ * fp32 when fp32 = 1) -- predecessors q = s_{k-1}, states x = s_k, successors n = s_{k+1}.
+ * mean[0:4] and inv_std[0:4] are the mean and 1 / standard deviation of the four fields of x over
+ * the set; the change channels keep mean[4:8] = 0, inv_std[4:8] = 1 (they are already in units of
+ * their per-sample RMS r); out_scale[c] is the standard deviation over the set of the
+ * extrapolation's correction in those units, ((n - x) - (x - q)) / r.  Standard deviations use the
+ * n - 1 divisor, floors 1e-30; sums in a fixed order (reproducible).  norm20 (host, 20 doubles)
+ * receives (mean[8], inv_std[8], out_scale[4]).  Allocates and frees its own small scratch. */
+ch_status ch_ws_fit_norm(ch_ws_t* w, const void* q, const void* x, const void* n, int32_t nsamples, int32_t fp32,
+                         double* norm20, void* stream);
 /* pred (N x 4 fp64 device): the prediction of the next state from the state s and its predecessor */
 ch_status ch_ws_predict(ch_ws_t* w, const double* state, const double* prev, double* pred, void* stream);
 /* One training step on B <= max_batch samples (device fp32, B x N x 4 each): states x = s_k, their
@@ -332,6 +362,24 @@ ch_status ch_ws_train_residual(ch_ws_t* w, const ch_system_t* sys, ch_precond_t*
  * stats->ms includes the prediction.  CH_ERR_ARG: a network sized for another mesh, or a state
  * of several runs. */
 ch_status ch_step_learned(ch_state_t* st, ch_ws_t* w, void* stream, ch_step_stats* stats);
+
+/* ---------------------------------------------------------------- morphology projection (Section 5)
+ * Section 5 passes a simulated morphology to a device model on a finite-difference grid: the field
+ * is thresholded into a binary image, and each grid point is classified by the parity of the
+ * number of object faces crossed by a ray from the point.  Here the image has one pixel per node of
+ * a 2D nx x ny mesh of [0,Lx]x[0,Ly] (node i + (nx+1) j; pixel (i, j) is the half-open cell
+ * [(i-1/2)hx, (i+1/2)hx) x [(j-1/2)hy, (j+1/2)hy) clipped to the box), set where phi_p > phi_nfa
+ * (use_threshold = 0) or phi_p > threshold (use_threshold = 1; phi_nfa may then be NULL); the
+ * grid points are the centres of a uniform gx x gy cell grid of the box (point k + gx l at
+ * ((k+1/2) Lx/gx, (l+1/2) Ly/gy)); each point's ray runs upward and crosses the horizontal pixel
+ * faces between vertically adjacent pixels of different value and the top edge above a set
+ * top-row pixel.  Device inputs: phi_p, phi_nfa ((nx+1)(ny+1) fp64, e.g. from ch_state_get).
+ * Device outputs (gx gy each, any may be NULL): polymer (1 inside the polymer phase, else 0), and
+ * Section 5's mobilities: mu_e = 1e-10, mu_h = 0.1 m^2/(V s) in the polymer phase, the other way
+ * round elsewhere.  CH_ERR_ARG for sizes < 1, a non-positive box, a NULL field. */
+ch_status ch_morphology_project(const double* phi_p, const double* phi_nfa, int32_t nx, int32_t ny, double Lx,
+                                double Ly, int32_t use_threshold, double threshold, int32_t gx, int32_t gy,
+                                uint8_t* polymer, double* mu_e, double* mu_h, void* stream);
 
 /* ---------------------------------------------------------------- launch accounting
  * Every kernel launch of the library is counted per kernel and working precision, with the

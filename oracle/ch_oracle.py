@@ -31,7 +31,8 @@ Readings of points the paper leaves open:
   R2 mobilities are 1 unless given ("appropriate constants");
   R3 df/dphi_p differentiates f(phi_p, phi_nfa, 1 - phi_p - phi_nfa) by the chain
      rule: f_p' = 7 phi_p phi_nfa^2 - 0.2 phi_s ('poly'); 'poly_partial' drops the
-     solvent term, 'none' sets f' = 0 (used by closed-form tests);
+     solvent term, 'none' sets f' = 0 (used by closed-form tests), 'fh' is the
+     Flory-Huggins f of R14;
   R4 f^(k) is the exact load vector int f'(phi_h^k) lambda_i, not M f'(phi^k);
   R5 the evaporation flux on Gamma_t enters with sign ``evap_sign`` (+1: inflow of
      polymer and NFA as the text describes; -1: Eq. (10) read literally);
@@ -433,7 +434,10 @@ class Solver:
         return self._lu.solve(B)
 
     def rhs_pair(self, s: State):
-        Fp, Fn = load_vector(self.m, s.phi_p, s.phi_nfa, self.p.potential)
+        if self.p.potential == "fh":     # the logarithmic potential of Section 2 (reading R14)
+            Fp, Fn = load_vector_fh(self.m, s.phi_p, s.phi_nfa, self.p)
+        else:
+            Fp, Fn = load_vector(self.m, s.phi_p, s.phi_nfa, self.p.potential)
         gp, gn = boundary_load(self.m, s.phi_p, s.phi_nfa, self.p)
         return (rhs(self.M, s.phi_p, Fp, gp, self.p), rhs(self.M, s.phi_nfa, Fn, gn, self.p))
 

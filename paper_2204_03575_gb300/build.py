@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libch.so")
-SOURCES = ["sparse.cu", "assemble.cu", "amg.cu", "krylov.cu", "capi.cu", "prof.cu", "warmstart.cu"]
+SOURCES = ["sparse.cu", "assemble.cu", "amg.cu", "krylov.cu", "capi.cu", "prof.cu", "warmstart.cu",
+           "morphology.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -44,6 +44,10 @@ class Params(ctypes.Structure):
         ("vcycles_M", ctypes.c_int32), ("vcycles_H", ctypes.c_int32), ("autotune", ctypes.c_int32),
         ("cheb_lower", ctypes.c_double), ("graphs", ctypes.c_int32), ("cheb_degree_coarse", ctypes.c_int32),
         ("cheb_degree_M", ctypes.c_int32), ("krylov", ctypes.c_int32), ("pattern", ctypes.c_int32),
+        ("precond_M", ctypes.c_int32), ("cheb_M_steps", ctypes.c_int32),
+        ("chi_pn", ctypes.c_double), ("chi_ps", ctypes.c_double), ("chi_ns", ctypes.c_double),
+        ("N_p", ctypes.c_double), ("N_nfa", ctypes.c_double), ("N_s", ctypes.c_double),
+        ("fh_delta", ctypes.c_double),
     ]
 
     def __init__(self, **kw):
@@ -106,6 +110,12 @@ _SIGNATURES = {
     "ch_vcycle": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
     "ch_precond_destroy": (None, [_VP]),
     "ch_vcycle_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
+    "ch_mass_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ch_ws_fit_norm": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_double), _VP]),
+    "ch_morphology_project": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                             ctypes.c_int32, _VP, _VP, _VP, _VP]),
     "ch_state_create": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(_VP)]),
     "ch_state_set": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "ch_state_init_seeded": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -326,6 +336,13 @@ class Precond:
         _check(lib().ch_vcycle(self._h, which, vcycles, _ptr(b), _ptr(x), _stream(stream)), "ch_vcycle")
         return x
 
+    def mass_solve(self, b, stream=None):
+        """ch_mass_solve: Algorithm 1's step 1 (M~^-1 b) on N x 2 right-hand sides."""
+        b = _f64(b, self.system.n)
+        x = torch.empty_like(b)
+        _check(lib().ch_mass_solve(self._h, _ptr(b), _ptr(x), _stream(stream)), "ch_mass_solve")
+        return x
+
     def vcycle_noalloc(self, which: int, b, vcycles: int = 1, stream=None):
         """ch_vcycle_noalloc: the same V-cycles with work space in the library's static array."""
         b = _f64(b, self.system.n)
@@ -423,6 +440,25 @@ class State:
             self._h = None
 
 
+def morphology_project(phi_p, phi_nfa, nx: int, ny: int, Lx: float, Ly: float, gx: int, gy: int,
+                       threshold=None, stream=None):
+    """ch_morphology_project (Section 5): the thresholded nodal image of an nx x ny 2D mesh
+    classified onto the centres of a gx x gy grid by upward ray-crossing parity.  Returns device
+    tensors (polymer uint8, mu_e, mu_h), each gy x gx."""
+    n = (nx + 1) * (ny + 1)
+    pp = _f64(phi_p, n)
+    pn = _f64(phi_nfa, n) if phi_nfa is not None else None
+    dev = pp.device
+    polymer = torch.empty((gy, gx), dtype=torch.uint8, device=dev)
+    mu_e = torch.empty((gy, gx), dtype=torch.float64, device=dev)
+    mu_h = torch.empty((gy, gx), dtype=torch.float64, device=dev)
+    use = 0 if threshold is None else 1
+    _check(lib().ch_morphology_project(_ptr(pp), _ptr(pn) if pn is not None else None, nx, ny, Lx, Ly, use,
+                                       float(threshold) if use else 0.0, gx, gy, _ptr(polymer), _ptr(mu_e),
+                                       _ptr(mu_h), _stream(stream)), "ch_morphology_project")
+    return polymer, mu_e, mu_h
+
+
 def profile_enable(on: bool):
     """Turn per-launch CUDA-event timing on or off (launch counts are always kept)."""
     _check(lib().ch_profile_enable(1 if on else 0), "ch_profile_enable")
@@ -470,6 +506,21 @@ class WarmStartNet:
         assert a.size == 20
         _check(lib().ch_ws_set_norm(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream(stream)),
                "ch_ws_set_norm")
+
+    def fit_norm(self, Q, X, Y, stream=None):
+        """ch_ws_fit_norm on a training set (S x N x 4 CUDA tensors, float64 or float32, all one
+        dtype): sets the network's normalisation and returns (mean[8], inv_std[8], out_scale[4])."""
+        import numpy as np
+        if not (Q.dtype == X.dtype == Y.dtype) or X.dtype not in (torch.float64, torch.float32):
+            raise ValueError("Q, X, Y must share a float64 or float32 dtype")
+        if not (Q.is_cuda and X.is_cuda and Y.is_cuda) or Q.shape != X.shape or Y.shape != X.shape:
+            raise ValueError("Q, X, Y must be CUDA tensors of one shape")
+        Q, X, Y = Q.contiguous(), X.contiguous(), Y.contiguous()
+        out = (ctypes.c_double * 20)()
+        _check(lib().ch_ws_fit_norm(self._h, _ptr(Q), _ptr(X), _ptr(Y), X.shape[0], 1 if X.dtype == torch.float32 else 0,
+                                    out, _stream(stream)), "ch_ws_fit_norm")
+        a = np.array(out[:])
+        return a[:8], a[8:16], a[16:20]
 
     def predict(self, state4, prev4, stream=None):
         s, q = _f64(state4), _f64(prev4)

@@ -1233,9 +1233,10 @@ struct ChebCoef {
   double alpha[16], beta[16];
 };
 
-static ChebCoef cheb_coef(double rho, int deg, double lower) {
+// Coefficients of `deg` Chebyshev semi-iteration steps for eigenvalues in [lo, hi]: the first
+// step from zero is x = D^-1 b / theta, then d = alpha_s d + beta_s D^-1 (b - A x), x += d.
+static ChebCoef cheb_coef_interval(double lo, double hi, int deg) {
   ChebCoef c{};
-  const double hi = 1.1 * rho, lo = lower * hi;
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
   c.invtheta = 1.0 / theta;
   c.alpha[0] = 0.0;
@@ -1250,21 +1251,26 @@ static ChebCoef cheb_coef(double rho, int deg, double lower) {
   return c;
 }
 
-template <typename T_>
+// the V-cycle smoother's interval: [lower, 1] x 1.1 rho
+static ChebCoef cheb_coef(double rho, int deg, double lower) {
+  const double hi = 1.1 * rho;
+  return cheb_coef_interval(lower * hi, hi, deg);
+}
+
+// `deg` Chebyshev steps with coefficients c on level L (accounted as kernels kfirst / kstep).
 // zero_guess: 0 continue from *xcur; 1 start from zero (the first step is pointwise); 2 start from
 // zero with that first step already taken by the caller (fused into the restriction)
-static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, int zero_guess,
-                        typename V2T<T_>::t** xcur, cudaStream_t st) {
+template <typename T_>
+static ch_status smooth_coef(LevelT<T_>& L, const ChebCoef& c, int deg, int zero_guess, int kfirst, int kstep,
+                             typename V2T<T_>::t** xcur, cudaStream_t st) {
   using V2 = typename V2T<T_>::t;
   const int n = L.A.nrows;
-  const int deg = l == 0 ? h->cheb_degree : h->cheb_degree_coarse;
-  const ChebCoef c = cheb_coef(h->rho[l], deg, h->cheb_lower);
   V2* x = *xcur;
   V2* other = (x == L.x) ? L.x2 : L.x;
   int s0 = 0;
   const double T = sizeof(T_), nnz = (double)L.A.nnz;
   if (zero_guess == 1) {
-    ProfScope ps(st, l == 0 ? K_CHEB_FIRST : K_CHEB_FIRST_C, sizeof(T_) == 4, 7.0 * T * n, 2.0 * n);
+    ProfScope ps(st, kfirst, sizeof(T_) == 4, 7.0 * T * n, 2.0 * n);
     k_cheb_first<T_, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.dinv, L.b, (T_)c.invtheta, x, L.d);
     s0 = 1;
   } else if (zero_guess == 2) {
@@ -1273,8 +1279,7 @@ static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, int zero_guess,
   // operator bytes: CSR values + column indices + row pointers, or the diagonals' values
   const double opb = L.dia.nd ? T * L.dia.nd * (double)n : nnz * (4 + T) + 4.0 * (n + 1);
   for (int s = s0; s < deg; ++s) {
-    ProfScope ps(st, l == 0 ? K_CHEB_STEP : K_CHEB_STEP_C, sizeof(T_) == 4,
-                 opb + T * n * (c.alpha[s] != 0.0 ? 11 : 9), 2.0 * nnz + 4.0 * n);
+    ProfScope ps(st, kstep, sizeof(T_) == 4, opb + T * n * (c.alpha[s] != 0.0 ? 11 : 9), 2.0 * nnz + 4.0 * n);
     launch_cheb_step<T_, V2>(L.tprA, L.A, L.dinv, L.b, x, L.d, other, (T_)c.alpha[s], (T_)c.beta[s], st,
                              &L.dia);
     std::swap(x, other);
@@ -1282,6 +1287,27 @@ static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, int zero_guess,
   CH_LAUNCHED();
   *xcur = x;
   return CH_OK;
+}
+
+// the V-cycle's smoother on level l: its degree and interval
+template <typename T_>
+static ch_status smooth(Hierarchy* h, LevelT<T_>& L, int l, int zero_guess,
+                        typename V2T<T_>::t** xcur, cudaStream_t st) {
+  const int deg = l == 0 ? h->cheb_degree : h->cheb_degree_coarse;
+  const ChebCoef c = cheb_coef(h->rho[l], deg, h->cheb_lower);
+  return smooth_coef<T_>(L, c, deg, zero_guess, l == 0 ? K_CHEB_FIRST : K_CHEB_FIRST_C,
+                         l == 0 ? K_CHEB_STEP : K_CHEB_STEP_C, xcur, st);
+}
+
+// M~^-1 by the Chebyshev semi-iteration (Section 3's alternative to AMG for the mass matrix):
+// `steps` steps on D^-1 M from a zero guess over Wathen's bounds of its eigenvalues for P1
+// simplices, [1/2, 2] (triangles) and [1/2, 5/2] (tetrahedra), on the finest level of M's
+// hierarchy (its working-precision copy of M and D^-1).  b in L.b; result in *xres.
+template <typename T_>
+static ch_status semi_iteration(LevelT<T_>& L, int dim, int steps, typename V2T<T_>::t** xres, cudaStream_t st) {
+  const ChebCoef c = cheb_coef_interval(0.5, dim == 2 ? 2.0 : 2.5, steps);
+  *xres = L.x;
+  return smooth_coef<T_>(L, c, steps, 1, K_CHEB_SEMI, K_CHEB_SEMI, xres, st);
 }
 
 // one V-cycle at level l on L[l].b; result in *xres (L[l].x or L[l].x2)
@@ -1361,6 +1387,8 @@ ch_status hierarchy_solve(Hierarchy* h, const double* b, int ldb, double* x, int
 // ---------------------------------------------------------------- Algorithm 1
 // w_1 = AMG(M) v_1;  w_2 = AMG(H) v_2;  w_2 = M w_2;  w_2 = AMG(H) w_2.
 // v, w are N x 4 (phi_p, phi_n, mu_p, mu_n per node): block 1 at offset 0, block 2 at offset 2.
+static int semi_steps(const ch_params& p) { return p.cheb_M_steps > 0 ? p.cheb_M_steps : 5; }
+
 template <typename T>
 static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::vector<LevelT<T>>& LH,
                            const T* cinvM, const T* cinvH, const double* v, double* w,
@@ -1387,7 +1415,11 @@ static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::ve
       k_load2<T, V2><<<blocks_for(n), TPB, 0, sm>>>(n, v, 4, L.b);
     }
     V2* xr = L.x;
-    for (int c = 0; c < p.vcycles_M; ++c) CH_TRY(vcycle<T>(pc->hM, LM, cinvM, 0, c == 0, &xr, sm));
+    if (p.precond_M == 1) {
+      CH_TRY(semi_iteration<T>(L, pc->sys->mesh->dim, semi_steps(p), &xr, sm));
+    } else {
+      for (int c = 0; c < p.vcycles_M; ++c) CH_TRY(vcycle<T>(pc->hM, LM, cinvM, 0, c == 0, &xr, sm));
+    }
     {
       ProfScope ps(sm, K_VSTORE, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
       k_store2<T, V2><<<blocks_for(n), TPB, 0, sm>>>(n, xr, w, 4);
@@ -1428,6 +1460,32 @@ ch_status precond_apply(ch_precond_s* pc, const double* v, double* w, cudaStream
   if (pc->precision == 0)
     return precond_t<double>(pc, pc->hM->Ld, pc->hH->Ld, pc->hM->cinv, pc->hH->cinv, v, w, st);
   return precond_t<float>(pc, pc->hM->Lf, pc->hH->Lf, pc->hM->cinvf, pc->hH->cinvf, v, w, st);
+}
+
+// Algorithm 1's step 1 alone on two right-hand sides (N x 2): x = M~^-1 b
+template <typename T>
+static ch_status mass_solve_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, const T* cinvM, const double* b,
+                              double* x, cudaStream_t st) {
+  using V2 = typename V2T<T>::t;
+  const ch_params& p = pc->sys->p;
+  LevelT<T>& L = LM[0];
+  const int n = L.A.nrows;
+  k_load2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, b, 2, L.b);
+  CH_LAUNCHED();
+  V2* xr = L.x;
+  if (p.precond_M == 1) {
+    CH_TRY(semi_iteration<T>(L, pc->sys->mesh->dim, semi_steps(p), &xr, st));
+  } else {
+    for (int c = 0; c < p.vcycles_M; ++c) CH_TRY(vcycle<T>(pc->hM, LM, cinvM, 0, c == 0, &xr, st));
+  }
+  k_store2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, xr, x, 2);
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+ch_status mass_solve(ch_precond_s* pc, const double* b, double* x, cudaStream_t st) {
+  if (pc->precision == 0) return mass_solve_t<double>(pc, pc->hM->Ld, pc->hM->cinv, b, x, st);
+  return mass_solve_t<float>(pc, pc->hM->Lf, pc->hM->cinvf, b, x, st);
 }
 
 }  // namespace ch

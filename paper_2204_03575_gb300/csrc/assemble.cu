@@ -3,6 +3,8 @@
 // Everything is node-centric ("gather"): the thread of node i visits the simplices or
 // boundary facets incident to i in increasing index order and adds their contributions,
 // so every sum has a fixed order and results are bitwise reproducible (no atomics).
+#include <cmath>
+
 #include "ch_internal.cuh"
 
 namespace ch {
@@ -607,6 +609,98 @@ __global__ void k_elem_loads(const MeshPod m, LoadCoef L, const double* pp, cons
   }
 }
 
+// ---- The Flory-Huggins load (potential = 3).  Section 2's bulk energy
+//   f = phi_p ln(phi_p) / N_p + phi_n ln(phi_n) / N_n + phi_s ln(phi_s) / N_s
+//       + chi_pn phi_p phi_n + chi_ps phi_p phi_s + chi_ns phi_n phi_s,   phi_s = 1 - phi_p - phi_n,
+// differentiated through phi_s like Eq. (15):
+//   f_p' = (ln phi_p + 1) / N_p - (ln phi_s + 1) / N_s + chi_pn phi_n + chi_ps (phi_s - phi_p) - chi_ns phi_n
+//   f_n' = (ln phi_n + 1) / N_n - (ln phi_s + 1) / N_s + (chi_pn - chi_ps) phi_p + chi_ns (phi_s - phi_n)
+// with each logarithm taken at max(phi, delta) (a NaN stays a NaN).  The integrand is not a
+// polynomial, so a fixed rule defines the load: on every simplex the product of 3-point
+// Gauss-Legendre rules collapsed onto it (Duffy), 9 points on a triangle, 27 on a tetrahedron.
+struct FhRule {
+  int nq;
+  double lam[27][4];  // barycentric coordinates of the points
+  double w[27];       // weights, summing to 1: int_T g ~ |T| sum_q w_q g(x_q)
+};
+
+struct FhCoef {
+  double chi_pn, chi_ps, chi_ns, inv_np, inv_nn, inv_ns, delta;
+};
+
+// Gauss-Legendre on [0, 1] with 3 points: 1/2 -+ sqrt(15)/10 and 1/2, weights 5/18, 4/9, 5/18.
+// Square (u, v) -> triangle (u, v (1 - u)), Jacobian 1 - u; cube (u, v, t) -> tetrahedron
+// (u, v (1 - u), t (1 - u)(1 - v)), Jacobian (1 - u)^2 (1 - v); normalised by the reference
+// simplex's measure (1/2, 1/6).
+static FhRule fh_rule(int dim) {
+  const double g[3] = {0.5 - std::sqrt(15.0) / 10.0, 0.5, 0.5 + std::sqrt(15.0) / 10.0};
+  const double w[3] = {5.0 / 18.0, 4.0 / 9.0, 5.0 / 18.0};
+  FhRule R{};
+  int q = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < (dim == 3 ? 3 : 1); ++k) {
+        const double u = g[i], v = g[j];
+        double xi[3] = {u, v * (1.0 - u), 0.0};
+        double wt;
+        if (dim == 2) {
+          wt = 2.0 * w[i] * w[j] * (1.0 - u);
+        } else {
+          xi[2] = g[k] * (1.0 - u) * (1.0 - v);
+          wt = 6.0 * w[i] * w[j] * w[k] * (1.0 - u) * (1.0 - u) * (1.0 - v);
+        }
+        R.lam[q][0] = 1.0 - xi[0] - xi[1] - xi[2];
+        for (int a = 1; a <= dim; ++a) R.lam[q][a] = xi[a - 1];
+        R.w[q] = wt;
+        ++q;
+      }
+  R.nq = q;
+  return R;
+}
+
+__device__ __forceinline__ double guarded_log(double x, double delta) { return log(x < delta ? delta : x); }
+
+// eload[(e (D+1) + a) 2 + {0, 1}] = |T| sum_q w_q f_{p,n}'(phi_h(x_q)) lambda_a(x_q)
+template <int D>
+__global__ void k_elem_loads_fh(const MeshPod m, const FhRule R, const FhCoef F, const double* pp,
+                                const double* pn, int ld, double* __restrict__ eload) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const int* ev = m.elems + (D + 1) * e;
+  double P[D + 1], Q[D + 1], Fp[D + 1], Fn[D + 1];
+#pragma unroll
+  for (int a = 0; a <= D; ++a) {
+    P[a] = pp[(size_t)ld * ev[a]];
+    Q[a] = pn[(size_t)ld * ev[a]];
+    Fp[a] = 0.0;
+    Fn[a] = 0.0;
+  }
+  for (int q = 0; q < R.nq; ++q) {
+    double p = 0.0, n = 0.0;
+#pragma unroll
+    for (int a = 0; a <= D; ++a) {
+      p += R.lam[q][a] * P[a];
+      n += R.lam[q][a] * Q[a];
+    }
+    const double s = 1.0 - p - n;
+    const double ls = (guarded_log(s, F.delta) + 1.0) * F.inv_ns;
+    const double fp = (guarded_log(p, F.delta) + 1.0) * F.inv_np - ls + F.chi_pn * n + F.chi_ps * (s - p) -
+                      F.chi_ns * n;
+    const double fn = (guarded_log(n, F.delta) + 1.0) * F.inv_nn - ls + (F.chi_pn - F.chi_ps) * p +
+                      F.chi_ns * (s - n);
+    const double wq = R.w[q];
+#pragma unroll
+    for (int a = 0; a <= D; ++a) {
+      Fp[a] += wq * fp * R.lam[q][a];
+      Fn[a] += wq * fn * R.lam[q][a];
+    }
+  }
+  const double vol = m.vol[e];
+#pragma unroll
+  for (int a = 0; a <= D; ++a)
+    reinterpret_cast<double2*>(eload)[(size_t)e * (D + 1) + a] = make_double2(vol * Fp[a], vol * Fn[a]);
+}
+
 template <int D>
 __device__ void node_loads(const MeshPod& m, const LoadCoef& L, const double* __restrict__ eload,
                            const double* pp, const double* pn, int ld, int v, double* Fp, double* Fn,
@@ -749,6 +843,17 @@ __global__ void k_rhs(const MeshPod m, LoadCoef L, const double* eload, const in
 static void elem_loads(const ch_system_s* s, const MeshPod& m, const LoadCoef& L, const double* pp,
                        const double* pn, int ld, cudaStream_t st) {
   const double E = m.E, d1 = m.dim + 1;
+  if (s->p.potential == 3) {
+    const FhRule R = fh_rule(m.dim);
+    const ch_params& p = s->p;
+    const FhCoef F{p.chi_pn, p.chi_ps, p.chi_ns, 1.0 / p.N_p, 1.0 / p.N_nfa, 1.0 / p.N_s, p.fh_delta};
+    ProfScope ps(st, K_ELEM_LOADS, 0, E * (d1 * (4.0 + 16.0) + 8.0 + 16.0 * d1), E * R.nq * (4.0 * d1 + 10.0));
+    if (m.dim == 2)
+      k_elem_loads_fh<2><<<blocks_for(m.E), TPB, 0, st>>>(m, R, F, pp, pn, ld, s->eload);
+    else
+      k_elem_loads_fh<3><<<blocks_for(m.E), TPB, 0, st>>>(m, R, F, pp, pn, ld, s->eload);
+    return;
+  }
   ProfScope ps(st, K_ELEM_LOADS, 0, E * (d1 * (4.0 + 16.0) + 8.0 + 16.0 * d1), E * (22.0 + 12.0 * d1));
   if (m.dim == 2)
     k_elem_loads<2><<<blocks_for(m.E), TPB, 0, st>>>(m, L, pp, pn, ld, s->eload);

@@ -23,7 +23,7 @@ ch_status check_params(const ch_params* p) {
   CH_ARG(p->mobility > 0 && std::isfinite(p->mobility), "mobility must be > 0");
   CH_ARG(p->bc_mode == 0 || p->bc_mode == 1, "bc_mode must be 0 or 1");
   CH_ARG(p->evap_sign == 1 || p->evap_sign == -1, "evap_sign must be +1 or -1");
-  CH_ARG(p->potential >= 0 && p->potential <= 2, "potential must be 0, 1 or 2");
+  CH_ARG(p->potential >= 0 && p->potential <= 3, "potential must be 0, 1, 2 or 3");
   CH_ARG(p->precision == 0 || p->precision == 1, "precision must be 0 or 1");
   CH_ARG(p->rtol > 0 && p->rtol < 1, "rtol must be in (0, 1)");
   CH_ARG(p->restart >= 1 && p->restart <= 64, "restart must be in [1, 64]");
@@ -39,6 +39,14 @@ ch_status check_params(const ch_params* p) {
   CH_ARG(p->krylov == 0 || p->krylov == 1, "krylov must be 0 (FGMRES) or 1 (MINRES)");
   CH_ARG(p->cheb_degree_M >= 0 && p->cheb_degree_M <= 16, "cheb_degree_M must be in [0, 16]");
   CH_ARG(p->pattern == 0 || p->pattern == 1, "pattern must be 0 or 1");
+  CH_ARG(p->precond_M == 0 || p->precond_M == 1, "precond_M must be 0 (AMG) or 1 (Chebyshev semi-iteration)");
+  CH_ARG(p->cheb_M_steps >= 0 && p->cheb_M_steps <= 16, "cheb_M_steps must be in [0, 16]");
+  CH_ARG(std::isfinite(p->chi_pn) && std::isfinite(p->chi_ps) && std::isfinite(p->chi_ns),
+         "chi parameters must be finite");
+  CH_ARG(p->N_p > 0 && p->N_nfa > 0 && p->N_s > 0 && std::isfinite(p->N_p) && std::isfinite(p->N_nfa) &&
+             std::isfinite(p->N_s),
+         "N_p, N_nfa, N_s must be > 0");
+  CH_ARG(p->fh_delta > 0 && p->fh_delta < 1, "fh_delta must be in (0, 1)");
   return CH_OK;
 }
 }  // namespace
@@ -99,6 +107,15 @@ void ch_params_default(ch_params* p) {
   d.cheb_degree_M = 0;
   d.krylov = 0;
   d.pattern = 0;
+  d.precond_M = 0;
+  d.cheb_M_steps = 0;
+  d.chi_pn = 1.0;
+  d.chi_ps = 0.3;
+  d.chi_ns = 0.3;
+  d.N_p = 20.0;
+  d.N_nfa = 20.0;
+  d.N_s = 1.0;
+  d.fh_delta = 1e-10;
   *p = d;
 }
 
@@ -350,7 +367,29 @@ ch_status ch_vcycle(ch_precond_t* pc, int32_t which, int32_t vcycles, const doub
   return ch::hierarchy_solve(which == 0 ? pc->hM : pc->hH, b, 2, x, 2, vcycles, S(stream));
 }
 
+ch_status ch_mass_solve(ch_precond_t* pc, const double* b, double* x, void* stream) {
+  CH_ARG(pc != nullptr && b != nullptr && x != nullptr, "NULL argument");
+  CH_ARG(b != x, "b and x must not alias");
+  CH_ARG(((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15) == 0,
+         "b and x must be 16-byte aligned");
+  return ch::mass_solve(pc, b, x, S(stream));
+}
+
 void ch_precond_destroy(ch_precond_t* pc) { delete pc; }
+
+// ---------------------------------------------------------------- morphology projection
+ch_status ch_morphology_project(const double* phi_p, const double* phi_nfa, int32_t nx, int32_t ny, double Lx,
+                                double Ly, int32_t use_threshold, double threshold, int32_t gx, int32_t gy,
+                                uint8_t* polymer, double* mu_e, double* mu_h, void* stream) {
+  CH_ARG(phi_p != nullptr && (use_threshold || phi_nfa != nullptr), "NULL field");
+  CH_ARG(use_threshold == 0 || use_threshold == 1, "use_threshold must be 0 or 1");
+  CH_ARG(nx >= 1 && ny >= 1 && gx >= 1 && gy >= 1, "mesh and grid sizes must be >= 1");
+  CH_ARG((double)(nx + 1) * (ny + 1) < 2.0e9 && (double)gx * gy < 2.0e9, "image or grid too large");
+  CH_ARG(Lx > 0 && Ly > 0 && std::isfinite(Lx) && std::isfinite(Ly), "box extents must be > 0");
+  CH_ARG(!use_threshold || std::isfinite(threshold), "threshold must be finite");
+  return ch::morphology_project(phi_p, phi_nfa, nx, ny, Lx, Ly, use_threshold, threshold, gx, gy, polymer, mu_e,
+                                mu_h, S(stream));
+}
 
 ch_status ch_vcycle_noalloc(ch_precond_t* pc, int32_t which, int32_t vcycles, const double* b,
                             double* x, void* stream) {
@@ -462,6 +501,14 @@ ch_status ch_ws_get_params(const ch_ws_t* w, float* params, float* grads, void* 
 ch_status ch_ws_set_norm(ch_ws_t* w, const float* norm20, void* stream) {
   CH_ARG(w != nullptr && norm20 != nullptr, "NULL argument");
   return ch::ws_set_norm(w, norm20, S(stream));
+}
+
+ch_status ch_ws_fit_norm(ch_ws_t* w, const void* q, const void* x, const void* n, int32_t nsamples, int32_t fp32,
+                         double* norm20, void* stream) {
+  CH_ARG(w != nullptr && q != nullptr && x != nullptr && n != nullptr && norm20 != nullptr, "NULL argument");
+  CH_ARG(nsamples >= 1, "nsamples must be >= 1");
+  CH_ARG(fp32 == 0 || fp32 == 1, "fp32 must be 0 or 1");
+  return ch::ws_fit_norm(w, q, x, n, nsamples, fp32, norm20, S(stream));
 }
 
 ch_status ch_ws_predict(ch_ws_t* w, const double* state, const double* prev, double* pred, void* stream) {

@@ -118,7 +118,7 @@ enum KernelId {
   K_COARSE, K_VLOAD, K_VSTORE, K_SPMV_M, K_STATE_IO,
   // the same V-cycle kernels on levels below the finest (accounted separately)
   K_CHEB_FIRST_C, K_CHEB_STEP_C, K_VRESIDUAL_C, K_RESTRICT_C, K_PROLONG_C,
-  K_WS_CONV, K_WS_IO, K_GUESS, K_ELEM_LOADS, K_MR_DOT, K_MR_VEC, K_COUNT
+  K_WS_CONV, K_WS_IO, K_GUESS, K_ELEM_LOADS, K_MR_DOT, K_MR_VEC, K_CHEB_SEMI, K_MORPH, K_COUNT
 };
 // RAII around one kernel launch: counts it with its algorithmic bytes / FMAs and, when timing
 // is on, records CUDA events around it on the launching stream.
@@ -252,6 +252,12 @@ struct ch_precond_s {
 struct ch_state_s;
 namespace ch {
 ch_status precond_apply(ch_precond_s* pc, const double* v, double* w, cudaStream_t st);
+// Algorithm 1's step 1 on two right-hand sides (N x 2 fp64): x = M~^-1 b
+ch_status mass_solve(ch_precond_s* pc, const double* b, double* x, cudaStream_t st);
+// morphology.cu: Section 5's projection of a thresholded 2D morphology onto a finite-difference grid
+ch_status morphology_project(const double* pp, const double* pn, int nx, int ny, double Lx, double Ly,
+                             int use_thr, double thr, int gx, int gy, uint8_t* polymer, double* mu_e,
+                             double* mu_h, cudaStream_t st);
 const char* last_error();
 ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, ch_state_s** out);
 void state_destroy(ch_state_s* S);
@@ -277,6 +283,8 @@ void ws_destroy(ch_ws_s* w);
 ch_status ws_set_params(ch_ws_s* w, const float* host, cudaStream_t st);
 ch_status ws_get_params(const ch_ws_s* w, float* host, float* host_grads, cudaStream_t st);
 ch_status ws_set_norm(ch_ws_s* w, const float* host20, cudaStream_t st);
+ch_status ws_fit_norm(ch_ws_s* w, const void* q, const void* x, const void* n, int S, int fp32, double* host20,
+                      cudaStream_t st);
 ch_status ws_predict(ch_ws_s* w, const double* state, const double* prev, double* pred, cudaStream_t st);
 ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float* n, int B, float lap,
                         float lr, float* loss, cudaStream_t st);

@@ -781,6 +781,127 @@ ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc
   return CH_OK;
 }
 
+// ---------------------------------------------------------------- normalisation of a training set
+// S samples of P x 4 states x, their predecessors q and successors n (fp64, or fp32 with F = float).
+// The network's inputs are the fields (normalised by their mean and standard deviation over the
+// set) and the change d = x - q in units of its per-sample RMS r (mean 0, scale 1 as they are);
+// its output is scaled by the standard deviation of the extrapolation's correction in those units,
+// e = ((n - x) - d) / r.  Standard deviations use the n - 1 divisor.  Sums run in a fixed order
+// (per-block partials, then one block in block order), so the statistics are reproducible.
+constexpr int FIT_BLOCKS = 152 * 4;
+
+template <typename F>
+__global__ void k_fit_r(const F* __restrict__ x, const F* __restrict__ q, int P, double* __restrict__ r) {
+  __shared__ double sm[TPB / 32][4];
+  const F* xs = x + (size_t)blockIdx.x * P * 4;
+  const F* qs = q + (size_t)blockIdx.x * P * 4;
+  double acc[4] = {0, 0, 0, 0};
+  for (int p = threadIdx.x; p < P; p += blockDim.x)
+    for (int c = 0; c < 4; ++c) {
+      const double d = (double)xs[(size_t)p * 4 + c] - (double)qs[(size_t)p * 4 + c];
+      acc[c] = fma(d, d, acc[c]);
+    }
+  for (int c = 0; c < 4; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < TPB / 32; ++w) t += sm[w][threadIdx.x];
+    r[blockIdx.x * 4 + threadIdx.x] = fmax(sqrt(t / P), 1e-30);
+  }
+}
+
+// pass 0: sums of x and e per channel; pass 1: sums of squared deviations from mean[8]
+template <typename F, int PASS>
+__global__ void k_fit_sums(const F* __restrict__ x, const F* __restrict__ q, const F* __restrict__ n, int P,
+                           int64_t total, const double* __restrict__ r, const double* __restrict__ mean,
+                           double* __restrict__ part) {
+  __shared__ double sm[TPB / 32][8];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t smp = v / P;
+    for (int c = 0; c < 4; ++c) {
+      const double xv = x[v * 4 + c], qv = q[v * 4 + c], nv = n[v * 4 + c];
+      const double e = ((nv - xv) - (xv - qv)) / r[smp * 4 + c];
+      if (PASS == 0) {
+        acc[c] += xv;
+        acc[4 + c] += e;
+      } else {
+        const double dx = xv - mean[c], de = e - mean[4 + c];
+        acc[c] = fma(dx, dx, acc[c]);
+        acc[4 + c] = fma(de, de, acc[4 + c]);
+      }
+    }
+  }
+  for (int k = 0; k < 8; ++k) {
+    double t = acc[k];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5][k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double t = 0.0;
+    for (int w = 0; w < TPB / 32; ++w) t += sm[w][threadIdx.x];
+    part[blockIdx.x * 8 + threadIdx.x] = t;
+  }
+}
+
+// one block: out[k] = sum over the blocks' partials (in block order) / div
+__global__ void k_fit_reduce(const double* __restrict__ part, int nparts, double div, double* __restrict__ out) {
+  if (threadIdx.x >= 8) return;
+  double t = 0.0;
+  for (int b = 0; b < nparts; ++b) t += part[b * 8 + threadIdx.x];
+  out[threadIdx.x] = t / div;
+}
+
+// norm[20] = (mean of the fields, 0 x 4; 1/std of the fields, 1 x 4; std of e) from the means
+// (stats[0..8)) and variances (stats[8..16))
+__global__ void k_fit_norm(const double* __restrict__ stats, float* __restrict__ norm, double* __restrict__ out20) {
+  const int c = threadIdx.x;
+  if (c >= 4) return;
+  const double mx = stats[c], sx = fmax(sqrt(stats[8 + c]), 1e-30), se = fmax(sqrt(stats[12 + c]), 1e-30);
+  const double vals[5] = {mx, 0.0, 1.0 / sx, 1.0, se};
+  for (int k = 0; k < 5; ++k) {
+    norm[4 * k + c] = (float)vals[k];
+    out20[4 * k + c] = vals[k];
+  }
+}
+
+template <typename F>
+static ch_status fit_norm_t(ch_ws_s* w, const F* q, const F* x, const F* n, int S, double* host20, cudaStream_t st) {
+  const int P = w->P;
+  const int64_t total = (int64_t)S * P;
+  Alloc tmp;
+  double *r = nullptr, *part = nullptr, *stats = nullptr, *out20 = nullptr;
+  CH_TRY(tmp.get(&r, (size_t)S * 4));
+  CH_TRY(tmp.get(&part, (size_t)FIT_BLOCKS * 8));
+  CH_TRY(tmp.get(&stats, 16));
+  CH_TRY(tmp.get(&out20, 20));
+  const int nb = (int)std::min<int64_t>(FIT_BLOCKS, (total + TPB - 1) / TPB);
+  k_fit_r<F><<<S, TPB, 0, st>>>(x, q, P, r);
+  k_fit_sums<F, 0><<<nb, TPB, 0, st>>>(x, q, n, P, total, r, nullptr, part);
+  k_fit_reduce<<<1, 32, 0, st>>>(part, nb, (double)total, stats);
+  k_fit_sums<F, 1><<<nb, TPB, 0, st>>>(x, q, n, P, total, r, stats, part);
+  k_fit_reduce<<<1, 32, 0, st>>>(part, nb, (double)(total - 1), stats + 8);
+  k_fit_norm<<<1, 32, 0, st>>>(stats, w->norm, out20);
+  CH_LAUNCHED();
+  CH_CUDA(cudaMemcpyAsync(host20, out20, sizeof(double) * 20, cudaMemcpyDeviceToHost, st));
+  CH_CUDA(cudaStreamSynchronize(st));
+  return CH_OK;
+}
+
+ch_status ws_fit_norm(ch_ws_s* w, const void* q, const void* x, const void* n, int S, int fp32, double* host20,
+                      cudaStream_t st) {
+  if (fp32)
+    return fit_norm_t<float>(w, static_cast<const float*>(q), static_cast<const float*>(x),
+                             static_cast<const float*>(n), S, host20, st);
+  return fit_norm_t<double>(w, static_cast<const double*>(q), static_cast<const double*>(x),
+                            static_cast<const double*>(n), S, host20, st);
+}
+
 int ws_nparam() { return WS_NPARAM; }
 
 void ws_dims(const ch_ws_s* w, int* H, int* W) {

@@ -11,9 +11,9 @@ FP64 residual decides between it and the previous step, which stays the fallback
     net, info = train_residual(data, net, make_system(nx, ny))   # library kernels, Adam
     stats = run_steps(nx, ny, seed, 20, net=net)                  # ch_step_learned per step
 
-PyTorch holds the tensors (state stacks, shuffling indices) and computes the normalisation
-statistics once before training; every layer, loss, gradient and optimiser update, and every
-prediction during stepping, runs in the library.
+PyTorch holds the tensors (state stacks, shuffling indices); the normalisation statistics, every
+layer, loss, gradient and optimiser update, and every prediction during stepping run in the
+library.
 """
 from __future__ import annotations
 
@@ -67,20 +67,6 @@ def generate_pairs(nx: int, ny: int, seeds, steps: int, precision: int = 0, burn
     return torch.stack(qs), torch.stack(xs), torch.stack(ys)
 
 
-def normalisation(Q: torch.Tensor, X: torch.Tensor, Y: torch.Tensor):
-    """Input mean and 1/std per channel (the fields; the change channels are already in units of
-    their RMS and keep mean 0, scale 1) and the output scale: the std of the correction to the
-    linear extrapolation in those units."""
-    x = X.reshape(-1, 4).double()
-    d = X.double() - Q.double()
-    r = d.pow(2).mean(1, keepdim=True).sqrt().clamp_min(1e-30)          # (S, 1, 4)
-    e = ((Y.double() - X.double()) - d) / r
-    mean = torch.cat([x.mean(0), torch.zeros(4, dtype=torch.float64, device=x.device)])
-    inv_std = torch.cat([1.0 / x.std(0).clamp_min(1e-30), torch.ones(4, dtype=torch.float64, device=x.device)])
-    out = e.reshape(-1, 4).std(0).clamp_min(1e-30)
-    return mean.cpu().numpy(), inv_std.cpu().numpy(), out.cpu().numpy()
-
-
 def init_params(nparams: int, seed: int = 0):
     """He-uniform initial weights (zero biases) in the library's parameter layout."""
     rng = np.random.default_rng(seed)
@@ -103,10 +89,10 @@ def train(data, net, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: in
     grid-Laplacian term of the loss.  Returns (net, info)."""
     Q, X, Y = data
     S, N = X.shape[0], X.shape[1]
-    mean, inv_std, out_scale = normalisation(Q, X, Y)
+    mean, inv_std, out_scale = net.fit_norm(Q, X, Y)  # computed on the device by the library
     if not use_fields:
         mean[:4], inv_std[:4] = 0.0, 0.0
-    net.set_norm(mean, inv_std, out_scale)
+        net.set_norm(mean, inv_std, out_scale)
     net.set_params(init_params(net.nparams, seed))
     g = torch.Generator(device="cpu").manual_seed(seed)
     losses = []
@@ -131,10 +117,10 @@ def train_residual(data, net, system, epochs: int = 8, batch: int = 8, lr: float
     loss is the mean |r|^2 / |r_extrapolation|^2: below 1 beats extrapolation."""
     Q, X, Y = data
     S, N = X.shape[0], X.shape[1]
-    mean, inv_std, out_scale = normalisation(Q, X, Y)
+    mean, inv_std, out_scale = net.fit_norm(Q, X, Y)  # computed on the device by the library
     if not use_fields:
         mean[:4], inv_std[:4] = 0.0, 0.0
-    net.set_norm(mean, inv_std, out_scale)
+        net.set_norm(mean, inv_std, out_scale)
     net.set_params(init_params(net.nparams, seed))
     g = torch.Generator(device="cpu").manual_seed(seed)
     losses = []

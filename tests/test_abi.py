@@ -72,6 +72,9 @@ def test_defaults_are_the_papers(L):
     assert p.cheb_degree == 5 and p.vcycles_H == 2 and p.vcycles_M == 1 and p.autotune == 1
     assert p.coarse_max == 0 and p.cheb_degree_coarse == 0 and p.krylov == 0
     assert p.cheb_degree_M == 0 and p.pattern == 0
+    assert p.precond_M == 0 and p.cheb_M_steps == 0
+    assert (p.chi_pn, p.chi_ps, p.chi_ns, p.N_p, p.N_nfa, p.N_s) == (1.0, 0.3, 0.3, 20.0, 20.0, 1.0)
+    assert p.fh_delta == 1e-10
 
 
 def test_status_strings(L):
@@ -84,7 +87,10 @@ def test_status_strings(L):
                                  dict(evap_sign=0), dict(coarse_max=-1), dict(coarse_max=4097),
                                  dict(cheb_degree_coarse=-1), dict(cheb_degree_coarse=17),
                                  dict(krylov=2), dict(cheb_degree_M=-1), dict(cheb_degree_M=17),
-                                 dict(pattern=2), dict(pattern=-1)])
+                                 dict(pattern=2), dict(pattern=-1), dict(potential=4),
+                                 dict(precond_M=2), dict(cheb_M_steps=17), dict(cheb_M_steps=-1),
+                                 dict(N_p=0.0), dict(N_s=-1.0), dict(fh_delta=0.0), dict(fh_delta=1.0),
+                                 dict(chi_pn=float("nan"))])
 def test_invalid_params_rejected_on_host(L, bad):
     p = ch.Params(**bad)
     h = ctypes.c_void_p()

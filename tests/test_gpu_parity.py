@@ -17,7 +17,7 @@ from paper_2204_03575_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-POT = {"poly": 0, "poly_partial": 1, "none": 2}
+POT = {"poly": 0, "poly_partial": 1, "none": 2, "fh": 3}
 
 
 def make(ch, **kw):
@@ -85,6 +85,39 @@ def test_loads_parity(lib, kw, potential):
     else:
         assert rel(Fp, eFp) < 1e-13 and rel(Fn, eFn) < 1e-13
     assert rel(gp, egp) < 1e-13 and rel(gn, egn) < 1e-13
+
+
+@pytest.mark.parametrize("kw", CASES)
+@pytest.mark.parametrize("chi", [{}, dict(chi_pn=2.5, chi_ps=-0.4, chi_ns=0.7, N_p=7.0, N_nfa=3.0, N_s=2.0)])
+def test_flory_huggins_loads_parity(lib, kw, chi):
+    """potential = 3 (Section 2's logarithmic f, reading R14): the device's element rule (its own
+    3-point Gauss-Legendre table collapsed onto the simplex) against the oracle's rule, on states
+    that reach the guard (values at and below 0 at some nodes, so quadrature points fall below
+    fh_delta).  Logarithms are correctly rounded to within an ulp on both sides: 1e-12."""
+    cp, op = make(lib, potential="fh", **chi, **kw)
+    system = lib.System(lib.Mesh(cp), cp)
+    om = o.mesh(op)
+    rng = np.random.default_rng(13)
+    pp, pn = 0.05 + 0.5 * rng.random(system.n), 0.05 + 0.4 * rng.random(system.n)
+    pp[::17] = -0.02
+    pn[5::23] = 0.0
+    pp[3::29] = 1e-12
+    Fp, Fn, gp, gn = [t.cpu().numpy() for t in system.loads(cuda(pp), cuda(pn))]
+    eFp, eFn = o.load_vector_fh(om, pp, pn, op)
+    assert np.isfinite(Fp).all() and np.isfinite(Fn).all()
+    assert rel(Fp, eFp) < 1e-12 and rel(Fn, eFn) < 1e-12
+    egp, egn = o.boundary_load(om, pp, pn, op)
+    assert rel(gp, egp) < 1e-13 and rel(gn, egn) < 1e-13
+
+
+@pytest.mark.parametrize("kw", [dict(nx=32, ny=32), dict(dim=3, nx=16, ny=16, nz=4, Lz=0.25)])
+def test_flory_huggins_step_parity(lib, kw):
+    """Three steps with the Flory-Huggins load: fields 1e-10 against the oracle's direct solve."""
+    _, out = run_pair(lib, 3, rtol=1e-13, max_iter=1000, potential="fh", **kw)
+    for st, g, _, ref in out:
+        assert st["status"] == 0
+        for k in ("phi_p", "phi_nfa", "mu_p", "mu_nfa"):
+            assert rel(g[k], getattr(ref, k)) < 1e-10, k
 
 
 @pytest.mark.parametrize("kw", CASES + [dict(nx=36, ny=12, Lx=10.0, Ly=2.5),

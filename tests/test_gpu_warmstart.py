@@ -276,3 +276,37 @@ def test_step_learned_rejects_a_network_of_another_size(lib):
     s.init_seeded(0.33, 0.31, 0.01, seed=5)
     with pytest.raises(lib.ChError):
         s.step_learned(ws.zero_net(20, 24))
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_fit_norm_matches_its_definition(lib, fp32):
+    """ch_ws_fit_norm: field means and 1/std over the set, change channels (0, 1), and the std of
+    the extrapolation's correction in units of the per-sample RMS of the change (n - 1 divisors),
+    against numpy in float64; the statistics are set on the network (a bias-only last layer makes
+    the prediction s + d + b3 * out_scale * r)."""
+    rng = np.random.default_rng(8)
+    S, H, W = 5, 9, 13
+    X = rng.standard_normal((S, H * W, 4)) * [1.0, 2.0, 0.5, 3.0] + [0.3, -0.2, 1.0, 0.0]
+    Q = X - 0.01 * rng.standard_normal(X.shape)
+    Y = 2 * X - Q + 1e-3 * rng.standard_normal(X.shape)
+    dt = np.float32 if fp32 else np.float64
+    X, Q, Y = (a.astype(dt) for a in (X, Q, Y))
+    net = lib.WarmStartNet(H, W, max_batch=1)
+    mean, inv_std, out = net.fit_norm(*(torch.from_numpy(a).cuda() for a in (Q, X, Y)))
+    x, q, y = (a.astype(np.float64) for a in (X, Q, Y))
+    d = x - q
+    r = np.maximum(np.sqrt((d ** 2).mean(1, keepdims=True)), 1e-30)
+    e = ((y - x) - d) / r
+    np.testing.assert_allclose(mean[:4], x.reshape(-1, 4).mean(0), rtol=1e-12, atol=1e-15)
+    np.testing.assert_array_equal(mean[4:], 0.0)
+    np.testing.assert_allclose(inv_std[:4], 1.0 / x.reshape(-1, 4).std(0, ddof=1), rtol=1e-12)
+    np.testing.assert_array_equal(inv_std[4:], 1.0)
+    np.testing.assert_allclose(out, e.reshape(-1, 4).std(0, ddof=1), rtol=1e-11)
+    theta = np.zeros(net.nparams, np.float32)
+    theta[-8:-4] = [0.5, -1.0, 2.0, 0.25]  # b3 (first four output channels)
+    net.set_params(theta)
+    s0, q0 = x[0], q[0]
+    pred = net.predict(torch.from_numpy(s0).cuda(), torch.from_numpy(q0).cuda()).cpu().numpy()
+    rr = wo.change_scale(s0.reshape(H, W, 4), q0.reshape(H, W, 4))
+    want = s0 + (s0 - q0) + theta[-8:-4].astype(np.float64) * out.astype(np.float32) * rr
+    np.testing.assert_allclose(pred, want, rtol=1e-5, atol=1e-6 * np.abs(want).max())

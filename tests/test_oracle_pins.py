@@ -372,6 +372,28 @@ def test_constant_state_is_fixed_point(dim):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
+def test_constant_state_is_fixed_point_flory_huggins(dim):
+    """potential 'fh': the step of a constant state under zero flux keeps phi and sets mu to the
+    Flory-Huggins f'(c), the chain-rule derivative of f(phi_p, phi_nfa, 1 - phi_p - phi_nfa)
+    taken here by central differences of f itself."""
+    p = o.Params(dim=dim, nx=5, ny=4, nz=3 if dim == 3 else 0, bc_mode=0, potential="fh")
+    s = o.Solver(p)
+    c_p, c_n = 0.35, 0.25
+    st = o.initial(s.N, np.full(s.N, c_p), np.full(s.N, c_n))
+    nxt = s.step(st)
+    h = 1e-6
+    efp = (o.flory_huggins(np.array(c_p + h), np.array(c_n), p) - o.flory_huggins(np.array(c_p - h), np.array(c_n), p)) / (2 * h)
+    efn = (o.flory_huggins(np.array(c_p), np.array(c_n + h), p) - o.flory_huggins(np.array(c_p), np.array(c_n - h), p)) / (2 * h)
+    np.testing.assert_allclose(nxt.phi_p, c_p, rtol=1e-12)
+    np.testing.assert_allclose(nxt.phi_nfa, c_n, rtol=1e-12)
+    np.testing.assert_allclose(nxt.mu_p, float(efp), rtol=1e-7)
+    np.testing.assert_allclose(nxt.mu_nfa, float(efn), rtol=1e-7)
+    # and it differs from Eq. (15)'s fixed point (the dispatch really changed the load)
+    poly = o.Solver(o.Params(dim=dim, nx=5, ny=4, nz=3 if dim == 3 else 0, bc_mode=0)).step(st)
+    assert abs(poly.mu_p[0] - nxt.mu_p[0]) > 1e-2
+
+
+@pytest.mark.parametrize("dim", [2, 3])
 def test_linear_mode_closed_form(dim):
     """f' = 0, zero flux: a generalized eigenvector K v = lam M v decays as 1/(1 + tau eps lam^2)."""
     p = o.Params(dim=dim, nx=6, ny=5, nz=3 if dim == 3 else 0, bc_mode=0, potential="none",
@@ -849,3 +871,29 @@ def test_vcycle_contracts_the_error():
     for _ in range(40):
         x = o.vcycle(levels, b, x)
     np.testing.assert_allclose(x, spla.spsolve(A.tocsc(), b), rtol=1e-9)
+
+
+def test_imex_scheme_is_first_order_in_tau():
+    """Section 4's convergence study: the semi-implicit scheme of Eq. (12) is first order in tau.
+    On the paper's 10 x 2.5 box (16 x 8 points, 0.35 +/- 0.01, polynomial potential) the error
+    at T = 1.6e-2 against tau = 1e-5 halves with tau: the experimental order between tau = 2e-4
+    and 4e-4 is within [0.9, 1.1], and the errors grow monotonically with tau."""
+    from paper_2204_03575_gb300 import inputs
+
+    def run(tau, T=1.6e-2):
+        s = o.Solver(o.Params(nx=15, ny=7, Lx=10.0, Ly=2.5, tau=tau))
+        pp, pn = inputs.initial_state(s.N, 0.35, 0.35, 0.01, seed=0)
+        st = o.initial(s.N, pp, pn)
+        for _ in range(int(round(T / tau))):
+            st = s.step(st)
+        return st, s.M
+
+    ref, M = run(1e-5)
+    errs = []
+    for tau in (2e-4, 4e-4, 8e-4):
+        st, _ = run(tau)
+        d = st.phi_p - ref.phi_p
+        errs.append(math.sqrt(d @ (M @ d)))
+    assert errs[0] < errs[1] < errs[2]
+    eoc = math.log(errs[1] / errs[0]) / math.log(2.0)
+    assert 0.9 <= eoc <= 1.1, eoc
