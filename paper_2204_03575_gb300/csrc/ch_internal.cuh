@@ -143,8 +143,6 @@ struct ProfTally {
   double bytes[K_COUNT * 2] = {};
   double fmas[K_COUNT * 2] = {};
 };
-void prof_capture_begin();
-ProfTally prof_capture_end();
 // the tally that ProfScopes record into while capturing (nullptr: none); returns the previous one
 ProfTally* prof_capture_swap(ProfTally* t);
 void prof_add(const ProfTally& t);

@@ -554,6 +554,99 @@ __global__ void k_ctl(int nruns, const KrylovDev* kds, Ctl* c, int m, int max_it
   cudaGraphSetConditional(hw, (unsigned)go);
 }
 
+// MINRES's control kernel (same record): case 0 starts the recurrence, cases 1 and 3 take an
+// iteration (3 after retargeting), case 2 checks the true residual.  As in `minres`: iterate while
+// some system's estimate is above its target, then check; stop when every system has converged,
+// at max_iter or at a non-finite value.  Passes are bounded: every pass but a start or a check
+// raises `total`, and a check follows at least one other pass.
+__global__ void k_ctl_mr(int nruns, const KrylovDev* kds, Ctl* c, int max_iter, int init,
+                         cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hs) {
+  __shared__ int cnt[3];
+  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+  if (init)
+    for (int k = threadIdx.x; k < 4; k += blockDim.x) c->count[k] = 0;
+  __syncthreads();
+  int ca = 0, ac = 0, nf = 0;
+  for (int r = threadIdx.x; r < nruns; r += blockDim.x) {
+    const KrylovDev* kd = kds + r;
+    ca += kd->cycle_active[0] + kd->cycle_active[1];
+    ac += kd->active[0] + kd->active[1];
+    nf += kd->nonfinite;
+  }
+  if (ca) atomicAdd(&cnt[0], ca);
+  if (ac) atomicAdd(&cnt[1], ac);
+  if (nf) atomicAdd(&cnt[2], nf);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int cycle_active = cnt[0], active = cnt[1], nonfinite = cnt[2];
+  int go = 1, sel = 0;
+  auto iterate_or_check = [&]() {
+    if (cycle_active > 0) {
+      if (c->total >= max_iter) {
+        c->status = CH_ERR_NOT_CONVERGED;
+        go = 0;
+      } else {
+        sel = 1;
+      }
+    } else {
+      sel = 2;
+    }
+  };
+  if (init) {
+    c->total = 0;
+    c->restarts = 0;
+    c->passes = 0;
+    c->sum_j = 0;
+    c->jcycle = 0;
+    c->where = 0;
+    c->status = CH_OK;
+    if (nonfinite) {
+      c->status = CH_ERR_NONFINITE;
+      go = 0;
+    } else if (active == 0) {
+      go = 0;
+    }
+  } else {
+    const int cur = c->sel;
+    c->count[cur] += 1;
+    c->passes += 1;
+    if (cur == 0) {
+      iterate_or_check();
+    } else if (cur == 2) {
+      if (nonfinite) {
+        c->status = CH_ERR_NONFINITE;
+        c->where = 2;
+        go = 0;
+      } else if (active == 0) {
+        go = 0;
+      } else if (c->total >= max_iter) {
+        c->status = CH_ERR_NOT_CONVERGED;
+        go = 0;
+      } else {
+        c->restarts += 1;
+        sel = 3;
+      }
+    } else {
+      c->total += 1;
+      if (nonfinite) {
+        c->status = CH_ERR_NONFINITE;
+        c->where = 1;
+        go = 0;
+      } else {
+        iterate_or_check();
+      }
+    }
+    if (go && c->passes > 2 * max_iter + 4) {  // cannot happen by the rules above; a backstop
+      c->status = CH_ERR_INTERNAL;
+      go = 0;
+    }
+  }
+  c->active = active;
+  c->sel = sel;
+  cudaGraphSetConditional(hs, (unsigned)sel);
+  cudaGraphSetConditional(hw, (unsigned)go);
+}
+
 // mass_s = sum_i (M 1)_i phi_s,i  (M symmetric: 1^T M phi), per run
 __global__ void k_mass(Seg sg, const double* mlump, const double4_32a* x, double* partials,
                        KrylovDev* kds) {
@@ -672,8 +765,6 @@ struct ch_state_s {
   cudaStream_t cap_stream = nullptr;            // private stream for graph capture
   cudaStream_t body_stream = nullptr;           // nested captures of the device loop's body
   ch::MrDev* mr = nullptr;                      // MINRES scalars, one per run
-  cudaGraphExec_t mr_graph = nullptr;           // one MINRES iteration, captured on first use
-  ch::ProfTally mr_tally;
   // device-side FGMRES loop (graphs on, per-launch timing off): one graph per plain step, and
   // the solve alone for steps with a caller's guess; built on first use
   ch::Ctl* dctl = nullptr;
@@ -689,7 +780,6 @@ struct ch_state_s {
     if (solve_graph) cudaGraphExecDestroy(solve_graph);
     if (step_g) cudaGraphDestroy(step_g);
     if (solve_g) cudaGraphDestroy(solve_g);
-    if (mr_graph) cudaGraphExecDestroy(mr_graph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (body_stream) cudaStreamDestroy(body_stream);
     if (hflags) cudaFreeHost(hflags);
@@ -956,202 +1046,6 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
   return CH_OK;
 }
 
-// ---------------------------------------------------------------- FGMRES on the device
-// The loop of `fgmres` as one CUDA graph (see Ctl): no host synchronisation inside a solve.
-static bool device_loop(const ch_state_s* S) {
-  return S->use_graphs && S->sys->p.krylov == 0 && !prof_timing();
-}
-
-// Case j < m of the loop body: Arnoldi step j (case 0 first forms V_0 = r / beta); case m: the
-// end of a restart cycle (y = R^-1 g, x += Z y over the cycle's steps, the true residual).
-static ch_status loop_case(ch_state_s* S, int j, cudaStream_t st) {
-  const int N = S->N, nb = S->nblocks;
-  double4_32a* W4 = reinterpret_cast<double4_32a*>(S->W);
-  double4_32a* V4 = reinterpret_cast<double4_32a*>(S->V);
-  if (j < S->m) {
-    if (j == 0) {
-      ProfScope ps(st, K_SCALE4, 0, 64.0 * N, 0.0);
-      k_scale4<<<nb, TPB, 0, st>>>(S->seg, W4, V4, S->kd);
-    }
-    CH_LAUNCHED();
-    return arnoldi_step(S, j, st);
-  }
-  {
-    ProfScope ps(st, K_CYCLE_SOLVE, 0, 0.0, 0.0);
-    k_cycle_solve<<<blocks_for(2 * S->R, 64), 64, 0, st>>>(S->R, S->kd);
-  }
-  {
-    // bytes of the x update beyond x itself (32 N per Krylov vector) are added per cycle from
-    // the loop's record (Ctl::sum_j), the length being known on the device only
-    ProfScope ps(st, K_UPDATE_X, 0, 2 * 32.0 * N, 0.0);
-    k_update_x<<<nb, TPB, 0, st>>>(S->seg, N, S->m, &S->dctl->jcycle, reinterpret_cast<const double4_32a*>(S->Z),
-                                    reinterpret_cast<double4_32a*>(S->x), S->kd);
-  }
-  CH_LAUNCHED();
-  return residual_launch(S, 0, st);
-}
-
-// Capture `fill` into the graph `g` on the body stream, after the nodes deps[0..nd).
-template <typename F>
-static ch_status capture_into(ch_state_s* S, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, F fill) {
-  cudaStream_t bs = S->body_stream;
-  CH_CUDA(cudaStreamBeginCaptureToGraph(bs, g, deps, nullptr, nd, cudaStreamCaptureModeThreadLocal));
-  const ch_status r = fill(bs);
-  cudaGraph_t out = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(bs, &out);
-  CH_TRY(r);
-  CH_CUDA(e);
-  return CH_OK;
-}
-
-// Enqueue the whole solve on the capturing stream cs: the initial residual, k_ctl, and the while
-// node with its body.  Launch accounting: the initial residual and k_ctl go to the tally that is
-// current on entry, case j to tally_case[j], the body's k_ctl to tally_ctl.
-static ch_status capture_solve(ch_state_s* S, cudaStream_t cs) {
-  const int m = S->m, max_iter = S->sys->p.max_iter;
-  cudaStreamCaptureStatus cst;
-  cudaGraph_t g = nullptr;
-  CH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr));
-  cudaGraphConditionalHandle hw, hs;
-  CH_CUDA(cudaGraphConditionalHandleCreate(&hw, g, 0, 0));
-  CH_CUDA(cudaGraphConditionalHandleCreate(&hs, g, 0, 0));
-  CH_TRY(residual_launch(S, 1, cs));
-  {
-    ProfScope ps(cs, K_FLAGS, 0, 0.0, 0.0);
-    k_ctl<<<1, 256, 0, cs>>>(S->R, S->kd, S->dctl, m, max_iter, 1, hw, hs);
-  }
-  CH_LAUNCHED();
-  const cudaGraphNode_t* deps = nullptr;
-  size_t nd = 0;
-  CH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd));
-  cudaGraphNodeParams wp = {};
-  wp.type = cudaGraphNodeTypeConditional;
-  wp.conditional.handle = hw;
-  wp.conditional.type = cudaGraphCondTypeWhile;
-  wp.conditional.size = 1;
-  cudaGraphNode_t wn = nullptr;
-  CH_CUDA(cudaGraphAddNode(&wn, g, deps, nullptr, nd, &wp));
-  cudaGraph_t body = wp.conditional.phGraph_out[0];
-  cudaGraphNodeParams sp = {};
-  sp.type = cudaGraphNodeTypeConditional;
-  sp.conditional.handle = hs;
-  sp.conditional.type = cudaGraphCondTypeSwitch;
-  sp.conditional.size = (unsigned)(m + 1);
-  cudaGraphNode_t sn = nullptr;
-  CH_CUDA(cudaGraphAddNode(&sn, body, nullptr, nullptr, 0, &sp));
-  ProfTally* outer = prof_capture_swap(nullptr);
-  ch_status r = CH_OK;
-  for (int j = 0; j <= m && r == CH_OK; ++j) {
-    S->tally_case[j] = ProfTally();
-    prof_capture_swap(&S->tally_case[j]);
-    r = capture_into(S, sp.conditional.phGraph_out[j], nullptr, 0,
-                     [&](cudaStream_t bs) { return loop_case(S, j, bs); });
-  }
-  if (r == CH_OK) {
-    S->tally_ctl = ProfTally();
-    prof_capture_swap(&S->tally_ctl);
-    r = capture_into(S, body, &sn, 1, [&](cudaStream_t bs) -> ch_status {
-      ProfScope ps(bs, K_FLAGS, 0, 0.0, 0.0);
-      k_ctl<<<1, 256, 0, bs>>>(S->R, S->kd, S->dctl, m, max_iter, 0, hw, hs);
-      CH_LAUNCHED();
-      return CH_OK;
-    });
-  }
-  prof_capture_swap(outer);
-  CH_TRY(r);
-  CH_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
-  return CH_OK;
-}
-
-// Build the graph of a whole plain step (whole = true: right-hand sides, solve, masses, run
-// statistics, and the copies of the statistics and the loop record to pinned host memory) or of
-// the solve alone (the loop record copied out).
-static ch_status build_loop_graph(ch_state_s* S, bool whole, cudaGraph_t* gout, cudaGraphExec_t* xout,
-                                  ProfTally* tally) {
-  cudaGraph_t G = nullptr;
-  CH_CUDA(cudaGraphCreate(&G, 0));
-  cudaStream_t cs = S->cap_stream;
-  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(G);
-    CH_CUDA(e);
-  }
-  *tally = ProfTally();
-  ProfTally* prev = prof_capture_swap(tally);
-  ch_status r = CH_OK;
-  if (whole) {
-    r = rhs_strided(S->sys, S->x, S->x + 1, 4, S->b, cs);
-    if (r == CH_OK) {
-      k_clear_warm<<<blocks_for(S->R, 64), 64, 0, cs>>>(S->R, S->kd);
-      if (cudaGetLastError() != cudaSuccess) r = CH_ERR_CUDA;
-    }
-  }
-  if (r == CH_OK) r = capture_solve(S, cs);
-  if (r == CH_OK && whole) {
-    {
-      ProfScope ps(cs, K_MASS, 0, 40.0 * S->N, 2.0 * S->N);
-      k_mass<<<S->nblocks, TPB, 0, cs>>>(S->seg, S->mlump, reinterpret_cast<const double4_32a*>(S->x),
-                                          S->partials, S->kd);
-    }
-    k_run_stats<<<blocks_for(S->R, 64), 64, 0, cs>>>(S->R, S->kd, S->dstats);
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(S->hstats_pin, S->dstats, sizeof(RunStats) * S->R, cudaMemcpyDeviceToHost, cs) !=
-            cudaSuccess)
-      r = CH_ERR_CUDA;
-  }
-  if (r == CH_OK && cudaMemcpyAsync(S->hctl, S->dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
-    r = CH_ERR_CUDA;
-  prof_capture_swap(prev);
-  cudaGraph_t captured = nullptr;
-  e = cudaStreamEndCapture(cs, &captured);
-  if (r == CH_ERR_CUDA) set_error("capturing the device-side FGMRES loop failed: %s", cudaGetErrorString(cudaGetLastError()));
-  if (r == CH_OK && e != cudaSuccess) {
-    set_error("capturing the device-side FGMRES loop failed: %s", cudaGetErrorString(e));
-    r = CH_ERR_CUDA;
-  }
-  if (r == CH_OK) {
-    e = cudaGraphInstantiate(xout, G, 0);
-    if (e != cudaSuccess) {
-      set_error("instantiating the device-side FGMRES loop failed: %s", cudaGetErrorString(e));
-      *xout = nullptr;
-      r = CH_ERR_CUDA;
-    }
-  }
-  if (r != CH_OK) {
-    cudaGetLastError();
-    cudaGraphDestroy(G);
-    return r;
-  }
-  *gout = G;  // kept until the state goes (a graph with conditional nodes has one instantiation)
-  return CH_OK;
-}
-
-// After the loop's graph has completed (stream synchronised): launch accounting of the passes
-// taken and the solve's status from the loop record.
-static ch_status finish_loop(ch_state_s* S, const ProfTally& pro, int* restarts) {
-  const Ctl& c = *S->hctl;
-  prof_add(pro);
-  for (int j = 0; j <= S->m; ++j) prof_add_times(S->tally_case[j], c.count[j]);
-  prof_add_times(S->tally_ctl, c.passes);
-  prof_add_slot(K_UPDATE_X, 0, 0, 32.0 * S->N * c.sum_j, 4.0 * S->N * c.sum_j);
-  *restarts = c.restarts;
-  switch (c.status) {
-    case CH_OK:
-      return CH_OK;
-    case CH_ERR_NONFINITE:
-      set_error(c.where == 0 ? "non-finite right-hand side or initial residual"
-                : c.where == 1 ? "non-finite value in the Arnoldi process" : "non-finite residual");
-      return CH_ERR_NONFINITE;
-    case CH_ERR_NOT_CONVERGED:
-      set_error("FGMRES reached max_iter = %d with %d of %d systems unconverged", S->sys->p.max_iter, c.active,
-                2 * S->R);
-      return CH_ERR_NOT_CONVERGED;
-    default:
-      set_error("the device-side FGMRES loop stopped at its pass limit (%d passes)", c.passes);
-      return CH_ERR_INTERNAL;
-  }
-}
-
 // ---------------------------------------------------------------- preconditioned MINRES
 // The paper's Krylov method (Section 3): Lanczos vectors v_j (A-space) and z_j = P^-1 v_j, both
 // normalised by gamma_j = sqrt(v_j . z_j); the tridiagonal matrix (delta_j on the diagonal,
@@ -1351,6 +1245,12 @@ static ch_status mr_iteration(ch_state_s* S, cudaStream_t st) {
     ProfScope ps(st, K_MR_VEC, 0, 10.0 * 32.0 * N, 12.0 * N);
     k_mr_update<<<nb, TPB, 0, st>>>(S->seg, reinterpret_cast<double4_32a*>(S->x), w, wp, z, zn, v, vp, vn, S->mr);
   }
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+static ch_status mr_iteration_flags(ch_state_s* S, cudaStream_t st) {
+  CH_TRY(mr_iteration(S, st));
   {
     ProfScope ps(st, K_FLAGS, 0, 0.0, 0.0);
     k_flags<<<1, 256, 0, st>>>(S->R, S->kd, S->dflags);
@@ -1359,50 +1259,12 @@ static ch_status mr_iteration(ch_state_s* S, cudaStream_t st) {
   return CH_OK;
 }
 
-static ch_status mr_launch(ch_state_s* S, cudaStream_t st) {
-  if (!S->use_graphs || prof_timing()) {
-    CH_TRY(mr_iteration(S, st));
-  } else {
-    if (!S->mr_graph) {
-      cudaGraph_t g = nullptr;
-      CH_CUDA(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
-      prof_capture_begin();
-      const ch_status r = mr_iteration(S, S->cap_stream);
-      const cudaError_t e = cudaStreamEndCapture(S->cap_stream, &g);
-      S->mr_tally = prof_capture_end();
-      if (r != CH_OK) {
-        if (g) cudaGraphDestroy(g);
-        return r;
-      }
-      CH_CUDA(e);
-      const cudaError_t ei = cudaGraphInstantiate(&S->mr_graph, g, 0);
-      cudaGraphDestroy(g);
-      CH_CUDA(ei);
-    }
-    CH_CUDA(cudaGraphLaunch(S->mr_graph, st));
-    prof_add(S->mr_tally);
-  }
-  return read_flags(S, st);
-}
-
-// Preconditioned MINRES (the paper's Krylov method, Section 3) with Algorithm 1 as the fixed
-// preconditioner; the stopping test is the true FP64 residual, checked whenever every system's
-// MINRES estimate has reached its target (checks[0] counts the checks after the first).
-static ch_status minres(ch_state_s* S, cudaStream_t st, int* checks) {
-  const ch_params& p = S->sys->p;
+// The start of the recurrence: v_1 = r_0, z_1 = P^-1 v_1, v_0 = w_0 = w_{-1} = 0, gamma_1.
+static ch_status mr_start(ch_state_s* S, cudaStream_t st) {
   const int N = S->N, nb = S->nblocks;
   const size_t n4 = (size_t)N;
   double4_32a* V4 = reinterpret_cast<double4_32a*>(S->V);
   double4_32a* Z4 = reinterpret_cast<double4_32a*>(S->Z);
-  *checks = 0;
-  CH_TRY(residual_launch(S, 1, st));
-  CH_TRY(read_flags(S, st));
-  if (S->hflags->nonfinite) {
-    set_error("non-finite right-hand side or initial residual");
-    return CH_ERR_NONFINITE;
-  }
-  if (S->hflags->active == 0) return CH_OK;
-  // v_1 = r_0, z_1 = P^-1 v_1, v_0 = w_0 = w_{-1} = 0
   CH_CUDA(cudaMemcpyAsync(V4, S->W, sizeof(double4_32a) * n4, cudaMemcpyDeviceToDevice, st));
   CH_CUDA(cudaMemsetAsync(V4 + n4, 0, sizeof(double4_32a) * n4, st));
   CH_CUDA(cudaMemsetAsync(V4 + 3 * n4, 0, sizeof(double4_32a) * 2 * n4, st));
@@ -1415,8 +1277,31 @@ static ch_status minres(ch_state_s* S, cudaStream_t st, int* checks) {
     ProfScope ps(st, K_MR_VEC, 0, 128.0 * N, 4.0 * N);
     k_mr_scale<<<nb, TPB, 0, st>>>(S->seg, V4, Z4, S->mr);
   }
-  k_flags<<<1, 256, 0, st>>>(S->R, S->kd, S->dflags);
   CH_LAUNCHED();
+  return CH_OK;
+}
+
+// Host-driven MINRES iteration (graphs off, or per-launch event timing on): the iteration, the
+// summary flags, and a read of the flags.
+static ch_status mr_launch(ch_state_s* S, cudaStream_t st) {
+  CH_TRY(mr_iteration_flags(S, st));
+  return read_flags(S, st);
+}
+
+// Preconditioned MINRES (the paper's Krylov method, Section 3) with Algorithm 1 as the fixed
+// preconditioner; the stopping test is the true FP64 residual, checked whenever every system's
+// MINRES estimate has reached its target (checks[0] counts the checks after the first).
+static ch_status minres(ch_state_s* S, cudaStream_t st, int* checks) {
+  const ch_params& p = S->sys->p;
+  *checks = 0;
+  CH_TRY(residual_launch(S, 1, st));
+  CH_TRY(read_flags(S, st));
+  if (S->hflags->nonfinite) {
+    set_error("non-finite right-hand side or initial residual");
+    return CH_ERR_NONFINITE;
+  }
+  if (S->hflags->active == 0) return CH_OK;
+  CH_TRY(mr_start(S, st));
   CH_TRY(read_flags(S, st));
   int total = 0;
   for (;;) {
@@ -1454,6 +1339,232 @@ static ch_status minres(ch_state_s* S, cudaStream_t st, int* checks) {
 static ch_status krylov_solve(ch_state_s* S, cudaStream_t st, int* restarts) {
   return S->sys->p.krylov == 1 ? minres(S, st, restarts) : fgmres(S, st, restarts);
 }
+
+// ---------------------------------------------------------------- the Krylov loop on the device
+// The loops of `fgmres` and `minres` as one CUDA graph (see Ctl): no host synchronisation inside
+// a solve.
+static bool device_loop(const ch_state_s* S) { return S->use_graphs && !prof_timing(); }
+
+static bool is_minres(const ch_state_s* S) { return S->sys->p.krylov == 1; }
+
+// MINRES's cases: 0 the start of the recurrence, 1 an iteration, 2 the true-residual check,
+// 3 the retargeting of unconverged species followed by an iteration.
+static ch_status mr_case(ch_state_s* S, int c, cudaStream_t st) {
+  switch (c) {
+    case 0:
+      return mr_start(S, st);
+    case 1:
+      return mr_iteration(S, st);
+    case 2:
+      return residual_launch(S, 0, st);
+    default:
+      k_mr_retarget<<<blocks_for(2 * S->R, 64), 64, 0, st>>>(S->R, S->kd, S->mr);
+      CH_LAUNCHED();
+      return mr_iteration(S, st);
+  }
+}
+
+// Case j < m of the loop body: Arnoldi step j (case 0 first forms V_0 = r / beta); case m: the
+// end of a restart cycle (y = R^-1 g, x += Z y over the cycle's steps, the true residual).
+static ch_status loop_case(ch_state_s* S, int j, cudaStream_t st) {
+  const int N = S->N, nb = S->nblocks;
+  double4_32a* W4 = reinterpret_cast<double4_32a*>(S->W);
+  double4_32a* V4 = reinterpret_cast<double4_32a*>(S->V);
+  if (j < S->m) {
+    if (j == 0) {
+      ProfScope ps(st, K_SCALE4, 0, 64.0 * N, 0.0);
+      k_scale4<<<nb, TPB, 0, st>>>(S->seg, W4, V4, S->kd);
+    }
+    CH_LAUNCHED();
+    return arnoldi_step(S, j, st);
+  }
+  {
+    ProfScope ps(st, K_CYCLE_SOLVE, 0, 0.0, 0.0);
+    k_cycle_solve<<<blocks_for(2 * S->R, 64), 64, 0, st>>>(S->R, S->kd);
+  }
+  {
+    // bytes of the x update beyond x itself (32 N per Krylov vector) are added per cycle from
+    // the loop's record (Ctl::sum_j), the length being known on the device only
+    ProfScope ps(st, K_UPDATE_X, 0, 2 * 32.0 * N, 0.0);
+    k_update_x<<<nb, TPB, 0, st>>>(S->seg, N, S->m, &S->dctl->jcycle, reinterpret_cast<const double4_32a*>(S->Z),
+                                    reinterpret_cast<double4_32a*>(S->x), S->kd);
+  }
+  CH_LAUNCHED();
+  return residual_launch(S, 0, st);
+}
+
+// Capture `fill` into the graph `g` on the body stream, after the nodes deps[0..nd).
+template <typename F>
+static ch_status capture_into(ch_state_s* S, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, F fill) {
+  cudaStream_t bs = S->body_stream;
+  CH_CUDA(cudaStreamBeginCaptureToGraph(bs, g, deps, nullptr, nd, cudaStreamCaptureModeThreadLocal));
+  const ch_status r = fill(bs);
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(bs, &out);
+  CH_TRY(r);
+  CH_CUDA(e);
+  return CH_OK;
+}
+
+// Enqueue the whole solve on the capturing stream cs: the initial residual, k_ctl, and the while
+// node with its body.  Launch accounting: the initial residual and k_ctl go to the tally that is
+// current on entry, case j to tally_case[j], the body's k_ctl to tally_ctl.
+static ch_status capture_solve(ch_state_s* S, cudaStream_t cs) {
+  const int m = S->m, max_iter = S->sys->p.max_iter;
+  const bool mr = is_minres(S);
+  const int ncases = mr ? 4 : m + 1;
+  auto ctl = [&](cudaStream_t st, int init, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hs) {
+    if (mr)
+      k_ctl_mr<<<1, 256, 0, st>>>(S->R, S->kd, S->dctl, max_iter, init, hw, hs);
+    else
+      k_ctl<<<1, 256, 0, st>>>(S->R, S->kd, S->dctl, m, max_iter, init, hw, hs);
+  };
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  CH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle hw, hs;
+  CH_CUDA(cudaGraphConditionalHandleCreate(&hw, g, 0, 0));
+  CH_CUDA(cudaGraphConditionalHandleCreate(&hs, g, 0, 0));
+  CH_TRY(residual_launch(S, 1, cs));
+  {
+    ProfScope ps(cs, K_FLAGS, 0, 0.0, 0.0);
+    ctl(cs, 1, hw, hs);
+  }
+  CH_LAUNCHED();
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wn = nullptr;
+  CH_CUDA(cudaGraphAddNode(&wn, g, deps, nullptr, nd, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  cudaGraphNodeParams sp = {};
+  sp.type = cudaGraphNodeTypeConditional;
+  sp.conditional.handle = hs;
+  sp.conditional.type = cudaGraphCondTypeSwitch;
+  sp.conditional.size = (unsigned)ncases;
+  cudaGraphNode_t sn = nullptr;
+  CH_CUDA(cudaGraphAddNode(&sn, body, nullptr, nullptr, 0, &sp));
+  ProfTally* outer = prof_capture_swap(nullptr);
+  ch_status r = CH_OK;
+  for (int j = 0; j < ncases && r == CH_OK; ++j) {
+    S->tally_case[j] = ProfTally();
+    prof_capture_swap(&S->tally_case[j]);
+    r = capture_into(S, sp.conditional.phGraph_out[j], nullptr, 0,
+                     [&](cudaStream_t bs) { return mr ? mr_case(S, j, bs) : loop_case(S, j, bs); });
+  }
+  if (r == CH_OK) {
+    S->tally_ctl = ProfTally();
+    prof_capture_swap(&S->tally_ctl);
+    r = capture_into(S, body, &sn, 1, [&](cudaStream_t bs) -> ch_status {
+      ProfScope ps(bs, K_FLAGS, 0, 0.0, 0.0);
+      ctl(bs, 0, hw, hs);
+      CH_LAUNCHED();
+      return CH_OK;
+    });
+  }
+  prof_capture_swap(outer);
+  CH_TRY(r);
+  CH_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return CH_OK;
+}
+
+// Build the graph of a whole plain step (whole = true: right-hand sides, solve, masses, run
+// statistics, and the copies of the statistics and the loop record to pinned host memory) or of
+// the solve alone (the loop record copied out).
+static ch_status build_loop_graph(ch_state_s* S, bool whole, cudaGraph_t* gout, cudaGraphExec_t* xout,
+                                  ProfTally* tally) {
+  cudaGraph_t G = nullptr;
+  CH_CUDA(cudaGraphCreate(&G, 0));
+  cudaStream_t cs = S->cap_stream;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(G);
+    CH_CUDA(e);
+  }
+  *tally = ProfTally();
+  ProfTally* prev = prof_capture_swap(tally);
+  ch_status r = CH_OK;
+  if (whole) {
+    r = rhs_strided(S->sys, S->x, S->x + 1, 4, S->b, cs);
+    if (r == CH_OK) {
+      k_clear_warm<<<blocks_for(S->R, 64), 64, 0, cs>>>(S->R, S->kd);
+      if (cudaGetLastError() != cudaSuccess) r = CH_ERR_CUDA;
+    }
+  }
+  if (r == CH_OK) r = capture_solve(S, cs);
+  if (r == CH_OK && whole) {
+    {
+      ProfScope ps(cs, K_MASS, 0, 40.0 * S->N, 2.0 * S->N);
+      k_mass<<<S->nblocks, TPB, 0, cs>>>(S->seg, S->mlump, reinterpret_cast<const double4_32a*>(S->x),
+                                          S->partials, S->kd);
+    }
+    k_run_stats<<<blocks_for(S->R, 64), 64, 0, cs>>>(S->R, S->kd, S->dstats);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(S->hstats_pin, S->dstats, sizeof(RunStats) * S->R, cudaMemcpyDeviceToHost, cs) !=
+            cudaSuccess)
+      r = CH_ERR_CUDA;
+  }
+  if (r == CH_OK && cudaMemcpyAsync(S->hctl, S->dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+    r = CH_ERR_CUDA;
+  prof_capture_swap(prev);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cs, &captured);
+  if (r == CH_ERR_CUDA) set_error("capturing the device-side FGMRES loop failed: %s", cudaGetErrorString(cudaGetLastError()));
+  if (r == CH_OK && e != cudaSuccess) {
+    set_error("capturing the device-side FGMRES loop failed: %s", cudaGetErrorString(e));
+    r = CH_ERR_CUDA;
+  }
+  if (r == CH_OK) {
+    e = cudaGraphInstantiate(xout, G, 0);
+    if (e != cudaSuccess) {
+      set_error("instantiating the device-side FGMRES loop failed: %s", cudaGetErrorString(e));
+      *xout = nullptr;
+      r = CH_ERR_CUDA;
+    }
+  }
+  if (r != CH_OK) {
+    cudaGetLastError();
+    cudaGraphDestroy(G);
+    return r;
+  }
+  *gout = G;  // kept until the state goes (a graph with conditional nodes has one instantiation)
+  return CH_OK;
+}
+
+// After the loop's graph has completed (stream synchronised): launch accounting of the passes
+// taken and the solve's status from the loop record.
+static ch_status finish_loop(ch_state_s* S, const ProfTally& pro, int* restarts) {
+  const Ctl& c = *S->hctl;
+  prof_add(pro);
+  const bool mr = is_minres(S);
+  for (int j = 0; j < (mr ? 4 : S->m + 1); ++j) prof_add_times(S->tally_case[j], c.count[j]);
+  prof_add_times(S->tally_ctl, c.passes);
+  prof_add_slot(K_UPDATE_X, 0, 0, 32.0 * S->N * c.sum_j, 4.0 * S->N * c.sum_j);
+  *restarts = c.restarts;
+  switch (c.status) {
+    case CH_OK:
+      return CH_OK;
+    case CH_ERR_NONFINITE:
+      set_error(c.where == 0   ? "non-finite right-hand side or initial residual"
+                : c.where == 1 ? (mr ? "non-finite value in the MINRES recurrence"
+                                     : "non-finite value in the Arnoldi process")
+                               : "non-finite residual");
+      return CH_ERR_NONFINITE;
+    case CH_ERR_NOT_CONVERGED:
+      set_error("%s reached max_iter = %d with %d of %d systems unconverged", mr ? "MINRES" : "FGMRES",
+                S->sys->p.max_iter, c.active, 2 * S->R);
+      return CH_ERR_NOT_CONVERGED;
+    default:
+      set_error("the device-side Krylov loop stopped at its pass limit (%d passes)", c.passes);
+      return CH_ERR_INTERNAL;
+  }
+}
+
 
 __global__ void k_set_state(int N, const double* pp, const double* pn, const double* mp,
                             const double* mn, double4_32a* x) {

@@ -9,9 +9,13 @@
 // (x fixed).  It can only cross horizontal faces: the boundaries between vertically adjacent
 // pixels of different value, and the top edge of the box above a set top-row pixel.
 //
-// One thread per grid point walks its ray through the image column that contains it, counting
-// those faces; a warp's points lie in consecutive columns, so every step of the walk is one
-// coalesced row segment read.  No scratch memory.
+// A point in pixel row j0 of column i crosses the faces c_j (j >= j0) of its column, c_j = 1 where
+// rows j and j + 1 differ (c_ny = 1 where the top row is set).  Every point of a pixel sees the same
+// count, so it is formed once per pixel: a block takes 8 image columns, splits the rows into 32
+// segments, and forms the parity of sum_{j >= j0} c_j for every pixel by a suffix XOR (within each
+// segment while walking down it, then across the segments), held as bytes in shared memory; the
+// block then writes every grid point whose pixel lies in its columns.  Images too tall for shared
+// memory use one thread per grid point walking its ray instead (the same count).
 #include <cmath>
 
 #include "ch_internal.cuh"
@@ -55,13 +59,82 @@ __global__ void k_ray_parity(const double* __restrict__ pp, const double* __rest
   if (mu_h) mu_h[t] = inside ? MU_HIGH : MU_LOW;
 }
 
+constexpr int MP_COLS = 8, MP_SEGS = 32;        // block: image columns x row segments
+constexpr int MP_MAX_SMEM = 160 * 1024;          // parity bytes per block: MP_COLS x (ny + 1)
+
+__device__ __forceinline__ int pixel_of(int k, int g, double L, int n) {  // pixel index of grid index k
+  const double x = (k + 0.5) * (L / g), h = L / n;
+  int i = (int)floor(x / h + 0.5);
+  return i < 0 ? 0 : (i > n ? n : i);
+}
+
+__global__ void __launch_bounds__(MP_COLS * MP_SEGS) k_ray_parity_scan(
+    const double* __restrict__ pp, const double* __restrict__ pn, int nx, int ny, double Lx, double Ly,
+    int use_thr, double thr, int gx, int gy, uint8_t* __restrict__ polymer, double* __restrict__ mu_e,
+    double* __restrict__ mu_h) {
+  extern __shared__ uint8_t par[];  // [MP_COLS][ny + 1]
+  __shared__ uint8_t seg_par[MP_SEGS][MP_COLS];
+  const int c = threadIdx.x % MP_COLS, sgi = threadIdx.x / MP_COLS;
+  const int i0 = blockIdx.x * MP_COLS, i = i0 + c;
+  const int rows = ny + 1, W = nx + 1;
+  const int seg = (rows + MP_SEGS - 1) / MP_SEGS;
+  const int ja = sgi * seg, jb = min(rows, ja + seg);
+  uint8_t* col = par + c * rows;
+  // 1. within the segment, walking down: loc(j) = c_j ^ loc(j + 1), c_j = img_j ^ img_{j+1}
+  uint8_t acc = 0;
+  if (i <= nx && ja < jb) {
+    bool up = jb < rows ? set_at(pp, pn, use_thr, thr, (int64_t)jb * W + i) : false;  // above the box: unset
+    for (int j = jb - 1; j >= ja; --j) {
+      const bool here = set_at(pp, pn, use_thr, thr, (int64_t)j * W + i);
+      acc ^= (uint8_t)(here != up);
+      col[j] = acc;
+      up = here;
+    }
+  }
+  seg_par[sgi][c] = acc;
+  __syncthreads();
+  // 2. across the segments: every row of segment s also crosses the faces of the segments above
+  uint8_t carry = 0;
+  for (int t = sgi + 1; t < MP_SEGS; ++t) carry ^= seg_par[t][c];
+  if (i <= nx && carry)
+    for (int j = ja; j < jb; ++j) col[j] ^= 1;
+  __syncthreads();
+  // 3. the grid points whose pixel column is in [i0, i0 + MP_COLS): grid columns [k0, k1)
+  const int ilast = min(nx, i0 + MP_COLS - 1);
+  int k0 = (int)floor(((i0 - 0.5) * (Lx / nx)) / (Lx / gx) - 0.5);
+  int k1 = (int)ceil(((ilast + 0.5) * (Lx / nx)) / (Lx / gx) + 0.5);
+  k0 = max(0, k0 - 1);
+  k1 = min(gx, k1 + 1);
+  while (k0 < k1 && pixel_of(k0, gx, Lx, nx) < i0) ++k0;   // exact bounds by the same formula
+  while (k1 > k0 && pixel_of(k1 - 1, gx, Lx, nx) > ilast) --k1;
+  const int nk = k1 - k0;
+  if (nk <= 0) return;
+  for (int64_t t = threadIdx.x; t < (int64_t)nk * gy; t += blockDim.x) {
+    const int l = (int)(t / nk), k = k0 + (int)(t % nk);
+    const int ip = pixel_of(k, gx, Lx, nx), jp = pixel_of(l, gy, Ly, ny);
+    const bool inside = par[(ip - i0) * rows + jp] & 1;
+    const int64_t o = (int64_t)l * gx + k;
+    if (polymer) polymer[o] = inside;
+    if (mu_e) mu_e[o] = inside ? MU_LOW : MU_HIGH;
+    if (mu_h) mu_h[o] = inside ? MU_HIGH : MU_LOW;
+  }
+}
+
 ch_status morphology_project(const double* pp, const double* pn, int nx, int ny, double Lx, double Ly,
                              int use_thr, double thr, int gx, int gy, uint8_t* polymer, double* mu_e,
                              double* mu_h, cudaStream_t st) {
   const int64_t G = (int64_t)gx * gy;
+  const size_t smem = (size_t)MP_COLS * (ny + 1);
   ProfScope ps(st, K_MORPH, 0, (double)G * (1.0 + 16.0) + 16.0 * (double)(nx + 1) * (ny + 1), 0.0);
-  k_ray_parity<<<(unsigned)((G + TPB - 1) / TPB), TPB, 0, st>>>(pp, pn, nx, ny, Lx, Ly, use_thr, thr, gx, gy,
+  if (smem <= (size_t)MP_MAX_SMEM) {
+    CH_CUDA(cudaFuncSetAttribute(k_ray_parity_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_MAX_SMEM));
+    const int blocks = (nx + 1 + MP_COLS - 1) / MP_COLS;
+    k_ray_parity_scan<<<blocks, MP_COLS * MP_SEGS, smem, st>>>(pp, pn, nx, ny, Lx, Ly, use_thr, thr, gx, gy,
                                                                  polymer, mu_e, mu_h);
+  } else {
+    k_ray_parity<<<(unsigned)((G + TPB - 1) / TPB), TPB, 0, st>>>(pp, pn, nx, ny, Lx, Ly, use_thr, thr, gx, gy,
+                                                                   polymer, mu_e, mu_h);
+  }
   CH_LAUNCHED();
   return CH_OK;
 }

@@ -100,18 +100,6 @@ bool prof_timing() {
   return g.timing;
 }
 
-void prof_capture_begin() {
-  static thread_local ProfTally tally;
-  tally = ProfTally();
-  t_capture = &tally;
-}
-
-ProfTally prof_capture_end() {
-  ProfTally out = t_capture ? *t_capture : ProfTally();
-  t_capture = nullptr;
-  return out;
-}
-
 ProfTally* prof_capture_swap(ProfTally* t) {
   ProfTally* prev = t_capture;
   t_capture = t;

@@ -2,9 +2,12 @@
 
     python -m paper_2204_03575_gb300.profile_case --nx 1024 --ny 1024 --steps 1 --restart 10
     python -m paper_2204_03575_gb300.profile_case --batch 64 --precision 1 --restart 30 --warmup 0 --steps 2
+    python -m paper_2204_03575_gb300.profile_case --nx 128 --ny 128 --nz 32 --potential 3 --steps 1
+    python -m paper_2204_03575_gb300.profile_case --nx 512 --ny 512 --steps 1 --project 1024
 
 Builds the mesh, system, preconditioner and state on cuda:0 (seeded initial state, paper
-parameters), runs the warm-up and timed steps and prints per-step statistics.  Used as the
+parameters), runs the warm-up and timed steps and prints per-step statistics; with --project G,
+then projects the final 2D morphology onto a G x G grid (Section 5).  Used as the
 target of ncu captures, where the full benchmark would hold too much device memory.
 """
 import argparse
@@ -24,19 +27,26 @@ def main():
     ap.add_argument("--restart", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--potential", type=int, default=0)
+    ap.add_argument("--graphs", type=int, default=1,
+                    help="0: host-driven Krylov loop with direct launches (ncu profiles no kernel inside a "
+                         "graph that holds conditional nodes)")
+    ap.add_argument("--precond-m", type=int, default=0)
+    ap.add_argument("--project", type=int, default=0, help="grid size of a final morphology projection")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of one mesh: this many runs of inputs.batch_runs(n, seed=0)")
     a = ap.parse_args()
     import torch
     from paper_2204_03575_gb300 import ch
     torch.cuda.set_device(0)
-    kw = dict(nx=a.nx, ny=a.ny, precision=a.precision, restart=a.restart)
+    kw = dict(nx=a.nx, ny=a.ny, precision=a.precision, restart=a.restart, potential=a.potential,
+              precond_M=a.precond_m, graphs=a.graphs)
     if a.nz:
         kw.update(dim=3, nz=a.nz, Lz=a.nz / a.nx)
     if a.batch:
         from paper_2204_03575_gb300 import inputs
         spec = inputs.batch_runs(a.batch, seed=0)
-        p = ch.Params(precision=a.precision, restart=a.restart)
+        p = ch.Params(precision=a.precision, restart=a.restart, graphs=a.graphs)
         mesh = ch.Mesh(p, runs=[ch.Params(nx=nx, ny=ny) for nx, ny, _, _ in spec])
         system = ch.System(mesh, p)
         pc = ch.Precond(system)
@@ -52,6 +62,11 @@ def main():
         state.step()
     for k in range(a.steps):
         print(json.dumps({"step": k, **state.step()}), flush=True)
+    if a.project and not a.batch and not a.nz:
+        g = state.get()
+        polymer, _, _ = ch.morphology_project(g["phi_p"], g["phi_nfa"], a.nx, a.ny, 1.0, 1.0, a.project, a.project)
+        torch.cuda.synchronize()
+        print(json.dumps({"project": a.project, "polymer_fraction": float(polymer.float().mean())}), flush=True)
 
 
 if __name__ == "__main__":

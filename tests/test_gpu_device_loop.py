@@ -52,6 +52,19 @@ def _steps(lib, nsteps, batch, **kw):
 def test_device_loop_equals_host_loop(lib, batch, precision, restart):
     dev, pdev = _steps(lib, 3, batch, graphs=1, precision=precision, restart=restart)
     host, phost = _steps(lib, 3, batch, graphs=0, precision=precision, restart=restart)
+    _compare(dev, pdev, host, phost, restart)
+
+
+@pytest.mark.parametrize("batch", [False, True])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_device_loop_equals_host_loop_minres(lib, batch, precision):
+    """krylov = 1: MINRES's loop (start, iterations, true-residual checks, retargeting) on the device."""
+    dev, pdev = _steps(lib, 3, batch, graphs=1, precision=precision, krylov=1)
+    host, phost = _steps(lib, 3, batch, graphs=0, precision=precision, krylov=1)
+    _compare(dev, pdev, host, phost, None)
+
+
+def _compare(dev, pdev, host, phost, restart):
     for (sa, ra, ga), (sb, rb, gb) in zip(dev, host):
         assert sa["status"] == sb["status"] == 0
         for key in ("iters", "restarts", "relres", "mass"):
@@ -91,17 +104,19 @@ def test_device_loop_guess_step_equals_host_loop(lib):
             np.testing.assert_array_equal(ga[k], gb[k])
 
 
+@pytest.mark.parametrize("krylov", [0, 1])
 @pytest.mark.parametrize("graphs", [1, 0])
-def test_device_loop_statuses(lib, graphs):
+def test_device_loop_statuses(lib, graphs, krylov):
     """Iteration cap and a non-finite state give the same statuses as the host loop, and the state
     stays usable (the next step after a fresh initialisation converges)."""
-    p = lib.Params(nx=32, ny=32, max_iter=3, restart=2, graphs=graphs)
+    p = lib.Params(nx=32, ny=32, max_iter=3, restart=2 if krylov == 0 else 8, graphs=graphs, krylov=krylov)
     system = lib.System(lib.Mesh(p), p)
     state = lib.State(system, lib.Precond(system))
     state.init_seeded(0.33, 0.33, 0.01, seed=0)
     st = state.step(check=False)
     assert st["status"] == lib.ERR_NOT_CONVERGED
-    assert st["iters"] == [3, 3] and st["restarts"] == 2
+    if krylov == 0:
+        assert st["iters"] == [3, 3] and st["restarts"] == 2
     assert all(np.isfinite(v.cpu().numpy()).all() for v in state.get().values())
     n = system.n
     bad = torch.full((n,), 0.33, dtype=torch.float64, device="cuda")
@@ -109,7 +124,7 @@ def test_device_loop_statuses(lib, graphs):
     state.set(bad, bad.clone())
     st = state.step(check=False)
     assert st["status"] == lib.ERR_NONFINITE
-    p2 = lib.Params(nx=32, ny=32, graphs=graphs)
+    p2 = lib.Params(nx=32, ny=32, graphs=graphs, krylov=krylov)
     system2 = lib.System(lib.Mesh(p2), p2)
     state2 = lib.State(system2, lib.Precond(system2))
     state2.init_seeded(0.33, 0.33, 0.01, seed=0)

@@ -58,6 +58,15 @@ def test_smallest_sizes_and_uniform_images(lib):
     _run(lib, np.zeros(N), np.ones(N), 10, 5, 3.0, 1.0, 17, 9)      # none
 
 
+def test_tall_image_uses_the_walk_and_agrees(lib):
+    """An image too tall for the per-pixel parity in shared memory (more than 20480 rows) is
+    classified by walking each point's ray; both forms count the same faces."""
+    nx, ny = 2, 24000
+    rng = np.random.default_rng(9)
+    N = (nx + 1) * (ny + 1)
+    _run(lib, rng.random(N), rng.random(N), nx, ny, 1.0, 100.0, 5, 301)
+
+
 def test_projection_of_a_solver_morphology(lib):
     """The projection of a state the solver produced (64 x 48 box, 20 steps)."""
     p = lib.Params(nx=64, ny=48, Lx=4.0, Ly=3.0)
