@@ -1,6 +1,8 @@
 """Pins of the warm-start network oracle: its convolution against scipy's 2D correlation, its
-gradients against central finite differences of its own float64 loss, and its bfloat16 rounding
-against exactly representable values and the round-to-nearest-even rule."""
+gradients against central finite differences of its own float64 losses, its prediction against
+linear and quadratic extrapolation in the limiting cases and against the pace of the dynamics,
+and its bfloat16 rounding against exactly representable values and the round-to-nearest-even
+rule."""
 import numpy as np
 import pytest
 import scipy.signal
@@ -33,12 +35,22 @@ def test_conv_backward_is_the_adjoint():
     assert abs(lhs - (w * wo.conv_back_weight(x, z)).sum()) < 1e-10 * abs(lhs)
 
 
+def _history(rng, B, H, W):
+    """B samples of three consecutive smooth-ish states and the next one."""
+    s = rng.standard_normal((B, H, W, 4))
+    q = s - 0.1 * rng.standard_normal((B, H, W, 4))
+    q2 = q - 0.1 * rng.standard_normal((B, H, W, 4))
+    n = s + (s - q) + 0.05 * rng.standard_normal((B, H, W, 4))
+    return s, q, q2, n
+
+
 @pytest.mark.parametrize("lap", [0.0, 0.7])
 def test_gradient_matches_finite_differences(lap):
     rng = np.random.default_rng(2)
     theta = rand_theta(rng)
-    xs, ts = rng.standard_normal((2, 5, 6, wo.NIN)), rng.standard_normal((2, 5, 6, wo.NOUT))
-    _, g = wo.loss_and_grads(theta, xs, ts, lap=lap)
+    S, Q, Q2, Nn = _history(rng, 2, 5, 6)
+    norm = (rng.standard_normal(8) * 0.1, rng.uniform(0.5, 2.0, 8), np.array([0.7, 1.2, 0.5, 0.9]))
+    _, g = wo.loss_and_grads(theta, S, Q, Q2, Nn, norm, lap=lap)
     # parameters that exist in the network (the rest pad the library's layout and get zero)
     mask = np.ones(wo.NPARAM, bool)
     mask[:9 * 16 * 32] = np.tile(np.r_[np.ones(wo.NIN * 32), np.zeros((16 - wo.NIN) * 32)], 9).astype(bool)
@@ -53,9 +65,26 @@ def test_gradient_matches_finite_differences(lap):
         tp, tm = theta.copy(), theta.copy()
         tp[i] += h
         tm[i] -= h
-        fd = (wo.loss_and_grads(tp, xs, ts, lap=lap)[0] - wo.loss_and_grads(tm, xs, ts, lap=lap)[0]) / (2 * h)
+        fd = (wo.loss_and_grads(tp, S, Q, Q2, Nn, norm, lap=lap)[0]
+              - wo.loss_and_grads(tm, S, Q, Q2, Nn, norm, lap=lap)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
     assert np.all(g[~mask] == 0)
+
+
+def test_loss_vanishes_when_the_prediction_hits_the_next_state():
+    """A bias-only network predicts s + d + b3 * out_scale * D everywhere; with that as the next
+    state the state-space loss and its gradient vanish, and it grows quadratically away from it."""
+    rng = np.random.default_rng(12)
+    S, Q, Q2, _ = _history(rng, 2, 4, 5)
+    theta = np.zeros(wo.NPARAM)
+    theta[-8:-4] = [0.5, -1.0, 2.0, 0.25]
+    out = np.array([1.0, 0.5, 2.0, 3.0])
+    Nn = np.stack([s + (s - q) + theta[-8:-4] * out * wo.second_difference(s, q, q2) for s, q, q2 in zip(S, Q, Q2)])
+    L, g = wo.loss_and_grads(theta, S, Q, Q2, Nn, (None, None, out))
+    assert L < 1e-28 and np.abs(g).max() < 1e-12
+    L1, _ = wo.loss_and_grads(theta, S, Q, Q2, Nn + 1e-3, (None, None, out))
+    L2, _ = wo.loss_and_grads(theta, S, Q, Q2, Nn + 2e-3, (None, None, out))
+    assert abs(L2 / L1 - 4.0) < 1e-6
 
 
 def test_grid_laplacian():
@@ -89,49 +118,59 @@ def test_grid_laplacian():
 
 
 def test_zero_network_predicts_linear_extrapolation():
-    """With all weights and biases zero the correction vanishes: pred = 2 s_k - s_{k-1}; with only
-    the output bias set, every pixel moves by bias * out_scale * r."""
+    """With all weights and biases zero theta vanishes: pred = 2 s_k - s_{k-1}; with only the output
+    bias set, every pixel moves by bias * out_scale * D."""
     rng = np.random.default_rng(4)
-    s, q = rng.standard_normal((5, 7, 4)), rng.standard_normal((5, 7, 4))
+    s, q, q2 = (rng.standard_normal((5, 7, 4)) for _ in range(3))
     p = wo.unpack(np.zeros(wo.NPARAM))
-    np.testing.assert_allclose(wo.predict(p, s, q), 2 * s - q, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(wo.predict(p, s, q, q2), 2 * s - q, rtol=0, atol=1e-15)
     p["b3"] = np.array([1.0, -2.0, 0.5, 0.0])
     scale = np.array([1e-3, 2e-3, 3e-3, 4e-3])
-    r = np.sqrt(((s - q) ** 2).reshape(-1, 4).mean(0))
-    np.testing.assert_allclose(wo.predict(p, s, q, (None, None, scale)), 2 * s - q + p["b3"] * scale * r,
-                               rtol=1e-7, atol=1e-15)
+    np.testing.assert_allclose(wo.predict(p, s, q, q2, (None, None, scale)),
+                               2 * s - q + p["b3"] * scale * (s - 2 * q + q2), rtol=1e-12, atol=1e-15)
 
 
-def test_inputs_normalise_fields_and_change():
+def test_theta_one_is_quadratic_extrapolation():
+    """theta = 1 everywhere (zero weights, output bias 1, out_scale 1) is the quadratic
+    extrapolation 3 s_k - 3 s_{k-1} + s_{k-2}, exact for states on a quadratic in time."""
+    rng = np.random.default_rng(13)
+    a, b, c = (rng.standard_normal((4, 6, 4)) for _ in range(3))
+    state = lambda t: a + b * t + c * t * t
+    p = wo.unpack(np.zeros(wo.NPARAM))
+    p["b3"] = np.ones(4)
+    pred = wo.predict(p, state(2.0), state(1.0), state(0.0))
+    np.testing.assert_allclose(pred, 3 * state(2.0) - 3 * state(1.0) + state(0.0), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(pred, state(3.0), rtol=1e-10, atol=1e-10)
+
+
+def test_inputs_normalise_fields_change_and_second_difference():
     rng = np.random.default_rng(5)
-    s, q = rng.standard_normal((3, 4, 4)), rng.standard_normal((3, 4, 4))
+    s, q, q2 = (rng.standard_normal((3, 4, 4)) for _ in range(3))
     mean, inv = rng.standard_normal(8), rng.uniform(0.5, 2, 8)
-    x = wo.inputs(s, q, mean, inv)
+    x = wo.inputs(s, q, q2, mean, inv)
+    assert x.shape == (3, 4, wo.NIN)
     np.testing.assert_allclose(x[..., :4], (s - mean[:4]) * inv[:4], rtol=1e-6, atol=1e-6)
-    unit = wo.inputs(s, q)[..., 4:]  # the change in units of its RMS has unit RMS per channel
-    np.testing.assert_allclose(np.sqrt((unit.reshape(-1, 4) ** 2).mean(0)), 1.0, rtol=1e-6)
-    np.testing.assert_allclose(x[..., 4:], (unit - mean[4:]) * inv[4:], rtol=1e-5, atol=1e-5)
+    unit = wo.inputs(s, q, q2)
+    # the change and the second difference in units of their RMS have unit RMS per channel
+    np.testing.assert_allclose(np.sqrt((unit[..., 4:8].reshape(-1, 4) ** 2).mean(0)), 1.0, rtol=1e-6)
+    np.testing.assert_allclose(np.sqrt((unit[..., 8:12].reshape(-1, 4) ** 2).mean(0)), 1.0, rtol=1e-6)
+    np.testing.assert_allclose(x[..., 4:8], (unit[..., 4:8] - mean[4:]) * inv[4:], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(x[..., 8:12], unit[..., 8:12], rtol=0, atol=0)
+    D = s - 2 * q + q2
+    np.testing.assert_allclose(unit[..., 8:12], D / np.sqrt((D.reshape(-1, 4) ** 2).mean(0)), rtol=1e-6)
 
 
 @pytest.mark.parametrize("lam", [1e-4, 0.5, 3.0])
 def test_prediction_is_equivariant_to_the_pace(lam):
-    """Scaling the last change by lam leaves the network input unchanged and scales the predicted
-    change (pred - s) by lam: the map does not depend on how fast the state moves."""
+    """Scaling the history's changes by lam leaves the network input unchanged and scales the
+    predicted change (pred - s) by lam: the map does not depend on how fast the state moves."""
     rng = np.random.default_rng(6)
     p = wo.unpack(rand_theta(rng))
-    s, d = rng.standard_normal((6, 5, 4)), rng.standard_normal((6, 5, 4)) * 1e-2
-    base = wo.predict(p, s, s - d, (None, None, np.full(4, 0.1))) - s
-    scaled = wo.predict(p, s, s - lam * d, (None, None, np.full(4, 0.1))) - s
+    s, d1, d2 = rng.standard_normal((6, 5, 4)), rng.standard_normal((6, 5, 4)) * 1e-2, rng.standard_normal((6, 5, 4)) * 1e-2
+    norm = (None, None, np.full(4, 0.1))
+    base = wo.predict(p, s, s - d1, s - d1 - d2, norm) - s
+    scaled = wo.predict(p, s, s - lam * d1, s - lam * (d1 + d2), norm) - s
     np.testing.assert_allclose(scaled, lam * base, rtol=1e-4, atol=1e-12 * lam)
-
-
-def test_targets_recover_a_known_correction():
-    rng = np.random.default_rng(8)
-    s, d, y = rng.standard_normal((4, 6, 4)), rng.standard_normal((4, 6, 4)), rng.standard_normal((4, 6, 4))
-    out = np.array([0.5, 1.0, 2.0, 0.25])
-    r = np.sqrt((d.reshape(-1, 4) ** 2).mean(0))
-    n = s + d + y * out * r
-    np.testing.assert_allclose(wo.targets(s, s - d, n, out), y, rtol=1e-5, atol=1e-5)
 
 
 def test_bf16_rounding():
@@ -166,8 +205,8 @@ def test_residual_loss_zero_network_is_one_and_symmetric_operator():
     A = _random_symmetric_operator(rng, H, W)
     a, b = rng.standard_normal((H, W, 4)), rng.standard_normal((H, W, 4))
     assert abs((A(a) * b).sum() - (a * A(b)).sum()) < 1e-10
-    s, q, rhs = (rng.standard_normal((2, H, W, 4)) for _ in range(3))
-    L, g = wo.residual_loss_and_grads(np.zeros(wo.NPARAM), s, q, rhs, A)
+    s, q, q2, rhs = (rng.standard_normal((2, H, W, 4)) for _ in range(4))
+    L, g = wo.residual_loss_and_grads(np.zeros(wo.NPARAM), s, q, q2, rhs, A)
     assert L == 1.0
 
 
@@ -181,17 +220,16 @@ def test_residual_loss_gradient_matches_finite_differences(precond):
         dscale = rng.uniform(0.5, 2.0, (H, W, 4))
         Pinv = lambda v: dscale * v - 0.1 * wo.grid_laplacian(v)
     theta = rand_theta(rng, 0.2)
-    s = rng.standard_normal((2, H, W, 4))
-    q = s - 0.1 * rng.standard_normal((2, H, W, 4))
+    s, q, q2, _ = _history(rng, 2, H, W)
     rhs = rng.standard_normal((2, H, W, 4))
     norm = (None, None, np.array([0.3, 0.5, 0.2, 0.4]))
-    L, g = wo.residual_loss_and_grads(theta, s, q, rhs, A, norm, apply_Pinv=Pinv)
+    L, g = wo.residual_loss_and_grads(theta, s, q, q2, rhs, A, norm, apply_Pinv=Pinv)
     h = 1e-6
     idx = rng.choice(np.flatnonzero(g != 0), 30, replace=False)
     for i in idx:
         tp, tm = theta.copy(), theta.copy()
         tp[i] += h
         tm[i] -= h
-        fd = (wo.residual_loss_and_grads(tp, s, q, rhs, A, norm, apply_Pinv=Pinv)[0]
-              - wo.residual_loss_and_grads(tm, s, q, rhs, A, norm, apply_Pinv=Pinv)[0]) / (2 * h)
+        fd = (wo.residual_loss_and_grads(tp, s, q, q2, rhs, A, norm, apply_Pinv=Pinv)[0]
+              - wo.residual_loss_and_grads(tm, s, q, q2, rhs, A, norm, apply_Pinv=Pinv)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
