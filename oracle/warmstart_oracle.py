@@ -20,8 +20,8 @@ image of d and D per channel (the first two groups also shifted and scaled by me
 
 Losses: in state space, L = (sum E^2 + lap * sum (G E)^2) / count with E = (theta D - e) / r1,
 e = n - 2 s + q the linear extrapolation's error (n = s_{k+1}) and G the graph Laplacian of the
-pixel grid, (G E)_p = sum over the 4-neighbours q of p inside the image of (E_q - E_p); or against
-the step's residual (residual_loss_and_grads).  Everything is float64 numpy with loops over the 9
+pixel grid, (G E)_p = sum over the 4-neighbours q of p inside the image of (E_q - E_p); or the
+mean log ratio of the step's residual to linear extrapolation's (residual_loss_and_grads).  Everything is float64 numpy with loops over the 9
 taps only; `bf16=True` rounds to bfloat16 at the points where the GPU kernels store bfloat16
 values (input, weights, hidden activations, the output gradient and the hidden gradients), so
 that the two can be compared closely.
@@ -213,9 +213,11 @@ def residual_loss_and_grads(theta: np.ndarray, states, prevs, prevs2, rhss, appl
     side b of the step from s_k; apply_A: the symmetric block operator on an H x W x 4 image
     (node = pixel).  Per sample and species (channels sp and sp + 2), r_ex = b - A (2 s - q) (linear
     extrapolation) and r = r_ex - A c with c = theta D; |r|^2 is <r, z> with z = apply_Pinv(r) (a
-    symmetric positive definite preconditioner) or z = r.  The loss is the mean of |r|^2 / |r_ex|^2
-    over samples and species, so 1 for the zero network.  dL/dc = -2 A z / (|r_ex|^2 * 2B) and
-    dL/dy = dL/dc * out_scale * D."""
+    symmetric positive definite preconditioner) or z = r.  The loss is the mean of
+    ln(|r|^2 / |r_ex|^2) over samples and species -- 0 for the zero network, negative where the
+    prediction beats linear extrapolation; Krylov iteration counts grow with the logarithm of the
+    initial residual, so every sample's relative gain counts alike.  dL/dc = -2 A z / (|r|^2 * 2B)
+    and dL/dy = dL/dc * out_scale * D."""
     Pinv = apply_Pinv if apply_Pinv is not None else (lambda v: v)
     mean, inv_std, out_scale = (None, None, np.ones(NOUT)) if norm is None else norm
     out_scale = np.asarray(out_scale, np.float64)
@@ -236,8 +238,9 @@ def residual_loss_and_grads(theta: np.ndarray, states, prevs, prevs2, rhss, appl
         for sp in (0, 1):
             ch = [sp, sp + 2]
             den = float((rex[..., ch] * zex[..., ch]).sum())
-            if den > 0:
-                L += float((res[..., ch] * z[..., ch]).sum()) / den
-                dc[..., ch] = -2.0 * gA[..., ch] / (den * 2 * B)
+            num = float((res[..., ch] * z[..., ch]).sum())
+            if den > 0 and num > 0:
+                L += np.log(num / den)
+                dc[..., ch] = -2.0 * gA[..., ch] / (num * 2 * B)
         backward(p, cache, r16(dc * out_scale * D), g, bf)
     return L / (2 * B), pack_grads(g)

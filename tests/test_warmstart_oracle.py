@@ -207,7 +207,30 @@ def test_residual_loss_zero_network_is_one_and_symmetric_operator():
     assert abs((A(a) * b).sum() - (a * A(b)).sum()) < 1e-10
     s, q, q2, rhs = (rng.standard_normal((2, H, W, 4)) for _ in range(4))
     L, g = wo.residual_loss_and_grads(np.zeros(wo.NPARAM), s, q, q2, rhs, A)
-    assert L == 1.0
+    assert L == 0.0
+
+
+def test_residual_loss_is_the_mean_log_ratio():
+    """A bias-only network (theta constant per channel) has the loss mean_sp ln(|r|^2 / |r_ex|^2),
+    recomputed here from the residuals directly; theta that reproduces the next step's solution
+    makes the ratio small."""
+    rng = np.random.default_rng(14)
+    H, W = 4, 5
+    A = _random_symmetric_operator(rng, H, W)
+    s, q, q2, _ = _history(rng, 1, H, W)
+    th = np.array([0.7, 0.7, 0.7, 0.7])
+    sol = 2 * s[0] - q[0] + th * (s[0] - 2 * q[0] + q2[0])
+    rhs = A(sol)[None]
+    theta = np.zeros(wo.NPARAM)
+    theta[-8:-4] = 0.3
+    L, _ = wo.residual_loss_and_grads(theta, s, q, q2, rhs, A)
+    rex = rhs[0] - A(2 * s[0] - q[0])
+    res = rex - A(0.3 * (s[0] - 2 * q[0] + q2[0]))
+    want = np.mean([np.log((res[..., [sp, sp + 2]] ** 2).sum() / (rex[..., [sp, sp + 2]] ** 2).sum()) for sp in (0, 1)])
+    assert abs(L - want) < 1e-12
+    theta[-8:-4] = 0.7
+    L_exact, _ = wo.residual_loss_and_grads(theta, s, q, q2, rhs, A)
+    assert L_exact < -20
 
 
 @pytest.mark.parametrize("precond", [False, True])
