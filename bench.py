@@ -451,10 +451,12 @@ def morphology_section(torch, ch, state_fields, nx, reps=20):
 
 
 def learned_section(torch, ch, nx, K, flush, ranks):
-    """The learned warm start on an nx x nx grid: 2000 (s_{k-1}, s_k, s_{k+1}) triples from the
-    plain FP64 solver (20 seeded runs x 100 steps), residual-loss training by the library's
-    kernels, then K timed steps of a held-out run per form: previous-state guess, the network,
-    and linear extrapolation (the zero network), in FP64 and mixed precision."""
+    """The learned warm start on an nx x nx grid: 2000 (s_{k-2}, s_{k-1}, s_k, s_{k+1}) quadruples
+    from the plain FP64 solver (20 seeded runs x 100 steps), residual-loss training by the library's
+    kernels, then K timed steps of a held-out run per form: previous-state guess, the network (a
+    learned second-order extrapolation), linear extrapolation (the zero network) and quadratic
+    extrapolation (theta = 1), in FP64 and mixed precision; plus the network's share of a learned
+    step and its convolutions' tensor throughput."""
     import time
     import numpy as np
     from paper_2204_03575_gb300 import warmstart as ws
@@ -469,22 +471,24 @@ def learned_section(torch, ch, nx, K, flush, ranks):
     torch.cuda.synchronize()
     t_train = time.time() - t0
     del data
-    zero = ws.zero_net(nx, nx)
+    zero, quad = ws.zero_net(nx, nx), ws.quadratic_net(nx, nx)
     out = {"workload": f"2D {nx}x{nx} P1 triangles ({(nx + 1) ** 2} nodes), held-out seed 1000, bases from "
-                       f"SplitMix64 in [0.20, 0.45), noise +/-0.01; timed steps 3..{K + 2} of the run",
+                       f"SplitMix64 in [0.20, 0.45), noise +/-0.01; timed steps 4..{K + 3} of the run",
            "pairs": info["pairs"], "generate_s": round(t_gen, 2), "train_s": round(t_train, 2),
            "train_loss_first_last_epoch": [info["loss_per_epoch"][0], info["loss_per_epoch"][-1]],
-           "loss_meaning": "mean |r|^2 / |r_extrapolation|^2 of the step residual"}
+           "loss_meaning": "mean |r|^2 / |r_linear extrapolation|^2 of the step residual",
+           "out_scale_theta_star": info["out_scale"]}
+    forms = (("previous_state", None), ("learned", net), ("linear_extrapolation", zero),
+             ("quadratic_extrapolation", quad))
     for prec, tag in ((0, "fp64"), (1, "mixed")):
         res = {}
-        # one solver per precision: the three forms share its hierarchy and autotuned launch shapes,
-        # so they differ only in the initial guess (a preconditioner per form would tune anew);
-        # re-seeding restarts the run and the learned step's history
+        # one solver per precision: the forms share its hierarchy and autotuned launch shapes, so
+        # they differ only in the initial guess; re-seeding restarts the run and the learned history
         state = ws.make_state(nx, nx, prec)
-        for form, n in (("previous_state", None), ("learned", net), ("extrapolation", zero)):
+        for form, n in forms:
             b0, b1 = ws.seed_bases(1000)
             state.init_seeded(b0, b1, 0.01, seed=1000)
-            for _ in range(2):  # ch_step_learned starts from the previous state for two steps
+            for _ in range(3):  # ch_step_learned starts from the previous state for three steps
                 if n is None:
                     state.step()
                 else:
@@ -492,6 +496,25 @@ def learned_section(torch, ch, nx, K, flush, ranks):
             ms, iters = timed_steps(torch, ch, state, K, flush, ranks, net=n)
             res[form] = {"steps_per_s": ranks.rate(K, ms), "ms_per_step": ms / K,
                          "iters_per_step_mean": float(np.mean(iters))}
+        if prec == 0:  # the network's share of a learned step (per-launch event timing)
+            b0, b1 = ws.seed_bases(1000)
+            state.init_seeded(b0, b1, 0.01, seed=1000)
+            for _ in range(3):
+                state.step_learned(net)
+            ch.profile_enable(True)
+            ch.profile_read(reset=True)
+            for _ in range(5):
+                flush.zero_()
+                state.step_learned(net)
+            torch.cuda.synchronize()
+            prof = ch.profile_read(reset=True)
+            ch.profile_enable(False)
+            tot = sum(v["ms"] for v in prof.values()) or 1.0
+            conv = prof.get("ws_conv_f32", {"ms": 0.0, "fmas": 0.0, "launches": 0})
+            io = prof.get("ws_io_f64", {"ms": 0.0})
+            out["network_share_of_learned_step"] = (conv["ms"] + io["ms"]) / tot
+            out["conv_tflops"] = (2 * conv["fmas"] / (conv["ms"] * 1e-3) / 1e12) if conv["ms"] > 0 else None
+            out["conv_ms_per_prediction"] = conv["ms"] / 5
         out[tag] = res
     out["mixed_learned_over_fp64_previous_state"] = (out["mixed"]["learned"]["steps_per_s"]
                                                      / out["fp64"]["previous_state"]["steps_per_s"])

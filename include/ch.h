@@ -298,14 +298,17 @@ void ch_state_destroy(ch_state_t* st);
 
 /* ---------------------------------------------------------------- learned warm start
  * A 3-layer convolutional network on the nodal image of a 2D structured mesh (H = ny+1 rows,
- * W = nx+1 columns, node i + W j = pixel (j, i)) that predicts the next step's state, used as the
- * guess of ch_step_guess.  The paper has no counterpart (this extension is one of the build's own).
- * Layers: 3x3 convolutions with zero padding, 8 -> 32 (ReLU) -> 32 (ReLU) -> 4; BF16 weights and
+ * W = nx+1 columns, node i + W j = pixel (j, i)) that predicts the next step's state from the last
+ * three, used as the guess of ch_step_guess.  The paper has no counterpart (this extension is one
+ * of the build's own).  The prediction is a learned second-order extrapolation:
+ *   pred = s + d + theta * D,  d = s - q,  D = s - 2 q + q2,  theta = y * out_scale,
+ * with s = s_k, q = s_{k-1}, q2 = s_{k-2} (phi_p, phi_nfa, mu_p, mu_nfa) and y the network's output:
+ * the zero network is linear extrapolation, theta = 1 quadratic extrapolation, and the network
+ * only scales the second difference pixel by pixel.
+ * Layers: 3x3 convolutions with zero padding, 12 -> 32 (ReLU) -> 32 (ReLU) -> 4; BF16 weights and
  * activations, FP32 accumulation on the tensor cores, FP32 master weights with Adam.
- * Input: the state s_k = (phi_p, phi_nfa, mu_p, mu_nfa) and its change d_k = s_k - s_{k-1};
- * r_k[c] = RMS over the image of channel c of d_k.  Channels (s_k - mean[0:4]) * inv_std[0:4] and
- * (d_k / r_k - mean[4:8]) * inv_std[4:8]; output y: the correction to the linear extrapolation,
- * pred = s_k + d_k + y * out_scale * r_k.
+ * Input channels, with r1[c], r2[c] the RMS over the image of channel c of d and D:
+ * (s - mean[0:4]) * inv_std[0:4], (d / r1 - mean[4:8]) * inv_std[4:8], D / r2.
  * Parameters (ch_ws_nparams() floats, host arrays), in order: w1[9][16][32] (tap = 3 ky + kx,
  * input channel padded to 16, output channel), b1[32], w2[9][32][32], b2[32], w3[9][32][8]
  * (output channel padded to 8), b3[8]; padded entries are ignored. */
@@ -318,47 +321,48 @@ ch_status ch_ws_get_params(const ch_ws_t* w, float* params, float* grads, void* 
 /* host: mean[8], inv_std[8], out_scale[4] */
 ch_status ch_ws_set_norm(ch_ws_t* w, const float* norm20, void* stream);
 /* Normalisation of a training set, computed on the device and set on the network (as
- * ch_ws_set_norm): nsamples consecutive-state triples, device arrays of nsamples x N x 4 (fp64, or
- * fp32 when fp32 = 1) -- predecessors q = s_{k-1}, states x = s_k, successors n = s_{k+1}.
- * mean[0:4] and inv_std[0:4] are the mean and 1 / standard deviation of the four fields of x over
- * the set; the change channels keep mean[4:8] = 0, inv_std[4:8] = 1 (they are already in units of
- * their per-sample RMS r); out_scale[c] is the standard deviation over the set of the
- * extrapolation's correction in those units, ((n - x) - (x - q)) / r.  Standard deviations use the
- * n - 1 divisor, floors 1e-30; sums in a fixed order (reproducible).  norm20 (host, 20 doubles)
- * receives (mean[8], inv_std[8], out_scale[4]).  Allocates and frees its own small scratch. */
-ch_status ch_ws_fit_norm(ch_ws_t* w, const void* q, const void* x, const void* n, int32_t nsamples, int32_t fp32,
-                         double* norm20, void* stream);
-/* pred (N x 4 fp64 device): the prediction of the next state from the state s and its predecessor */
-ch_status ch_ws_predict(ch_ws_t* w, const double* state, const double* prev, double* pred, void* stream);
+ * ch_ws_set_norm): the states x = s_k of nsamples samples, a device array of nsamples x N x 4
+ * (fp64, or fp32 when fp32 = 1).  mean[0:4] and inv_std[0:4] are the mean and 1 / standard
+ * deviation of the four fields over the set (n - 1 divisor, floor 1e-30); mean[4:8] = 0,
+ * inv_std[4:8] = 1 (the change is already in units of its RMS); out_scale = 1 (theta = y).  Sums in
+ * a fixed order (reproducible).  norm20 (host, 20 doubles) receives (mean[8], inv_std[8],
+ * out_scale[4]).  Allocates and frees its own small scratch. */
+ch_status ch_ws_fit_norm(ch_ws_t* w, const void* x, int32_t nsamples, int32_t fp32, double* norm20, void* stream);
+/* pred (N x 4 fp64 device): the prediction of the next state from the state and its two
+ * predecessors (N x 4 fp64 device each); pred must not alias them */
+ch_status ch_ws_predict(ch_ws_t* w, const double* state, const double* prev, const double* prev2, double* pred,
+                        void* stream);
 /* One training step on B <= max_batch samples (device fp32, B x N x 4 each): states x = s_k, their
- * predecessors q = s_{k-1} and successors n = s_{k+1}; the target of y is
- * t = ((n - x) - (x - q)) / (out_scale * r_k).  With E = y - t and G the graph Laplacian of the
- * pixel grid ((G E)_p = sum over the 4-neighbours q of p in the image of E_q - E_p), the loss is
- * (sum E^2 + lap * sum (G E)^2) / (4 B N): lap >= 0 weighs rough errors, which dominate the step's
- * residual through its stiffness rows.  Computes the gradients (ch_ws_get_params); lr > 0 also
- * takes an Adam step.  *loss (host) may be NULL.  CH_ERR_ARG: B outside [1, max_batch], lap < 0
- * or not finite. */
-ch_status ch_ws_train_step(ch_ws_t* w, const float* x, const float* q, const float* n, int32_t B,
+ * predecessors q = s_{k-1}, q2 = s_{k-2} and successors n = s_{k+1}.  With E = (theta D - e) / r1
+ * (the prediction's error in units of the change's RMS; e = n - 2 x + q) and G the graph Laplacian
+ * of the pixel grid ((G E)_p = sum over the 4-neighbours q of p in the image of E_q - E_p), the
+ * loss is (sum E^2 + lap * sum (G E)^2) / (4 B N): lap >= 0 weighs rough errors, which dominate the
+ * step's residual through its stiffness rows.  Computes the gradients (ch_ws_get_params); lr > 0
+ * also takes an Adam step.  *loss (host) may be NULL.  CH_ERR_ARG: B outside [1, max_batch],
+ * lap < 0 or not finite. */
+ch_status ch_ws_train_step(ch_ws_t* w, const float* x, const float* q, const float* q2, const float* n, int32_t B,
                            float lap, float lr, float* loss, void* stream);
 
 /* One training step against the residual of Eq. (14) (the quantity FGMRES's stopping test
  * measures), on B <= max_batch samples of consecutive states (device fp64, B x N x 4 each:
- * x = s_k, q = s_{k-1}) of the 2D single-run mesh of `sys` (N = H W).  Per sample and species,
- * with b the right-hand side of the step from s_k and c the network's correction,
- * r_ex = b - A (2 s_k - s_{k-1}) and r = r_ex - A c, measured in the norm of the preconditioner
- * `pc` (<r, P^-1 r>, Algorithm 1 built on `sys`) or, if pc is NULL, the Euclidean norm.  The loss
- * is the mean over samples and species of |r|^2 / |r_ex|^2, so a loss below 1 means the
- * prediction beats linear extrapolation.  Computes the gradients; lr > 0 also takes an Adam step.
- * *loss (host) may be NULL.  CH_ERR_ARG: B outside [1, max_batch], a system that is not a
- * single-run 2D mesh of H x W nodes, or a preconditioner of another system. */
+ * x = s_k, q = s_{k-1}, q2 = s_{k-2}) of the 2D single-run mesh of `sys` (N = H W).  Per sample and
+ * species, with b the right-hand side of the step from s_k and c = theta D the network's change of
+ * the linear extrapolation, r_ex = b - A (2 s_k - s_{k-1}) and r = r_ex - A c, measured in the norm
+ * of the preconditioner `pc` (<r, P^-1 r>, Algorithm 1 built on `sys`) or, if pc is NULL, the
+ * Euclidean norm.  The loss is the mean over samples and species of ln(|r|^2 / |r_ex|^2): 0 for
+ * linear extrapolation, negative where the prediction beats it; Krylov iteration counts grow with
+ * the logarithm of the initial residual, so each sample's relative gain counts alike.  Computes
+ * the gradients; lr > 0 also
+ * takes an Adam step.  *loss (host) may be NULL.  CH_ERR_ARG: B outside [1, max_batch], a system
+ * that is not a single-run 2D mesh of H x W nodes, or a preconditioner of another system. */
 ch_status ch_ws_train_residual(ch_ws_t* w, const ch_system_t* sys, ch_precond_t* pc, const double* x,
-                               const double* q, int32_t B, float lr, float* loss, void* stream);
+                               const double* q, const double* q2, int32_t B, float lr, float* loss, void* stream);
 
-/* One time step whose candidate guess is the network's prediction from the state and its
- * predecessor, which the state keeps on the device across consecutive ch_step_learned calls; the
- * choice between guess and previous state is that of ch_step_guess.  Until two steps have been
- * taken since the state was set (the first sets up the chemical potentials), and on the first
- * learned step after a step of another kind, the step starts from the previous state.
+/* One time step whose candidate guess is the network's prediction from the state and its two
+ * predecessors, which the state keeps on the device across consecutive ch_step_learned calls; the
+ * choice between guess and previous state is that of ch_step_guess.  Until three steps have been
+ * taken since the state was set (the first sets up the chemical potentials), and until two learned
+ * steps in a row have recorded the history, the step starts from the previous state.
  * stats->ms includes the prediction.  CH_ERR_ARG: a network sized for another mesh, or a state
  * of several runs. */
 ch_status ch_step_learned(ch_state_t* st, ch_ws_t* w, void* stream, ch_step_stats* stats);

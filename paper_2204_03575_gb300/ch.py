@@ -111,8 +111,7 @@ _SIGNATURES = {
     "ch_precond_destroy": (None, [_VP]),
     "ch_vcycle_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
     "ch_mass_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
-    "ch_ws_fit_norm": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32,
-                                      ctypes.POINTER(ctypes.c_double), _VP]),
+    "ch_ws_fit_norm": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _VP]),
     "ch_morphology_project": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                              ctypes.c_int32, _VP, _VP, _VP, _VP]),
@@ -137,10 +136,10 @@ _SIGNATURES = {
     "ch_ws_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), _VP]),
     "ch_ws_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _VP]),
     "ch_ws_set_norm": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), _VP]),
-    "ch_ws_predict": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
-    "ch_ws_train_residual": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_float,
+    "ch_ws_predict": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "ch_ws_train_residual": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_float,
                                             ctypes.POINTER(ctypes.c_float), _VP]),
-    "ch_ws_train_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+    "ch_ws_train_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                                         ctypes.POINTER(ctypes.c_float), _VP]),
     "ch_profile_enable": (ctypes.c_int, [ctypes.c_int32]),
     "ch_profile_read": (ctypes.c_int, [ctypes.POINTER(ProfEntry), ctypes.c_int32, _I32P, ctypes.c_int32]),
@@ -507,48 +506,49 @@ class WarmStartNet:
         _check(lib().ch_ws_set_norm(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream(stream)),
                "ch_ws_set_norm")
 
-    def fit_norm(self, Q, X, Y, stream=None):
-        """ch_ws_fit_norm on a training set (S x N x 4 CUDA tensors, float64 or float32, all one
-        dtype): sets the network's normalisation and returns (mean[8], inv_std[8], out_scale[4])."""
+    def fit_norm(self, X, stream=None):
+        """ch_ws_fit_norm on the states of a training set (S x N x 4 CUDA tensor, float64 or
+        float32): sets the network's normalisation and returns (mean[8], inv_std[8], out_scale[4])."""
         import numpy as np
-        if not (Q.dtype == X.dtype == Y.dtype) or X.dtype not in (torch.float64, torch.float32):
-            raise ValueError("Q, X, Y must share a float64 or float32 dtype")
-        if not (Q.is_cuda and X.is_cuda and Y.is_cuda) or Q.shape != X.shape or Y.shape != X.shape:
-            raise ValueError("Q, X, Y must be CUDA tensors of one shape")
-        Q, X, Y = Q.contiguous(), X.contiguous(), Y.contiguous()
+        if X.dtype not in (torch.float64, torch.float32) or not X.is_cuda:
+            raise ValueError("X must be a float64 or float32 CUDA tensor")
+        X = X.contiguous()
         out = (ctypes.c_double * 20)()
-        _check(lib().ch_ws_fit_norm(self._h, _ptr(Q), _ptr(X), _ptr(Y), X.shape[0], 1 if X.dtype == torch.float32 else 0,
-                                    out, _stream(stream)), "ch_ws_fit_norm")
+        _check(lib().ch_ws_fit_norm(self._h, _ptr(X), X.shape[0], 1 if X.dtype == torch.float32 else 0, out,
+                                    _stream(stream)), "ch_ws_fit_norm")
         a = np.array(out[:])
         return a[:8], a[8:16], a[16:20]
 
-    def predict(self, state4, prev4, stream=None):
-        s, q = _f64(state4), _f64(prev4)
+    def predict(self, state4, prev4, prev2_4, stream=None):
+        """The next state predicted from s_k, s_{k-1}, s_{k-2} (N x 4 fp64 CUDA each)."""
+        s, q, q2 = _f64(state4), _f64(prev4), _f64(prev2_4)
         pred = torch.empty_like(s)
-        _check(lib().ch_ws_predict(self._h, _ptr(s), _ptr(q), _ptr(pred), _stream(stream)), "ch_ws_predict")
+        _check(lib().ch_ws_predict(self._h, _ptr(s), _ptr(q), _ptr(q2), _ptr(pred), _stream(stream)),
+               "ch_ws_predict")
         return pred
 
-    def train_residual(self, system, x, q, lr: float, precond=None, stream=None):
-        """One step against the residual of the time step (x = s_k, q = s_{k-1}: B x N x 4 fp64
-        CUDA), in the norm of `precond` if given; returns the loss (mean |r|^2 / |r_extrap|^2)."""
-        for a in (x, q):
+    def train_residual(self, system, x, q, q2, lr: float, precond=None, stream=None):
+        """One step against the residual of the time step (x = s_k, q = s_{k-1}, q2 = s_{k-2}:
+        B x N x 4 fp64 CUDA), in the norm of `precond` if given; returns the loss
+        (mean ln(|r|^2 / |r_linear extrapolation|^2))."""
+        for a in (x, q, q2):
             if a.dtype != torch.float64 or not a.is_contiguous() or not a.is_cuda:
                 raise ValueError("expected contiguous float64 CUDA tensors")
         loss = ctypes.c_float()
         pc = precond._h if precond is not None else None
-        _check(lib().ch_ws_train_residual(self._h, system._h, pc, _ptr(x), _ptr(q), x.shape[0], lr, ctypes.byref(loss),
-                                          _stream(stream)), "ch_ws_train_residual")
+        _check(lib().ch_ws_train_residual(self._h, system._h, pc, _ptr(x), _ptr(q), _ptr(q2), x.shape[0], lr,
+                                          ctypes.byref(loss), _stream(stream)), "ch_ws_train_residual")
         return loss.value
 
-    def train_step(self, x, q, n, lr: float, lap: float = 0.0, stream=None):
-        """One step on states x, predecessors q and successors n (B x N x 4 fp32 CUDA); `lap`
-        weighs the grid-Laplacian term of the loss."""
-        for a in (x, q, n):
+    def train_step(self, x, q, q2, n, lr: float, lap: float = 0.0, stream=None):
+        """One step on states x, their predecessors q, q2 and successors n (B x N x 4 fp32 CUDA);
+        `lap` weighs the grid-Laplacian term of the state-space loss."""
+        for a in (x, q, q2, n):
             if a.dtype != torch.float32 or not a.is_contiguous() or not a.is_cuda:
                 raise ValueError("expected contiguous float32 CUDA tensors")
         loss = ctypes.c_float()
-        _check(lib().ch_ws_train_step(self._h, _ptr(x), _ptr(q), _ptr(n), x.shape[0], lap, lr, ctypes.byref(loss),
-                                      _stream(stream)), "ch_ws_train_step")
+        _check(lib().ch_ws_train_step(self._h, _ptr(x), _ptr(q), _ptr(q2), _ptr(n), x.shape[0], lap, lr,
+                                      ctypes.byref(loss), _stream(stream)), "ch_ws_train_step")
         return loss.value
 
     def __del__(self):

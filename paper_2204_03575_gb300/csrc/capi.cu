@@ -503,30 +503,31 @@ ch_status ch_ws_set_norm(ch_ws_t* w, const float* norm20, void* stream) {
   return ch::ws_set_norm(w, norm20, S(stream));
 }
 
-ch_status ch_ws_fit_norm(ch_ws_t* w, const void* q, const void* x, const void* n, int32_t nsamples, int32_t fp32,
-                         double* norm20, void* stream) {
-  CH_ARG(w != nullptr && q != nullptr && x != nullptr && n != nullptr && norm20 != nullptr, "NULL argument");
+ch_status ch_ws_fit_norm(ch_ws_t* w, const void* x, int32_t nsamples, int32_t fp32, double* norm20, void* stream) {
+  CH_ARG(w != nullptr && x != nullptr && norm20 != nullptr, "NULL argument");
   CH_ARG(nsamples >= 1, "nsamples must be >= 1");
   CH_ARG(fp32 == 0 || fp32 == 1, "fp32 must be 0 or 1");
-  return ch::ws_fit_norm(w, q, x, n, nsamples, fp32, norm20, S(stream));
+  return ch::ws_fit_norm(w, x, nsamples, fp32, norm20, S(stream));
 }
 
-ch_status ch_ws_predict(ch_ws_t* w, const double* state, const double* prev, double* pred, void* stream) {
-  CH_ARG(w != nullptr && state != nullptr && prev != nullptr && pred != nullptr, "NULL argument");
-  CH_ARG(state != pred && prev != pred, "pred must not alias the inputs");
-  return ch::ws_predict(w, state, prev, pred, S(stream));
+ch_status ch_ws_predict(ch_ws_t* w, const double* state, const double* prev, const double* prev2, double* pred,
+                        void* stream) {
+  CH_ARG(w != nullptr && state != nullptr && prev != nullptr && prev2 != nullptr && pred != nullptr,
+         "NULL argument");
+  CH_ARG(state != pred && prev != pred && prev2 != pred, "pred must not alias the inputs");
+  return ch::ws_predict(w, state, prev, prev2, pred, S(stream));
 }
 
-ch_status ch_ws_train_step(ch_ws_t* w, const float* x, const float* q, const float* n, int32_t B,
+ch_status ch_ws_train_step(ch_ws_t* w, const float* x, const float* q, const float* q2, const float* n, int32_t B,
                            float lap, float lr, float* loss, void* stream) {
-  CH_ARG(w != nullptr && x != nullptr && q != nullptr && n != nullptr, "NULL argument");
-  return ch::ws_train_step(w, x, q, n, B, lap, lr, loss, S(stream));
+  CH_ARG(w != nullptr && x != nullptr && q != nullptr && q2 != nullptr && n != nullptr, "NULL argument");
+  return ch::ws_train_step(w, x, q, q2, n, B, lap, lr, loss, S(stream));
 }
 
 ch_status ch_ws_train_residual(ch_ws_t* w, const ch_system_t* sys, ch_precond_t* pc, const double* x,
-                               const double* q, int32_t B, float lr, float* loss, void* stream) {
-  CH_ARG(w != nullptr && sys != nullptr && x != nullptr && q != nullptr, "NULL argument");
-  return ch::ws_train_residual(w, sys, pc, x, q, B, lr, loss, S(stream));
+                               const double* q, const double* q2, int32_t B, float lr, float* loss, void* stream) {
+  CH_ARG(w != nullptr && sys != nullptr && x != nullptr && q != nullptr && q2 != nullptr, "NULL argument");
+  return ch::ws_train_residual(w, sys, pc, x, q, q2, B, lr, loss, S(stream));
 }
 
 }  // extern "C"

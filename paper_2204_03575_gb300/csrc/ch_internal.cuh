@@ -281,13 +281,13 @@ void ws_destroy(ch_ws_s* w);
 ch_status ws_set_params(ch_ws_s* w, const float* host, cudaStream_t st);
 ch_status ws_get_params(const ch_ws_s* w, float* host, float* host_grads, cudaStream_t st);
 ch_status ws_set_norm(ch_ws_s* w, const float* host20, cudaStream_t st);
-ch_status ws_fit_norm(ch_ws_s* w, const void* q, const void* x, const void* n, int S, int fp32, double* host20,
-                      cudaStream_t st);
-ch_status ws_predict(ch_ws_s* w, const double* state, const double* prev, double* pred, cudaStream_t st);
-ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float* n, int B, float lap,
-                        float lr, float* loss, cudaStream_t st);
+ch_status ws_fit_norm(ch_ws_s* w, const void* x, int S, int fp32, double* host20, cudaStream_t st);
+ch_status ws_predict(ch_ws_s* w, const double* state, const double* prev, const double* prev2, double* pred,
+                     cudaStream_t st);
+ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float* q2, const float* n, int B,
+                        float lap, float lr, float* loss, cudaStream_t st);
 ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc, const double* x,
-                            const double* q, int B, float lr, float* loss, cudaStream_t st);
+                            const double* q, const double* q2, int B, float lr, float* loss, cudaStream_t st);
 int ws_nparam();
 void ws_dims(const ch_ws_s* w, int* H, int* W);
 ch_status state_step_learned(ch_state_s* S, ch_ws_s* w, cudaStream_t st, ch_step_stats* stats);

@@ -759,8 +759,9 @@ struct ch_state_s {
   bool set = false;
   bool use_graphs = true;
   int since_set = 0;                // steps taken since the state was last set
-  int learn_k = 0;                  // consecutive learned steps (x_prev valid when >= 1)
+  int learn_k = 0;                  // consecutive learned steps (x_prev valid when >= 1, x_prev2 when >= 2)
   double* x_prev = nullptr;         // N x 4: the state before the last learned step
+  double* x_prev2 = nullptr;        // N x 4: the state before that
   double* guess = nullptr;          // N x 4: the network's prediction
   cudaStream_t cap_stream = nullptr;            // private stream for graph capture
   cudaStream_t body_stream = nullptr;           // nested captures of the device loop's body
@@ -1836,11 +1837,12 @@ ch_status state_step_guess(ch_state_s* S, const double* guess, cudaStream_t st, 
   return step_guess_core(S, guess, st, stats, true);
 }
 
-// A step whose guess is the warm-start network's prediction from the state and its predecessor
-// (kept on the device across consecutive learned steps).  The network needs a predecessor that
-// is not the initial state (whose chemical potentials the first step sets up): until two steps
-// have been taken since the state was set, and after any step of another kind, the step starts
-// from the previous state.  ms in the statistics includes the prediction.
+// A step whose guess is the warm-start network's prediction from the state and its two
+// predecessors (kept on the device across consecutive learned steps).  The network needs
+// predecessors that are not the initial state (whose chemical potentials the first step sets up):
+// until three steps have been taken since the state was set, and until two learned steps in a row
+// have recorded the history, the step starts from the previous state.  ms in the statistics
+// includes the prediction.
 ch_status state_step_learned(ch_state_s* S, ch_ws_s* w, cudaStream_t st, ch_step_stats* stats) {
   if (!S->set) {
     set_error("state not initialised (call ch_state_set or ch_state_init_seeded)");
@@ -1856,11 +1858,13 @@ ch_status state_step_learned(ch_state_s* S, ch_ws_s* w, cudaStream_t st, ch_step
   }
   if (!S->x_prev) {
     CH_TRY(S->mem.get(&S->x_prev, (size_t)S->N * 4));
+    CH_TRY(S->mem.get(&S->x_prev2, (size_t)S->N * 4));
     CH_TRY(S->mem.get(&S->guess, (size_t)S->N * 4));
   }
-  const bool use_net = S->learn_k >= 1 && S->since_set >= 2;
+  const bool use_net = S->learn_k >= 2 && S->since_set >= 3;
   CH_CUDA(cudaEventRecord(S->ev0, st));
-  if (use_net) CH_TRY(ws_predict(w, S->x, S->x_prev, S->guess, st));
+  if (use_net) CH_TRY(ws_predict(w, S->x, S->x_prev, S->x_prev2, S->guess, st));
+  std::swap(S->x_prev, S->x_prev2);  // the history moves on: s_{k-1} becomes s_{k-2}, s_k becomes s_{k-1}
   {
     ProfScope ps(st, K_STATE_IO, 0, 64.0 * S->N, 0.0);
     CH_CUDA(cudaMemcpyAsync(S->x_prev, S->x, sizeof(double) * 4 * S->N, cudaMemcpyDeviceToDevice, st));

@@ -2,15 +2,16 @@
 // that predicts the next time step's state, used as the initial guess of FGMRES.
 //
 // Network (3 layers, 3x3 convolutions, "same" zero padding, stride 1):
-//   z1 = W1 * x + b1 (8 -> C),  a1 = relu(z1)
+//   z1 = W1 * x + b1 (12 -> C), a1 = relu(z1)
 //   z2 = W2 * a1 + b2 (C -> C), a2 = relu(z2)
 //   y  = W3 * a2 + b3 (C -> 4)
-// x holds the state s_k = (phi_p, phi_n, mu_p, mu_n) at step k, normalised per channel, and its
-// change d_k = s_k - s_{k-1} in units of its RMS over the image (8 of 16 input channels); y is the
-// correction to the linearly extrapolated next state in the same units,
-// pred = s_k + d_k + y * out_scale * rms(d_k).  Scaling by the sample's own rms(d_k) makes the
-// map independent of how fast the state is moving (early steps change it by orders of magnitude
-// more than later ones).  Activations are NHWC BF16
+// From the last three states s = s_k, q = s_{k-1}, q2 = s_{k-2} (phi_p, phi_n, mu_p, mu_n) the
+// prediction is a learned second-order extrapolation,
+//   pred = s + d + theta * D,  d = s - q,  D = s - 2 q + q2,  theta = y * out_scale,
+// so the zero network is linear and theta = 1 quadratic extrapolation, and the network only scales
+// the (smooth) second difference pixel by pixel.  x holds the fields normalised per channel, d in
+// units of its RMS over the image and D in units of its RMS (12 of 16 input channels): the map
+// does not depend on how fast the state moves.  Activations are NHWC BF16
 // with FP32 accumulation; weights are kept as FP32 master copies (Adam) and BF16 copies for the
 // tensor cores, the latter also in tap-flipped, channel-transposed form for the backward pass
 // through the data.
@@ -31,7 +32,7 @@
 namespace ch {
 
 constexpr int WS_C = 32;       // hidden channels
-constexpr int WS_CIN = 16;     // input channels padded for the k16 MMA (8 used)
+constexpr int WS_CIN = 16;     // input channels padded for the k16 MMA (12 used)
 constexpr int WS_COUT = 8;     // output channels padded for the n8 MMA (4 used)
 constexpr int WS_CHUNK = 1024; // pixels per weight-gradient partial
 
@@ -140,48 +141,59 @@ __global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict
 }
 
 // ---------------------------------------------------------------- data movement
-// Per-sample scale of the last change: dscale[smp][c] = sqrt(mean_i (s_ic - q_ic)^2), the RMS over
-// the image of channel c of d = s - q (at least 1e-30).  One block per sample; FP64 sums reduced in
-// a fixed order (deterministic).
+// Per-sample scales: dscale[smp][c] = RMS over the image of channel c of d = s - q, and
+// dscale[smp][4 + c] that of D = s - 2 q + q2 (1 when q2 is null); at least 1e-30.  One block per
+// sample; FP64 sums reduced in a fixed order (deterministic).
 template <typename T>
-__global__ void k_ws_dscale(const T* __restrict__ s, const T* __restrict__ q, int P, float* __restrict__ dscale) {
-  __shared__ double red[4][256];
+__global__ void k_ws_rms(const T* __restrict__ s, const T* __restrict__ q, const T* __restrict__ q2, int P,
+                         float* __restrict__ dscale) {
+  __shared__ double red[8][256];
   const int smp = blockIdx.x;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (size_t i = threadIdx.x; i < (size_t)P; i += blockDim.x) {
     const size_t o = ((size_t)smp * P + i) * 4;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const double d = (double)s[o + c] - (double)q[o + c];
+      const double a = s[o + c], b = q[o + c];
+      const double d = a - b;
       acc[c] = fma(d, d, acc[c]);
+      if (q2) {
+        const double D = a - 2.0 * b + (double)q2[o + c];
+        acc[4 + c] = fma(D, D, acc[4 + c]);
+      }
     }
   }
 #pragma unroll
-  for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];
+  for (int c = 0; c < 8; ++c) red[c][threadIdx.x] = acc[c];
   __syncthreads();
   for (int h = 128; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+      for (int c = 0; c < 8; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
     }
     __syncthreads();
   }
-  if (threadIdx.x < 4) dscale[smp * 4 + threadIdx.x] = (float)fmax(sqrt(red[threadIdx.x][0] / (double)P), 1e-30);
+  if (threadIdx.x < 8)
+    dscale[smp * 8 + threadIdx.x] = (threadIdx.x >= 4 && !q2) ? 1.f
+                                    : (float)fmax(sqrt(red[threadIdx.x][0] / (double)P), 1e-30);
 }
 
-// Input image of the network from the state s and the previous state q (N x 4 each, fp64 node
-// major or fp32 sample-major): channels 0-3 = (s - mean[0:4]) * inv_std[0:4] (the fields at step
-// k), channels 4-7 = ((s - q) / dscale - mean[4:8]) * inv_std[4:8] (their change over the last
-// step in units of its RMS), channels 8-15 zero.
+// Input image of the network from the states s, q, q2 (N x 4 each, fp64 node major or fp32
+// sample-major): channels 0-3 = (s - mean[0:4]) * inv_std[0:4] (the fields at step k), channels
+// 4-7 = ((s - q) / r1 - mean[4:8]) * inv_std[4:8] (the last change in units of its RMS), channels
+// 8-11 = (s - 2 q + q2) / r2 (the second difference in units of its RMS), channels 12-15 zero.
 template <typename T>
-__global__ void k_ws_pack(const T* __restrict__ s, const T* __restrict__ q, int P,
+__global__ void k_ws_pack(const T* __restrict__ s, const T* __restrict__ q, const T* __restrict__ q2, int P,
                           const float* __restrict__ mean, const float* __restrict__ inv_std,
                           const float* __restrict__ dscale, __nv_bfloat16* __restrict__ x) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // pixel; blockIdx.y = sample
   const int smp = blockIdx.y;
   if (i >= (size_t)P) return;
-  const T* a = s + ((size_t)smp * P + i) * 4;
-  const T* b = q + ((size_t)smp * P + i) * 4;
+  const size_t o = ((size_t)smp * P + i) * 4;
+  const T* a = s + o;
+  const T* b = q + o;
+  const T* b2 = q2 + o;
+  const float* sc = dscale + smp * 8;
   __nv_bfloat16* dst = x + ((size_t)smp * P + i) * WS_CIN;
 #pragma unroll
   for (int c = 0; c < WS_CIN; ++c) {
@@ -189,57 +201,61 @@ __global__ void k_ws_pack(const T* __restrict__ s, const T* __restrict__ q, int 
     if (c < 4) {
       v = ((float)a[c] - mean[c]) * inv_std[c];
     } else if (c < 8) {
-      const double d = ((double)a[c - 4] - (double)b[c - 4]) / (double)dscale[smp * 4 + c - 4];
+      const double d = ((double)a[c - 4] - (double)b[c - 4]) / (double)sc[c - 4];
       v = ((float)d - mean[c]) * inv_std[c];
+    } else if (c < 12) {
+      const double D = (double)a[c - 8] - 2.0 * (double)b[c - 8] + (double)b2[c - 8];
+      v = (float)(D / (double)sc[c - 4]);
     }
     dst[c] = __float2bfloat16_rn(v);
   }
 }
 
-// Training target: t = ((n - s) - (s - q)) / (dscale * out_scale), the normalised correction to
-// the linear extrapolation (fp32 inputs, sample-major B x N x 4).
-__global__ void k_ws_target(const float* __restrict__ s, const float* __restrict__ q,
-                            const float* __restrict__ n, int P, const float* __restrict__ dscale,
-                            const float* __restrict__ out_scale, float* __restrict__ t) {
+// State-space error of the prediction in units of the change's RMS, E = (theta D - e) / r1 with
+// theta = y out_scale, D = s - 2 q + q2 and e = n - 2 s + q (the linear extrapolation's error), and
+// the factor dE/dy = out_scale D / r1 (fp32 inputs, sample-major B x N x 4).
+__global__ void k_ws_err_theta(const float* __restrict__ y, const float* __restrict__ s, const float* __restrict__ q,
+                               const float* __restrict__ q2, const float* __restrict__ n, int P,
+                               const float* __restrict__ out_scale, const float* __restrict__ dscale,
+                               float* __restrict__ e, float* __restrict__ fac) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int smp = blockIdx.y;
   if (i >= (size_t)P) return;
   const size_t o = ((size_t)smp * P + i) * 4;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const double a = s[o + c], e = ((double)n[o + c] - a) - (a - (double)q[o + c]);
-    t[o + c] = (float)(e / ((double)dscale[smp * 4 + c] * (double)out_scale[c]));
+    const double a = s[o + c], b = q[o + c];
+    const double D = a - 2.0 * b + (double)q2[o + c];
+    const double err = (double)n[o + c] - 2.0 * a + b;
+    const double r1 = dscale[smp * 8 + c], os = out_scale[c];
+    const double th = (double)y[((size_t)smp * P + i) * WS_COUT + c] * os;
+    e[o + c] = (float)((th * D - err) / r1);
+    fac[o + c] = (float)(os * D / r1);
   }
 }
 
-// pred = s + (s - q) + y * out_scale * dscale (fp64, N x 4): linear extrapolation plus the
-// learned correction
-__global__ void k_ws_unpack(const double* __restrict__ s, const double* __restrict__ q,
+// pred = s + (s - q) + y * out_scale * (s - 2 q + q2) (fp64, N x 4): the learned second-order
+// extrapolation
+__global__ void k_ws_unpack(const double* __restrict__ s, const double* __restrict__ q, const double* __restrict__ q2,
                             const float* __restrict__ y, int P, const float* __restrict__ out_scale,
-                            const float* __restrict__ dscale, double* __restrict__ pred) {
+                            double* __restrict__ pred) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const double a = s[(size_t)i * 4 + c], b = q[(size_t)i * 4 + c];
-    const double corr = (double)y[(size_t)i * WS_COUT + c] * ((double)out_scale[c] * (double)dscale[c]);
-    pred[(size_t)i * 4 + c] = a + (a - b) + corr;
+    const size_t o = (size_t)i * 4 + c;
+    const double a = s[o], b = q[o];
+    const double D = a - 2.0 * b + q2[o];
+    pred[o] = a + (a - b) + (double)y[(size_t)i * WS_COUT + c] * (double)out_scale[c] * D;
   }
 }
 
-// Loss on the 4 used output channels, L = (sum E^2 + lap * sum (G E)^2) / count with E = y - t and
-// G the graph Laplacian of the pixel grid, (G E)_p = sum over the 4-neighbours q of p inside the
-// image of (E_q - E_p).  The second term weighs errors the way the stiffness rows of the step's
-// residual do.  Three passes: E, then G E with the per-block partial losses (summed in block
-// order), then dy = 2 (E + lap G (G E)) / count as a bf16 NHWC image with 16 channels.
-__global__ void k_ws_err(const float* __restrict__ y, const float* __restrict__ tgt, size_t total,
-                         float* __restrict__ e) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) e[i * 4 + c] = y[i * WS_COUT + c] - tgt[i * 4 + c];
-  }
-}
-
+// Loss on the 4 used output channels, L = (sum E^2 + lap * sum (G E)^2) / count with E the error
+// above and G the graph Laplacian of the pixel grid, (G E)_p = sum over the 4-neighbours q of p
+// inside the image of (E_q - E_p).  The second term weighs errors the way the stiffness rows of
+// the step's residual do.  Two passes after E: G E with the per-block partial losses (summed in
+// block order), then dy = 2 (E + lap G (G E)) / count * dE/dy as a bf16 NHWC image with 16
+// channels.
 __device__ __forceinline__ float4 grid_laplacian(const float* __restrict__ e, int H, int W, size_t base, int r, int q) {
   const float4 c = *reinterpret_cast<const float4*>(e + (base + (size_t)r * W + q) * 4);
   float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -281,8 +297,8 @@ __global__ void k_ws_lap_loss(const float* __restrict__ e, int H, int W, int B, 
   if (threadIdx.x == 0) loss_part[blockIdx.x] = sm[0];
 }
 
-__global__ void k_ws_dy(const float* __restrict__ e, const float* __restrict__ ge, int H, int W, int B,
-                        float lap, __nv_bfloat16* __restrict__ dy) {
+__global__ void k_ws_dy(const float* __restrict__ e, const float* __restrict__ ge, const float* __restrict__ fac,
+                        int H, int W, int B, float lap, __nv_bfloat16* __restrict__ dy) {
   const size_t P = (size_t)H * W, total = (size_t)B * P;
   const float scale = 2.f / (float)(total * 4);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -297,7 +313,7 @@ __global__ void k_ws_dy(const float* __restrict__ e, const float* __restrict__ g
     }
     const float vals[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int c = 0; c < 16; ++c) dy[i * 16 + c] = __float2bfloat16_rn(c < 4 ? scale * vals[c] : 0.f);
+    for (int c = 0; c < 16; ++c) dy[i * 16 + c] = __float2bfloat16_rn(c < 4 ? scale * vals[c] * fac[i * 4 + c] : 0.f);
   }
 }
 
@@ -404,8 +420,8 @@ struct ch_ws_s {
   __nv_bfloat16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr;     // forward copies
   __nv_bfloat16 *w2f = nullptr, *w3f = nullptr;                    // flipped copies (backward)
   float* norm = nullptr;  // mean[8], inv_std[8], out_scale[4]
-  float* dscale = nullptr;  // Bmax x 4: RMS of the last change per sample and channel
-  float* t = nullptr;       // Bmax x P x 4 training targets
+  float* dscale = nullptr;  // Bmax x 8: RMS of the last change and of the second difference per sample and channel
+  float* t = nullptr;       // Bmax x P x 4: dE/dy of the state-space loss
   float* e = nullptr;       // Bmax x P x 4 output errors y - t
   float* ge = nullptr;      // Bmax x P x 4 their grid Laplacian
   double* rex = nullptr;    // Bmax x P x 4 residuals of the extrapolation (residual loss)
@@ -485,7 +501,7 @@ ch_status ws_create(int H, int W, int Bmax, ch_ws_s** out) {
   if (r == CH_OK) r = w->mem.get(&w->w2f, 9 * WS_C * WS_C);
   if (r == CH_OK) r = w->mem.get(&w->w3f, 9 * 16 * WS_C);
   if (r == CH_OK) r = w->mem.get(&w->norm, 20);
-  if (r == CH_OK) r = w->mem.get(&w->dscale, (size_t)Bmax * 4);
+  if (r == CH_OK) r = w->mem.get(&w->dscale, (size_t)Bmax * 8);
   if (r == CH_OK) r = w->mem.get(&w->t, P * 4);
   if (r == CH_OK) r = w->mem.get(&w->e, P * 4);
   if (r == CH_OK) r = w->mem.get(&w->ge, P * 4);
@@ -573,30 +589,31 @@ static ch_status ws_backward_update(ch_ws_s* w, int B, float lr, cudaStream_t st
   return CH_OK;
 }
 
-// inference: pred = s + d + net(s, d / dscale) * out_scale * dscale for one state s, its
-// predecessor q and d = s - q
-ch_status ws_predict(ch_ws_s* w, const double* state, const double* prev, double* pred, cudaStream_t st) {
+// inference: pred = s + d + (net(...) * out_scale) * D for one state s and its two predecessors
+// q, q2 (d = s - q, D = s - 2 q + q2)
+ch_status ws_predict(ch_ws_s* w, const double* state, const double* prev, const double* prev2, double* pred,
+                     cudaStream_t st) {
   {
-    ProfScope ps(st, K_WS_IO, 0, w->P * (32.0 + 32.0 + 32.0 + 32.0), 0.0);
-    k_ws_dscale<double><<<1, 256, 0, st>>>(state, prev, w->P, w->dscale);
-    k_ws_pack<double><<<dim3(blocks_for(w->P), 1), TPB, 0, st>>>(state, prev, w->P, w->norm, w->norm + 8,
+    ProfScope ps(st, K_WS_IO, 0, w->P * (32.0 * 3 + 32.0), 0.0);
+    k_ws_rms<double><<<1, 256, 0, st>>>(state, prev, prev2, w->P, w->dscale);
+    k_ws_pack<double><<<dim3(blocks_for(w->P), 1), TPB, 0, st>>>(state, prev, prev2, w->P, w->norm, w->norm + 8,
                                                                   w->dscale, w->x0);
   }
   CH_LAUNCHED();
   CH_TRY(ws_forward_packed(w, 1, st));
   {
-    ProfScope ps(st, K_WS_IO, 0, w->P * (32.0 + 32.0 + 32.0 + 32.0), 0.0);
-    k_ws_unpack<<<blocks_for(w->P), TPB, 0, st>>>(state, prev, w->y, w->P, w->norm + 16, w->dscale, pred);
+    ProfScope ps(st, K_WS_IO, 0, w->P * (32.0 * 3 + 32.0 + 32.0), 0.0);
+    k_ws_unpack<<<blocks_for(w->P), TPB, 0, st>>>(state, prev, prev2, w->y, w->P, w->norm + 16, pred);
   }
   CH_LAUNCHED();
   return CH_OK;
 }
 
-// one training step on B samples (fp32, B x N x 4 each): states x, their predecessors q and
-// successors n.  Computes the loss (with the grid-Laplacian term weighted by lap) and the
-// gradients; if lr > 0 also takes an Adam step.
-ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float* n, int B, float lap,
-                        float lr, float* loss, cudaStream_t st) {
+// one training step on B samples (fp32, B x N x 4 each): states x, their two predecessors q, q2
+// and successors n.  Computes the state-space loss (with the grid-Laplacian term weighted by lap)
+// and the gradients; if lr > 0 also takes an Adam step.
+ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float* q2, const float* n, int B,
+                        float lap, float lr, float* loss, cudaStream_t st) {
   if (B < 1 || B > w->Bmax) {
     set_error("batch of %d samples outside [1, %d]", B, w->Bmax);
     return CH_ERR_ARG;
@@ -606,15 +623,14 @@ ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float*
     return CH_ERR_ARG;
   }
   const int P = w->P;
-  k_ws_dscale<float><<<B, 256, 0, st>>>(x, q, P, w->dscale);
-  k_ws_pack<float><<<dim3(blocks_for(P), B), TPB, 0, st>>>(x, q, P, w->norm, w->norm + 8, w->dscale, w->x0);
-  k_ws_target<<<dim3(blocks_for(P), B), TPB, 0, st>>>(x, q, n, P, w->dscale, w->norm + 16, w->t);
+  k_ws_rms<float><<<B, 256, 0, st>>>(x, q, q2, P, w->dscale);
+  k_ws_pack<float><<<dim3(blocks_for(P), B), TPB, 0, st>>>(x, q, q2, P, w->norm, w->norm + 8, w->dscale, w->x0);
   CH_LAUNCHED();
   CH_TRY(ws_forward_packed(w, B, st));
   const int lb = 304;
-  k_ws_err<<<lb, 256, 0, st>>>(w->y, w->t, (size_t)B * P, w->e);
+  k_ws_err_theta<<<dim3(blocks_for(P), B), TPB, 0, st>>>(w->y, x, q, q2, n, P, w->norm + 16, w->dscale, w->e, w->t);
   k_ws_lap_loss<<<lb, 256, 0, st>>>(w->e, w->H, w->W, B, lap, w->ge, w->loss_part);
-  k_ws_dy<<<lb, 256, 0, st>>>(w->e, w->ge, w->H, w->W, B, lap, w->dy);
+  k_ws_dy<<<lb, 256, 0, st>>>(w->e, w->ge, w->t, w->H, w->W, B, lap, w->dy);
   CH_TRY(ws_backward_update(w, B, lr, st));
   if (loss) {
     float parts[lb];
@@ -628,18 +644,18 @@ ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float*
 }
 
 // ---------------------------------------------------------------- residual-loss training
-// The correction c = y * out_scale * dscale (fp64, N x 4) of one sample, or the extrapolation
-// 2 s - q (mode 0).
+// The correction c = y * out_scale * D (fp64, N x 4, D = s - 2 q + q2) of one sample, or the
+// linear extrapolation 2 s - q (mode 0).
 __global__ void k_ws_guess_part(int P, int mode, const double* __restrict__ s, const double* __restrict__ q,
-                                const float* __restrict__ y, const float* __restrict__ out_scale,
-                                const float* __restrict__ dscale, double* __restrict__ out) {
+                                const double* __restrict__ q2, const float* __restrict__ y,
+                                const float* __restrict__ out_scale, double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const size_t o = (size_t)i * 4 + c;
     out[o] = mode == 0 ? 2.0 * s[o] - q[o]
-                       : (double)y[(size_t)i * WS_COUT + c] * ((double)out_scale[c] * (double)dscale[c]);
+                       : (double)y[(size_t)i * WS_COUT + c] * (double)out_scale[c] * (s[o] - 2.0 * q[o] + q2[o]);
   }
 }
 
@@ -676,32 +692,35 @@ __global__ void k_ws_resnorm(int P, const double* __restrict__ rex, const double
   if (threadIdx.x < 8) nrm[threadIdx.x] = red[threadIdx.x][0];
 }
 
-// dy of one sample from g = A z: L = sum_species <r, z>_sp / <rex, zex>_sp / (2B) with z = P^-1 r
-// (P^-1 symmetric, or the identity), r = rex - A c, so dL/dc = -2 A z / <rex, zex>_sp / (2B) and
-// dL/dy_c = dL/dc_c * out_scale_c * dscale_c.
+// dy of one sample from g = A z: L = sum_species ln(<r, z>_sp / <rex, zex>_sp) / (2B) with
+// z = P^-1 r (P^-1 symmetric, or the identity), r = rex - A c, so dL/dc = -2 A z / <r, z>_sp / (2B)
+// and dL/dy_c = dL/dc_c * out_scale_c * D_c (c = y out_scale D).
 // Channel c belongs to species c % 2 (channels phi_p, phi_n, mu_p, mu_n).
 __global__ void k_ws_res_dy(int P, int B, const double* __restrict__ g, const double* __restrict__ nrm,
-                            const float* __restrict__ out_scale, const float* __restrict__ dscale,
+                            const float* __restrict__ out_scale, const double* __restrict__ s,
+                            const double* __restrict__ q, const double* __restrict__ q2,
                             __nv_bfloat16* __restrict__ dy) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
   double wsp[2];
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
-    const double den = nrm[sp] + nrm[sp + 2];
-    wsp[sp] = den > 0.0 ? 1.0 / (den * (double)B) : 0.0;
+    const double den = nrm[sp] + nrm[sp + 2], num = nrm[4 + sp] + nrm[6 + sp];
+    wsp[sp] = (den > 0.0 && num > 0.0) ? 1.0 / (num * (double)B) : 0.0;
   }
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
     float v = 0.f;
-    if (c < 4)
-      v = (float)(-g[(size_t)i * 4 + c] * wsp[c % 2] * ((double)out_scale[c] * (double)dscale[c]));
+    if (c < 4) {
+      const size_t o = (size_t)i * 4 + c;
+      v = (float)(-g[o] * wsp[c % 2] * ((double)out_scale[c] * (s[o] - 2.0 * q[o] + q2[o])));
+    }
     dy[(size_t)i * 16 + c] = __float2bfloat16_rn(v);
   }
 }
 
 ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc, const double* x,
-                            const double* q, int B, float lr, float* loss, cudaStream_t st) {
+                            const double* q, const double* q2, int B, float lr, float* loss, cudaStream_t st) {
   if (B < 1 || B > w->Bmax) {
     set_error("batch of %d samples outside [1, %d]", B, w->Bmax);
     return CH_ERR_ARG;
@@ -727,25 +746,25 @@ ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc
     CH_TRY(w->mem.get(&w->tmp2, (size_t)P * 4));
     CH_TRY(w->mem.get(&w->nrm, (size_t)w->Bmax * 8));
   }
-  k_ws_dscale<double><<<B, 256, 0, st>>>(x, q, P, w->dscale);
-  k_ws_pack<double><<<dim3(blocks_for(P), B), TPB, 0, st>>>(x, q, P, w->norm, w->norm + 8, w->dscale, w->x0);
+  k_ws_rms<double><<<B, 256, 0, st>>>(x, q, q2, P, w->dscale);
+  k_ws_pack<double><<<dim3(blocks_for(P), B), TPB, 0, st>>>(x, q, q2, P, w->norm, w->norm + 8, w->dscale, w->x0);
   CH_LAUNCHED();
   CH_TRY(ws_forward_packed(w, B, st));
   const int nb = blocks_for(P), nb4 = blocks_for(4 * P);
   for (int b = 0; b < B; ++b) {
     const double* xs = x + (size_t)b * P * 4;
     const double* qs = q + (size_t)b * P * 4;
+    const double* q2s = q2 + (size_t)b * P * 4;
     double* rex = w->rex + (size_t)b * P * 4;
     double* r = w->rres + (size_t)b * P * 4;
     // rex = b(s) - A (2 s - q)
     CH_TRY(rhs_strided(sys, xs, xs + 1, 4, w->tmp1, st));
-    k_ws_guess_part<<<nb, TPB, 0, st>>>(P, 0, xs, qs, nullptr, nullptr, nullptr, w->tmp2);
+    k_ws_guess_part<<<nb, TPB, 0, st>>>(P, 0, xs, qs, q2s, nullptr, nullptr, w->tmp2);
     CH_LAUNCHED();
     CH_TRY(apply_A(sys, w->tmp2, rex, st));
     k_ws_sub<<<nb4, TPB, 0, st>>>(4 * P, w->tmp1, rex, rex);
     // r = rex - A c
-    k_ws_guess_part<<<nb, TPB, 0, st>>>(P, 1, nullptr, nullptr, w->y + (size_t)b * P * WS_COUT, w->norm + 16,
-                                        w->dscale + 4 * b, w->tmp2);
+    k_ws_guess_part<<<nb, TPB, 0, st>>>(P, 1, xs, qs, q2s, w->y + (size_t)b * P * WS_COUT, w->norm + 16, w->tmp2);
     CH_LAUNCHED();
     CH_TRY(apply_A(sys, w->tmp2, w->tmp1, st));
     k_ws_sub<<<nb4, TPB, 0, st>>>(4 * P, rex, w->tmp1, r);
@@ -761,7 +780,7 @@ ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc
     k_ws_resnorm<<<1, 256, 0, st>>>(P, rex, zex, r, z, w->nrm + 8 * b);
     // g = A z (A is symmetric) -> dy of this sample
     CH_TRY(apply_A(sys, z, w->tmp1, st));
-    k_ws_res_dy<<<nb, TPB, 0, st>>>(P, B, w->tmp1, w->nrm + 8 * b, w->norm + 16, w->dscale + 4 * b,
+    k_ws_res_dy<<<nb, TPB, 0, st>>>(P, B, w->tmp1, w->nrm + 8 * b, w->norm + 16, xs, qs, q2s,
                                     w->dy + (size_t)b * P * 16);
     CH_LAUNCHED();
   }
@@ -773,8 +792,8 @@ ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc
     double L = 0.0;
     for (int b = 0; b < B; ++b)
       for (int sp = 0; sp < 2; ++sp) {
-        const double den = h[8 * b + sp] + h[8 * b + sp + 2];
-        if (den > 0.0) L += (h[8 * b + 4 + sp] + h[8 * b + 6 + sp]) / den;
+        const double den = h[8 * b + sp] + h[8 * b + sp + 2], num = h[8 * b + 4 + sp] + h[8 * b + 6 + sp];
+        if (den > 0.0 && num > 0.0) L += std::log(num / den);
       }
     *loss = (float)(L / (2.0 * B));
   }
@@ -782,88 +801,59 @@ ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc
 }
 
 // ---------------------------------------------------------------- normalisation of a training set
-// S samples of P x 4 states x, their predecessors q and successors n (fp64, or fp32 with F = float).
-// The network's inputs are the fields (normalised by their mean and standard deviation over the
-// set) and the change d = x - q in units of its per-sample RMS r (mean 0, scale 1 as they are);
-// its output is scaled by the standard deviation of the extrapolation's correction in those units,
-// e = ((n - x) - d) / r.  Standard deviations use the n - 1 divisor.  Sums run in a fixed order
-// (per-block partials, then one block in block order), so the statistics are reproducible.
+// S samples of P x 4 states x = s_k (fp64, or fp32 with F = float).  The network's inputs are the
+// fields, normalised by their mean and standard deviation over the set (n - 1 divisor), and the
+// change and the second difference in units of their per-sample RMS (mean 0, scale 1 as they are);
+// its output is theta itself (out_scale = 1).  Sums run in a fixed order (per-block partials, then
+// one block in block order), so the statistics are reproducible.
 constexpr int FIT_BLOCKS = 152 * 4;
 
-template <typename F>
-__global__ void k_fit_r(const F* __restrict__ x, const F* __restrict__ q, int P, double* __restrict__ r) {
-  __shared__ double sm[TPB / 32][4];
-  const F* xs = x + (size_t)blockIdx.x * P * 4;
-  const F* qs = q + (size_t)blockIdx.x * P * 4;
-  double acc[4] = {0, 0, 0, 0};
-  for (int p = threadIdx.x; p < P; p += blockDim.x)
-    for (int c = 0; c < 4; ++c) {
-      const double d = (double)xs[(size_t)p * 4 + c] - (double)qs[(size_t)p * 4 + c];
-      acc[c] = fma(d, d, acc[c]);
-    }
-  for (int c = 0; c < 4; ++c) {
-    double v = acc[c];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5][c] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double t = 0.0;
-    for (int w = 0; w < TPB / 32; ++w) t += sm[w][threadIdx.x];
-    r[blockIdx.x * 4 + threadIdx.x] = fmax(sqrt(t / P), 1e-30);
-  }
-}
-
-// pass 0: sums of x and e per channel; pass 1: sums of squared deviations from mean[8]
+// PASS 0: per channel sums of x; PASS 1: of (x - mean)^2
 template <typename F, int PASS>
-__global__ void k_fit_sums(const F* __restrict__ x, const F* __restrict__ q, const F* __restrict__ n, int P,
-                           int64_t total, const double* __restrict__ r, const double* __restrict__ mean,
+__global__ void k_fit_sums(const F* __restrict__ x, int64_t total, const double* __restrict__ mean,
                            double* __restrict__ part) {
-  __shared__ double sm[TPB / 32][8];
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  __shared__ double sm[TPB / 32][4];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t smp = v / P;
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const double xv = x[v * 4 + c], qv = q[v * 4 + c], nv = n[v * 4 + c];
-      const double e = ((nv - xv) - (xv - qv)) / r[smp * 4 + c];
+      const double xv = x[v * 4 + c];
       if (PASS == 0) {
         acc[c] += xv;
-        acc[4 + c] += e;
       } else {
-        const double dx = xv - mean[c], de = e - mean[4 + c];
+        const double dx = xv - mean[c];
         acc[c] = fma(dx, dx, acc[c]);
-        acc[4 + c] = fma(de, de, acc[4 + c]);
       }
     }
   }
-  for (int k = 0; k < 8; ++k) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
     double t = acc[k];
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5][k] = t;
   }
   __syncthreads();
-  if (threadIdx.x < 8) {
+  if (threadIdx.x < 4) {
     double t = 0.0;
     for (int w = 0; w < TPB / 32; ++w) t += sm[w][threadIdx.x];
-    part[blockIdx.x * 8 + threadIdx.x] = t;
+    part[blockIdx.x * 4 + threadIdx.x] = t;
   }
 }
 
-// one block: out[k] = sum over the blocks' partials (in block order) / div
+// one block: out[c] = (sum over the blocks' partials, in block order) / div
 __global__ void k_fit_reduce(const double* __restrict__ part, int nparts, double div, double* __restrict__ out) {
-  if (threadIdx.x >= 8) return;
+  if (threadIdx.x >= 4) return;
   double t = 0.0;
-  for (int b = 0; b < nparts; ++b) t += part[b * 8 + threadIdx.x];
+  for (int b = 0; b < nparts; ++b) t += part[b * 4 + threadIdx.x];
   out[threadIdx.x] = t / div;
 }
 
-// norm[20] = (mean of the fields, 0 x 4; 1/std of the fields, 1 x 4; std of e) from the means
-// (stats[0..8)) and variances (stats[8..16))
+// norm[20] = (mean of the fields, 0 x 4; 1/std of the fields, 1 x 4; 1 x 4) from the means
+// (stats[0..4)) and variances (stats[4..8))
 __global__ void k_fit_norm(const double* __restrict__ stats, float* __restrict__ norm, double* __restrict__ out20) {
   const int c = threadIdx.x;
   if (c >= 4) return;
-  const double mx = stats[c], sx = fmax(sqrt(stats[8 + c]), 1e-30), se = fmax(sqrt(stats[12 + c]), 1e-30);
-  const double vals[5] = {mx, 0.0, 1.0 / sx, 1.0, se};
+  const double vals[5] = {stats[c], 0.0, 1.0 / fmax(sqrt(stats[4 + c]), 1e-30), 1.0, 1.0};
   for (int k = 0; k < 5; ++k) {
     norm[4 * k + c] = (float)vals[k];
     out20[4 * k + c] = vals[k];
@@ -871,21 +861,22 @@ __global__ void k_fit_norm(const double* __restrict__ stats, float* __restrict__
 }
 
 template <typename F>
-static ch_status fit_norm_t(ch_ws_s* w, const F* q, const F* x, const F* n, int S, double* host20, cudaStream_t st) {
-  const int P = w->P;
-  const int64_t total = (int64_t)S * P;
+static ch_status fit_norm_t(ch_ws_s* w, const F* x, int S, double* host20, cudaStream_t st) {
+  const int64_t total = (int64_t)S * w->P;
+  if (total < 2) {
+    set_error("the normalisation needs at least two pixels of data");
+    return CH_ERR_ARG;
+  }
   Alloc tmp;
-  double *r = nullptr, *part = nullptr, *stats = nullptr, *out20 = nullptr;
-  CH_TRY(tmp.get(&r, (size_t)S * 4));
-  CH_TRY(tmp.get(&part, (size_t)FIT_BLOCKS * 8));
-  CH_TRY(tmp.get(&stats, 16));
+  double *part = nullptr, *stats = nullptr, *out20 = nullptr;
+  CH_TRY(tmp.get(&part, (size_t)FIT_BLOCKS * 4));
+  CH_TRY(tmp.get(&stats, 8));  // the fields' means [0, 4), variances [4, 8)
   CH_TRY(tmp.get(&out20, 20));
   const int nb = (int)std::min<int64_t>(FIT_BLOCKS, (total + TPB - 1) / TPB);
-  k_fit_r<F><<<S, TPB, 0, st>>>(x, q, P, r);
-  k_fit_sums<F, 0><<<nb, TPB, 0, st>>>(x, q, n, P, total, r, nullptr, part);
+  k_fit_sums<F, 0><<<nb, TPB, 0, st>>>(x, total, nullptr, part);
   k_fit_reduce<<<1, 32, 0, st>>>(part, nb, (double)total, stats);
-  k_fit_sums<F, 1><<<nb, TPB, 0, st>>>(x, q, n, P, total, r, stats, part);
-  k_fit_reduce<<<1, 32, 0, st>>>(part, nb, (double)(total - 1), stats + 8);
+  k_fit_sums<F, 1><<<nb, TPB, 0, st>>>(x, total, stats, part);
+  k_fit_reduce<<<1, 32, 0, st>>>(part, nb, (double)(total - 1), stats + 4);
   k_fit_norm<<<1, 32, 0, st>>>(stats, w->norm, out20);
   CH_LAUNCHED();
   CH_CUDA(cudaMemcpyAsync(host20, out20, sizeof(double) * 20, cudaMemcpyDeviceToHost, st));
@@ -893,13 +884,9 @@ static ch_status fit_norm_t(ch_ws_s* w, const F* q, const F* x, const F* n, int 
   return CH_OK;
 }
 
-ch_status ws_fit_norm(ch_ws_s* w, const void* q, const void* x, const void* n, int S, int fp32, double* host20,
-                      cudaStream_t st) {
-  if (fp32)
-    return fit_norm_t<float>(w, static_cast<const float*>(q), static_cast<const float*>(x),
-                             static_cast<const float*>(n), S, host20, st);
-  return fit_norm_t<double>(w, static_cast<const double*>(q), static_cast<const double*>(x),
-                            static_cast<const double*>(n), S, host20, st);
+ch_status ws_fit_norm(ch_ws_s* w, const void* x, int S, int fp32, double* host20, cudaStream_t st) {
+  if (fp32) return fit_norm_t<float>(w, static_cast<const float*>(x), S, host20, st);
+  return fit_norm_t<double>(w, static_cast<const double*>(x), S, host20, st);
 }
 
 int ws_nparam() { return WS_NPARAM; }

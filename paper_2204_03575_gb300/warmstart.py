@@ -1,10 +1,11 @@
 """Learned warm start: training data from the solver, training and use of the network.
 
 The network (``ch.WarmStartNet``, kernels in ``csrc/warmstart.cu``) predicts the state at step k+1
-from the states at steps k and k-1 on the nodal image of a 2D structured mesh, as a learned
-correction to the linear extrapolation 2 s_k - s_{k-1}; ``ch_step_guess`` takes the prediction as
-FGMRES's initial iterate wherever its true FP64 residual beats that of the previous state, so the
-FP64 residual decides between it and the previous step, which stays the fallback.
+from the states at steps k, k-1 and k-2 on the nodal image of a 2D structured mesh as a learned
+second-order extrapolation s_k + d + theta * D (d the last change, D the second difference, theta
+the network's output scaled per channel); ``ch_step_guess`` takes the prediction as FGMRES's
+initial iterate wherever its true FP64 residual beats that of the previous state, so the FP64
+residual decides between it and the previous step, which stays the fallback.
 
     data = generate_pairs(nx, ny, seeds=range(20), steps=100, dtype=torch.float64)  # plain solver
     net = ch.WarmStartNet(ny + 1, nx + 1, 8)
@@ -44,38 +45,44 @@ def make_system(nx: int, ny: int, **kw):
 
 def generate_pairs(nx: int, ny: int, seeds, steps: int, precision: int = 0, burn_in: int = 1,
                    dtype=torch.float32):
-    """(Q, X, Y): CUDA tensors (S, N, 4) of `dtype` holding consecutive states s_{k-1}, s_k,
-    s_{k+1} along the solver's own trajectories, `steps` triples per seed.  The first triple starts
-    `burn_in` steps after the initial state (whose chemical potentials the first step sets up)."""
-    qs, xs, ys = [], [], []
+    """(Q2, Q, X, Y): CUDA tensors (S, N, 4) of `dtype` holding consecutive states s_{k-2}, s_{k-1},
+    s_k, s_{k+1} along the solver's own trajectories, `steps` quadruples per seed.  The first
+    quadruple starts `burn_in` steps after the initial state (whose chemical potentials the first
+    step sets up)."""
+    q2s, qs, xs, ys = [], [], [], []
     state = make_state(nx, ny, precision)
     for seed in seeds:
         b0, b1 = seed_bases(seed)
         state.init_seeded(b0, b1, 0.01, seed=int(seed))
         for _ in range(burn_in):
             state.step()
-        prev = state.state4()
-        state.step()
-        cur = state.state4()
+        hist = [state.state4()]
+        for _ in range(2):
+            state.step()
+            hist.append(state.state4())
         for _ in range(steps):
             state.step()
             nxt = state.state4()
-            qs.append(prev.to(dtype))
-            xs.append(cur.to(dtype))
+            q2s.append(hist[-3].to(dtype))
+            qs.append(hist[-2].to(dtype))
+            xs.append(hist[-1].to(dtype))
             ys.append(nxt.to(dtype))
-            prev, cur = cur, nxt
-    return torch.stack(qs), torch.stack(xs), torch.stack(ys)
+            hist = hist[-2:] + [nxt]
+    return torch.stack(q2s), torch.stack(qs), torch.stack(xs), torch.stack(ys)
 
 
 def init_params(nparams: int, seed: int = 0):
-    """He-uniform initial weights (zero biases) in the library's parameter layout."""
+    """He-uniform initial weights in the library's parameter layout, zero biases but for the output
+    bias of the four used channels, 1: with out_scale 1 the network starts close to theta = 1,
+    quadratic extrapolation."""
     rng = np.random.default_rng(seed)
-    layers = [(9 * 16 * 32, 9 * 8, 32), (9 * 32 * 32, 9 * 32, 32), (9 * 32 * 8, 9 * 32, 8)]
+    layers = [(9 * 16 * 32, 9 * 12, 32), (9 * 32 * 32, 9 * 32, 32), (9 * 32 * 8, 9 * 32, 8)]
     out = []
     for i, (n, fan_in, nb) in enumerate(layers):
-        lim = np.sqrt(6.0 / fan_in) * (0.1 if i == 2 else 1.0)  # start close to pure extrapolation
+        lim = np.sqrt(6.0 / fan_in) * (0.1 if i == 2 else 1.0)  # start close to theta = 1
         out.append(rng.uniform(-lim, lim, n))
         out.append(np.zeros(nb))
+    out[-1][:4] = 1.0
     theta = np.concatenate(out).astype(np.float32)
     assert theta.size == nparams
     return theta
@@ -83,13 +90,13 @@ def init_params(nparams: int, seed: int = 0):
 
 def train(data, net, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: int = 0,
           use_fields: bool = True, lap: float = 0.0):
-    """Fit `net` (a ch.WarmStartNet sized for the mesh) to the correction of the linear
-    extrapolation on `data` = (Q, X, Y) from generate_pairs.  With use_fields=False the field
-    channels are switched off (scale 0) and the network sees only the change; `lap` weighs the
-    grid-Laplacian term of the loss.  Returns (net, info)."""
-    Q, X, Y = data
+    """Fit `net` (a ch.WarmStartNet sized for the mesh) to the next states in state space on
+    `data` = (Q2, Q, X, Y) from generate_pairs.  With use_fields=False the field channels are
+    switched off (scale 0) and the network sees only the change and the second difference; `lap`
+    weighs the grid-Laplacian term of the loss.  Returns (net, info)."""
+    Q2, Q, X, Y = data
     S, N = X.shape[0], X.shape[1]
-    mean, inv_std, out_scale = net.fit_norm(Q, X, Y)  # computed on the device by the library
+    mean, inv_std, out_scale = net.fit_norm(X)  # computed on the device by the library
     if not use_fields:
         mean[:4], inv_std[:4] = 0.0, 0.0
         net.set_norm(mean, inv_std, out_scale)
@@ -102,7 +109,8 @@ def train(data, net, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: in
         tot, nb = 0.0, 0
         for i in range(0, S - batch + 1, batch):
             idx = perm[i:i + batch].to(X.device)
-            tot += net.train_step(X[idx].contiguous(), Q[idx].contiguous(), Y[idx].contiguous(), lr_ep, lap=lap)
+            tot += net.train_step(X[idx].contiguous(), Q[idx].contiguous(), Q2[idx].contiguous(), Y[idx].contiguous(),
+                                  lr_ep, lap=lap)
             nb += 1
         losses.append(tot / max(nb, 1))
     return net, {"loss_per_epoch": losses, "mean": mean.tolist(), "inv_std": inv_std.tolist(),
@@ -112,12 +120,12 @@ def train(data, net, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: in
 def train_residual(data, net, system, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: int = 0,
                    use_fields: bool = True, precond=None):
     """Fit `net` against the residual of the time step (ch_ws_train_residual) on fp64 `data` =
-    (Q, X, Y) from generate_pairs(..., dtype=torch.float64); Y only sets the normalisation.
+    (Q2, Q, X, Y) from generate_pairs(..., dtype=torch.float64); Y only sets the normalisation.
     With `precond` (a ch.Precond of `system`) the residual is measured in its norm.  The per-epoch
-    loss is the mean |r|^2 / |r_extrapolation|^2: below 1 beats extrapolation."""
-    Q, X, Y = data
+    loss is the mean ln(|r|^2 / |r_linear extrapolation|^2): below 0 beats linear extrapolation."""
+    Q2, Q, X, Y = data
     S, N = X.shape[0], X.shape[1]
-    mean, inv_std, out_scale = net.fit_norm(Q, X, Y)  # computed on the device by the library
+    mean, inv_std, out_scale = net.fit_norm(X)  # computed on the device by the library
     if not use_fields:
         mean[:4], inv_std[:4] = 0.0, 0.0
         net.set_norm(mean, inv_std, out_scale)
@@ -130,7 +138,8 @@ def train_residual(data, net, system, epochs: int = 8, batch: int = 8, lr: float
         tot, nb = 0.0, 0
         for i in range(0, S - batch + 1, batch):
             idx = perm[i:i + batch].to(X.device)
-            tot += net.train_residual(system, X[idx].contiguous(), Q[idx].contiguous(), lr_ep, precond=precond)
+            tot += net.train_residual(system, X[idx].contiguous(), Q[idx].contiguous(), Q2[idx].contiguous(), lr_ep,
+                                      precond=precond)
             nb += 1
         losses.append(tot / max(nb, 1))
     return net, {"loss_per_epoch": losses, "mean": mean.tolist(), "inv_std": inv_std.tolist(),
@@ -138,16 +147,27 @@ def train_residual(data, net, system, epochs: int = 8, batch: int = 8, lr: float
 
 
 def zero_net(nx: int, ny: int):
-    """A network whose correction is zero: its prediction is the linear extrapolation 2 s_k - s_{k-1}."""
+    """A network whose output is zero: its prediction is the linear extrapolation 2 s_k - s_{k-1}."""
     net = ch.WarmStartNet(ny + 1, nx + 1, max_batch=1)
     net.set_params(np.zeros(net.nparams, np.float32))
+    return net
+
+
+def quadratic_net(nx: int, ny: int):
+    """A network whose theta is 1 everywhere (zero weights, output bias 1, out_scale 1): its
+    prediction is the quadratic extrapolation 3 s_k - 3 s_{k-1} + s_{k-2}."""
+    net = ch.WarmStartNet(ny + 1, nx + 1, max_batch=1)
+    theta = np.zeros(net.nparams, np.float32)
+    theta[-8:-4] = 1.0
+    net.set_params(theta)
+    net.set_norm(np.zeros(8), np.ones(8), np.ones(4))
     return net
 
 
 def run_steps(nx: int, ny: int, seed: int, steps: int, net=None, extrapolate: bool = False,
               precision: int = 0, warm_up: int = 0):
     """Advance a seeded run; return per-step stats.  With `net`, every step is ch_step_learned
-    (the network's prediction where it beats the previous state, from the third step on); with
+    (the network's prediction where it beats the previous state, from the fourth step on); with
     `extrapolate`, the same with the zero network, i.e. the guess 2 s_k - s_{k-1}."""
     state = make_state(nx, ny, precision)
     b0, b1 = seed_bases(seed)
