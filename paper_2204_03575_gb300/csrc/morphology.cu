@@ -14,8 +14,10 @@
 // count, so it is formed once per pixel: a block takes 8 image columns, splits the rows into 32
 // segments, and forms the parity of sum_{j >= j0} c_j for every pixel by a suffix XOR (within each
 // segment while walking down it, then across the segments), held as bytes in shared memory; the
-// block then writes every grid point whose pixel lies in its columns.  Images too tall for shared
-// memory use one thread per grid point walking its ray instead (the same count).
+// block then writes the grid points of its share of the grid rows whose pixel lies in its columns.
+// Images too tall for shared memory, or grids much finer than the image, use one thread per grid
+// point walking its ray instead (the same count).
+#include <algorithm>
 #include <cmath>
 
 #include "ch_internal.cuh"
@@ -61,6 +63,7 @@ __global__ void k_ray_parity(const double* __restrict__ pp, const double* __rest
 
 constexpr int MP_COLS = 8, MP_SEGS = 32;        // block: image columns x row segments
 constexpr int MP_MAX_SMEM = 160 * 1024;          // parity bytes per block: MP_COLS x (ny + 1)
+constexpr int MP_MAXK = 2048, MP_MAXL = 1024;    // grid columns / rows one block writes (scan form)
 
 __device__ __forceinline__ int pixel_of(int k, int g, double L, int n) {  // pixel index of grid index k
   const double x = (k + 0.5) * (L / g), h = L / n;
@@ -99,21 +102,37 @@ __global__ void __launch_bounds__(MP_COLS * MP_SEGS) k_ray_parity_scan(
   if (i <= nx && carry)
     for (int j = ja; j < jb; ++j) col[j] ^= 1;
   __syncthreads();
-  // 3. the grid points whose pixel column is in [i0, i0 + MP_COLS): grid columns [k0, k1)
-  const int ilast = min(nx, i0 + MP_COLS - 1);
-  int k0 = (int)floor(((i0 - 0.5) * (Lx / nx)) / (Lx / gx) - 0.5);
-  int k1 = (int)ceil(((ilast + 0.5) * (Lx / nx)) / (Lx / gx) + 0.5);
-  k0 = max(0, k0 - 1);
-  k1 = min(gx, k1 + 1);
-  while (k0 < k1 && pixel_of(k0, gx, Lx, nx) < i0) ++k0;   // exact bounds by the same formula
-  while (k1 > k0 && pixel_of(k1 - 1, gx, Lx, nx) > ilast) --k1;
-  const int nk = k1 - k0;
-  if (nk <= 0) return;
-  for (int64_t t = threadIdx.x; t < (int64_t)nk * gy; t += blockDim.x) {
-    const int l = (int)(t / nk), k = k0 + (int)(t % nk);
-    const int ip = pixel_of(k, gx, Lx, nx), jp = pixel_of(l, gy, Ly, ny);
-    const bool inside = par[(ip - i0) * rows + jp] & 1;
-    const int64_t o = (int64_t)l * gx + k;
+  // 3. the grid points whose pixel column is in [i0, i0 + MP_COLS): grid columns [k0, k1), rows of
+  // this block's share (blockIdx.y); pixel indices of its columns and rows formed once into
+  // shared memory (the same floor formula as the classification, so the bounds are exact)
+  // (one thread finds the column range: FP64 divisions are costly on this part's FP64 pipe)
+  __shared__ int krange[2];
+  if (threadIdx.x == 0) {
+    const int ilast = min(nx, i0 + MP_COLS - 1);
+    int a = (int)floor(((i0 - 0.5) * (Lx / nx)) / (Lx / gx) - 0.5);
+    int b = (int)ceil(((ilast + 0.5) * (Lx / nx)) / (Lx / gx) + 0.5);
+    a = max(0, a - 1);
+    b = min(gx, b + 1);
+    while (a < b && pixel_of(a, gx, Lx, nx) < i0) ++a;
+    while (b > a && pixel_of(b - 1, gx, Lx, nx) > ilast) --b;
+    krange[0] = a;
+    krange[1] = b;
+  }
+  __syncthreads();
+  const int k0 = krange[0];
+  const int nk = min(krange[1] - k0, MP_MAXK);
+  const int rows_per = (gy + gridDim.y - 1) / gridDim.y;
+  const int l0 = blockIdx.y * rows_per, l1 = min(gy, l0 + rows_per);
+  const int nl = min(l1 - l0, MP_MAXL);
+  __shared__ int ipix[MP_MAXK], jpix[MP_MAXL];
+  for (int t = threadIdx.x; t < nk; t += blockDim.x) ipix[t] = pixel_of(k0 + t, gx, Lx, nx) - i0;
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) jpix[t] = pixel_of(l0 + t, gy, Ly, ny);
+  __syncthreads();
+  if (nk <= 0 || nl <= 0) return;
+  for (int64_t t = threadIdx.x; t < (int64_t)nk * nl; t += blockDim.x) {
+    const int l = (int)(t / nk), kk = (int)(t % nk);
+    const bool inside = par[ipix[kk] * rows + jpix[l]] & 1;
+    const int64_t o = (int64_t)(l0 + l) * gx + k0 + kk;
     if (polymer) polymer[o] = inside;
     if (mu_e) mu_e[o] = inside ? MU_LOW : MU_HIGH;
     if (mu_h) mu_h[o] = inside ? MU_HIGH : MU_LOW;
@@ -126,11 +145,15 @@ ch_status morphology_project(const double* pp, const double* pn, int nx, int ny,
   const int64_t G = (int64_t)gx * gy;
   const size_t smem = (size_t)MP_COLS * (ny + 1);
   ProfScope ps(st, K_MORPH, 0, (double)G * (1.0 + 16.0) + 16.0 * (double)(nx + 1) * (ny + 1), 0.0);
-  if (smem <= (size_t)MP_MAX_SMEM) {
+  // grid columns per block of 8 image columns: 8 gx / nx (+2 at the edges); rows split over blockIdx.y
+  const double kper = (double)MP_COLS * gx / nx + 4.0;
+  const int ychunks = (gy + MP_MAXL - 1) / MP_MAXL;
+  const int cols_blocks = (nx + 1 + MP_COLS - 1) / MP_COLS;
+  const int yblocks = std::max(ychunks, std::min((gy + 63) / 64, (2 * 152 + cols_blocks - 1) / cols_blocks));
+  if (smem <= (size_t)MP_MAX_SMEM && kper <= MP_MAXK) {
     CH_CUDA(cudaFuncSetAttribute(k_ray_parity_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_MAX_SMEM));
-    const int blocks = (nx + 1 + MP_COLS - 1) / MP_COLS;
-    k_ray_parity_scan<<<blocks, MP_COLS * MP_SEGS, smem, st>>>(pp, pn, nx, ny, Lx, Ly, use_thr, thr, gx, gy,
-                                                                 polymer, mu_e, mu_h);
+    k_ray_parity_scan<<<dim3(cols_blocks, yblocks), MP_COLS * MP_SEGS, smem, st>>>(
+        pp, pn, nx, ny, Lx, Ly, use_thr, thr, gx, gy, polymer, mu_e, mu_h);
   } else {
     k_ray_parity<<<(unsigned)((G + TPB - 1) / TPB), TPB, 0, st>>>(pp, pn, nx, ny, Lx, Ly, use_thr, thr, gx, gy,
                                                                    polymer, mu_e, mu_h);
