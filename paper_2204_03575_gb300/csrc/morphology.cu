@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(MP_COLS * MP_SEGS) k_ray_parity_scan(
   for (int t = threadIdx.x; t < nl; t += blockDim.x) jpix[t] = pixel_of(l0 + t, gy, Ly, ny);
   __syncthreads();
   if (nk <= 0 || nl <= 0) return;
-  for (int64_t t = threadIdx.x; t < (int64_t)nk * nl; t += blockDim.x) {
-    const int l = (int)(t / nk), kk = (int)(t % nk);
+  for (int t = threadIdx.x; t < nk * nl; t += blockDim.x) {  // nk * nl <= MP_MAXK * MP_MAXL
+    const int l = t / nk, kk = t - l * nk;
     const bool inside = par[ipix[kk] * rows + jpix[l]] & 1;
     const int64_t o = (int64_t)(l0 + l) * gx + k0 + kk;
     if (polymer) polymer[o] = inside;
