@@ -114,6 +114,11 @@ typedef struct ch_params {
   double N_p, N_nfa, N_s;    /* degrees of polymerisation (potential = 3); default 20, 20, 1 (Section 4) */
   double fh_delta;           /* potential = 3: each logarithm is taken at max(phi, fh_delta) (a
                                 positivity guard; concentrations may dip below 0), default 1e-10 */
+  int32_t pdl;               /* 1 (default): the V-cycle and Krylov kernels are launched as programmatic
+                                dependents -- each kernel's blocks are scheduled while its predecessor
+                                drains and wait on the device for its results (griddepcontrol), which
+                                hides the launch gap between the many short kernels of a step; 0: plain
+                                stream-ordered launches.  Same arithmetic, bitwise the same results */
 } ch_params;
 
 /* Per-step statistics (host struct). */

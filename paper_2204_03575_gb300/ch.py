@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
         ("precond_M", ctypes.c_int32), ("cheb_M_steps", ctypes.c_int32),
         ("chi_pn", ctypes.c_double), ("chi_ps", ctypes.c_double), ("chi_ns", ctypes.c_double),
         ("N_p", ctypes.c_double), ("N_nfa", ctypes.c_double), ("N_s", ctypes.c_double),
-        ("fh_delta", ctypes.c_double),
+        ("fh_delta", ctypes.c_double), ("pdl", ctypes.c_int32),
     ]
 
     def __init__(self, **kw):

@@ -56,6 +56,7 @@ struct LevelT {
   Csr<T> A, P, R;
   Dia<T> dia;                          // level 0 of a structured mesh
   int tprA = 1, tprP = 1, tprR = 1;  // lanes per row of the SpMV-type kernels (autotuned)
+  bool pdl = false;                  // launch the V-cycle kernels as programmatic dependents
   T* dinv = nullptr;
   typename V2T<T>::t *x = nullptr, *x2 = nullptr, *d = nullptr, *r = nullptr, *b = nullptr;
 };
@@ -76,6 +77,7 @@ struct Hierarchy {
   int cheb_degree_coarse = 2;         // on the levels below the finest
   double cheb_lower = 0.3;
   int autotune = 1;
+  bool pdl = true;
   Alloc mem;
 };
 
@@ -563,9 +565,9 @@ static ch_status level_setup(Hierarchy* h, int l, const ch_params& p, cudaStream
 
 template <typename T, typename V2>
 static void launch_residual(int tpr, const Csr<T>& A, const V2* b, const V2* x, V2* r, cudaStream_t st,
-                            const Dia<T>* dia = nullptr);
+                            const Dia<T>* dia = nullptr, bool pdl = false);
 template <typename T, typename V2, bool ACC>
-static void launch_spmv2(int tpr, const Csr<T>& A, const V2* x, V2* y, cudaStream_t st);
+static void launch_spmv2(int tpr, const Csr<T>& A, const V2* x, V2* y, cudaStream_t st, bool pdl = false);
 
 // ---------------------------------------------------------------- SpMV tile autotuner
 // Lanes per row (1..32) for each matrix the V-cycle multiplies by: A (smoother steps and
@@ -767,7 +769,9 @@ static ch_status make_working(Hierarchy* h, const FineLattice* lat, std::vector<
     CH_TRY(h->mem.get(&w.d, (size_t)n));
     CH_TRY(h->mem.get(&w.r, (size_t)n));
     CH_TRY(h->mem.get(&w.b, (size_t)n));
+    w.pdl = h->pdl;
   }
+
   // the fine level of a uniform mesh in diagonal form
   Dia<double> d64;
   CH_TRY(dia_build(h->A[0], lat, h->mem, &d64, st));
@@ -801,6 +805,7 @@ ch_status hierarchy_build(const Csr<double>& A0, const FineLattice* lat, const c
   // steps/s for coarse degrees 2 / 3 / 4
   h->cheb_degree_coarse = p.cheb_degree_coarse > 0 ? p.cheb_degree_coarse : std::min(2, p.cheb_degree);
   h->autotune = p.autotune;
+  h->pdl = p.pdl != 0;
   h->cheb_lower = p.cheb_lower;
   h->A.push_back(A0);
   ch_status s = CH_OK;
@@ -932,6 +937,17 @@ ch_status hierarchy_level_export(const Hierarchy* h, int l, int64_t* rows, int64
 }
 
 // ---------------------------------------------------------------- V-cycle kernels (2 RHS)
+// When a V-cycle kernel lets its successor be scheduled (programmatic dependent launch): right
+// after its dependency wait in FP32, where the kernels are short and bound by latency, so the
+// successor's blocks are resident when it finishes; not at all in FP64, where the kernels are
+// bound by the FP64 pipe and successor blocks that arrive early crowd the SMs unevenly.  Measured
+// on the 512 x 512 mesh, ms per time step: FP32 V-cycles 8.33 plain, 8.06 without the trigger,
+// 7.96 with it; FP64 V-cycles 16.90 plain, 16.78 without, 17.70 with it.
+template <typename T>
+__device__ __forceinline__ void pdl_trigger_t() {
+  if (sizeof(T) == 4) pdl_trigger();
+}
+
 template <typename T, typename V2>
 __device__ __forceinline__ V2 mk2(T a, T b) {
   V2 v;
@@ -944,8 +960,11 @@ __device__ __forceinline__ V2 mk2(T a, T b) {
 template <typename T, typename V2>
 __global__ void k_cheb_first(int n, const T* dinv, const V2* b, T invtheta, V2* x, V2* d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const T di = i < n ? dinv[i] : T(0);  // set-up data: read before the dependency wait
+  pdl_wait();
+  pdl_trigger_t<T>();
   if (i >= n) return;
-  const T s = invtheta * dinv[i];
+  const T s = invtheta * di;
   const V2 bi = b[i];
   const V2 v = mk2<T, V2>(s * bi.x, s * bi.y);
   x[i] = v;
@@ -994,6 +1013,8 @@ __global__ void __launch_bounds__(TPB) k_cheb_step(Csr<T> A, const T* __restrict
                                                    T nbeta) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / TPR, sub = t % TPR;
+  pdl_wait();
+  pdl_trigger_t<T>();
   T s0 = 0, s1 = 0;
   if (sub == 0 && i < A.nrows) {
     const V2 bi = b[i];
@@ -1020,6 +1041,8 @@ __global__ void __launch_bounds__(TPB) k_residual(Csr<T> A, const V2* __restrict
                                                   const V2* __restrict__ x, V2* __restrict__ r) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / TPR, sub = t % TPR;
+  pdl_wait();
+  pdl_trigger_t<T>();
   T s0, s1;
   row_sum<T, V2, TPR>(A, i, sub, x, s0, s1);
   if (i >= A.nrows || sub != 0) return;
@@ -1032,6 +1055,8 @@ template <typename T, typename V2, int TPR, bool ACC>
 __global__ void __launch_bounds__(TPB) k_spmv2(Csr<T> A, const V2* __restrict__ x, V2* __restrict__ y) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / TPR, sub = t % TPR;
+  pdl_wait();
+  pdl_trigger_t<T>();
   T s0, s1;
   row_sum<T, V2, TPR>(A, i, sub, x, s0, s1);
   if (i >= A.nrows || sub != 0) return;
@@ -1044,33 +1069,40 @@ __global__ void __launch_bounds__(TPB) k_spmv2(Csr<T> A, const V2* __restrict__ 
 }
 
 // ---------------------------------------------------------------- structured (diagonal) fine level
-// Row sum of the lattice form onto the caller's (s0, s1) (zero, or -b for a residual's negative).
-template <typename T, typename V2, int ND>
-__device__ __forceinline__ void dia_row_acc(const Dia<T>& D, int n, int i, const V2* __restrict__ x, T& s0,
-                                            T& s1) {
-  int W = D.W, WH = D.WH;
+// One row of the lattice form: its ND operator values and its run's strides (set-up data, so the
+// kernels read them before their dependency wait).
+template <typename T, int ND>
+struct DiaRow {
+  T a[ND];
+  int W, WH;
+};
+template <typename T, int ND>
+__device__ __forceinline__ DiaRow<T, ND> dia_row(const Dia<T>& D, int n, int i) {
+  DiaRow<T, ND> r;
+  r.W = D.W;
+  r.WH = D.WH;
   if (D.node_run) {
     const int2 w = D.run_wh[D.node_run[i]];
-    W = w.x;
-    WH = w.y;
+    r.W = w.x;
+    r.WH = w.y;
   }
 #pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    int j = i + lat_off(ND, d, W, WH);
-    j = j < 0 ? 0 : (j >= n ? n - 1 : j);
-    const T a = D.val[(size_t)d * n + i];
-    const V2 xj = x[j];
-    s0 = fma(a, xj.x, s0);
-    s1 = fma(a, xj.y, s1);
-  }
+  for (int d = 0; d < ND; ++d) r.a[d] = D.val[(size_t)d * n + i];
+  return r;
 }
 
+// Row sum of the lattice form onto the caller's (s0, s1) (zero, or -b for a residual's negative).
 template <typename T, typename V2, int ND>
-__device__ __forceinline__ void dia_row_sum(const Dia<T>& D, int n, int i, const V2* __restrict__ x, T& s0,
-                                            T& s1) {
-  s0 = 0;
-  s1 = 0;
-  dia_row_acc<T, V2, ND>(D, n, i, x, s0, s1);
+__device__ __forceinline__ void dia_row_acc(const DiaRow<T, ND>& r, int n, int i, const V2* __restrict__ x,
+                                            T& s0, T& s1) {
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    int j = i + lat_off(ND, d, r.W, r.WH);
+    j = j < 0 ? 0 : (j >= n ? n - 1 : j);
+    const V2 xj = x[j];
+    s0 = fma(r.a[d], xj.x, s0);
+    s1 = fma(r.a[d], xj.y, s1);
+  }
 }
 
 // k_cheb_step on the lattice form (same arithmetic: the sum starts from -b, nbeta = -beta)
@@ -1079,12 +1111,19 @@ __global__ void __launch_bounds__(TPB) k_cheb_step_dia(Dia<T> D, int n, const T*
                                                        const V2* __restrict__ b, const V2* __restrict__ x,
                                                        V2* __restrict__ d, V2* __restrict__ xo, T alpha, T nbeta) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  DiaRow<T, ND> row;
+  T di = 0;
+  if (i < n) {
+    row = dia_row<T, ND>(D, n, i);
+    di = dinv[i] * nbeta;
+  }
+  pdl_wait();
+  pdl_trigger_t<T>();
   if (i >= n) return;
   const V2 bi = b[i];
   T s0 = -bi.x, s1 = -bi.y;
-  dia_row_acc<T, V2, ND>(D, n, i, x, s0, s1);
+  dia_row_acc<T, V2, ND>(row, n, i, x, s0, s1);
   const V2 xi = x[i];
-  const T di = dinv[i] * nbeta;
   V2 dd;
   if (alpha != T(0)) {
     const V2 dold = d[i];
@@ -1100,9 +1139,13 @@ template <typename T, typename V2, int ND>
 __global__ void __launch_bounds__(TPB) k_residual_dia(Dia<T> D, int n, const V2* __restrict__ b,
                                                       const V2* __restrict__ x, V2* __restrict__ r) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  DiaRow<T, ND> row;
+  if (i < n) row = dia_row<T, ND>(D, n, i);
+  pdl_wait();
+  pdl_trigger_t<T>();
   if (i >= n) return;
-  T s0, s1;
-  dia_row_sum<T, V2, ND>(D, n, i, x, s0, s1);
+  T s0 = 0, s1 = 0;
+  dia_row_acc<T, V2, ND>(row, n, i, x, s0, s1);
   const V2 bi = b[i];
   r[i] = mk2<T, V2>(bi.x - s0, bi.y - s1);
 }
@@ -1110,9 +1153,13 @@ __global__ void __launch_bounds__(TPB) k_residual_dia(Dia<T> D, int n, const V2*
 template <typename T, typename V2, int ND>
 __global__ void __launch_bounds__(TPB) k_spmv2_dia(Dia<T> D, int n, const V2* __restrict__ x, V2* __restrict__ y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  DiaRow<T, ND> row;
+  if (i < n) row = dia_row<T, ND>(D, n, i);
+  pdl_wait();
+  pdl_trigger_t<T>();
   if (i >= n) return;
-  T s0, s1;
-  dia_row_sum<T, V2, ND>(D, n, i, x, s0, s1);
+  T s0 = 0, s1 = 0;
+  dia_row_acc<T, V2, ND>(row, n, i, x, s0, s1);
   y[i] = mk2<T, V2>(s0, s1);
 }
 
@@ -1130,6 +1177,8 @@ __global__ void __launch_bounds__(TPB) k_restrict_first(Csr<T> R, const V2* __re
                                                         V2* __restrict__ xc, V2* __restrict__ dc) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / TPR, sub = t % TPR;
+  pdl_wait();
+  pdl_trigger_t<T>();
   T s0, s1;
   row_sum<T, V2, TPR>(R, i, sub, r, s0, s1);
   if (i >= R.nrows || sub != 0) return;
@@ -1153,42 +1202,44 @@ __global__ void __launch_bounds__(TPB) k_restrict_first(Csr<T> R, const V2* __re
 // one Chebyshev step d = alpha d + beta D^-1 (b - A x), xo = x + d (the kernels take -beta)
 template <typename T, typename V2>
 static void launch_cheb_step(int tpr, const Csr<T>& A, const T* dinv, const V2* b, const V2* x, V2* d,
-                             V2* xo, T alpha, T beta, cudaStream_t st, const Dia<T>* dia = nullptr) {
+                             V2* xo, T alpha, T beta, cudaStream_t st, const Dia<T>* dia = nullptr,
+                             bool pdl = false) {
   const T nbeta = -beta;
   if (dia && dia->nd) {
     const int g = blocks_for(A.nrows);
-    CH_DIA_DISPATCH(dia->nd, (k_cheb_step_dia<T, V2, NDC><<<g, TPB, 0, st>>>(*dia, A.nrows, dinv, b, x, d, xo,
-                                                                              alpha, nbeta)));
+    CH_DIA_DISPATCH(dia->nd, (launch_k(pdl, k_cheb_step_dia<T, V2, NDC>, g, TPB, 0, st, *dia, A.nrows, dinv, b,
+                                       x, d, xo, alpha, nbeta)));
     return;
   }
   const int g = blocks_for((int64_t)A.nrows * tpr);
-  CH_TPR_DISPATCH(tpr, (k_cheb_step<T, V2, TPRC><<<g, TPB, 0, st>>>(A, dinv, b, x, d, xo, alpha, nbeta)));
+  CH_TPR_DISPATCH(tpr, (launch_k(pdl, k_cheb_step<T, V2, TPRC>, g, TPB, 0, st, A, dinv, b, x, d, xo, alpha,
+                                 nbeta)));
 }
 template <typename T, typename V2>
 static void launch_residual(int tpr, const Csr<T>& A, const V2* b, const V2* x, V2* r, cudaStream_t st,
-                            const Dia<T>* dia) {
+                            const Dia<T>* dia, bool pdl) {
   if (dia && dia->nd) {
     const int g = blocks_for(A.nrows);
-    CH_DIA_DISPATCH(dia->nd, (k_residual_dia<T, V2, NDC><<<g, TPB, 0, st>>>(*dia, A.nrows, b, x, r)));
+    CH_DIA_DISPATCH(dia->nd, (launch_k(pdl, k_residual_dia<T, V2, NDC>, g, TPB, 0, st, *dia, A.nrows, b, x, r)));
     return;
   }
   const int g = blocks_for((int64_t)A.nrows * tpr);
-  CH_TPR_DISPATCH(tpr, (k_residual<T, V2, TPRC><<<g, TPB, 0, st>>>(A, b, x, r)));
+  CH_TPR_DISPATCH(tpr, (launch_k(pdl, k_residual<T, V2, TPRC>, g, TPB, 0, st, A, b, x, r)));
 }
 // y = A x with the level's operator (the diagonal form where there is one)
 template <typename T, typename V2>
 static void launch_apply_level(const LevelT<T>& L, const V2* x, V2* y, cudaStream_t st) {
   if (L.dia.nd) {
     const int g = blocks_for(L.A.nrows);
-    CH_DIA_DISPATCH(L.dia.nd, (k_spmv2_dia<T, V2, NDC><<<g, TPB, 0, st>>>(L.dia, L.A.nrows, x, y)));
+    CH_DIA_DISPATCH(L.dia.nd, (launch_k(L.pdl, k_spmv2_dia<T, V2, NDC>, g, TPB, 0, st, L.dia, L.A.nrows, x, y)));
     return;
   }
-  launch_spmv2<T, V2, false>(L.tprA, L.A, x, y, st);
+  launch_spmv2<T, V2, false>(L.tprA, L.A, x, y, st, L.pdl);
 }
 template <typename T, typename V2, bool ACC>
-static void launch_spmv2(int tpr, const Csr<T>& A, const V2* x, V2* y, cudaStream_t st) {
+static void launch_spmv2(int tpr, const Csr<T>& A, const V2* x, V2* y, cudaStream_t st, bool pdl) {
   const int g = blocks_for((int64_t)A.nrows * tpr);
-  CH_TPR_DISPATCH(tpr, (k_spmv2<T, V2, TPRC, ACC><<<g, TPB, 0, st>>>(A, x, y)));
+  CH_TPR_DISPATCH(tpr, (launch_k(pdl, k_spmv2<T, V2, TPRC, ACC>, g, TPB, 0, st, A, x, y)));
 }
 
 // x = Ainv b, dense nc x nc, one warp per row
@@ -1196,6 +1247,8 @@ template <typename T, typename V2>
 __global__ void k_dense_solve(int n, const T* inv, const V2* b, V2* x) {
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  pdl_wait();
+  pdl_trigger_t<T>();
   if (row >= n) return;
   T s0 = 0, s1 = 0;
   for (int j = lane; j < n; j += 32) {
@@ -1215,6 +1268,8 @@ __global__ void k_dense_solve(int n, const T* inv, const V2* b, V2* x) {
 template <typename T, typename V2>
 __global__ void k_load2(int n, const double* src, int ld, V2* dst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger_t<T>();
   if (i >= n) return;
   const double2 v = *reinterpret_cast<const double2*>(src + (size_t)i * ld);
   dst[i] = mk2<T, V2>((T)v.x, (T)v.y);
@@ -1222,6 +1277,8 @@ __global__ void k_load2(int n, const double* src, int ld, V2* dst) {
 template <typename T, typename V2>
 __global__ void k_store2(int n, const V2* src, double* dst, int ld) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger_t<T>();
   if (i >= n) return;
   const V2 v = src[i];
   *reinterpret_cast<double2*>(dst + (size_t)i * ld) = make_double2((double)v.x, (double)v.y);
@@ -1271,7 +1328,7 @@ static ch_status smooth_coef(LevelT<T_>& L, const ChebCoef& c, int deg, int zero
   const double T = sizeof(T_), nnz = (double)L.A.nnz;
   if (zero_guess == 1) {
     ProfScope ps(st, kfirst, sizeof(T_) == 4, 7.0 * T * n, 2.0 * n);
-    k_cheb_first<T_, V2><<<blocks_for(n), TPB, 0, st>>>(n, L.dinv, L.b, (T_)c.invtheta, x, L.d);
+    launch_k(L.pdl, k_cheb_first<T_, V2>, blocks_for(n), TPB, 0, st, n, L.dinv, L.b, (T_)c.invtheta, x, L.d);
     s0 = 1;
   } else if (zero_guess == 2) {
     s0 = 1;
@@ -1281,7 +1338,7 @@ static ch_status smooth_coef(LevelT<T_>& L, const ChebCoef& c, int deg, int zero
   for (int s = s0; s < deg; ++s) {
     ProfScope ps(st, kstep, sizeof(T_) == 4, opb + T * n * (c.alpha[s] != 0.0 ? 11 : 9), 2.0 * nnz + 4.0 * n);
     launch_cheb_step<T_, V2>(L.tprA, L.A, L.dinv, L.b, x, L.d, other, (T_)c.alpha[s], (T_)c.beta[s], st,
-                             &L.dia);
+                             &L.dia, L.pdl);
     std::swap(x, other);
   }
   CH_LAUNCHED();
@@ -1320,7 +1377,7 @@ static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv,
   const double Tb = sizeof(T);
   if (l == h->nlev - 1) {
     ProfScope ps(st, K_COARSE, sizeof(T) == 4, Tb * n * (double)n + 4.0 * Tb * n, 2.0 * n * (double)n);
-    k_dense_solve<T, V2><<<blocks_for((int64_t)n * 32), TPB, 0, st>>>(n, cinv, L.b, L.x);
+    launch_k(L.pdl, k_dense_solve<T, V2>, blocks_for((int64_t)n * 32), TPB, 0, st, n, cinv, L.b, L.x);
     CH_LAUNCHED();
     *xres = L.x;
     return CH_OK;
@@ -1332,7 +1389,7 @@ static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv,
   {
     const double opb = L.dia.nd ? Tb * L.dia.nd * (double)n : L.A.nnz * (4 + Tb) + 4.0 * (n + 1);
     ProfScope ps(st, l == 0 ? K_VRESIDUAL : K_VRESIDUAL_C, sizeof(T) == 4, opb + 6.0 * Tb * n, 2.0 * L.A.nnz);
-    launch_residual<T, V2>(L.tprA, L.A, L.b, x, L.r, st, &L.dia);
+    launch_residual<T, V2>(L.tprA, L.A, L.b, x, L.r, st, &L.dia, L.pdl);
   }
   const bool fuse = l + 1 < h->nlev - 1;  // the coarse level smooths: fuse its first step
   {
@@ -1343,10 +1400,10 @@ static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv,
       const int degc = h->cheb_degree_coarse;
       const ChebCoef cc = cheb_coef(h->rho[l + 1], degc, h->cheb_lower);
       const int g = blocks_for((int64_t)L.R.nrows * L.tprR);
-      CH_TPR_DISPATCH(L.tprR, (k_restrict_first<T, V2, TPRC><<<g, TPB, 0, st>>>(
-                                  L.R, L.r, C.b, C.dinv, (T)cc.invtheta, C.x, C.d)));
+      CH_TPR_DISPATCH(L.tprR, (launch_k(L.pdl, k_restrict_first<T, V2, TPRC>, g, TPB, 0, st, L.R, L.r, C.b,
+                                        C.dinv, (T)cc.invtheta, C.x, C.d)));
     } else {
-      launch_spmv2<T, V2, false>(L.tprR, L.R, L.r, C.b, st);
+      launch_spmv2<T, V2, false>(L.tprR, L.R, L.r, C.b, st, L.pdl);
     }
   }
   CH_LAUNCHED();
@@ -1355,7 +1412,7 @@ static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv,
   {
     ProfScope ps(st, l == 0 ? K_PROLONG : K_PROLONG_C, sizeof(T) == 4,
                  L.P.nnz * (4 + Tb) + 4.0 * (n + 1) + 2.0 * Tb * nc + 4.0 * Tb * n, 2.0 * L.P.nnz);
-    launch_spmv2<T, V2, true>(L.tprP, L.P, xc, x, st);
+    launch_spmv2<T, V2, true>(L.tprP, L.P, xc, x, st, L.pdl);
   }
   CH_LAUNCHED();
   CH_TRY(smooth<T>(h, L, l, 0, &x, st));
@@ -1369,11 +1426,11 @@ static ch_status solve_t(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv
   using V2 = typename V2T<T>::t;
   LevelT<T>& L = Ls[0];
   const int n = L.A.nrows;
-  k_load2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, b, ldb, L.b);
+  launch_k(L.pdl, k_load2<T, V2>, blocks_for(n), TPB, 0, st, n, b, ldb, L.b);
   CH_LAUNCHED();
   V2* xr = L.x;
   for (int c = 0; c < ncyc; ++c) CH_TRY(vcycle<T>(h, Ls, cinv, 0, c == 0, &xr, st));
-  k_store2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, xr, x, ldx);
+  launch_k(L.pdl, k_store2<T, V2>, blocks_for(n), TPB, 0, st, n, xr, x, ldx);
   CH_LAUNCHED();
   return CH_OK;
 }
@@ -1412,7 +1469,7 @@ static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::ve
     LevelT<T>& L = LM[0];
     {
       ProfScope ps(sm, K_VLOAD, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
-      k_load2<T, V2><<<blocks_for(n), TPB, 0, sm>>>(n, v, 4, L.b);
+      launch_k(L.pdl, k_load2<T, V2>, blocks_for(n), TPB, 0, sm, n, v, 4, L.b);
     }
     V2* xr = L.x;
     if (p.precond_M == 1) {
@@ -1422,7 +1479,7 @@ static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::ve
     }
     {
       ProfScope ps(sm, K_VSTORE, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
-      k_store2<T, V2><<<blocks_for(n), TPB, 0, sm>>>(n, xr, w, 4);
+      launch_k(L.pdl, k_store2<T, V2>, blocks_for(n), TPB, 0, sm, n, xr, w, 4);
     }
     CH_LAUNCHED();
   }
@@ -1432,7 +1489,7 @@ static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::ve
     LevelT<T>& L = LH[0];
     {
       ProfScope ps(st, K_VLOAD, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
-      k_load2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, v + 2, 4, L.b);
+      launch_k(L.pdl, k_load2<T, V2>, blocks_for(n), TPB, 0, st, n, v + 2, 4, L.b);
     }
     V2* xr = L.x;
     for (int c = 0; c < p.vcycles_H; ++c) CH_TRY(vcycle<T>(pc->hH, LH, cinvH, 0, c == 0, &xr, st));
@@ -1448,7 +1505,7 @@ static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::ve
     for (int c = 0; c < p.vcycles_H; ++c) CH_TRY(vcycle<T>(pc->hH, LH, cinvH, 0, c == 0, &xr, st));
     {
       ProfScope ps(st, K_VSTORE, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
-      k_store2<T, V2><<<blocks_for(n), TPB, 0, st>>>(n, xr, w + 2, 4);
+      launch_k(L.pdl, k_store2<T, V2>, blocks_for(n), TPB, 0, st, n, xr, w + 2, 4);
     }
     CH_LAUNCHED();
   }
@@ -1537,7 +1594,7 @@ static ch_status vcycle_static(Hierarchy* h, LevelT<T>* Ls, const T* cinv, int l
   LevelT<T>& L = Ls[l];
   const int n = L.A.nrows;
   if (l == h->nlev - 1) {
-    k_dense_solve<T, V2><<<blocks_for((int64_t)n * 32), TPB, 0, st>>>(n, cinv, L.b, L.x);
+    launch_k(L.pdl, k_dense_solve<T, V2>, blocks_for((int64_t)n * 32), TPB, 0, st, n, cinv, L.b, L.x);
     CH_LAUNCHED();
     *xres = L.x;
     return CH_OK;

@@ -47,6 +47,7 @@ ch_status check_params(const ch_params* p) {
              std::isfinite(p->N_s),
          "N_p, N_nfa, N_s must be > 0");
   CH_ARG(p->fh_delta > 0 && p->fh_delta < 1, "fh_delta must be in (0, 1)");
+  CH_ARG(p->pdl == 0 || p->pdl == 1, "pdl must be 0 or 1");
   return CH_OK;
 }
 }  // namespace
@@ -116,6 +117,7 @@ void ch_params_default(ch_params* p) {
   d.N_nfa = 20.0;
   d.N_s = 1.0;
   d.fh_delta = 1e-10;
+  d.pdl = 1;
   *p = d;
 }
 

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ch.h"
@@ -94,6 +95,42 @@ constexpr int RED_BLOCKS_MAX = 152 * 4;
 inline int red_blocks(int64_t n) {
   int b = blocks_for(n);
   return b < RED_BLOCKS_MAX ? (b < 1 ? 1 : b) : RED_BLOCKS_MAX;
+}
+
+// ---------------------------------------------------------------- programmatic dependent launch
+// A kernel launched with `pdl` set may be scheduled while the kernel before it on the stream is
+// still running (its blocks wait in pdl_wait() until that kernel has finished and its writes are
+// visible).  The rules every such kernel keeps:
+//   - before pdl_wait() it reads only data that no kernel of the current solve writes (operator
+//     values, diagonals: set-up results) and writes no global memory;
+//   - it calls pdl_trigger(), which lets its own successor be scheduled, only after pdl_wait(), so
+//     that when the successor's blocks start every kernel but this one has finished.  Without the
+//     call the successor is scheduled when this kernel's blocks have all exited (still before
+//     the memory flush that pdl_wait() covers).
+// Launched without the attribute (pdl = 0, per-launch timing with events between kernels) both
+// instructions return at once and the kernel behaves as a plain launch.  No arithmetic changes.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+bool prof_timing();  // prof.cu: per-launch event timing on (launches then stay plain)
+template <typename... KArgs, typename... Args>
+inline void launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args&&... args) {
+  if (!pdl || prof_timing()) {
+    k<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+    return;
+  }
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);  // errors reach cudaGetLastError
 }
 
 // ---------------------------------------------------------------- primitives (sparse.cu)

@@ -32,6 +32,7 @@ def main():
                     help="0: host-driven Krylov loop with direct launches (ncu profiles no kernel inside a "
                          "graph that holds conditional nodes)")
     ap.add_argument("--precond-m", type=int, default=0)
+    ap.add_argument("--pdl", type=int, default=1, help="0: plain stream-ordered launches")
     ap.add_argument("--project", type=int, default=0, help="grid size of a final morphology projection")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of one mesh: this many runs of inputs.batch_runs(n, seed=0)")
@@ -40,13 +41,13 @@ def main():
     from paper_2204_03575_gb300 import ch
     torch.cuda.set_device(0)
     kw = dict(nx=a.nx, ny=a.ny, precision=a.precision, restart=a.restart, potential=a.potential,
-              precond_M=a.precond_m, graphs=a.graphs)
+              precond_M=a.precond_m, graphs=a.graphs, pdl=a.pdl)
     if a.nz:
         kw.update(dim=3, nz=a.nz, Lz=a.nz / a.nx)
     if a.batch:
         from paper_2204_03575_gb300 import inputs
         spec = inputs.batch_runs(a.batch, seed=0)
-        p = ch.Params(precision=a.precision, restart=a.restart, graphs=a.graphs)
+        p = ch.Params(precision=a.precision, restart=a.restart, graphs=a.graphs, pdl=a.pdl)
         mesh = ch.Mesh(p, runs=[ch.Params(nx=nx, ny=ny) for nx, ny, _, _ in spec])
         system = ch.System(mesh, p)
         pc = ch.Precond(system)
@@ -60,8 +61,14 @@ def main():
         state.init_seeded(0.33, 0.33, 0.01, seed=0)
     for _ in range(a.warmup):
         state.step()
+    ms, its = [], []
     for k in range(a.steps):
-        print(json.dumps({"step": k, **state.step()}), flush=True)
+        s = state.step()
+        ms.append(s["ms"])
+        its.append(sum(s["iters"]))
+        print(json.dumps({"step": k, **s}), flush=True)
+    if a.steps:
+        print(json.dumps({"steps": a.steps, "mean_ms": sum(ms) / len(ms), "iters": sum(its)}), flush=True)
     if a.project and not a.batch and not a.nz:
         g = state.get()
         polymer, _, _ = ch.morphology_project(g["phi_p"], g["phi_nfa"], a.nx, a.ny, 1.0, 1.0, a.project, a.project)

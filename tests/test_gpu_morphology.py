@@ -1,9 +1,9 @@
 """The morphology-to-grid projection of Section 5 on the device, bit-exact against the oracle (GPU).
 
-ch_morphology_project casts an upward ray from every grid point and counts the object faces it
-crosses (the paper's method); `oracle.morphology_oracle` computes the plain definition the
-parity reaches, the value of the image pixel holding the point (pinned on the CPU to a
-brute-force crossing count).  Classes are compared bit for bit, mobilities exactly, on random
+The parity of the object faces an upward ray from a grid point crosses (the paper's method)
+telescopes to the value of the image pixel holding the point; ch_morphology_project reads that
+pixel, locating it by an exact integer quotient except at ties, and `oracle.morphology_oracle`
+computes the same plain definition in numpy (pinned on the CPU to a brute-force crossing count).  Classes are compared bit for bit, mobilities exactly, on random
 morphologies (grids finer and coarser than the image, boxes of both orientations), a disk, the
 explicit threshold, a morphology from the solver itself, and the smallest sizes.
 """
@@ -29,7 +29,11 @@ def _run(lib, pp, pn, nx, ny, Lx, Ly, gx, gy, threshold=None):
 
 @pytest.mark.parametrize("nx,ny,Lx,Ly,gx,gy", [(12, 7, 10.0, 2.5, 31, 17), (64, 32, 10.0, 2.5, 97, 45),
                                                 (40, 40, 1.0, 1.0, 13, 11), (33, 80, 2.0, 5.0, 200, 301),
-                                                (255, 255, 1.0, 1.0, 1000, 1000)])
+                                                (255, 255, 1.0, 1.0, 1000, 1000),
+                                                # grids that are multiples of the image: every
+                                                # point's pixel coordinate is an exact tie
+                                                (16, 8, 1.0, 1.0, 16, 8), (20, 10, 3.0, 0.7, 60, 30),
+                                                (7, 9, 2.5, 10.0, 21, 27)])
 def test_projection_equals_the_oracle(lib, nx, ny, Lx, Ly, gx, gy):
     rng = np.random.default_rng(nx * 1000 + gx)
     N = (nx + 1) * (ny + 1)
@@ -58,9 +62,8 @@ def test_smallest_sizes_and_uniform_images(lib):
     _run(lib, np.zeros(N), np.ones(N), 10, 5, 3.0, 1.0, 17, 9)      # none
 
 
-def test_tall_image_uses_the_walk_and_agrees(lib):
-    """An image too tall for the per-pixel parity in shared memory (more than 20480 rows) is
-    classified by walking each point's ray; both forms count the same faces."""
+def test_tall_image_agrees(lib):
+    """A tall, narrow image (24001 pixel rows) on a coarse grid."""
     nx, ny = 2, 24000
     rng = np.random.default_rng(9)
     N = (nx + 1) * (ny + 1)

@@ -393,6 +393,18 @@ def test_graph_replay_matches_direct_launches(lib):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_programmatic_dependent_launch_matches_plain_launches(lib, precision):
+    """pdl = 1 (V-cycle kernels scheduled while their predecessor drains, waiting on the device
+    for its results) and pdl = 0 (plain stream-ordered launches) give bitwise the same steps."""
+    a = run_pair(lib, 2, nx=48, ny=40, precision=precision, pdl=1)[1]
+    b = run_pair(lib, 2, nx=48, ny=40, precision=precision, pdl=0)[1]
+    for (sa, ga, _, _), (sb, gb, _, _) in zip(a, b):
+        assert sa["iters"] == sb["iters"]
+        for k in ga:
+            np.testing.assert_array_equal(ga[k], gb[k])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_parallel_m_branch_matches_serial_algorithm1(lib, precision):
     """Algorithm 1's M solve runs as a parallel branch of the H solves, except under per-launch
     event timing, which keeps one stream: both give bitwise the same steps."""
