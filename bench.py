@@ -558,6 +558,76 @@ def roofline(prof, peaks):
     return out
 
 
+def smoother_in_sequence(torch, ch, flush, pc, n, precision, passes=40, degree=5, reps=5):
+    """The fine level's Chebyshev step timed as the solve runs it: ch_smooth (H's hierarchy,
+    `passes` passes of `degree` steps, the solver's own kernels with its programmatic dependent
+    launches) captured in one CUDA graph and replayed after an L2 flush; the time per launch is the
+    graph's event time over its launches (the steps plus two vector loads and one store).
+    Algorithmic bytes and FMAs are the library's own launch accounting of the same call."""
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev).manual_seed(0)
+    b = torch.randn(n, 2, dtype=torch.float64, device=dev, generator=g)
+    x0 = torch.randn(n, 2, dtype=torch.float64, device=dev, generator=g)
+    x = x0.clone()
+    ch.profile_read(reset=True)
+    pc.smooth(1, b, x, degree, passes)
+    torch.cuda.synchronize()
+    acc = ch.profile_read(reset=True)
+    launches = sum(v["launches"] for v in acc.values())
+    nbytes = sum(v["bytes"] for v in acc.values())
+    fmas = sum(v["fmas"] for v in acc.values())
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            pc.smooth(1, b, x, degree, passes, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        x.copy_(x0)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(statistics.median(times))
+    del graph
+    return {"nodes": n, "precision": "fp32" if precision else "fp64", "launches": launches,
+            "steps": passes * degree, "avg_launch_us": 1e3 * ms / launches,
+            "bytes_per_launch": nbytes / launches, "achieved_GBps": nbytes / (ms * 1e-3) / 1e9,
+            "achieved_TFLOPs": 2 * fmas / (ms * 1e-3) / 1e12,
+            "how": f"ch_smooth (H, {passes} passes x degree {degree}) in one CUDA graph, L2 flushed "
+                   f"before each of {reps} replays (median)"}
+
+
+def in_sequence(torch, ch, flush, peaks, pc, n, precision, passes=40):
+    """smoother_in_sequence with its fractions of the measured HBM rate and, in FP64, of the FP64
+    pipe's peak."""
+    r = smoother_in_sequence(torch, ch, flush, pc, n, precision, passes=passes)
+    r["frac_hbm"] = r["achieved_GBps"] / peaks.get("hbm_gbs", 6800.0)
+    if not precision:
+        r["frac_alu"] = r["achieved_TFLOPs"] / (152 * FP64_FMA_PER_CLK_SM * 2 * peaks.get("sm_max_mhz", 2070.0)
+                                                * 1e6 / 1e12)
+    return r
+
+
+def hbm_bound_smoother(torch, ch, flush, peaks):
+    """The same kernel on a 2048 x 2048 lattice in FP32: its fine level (4.2 M rows, ~270 MB of
+    operator and vectors) exceeds the 129 MB L2, so the steps stream from HBM."""
+    p = ch.Params(nx=2048, ny=2048, precision=1)
+    system = ch.System(ch.Mesh(p), p)
+    pc = ch.Precond(system)
+    r = in_sequence(torch, ch, flush, peaks, pc, system.n, 1, passes=20)
+    r["workload"] = "2D 2048x2048 P1 lattice (4,198,401 nodes), H's finest level, FP32"
+    del pc, system
+    torch.cuda.synchronize()
+    return r
+
+
 def traffic_for(kernel):
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
@@ -654,6 +724,7 @@ def main():
     prof64 = ch.profile_read(reset=True)
     ch.profile_enable(False)
     roof = roofline(prof64, peaks)
+    roof["in_sequence"] = in_sequence(torch, ch, flush, peaks, pc, N, 0)
 
     # ---- end to end through the public API with host buffers
     sysE, pcE, stateE = make_solver(ch, args.nx, args.ny, precision=0)
@@ -708,6 +779,7 @@ def main():
                  "iters_per_step_mean": float(np.mean(iters_m)),
                  "max_rel_diff_phi_vs_fp64_form_after_run": diff,
                  "roofline": roofline(profm, peaks), "top_kernels": top_kernels(profm)}
+        mixed["roofline"]["in_sequence"] = in_sequence(torch, ch, flush, peaks, pcM, N, 1)
         del sysM, pcM, stateM
 
     # ---- batched workload: 64 independent runs of uneven size in one state (FP32 V-cycles)
@@ -748,11 +820,12 @@ def main():
 
     # ---- the solver's variants (Chebyshev M~, Flory-Huggins), Section 4's EOC study in tau and
     # Section 5's morphology projection
-    variants = eoc = morph = None
+    variants = eoc = morph = smoother_hbm = None
     if not args.no_extra and world == 1:
         variants = variants_section(torch, ch, np, args.nx, min(K, 20), W, flush, ranks)
         eoc = eoc_section(torch, ch, np)
         morph = morphology_section(torch, ch, fields64, args.nx)
+        smoother_hbm = hbm_bound_smoother(torch, ch, flush, peaks)
 
     # ---- learned warm start (256 x 256 grid): training, then FP64 / mixed with and without it
     learned = None
@@ -798,7 +871,8 @@ def main():
         "iters_per_step_mean": float(np.mean(iters)), "iters_per_step_max": int(np.max(iters)),
         "amg_levels": {k: [r for r, _ in v] for k, v in levels.items()},
         "mixed": mixed, "batch": batch, "learned": learned, "configs": extra, "variants": variants,
-        "eoc_tau": eoc, "morphology_projection": morph, "cpu_baseline": cpu,
+        "eoc_tau": eoc, "morphology_projection": morph, "fine_smoother_hbm_bound": smoother_hbm,
+        "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -224,6 +224,17 @@ ch_status ch_precond_tiles(const ch_precond_t* pc, int32_t which, int32_t level,
  * `stream` before the call's work ends (stream order for the caller is unchanged).
  * v, w: N x 4 fp64, must not alias. */
 ch_status ch_precond_apply(ch_precond_t* pc, const double* v, double* w, void* stream);
+/* The V-cycles' finest-level smoother on its own (Section 3's AMG relaxation): `passes` passes of
+ * `degree` Chebyshev steps on D^-1 A x = D^-1 b over the V-cycle's interval of D^-1 A (as
+ * ch_precond_level exports it), each pass continuing from the previous one's x, as the V-cycle's
+ * post-smoothing does, in the hierarchy's working precision; A = M (which = 0) or H (which = 1).
+ * b, x: N x 2 fp64 device arrays, 16-byte aligned, not aliased; x is the initial iterate on entry
+ * and the result on exit.  The steps are the solver's own fine-level kernels, launched as it
+ * launches them (a caller may capture the call in a CUDA graph).  CH_ERR_ARG for degree outside
+ * [1, 16], passes < 1, which outside {0, 1}, NULL, aliased or misaligned arrays, and for a
+ * hierarchy of one level (solved directly by the V-cycle: it has no smoother). */
+ch_status ch_smooth(ch_precond_t* pc, int32_t which, int32_t degree, int32_t passes, const double* b, double* x,
+                    void* stream);
 /* vcycles V-cycles (zero initial guess) on M (which = 0) or H (which = 1) for two right-hand
  * sides stored N x 2 (fp64): x ~ A^-1 b.  b, x must not alias. */
 ch_status ch_vcycle(ch_precond_t* pc, int32_t which, int32_t vcycles, const double* b, double* x,
@@ -320,6 +331,15 @@ void ch_state_destroy(ch_state_t* st);
 int32_t ch_ws_nparams(void);
 ch_status ch_ws_create(int32_t H, int32_t W, int32_t max_batch, ch_ws_t** out);
 void ch_ws_destroy(ch_ws_t* w);
+/* The tensor-core path of the network's convolutions (host setting, applies to later calls):
+ * 0 (default): mma.sync, each warp 16 pixels x the output channels with fragments gathered from
+ * the image; 1: tcgen05 -- a block of 128 threads stages the 128-pixel im2col tile and the
+ * weights in shared memory, one thread issues the MMAs into a tensor-memory accumulator, and the
+ * warps read it back for the epilogue.  Both compute the same convolutions (FP32 accumulation, in
+ * a different order).  A tcgen05 block whose wait for its MMAs runs out records it; the next
+ * training call or learned step that synchronises returns CH_ERR_INTERNAL.  CH_ERR_ARG for an
+ * engine other than 0 or 1. */
+ch_status ch_ws_set_engine(ch_ws_t* w, int32_t engine);
 ch_status ch_ws_set_params(ch_ws_t* w, const float* params, void* stream);     /* host; resets Adam */
 /* host outputs, either may be NULL; grads are those of the last ch_ws_train_step */
 ch_status ch_ws_get_params(const ch_ws_t* w, float* params, float* grads, void* stream);

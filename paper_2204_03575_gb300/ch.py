@@ -108,6 +108,7 @@ _SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         _I32P, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "ch_vcycle": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
+    "ch_smooth": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
     "ch_precond_destroy": (None, [_VP]),
     "ch_vcycle_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]),
     "ch_mass_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -133,6 +134,7 @@ _SIGNATURES = {
     "ch_ws_nparams": (ctypes.c_int32, []),
     "ch_ws_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_VP)]),
     "ch_ws_destroy": (None, [_VP]),
+    "ch_ws_set_engine": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "ch_ws_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), _VP]),
     "ch_ws_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _VP]),
     "ch_ws_set_norm": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), _VP]),
@@ -335,6 +337,16 @@ class Precond:
         _check(lib().ch_vcycle(self._h, which, vcycles, _ptr(b), _ptr(x), _stream(stream)), "ch_vcycle")
         return x
 
+    def smooth(self, which: int, b, x, degree: int, passes: int = 1, stream=None):
+        """ch_smooth: `passes` passes of the finest level's degree-`degree` Chebyshev smoother on
+        M (which = 0) or H (which = 1), updating x (N x 2, fp64, on the device) in place."""
+        b = _f64(b, self.system.n)
+        if not (isinstance(x, torch.Tensor) and x.dtype == torch.float64 and x.is_cuda and x.is_contiguous()
+                and tuple(x.shape) == (self.system.n, 2)):
+            raise TypeError("x must be a contiguous N x 2 float64 CUDA tensor")
+        _check(lib().ch_smooth(self._h, which, degree, passes, _ptr(b), _ptr(x), _stream(stream)), "ch_smooth")
+        return x
+
     def mass_solve(self, b, stream=None):
         """ch_mass_solve: Algorithm 1's step 1 (M~^-1 b) on N x 2 right-hand sides."""
         b = _f64(b, self.system.n)
@@ -481,6 +493,10 @@ class WarmStartNet:
         self._h = _VP()
         _check(lib().ch_ws_create(H, W, max_batch, ctypes.byref(self._h)), "ch_ws_create")
         self.nparams = lib().ch_ws_nparams()
+
+    def set_engine(self, engine: int):
+        """ch_ws_set_engine: 0 mma.sync, 1 tcgen05 convolutions."""
+        _check(lib().ch_ws_set_engine(self._h, engine), "ch_ws_set_engine")
 
     def set_params(self, params, stream=None):
         import numpy as np

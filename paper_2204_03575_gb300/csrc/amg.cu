@@ -1435,6 +1435,40 @@ static ch_status solve_t(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv
   return CH_OK;
 }
 
+// `passes` passes of the finest level's Chebyshev smoother of degree `degree` (the V-cycle's
+// interval), each continuing from the previous pass's x; x (N x 2, fp64) is read and overwritten
+template <typename T>
+static ch_status smooth_t(Hierarchy* h, std::vector<LevelT<T>>& Ls, const double* b, double* x, int degree,
+                          int passes, cudaStream_t st) {
+  using V2 = typename V2T<T>::t;
+  LevelT<T>& L = Ls[0];
+  const int n = L.A.nrows;
+  const double io = n * (16.0 + 2.0 * sizeof(T));
+  {
+    ProfScope ps(st, K_VLOAD, sizeof(T) == 4, 2.0 * io, 0.0);
+    launch_k(L.pdl, k_load2<T, V2>, blocks_for(n), TPB, 0, st, n, b, 2, L.b);
+  }
+  {
+    ProfScope ps(st, K_VLOAD, sizeof(T) == 4, 0.0, 0.0);  // its bytes are counted with the first load
+    launch_k(L.pdl, k_load2<T, V2>, blocks_for(n), TPB, 0, st, n, x, 2, L.x);
+  }
+  CH_LAUNCHED();
+  const ChebCoef c = cheb_coef(h->rho[0], degree, h->cheb_lower);
+  V2* xr = L.x;
+  for (int k = 0; k < passes; ++k) CH_TRY(smooth_coef<T>(L, c, degree, 0, K_CHEB_FIRST, K_CHEB_STEP, &xr, st));
+  {
+    ProfScope ps(st, K_VSTORE, sizeof(T) == 4, io, 0.0);
+    launch_k(L.pdl, k_store2<T, V2>, blocks_for(n), TPB, 0, st, n, xr, x, 2);
+  }
+  CH_LAUNCHED();
+  return CH_OK;
+}
+
+ch_status hierarchy_smooth(Hierarchy* h, const double* b, double* x, int degree, int passes, cudaStream_t st) {
+  if (h->precision == 0) return smooth_t<double>(h, h->Ld, b, x, degree, passes, st);
+  return smooth_t<float>(h, h->Lf, b, x, degree, passes, st);
+}
+
 ch_status hierarchy_solve(Hierarchy* h, const double* b, int ldb, double* x, int ldx, int ncyc,
                           cudaStream_t st) {
   if (h->precision == 0) return solve_t<double>(h, h->Ld, h->cinv, b, ldb, x, ldx, ncyc, st);

@@ -369,6 +369,20 @@ ch_status ch_vcycle(ch_precond_t* pc, int32_t which, int32_t vcycles, const doub
   return ch::hierarchy_solve(which == 0 ? pc->hM : pc->hH, b, 2, x, 2, vcycles, S(stream));
 }
 
+ch_status ch_smooth(ch_precond_t* pc, int32_t which, int32_t degree, int32_t passes, const double* b, double* x,
+                    void* stream) {
+  CH_ARG(pc != nullptr && b != nullptr && x != nullptr, "NULL argument");
+  CH_ARG(which == 0 || which == 1, "which must be 0 (M) or 1 (H)");
+  CH_ARG(degree >= 1 && degree <= 16, "degree must be in [1, 16]");
+  CH_ARG(passes >= 1, "passes must be >= 1");
+  CH_ARG(b != x, "b and x must not alias");
+  CH_ARG(((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15) == 0,
+         "b and x must be 16-byte aligned");
+  ch::Hierarchy* h = which == 0 ? pc->hM : pc->hH;
+  CH_ARG(ch::hierarchy_levels(h) >= 2, "the hierarchy has one level (solved directly: it has no smoother)");
+  return ch::hierarchy_smooth(h, b, x, degree, passes, S(stream));
+}
+
 ch_status ch_mass_solve(ch_precond_t* pc, const double* b, double* x, void* stream) {
   CH_ARG(pc != nullptr && b != nullptr && x != nullptr, "NULL argument");
   CH_ARG(b != x, "b and x must not alias");
@@ -489,6 +503,12 @@ ch_status ch_ws_create(int32_t H, int32_t W, int32_t max_batch, ch_ws_t** out) {
 }
 
 void ch_ws_destroy(ch_ws_t* w) { ch::ws_destroy(w); }
+
+ch_status ch_ws_set_engine(ch_ws_t* w, int32_t engine) {
+  CH_ARG(w != nullptr, "NULL argument");
+  CH_ARG(engine == 0 || engine == 1, "engine must be 0 (mma.sync) or 1 (tcgen05)");
+  return ch::ws_set_engine(w, engine);
+}
 
 ch_status ch_ws_set_params(ch_ws_t* w, const float* params, void* stream) {
   CH_ARG(w != nullptr && params != nullptr, "NULL argument");

@@ -250,6 +250,8 @@ void hierarchy_level_tiles(const Hierarchy* h, int l, int* tA, int* tR, int* tP)
 // x (N x 2, fp64, row stride ldx) ~ A^-1 b (N x 2, fp64, row stride ldb), ncyc V-cycles
 ch_status hierarchy_solve(Hierarchy* h, const double* b, int ldb, double* x, int ldx, int ncyc,
                           cudaStream_t st);
+// x (N x 2, fp64, read and overwritten) after `passes` passes of the finest level's Chebyshev smoother
+ch_status hierarchy_smooth(Hierarchy* h, const double* b, double* x, int degree, int passes, cudaStream_t st);
 // as hierarchy_solve (strides 2), work vectors in a static device array: no device allocation
 ch_status hierarchy_solve_noalloc(Hierarchy* h, const double* b, double* x, int ncyc, cudaStream_t st);
 // y (N x 2, fp64, stride ldy) = A0 x (N x 2, fp64, stride ldx) in the hierarchy's working precision
@@ -314,6 +316,10 @@ ch_status state_step(ch_state_s* S, cudaStream_t st, ch_step_stats* stats);
 struct ch_ws_s;
 namespace ch {
 ch_status ws_create(int H, int W, int Bmax, ch_ws_s** out);
+// convolution engine: 0 mma.sync, 1 tcgen05; ws_check reports a timed-out tcgen05 block (call
+// after synchronising with the network's work)
+ch_status ws_set_engine(ch_ws_s* w, int engine);
+ch_status ws_check(const ch_ws_s* w);
 void ws_destroy(ch_ws_s* w);
 ch_status ws_set_params(ch_ws_s* w, const float* host, cudaStream_t st);
 ch_status ws_get_params(const ch_ws_s* w, float* host, float* host_grads, cudaStream_t st);

@@ -1872,6 +1872,7 @@ ch_status state_step_learned(ch_state_s* S, ch_ws_s* w, cudaStream_t st, ch_step
   const ch_status r = use_net ? step_guess_core(S, S->guess, st, stats, false)
                               : step_plain_core(S, st, stats, false);
   S->learn_k += 1;
+  if (r == CH_OK && use_net) return ws_check(w);  // the step synchronised: its prediction is done
   return r;
 }
 

@@ -69,6 +69,59 @@ __device__ __forceinline__ uint32_t load_pair(const __nv_bfloat16* X, int H, int
   return *reinterpret_cast<const uint32_t*>(X + ((size_t)r * W + q) * C + c);
 }
 
+// ---------------------------------------------------------------- tcgen05 primitives (inline PTX)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor of a K-major operand without swizzle: the canonical layout of
+// 8-row x 16-byte core matrices, lbo = byte distance between core matrices adjacent along K, sbo =
+// between core matrices adjacent along M (or N); bits 46-47 hold the descriptor version (1).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D in FP32, A and B BF16, both K-major, dense, M x N.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// Bounded wait for the phase of parity `parity` of an mbarrier: false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  for (int i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// 8 consecutive FP32 accumulator columns of the warp's 32 TMEM lanes (one lane per thread); the
+// wait carries the registers so that nothing reads them before the load has completed
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 // ---------------------------------------------------------------- 3x3 convolution (implicit GEMM)
 // Y[p][co] = sum_{tap, ci} X[p + off(tap)][ci] Wt[tap][ci][co] (+ bias[co]), p = r W + q, then
 //   MODE 0: Yb = bf16(relu(.))                          (hidden layer forward)
@@ -138,6 +191,137 @@ __global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict
       }
     }
   }
+}
+
+// ---------------------------------------------------------------- 3x3 convolution on tcgen05
+// The same implicit GEMM and epilogues as k_conv3x3 on the fifth-generation tensor cores.  A block
+// of 128 threads computes 128 consecutive pixels (M = 128) x N output channels (N = COUT, at least
+// 16 as the M = 128 shape requires; padded rows of B are zero and not stored) over K = 9 CIN:
+//   - the im2col tile A (128 x K) and the weights B (N x K) are staged in shared memory in the
+//     K-major canonical layout; one core-matrix row of A is 8 channels of one tap of one pixel, a
+//     single 16-byte load of the NHWC image (zero outside it);
+//   - one thread issues the K / 16 MMAs (M = 128, N, K = 16) into an FP32 accumulator in tensor
+//     memory and commits them to an mbarrier;
+//   - each warp reads its 32 accumulator lanes (pixel = lane, one pixel per thread) back with
+//     tcgen05.ld for the epilogue.
+// The wait on the mbarrier is bounded: past it the block records the failure in *err, waits once
+// more (bounded) for its MMAs, frees its tensor memory and writes nothing.
+constexpr int TC_M = 128;
+constexpr int TC_WAIT = 1 << 20;
+
+template <int CIN, int COUT>
+constexpr int tc_smem_bytes() {
+  return TC_M * 9 * CIN * 2 + (COUT < 16 ? 16 : COUT) * 9 * CIN * 2 + 16;
+}
+
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(TC_M) k_conv3x3_tc(const __nv_bfloat16* __restrict__ X,
+                                                     const __nv_bfloat16* __restrict__ Wt,
+                                                     const float* __restrict__ bias, int H, int W,
+                                                     __nv_bfloat16* __restrict__ Yb, float* __restrict__ Yf,
+                                                     const __nv_bfloat16* __restrict__ mask, int* __restrict__ err) {
+  constexpr int N = COUT < 16 ? 16 : COUT;
+  constexpr int K = 9 * CIN, KB = K / 8, NB = N / 8, MB = TC_M / 8;
+  constexpr uint32_t TMEM_COLS = 32;  // a power of two >= 32 holding the N FP32 columns
+  static_assert(CIN % 8 == 0 && N % 16 == 0 && N <= 32, "tile shape");
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* sA = tc_smem;
+  unsigned char* sB = tc_smem + TC_M * K * 2;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + N * K * 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int P = H * W;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  X += (size_t)blockIdx.y * P * CIN;
+  const size_t yo = (size_t)blockIdx.y * P * COUT;
+  const int p = blockIdx.x * TC_M + tid;  // this thread's pixel (A row, accumulator lane)
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  // B: row n of core matrix (kb, n / 8) holds Wt[k][n], k = 8 kb .. 8 kb + 7
+  for (int c = tid; c < KB * N; c += TC_M) {
+    const int n = c % N, kb = c / N;
+    uint32_t v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = kb * 8 + 2 * j;
+      const __nv_bfloat16 lo = n < COUT ? Wt[k * COUT + n] : __float2bfloat16_rn(0.f);
+      const __nv_bfloat16 hi = n < COUT ? Wt[(k + 1) * COUT + n] : __float2bfloat16_rn(0.f);
+      v[j] = pack_bf16(lo, hi);
+    }
+    *reinterpret_cast<uint4*>(sB + (kb * NB + n / 8) * 128 + (n % 8) * 16) = make_uint4(v[0], v[1], v[2], v[3]);
+  }
+  // A: row (tid % 8) of core matrix (kb, tid / 8) = channels ci0 .. ci0 + 7 of tap kb 8 / CIN
+  {
+    const int r = p / W, q = p - (p / W) * W;
+#pragma unroll 4
+    for (int kb = 0; kb < KB; ++kb) {
+      const int tap = (kb * 8) / CIN, ci0 = (kb * 8) % CIN;
+      const int rr = r + tap / 3 - 1, qq = q + tap % 3 - 1;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (p < P && rr >= 0 && rr < H && qq >= 0 && qq < W)
+        v = *reinterpret_cast<const uint4*>(X + ((size_t)rr * W + qq) * CIN + ci0);
+      *reinterpret_cast<uint4*>(sA + (kb * MB + tid / 8) * 128 + (tid % 8) * 16) = v;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes -> tensor core reads
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    constexpr uint32_t idesc = tc_idesc(TC_M, N);
+#pragma unroll 1
+    for (int kk = 0; kk < K / 16; ++kk) {
+      const uint64_t ad = tc_desc(smem_u32(sA) + kk * 2 * MB * 128, MB * 128, 128);
+      const uint64_t bd = tc_desc(smem_u32(sB) + kk * 2 * NB * 128, NB * 128, 128);
+      tc_mma(tmem, ad, bd, idesc, kk > 0);
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+  }
+  const bool ok = mbar_wait(smem_u32(bar), 0, TC_WAIT);
+  const bool failed = __syncthreads_or(!ok);
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+    mbar_wait(smem_u32(bar), 0, TC_WAIT);  // the MMAs may still be running: give them a last bound
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (!failed) {
+    float acc[N];
+#pragma unroll
+    for (int c8 = 0; c8 < NB; ++c8) {
+      float v[8];
+      tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + c8 * 8, v);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[c8 * 8 + j] = v[j];
+    }
+    if (p < P) {
+#pragma unroll
+      for (int co = 0; co < COUT; ++co) {
+        const float v = acc[co] + (bias ? bias[co] : 0.f);
+        const size_t o = yo + (size_t)p * COUT + co;
+        if (MODE == 0) {
+          Yb[o] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+        } else if (MODE == 1) {
+          Yf[o] = v;
+        } else {
+          Yb[o] = __float2bfloat16_rn(__bfloat162float(mask[o]) > 0.f ? v : 0.f);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 // ---------------------------------------------------------------- data movement
@@ -435,7 +619,13 @@ struct ch_ws_s {
   float* part = nullptr;                                           // weight-gradient partials
   float* loss_part = nullptr;
   bool fresh = false;  // bf16 copies up to date
+  int engine = 0;      // convolutions: 0 mma.sync (warp-level), 1 tcgen05 (tensor memory)
+  int* err_host = nullptr;  // pinned, device-mapped: set by a tcgen05 block whose MMA wait ran out
+  int* err_dev = nullptr;
   ch::Alloc mem;
+  ~ch_ws_s() {
+    if (err_host) cudaFreeHost(err_host);
+  }
 };
 
 namespace ch {
@@ -461,22 +651,64 @@ static ch_status ws_refresh(ch_ws_s* w, cudaStream_t st) {
   return CH_OK;
 }
 
+// The convolutions' shared-memory limits on the tcgen05 path (above the 48 KB default).
+static ch_status ws_tc_setup() {
+  CH_CUDA(cudaFuncSetAttribute(k_conv3x3_tc<WS_CIN, WS_C, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tc_smem_bytes<WS_CIN, WS_C>()));
+  CH_CUDA(cudaFuncSetAttribute(k_conv3x3_tc<WS_C, WS_C, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tc_smem_bytes<WS_C, WS_C>()));
+  CH_CUDA(cudaFuncSetAttribute(k_conv3x3_tc<WS_C, WS_COUT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tc_smem_bytes<WS_C, WS_COUT>()));
+  CH_CUDA(cudaFuncSetAttribute(k_conv3x3_tc<16, WS_C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tc_smem_bytes<16, WS_C>()));
+  CH_CUDA(cudaFuncSetAttribute(k_conv3x3_tc<WS_C, WS_C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tc_smem_bytes<WS_C, WS_C>()));
+  return CH_OK;
+}
+
+// One convolution of B samples on the handle's engine.
+template <int CIN, int COUT, int MODE>
+static void ws_conv(ch_ws_s* w, const __nv_bfloat16* X, const __nv_bfloat16* Wt, const float* bias,
+                    __nv_bfloat16* Yb, float* Yf, const __nv_bfloat16* mask, int B, cudaStream_t st) {
+  if (w->engine == 1) {
+    k_conv3x3_tc<CIN, COUT, MODE><<<dim3(blocks_for(w->P, TC_M), B), TC_M, tc_smem_bytes<CIN, COUT>(), st>>>(
+        X, Wt, bias, w->H, w->W, Yb, Yf, mask, w->err_dev);
+  } else {
+    k_conv3x3<CIN, COUT, MODE><<<dim3(blocks_for(w->P, 128), B), 256, 0, st>>>(X, Wt, bias, w->H, w->W, Yb, Yf,
+                                                                                 mask);
+  }
+}
+
+// The flag a tcgen05 convolution block sets when its MMA wait ran out (read after the host has
+// synchronised with the work that could set it).
+ch_status ws_check(const ch_ws_s* w) {
+  if (w->err_host && *reinterpret_cast<volatile int*>(w->err_host)) {
+    set_error("warm start: a tcgen05 convolution block timed out waiting for its MMAs");
+    return CH_ERR_INTERNAL;
+  }
+  return CH_OK;
+}
+
+ch_status ws_set_engine(ch_ws_s* w, int engine) {
+  w->engine = engine;
+  return CH_OK;
+}
+
 // forward pass of B samples whose inputs are already packed in w->x0
 static ch_status ws_forward_packed(ch_ws_s* w, int B, cudaStream_t st) {
   if (!w->fresh) CH_TRY(ws_refresh(w, st));
   const WsParams p = ws_views(w->params);
-  const dim3 grid(blocks_for(w->P, 128), B);
   {
     ProfScope ps(st, K_WS_CONV, 1, (double)B * w->P * (16 + 32) * 2, (double)B * w->P * 9 * 16 * 32);
-    k_conv3x3<WS_CIN, WS_C, 0><<<grid, 256, 0, st>>>(w->x0, w->w1, p.b1, w->H, w->W, w->a1, nullptr, nullptr);
+    ws_conv<WS_CIN, WS_C, 0>(w, w->x0, w->w1, p.b1, w->a1, nullptr, nullptr, B, st);
   }
   {
     ProfScope ps(st, K_WS_CONV, 1, (double)B * w->P * (32 + 32) * 2, (double)B * w->P * 9 * 32 * 32);
-    k_conv3x3<WS_C, WS_C, 0><<<grid, 256, 0, st>>>(w->a1, w->w2, p.b2, w->H, w->W, w->a2, nullptr, nullptr);
+    ws_conv<WS_C, WS_C, 0>(w, w->a1, w->w2, p.b2, w->a2, nullptr, nullptr, B, st);
   }
   {
     ProfScope ps(st, K_WS_CONV, 1, (double)B * w->P * (32 * 2 + 8 * 4), (double)B * w->P * 9 * 32 * 8);
-    k_conv3x3<WS_C, WS_COUT, 1><<<grid, 256, 0, st>>>(w->a2, w->w3, p.b3, w->H, w->W, nullptr, w->y, nullptr);
+    ws_conv<WS_C, WS_COUT, 1>(w, w->a2, w->w3, p.b3, nullptr, w->y, nullptr, B, st);
   }
   CH_LAUNCHED();
   return CH_OK;
@@ -514,6 +746,18 @@ ch_status ws_create(int H, int W, int Bmax, ch_ws_s** out) {
   if (r == CH_OK) r = w->mem.get(&w->y, P * WS_COUT);
   if (r == CH_OK) r = w->mem.get(&w->part, (size_t)Bmax * nchunk * (9 * WS_C * WS_C + WS_C));
   if (r == CH_OK) r = w->mem.get(&w->loss_part, 1024);
+  if (r == CH_OK) {
+    if (cudaHostAlloc(&w->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&w->err_dev, w->err_host, 0) != cudaSuccess) {
+      cudaGetLastError();
+      w->err_host = nullptr;
+      set_error("warm-start error flag allocation failed");
+      r = CH_ERR_CUDA;
+    } else {
+      *w->err_host = 0;
+    }
+  }
+  if (r == CH_OK) r = ws_tc_setup();
   if (r == CH_OK) {
     cudaMemset(w->params, 0, sizeof(float) * WS_NPARAM);
     cudaMemset(w->adam_m, 0, sizeof(float) * WS_NPARAM);
@@ -562,9 +806,8 @@ ch_status ws_set_norm(ch_ws_s* w, const float* host20, cudaStream_t st) {
 static ch_status ws_backward_update(ch_ws_s* w, int B, float lr, cudaStream_t st) {
   const int P = w->P;
   // backward through the data: dz2 = (W3 flipped * dy) . [a2 > 0];  dz1 = (W2 flipped * dz2) . [a1 > 0]
-  const dim3 grid(blocks_for(P, 128), B);
-  k_conv3x3<16, WS_C, 2><<<grid, 256, 0, st>>>(w->dy, w->w3f, nullptr, w->H, w->W, w->dz2, nullptr, w->a2);
-  k_conv3x3<WS_C, WS_C, 2><<<grid, 256, 0, st>>>(w->dz2, w->w2f, nullptr, w->H, w->W, w->dz1, nullptr, w->a1);
+  ws_conv<16, WS_C, 2>(w, w->dy, w->w3f, nullptr, w->dz2, nullptr, w->a2, B, st);
+  ws_conv<WS_C, WS_C, 2>(w, w->dz2, w->w2f, nullptr, w->dz1, nullptr, w->a1, B, st);
   CH_LAUNCHED();
   // weight gradients, per sample and pixel chunk, then summed in order
   const int nchunk = (P + WS_CHUNK - 1) / WS_CHUNK;
@@ -636,6 +879,7 @@ ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float*
     float parts[lb];
     CH_CUDA(cudaMemcpyAsync(parts, w->loss_part, sizeof(parts), cudaMemcpyDeviceToHost, st));
     CH_CUDA(cudaStreamSynchronize(st));
+    CH_TRY(ws_check(w));
     double s = 0.0;
     for (int i = 0; i < lb; ++i) s += parts[i];
     *loss = (float)(s / ((double)B * P * 4));
@@ -789,6 +1033,7 @@ ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc
     std::vector<double> h((size_t)B * 8);
     CH_CUDA(cudaMemcpyAsync(h.data(), w->nrm, sizeof(double) * 8 * B, cudaMemcpyDeviceToHost, st));
     CH_CUDA(cudaStreamSynchronize(st));
+    CH_TRY(ws_check(w));
     double L = 0.0;
     for (int b = 0; b < B; ++b)
       for (int sp = 0; sp < 2; ++sp) {

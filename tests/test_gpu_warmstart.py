@@ -32,10 +32,12 @@ def _history(rng, P, B=None, dtype=np.float64):
 
 # small images, and the 129 x 129 and 257 x 257 images of the benchmark's meshes (many tiles per
 # row and many rows of blocks: the multi-block tiling at full size)
+@pytest.mark.parametrize("engine", [0, 1])  # mma.sync, tcgen05
 @pytest.mark.parametrize("H,W", [(12, 20), (17, 9), (129, 129), (257, 257)])
-def test_forward_matches_oracle(lib, H, W):
+def test_forward_matches_oracle(lib, H, W, engine):
     rng = np.random.default_rng(0)
     net = lib.WarmStartNet(H, W, max_batch=2)
+    net.set_engine(engine)
     theta = small_theta(rng)
     net.set_params(theta)
     mean, inv_std, scale = rng.standard_normal(8) * 0.1, rng.uniform(0.5, 2.0, 8), rng.uniform(0.5, 2.0, 4)
@@ -64,11 +66,13 @@ def test_zero_and_unit_networks_are_linear_and_quadratic_extrapolation(lib):
                                rtol=1e-14, atol=1e-14)
 
 
+@pytest.mark.parametrize("engine", [0, 1])  # mma.sync, tcgen05
 @pytest.mark.parametrize("lap,H,W", [(0.0, 12, 20), (0.5, 12, 20), (0.0, 129, 129), (0.5, 129, 131)])
-def test_gradients_match_oracle(lib, lap, H, W):
+def test_gradients_match_oracle(lib, lap, H, W, engine):
     rng = np.random.default_rng(1)
     B = 2
     net = lib.WarmStartNet(H, W, max_batch=B)
+    net.set_engine(engine)
     theta = small_theta(rng)
     net.set_params(theta)
     norm = (rng.standard_normal(8) * 0.05, rng.uniform(0.5, 2.0, 8), np.array([0.7, 1.2, 0.5, 0.9]))
@@ -329,3 +333,24 @@ def test_fit_norm_matches_its_definition(lib, fp32):
                      q20.reshape(H, W, 4), (mean, inv_std, out), bf=True)
     c, cr = a.reshape(H, W, 4) - 2 * s0.reshape(H, W, 4) + q0.reshape(H, W, 4), ref - 2 * s0.reshape(H, W, 4) + q0.reshape(H, W, 4)
     assert np.linalg.norm(c - cr) <= 5e-3 * np.linalg.norm(cr)
+
+
+def test_engines_agree_and_bad_engine_is_refused(lib):
+    """The tcgen05 and mma.sync convolutions give the same predictions up to FP32 accumulation
+    order (then one BF16 rounding of the activations); an unknown engine is refused."""
+    H, W = 65, 97
+    rng = np.random.default_rng(3)
+    theta = small_theta(rng)
+    q2, q, s, _ = (torch.from_numpy(a).cuda() for a in _history(rng, H * W))
+    preds = []
+    for engine in (0, 1):
+        net = lib.WarmStartNet(H, W, max_batch=1)
+        net.set_engine(engine)
+        net.set_params(theta)
+        net.set_norm(np.zeros(8), np.ones(8), np.ones(4))
+        preds.append(net.predict(s, q, q2).cpu().numpy() - (2 * s - q).cpu().numpy())
+    a, b = preds
+    assert np.linalg.norm(a - b) <= 1e-2 * np.linalg.norm(b)
+    with pytest.raises(lib.ChError) as e:
+        net.set_engine(2)
+    assert e.value.status == lib.ERR_ARG
