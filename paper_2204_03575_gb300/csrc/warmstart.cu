@@ -16,16 +16,20 @@
 // tensor cores, the latter also in tap-flipped, channel-transposed form for the backward pass
 // through the data.
 //
-// Convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16, BF16 in, FP32
-// accumulate): M = pixels (16 per warp), N = output channels (8 per tile), K = 9 taps x input
-// channels (16 per step); each lane gathers its A-fragment elements straight from the shifted
-// input (zero outside the image), the B fragments come from the weights staged in shared memory.
+// Convolutions are implicit GEMMs on the tensor cores, BF16 in, FP32 accumulate, M = pixels,
+// N = output channels, K = 9 taps x input channels: by default on tcgen05 (k_conv3x3_tc: tensor
+// memory accumulators, operands staged in shared memory as row bands), or on mma.sync m16n8k16
+// (k_conv3x3: 16 pixels per warp, 8 channels per tile; each lane gathers its A-fragment elements
+// straight from the shifted input, zero outside the image, the B fragments from the weights
+// staged in shared memory).
 // Weight gradients are reduced over pixels by FP32 FMAs in fixed-size pixel chunks and summed in
 // chunk order (deterministic).
 #include <cuda_bf16.h>
 
 #include <cmath>
 #include <vector>
+
+#include <algorithm>
 
 #include "ch_internal.cuh"
 
@@ -194,46 +198,61 @@ __global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict
 }
 
 // ---------------------------------------------------------------- 3x3 convolution on tcgen05
-// The same implicit GEMM and epilogues as k_conv3x3 on the fifth-generation tensor cores.  A block
-// of 128 threads computes 128 consecutive pixels (M = 128) x N output channels (N = COUT, at least
-// 16 as the M = 128 shape requires; padded rows of B are zero and not stored) over K = 9 CIN:
-//   - the im2col tile A (128 x K) and the weights B (N x K) are staged in shared memory in the
-//     K-major canonical layout; one core-matrix row of A is 8 channels of one tap of one pixel, a
-//     single 16-byte load of the NHWC image (zero outside it);
-//   - one thread issues the K / 16 MMAs (M = 128, N, K = 16) into an FP32 accumulator in tensor
-//     memory and commits them to an mbarrier;
-//   - each warp reads its 32 accumulator lanes (pixel = lane, one pixel per thread) back with
-//     tcgen05.ld for the epilogue.
-// The wait on the mbarrier is bounded: past it the block records the failure in *err, waits once
-// more (bounded) for its MMAs, frees its tensor memory and writes nothing.
+// The same implicit GEMM and epilogues as k_conv3x3 on the fifth-generation tensor cores.  A tile is
+// a segment of at most 128 pixels of one image row (M = 128 accumulator rows, one per pixel) x N
+// output channels (N = COUT, at least 16 as the M = 128 shape requires; padded rows of B are zero)
+// over K = 9 taps x CIN channels.  No im2col tile is built: the block stages the three input row
+// bands the tile's taps read -- rows r - 1, r, r + 1, from one pixel left of the segment to one
+// right of it, zero outside the image -- in shared memory as arrays of 16-byte pixel rows, one
+// array per group of 8 channels (the K-major canonical layout without swizzle: 8 consecutive
+// pixel rows form a core matrix).  Tap (dy, dx) is then the same arrays read from band dy, one
+// pixel row further for each step of dx: each MMA's A operand is a descriptor into the bands, and
+// the bands are contiguous in the NHWC image, so the block reads them with coalesced 16-byte
+// loads.  Blocks are persistent over tiles: they stage the weights B (N x K) and allocate the
+// tensor-memory accumulator once; per tile one thread issues the 9 CIN / 16 MMAs (M = 128, N,
+// K = 16) and commits them to an mbarrier (phase = tile parity), and each warp reads its 32
+// accumulator lanes back with tcgen05.ld for a vectorised epilogue.  A wait that runs out records
+// the failure in *err, waits once more (bounded) for the MMAs, and ends the block's tiles; the
+// block always frees its tensor memory.
 constexpr int TC_M = 128;
 constexpr int TC_WAIT = 1 << 20;
+constexpr int TC_ROWS = TC_M + 2;             // pixel rows of a band: the segment and one each side
+constexpr int TC_CGS = (TC_ROWS + 7) * 16;    // bytes per 8-channel array of a band (2192: not a
+                                              // multiple of 128, so the staging stores spread over banks)
 
 template <int CIN, int COUT>
 constexpr int tc_smem_bytes() {
-  return TC_M * 9 * CIN * 2 + (COUT < 16 ? 16 : COUT) * 9 * CIN * 2 + 16;
+  return (COUT < 16 ? 16 : COUT) * 9 * CIN * 2 + 3 * (CIN / 8) * TC_CGS + 16;
+}
+
+// tiles of an H x W image: each row split into nseg segments of at most seg <= TC_M pixels
+struct TcTiles {
+  int nseg, seg;
+};
+inline TcTiles tc_tiles(int W) {
+  const int nseg = (W + TC_M - 1) / TC_M;
+  return {nseg, (W + nseg - 1) / nseg};
 }
 
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(TC_M) k_conv3x3_tc(const __nv_bfloat16* __restrict__ X,
                                                      const __nv_bfloat16* __restrict__ Wt,
-                                                     const float* __restrict__ bias, int H, int W,
-                                                     __nv_bfloat16* __restrict__ Yb, float* __restrict__ Yf,
-                                                     const __nv_bfloat16* __restrict__ mask, int* __restrict__ err) {
+                                                     const float* __restrict__ bias, int H, int W, int nseg,
+                                                     int seg, int B, __nv_bfloat16* __restrict__ Yb,
+                                                     float* __restrict__ Yf, const __nv_bfloat16* __restrict__ mask,
+                                                     int* __restrict__ err) {
   constexpr int N = COUT < 16 ? 16 : COUT;
-  constexpr int K = 9 * CIN, KB = K / 8, NB = N / 8, MB = TC_M / 8;
+  constexpr int CG = CIN / 8, K = 9 * CIN, KB = K / 8, NB = N / 8;
   constexpr uint32_t TMEM_COLS = 32;  // a power of two >= 32 holding the N FP32 columns
-  static_assert(CIN % 8 == 0 && N % 16 == 0 && N <= 32, "tile shape");
+  static_assert(CIN % 16 == 0 && COUT % 8 == 0 && N % 16 == 0 && N <= 32, "tile shape");
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  unsigned char* sA = tc_smem;
-  unsigned char* sB = tc_smem + TC_M * K * 2;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + N * K * 2);
+  unsigned char* sB = tc_smem;                // B: core matrix (kb, nb) at (kb NB + nb) x 128 bytes
+  unsigned char* sX = tc_smem + N * K * 2;    // bands: array (band, cg) at (band CG + cg) x TC_CGS
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sX + 3 * CG * TC_CGS);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
   const int P = H * W;
   const int tid = threadIdx.x, warp = tid >> 5;
-  X += (size_t)blockIdx.y * P * CIN;
-  const size_t yo = (size_t)blockIdx.y * P * COUT;
-  const int p = blockIdx.x * TC_M + tid;  // this thread's pixel (A row, accumulator lane)
+  const int ntiles = B * H * nseg;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
@@ -244,7 +263,7 @@ __global__ void __launch_bounds__(TC_M) k_conv3x3_tc(const __nv_bfloat16* __rest
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  // B: row n of core matrix (kb, n / 8) holds Wt[k][n], k = 8 kb .. 8 kb + 7
+  // B: row n of core matrix (kb, n / 8) holds Wt[k][n], k = 8 kb .. 8 kb + 7 (zero for n >= COUT)
   for (int c = tid; c < KB * N; c += TC_M) {
     const int n = c % N, kb = c / N;
     uint32_t v[4];
@@ -257,44 +276,51 @@ __global__ void __launch_bounds__(TC_M) k_conv3x3_tc(const __nv_bfloat16* __rest
     }
     *reinterpret_cast<uint4*>(sB + (kb * NB + n / 8) * 128 + (n % 8) * 16) = make_uint4(v[0], v[1], v[2], v[3]);
   }
-  // A: row (tid % 8) of core matrix (kb, tid / 8) = channels ci0 .. ci0 + 7 of tap kb 8 / CIN
-  {
-    const int r = p / W, q = p - (p / W) * W;
-#pragma unroll 4
-    for (int kb = 0; kb < KB; ++kb) {
-      const int tap = (kb * 8) / CIN, ci0 = (kb * 8) % CIN;
-      const int rr = r + tap / 3 - 1, qq = q + tap % 3 - 1;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (p < P && rr >= 0 && rr < H && qq >= 0 && qq < W)
-        v = *reinterpret_cast<const uint4*>(X + ((size_t)rr * W + qq) * CIN + ci0);
-      *reinterpret_cast<uint4*>(sA + (kb * MB + tid / 8) * 128 + (tid % 8) * 16) = v;
-    }
-  }
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes -> tensor core reads
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
-  if (tid == 0) {
-    constexpr uint32_t idesc = tc_idesc(TC_M, N);
-#pragma unroll 1
-    for (int kk = 0; kk < K / 16; ++kk) {
-      const uint64_t ad = tc_desc(smem_u32(sA) + kk * 2 * MB * 128, MB * 128, 128);
-      const uint64_t bd = tc_desc(smem_u32(sB) + kk * 2 * NB * 128, NB * 128, 128);
-      tc_mma(tmem, ad, bd, idesc, kk > 0);
+  constexpr uint32_t idesc = tc_idesc(TC_M, N);
+  int it = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int smp = t / (H * nseg), rt = t - smp * (H * nseg);
+    const int r = rt / nseg, c0 = (rt - r * nseg) * seg, len = min(seg, W - c0);
+    const __nv_bfloat16* Xs = X + (size_t)smp * P * CIN;
+    // bands: row j of array (band, cg) = channels 8 cg .. 8 cg + 7 of pixel (r + band - 1, c0 - 1 + j)
+    for (int f = tid; f < 3 * TC_ROWS * CG; f += TC_M) {
+      const int cg = f % CG, j = (f / CG) % TC_ROWS, band = f / (CG * TC_ROWS);
+      const int rr = r + band - 1, qq = c0 - 1 + j;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (j < len + 2 && rr >= 0 && rr < H && qq >= 0 && qq < W)
+        v = *reinterpret_cast<const uint4*>(Xs + ((size_t)rr * W + qq) * CIN + cg * 8);
+      *reinterpret_cast<uint4*>(sX + (band * CG + cg) * TC_CGS + j * 16) = v;
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-  }
-  const bool ok = mbar_wait(smem_u32(bar), 0, TC_WAIT);
-  const bool failed = __syncthreads_or(!ok);
-  if (failed) {
-    if (tid == 0) atomicExch(err, 1);
-    mbar_wait(smem_u32(bar), 0, TC_WAIT);  // the MMAs may still be running: give them a last bound
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (!failed) {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes -> tensor core reads
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (tid == 0) {
+#pragma unroll 1
+      for (int tap = 0; tap < 9; ++tap) {
+        const int band = tap / 3, dx = tap % 3;  // input row r + band - 1, column offset dx - 1
+#pragma unroll
+        for (int kp = 0; kp < CG / 2; ++kp) {
+          const uint64_t ad = tc_desc(smem_u32(sX) + (band * CG + 2 * kp) * TC_CGS + dx * 16, TC_CGS, 128);
+          const uint64_t bd = tc_desc(smem_u32(sB) + (tap * CG + 2 * kp) * NB * 128, NB * 128, 128);
+          tc_mma(tmem, ad, bd, idesc, (tap | kp) != 0);
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(bar))
+                   : "memory");
+    }
+    const bool ok = mbar_wait(smem_u32(bar), it & 1, TC_WAIT);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      mbar_wait(smem_u32(bar), it & 1, TC_WAIT);  // the MMAs may still be running: a last bound
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     float acc[N];
 #pragma unroll
     for (int c8 = 0; c8 < NB; ++c8) {
@@ -303,20 +329,44 @@ __global__ void __launch_bounds__(TC_M) k_conv3x3_tc(const __nv_bfloat16* __rest
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[c8 * 8 + j] = v[j];
     }
-    if (p < P) {
+    if (tid < len) {  // accumulator lane tid = pixel c0 + tid of row r
+      const size_t o = ((size_t)smp * P + (size_t)r * W + c0 + tid) * COUT;
+      if (MODE == 1) {
 #pragma unroll
-      for (int co = 0; co < COUT; ++co) {
-        const float v = acc[co] + (bias ? bias[co] : 0.f);
-        const size_t o = yo + (size_t)p * COUT + co;
-        if (MODE == 0) {
-          Yb[o] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
-        } else if (MODE == 1) {
-          Yf[o] = v;
-        } else {
-          Yb[o] = __float2bfloat16_rn(__bfloat162float(mask[o]) > 0.f ? v : 0.f);
+        for (int c4 = 0; c4 < COUT / 4; ++c4) {
+          float4 v;
+          v.x = acc[4 * c4 + 0] + (bias ? bias[4 * c4 + 0] : 0.f);
+          v.y = acc[4 * c4 + 1] + (bias ? bias[4 * c4 + 1] : 0.f);
+          v.z = acc[4 * c4 + 2] + (bias ? bias[4 * c4 + 2] : 0.f);
+          v.w = acc[4 * c4 + 3] + (bias ? bias[4 * c4 + 3] : 0.f);
+          *reinterpret_cast<float4*>(Yf + o + 4 * c4) = v;
+        }
+      } else {
+#pragma unroll
+        for (int c8 = 0; c8 < COUT / 8; ++c8) {
+          uint4 m4 = make_uint4(0u, 0u, 0u, 0u);
+          if (MODE == 2) m4 = *reinterpret_cast<const uint4*>(mask + o + 8 * c8);
+          const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+          uint32_t packed[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int co = 8 * c8 + 2 * j;
+            float a = acc[co] + (bias ? bias[co] : 0.f), b = acc[co + 1] + (bias ? bias[co + 1] : 0.f);
+            if (MODE == 0) {
+              a = a > 0.f ? a : 0.f;
+              b = b > 0.f ? b : 0.f;
+            } else {
+              a = __uint_as_float(mw[j] << 16) > 0.f ? a : 0.f;           // bf16 (low half) -> fp32
+              b = __uint_as_float(mw[j] & 0xFFFF0000u) > 0.f ? b : 0.f;  // bf16 (high half)
+            }
+            packed[j] = pack_bf16(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+          }
+          *reinterpret_cast<uint4*>(Yb + o + 8 * c8) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
         }
       }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();  // the next tile's staging and MMAs come after every read of this one
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -326,23 +376,28 @@ __global__ void __launch_bounds__(TC_M) k_conv3x3_tc(const __nv_bfloat16* __rest
 
 // ---------------------------------------------------------------- data movement
 // Per-sample scales: dscale[smp][c] = RMS over the image of channel c of d = s - q, and
-// dscale[smp][4 + c] that of D = s - 2 q + q2 (1 when q2 is null); at least 1e-30.  One block per
-// sample; FP64 sums reduced in a fixed order (deterministic).
+// dscale[smp][4 + c] that of D = s - 2 q + q2 (1 when q2 is null); at least 1e-30.  Two passes,
+// both in a fixed order (deterministic): block (b, smp) of k_ws_rms_part sums the squares of
+// pixels [b chunk, (b + 1) chunk) in FP64, thread-strided and then by a tree over its threads, into
+// part[smp][b][8]; k_ws_rms_fin adds a sample's block partials in block order.
+constexpr int WS_RMS_BLOCKS = 256;  // most blocks per sample of the first pass
+
 template <typename T>
-__global__ void k_ws_rms(const T* __restrict__ s, const T* __restrict__ q, const T* __restrict__ q2, int P,
-                         float* __restrict__ dscale) {
+__global__ void k_ws_rms_part(const T* __restrict__ s, const T* __restrict__ q, const T* __restrict__ q2, int P,
+                              int chunk, double* __restrict__ part) {
   __shared__ double red[8][256];
-  const int smp = blockIdx.x;
+  const int smp = blockIdx.y, b = blockIdx.x;
+  const int i0 = b * chunk, i1 = min(P, i0 + chunk);
   double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  for (size_t i = threadIdx.x; i < (size_t)P; i += blockDim.x) {
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const size_t o = ((size_t)smp * P + i) * 4;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const double a = s[o + c], b = q[o + c];
-      const double d = a - b;
+      const double a = s[o + c], bq = q[o + c];
+      const double d = a - bq;
       acc[c] = fma(d, d, acc[c]);
       if (q2) {
-        const double D = a - 2.0 * b + (double)q2[o + c];
+        const double D = a - 2.0 * bq + (double)q2[o + c];
         acc[4 + c] = fma(D, D, acc[4 + c]);
       }
     }
@@ -357,9 +412,15 @@ __global__ void k_ws_rms(const T* __restrict__ s, const T* __restrict__ q, const
     }
     __syncthreads();
   }
-  if (threadIdx.x < 8)
-    dscale[smp * 8 + threadIdx.x] = (threadIdx.x >= 4 && !q2) ? 1.f
-                                    : (float)fmax(sqrt(red[threadIdx.x][0] / (double)P), 1e-30);
+  if (threadIdx.x < 8) part[((size_t)smp * gridDim.x + b) * 8 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_ws_rms_fin(const double* __restrict__ part, int nblk, int P, int has_q2, float* __restrict__ dscale) {
+  const int smp = blockIdx.x, c = threadIdx.x;
+  if (c >= 8) return;
+  double sum = 0.0;
+  for (int b = 0; b < nblk; ++b) sum += part[((size_t)smp * nblk + b) * 8 + c];
+  dscale[smp * 8 + c] = (c >= 4 && !has_q2) ? 1.f : (float)fmax(sqrt(sum / (double)P), 1e-30);
 }
 
 // Input image of the network from the states s, q, q2 (N x 4 each, fp64 node major or fp32
@@ -618,8 +679,9 @@ struct ch_ws_s {
   float* y = nullptr;                                              // Bmax x P x 8
   float* part = nullptr;                                           // weight-gradient partials
   float* loss_part = nullptr;
+  double* rms_part = nullptr;  // Bmax x WS_RMS_BLOCKS x 8: first-pass partials of the RMS scales
   bool fresh = false;  // bf16 copies up to date
-  int engine = 0;      // convolutions: 0 mma.sync (warp-level), 1 tcgen05 (tensor memory)
+  int engine = 1;      // convolutions: 0 mma.sync (warp-level), 1 tcgen05 (tensor memory)
   int* err_host = nullptr;  // pinned, device-mapped: set by a tcgen05 block whose MMA wait ran out
   int* err_dev = nullptr;
   ch::Alloc mem;
@@ -666,13 +728,25 @@ static ch_status ws_tc_setup() {
   return CH_OK;
 }
 
+// The per-sample RMS scales of B samples into w->dscale (two fixed-order passes).
+template <typename T>
+static void ws_rms(ch_ws_s* w, const T* s, const T* q, const T* q2, int B, cudaStream_t st) {
+  const int P = w->P;
+  const int chunk = std::max(1024, (P + WS_RMS_BLOCKS - 1) / WS_RMS_BLOCKS);
+  const int nblk = (P + chunk - 1) / chunk;
+  k_ws_rms_part<T><<<dim3(nblk, B), 256, 0, st>>>(s, q, q2, P, chunk, w->rms_part);
+  k_ws_rms_fin<<<B, 32, 0, st>>>(w->rms_part, nblk, P, q2 != nullptr, w->dscale);
+}
+
 // One convolution of B samples on the handle's engine.
 template <int CIN, int COUT, int MODE>
 static void ws_conv(ch_ws_s* w, const __nv_bfloat16* X, const __nv_bfloat16* Wt, const float* bias,
                     __nv_bfloat16* Yb, float* Yf, const __nv_bfloat16* mask, int B, cudaStream_t st) {
   if (w->engine == 1) {
-    k_conv3x3_tc<CIN, COUT, MODE><<<dim3(blocks_for(w->P, TC_M), B), TC_M, tc_smem_bytes<CIN, COUT>(), st>>>(
-        X, Wt, bias, w->H, w->W, Yb, Yf, mask, w->err_dev);
+    const TcTiles tt = tc_tiles(w->W);
+    const int ntiles = B * w->H * tt.nseg;
+    k_conv3x3_tc<CIN, COUT, MODE><<<std::min(ntiles, 4 * 152), TC_M, tc_smem_bytes<CIN, COUT>(), st>>>(
+        X, Wt, bias, w->H, w->W, tt.nseg, tt.seg, B, Yb, Yf, mask, w->err_dev);
   } else {
     k_conv3x3<CIN, COUT, MODE><<<dim3(blocks_for(w->P, 128), B), 256, 0, st>>>(X, Wt, bias, w->H, w->W, Yb, Yf,
                                                                                  mask);
@@ -746,6 +820,7 @@ ch_status ws_create(int H, int W, int Bmax, ch_ws_s** out) {
   if (r == CH_OK) r = w->mem.get(&w->y, P * WS_COUT);
   if (r == CH_OK) r = w->mem.get(&w->part, (size_t)Bmax * nchunk * (9 * WS_C * WS_C + WS_C));
   if (r == CH_OK) r = w->mem.get(&w->loss_part, 1024);
+  if (r == CH_OK) r = w->mem.get(&w->rms_part, (size_t)Bmax * WS_RMS_BLOCKS * 8);
   if (r == CH_OK) {
     if (cudaHostAlloc(&w->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer(&w->err_dev, w->err_host, 0) != cudaSuccess) {
@@ -838,7 +913,7 @@ ch_status ws_predict(ch_ws_s* w, const double* state, const double* prev, const 
                      cudaStream_t st) {
   {
     ProfScope ps(st, K_WS_IO, 0, w->P * (32.0 * 3 + 32.0), 0.0);
-    k_ws_rms<double><<<1, 256, 0, st>>>(state, prev, prev2, w->P, w->dscale);
+    ws_rms<double>(w, state, prev, prev2, 1, st);
     k_ws_pack<double><<<dim3(blocks_for(w->P), 1), TPB, 0, st>>>(state, prev, prev2, w->P, w->norm, w->norm + 8,
                                                                   w->dscale, w->x0);
   }
@@ -866,7 +941,7 @@ ch_status ws_train_step(ch_ws_s* w, const float* x, const float* q, const float*
     return CH_ERR_ARG;
   }
   const int P = w->P;
-  k_ws_rms<float><<<B, 256, 0, st>>>(x, q, q2, P, w->dscale);
+  ws_rms<float>(w, x, q, q2, B, st);
   k_ws_pack<float><<<dim3(blocks_for(P), B), TPB, 0, st>>>(x, q, q2, P, w->norm, w->norm + 8, w->dscale, w->x0);
   CH_LAUNCHED();
   CH_TRY(ws_forward_packed(w, B, st));
@@ -990,7 +1065,7 @@ ch_status ws_train_residual(ch_ws_s* w, const ch_system_s* sys, ch_precond_s* pc
     CH_TRY(w->mem.get(&w->tmp2, (size_t)P * 4));
     CH_TRY(w->mem.get(&w->nrm, (size_t)w->Bmax * 8));
   }
-  k_ws_rms<double><<<B, 256, 0, st>>>(x, q, q2, P, w->dscale);
+  ws_rms<double>(w, x, q, q2, B, st);
   k_ws_pack<double><<<dim3(blocks_for(P), B), TPB, 0, st>>>(x, q, q2, P, w->norm, w->norm + 8, w->dscale, w->x0);
   CH_LAUNCHED();
   CH_TRY(ws_forward_packed(w, B, st));

@@ -4,10 +4,13 @@
     python -m paper_2204_03575_gb300.profile_case --batch 64 --precision 1 --restart 30 --warmup 0 --steps 2
     python -m paper_2204_03575_gb300.profile_case --nx 128 --ny 128 --nz 32 --potential 3 --steps 1
     python -m paper_2204_03575_gb300.profile_case --nx 512 --ny 512 --steps 1 --project 1024
+    python -m paper_2204_03575_gb300.profile_case --nx 256 --ny 256 --steps 3 --ws 4
 
 Builds the mesh, system, preconditioner and state on cuda:0 (seeded initial state, paper
 parameters), runs the warm-up and timed steps and prints per-step statistics; with --project G,
-then projects the final 2D morphology onto a G x G grid (Section 5).  Used as the
+then projects the final 2D morphology onto a G x G grid (Section 5); with --ws B, runs the
+warm-start network (seeded random weights) on the last three states: one prediction and one
+training step on a batch of B copies.  Used as the
 target of ncu captures, where the full benchmark would hold too much device memory.
 """
 import argparse
@@ -33,6 +36,8 @@ def main():
                          "graph that holds conditional nodes)")
     ap.add_argument("--precond-m", type=int, default=0)
     ap.add_argument("--pdl", type=int, default=1, help="0: plain stream-ordered launches")
+    ap.add_argument("--ws", type=int, default=0, help="batch of a warm-start network prediction and training step")
+    ap.add_argument("--ws-engine", type=int, default=1, help="warm-start convolutions: 0 mma.sync, 1 tcgen05")
     ap.add_argument("--project", type=int, default=0, help="grid size of a final morphology projection")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of one mesh: this many runs of inputs.batch_runs(n, seed=0)")
@@ -61,14 +66,30 @@ def main():
         state.init_seeded(0.33, 0.33, 0.01, seed=0)
     for _ in range(a.warmup):
         state.step()
+    hist = []
     ms, its = [], []
     for k in range(a.steps):
         s = state.step()
         ms.append(s["ms"])
         its.append(sum(s["iters"]))
         print(json.dumps({"step": k, **s}), flush=True)
+        if a.ws and not a.batch and not a.nz:
+            g = state.get()
+            hist = (hist + [torch.stack([g["phi_p"], g["phi_nfa"], g["mu_p"], g["mu_nfa"]], 1).contiguous()])[-3:]
     if a.steps:
         print(json.dumps({"steps": a.steps, "mean_ms": sum(ms) / len(ms), "iters": sum(its)}), flush=True)
+    if a.ws and len(hist) == 3:
+        import numpy as np
+        net = ch.WarmStartNet(a.ny + 1, a.nx + 1, max_batch=a.ws)
+        net.set_engine(a.ws_engine)
+        net.set_params((np.random.default_rng(0).standard_normal(ch.lib().ch_ws_nparams()) * 0.1).astype(np.float32))
+        q2, q, s4 = hist
+        pred = net.predict(s4, q, q2)
+        batch = [t.float().unsqueeze(0).repeat(a.ws, 1, 1).contiguous() for t in (s4, q, q2, 2 * s4 - q)]
+        loss = net.train_step(*batch, 0.0)
+        torch.cuda.synchronize()
+        print(json.dumps({"ws_batch": a.ws, "pred_finite": bool(torch.isfinite(pred).all()), "loss": loss}),
+              flush=True)
     if a.project and not a.batch and not a.nz:
         g = state.get()
         polymer, _, _ = ch.morphology_project(g["phi_p"], g["phi_nfa"], a.nx, a.ny, 1.0, 1.0, a.project, a.project)
