@@ -464,9 +464,11 @@ static ch_status level_setup(Hierarchy* h, int l, const ch_params& p, cudaStream
   CH_TRY(power_estimate(A, dinv, st, &lam));
   if (lam > 0.0 && std::isfinite(lam)) rho = std::min(rho, 1.05 * lam);
   h->rho.push_back(rho);
-  // coarse_max 0: 512 rows for FP64 V-cycles, 4096 for FP32 (where the dense inverse is half the
+  // coarse_max 0: 512 rows for FP64 V-cycles, 2048 for FP32 (where the dense inverse is half the
   // bytes); measured on 512 x 512: the dense solve beats the per-level launch chain up to there
-  const int cmax = p.coarse_max > 0 ? p.coarse_max : (h->precision == 0 ? 512 : 4096);
+  // (FP32 with programmatic dependent launch: 6.85 / 6.77 / 6.78 / 6.78 ms per step at
+  // 4096 / 2048 / 1024 / 512 rows)
+  const int cmax = p.coarse_max > 0 ? p.coarse_max : (h->precision == 0 ? 512 : 2048);
   if (n <= cmax) {
     *last = true;
     return CH_OK;
@@ -942,7 +944,8 @@ ch_status hierarchy_level_export(const Hierarchy* h, int l, int64_t* rows, int64
 // successor's blocks are resident when it finishes; not at all in FP64, where the kernels are
 // bound by the FP64 pipe and successor blocks that arrive early crowd the SMs unevenly.  Measured
 // on the 512 x 512 mesh, ms per time step: FP32 V-cycles 8.33 plain, 8.06 without the trigger,
-// 7.96 with it; FP64 V-cycles 16.90 plain, 16.78 without, 17.70 with it.
+// 7.96 with it; FP64 V-cycles 16.90 plain, 16.78 without, 17.70 with it (16.75 when only grids of
+// at most 152 blocks trigger, 17.28 at most 608).
 template <typename T>
 __device__ __forceinline__ void pdl_trigger_t() {
   if (sizeof(T) == 4) pdl_trigger();

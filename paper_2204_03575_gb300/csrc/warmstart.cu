@@ -126,6 +126,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// 16-byte asynchronous copy global -> shared; with valid = false the 16 bytes are zero-filled and
+// nothing is read (src must still be a mapped address)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // ---------------------------------------------------------------- 3x3 convolution (implicit GEMM)
 // Y[p][co] = sum_{tap, ci} X[p + off(tap)][ci] Wt[tap][ci][co] (+ bias[co]), p = r W + q, then
 //   MODE 0: Yb = bf16(relu(.))                          (hidden layer forward)
@@ -263,19 +273,9 @@ __global__ void __launch_bounds__(TC_M) k_conv3x3_tc(const __nv_bfloat16* __rest
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  // B: row n of core matrix (kb, n / 8) holds Wt[k][n], k = 8 kb .. 8 kb + 7 (zero for n >= COUT)
-  for (int c = tid; c < KB * N; c += TC_M) {
-    const int n = c % N, kb = c / N;
-    uint32_t v[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int k = kb * 8 + 2 * j;
-      const __nv_bfloat16 lo = n < COUT ? Wt[k * COUT + n] : __float2bfloat16_rn(0.f);
-      const __nv_bfloat16 hi = n < COUT ? Wt[(k + 1) * COUT + n] : __float2bfloat16_rn(0.f);
-      v[j] = pack_bf16(lo, hi);
-    }
-    *reinterpret_cast<uint4*>(sB + (kb * NB + n / 8) * 128 + (n % 8) * 16) = make_uint4(v[0], v[1], v[2], v[3]);
-  }
+  // B: Wt is already in the canonical layout (k_ws_tc_layout): copied as it is
+  for (int c = tid; c < KB * N; c += TC_M) cp_async16(smem_u32(sB) + c * 16, Wt + c * 8, true);  // N K / 8 chunks
+  cp_async_wait_all();
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -290,12 +290,12 @@ __global__ void __launch_bounds__(TC_M) k_conv3x3_tc(const __nv_bfloat16* __rest
     for (int f = tid; f < 3 * TC_ROWS * CG; f += TC_M) {
       const int cg = f % CG, j = (f / CG) % TC_ROWS, band = f / (CG * TC_ROWS);
       const int rr = r + band - 1, qq = c0 - 1 + j;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (j < len + 2 && rr >= 0 && rr < H && qq >= 0 && qq < W)
-        v = *reinterpret_cast<const uint4*>(Xs + ((size_t)rr * W + qq) * CIN + cg * 8);
-      *reinterpret_cast<uint4*>(sX + (band * CG + cg) * TC_CGS + j * 16) = v;
+      const bool in = j < len + 2 && rr >= 0 && rr < H && qq >= 0 && qq < W;
+      cp_async16(smem_u32(sX + (band * CG + cg) * TC_CGS + j * 16),
+                 in ? Xs + ((size_t)rr * W + qq) * CIN + cg * 8 : Xs, in);  // zero outside the image
     }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes -> tensor core reads
+    cp_async_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // shared writes -> tensor core reads
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -636,6 +636,20 @@ __global__ void k_ws_adam(float* __restrict__ w, const float* __restrict__ g, fl
   w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// The weights of one convolution (Wt[k][co], k = tap CIN + ci) as the tcgen05 path's B operand:
+// N x K (N >= COUT output channels, padded rows zero) in the K-major canonical layout of 8-row x
+// 16-byte core matrices, core matrix (kb, nb) at element (kb N/8 + nb) x 64, row n % 8 of it at
+// (n % 8) x 8; a block copies it to shared memory as it is.
+__global__ void k_ws_tc_layout(const __nv_bfloat16* __restrict__ Wt, int K, int cout, int N,
+                               __nv_bfloat16* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * K) return;
+  const int NB = N / 8, c = idx / 8, e = idx % 8;
+  const int kb = c / (NB * 8), rem = c % (NB * 8), n = (rem / 8) * 8 + rem % 8;
+  const int k = kb * 8 + e;
+  out[idx] = n < cout ? Wt[k * cout + n] : __float2bfloat16_rn(0.f);
+}
+
 // BF16 copies of the weights: forward [tap][ci][co] and, for the backward pass through the data,
 // flipped [8 - tap][co][ci] with the channel counts of that pass (co padded to CPAD rows).
 __global__ void k_ws_bf16(const float* __restrict__ w, int cin, int cout, int cout_used, int cpad,
@@ -664,6 +678,8 @@ struct ch_ws_s {
   int adam_t = 0;
   __nv_bfloat16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr;     // forward copies
   __nv_bfloat16 *w2f = nullptr, *w3f = nullptr;                    // flipped copies (backward)
+  __nv_bfloat16 *c1 = nullptr, *c2 = nullptr, *c3 = nullptr;       // the same as tcgen05 B operands
+  __nv_bfloat16 *c2f = nullptr, *c3f = nullptr;
   float* norm = nullptr;  // mean[8], inv_std[8], out_scale[4]
   float* dscale = nullptr;  // Bmax x 8: RMS of the last change and of the second difference per sample and channel
   float* t = nullptr;       // Bmax x P x 4: dE/dy of the state-space loss
@@ -708,6 +724,11 @@ static ch_status ws_refresh(ch_ws_s* w, cudaStream_t st) {
   k_ws_bf16<<<blocks_for(9 * WS_CIN * WS_C), TPB, 0, st>>>(p.w1, WS_CIN, WS_C, WS_C, 0, w->w1, nullptr);
   k_ws_bf16<<<blocks_for(9 * WS_C * WS_C), TPB, 0, st>>>(p.w2, WS_C, WS_C, WS_C, WS_C, w->w2, w->w2f);
   k_ws_bf16<<<blocks_for(9 * 16 * WS_C), TPB, 0, st>>>(p.w3, WS_C, WS_COUT, 4, 16, w->w3, w->w3f);
+  k_ws_tc_layout<<<blocks_for(9 * WS_CIN * WS_C), TPB, 0, st>>>(w->w1, 9 * WS_CIN, WS_C, WS_C, w->c1);
+  k_ws_tc_layout<<<blocks_for(9 * WS_C * WS_C), TPB, 0, st>>>(w->w2, 9 * WS_C, WS_C, WS_C, w->c2);
+  k_ws_tc_layout<<<blocks_for(9 * WS_C * 16), TPB, 0, st>>>(w->w3, 9 * WS_C, WS_COUT, 16, w->c3);
+  k_ws_tc_layout<<<blocks_for(9 * WS_C * WS_C), TPB, 0, st>>>(w->w2f, 9 * WS_C, WS_C, WS_C, w->c2f);
+  k_ws_tc_layout<<<blocks_for(9 * 16 * WS_C), TPB, 0, st>>>(w->w3f, 9 * 16, WS_C, WS_C, w->c3f);
   CH_LAUNCHED();
   w->fresh = true;
   return CH_OK;
@@ -740,13 +761,14 @@ static void ws_rms(ch_ws_s* w, const T* s, const T* q, const T* q2, int B, cudaS
 
 // One convolution of B samples on the handle's engine.
 template <int CIN, int COUT, int MODE>
-static void ws_conv(ch_ws_s* w, const __nv_bfloat16* X, const __nv_bfloat16* Wt, const float* bias,
-                    __nv_bfloat16* Yb, float* Yf, const __nv_bfloat16* mask, int B, cudaStream_t st) {
+static void ws_conv(ch_ws_s* w, const __nv_bfloat16* X, const __nv_bfloat16* Wt, const __nv_bfloat16* Bc,
+                    const float* bias, __nv_bfloat16* Yb, float* Yf, const __nv_bfloat16* mask, int B,
+                    cudaStream_t st) {
   if (w->engine == 1) {
     const TcTiles tt = tc_tiles(w->W);
     const int ntiles = B * w->H * tt.nseg;
     k_conv3x3_tc<CIN, COUT, MODE><<<std::min(ntiles, 4 * 152), TC_M, tc_smem_bytes<CIN, COUT>(), st>>>(
-        X, Wt, bias, w->H, w->W, tt.nseg, tt.seg, B, Yb, Yf, mask, w->err_dev);
+        X, Bc, bias, w->H, w->W, tt.nseg, tt.seg, B, Yb, Yf, mask, w->err_dev);
   } else {
     k_conv3x3<CIN, COUT, MODE><<<dim3(blocks_for(w->P, 128), B), 256, 0, st>>>(X, Wt, bias, w->H, w->W, Yb, Yf,
                                                                                  mask);
@@ -774,15 +796,15 @@ static ch_status ws_forward_packed(ch_ws_s* w, int B, cudaStream_t st) {
   const WsParams p = ws_views(w->params);
   {
     ProfScope ps(st, K_WS_CONV, 1, (double)B * w->P * (16 + 32) * 2, (double)B * w->P * 9 * 16 * 32);
-    ws_conv<WS_CIN, WS_C, 0>(w, w->x0, w->w1, p.b1, w->a1, nullptr, nullptr, B, st);
+    ws_conv<WS_CIN, WS_C, 0>(w, w->x0, w->w1, w->c1, p.b1, w->a1, nullptr, nullptr, B, st);
   }
   {
     ProfScope ps(st, K_WS_CONV, 1, (double)B * w->P * (32 + 32) * 2, (double)B * w->P * 9 * 32 * 32);
-    ws_conv<WS_C, WS_C, 0>(w, w->a1, w->w2, p.b2, w->a2, nullptr, nullptr, B, st);
+    ws_conv<WS_C, WS_C, 0>(w, w->a1, w->w2, w->c2, p.b2, w->a2, nullptr, nullptr, B, st);
   }
   {
     ProfScope ps(st, K_WS_CONV, 1, (double)B * w->P * (32 * 2 + 8 * 4), (double)B * w->P * 9 * 32 * 8);
-    ws_conv<WS_C, WS_COUT, 1>(w, w->a2, w->w3, p.b3, nullptr, w->y, nullptr, B, st);
+    ws_conv<WS_C, WS_COUT, 1>(w, w->a2, w->w3, w->c3, p.b3, nullptr, w->y, nullptr, B, st);
   }
   CH_LAUNCHED();
   return CH_OK;
@@ -806,6 +828,11 @@ ch_status ws_create(int H, int W, int Bmax, ch_ws_s** out) {
   if (r == CH_OK) r = w->mem.get(&w->w3, 9 * WS_C * WS_COUT);
   if (r == CH_OK) r = w->mem.get(&w->w2f, 9 * WS_C * WS_C);
   if (r == CH_OK) r = w->mem.get(&w->w3f, 9 * 16 * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->c1, 9 * WS_CIN * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->c2, 9 * WS_C * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->c3, 9 * WS_C * 16);
+  if (r == CH_OK) r = w->mem.get(&w->c2f, 9 * WS_C * WS_C);
+  if (r == CH_OK) r = w->mem.get(&w->c3f, 9 * 16 * WS_C);
   if (r == CH_OK) r = w->mem.get(&w->norm, 20);
   if (r == CH_OK) r = w->mem.get(&w->dscale, (size_t)Bmax * 8);
   if (r == CH_OK) r = w->mem.get(&w->t, P * 4);
@@ -881,8 +908,8 @@ ch_status ws_set_norm(ch_ws_s* w, const float* host20, cudaStream_t st) {
 static ch_status ws_backward_update(ch_ws_s* w, int B, float lr, cudaStream_t st) {
   const int P = w->P;
   // backward through the data: dz2 = (W3 flipped * dy) . [a2 > 0];  dz1 = (W2 flipped * dz2) . [a1 > 0]
-  ws_conv<16, WS_C, 2>(w, w->dy, w->w3f, nullptr, w->dz2, nullptr, w->a2, B, st);
-  ws_conv<WS_C, WS_C, 2>(w, w->dz2, w->w2f, nullptr, w->dz1, nullptr, w->a1, B, st);
+  ws_conv<16, WS_C, 2>(w, w->dy, w->w3f, w->c3f, nullptr, w->dz2, nullptr, w->a2, B, st);
+  ws_conv<WS_C, WS_C, 2>(w, w->dz2, w->w2f, w->c2f, nullptr, w->dz1, nullptr, w->a1, B, st);
   CH_LAUNCHED();
   // weight gradients, per sample and pixel chunk, then summed in order
   const int nchunk = (P + WS_CHUNK - 1) / WS_CHUNK;

@@ -117,33 +117,90 @@ def train(data, net, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: in
                  "out_scale": out_scale.tolist(), "pairs": S, "nodes": N}
 
 
+def validation_iterations(net, nx: int, ny: int, seed: int = 999, steps: int = 12, state=None):
+    """Mean FGMRES iterations per step (worse species) over steps 4 .. steps + 3 of a seeded run whose
+    steps are ch_step_learned with `net` (seed 999: neither a training seed nor the timed seed 1000)."""
+    state = state or make_state(nx, ny)
+    b0, b1 = seed_bases(seed)
+    state.init_seeded(b0, b1, 0.01, seed=int(seed))
+    for _ in range(3):  # ch_step_learned starts from the previous state for three steps
+        state.step_learned(net)
+    its = [max(state.step_learned(net)["iters"]) for _ in range(steps)]
+    return float(np.mean(its))
+
+
 def train_residual(data, net, system, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: int = 0,
-                   use_fields: bool = True, precond=None):
+                   use_fields: bool = True, precond=None, val_frac: float = 0.1, select: str = "iterations",
+                   val_seed: int = 999, val_steps: int = 12):
     """Fit `net` against the residual of the time step (ch_ws_train_residual) on fp64 `data` =
     (Q2, Q, X, Y) from generate_pairs(..., dtype=torch.float64); Y only sets the normalisation.
-    With `precond` (a ch.Precond of `system`) the residual is measured in its norm.  The per-epoch
-    loss is the mean ln(|r|^2 / |r_linear extrapolation|^2): below 0 beats linear extrapolation."""
+    With `precond` (a ch.Precond of `system`) the residual is measured in its norm.  The loss is
+    the mean ln(|r|^2 / |r_linear extrapolation|^2): below 0 beats linear extrapolation.
+
+    The last `val_frac` of the pairs (the last seeds' trajectories: generate_pairs orders them by
+    seed) are held out; their loss (lr = 0: no update) is reported for exactly theta = 1 -- the
+    quadratic extrapolation, the network's starting point -- and after every epoch.  Model
+    selection among those candidates: select = "iterations" (default) keeps the one with the
+    fewest FGMRES iterations per step on a validation run (validation_iterations, seed val_seed,
+    the solver's own measure of a guess), select = "loss" the lowest held-out loss.  Either way
+    theta = 1 is a candidate, so training can only improve on it as the selection measures it."""
     Q2, Q, X, Y = data
     S, N = X.shape[0], X.shape[1]
-    mean, inv_std, out_scale = net.fit_norm(X)  # computed on the device by the library
+    nval = int(round(S * val_frac)) if val_frac > 0 else 0
+    St = S - nval
+    mean, inv_std, out_scale = net.fit_norm(X[:St])  # computed on the device by the library
     if not use_fields:
         mean[:4], inv_std[:4] = 0.0, 0.0
         net.set_norm(mean, inv_std, out_scale)
+
+    def held_out_loss():
+        tot, nb = 0.0, 0
+        for i in range(St, S, batch):
+            sl = slice(i, min(i + batch, S))
+            tot += net.train_residual(system, X[sl].contiguous(), Q[sl].contiguous(), Q2[sl].contiguous(), 0.0,
+                                      precond=precond)
+            nb += 1
+        return tot / nb if nb else float("nan")
+
+    nx, ny = net.W - 1, net.H - 1
+    vstate = make_state(nx, ny) if select == "iterations" else None
+
+    def score(loss):
+        return validation_iterations(net, nx, ny, val_seed, val_steps, vstate) if vstate else loss
+
+    quad = np.zeros(net.nparams, np.float32)
+    quad[-8:-4] = 1.0  # zero weights, output bias 1: theta = out_scale = 1
+    best, quad_loss, scores = None, None, []
+    if nval:
+        net.set_params(quad)
+        quad_loss = held_out_loss()
+        scores.append(score(quad_loss))
+        best = (scores[-1], quad, "quadratic")
     net.set_params(init_params(net.nparams, seed))
     g = torch.Generator(device="cpu").manual_seed(seed)
-    losses = []
+    losses, val = [], []
     for ep in range(epochs):
-        perm = torch.randperm(S, generator=g)
+        perm = torch.randperm(St, generator=g)
         lr_ep = lr * (0.5 ** (ep // max(1, epochs // 3)))
         tot, nb = 0.0, 0
-        for i in range(0, S - batch + 1, batch):
+        for i in range(0, St - batch + 1, batch):
             idx = perm[i:i + batch].to(X.device)
             tot += net.train_residual(system, X[idx].contiguous(), Q[idx].contiguous(), Q2[idx].contiguous(), lr_ep,
                                       precond=precond)
             nb += 1
         losses.append(tot / max(nb, 1))
-    return net, {"loss_per_epoch": losses, "mean": mean.tolist(), "inv_std": inv_std.tolist(),
-                 "out_scale": out_scale.tolist(), "pairs": S, "nodes": N}
+        if nval:
+            val.append(held_out_loss())
+            scores.append(score(val[-1]))
+            if scores[-1] < best[0]:
+                best = (scores[-1], net.get_params()[0].copy(), f"epoch {ep + 1}")
+    if best is not None:
+        net.set_params(best[1])
+    return net, {"loss_per_epoch": losses, "held_out_loss_per_epoch": val,
+                 "held_out_loss_quadratic": quad_loss, "selection": select,
+                 "selection_scores_quadratic_then_epochs": scores, "mean": mean.tolist(),
+                 "inv_std": inv_std.tolist(), "out_scale": out_scale.tolist(), "pairs": S, "held_out_pairs": nval,
+                 "nodes": N, "selected": best[2] if best else f"epoch {epochs}"}
 
 
 def zero_net(nx: int, ny: int):

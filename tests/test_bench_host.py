@@ -56,6 +56,25 @@ def test_roofline_of_an_hbm_bound_kernel():
     assert r_fallback["peak"] == 6800.0 and r_fallback["peak_source"] == "fallback"
 
 
+def test_roofline_takes_the_in_sequence_launch_time():
+    """With the kernel timed in sequence (back-to-back launches in one graph) the launch time is
+    that one, the event-timed figures are kept beside it, and a rate above the HBM peak (an
+    L2-resident working set) carries the note that says so; another dominant kernel ignores it."""
+    prof = {"cheb_step_f32": {"ms": 50.0, "launches": 7000, "bytes": 7000 * 18.6e6, "fmas": 7000 * 4.73e6}}
+    seq = {"avg_launch_us": 2.4, "achieved_GBps": 7750.0}
+    r = bench.roofline(prof, PEAKS, seq)
+    achieved = 18.6e6 / 2.4e-6 / 1e9
+    assert math.isclose(r["achieved"], achieved, rel_tol=1e-12) and r["avg_launch_us"] == 2.4
+    assert math.isclose(r["event_timed"]["avg_launch_us"], 1e3 * 50.0 / 7000, rel_tol=1e-12)
+    assert r["in_sequence"] is seq and r["frac"] > 1.0 and "L2" in r["note"]
+    r64 = bench.roofline(_prof(), PEAKS, {"avg_launch_us": 11.76})
+    assert r64["bound"] == "alu"
+    assert math.isclose(r64["achieved"], 2 * 4.73e6 / 11.76e-6 / 1e12, rel_tol=1e-12)
+    other = {"orth_dots_f64": {"ms": 5.0, "launches": 160, "bytes": 160 * 40e6, "fmas": 160 * 3e6}}
+    r_other = bench.roofline(other, PEAKS, seq)
+    assert "in_sequence" not in r_other and math.isclose(r_other["avg_launch_us"], 1e3 * 5.0 / 160)
+
+
 def test_top_kernels_are_sorted_shares():
     t = bench.top_kernels(_prof())
     names = list(t)
