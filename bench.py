@@ -479,7 +479,7 @@ def learned_section(torch, ch, nx, K, flush, ranks):
            "train_loss_first_last_epoch": [info["loss_per_epoch"][0], info["loss_per_epoch"][-1]],
            "held_out_loss_per_epoch": info["held_out_loss_per_epoch"],
            "held_out_loss_quadratic": info["held_out_loss_quadratic"], "selected": info["selected"],
-           "selection": "fewest FGMRES iterations per step on a validation run (seed 999, steps 4..15) among "
+           "selection": "fewest FGMRES iterations per step on a validation run (seed 999, steps 4..43) among "
                         "theta = 1 and the network after each epoch",
            "selection_iterations_quadratic_then_epochs": info["selection_scores_quadratic_then_epochs"],
            "loss_meaning": "mean ln(|r|^2 / |r_linear extrapolation|^2) of the step residual; the last 10% of "

@@ -117,7 +117,7 @@ def train(data, net, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: in
                  "out_scale": out_scale.tolist(), "pairs": S, "nodes": N}
 
 
-def validation_iterations(net, nx: int, ny: int, seed: int = 999, steps: int = 12, state=None):
+def validation_iterations(net, nx: int, ny: int, seed: int = 999, steps: int = 40, state=None):
     """Mean FGMRES iterations per step (worse species) over steps 4 .. steps + 3 of a seeded run whose
     steps are ch_step_learned with `net` (seed 999: neither a training seed nor the timed seed 1000)."""
     state = state or make_state(nx, ny)
@@ -131,7 +131,7 @@ def validation_iterations(net, nx: int, ny: int, seed: int = 999, steps: int = 1
 
 def train_residual(data, net, system, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: int = 0,
                    use_fields: bool = True, precond=None, val_frac: float = 0.1, select: str = "iterations",
-                   val_seed: int = 999, val_steps: int = 12):
+                   val_seed: int = 999, val_steps: int = 40):
     """Fit `net` against the residual of the time step (ch_ws_train_residual) on fp64 `data` =
     (Q2, Q, X, Y) from generate_pairs(..., dtype=torch.float64); Y only sets the normalisation.
     With `precond` (a ch.Precond of `system`) the residual is measured in its norm.  The loss is
