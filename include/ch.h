@@ -119,6 +119,12 @@ typedef struct ch_params {
                                 drains and wait on the device for its results (griddepcontrol), which
                                 hides the launch gap between the many short kernels of a step; 0: plain
                                 stream-ordered launches.  Same arithmetic, bitwise the same results */
+  int32_t gs_reorth;         /* FGMRES's Gram-Schmidt: 0 (default) classical Gram-Schmidt twice at every
+                                Arnoldi step; 1 selective reorthogonalisation -- one projection, and the
+                                second only for a species whose vector lost more than half its squared
+                                norm to it (||w'|| < ||w|| / sqrt(2)).  On the 512 x 512 workload the
+                                second pass is still needed on ~72 % of the steps, which makes 1 slightly
+                                slower than 0; ch_step_stats.reorth counts the second passes */
 } ch_params;
 
 /* Per-step statistics (host struct). */
@@ -130,6 +136,8 @@ typedef struct ch_step_stats {
   double mass[2];            /* int phi_h = 1^T M phi^{k+1} per species */
   double ms;                 /* wall time of the step (ms, CUDA events) */
   int32_t warm[2];           /* ch_step_guess: 1 if the caller's guess was used as initial iterate */
+  int32_t reorth[2];         /* FGMRES: Arnoldi steps that took the second Gram-Schmidt pass (all of them
+                                with gs_reorth = 0) */
 } ch_step_stats;
 
 typedef struct ch_mesh_s ch_mesh_t;

@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
         ("precond_M", ctypes.c_int32), ("cheb_M_steps", ctypes.c_int32),
         ("chi_pn", ctypes.c_double), ("chi_ps", ctypes.c_double), ("chi_ns", ctypes.c_double),
         ("N_p", ctypes.c_double), ("N_nfa", ctypes.c_double), ("N_s", ctypes.c_double),
-        ("fh_delta", ctypes.c_double), ("pdl", ctypes.c_int32),
+        ("fh_delta", ctypes.c_double), ("pdl", ctypes.c_int32), ("gs_reorth", ctypes.c_int32),
     ]
 
     def __init__(self, **kw):
@@ -66,11 +66,12 @@ class StepStats(ctypes.Structure):
     """Mirror of ch_step_stats."""
     _fields_ = [("iters", ctypes.c_int32 * 2), ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("relres", ctypes.c_double * 2), ("mass", ctypes.c_double * 2), ("ms", ctypes.c_double),
-                ("warm", ctypes.c_int32 * 2)]
+                ("warm", ctypes.c_int32 * 2), ("reorth", ctypes.c_int32 * 2)]
 
     def as_dict(self):
         return {"iters": list(self.iters), "restarts": self.restarts, "status": self.status,
-                "relres": list(self.relres), "mass": list(self.mass), "ms": self.ms, "warm": list(self.warm)}
+                "relres": list(self.relres), "mass": list(self.mass), "ms": self.ms, "warm": list(self.warm),
+                "reorth": list(self.reorth)}
 
 
 class ProfEntry(ctypes.Structure):

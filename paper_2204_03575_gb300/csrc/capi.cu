@@ -48,6 +48,7 @@ ch_status check_params(const ch_params* p) {
          "N_p, N_nfa, N_s must be > 0");
   CH_ARG(p->fh_delta > 0 && p->fh_delta < 1, "fh_delta must be in (0, 1)");
   CH_ARG(p->pdl == 0 || p->pdl == 1, "pdl must be 0 or 1");
+  CH_ARG(p->gs_reorth == 0 || p->gs_reorth == 1, "gs_reorth must be 0 or 1");
   return CH_OK;
 }
 }  // namespace
@@ -118,6 +119,7 @@ void ch_params_default(ch_params* p) {
   d.N_s = 1.0;
   d.fh_delta = 1e-10;
   d.pdl = 1;
+  d.gs_reorth = 0;
   *p = d;
 }
 

@@ -155,7 +155,7 @@ enum KernelId {
   K_COARSE, K_VLOAD, K_VSTORE, K_SPMV_M, K_STATE_IO,
   // the same V-cycle kernels on levels below the finest (accounted separately)
   K_CHEB_FIRST_C, K_CHEB_STEP_C, K_VRESIDUAL_C, K_RESTRICT_C, K_PROLONG_C,
-  K_WS_CONV, K_WS_IO, K_GUESS, K_ELEM_LOADS, K_MR_DOT, K_MR_VEC, K_CHEB_SEMI, K_MORPH, K_COUNT
+  K_WS_CONV, K_WS_IO, K_GUESS, K_ELEM_LOADS, K_MR_DOT, K_MR_VEC, K_CHEB_SEMI, K_MORPH, K_ORTH_RE, K_COUNT
 };
 // RAII around one kernel launch: counts it with its algorithmic bytes / FMAs and, when timing
 // is on, records CUDA events around it on the launching stream.

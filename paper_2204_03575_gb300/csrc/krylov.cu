@@ -43,6 +43,9 @@ struct KrylovDev {
   unsigned int ticket;  // last-block counter of this run
   double relres_prev[2];  // initial-guess selection: residual of the previous step's state
   int warm[2];            // the caller's guess was taken for this species
+  double w2[2];           // selective reorthogonalisation: ||w||^2 before the projection
+  int reorth[2];          // ... this Arnoldi step needs the second Gram-Schmidt pass
+  int reorth_count[2];    // Arnoldi steps of this time step that took the second pass
 };
 
 // Preconditioned MINRES scalars of one run, per species (the Lanczos process on P^-1 A in the
@@ -170,6 +173,7 @@ __global__ void k_residual4(Seg sg, const int* rowptr, const int* col, const dou
       kd->bnorm[s] = bn;
       kd->tol[s] = rtol * bn;
       kd->its[s] = 0;
+      kd->reorth_count[s] = 0;
       kd->active[s] = 1;
       if (s == 0) kd->nonfinite = 0;
     }
@@ -197,10 +201,19 @@ __global__ void k_scale4(Seg sg, const double4_32a* src, double4_32a* dst, const
   }
 }
 
-// ---------------------------------------------------------------- CGS2 passes
+// ---------------------------------------------------------------- Gram-Schmidt passes
+// Classical Gram-Schmidt twice (CGS2, gs_reorth = 0):
 // MODE 0: h1[s][k] = <V_k, W>_s                       k = 0..nv-1
 // MODE 1: W -= sum_k h1[s][k] V_k;  h2[s][k] = <V_k, W>_s
 // MODE 2: W -= sum_k h2[s][k] V_k;  ||W||_s^2, then the Hessenberg / Givens update (last block)
+// Selective reorthogonalisation (gs_reorth = 1; Daniel, Gragg, Kaufman and Stewart 1976): MODE 0
+// with with_norm also records ||W||_s^2, then
+// MODE 3: W -= sum_k h1[s][k] V_k;  ||W||_s^2; a species whose norm kept at least half its square
+//         (||W'|| >= ||W|| / sqrt(2): little cancellation) takes h2 = 0 and its column now; the others
+//         are flagged for the second pass
+// MODE 4: h2[s][k] = <V_k, W>_s for the flagged species (0 for the others)
+// MODE 5: W -= sum_k h2[s][k] V_k;  ||W||_s^2, the column of the flagged species
+// Blocks of a run with no flagged species leave MODE 4 and 5 at entry.
 // <a, b>_s sums components (x, z) for species 0 and (y, w) for species 1 over the run's nodes.
 constexpr int KC = 16;                // basis vectors per chunk: 2 KC = 32 values, one per lane
 constexpr int ORTH_BLOCKS = 152 * 2;  // target grid of the segmented kernels (2 blocks per SM)
@@ -297,27 +310,64 @@ __device__ __forceinline__ void orth_dots_dispatch(int kw, const double4_32a* __
 #undef CH_ORTH_CASE
 }
 
+// Column j of the Arnoldi process for species sp once w is orthogonal to V_0..V_j with squared norm
+// hsq: h = h1 + h2 (the two Gram-Schmidt passes' coefficients), h_{j+1} = ||w||, the previous
+// Givens rotations, a new one, the residual estimate |g_{j+1}| and the cycle's stopping tests.
+__device__ __forceinline__ void arnoldi_column(KrylovDev* kd, int sp, int j, double hsq) {
+  double h[MAXM + 1];
+  for (int k = 0; k <= j; ++k) h[k] = kd->h1[sp][k] + kd->h2[sp][k];
+  const double hn = sqrt(hsq);
+  h[j + 1] = hn;
+  for (int k = 0; k < j; ++k) {  // previous rotations
+    const double t = kd->cs[sp][k] * h[k] + kd->sn[sp][k] * h[k + 1];
+    h[k + 1] = -kd->sn[sp][k] * h[k] + kd->cs[sp][k] * h[k + 1];
+    h[k] = t;
+  }
+  const double den = hypot(h[j], h[j + 1]);
+  double cs = 1.0, sn = 0.0;
+  if (den > 0.0) {
+    cs = h[j] / den;
+    sn = h[j + 1] / den;
+  }
+  kd->cs[sp][j] = cs;
+  kd->sn[sp][j] = sn;
+  h[j] = den;
+  for (int k = 0; k <= j; ++k) kd->R[sp][k][j] = h[k];
+  const double gj = kd->g[sp][j];
+  kd->g[sp][j + 1] = -sn * gj;
+  kd->g[sp][j] = cs * gj;
+  kd->k[sp] = j + 1;
+  kd->its[sp] += 1;
+  if (!isfinite(hn) || !isfinite(den)) kd->nonfinite = 1;
+  const bool breakdown = !(hn > 1e-300);
+  kd->hinv[sp] = breakdown ? 0.0 : 1.0 / hn;
+  if (fabs(kd->g[sp][j + 1]) <= kd->tol[sp] || breakdown || den == 0.0) kd->cycle_active[sp] = 0;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(TPB, 2) k_orth(Seg sg, int N, int nv, const double4_32a* __restrict__ V,
                                                double4_32a* __restrict__ W, double* partials,
-                                               KrylovDev* kds) {
+                                               KrylovDev* kds, int with_norm = 0) {
+  constexpr bool DOTS = MODE == 0 || MODE == 1 || MODE == 4;
   __shared__ double sm[(TPB / 32) * 32];
   __shared__ double coef[2][MAXM + 1];
   const int run = sg.run[blockIdx.x];
   KrylovDev* kd = kds + run;
+  if (MODE >= 4 && !(kd->reorth[0] | kd->reorth[1])) return;  // the run needs no second pass
   const int v0 = sg.lo[blockIdx.x] + threadIdx.x, v1 = sg.hi[blockIdx.x];
-  if (MODE >= 1) {
+  if (MODE == 1 || MODE == 2 || MODE == 3 || MODE == 5) {
+    const bool first = MODE == 1 || MODE == 3;
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-      coef[0][k] = MODE == 1 ? kd->h1[0][k] : kd->h2[0][k];
-      coef[1][k] = MODE == 1 ? kd->h1[1][k] : kd->h2[1][k];
+      coef[0][k] = first ? kd->h1[0][k] : kd->h2[0][k];
+      coef[1][k] = first ? kd->h1[1][k] : kd->h2[1][k];
     }
     __syncthreads();
   }
-  if (MODE == 2) {
+  if (MODE == 2 || MODE == 3 || MODE == 5) {
     for (int v = v0; v < v1; v += blockDim.x) orth_update_node(V, W, (size_t)N, nv, coef, v);
   }
   const int b0 = sg.first[run], b1 = sg.first[run + 1];
-  if (MODE <= 1) {
+  if (DOTS) {
     for (int k0 = 0; k0 < nv; k0 += KC) {
       double acc[32];
 #pragma unroll
@@ -331,15 +381,29 @@ __global__ void __launch_bounds__(TPB, 2) k_orth(Seg sg, int N, int nv, const do
       const double tot = block_sum32(acc, sm);
       if (threadIdx.x < 2 * kw) partials[(size_t)blockIdx.x * MAXV + 2 * k0 + threadIdx.x] = tot;
     }
+    const bool norm = MODE == 0 && with_norm;
+    if (norm) {  // ||W||_s^2 before the projection, into the slots after the dots
+      double acc[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) acc[t] = 0.0;
+      for (int v = v0; v < v1; v += blockDim.x) {
+        const double4_32a w = W[v];
+        acc[0] = fma(w.x, w.x, fma(w.z, w.z, acc[0]));
+        acc[1] = fma(w.y, w.y, fma(w.w, w.w, acc[1]));
+      }
+      const double bt = block_sum32(acc, sm);
+      if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + 2 * nv + threadIdx.x] = bt;
+    }
     if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
     __shared__ double tot[MAXV];
-    reduce_partials(partials, b0, b1, 2 * nv, tot);
+    reduce_partials(partials, b0, b1, 2 * nv + (norm ? 2 : 0), tot);
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
       double* dst0 = MODE == 0 ? kd->h1[0] : kd->h2[0];
       double* dst1 = MODE == 0 ? kd->h1[1] : kd->h2[1];
-      dst0[k] = tot[2 * k];
-      dst1[k] = tot[2 * k + 1];
+      dst0[k] = MODE == 4 && !kd->reorth[0] ? 0.0 : tot[2 * k];
+      dst1[k] = MODE == 4 && !kd->reorth[1] ? 0.0 : tot[2 * k + 1];
     }
+    if (norm && threadIdx.x < 2) kd->w2[threadIdx.x] = tot[2 * nv + threadIdx.x];
     if (threadIdx.x == 0) kd->ticket = 0;
   } else {
     double acc[32];
@@ -356,40 +420,34 @@ __global__ void __launch_bounds__(TPB, 2) k_orth(Seg sg, int N, int nv, const do
     __shared__ double tot[2];
     reduce_partials(partials, b0, b1, 2, tot);
     if (threadIdx.x < 2) {
-      const int s = threadIdx.x;
-      const int j = nv - 1;  // Arnoldi column
-      if (kd->cycle_active[s]) {
-        double h[MAXM + 1];
-        for (int k = 0; k <= j; ++k) h[k] = kd->h1[s][k] + kd->h2[s][k];
-        const double hn = sqrt(tot[s]);
-        h[j + 1] = hn;
-        for (int k = 0; k < j; ++k) {  // previous rotations
-          const double t = kd->cs[s][k] * h[k] + kd->sn[s][k] * h[k + 1];
-          h[k + 1] = -kd->sn[s][k] * h[k] + kd->cs[s][k] * h[k + 1];
-          h[k] = t;
+      const int sp = threadIdx.x;
+      if (MODE == 2) {
+        if (kd->cycle_active[sp]) {
+          arnoldi_column(kd, sp, nv - 1, tot[sp]);
+          kd->reorth_count[sp] += 1;
+        } else {
+          kd->hinv[sp] = 0.0;
         }
-        const double den = hypot(h[j], h[j + 1]);
-        double cs = 1.0, sn = 0.0;
-        if (den > 0.0) {
-          cs = h[j] / den;
-          sn = h[j + 1] / den;
+      } else if (MODE == 3) {
+        kd->reorth[sp] = 0;
+        if (kd->cycle_active[sp]) {
+          if (tot[sp] >= 0.5 * kd->w2[sp]) {
+            for (int k = 0; k < nv; ++k) kd->h2[sp][k] = 0.0;
+            arnoldi_column(kd, sp, nv - 1, tot[sp]);
+          } else {
+            kd->reorth[sp] = 1;
+          }
+        } else {
+          kd->hinv[sp] = 0.0;
         }
-        kd->cs[s][j] = cs;
-        kd->sn[s][j] = sn;
-        h[j] = den;
-        for (int k = 0; k <= j; ++k) kd->R[s][k][j] = h[k];
-        const double gj = kd->g[s][j];
-        kd->g[s][j + 1] = -sn * gj;
-        kd->g[s][j] = cs * gj;
-        kd->k[s] = j + 1;
-        kd->its[s] += 1;
-        if (!isfinite(hn) || !isfinite(den)) kd->nonfinite = 1;
-        const bool breakdown = !(hn > 1e-300);
-        kd->hinv[s] = breakdown ? 0.0 : 1.0 / hn;
-        if (fabs(kd->g[s][j + 1]) <= kd->tol[s] || breakdown || den == 0.0) kd->cycle_active[s] = 0;
-      } else {
-        kd->hinv[s] = 0.0;
+      } else if (kd->reorth[sp]) {  // MODE 5
+        arnoldi_column(kd, sp, nv - 1, tot[sp]);
+        kd->reorth_count[sp] += 1;
       }
+    }
+    if (MODE == 5) {
+      __syncthreads();
+      if (threadIdx.x < 2) kd->reorth[threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) kd->ticket = 0;
   }
@@ -680,6 +738,7 @@ __global__ void k_rowsum(int N, const int* rowptr, const double* val, double* ou
 // per-run statistics gathered for the host after a step
 struct RunStats {
   int its[2];
+  int reorth[2];
   double relres[2];
   double mass[2];
   int warm[2];
@@ -691,6 +750,7 @@ __global__ void k_run_stats(int nruns, const KrylovDev* kds, RunStats* out) {
   const KrylovDev* kd = kds + r;
   for (int s = 0; s < 2; ++s) {
     out[r].its[s] = kd->its[s];
+    out[r].reorth[s] = kd->reorth_count[s];
     out[r].relres[s] = kd->relres[s];
     out[r].mass[s] = kd->mass[s];
     out[r].warm[s] = kd->warm[s];
@@ -947,17 +1007,37 @@ static ch_status arnoldi_step(ch_state_s* S, int j, cudaStream_t st) {
   CH_TRY(precond_apply(S->pc, reinterpret_cast<double*>(Vj), reinterpret_cast<double*>(Zj), st));
   CH_TRY(apply_A(s, reinterpret_cast<double*>(Zj), S->W, st));
   const double nv = j + 1, n32 = 32.0 * N;
-  {
-    ProfScope ps(st, K_ORTH0, 0, (nv + 1) * n32, 4.0 * nv * N);
-    k_orth<0><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
-  }
-  {
-    ProfScope ps(st, K_ORTH1, 0, (nv + 2) * n32, 8.0 * nv * N);
-    k_orth<1><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
-  }
-  {
-    ProfScope ps(st, K_ORTH2, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
-    k_orth<2><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+  if (s->p.gs_reorth) {  // selective reorthogonalisation: the second pass only where it is needed
+    {
+      ProfScope ps(st, K_ORTH0, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
+      k_orth<0><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd, 1);
+    }
+    {
+      ProfScope ps(st, K_ORTH2, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
+      k_orth<3><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+    }
+    // the second pass's launches (its bytes count as if every run took it)
+    {
+      ProfScope ps(st, K_ORTH_RE, 0, (nv + 1) * n32, 4.0 * nv * N);
+      k_orth<4><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+    }
+    {
+      ProfScope ps(st, K_ORTH_RE, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
+      k_orth<5><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+    }
+  } else {
+    {
+      ProfScope ps(st, K_ORTH0, 0, (nv + 1) * n32, 4.0 * nv * N);
+      k_orth<0><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+    }
+    {
+      ProfScope ps(st, K_ORTH1, 0, (nv + 2) * n32, 8.0 * nv * N);
+      k_orth<1><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+    }
+    {
+      ProfScope ps(st, K_ORTH2, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
+      k_orth<2><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+    }
   }
   {
     ProfScope ps(st, K_SCALE4, 0, 64.0 * N, 0.0);
@@ -1733,6 +1813,8 @@ static void fill_stats(const ch_state_s* S, int run, ch_step_stats* o) {
   o->ms = S->last_ms;
   o->warm[0] = rs.warm[0];
   o->warm[1] = rs.warm[1];
+  o->reorth[0] = rs.reorth[0];
+  o->reorth[1] = rs.reorth[1];
 }
 
 // The end of a step: the run statistics are in the host copy, the CUDA events recorded.

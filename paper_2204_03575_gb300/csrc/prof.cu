@@ -18,7 +18,8 @@ static const char* const kNames[K_COUNT] = {
     "cheb_first",   "cheb_step",     "vresidual",   "restrict",    "prolong",   "coarse_solve",
     "vload",        "vstore",        "spmv_M",      "state_io",    "cheb_first_coarse",
     "cheb_step_coarse", "vresidual_coarse", "restrict_coarse", "prolong_coarse", "ws_conv",
-    "ws_io",        "guess_select",  "elem_loads",   "minres_dot",   "minres_update", "cheb_semi", "ray_parity"};
+    "ws_io",        "guess_select",  "elem_loads",   "minres_dot",   "minres_update", "cheb_semi", "ray_parity",
+    "orth_reorth"};
 
 struct Acc {
   int64_t launches = 0;

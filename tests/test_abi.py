@@ -74,7 +74,7 @@ def test_defaults_are_the_papers(L):
     assert p.cheb_degree_M == 0 and p.pattern == 0
     assert p.precond_M == 0 and p.cheb_M_steps == 0
     assert (p.chi_pn, p.chi_ps, p.chi_ns, p.N_p, p.N_nfa, p.N_s) == (1.0, 0.3, 0.3, 20.0, 20.0, 1.0)
-    assert p.fh_delta == 1e-10 and p.pdl == 1
+    assert p.fh_delta == 1e-10 and p.pdl == 1 and p.gs_reorth == 0
 
 
 def test_status_strings(L):
@@ -90,7 +90,8 @@ def test_status_strings(L):
                                  dict(pattern=2), dict(pattern=-1), dict(potential=4),
                                  dict(precond_M=2), dict(cheb_M_steps=17), dict(cheb_M_steps=-1),
                                  dict(N_p=0.0), dict(N_s=-1.0), dict(fh_delta=0.0), dict(fh_delta=1.0),
-                                 dict(chi_pn=float("nan")), dict(pdl=2), dict(pdl=-1)])
+                                 dict(chi_pn=float("nan")), dict(pdl=2), dict(pdl=-1),
+                                 dict(gs_reorth=2), dict(gs_reorth=-1)])
 def test_invalid_params_rejected_on_host(L, bad):
     p = ch.Params(**bad)
     h = ctypes.c_void_p()

@@ -268,6 +268,35 @@ def test_step_parity_2d_config1(lib, precision):
         assert math.isclose(stats["mass"][1], o.mass(s.M, g["phi_nfa"]), rel_tol=1e-12)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("kw", [dict(nx=32, ny=32), dict(nx=48, ny=40, restart=5)])
+def test_selective_reorthogonalisation_step_parity(lib, precision, kw):
+    """gs_reorth = 1 (one Gram-Schmidt projection, the second only where the vector lost more than
+    half its squared norm): every step's fields still match the oracle's step at the FP64 parity
+    tolerance, with and without restarts; the second pass is taken on some Arnoldi steps, never
+    more than there are; gs_reorth = 0 takes it on every one."""
+    s, out = run_pair(lib, 6, rtol=1e-12, precision=precision, gs_reorth=1, **kw)
+    for k, (stats, g, _, nxt) in enumerate(out):
+        assert stats["status"] == 0
+        for gk, ok in FIELDS:
+            assert rel(g[gk], getattr(nxt, ok)) < 1e-10, (k, gk)
+        assert all(0 <= r <= i for r, i in zip(stats["reorth"], stats["iters"]))
+    assert sum(sum(st["reorth"]) for st, _, _, _ in out) < sum(sum(st["iters"]) for st, _, _, _ in out)
+    _, out0 = run_pair(lib, 2, rtol=1e-12, precision=precision, **kw)
+    assert all(st["reorth"] == st["iters"] for st, _, _, _ in out0)
+
+
+def test_selective_reorthogonalisation_host_loop_matches_graphs(lib):
+    """The device-side loop and the host-driven loop run the same selective passes: bitwise the same
+    steps."""
+    a = run_pair(lib, 2, nx=48, ny=40, gs_reorth=1, graphs=1)[1]
+    b = run_pair(lib, 2, nx=48, ny=40, gs_reorth=1, graphs=0)[1]
+    for (sa, ga, _, _), (sb, gb, _, _) in zip(a, b):
+        assert sa["iters"] == sb["iters"] and sa["reorth"] == sb["reorth"]
+        for k in ga:
+            np.testing.assert_array_equal(ga[k], gb[k])
+
+
 def test_trajectory_parity_2d_config1(lib):
     """The whole 10-step GPU trajectory against the oracle's own trajectory (errors compound
     through the explicit nonlinearity; 1e-9 relative)."""
