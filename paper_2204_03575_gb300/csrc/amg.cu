@@ -945,7 +945,8 @@ ch_status hierarchy_level_export(const Hierarchy* h, int l, int64_t* rows, int64
 // bound by the FP64 pipe and successor blocks that arrive early crowd the SMs unevenly.  Measured
 // on the 512 x 512 mesh, ms per time step: FP32 V-cycles 8.33 plain, 8.06 without the trigger,
 // 7.96 with it; FP64 V-cycles 16.90 plain, 16.78 without, 17.70 with it (16.75 when only grids of
-// at most 152 blocks trigger, 17.28 at most 608).
+// at most 152 blocks trigger, 17.28 at most 608; that small-grid rule took FP64 32 x 32 steps from
+// 2.26 to 2.21 ms but 128 x 128 steps from 2.95 to 3.03).
 template <typename T>
 __device__ __forceinline__ void pdl_trigger_t() {
   if (sizeof(T) == 4) pdl_trigger();
