@@ -480,7 +480,9 @@ def learned_section(torch, ch, nx, K, flush, ranks):
            "held_out_loss_per_epoch": info["held_out_loss_per_epoch"],
            "held_out_loss_quadratic": info["held_out_loss_quadratic"], "selected": info["selected"],
            "selection": "fewest FGMRES iterations per step on a validation run (seed 999, steps 4..43) among "
-                        "theta = 1 and the network after each epoch",
+                        "theta = 1, per-field constants (theta_phi, theta_mu) fitted on that run by a "
+                        "coordinate search, and the network (started from those constants) after each epoch",
+           "constant_theta": info["constant_theta"],
            "selection_iterations_quadratic_then_epochs": info["selection_scores_quadratic_then_epochs"],
            "loss_meaning": "mean ln(|r|^2 / |r_linear extrapolation|^2) of the step residual; the last 10% of "
                            "the pairs (2 of the 20 seeds) held out",

@@ -129,6 +129,45 @@ def validation_iterations(net, nx: int, ny: int, seed: int = 999, steps: int = 4
     return float(np.mean(its))
 
 
+def constant_theta(nparams: int, theta_phi: float, theta_mu: float):
+    """Parameters of a network whose theta is constant per field: zero weights, output bias
+    (theta_phi, theta_phi, theta_mu, theta_mu) for (phi_p, phi_nfa, mu_p, mu_nfa); with out_scale 1
+    its prediction is s + d + theta_c D_c."""
+    th = np.zeros(nparams, np.float32)
+    th[-8:-4] = [theta_phi, theta_phi, theta_mu, theta_mu]
+    return th
+
+
+def calibrate_theta(net, nx: int, ny: int, seed: int = 999, steps: int = 40, state=None, start=(1.0, 1.0),
+                    step: float = 0.1, lo: float = 0.0, hi: float = 1.5, max_moves: int = 20):
+    """Fit the two constants (theta_phi, theta_mu) of constant_theta by the FGMRES iterations of a
+    validation run (validation_iterations): coordinate search from `start` with steps of `step`,
+    then `step` / 2, moving to the best of the four neighbours while it lowers the count.  Leaves
+    the best constants in `net` and returns ((theta_phi, theta_mu), iterations, evaluations)."""
+    state = state or make_state(nx, ny)
+    seen = {}
+
+    def cost(t):
+        key = (round(t[0], 4), round(t[1], 4))
+        if key not in seen:
+            net.set_params(constant_theta(net.nparams, *key))
+            seen[key] = validation_iterations(net, nx, ny, seed, steps, state)
+        return seen[key]
+
+    best = (float(start[0]), float(start[1]))
+    f = cost(best)
+    for h in (step, step / 2):
+        for _ in range(max_moves):
+            cand = [(min(hi, max(lo, best[0] + dx)), min(hi, max(lo, best[1] + dy)))
+                    for dx, dy in ((h, 0), (-h, 0), (0, h), (0, -h))]
+            fc, tc = min((cost(t), t) for t in cand)
+            if fc >= f:
+                break
+            best, f = tc, fc
+    net.set_params(constant_theta(net.nparams, *best))
+    return best, f, len(seen)
+
+
 def train_residual(data, net, system, epochs: int = 8, batch: int = 8, lr: float = 2e-3, seed: int = 0,
                    use_fields: bool = True, precond=None, val_frac: float = 0.1, select: str = "iterations",
                    val_seed: int = 999, val_steps: int = 40):
@@ -139,11 +178,13 @@ def train_residual(data, net, system, epochs: int = 8, batch: int = 8, lr: float
 
     The last `val_frac` of the pairs (the last seeds' trajectories: generate_pairs orders them by
     seed) are held out; their loss (lr = 0: no update) is reported for exactly theta = 1 -- the
-    quadratic extrapolation, the network's starting point -- and after every epoch.  Model
-    selection among those candidates: select = "iterations" (default) keeps the one with the
-    fewest FGMRES iterations per step on a validation run (validation_iterations, seed val_seed,
-    the solver's own measure of a guess), select = "loss" the lowest held-out loss.  Either way
-    theta = 1 is a candidate, so training can only improve on it as the selection measures it."""
+    quadratic extrapolation -- and after every epoch.  With select = "iterations" (default) the
+    per-field constants (theta_phi, theta_mu) are first fitted by the FGMRES iterations of a
+    validation run (calibrate_theta, seed val_seed), the network starts from them (output bias),
+    and the kept parameters are those with the fewest validation iterations among theta = 1, the
+    fitted constants and the network after every epoch; select = "loss" keeps the lowest held-out
+    loss among theta = 1 and the epochs.  Either way theta = 1 is a candidate, so training can only
+    improve on it as the selection measures it."""
     Q2, Q, X, Y = data
     S, N = X.shape[0], X.shape[1]
     nval = int(round(S * val_frac)) if val_frac > 0 else 0
@@ -168,15 +209,21 @@ def train_residual(data, net, system, epochs: int = 8, batch: int = 8, lr: float
     def score(loss):
         return validation_iterations(net, nx, ny, val_seed, val_steps, vstate) if vstate else loss
 
-    quad = np.zeros(net.nparams, np.float32)
-    quad[-8:-4] = 1.0  # zero weights, output bias 1: theta = out_scale = 1
-    best, quad_loss, scores = None, None, []
+    quad = constant_theta(net.nparams, 1.0, 1.0)  # zero weights, output bias 1: theta = out_scale = 1
+    best, quad_loss, scores, const = None, None, [], None
     if nval:
         net.set_params(quad)
         quad_loss = held_out_loss()
         scores.append(score(quad_loss))
         best = (scores[-1], quad, "quadratic")
-    net.set_params(init_params(net.nparams, seed))
+    theta0 = init_params(net.nparams, seed)
+    if vstate is not None and nval:
+        (tp, tm), f, nev = calibrate_theta(net, nx, ny, val_seed, val_steps, vstate)
+        const = {"theta_phi": tp, "theta_mu": tm, "iterations": f, "evaluations": nev}
+        if f < best[0]:
+            best = (f, constant_theta(net.nparams, tp, tm), "constant theta")
+        theta0[-8:-4] = [tp, tp, tm, tm]  # the network starts from the fitted constants
+    net.set_params(theta0)
     g = torch.Generator(device="cpu").manual_seed(seed)
     losses, val = [], []
     for ep in range(epochs):
@@ -198,7 +245,8 @@ def train_residual(data, net, system, epochs: int = 8, batch: int = 8, lr: float
         net.set_params(best[1])
     return net, {"loss_per_epoch": losses, "held_out_loss_per_epoch": val,
                  "held_out_loss_quadratic": quad_loss, "selection": select,
-                 "selection_scores_quadratic_then_epochs": scores, "mean": mean.tolist(),
+                 "selection_scores_quadratic_then_epochs": scores, "constant_theta": const,
+                 "mean": mean.tolist(),
                  "inv_std": inv_std.tolist(), "out_scale": out_scale.tolist(), "pairs": S, "held_out_pairs": nval,
                  "nodes": N, "selected": best[2] if best else f"epoch {epochs}"}
 

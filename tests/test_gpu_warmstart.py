@@ -261,11 +261,14 @@ def test_learned_warm_start_saves_iterations(lib):
     print({"previous": its(plain), "linear": its(linear), "quadratic": its(quad), "learned": its(learned)})
     assert its(learned) < 0.97 * its(plain), (its(learned), its(plain))
     assert its(learned) < its(linear), (its(learned), its(linear))
-    # selection by the iterations of a validation run (seed 999): theta = 1 (quadratic extrapolation)
-    # is a candidate, so the kept network is no worse than it there, and on this run within 5 %
-    sc = info["selection_scores_quadratic_then_epochs"]
+    # selection by the iterations of a validation run (seed 999) among theta = 1 (quadratic
+    # extrapolation), per-field constants fitted on that run, and the epochs: the kept network is no
+    # worse than theta = 1 there, and on this run within 5 % of it
+    sc, const = info["selection_scores_quadratic_then_epochs"], info["constant_theta"]
     assert info["held_out_pairs"] > 0 and len(info["held_out_loss_per_epoch"]) == 8 and len(sc) == 9
-    assert info["selected"] == "quadratic" or min(sc[1:]) < sc[0]
+    sel = info["selected"]
+    kept = sc[0] if sel == "quadratic" else const["iterations"] if sel == "constant theta" else sc[int(sel.split()[1])]
+    assert kept == min([sc[0], const["iterations"]] + sc[1:])  # the kept candidate has the fewest
     assert its(learned) <= 1.05 * its(quad), (its(learned), its(quad))
     # the guess was taken, and every step still met the tolerance
     assert np.mean([sum(s["warm"]) for s in learned[3:]]) > 1.0
