@@ -350,6 +350,12 @@ void ch_ws_destroy(ch_ws_t* w);
  * training call or learned step that synchronises returns CH_ERR_INTERNAL.  CH_ERR_ARG for an
  * engine other than 0 or 1. */
 ch_status ch_ws_set_engine(ch_ws_t* w, int32_t engine);
+/* Test of the failure path of the tcgen05 convolutions (host setting): with on = 1 their blocks
+ * issue and commit no MMA, so each block's bounded wait on its mbarrier runs out (after a short
+ * limit), the block records the timeout, frees its tensor memory and writes nothing; the next
+ * training call or learned step that synchronises returns CH_ERR_INTERNAL and clears the record.
+ * The device context stays usable: with on = 0 the network computes as before. */
+ch_status ch_ws_inject_mma_timeout(ch_ws_t* w, int32_t on);
 ch_status ch_ws_set_params(ch_ws_t* w, const float* params, void* stream);     /* host; resets Adam */
 /* host outputs, either may be NULL; grads are those of the last ch_ws_train_step */
 ch_status ch_ws_get_params(const ch_ws_t* w, float* params, float* grads, void* stream);

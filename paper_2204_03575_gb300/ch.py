@@ -136,6 +136,7 @@ _SIGNATURES = {
     "ch_ws_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_VP)]),
     "ch_ws_destroy": (None, [_VP]),
     "ch_ws_set_engine": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "ch_ws_inject_mma_timeout": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "ch_ws_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), _VP]),
     "ch_ws_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _VP]),
     "ch_ws_set_norm": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), _VP]),
@@ -498,6 +499,11 @@ class WarmStartNet:
     def set_engine(self, engine: int):
         """ch_ws_set_engine: 0 mma.sync, 1 tcgen05 convolutions."""
         _check(lib().ch_ws_set_engine(self._h, engine), "ch_ws_set_engine")
+
+    def inject_mma_timeout(self, on: bool):
+        """ch_ws_inject_mma_timeout: the tcgen05 convolutions withhold their MMAs (a test of the
+        bounded wait's failure path)."""
+        _check(lib().ch_ws_inject_mma_timeout(self._h, 1 if on else 0), "ch_ws_inject_mma_timeout")
 
     def set_params(self, params, stream=None):
         import numpy as np

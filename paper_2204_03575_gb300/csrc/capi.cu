@@ -506,6 +506,12 @@ ch_status ch_ws_create(int32_t H, int32_t W, int32_t max_batch, ch_ws_t** out) {
 
 void ch_ws_destroy(ch_ws_t* w) { ch::ws_destroy(w); }
 
+ch_status ch_ws_inject_mma_timeout(ch_ws_t* w, int32_t on) {
+  CH_ARG(w != nullptr, "NULL argument");
+  CH_ARG(on == 0 || on == 1, "on must be 0 or 1");
+  return ch::ws_withhold_mma(w, on);
+}
+
 ch_status ch_ws_set_engine(ch_ws_t* w, int32_t engine) {
   CH_ARG(w != nullptr, "NULL argument");
   CH_ARG(engine == 0 || engine == 1, "engine must be 0 (mma.sync) or 1 (tcgen05)");

@@ -319,6 +319,7 @@ ch_status ws_create(int H, int W, int Bmax, ch_ws_s** out);
 // convolution engine: 0 mma.sync, 1 tcgen05; ws_check reports a timed-out tcgen05 block (call
 // after synchronising with the network's work)
 ch_status ws_set_engine(ch_ws_s* w, int engine);
+ch_status ws_withhold_mma(ch_ws_s* w, int on);
 ch_status ws_check(const ch_ws_s* w);
 void ws_destroy(ch_ws_s* w);
 ch_status ws_set_params(ch_ws_s* w, const float* host, cudaStream_t st);

@@ -223,7 +223,8 @@ __global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict
 // K = 16) and commits them to an mbarrier (phase = tile parity), and each warp reads its 32
 // accumulator lanes back with tcgen05.ld for a vectorised epilogue.  A wait that runs out records
 // the failure in *err, waits once more (bounded) for the MMAs, and ends the block's tiles; the
-// block always frees its tensor memory.
+// block always frees its tensor memory.  With `withhold` (a host-set test of that path) no MMA is
+// issued or committed, so the wait (then of wait_limit = 256 polls) runs out in every block.
 constexpr int TC_M = 128;
 constexpr int TC_WAIT = 1 << 20;
 constexpr int TC_ROWS = TC_M + 2;             // pixel rows of a band: the segment and one each side
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(TC_M) k_conv3x3_tc(const __nv_bfloat16* __rest
                                                      const float* __restrict__ bias, int H, int W, int nseg,
                                                      int seg, int B, __nv_bfloat16* __restrict__ Yb,
                                                      float* __restrict__ Yf, const __nv_bfloat16* __restrict__ mask,
-                                                     int* __restrict__ err) {
+                                                     int* __restrict__ err, int wait_limit, int withhold) {
   constexpr int N = COUT < 16 ? 16 : COUT;
   constexpr int CG = CIN / 8, K = 9 * CIN, KB = K / 8, NB = N / 8;
   constexpr uint32_t TMEM_COLS = 32;  // a power of two >= 32 holding the N FP32 columns
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(TC_M) k_conv3x3_tc(const __nv_bfloat16* __rest
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (tid == 0) {
+    if (tid == 0 && !withhold) {  // withhold: a test of the timeout path (nothing arrives)
 #pragma unroll 1
       for (int tap = 0; tap < 9; ++tap) {
         const int band = tap / 3, dx = tap % 3;  // input row r + band - 1, column offset dx - 1
@@ -314,10 +315,10 @@ __global__ void __launch_bounds__(TC_M) k_conv3x3_tc(const __nv_bfloat16* __rest
                        smem_u32(bar))
                    : "memory");
     }
-    const bool ok = mbar_wait(smem_u32(bar), it & 1, TC_WAIT);
+    const bool ok = mbar_wait(smem_u32(bar), it & 1, wait_limit);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicExch(err, 1);
-      mbar_wait(smem_u32(bar), it & 1, TC_WAIT);  // the MMAs may still be running: a last bound
+      mbar_wait(smem_u32(bar), it & 1, wait_limit);  // the MMAs may still be running: a last bound
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -698,6 +699,7 @@ struct ch_ws_s {
   double* rms_part = nullptr;  // Bmax x WS_RMS_BLOCKS x 8: first-pass partials of the RMS scales
   bool fresh = false;  // bf16 copies up to date
   int engine = 1;      // convolutions: 0 mma.sync (warp-level), 1 tcgen05 (tensor memory)
+  int withhold = 0;    // test of the timeout path: tcgen05 blocks issue no MMA, so their wait runs out
   int* err_host = nullptr;  // pinned, device-mapped: set by a tcgen05 block whose MMA wait ran out
   int* err_dev = nullptr;
   ch::Alloc mem;
@@ -768,7 +770,8 @@ static void ws_conv(ch_ws_s* w, const __nv_bfloat16* X, const __nv_bfloat16* Wt,
     const TcTiles tt = tc_tiles(w->W);
     const int ntiles = B * w->H * tt.nseg;
     k_conv3x3_tc<CIN, COUT, MODE><<<std::min(ntiles, 4 * 152), TC_M, tc_smem_bytes<CIN, COUT>(), st>>>(
-        X, Bc, bias, w->H, w->W, tt.nseg, tt.seg, B, Yb, Yf, mask, w->err_dev);
+        X, Bc, bias, w->H, w->W, tt.nseg, tt.seg, B, Yb, Yf, mask, w->err_dev, w->withhold ? 256 : TC_WAIT,
+        w->withhold);
   } else {
     k_conv3x3<CIN, COUT, MODE><<<dim3(blocks_for(w->P, 128), B), 256, 0, st>>>(X, Wt, bias, w->H, w->W, Yb, Yf,
                                                                                  mask);
@@ -779,9 +782,15 @@ static void ws_conv(ch_ws_s* w, const __nv_bfloat16* X, const __nv_bfloat16* Wt,
 // synchronised with the work that could set it).
 ch_status ws_check(const ch_ws_s* w) {
   if (w->err_host && *reinterpret_cast<volatile int*>(w->err_host)) {
+    *reinterpret_cast<volatile int*>(w->err_host) = 0;  // reported once; later calls start clean
     set_error("warm start: a tcgen05 convolution block timed out waiting for its MMAs");
     return CH_ERR_INTERNAL;
   }
+  return CH_OK;
+}
+
+ch_status ws_withhold_mma(ch_ws_s* w, int on) {
+  w->withhold = on;
   return CH_OK;
 }
 

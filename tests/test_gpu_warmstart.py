@@ -364,3 +364,24 @@ def test_engines_agree_and_bad_engine_is_refused(lib):
     with pytest.raises(lib.ChError) as e:
         net.set_engine(2)
     assert e.value.status == lib.ERR_ARG
+
+
+def test_tcgen05_wait_timeout_is_reported_and_the_context_stays_usable(lib):
+    """The tcgen05 convolutions' only wait (on the mbarrier their MMAs commit to) is bounded: with
+    the MMAs withheld (ch_ws_inject_mma_timeout) every block's wait runs out, the blocks free their
+    tensor memory and return, and the synchronising training call reports CH_ERR_INTERNAL once; the
+    device context stays usable and the same step then reproduces its loss bitwise."""
+    H, W, B = 33, 41, 2
+    rng = np.random.default_rng(11)
+    net = lib.WarmStartNet(H, W, max_batch=B)
+    net.set_engine(1)
+    net.set_params(small_theta(rng))
+    net.set_norm(np.zeros(8), np.ones(8), np.ones(4))
+    q2, q, x, n = (torch.from_numpy(a).cuda() for a in _history(rng, H * W, B, np.float32))
+    ref = net.train_step(x, q, q2, n, 0.0)
+    net.inject_mma_timeout(True)
+    with pytest.raises(lib.ChError) as e:
+        net.train_step(x, q, q2, n, 0.0)
+    assert e.value.status == lib.ERR_INTERNAL
+    net.inject_mma_timeout(False)
+    assert net.train_step(x, q, q2, n, 0.0) == ref
