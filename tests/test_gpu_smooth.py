@@ -89,3 +89,28 @@ def test_smooth_rejects_bad_arguments(lib):
     with pytest.raises(lib.ChError) as e:
         pc.smooth(1, b, x, 3, 1)
     assert e.value.status == lib.ERR_ARG
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_smooth_on_a_batch_equals_the_oracle_smoother(lib, precision):
+    """A batch of runs of different sizes: the finest level is the per-run lattice form (each row
+    looks up its run's strides); the smoother of the disjoint union against the oracle's."""
+    p = lib.Params(precision=precision, coarse_max=256)
+    mesh = lib.Mesh(p, runs=[lib.Params(nx=40, ny=24), lib.Params(nx=17, ny=33), lib.Params(nx=64, ny=48)])
+    system = lib.System(mesh, p)
+    pc = lib.Precond(system)
+    e = pc.level(1, 0)
+    rowptr, col, val = [t.cpu().numpy() for t in e["A"]]
+    A = sp.csr_matrix((val, col, rowptr), shape=(system.n, system.n))
+    rng = np.random.default_rng(8)
+    b = rng.standard_normal((system.n, 2))
+    x0 = rng.standard_normal((system.n, 2))
+    x = torch.from_numpy(x0.copy()).cuda()
+    pc.smooth(1, torch.from_numpy(b).cuda(), x, 4, 2)
+    got = x.cpu().numpy()
+    for k in range(2):
+        want = x0[:, k].copy()
+        for _ in range(2):
+            want = o.chebyshev_smooth(A, b[:, k], want, 4, e["bounds"])
+        err = np.abs(got[:, k] - want).max() / np.abs(want).max()
+        assert err <= TOL[precision], (k, err)
