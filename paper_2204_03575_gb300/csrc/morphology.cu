@@ -60,7 +60,9 @@ __global__ void __launch_bounds__(MP_TX) k_classify(const double* __restrict__ p
                                                     int gx, int gy, int exact, uint8_t* __restrict__ polymer,
                                                     double* __restrict__ mu_e, double* __restrict__ mu_h) {
   __shared__ long long rowbase[MP_TY];  // first pixel of each grid row's pixel row
-  const int k = blockIdx.x * MP_TX + threadIdx.x, l0 = blockIdx.y * MP_TY;
+  const int nbx = (gx + MP_TX - 1) / MP_TX;  // blocks along a grid row (one grid dimension: any gy)
+  const int bx = (int)(blockIdx.x % (unsigned)nbx), by = (int)(blockIdx.x / (unsigned)nbx);
+  const int k = bx * MP_TX + threadIdx.x, l0 = by * MP_TY;
   if (threadIdx.x < MP_TY && l0 + (int)threadIdx.x < gy)
     rowbase[threadIdx.x] = (long long)pixel_index(l0 + threadIdx.x, gy, Ly, ny, exact) * (nx + 1);
   const int i = k < gx ? pixel_index(k, gx, Lx, nx, exact) : 0;
@@ -88,8 +90,9 @@ ch_status morphology_project(const double* pp, const double* pn, int nx, int ny,
   ProfScope ps(st, K_MORPH, 0, (double)G * (1.0 + 16.0) + (use_thr ? 8.0 : 16.0) * (double)(nx + 1) * (ny + 1),
                0.0);
   const int exact = (double)nx * gx <= 1e12 && (double)ny * gy <= 1e12;
-  const dim3 grid((gx + MP_TX - 1) / MP_TX, (gy + MP_TY - 1) / MP_TY);
-  k_classify<<<grid, MP_TX, 0, st>>>(pp, pn, nx, ny, Lx, Ly, use_thr, thr, gx, gy, exact, polymer, mu_e, mu_h);
+  const int64_t nblocks = (int64_t)((gx + MP_TX - 1) / MP_TX) * ((gy + MP_TY - 1) / MP_TY);  // < 2^31: G < 2e9
+  k_classify<<<(unsigned)nblocks, MP_TX, 0, st>>>(pp, pn, nx, ny, Lx, Ly, use_thr, thr, gx, gy, exact, polymer,
+                                                  mu_e, mu_h);
   CH_LAUNCHED();
   return CH_OK;
 }

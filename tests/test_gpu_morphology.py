@@ -63,11 +63,14 @@ def test_smallest_sizes_and_uniform_images(lib):
 
 
 def test_tall_image_agrees(lib):
-    """A tall, narrow image (24001 pixel rows) on a coarse grid."""
+    """A tall, narrow image (24001 pixel rows) on a coarse grid, and a grid of one column and
+    600,000 rows (more row blocks than a grid's second dimension could hold)."""
     nx, ny = 2, 24000
     rng = np.random.default_rng(9)
     N = (nx + 1) * (ny + 1)
-    _run(lib, rng.random(N), rng.random(N), nx, ny, 1.0, 100.0, 5, 301)
+    pp, pn = rng.random(N), rng.random(N)
+    _run(lib, pp, pn, nx, ny, 1.0, 100.0, 5, 301)
+    _run(lib, pp, pn, nx, ny, 1.0, 100.0, 1, 600000)
 
 
 def test_projection_of_a_solver_morphology(lib):
