@@ -217,6 +217,10 @@ __global__ void k_scale4(Seg sg, const double4_32a* src, double4_32a* dst, const
 // <a, b>_s sums components (x, z) for species 0 and (y, w) for species 1 over the run's nodes.
 constexpr int KC = 16;                // basis vectors per chunk: 2 KC = 32 values, one per lane
 constexpr int ORTH_BLOCKS = 152 * 2;  // target grid of the segmented kernels (2 blocks per SM)
+// threads per block of the Gram-Schmidt passes; measured (ms per step, 512 x 512 FP64 / mixed /
+// 64-run batch): 256 threads 14.1 / 6.75 / 37.3, 128 threads 14.1 / 6.71 / 38.5, 64 threads
+// 14.5 / 7.07 / 44.4 -- more nodes per thread halve the reduction's share but expose more latency
+constexpr int ORTH_TPB = 256;
 
 // Sum 32 per-lane values over the warp by recursive halving: at each step a lane keeps half of
 // its values and adds the partner's copy of that half.  On return lane l holds the warp sum of
@@ -237,15 +241,17 @@ __device__ __forceinline__ double warp_transpose_sum32(double (&a)[32]) {
   return a[0];
 }
 
-// Block sum of the 32 per-thread values: returns, in threads 0..31, the block total of value t.
-__device__ __forceinline__ double block_sum32(double (&a)[32], double* sm /* [TPB/32][32] */) {
+// Block sum of the 32 per-thread values over NT threads: returns, in threads 0..31, the block total
+// of value t.
+template <int NT>
+__device__ __forceinline__ double block_sum32(double (&a)[32], double* sm /* [NT/32][32] */) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const double r = warp_transpose_sum32(a);
   sm[w * 32 + lane] = r;
   __syncthreads();
   double t = 0.0;
   if (threadIdx.x < 32)
-    for (int q = 0; q < TPB / 32; ++q) t += sm[q * 32 + threadIdx.x];
+    for (int q = 0; q < NT / 32; ++q) t += sm[q * 32 + threadIdx.x];
   __syncthreads();
   return t;
 }
@@ -345,11 +351,11 @@ __device__ __forceinline__ void arnoldi_column(KrylovDev* kd, int sp, int j, dou
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(TPB, 2) k_orth(Seg sg, int N, int nv, const double4_32a* __restrict__ V,
+__global__ void __launch_bounds__(ORTH_TPB, 2) k_orth(Seg sg, int N, int nv, const double4_32a* __restrict__ V,
                                                double4_32a* __restrict__ W, double* partials,
                                                KrylovDev* kds, int with_norm = 0) {
   constexpr bool DOTS = MODE == 0 || MODE == 1 || MODE == 4;
-  __shared__ double sm[(TPB / 32) * 32];
+  __shared__ double sm[(ORTH_TPB / 32) * 32];
   __shared__ double coef[2][MAXM + 1];
   const int run = sg.run[blockIdx.x];
   KrylovDev* kd = kds + run;
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(TPB, 2) k_orth(Seg sg, int N, int nv, const do
         orth_dots_dispatch<true>(kw, V, W, (size_t)N, k0, nv, coef, v0, v1, acc);
       else
         orth_dots_dispatch<false>(kw, V, W, (size_t)N, k0, nv, coef, v0, v1, acc);
-      const double tot = block_sum32(acc, sm);
+      const double tot = block_sum32<ORTH_TPB>(acc, sm);
       if (threadIdx.x < 2 * kw) partials[(size_t)blockIdx.x * MAXV + 2 * k0 + threadIdx.x] = tot;
     }
     const bool norm = MODE == 0 && with_norm;
@@ -391,7 +397,7 @@ __global__ void __launch_bounds__(TPB, 2) k_orth(Seg sg, int N, int nv, const do
         acc[0] = fma(w.x, w.x, fma(w.z, w.z, acc[0]));
         acc[1] = fma(w.y, w.y, fma(w.w, w.w, acc[1]));
       }
-      const double bt = block_sum32(acc, sm);
+      const double bt = block_sum32<ORTH_TPB>(acc, sm);
       if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + 2 * nv + threadIdx.x] = bt;
     }
     if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
@@ -414,7 +420,7 @@ __global__ void __launch_bounds__(TPB, 2) k_orth(Seg sg, int N, int nv, const do
       acc[0] = fma(w.x, w.x, fma(w.z, w.z, acc[0]));
       acc[1] = fma(w.y, w.y, fma(w.w, w.w, acc[1]));
     }
-    const double bt = block_sum32(acc, sm);
+    const double bt = block_sum32<ORTH_TPB>(acc, sm);
     if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = bt;
     if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
     __shared__ double tot[2];
@@ -1010,33 +1016,33 @@ static ch_status arnoldi_step(ch_state_s* S, int j, cudaStream_t st) {
   if (s->p.gs_reorth) {  // selective reorthogonalisation: the second pass only where it is needed
     {
       ProfScope ps(st, K_ORTH0, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
-      k_orth<0><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd, 1);
+      k_orth<0><<<nb, ORTH_TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd, 1);
     }
     {
       ProfScope ps(st, K_ORTH2, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
-      k_orth<3><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+      k_orth<3><<<nb, ORTH_TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
     }
     // the second pass's launches (its bytes count as if every run took it)
     {
       ProfScope ps(st, K_ORTH_RE, 0, (nv + 1) * n32, 4.0 * nv * N);
-      k_orth<4><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+      k_orth<4><<<nb, ORTH_TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
     }
     {
       ProfScope ps(st, K_ORTH_RE, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
-      k_orth<5><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+      k_orth<5><<<nb, ORTH_TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
     }
   } else {
     {
       ProfScope ps(st, K_ORTH0, 0, (nv + 1) * n32, 4.0 * nv * N);
-      k_orth<0><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+      k_orth<0><<<nb, ORTH_TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
     }
     {
       ProfScope ps(st, K_ORTH1, 0, (nv + 2) * n32, 8.0 * nv * N);
-      k_orth<1><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+      k_orth<1><<<nb, ORTH_TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
     }
     {
       ProfScope ps(st, K_ORTH2, 0, (nv + 2) * n32, 4.0 * nv * N + 4.0 * N);
-      k_orth<2><<<nb, TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
+      k_orth<2><<<nb, ORTH_TPB, 0, st>>>(S->seg, N, j + 1, V4, W4, S->partials, S->kd);
     }
   }
   {
