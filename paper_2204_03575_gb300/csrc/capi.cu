@@ -28,7 +28,7 @@ ch_status check_params(const ch_params* p) {
   CH_ARG(p->rtol > 0 && p->rtol < 1, "rtol must be in (0, 1)");
   CH_ARG(p->restart >= 1 && p->restart <= 64, "restart must be in [1, 64]");
   CH_ARG(p->max_iter >= 1, "max_iter must be >= 1");
-  CH_ARG(p->cheb_degree >= 1 && p->cheb_degree <= 16, "cheb_degree must be in [1, 16]");
+  CH_ARG(p->cheb_degree >= 0 && p->cheb_degree <= 16, "cheb_degree must be in [0, 16]");
   CH_ARG(p->coarse_max >= 0 && p->coarse_max <= 4096, "coarse_max must be in [0, 4096]");
   CH_ARG(p->amg_theta >= 0 && p->amg_theta < 1, "amg_theta must be in [0, 1)");
   CH_ARG(p->vcycles_M >= 1 && p->vcycles_H >= 1, "vcycles must be >= 1");
@@ -97,7 +97,7 @@ void ch_params_default(ch_params* p) {
   d.rtol = 1e-8;
   d.restart = 30;
   d.max_iter = 300;
-  d.cheb_degree = 5;
+  d.cheb_degree = 0;
   d.coarse_max = 0;
   d.amg_theta = 0.08;
   d.vcycles_M = 1;
@@ -291,12 +291,17 @@ ch_status ch_precond_setup(const ch_system_t* s, void* stream, ch_precond_t** ou
     lat.WH.push_back((rp.nx + 1) * (rp.ny + 1));
   }
   lat.node_run = s->mesh->node_run;
-  // M's hierarchy smooths with its own finest degree (0: min(3, cheb_degree)); measured on
-  // 512 x 512 with cheb_degree 5: M degree 5 / 3 / 2 gave 79.8 / 81.7 / 76.0 FP64 steps/s
-  ch_params pm = s->p;
-  pm.cheb_degree = s->p.cheb_degree_M > 0 ? s->p.cheb_degree_M : std::min(3, s->p.cheb_degree);
+  // The finest level's Chebyshev degree, cheb_degree 0: 5 for FP64 V-cycles, 6 for FP32 (512 x 512:
+  // FP64 79.8 / 76.0 steps/s at degree 5 / 6; FP32 6.08 / 5.91 / 5.93 / 5.97 ms per step at degree
+  // 5 / 6 / 7 / 8 -- an FP32 step costs 2.4 us in sequence, an FP64 one 11.6 us of FP64 work).
+  // M's hierarchy smooths with its own finest degree (0: min(3, that degree)); measured on
+  // 512 x 512 with degree 5: M degree 5 / 3 / 2 gave 79.8 / 81.7 / 76.0 FP64 steps/s
+  ch_params ph = s->p;
+  if (ph.cheb_degree == 0) ph.cheb_degree = pc->precision == 0 ? 5 : 6;
+  ch_params pm = ph;
+  pm.cheb_degree = ph.cheb_degree_M > 0 ? ph.cheb_degree_M : std::min(3, ph.cheb_degree);
   ch_status r = ch::hierarchy_build(M, &lat, pm, pc->precision, S(stream), &pc->hM);
-  if (r == CH_OK) r = ch::hierarchy_build(H, &lat, s->p, pc->precision, S(stream), &pc->hH);
+  if (r == CH_OK) r = ch::hierarchy_build(H, &lat, ph, pc->precision, S(stream), &pc->hH);
   if (r == CH_OK && (cudaStreamCreateWithFlags(&pc->side, cudaStreamNonBlocking) != cudaSuccess ||
                      cudaEventCreateWithFlags(&pc->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                      cudaEventCreateWithFlags(&pc->ev_join, cudaEventDisableTiming) != cudaSuccess)) {

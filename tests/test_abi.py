@@ -69,7 +69,7 @@ def test_defaults_are_the_papers(L):
     p = ch.Params()
     assert (p.tau, p.eps, p.k_evap, p.g_p, p.g_nfa, p.h_p) == (1e-4, 1e-3, 5e-3, 0.01, 0.01, 0.0)
     assert p.rtol == 1e-8 and p.bc_mode == 1 and p.evap_sign == 1 and p.precision == 0
-    assert p.cheb_degree == 5 and p.vcycles_H == 2 and p.vcycles_M == 1 and p.autotune == 1
+    assert p.cheb_degree == 0 and p.vcycles_H == 2 and p.vcycles_M == 1 and p.autotune == 1
     assert p.coarse_max == 0 and p.cheb_degree_coarse == 0 and p.krylov == 0
     assert p.cheb_degree_M == 0 and p.pattern == 0
     assert p.precond_M == 0 and p.cheb_M_steps == 0
@@ -86,6 +86,7 @@ def test_status_strings(L):
                                  dict(restart=65), dict(rtol=2.0), dict(precision=3), dict(bc_mode=2),
                                  dict(evap_sign=0), dict(coarse_max=-1), dict(coarse_max=4097),
                                  dict(cheb_degree_coarse=-1), dict(cheb_degree_coarse=17),
+                                 dict(cheb_degree=-1), dict(cheb_degree=17),
                                  dict(krylov=2), dict(cheb_degree_M=-1), dict(cheb_degree_M=17),
                                  dict(pattern=2), dict(pattern=-1), dict(potential=4),
                                  dict(precond_M=2), dict(cheb_M_steps=17), dict(cheb_M_steps=-1),
