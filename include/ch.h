@@ -77,7 +77,7 @@ typedef struct ch_params {
   int32_t restart;           /* FGMRES restart length m (1..64), default 30 */
   int32_t max_iter;          /* total FGMRES iterations per step, default 300 */
   int32_t cheb_degree;       /* Chebyshev smoothing steps before and after coarse correction on the
-                                finest level; 0 (default): 5 in FP64 V-cycles, 6 in FP32 */
+                                finest level; 0 (default): 5 */
   int32_t coarse_max;        /* AMG: coarsest level is solved densely at or below this size (<= 4096);
                                 0 (default): 512 rows for FP64 V-cycles, 4096 for FP32 */
   double amg_theta;          /* AMG strength threshold, default 0.08 */

@@ -291,13 +291,13 @@ ch_status ch_precond_setup(const ch_system_t* s, void* stream, ch_precond_t** ou
     lat.WH.push_back((rp.nx + 1) * (rp.ny + 1));
   }
   lat.node_run = s->mesh->node_run;
-  // The finest level's Chebyshev degree, cheb_degree 0: 5 for FP64 V-cycles, 6 for FP32 (512 x 512:
-  // FP64 79.8 / 76.0 steps/s at degree 5 / 6; FP32 6.08 / 5.91 / 5.93 / 5.97 ms per step at degree
-  // 5 / 6 / 7 / 8 -- an FP32 step costs 2.4 us in sequence, an FP64 one 11.6 us of FP64 work).
+  // The finest level's Chebyshev degree, cheb_degree 0: 5 in both precisions.  (FP64 512 x 512:
+  // 79.8 / 76.0 steps/s at degree 5 / 6.  FP32 V-cycles: degree 6 gained 3 % on 512 x 512 steps
+  // 4..63 but lost 3.6 % on the 3D box and 2-5 % on the 256 x 256 warm-start runs.)
   // M's hierarchy smooths with its own finest degree (0: min(3, that degree)); measured on
   // 512 x 512 with degree 5: M degree 5 / 3 / 2 gave 79.8 / 81.7 / 76.0 FP64 steps/s
   ch_params ph = s->p;
-  if (ph.cheb_degree == 0) ph.cheb_degree = pc->precision == 0 ? 5 : 6;
+  if (ph.cheb_degree == 0) ph.cheb_degree = 5;
   ch_params pm = ph;
   pm.cheb_degree = ph.cheb_degree_M > 0 ? ph.cheb_degree_M : std::min(3, ph.cheb_degree);
   ch_status r = ch::hierarchy_build(M, &lat, pm, pc->precision, S(stream), &pc->hM);
