@@ -12,7 +12,7 @@
 // the Krylov scalars -- Hessenberg matrix, Givens rotations, convergence flags -- are kept per
 // (run, species).  Inner products and norms are segmented: the grid is split so that each
 // thread block owns a contiguous node range of exactly one run, and the last block of a run to
-// finish (a per-run ticket) sums that run's block partials in block order.  There are no
+// finish (a per-run ticket) sums that run's block partials in a fixed order.  There are no
 // floating-point atomics, so runs are bitwise reproducible.  Orthogonalisation is classical
 // Gram-Schmidt with one re-orthogonalisation (CGS2).  With CUDA graphs on, the convergence loop
 // itself runs on the device (conditional graph nodes, see Ctl): a step is one graph launch.
@@ -99,7 +99,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* [TPB/32
 }
 
 // After a block has written its partials, returns true in the last block of its run to finish,
-// which then reads the run's block partials in block order.
+// which then reads the run's block partials (reduce_partials, a fixed order).
 __device__ __forceinline__ bool last_block_of_run(unsigned int* ticket, int nblocks) {
   __shared__ bool am_last;
   __threadfence();
@@ -113,11 +113,19 @@ __device__ __forceinline__ bool last_block_of_run(unsigned int* ticket, int nblo
   return am_last;
 }
 
+// out[v] = sum over the run's blocks b0..b1-1 of partials[b][v], in the last block of the run.  One
+// warp per value: lane l sums blocks b0 + l, b0 + l + 32, ... (independent loads, a few L2 round
+// trips) and the warp adds the 32 lane sums by a fixed xor tree -- a thread walking all blocks in
+// turn would wait for one L2 load per block (304 for a single run).  blockDim.x is a multiple of 32.
 __device__ void reduce_partials(const double* partials, int b0, int b1, int nv, double* out) {
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int v = threadIdx.x >> 5; v < nv; v += nw) {
     double s = 0.0;
-    for (int b = b0; b < b1; ++b) s += partials[(size_t)b * MAXV + v];
-    out[v] = s;
+#pragma unroll 4
+    for (int b = b0 + lane; b < b1; b += 32) s += partials[(size_t)b * MAXV + v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[v] = s;
   }
   __syncthreads();
 }
@@ -1139,7 +1147,7 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
 // gamma_j off it) is reduced by Givens rotations, and x is updated by the direction w_{j+1}.
 // MODE 0: gamma_1 from (v_1, z_1) and the start of the recurrence; 1: delta_j = (A z_j) . z_j;
 // 2: gamma_{j+1} from (v_{j+1}, z_{j+1}) and the Givens step.  Dots per species: components
-// (x, z) for species 0 and (y, w) for species 1, over the run's nodes, reduced in block order.
+// (x, z) for species 0 and (y, w) for species 1, over the run's nodes, reduced in a fixed order.
 template <int MODE>
 __global__ void __launch_bounds__(TPB) k_mr_dot(Seg sg, const double4_32a* __restrict__ A_,
                                                 const double4_32a* __restrict__ B_, double* partials,
