@@ -978,33 +978,70 @@ __global__ void k_cheb_first(int n, const T* dinv, const V2* b, T invtheta, V2* 
 // Row sums of A x for both right-hand sides with TPR lanes per row: lane `sub` takes entries
 // sub, sub+TPR, ... of the row and a butterfly of shuffles adds the lanes' partial sums, so the
 // summation order is fixed for a given TPR.  Threads past the last row contribute zeros (no
-// early return before the shuffles).  row_acc adds onto the caller's (s0, s1), which lane 0 of a
+// early return before the shuffles).  The sum adds onto the caller's (s0, s1), which lane 0 of a
 // row may seed (with -b: the sum is then A x - b at no extra FP64 instruction).
-template <typename T, typename V2, int TPR>
-__device__ __forceinline__ void row_acc(const Csr<T>& A, int row, int sub, const V2* __restrict__ x,
-                                        T& s0, T& s1) {
+//
+// The row's structure and values are set-up data, so a kernel reads them before its programmatic
+// dependency wait (row_prefetch: the lane's first CsrRow::PF entries, i.e. rowptr, then val and col)
+// and only gathers x after it (row_acc): one dependent L2 round trip behind the wait instead of
+// three (rowptr, col, x).  Entries past the prefetched ones are read after the wait, in the same
+// order.
+template <typename T, int TPR>
+struct CsrRow {
+  static constexpr int PF = TPR == 1 ? 8 : (TPR <= 4 ? 4 : 2);  // entries per lane read early
+  int q = 0, e = 0;  // the lane's next entry after the prefetched ones; the row's end
+  T a[PF];
+  int c[PF];
+};
+
+template <typename T, int TPR>
+__device__ __forceinline__ void row_prefetch(const Csr<T>& A, int row, int sub, CsrRow<T, TPR>& r) {
+  constexpr int PF = CsrRow<T, TPR>::PF;
+#pragma unroll
+  for (int k = 0; k < PF; ++k) {
+    r.a[k] = T(0);
+    r.c[k] = -1;
+  }
   if (row < A.nrows) {
-    const int e = A.rowptr[row + 1];
-    for (int q = A.rowptr[row] + sub; q < e; q += TPR) {
-      const T a = A.val[q];
-      const V2 xj = x[A.col[q]];
-      s0 = fma(a, xj.x, s0);
-      s1 = fma(a, xj.y, s1);
+    const int b = A.rowptr[row] + sub;
+    r.e = A.rowptr[row + 1];
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+      const int q = b + k * TPR;
+      if (q < r.e) {
+        r.a[k] = A.val[q];
+        r.c[k] = A.col[q];
+      }
     }
+    r.q = b + PF * TPR;
+  }
+}
+
+template <typename T, typename V2, int TPR>
+__device__ __forceinline__ void row_acc(const Csr<T>& A, const CsrRow<T, TPR>& r, const V2* __restrict__ x,
+                                        T& s0, T& s1) {
+  constexpr int PF = CsrRow<T, TPR>::PF;
+  V2 xj[PF];
+#pragma unroll
+  for (int k = 0; k < PF; ++k)
+    if (r.c[k] >= 0) xj[k] = x[r.c[k]];
+#pragma unroll
+  for (int k = 0; k < PF; ++k)
+    if (r.c[k] >= 0) {
+      s0 = fma(r.a[k], xj[k].x, s0);
+      s1 = fma(r.a[k], xj[k].y, s1);
+    }
+  for (int q = r.q; q < r.e; q += TPR) {
+    const T a = A.val[q];
+    const V2 v = x[A.col[q]];
+    s0 = fma(a, v.x, s0);
+    s1 = fma(a, v.y, s1);
   }
 #pragma unroll
   for (int o = TPR / 2; o > 0; o >>= 1) {
     s0 += __shfl_xor_sync(0xffffffffu, s0, o);
     s1 += __shfl_xor_sync(0xffffffffu, s1, o);
   }
-}
-
-template <typename T, typename V2, int TPR>
-__device__ __forceinline__ void row_sum(const Csr<T>& A, int row, int sub, const V2* __restrict__ x,
-                                        T& s0, T& s1) {
-  s0 = 0;
-  s1 = 0;
-  row_acc<T, V2, TPR>(A, row, sub, x, s0, s1);
 }
 
 // r = b - A x;  d = alpha d + beta D^-1 r;  xo = x + d.  The row sum starts from -b, so it is
@@ -1017,6 +1054,9 @@ __global__ void __launch_bounds__(TPB) k_cheb_step(Csr<T> A, const T* __restrict
                                                    T nbeta) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / TPR, sub = t % TPR;
+  CsrRow<T, TPR> row;
+  row_prefetch<T, TPR>(A, i, sub, row);
+  const T di = (sub == 0 && i < A.nrows) ? dinv[i] * nbeta : T(0);
   pdl_wait();
   pdl_trigger_t<T>();
   T s0 = 0, s1 = 0;
@@ -1025,10 +1065,9 @@ __global__ void __launch_bounds__(TPB) k_cheb_step(Csr<T> A, const T* __restrict
     s0 = -bi.x;
     s1 = -bi.y;
   }
-  row_acc<T, V2, TPR>(A, i, sub, x, s0, s1);
+  row_acc<T, V2, TPR>(A, row, x, s0, s1);
   if (i >= A.nrows || sub != 0) return;
   const V2 xi = x[i];
-  const T di = dinv[i] * nbeta;
   V2 dd;
   if (alpha != T(0)) {
     const V2 dold = d[i];
@@ -1045,10 +1084,12 @@ __global__ void __launch_bounds__(TPB) k_residual(Csr<T> A, const V2* __restrict
                                                   const V2* __restrict__ x, V2* __restrict__ r) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / TPR, sub = t % TPR;
+  CsrRow<T, TPR> row;
+  row_prefetch<T, TPR>(A, i, sub, row);
   pdl_wait();
   pdl_trigger_t<T>();
-  T s0, s1;
-  row_sum<T, V2, TPR>(A, i, sub, x, s0, s1);
+  T s0 = 0, s1 = 0;
+  row_acc<T, V2, TPR>(A, row, x, s0, s1);
   if (i >= A.nrows || sub != 0) return;
   const V2 bi = b[i];
   r[i] = mk2<T, V2>(bi.x - s0, bi.y - s1);
@@ -1059,10 +1100,12 @@ template <typename T, typename V2, int TPR, bool ACC>
 __global__ void __launch_bounds__(TPB) k_spmv2(Csr<T> A, const V2* __restrict__ x, V2* __restrict__ y) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / TPR, sub = t % TPR;
+  CsrRow<T, TPR> row;
+  row_prefetch<T, TPR>(A, i, sub, row);
   pdl_wait();
   pdl_trigger_t<T>();
-  T s0, s1;
-  row_sum<T, V2, TPR>(A, i, sub, x, s0, s1);
+  T s0 = 0, s1 = 0;
+  row_acc<T, V2, TPR>(A, row, x, s0, s1);
   if (i >= A.nrows || sub != 0) return;
   if (ACC) {
     const V2 yi = y[i];
@@ -1181,13 +1224,15 @@ __global__ void __launch_bounds__(TPB) k_restrict_first(Csr<T> R, const V2* __re
                                                         V2* __restrict__ xc, V2* __restrict__ dc) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = t / TPR, sub = t % TPR;
+  CsrRow<T, TPR> row;
+  row_prefetch<T, TPR>(R, i, sub, row);
+  const T s = (sub == 0 && i < R.nrows) ? invtheta * dinv_c[i] : T(0);
   pdl_wait();
   pdl_trigger_t<T>();
-  T s0, s1;
-  row_sum<T, V2, TPR>(R, i, sub, r, s0, s1);
+  T s0 = 0, s1 = 0;
+  row_acc<T, V2, TPR>(R, row, r, s0, s1);
   if (i >= R.nrows || sub != 0) return;
   bc[i] = mk2<T, V2>(s0, s1);
-  const T s = invtheta * dinv_c[i];
   const V2 v = mk2<T, V2>(s * s0, s * s1);
   xc[i] = v;
   dc[i] = v;

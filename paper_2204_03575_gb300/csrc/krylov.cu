@@ -113,21 +113,42 @@ __device__ __forceinline__ bool last_block_of_run(unsigned int* ticket, int nblo
   return am_last;
 }
 
-// out[v] = sum over the run's blocks b0..b1-1 of partials[b][v], in the last block of the run.  One
-// warp per value: lane l sums blocks b0 + l, b0 + l + 32, ... (independent loads, a few L2 round
-// trips) and the warp adds the 32 lane sums by a fixed xor tree -- a thread walking all blocks in
-// turn would wait for one L2 load per block (304 for a single run).  blockDim.x is a multiple of 32.
+// out[v] = sum over the run's blocks b0..b1-1 of partials[b][v] for v < nv, in the last block of the
+// run (TPB threads).  Lanes take values and warps take blocks: warp w adds the rows b0 + w, b0 + w + 8,
+// ..., RP_ROWS of them loaded per round (independent loads: a round costs one L2 round trip), and
+// warp 0 then adds the 8 warp sums in warp order.  Every FP64 add is a warp instruction over up to 32
+// values (a warp-wide FP64 instruction holds the SM's FP64 pipe equally long whatever its active
+// lanes).  A thread walking the run's blocks in turn would wait for one L2 load per block (304 for a
+// single run) at the end of every pass.  The order is fixed, so the sums are reproducible.
+constexpr int RP_ROWS = 20;
 __device__ void reduce_partials(const double* partials, int b0, int b1, int nv, double* out) {
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int v = threadIdx.x >> 5; v < nv; v += nw) {
+  constexpr int NW = TPB / 32;
+  __shared__ double wsum[NW][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int v0 = 0; v0 < nv; v0 += 32) {
+    const int v = v0 + lane;
+    const bool on = v < nv;
     double s = 0.0;
-#pragma unroll 4
-    for (int b = b0 + lane; b < b1; b += 32) s += partials[(size_t)b * MAXV + v];
+    for (int base = b0 + w; base < b1; base += NW * RP_ROWS) {
+      double t[RP_ROWS];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[v] = s;
+      for (int i = 0; i < RP_ROWS; ++i) {
+        const int b = base + NW * i;
+        t[i] = (on && b < b1) ? partials[(size_t)b * MAXV + v] : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < RP_ROWS; ++i) s += t[i];
+    }
+    wsum[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && on) {
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) t += wsum[q][lane];
+      out[v] = t;
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------- residual / norms
@@ -229,15 +250,21 @@ constexpr int ORTH_BLOCKS = 152 * 2;  // target grid of the segmented kernels (2
 // 64-run batch): 256 threads 14.1 / 6.75 / 37.3, 128 threads 14.1 / 6.71 / 38.5, 64 threads
 // 14.5 / 7.07 / 44.4 -- more nodes per thread halve the reduction's share but expose more latency
 constexpr int ORTH_TPB = 256;
+static_assert(ORTH_TPB == TPB, "reduce_partials assumes TPB threads in the reducing block");
 
-// Sum 32 per-lane values over the warp by recursive halving: at each step a lane keeps half of
-// its values and adds the partner's copy of that half.  On return lane l holds the warp sum of
-// value l (31 shuffles instead of 32 x 5).
-__device__ __forceinline__ double warp_transpose_sum32(double (&a)[32]) {
+// Sum V per-lane values (V a power of two, 2..32) over the warp by recursive halving: at each of the
+// log2 V steps a lane keeps half of its values and adds the partner's copy of that half; plain xor
+// adds then finish each group of 32 / V lanes.  On return lane l holds the warp sum of value
+// l / (32 / V): V - 1 + 5 - log2 V shuffle-adds instead of 5 per value (32 values: 31 instead of
+// 160).  Every warp-wide FP64 add holds the SM's FP64 pipe for the same time, so V is the smallest
+// power of two that holds the values in use.
+template <int V>
+__device__ __forceinline__ double warp_transpose_sum(double (&a)[32]) {
+  static_assert(V >= 2 && V <= 32 && (V & (V - 1)) == 0, "V: a power of two in [2, 32]");
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int step = 0; step < 5; ++step) {
-    const int o = 16 >> step, h = 16 >> step;  // partner offset, values kept
+  for (int step = 0; (1 << step) < V; ++step) {
+    const int o = 16 >> step, h = V >> (step + 1);  // partner offset, values kept
     const bool up = (lane & o) != 0;
 #pragma unroll
     for (int k = 0; k < h; ++k) {
@@ -246,22 +273,36 @@ __device__ __forceinline__ double warp_transpose_sum32(double (&a)[32]) {
       a[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
-  return a[0];
+  double r = a[0];
+#pragma unroll
+  for (int o = 16 / V; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
 }
 
-// Block sum of the 32 per-thread values over NT threads: returns, in threads 0..31, the block total
-// of value t.
-template <int NT>
-__device__ __forceinline__ double block_sum32(double (&a)[32], double* sm /* [NT/32][32] */) {
+// Block sum of the first V per-thread values over NT threads: returns, in threads 0..V-1, the block
+// total of value t (the warps' sums added in warp order).
+template <int NT, int V>
+__device__ __forceinline__ double block_sum_v(double (&a)[32], double* sm /* [NT/32][V] */) {
+  constexpr int G = 32 / V;  // lanes that end up holding the same value
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const double r = warp_transpose_sum32(a);
-  sm[w * 32 + lane] = r;
+  const double r = warp_transpose_sum<V>(a);
+  if ((lane & (G - 1)) == 0) sm[w * V + lane / G] = r;
   __syncthreads();
   double t = 0.0;
-  if (threadIdx.x < 32)
-    for (int q = 0; q < NT / 32; ++q) t += sm[q * 32 + threadIdx.x];
+  if (threadIdx.x < V)
+    for (int q = 0; q < NT / 32; ++q) t += sm[q * V + threadIdx.x];
   __syncthreads();
   return t;
+}
+
+// block_sum_v for the first nvals (1..32) values, V rounded up to a power of two (uniform branch)
+template <int NT>
+__device__ __forceinline__ double block_sum_n(int nvals, double (&a)[32], double* sm) {
+  if (nvals <= 2) return block_sum_v<NT, 2>(a, sm);
+  if (nvals <= 4) return block_sum_v<NT, 4>(a, sm);
+  if (nvals <= 8) return block_sum_v<NT, 8>(a, sm);
+  if (nvals <= 16) return block_sum_v<NT, 16>(a, sm);
+  return block_sum_v<NT, 32>(a, sm);
 }
 
 // W[v] -= sum_{k < nv} c[s][k] V_k[v] for one node (two partial sums, even / odd k, halve the
@@ -324,24 +365,44 @@ __device__ __forceinline__ void orth_dots_dispatch(int kw, const double4_32a* __
 #undef CH_ORTH_CASE
 }
 
-// Column j of the Arnoldi process for species sp once w is orthogonal to V_0..V_j with squared norm
-// hsq: h = h1 + h2 (the two Gram-Schmidt passes' coefficients), h_{j+1} = ||w||, the previous
-// Givens rotations, a new one, the residual estimate |g_{j+1}| and the cycle's stopping tests.
-__device__ __forceinline__ void arnoldi_column(KrylovDev* kd, int sp, int j, double hsq) {
-  double h[MAXM + 1];
-  for (int k = 0; k <= j; ++k) h[k] = kd->h1[sp][k] + kd->h2[sp][k];
-  const double hn = sqrt(hsq);
-  h[j + 1] = hn;
-  for (int k = 0; k < j; ++k) {  // previous rotations
-    const double t = kd->cs[sp][k] * h[k] + kd->sn[sp][k] * h[k + 1];
-    h[k + 1] = -kd->sn[sp][k] * h[k] + kd->cs[sp][k] * h[k + 1];
-    h[k] = t;
+// Column j's inputs for both species, staged in shared memory by the whole block (parallel loads,
+// instead of one dependent L2 load per previous rotation in the thread that applies them):
+// h_k = h1_k + h2_k (the two Gram-Schmidt passes' coefficients; h1 alone with only_h1) and the
+// previous rotations (cs_k, sn_k), k < j.
+struct ColumnStage {
+  double h[2][MAXM + 1];
+  double cs[2][MAXM];
+  double sn[2][MAXM];
+};
+__device__ __forceinline__ void stage_columns(const KrylovDev* kd, int j, bool only_h1, ColumnStage* cst) {
+  for (int t = threadIdx.x; t < 2 * (j + 1); t += blockDim.x) {
+    const int sp = t / (j + 1), k = t - sp * (j + 1);
+    cst->h[sp][k] = only_h1 ? kd->h1[sp][k] : kd->h1[sp][k] + kd->h2[sp][k];
+    if (k < j) {
+      cst->cs[sp][k] = kd->cs[sp][k];
+      cst->sn[sp][k] = kd->sn[sp][k];
+    }
   }
-  const double den = hypot(h[j], h[j + 1]);
+  __syncthreads();
+}
+
+// Column j of the Arnoldi process for species sp once w is orthogonal to V_0..V_j with squared norm
+// hsq, from the staged h and rotations: h_{j+1} = ||w||, the previous Givens rotations, a new one, the
+// residual estimate |g_{j+1}| and the cycle's stopping tests.
+__device__ __forceinline__ void arnoldi_column(KrylovDev* kd, int sp, int j, double hsq, ColumnStage* cst) {
+  double* h = cst->h[sp];
+  const double hn = sqrt(hsq);
+  double cur = h[0];  // entry k after the rotations 0..k-1
+  for (int k = 0; k < j; ++k) {  // previous rotations
+    const double c = cst->cs[sp][k], s = cst->sn[sp][k], nxt = h[k + 1];
+    h[k] = c * cur + s * nxt;
+    cur = -s * cur + c * nxt;
+  }
+  const double den = hypot(cur, hn);
   double cs = 1.0, sn = 0.0;
   if (den > 0.0) {
-    cs = h[j] / den;
-    sn = h[j + 1] / den;
+    cs = cur / den;
+    sn = hn / den;
   }
   kd->cs[sp][j] = cs;
   kd->sn[sp][j] = sn;
@@ -392,7 +453,7 @@ __global__ void __launch_bounds__(ORTH_TPB, 2) k_orth(Seg sg, int N, int nv, con
         orth_dots_dispatch<true>(kw, V, W, (size_t)N, k0, nv, coef, v0, v1, acc);
       else
         orth_dots_dispatch<false>(kw, V, W, (size_t)N, k0, nv, coef, v0, v1, acc);
-      const double tot = block_sum32<ORTH_TPB>(acc, sm);
+      const double tot = block_sum_n<ORTH_TPB>(2 * kw, acc, sm);
       if (threadIdx.x < 2 * kw) partials[(size_t)blockIdx.x * MAXV + 2 * k0 + threadIdx.x] = tot;
     }
     const bool norm = MODE == 0 && with_norm;
@@ -405,7 +466,7 @@ __global__ void __launch_bounds__(ORTH_TPB, 2) k_orth(Seg sg, int N, int nv, con
         acc[0] = fma(w.x, w.x, fma(w.z, w.z, acc[0]));
         acc[1] = fma(w.y, w.y, fma(w.w, w.w, acc[1]));
       }
-      const double bt = block_sum32<ORTH_TPB>(acc, sm);
+      const double bt = block_sum_v<ORTH_TPB, 2>(acc, sm);
       if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + 2 * nv + threadIdx.x] = bt;
     }
     if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
@@ -428,16 +489,18 @@ __global__ void __launch_bounds__(ORTH_TPB, 2) k_orth(Seg sg, int N, int nv, con
       acc[0] = fma(w.x, w.x, fma(w.z, w.z, acc[0]));
       acc[1] = fma(w.y, w.y, fma(w.w, w.w, acc[1]));
     }
-    const double bt = block_sum32<ORTH_TPB>(acc, sm);
+    const double bt = block_sum_v<ORTH_TPB, 2>(acc, sm);
     if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = bt;
     if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
     __shared__ double tot[2];
     reduce_partials(partials, b0, b1, 2, tot);
+    __shared__ ColumnStage cst;
+    stage_columns(kd, nv - 1, MODE == 3, &cst);
     if (threadIdx.x < 2) {
       const int sp = threadIdx.x;
       if (MODE == 2) {
         if (kd->cycle_active[sp]) {
-          arnoldi_column(kd, sp, nv - 1, tot[sp]);
+          arnoldi_column(kd, sp, nv - 1, tot[sp], &cst);
           kd->reorth_count[sp] += 1;
         } else {
           kd->hinv[sp] = 0.0;
@@ -447,7 +510,7 @@ __global__ void __launch_bounds__(ORTH_TPB, 2) k_orth(Seg sg, int N, int nv, con
         if (kd->cycle_active[sp]) {
           if (tot[sp] >= 0.5 * kd->w2[sp]) {
             for (int k = 0; k < nv; ++k) kd->h2[sp][k] = 0.0;
-            arnoldi_column(kd, sp, nv - 1, tot[sp]);
+            arnoldi_column(kd, sp, nv - 1, tot[sp], &cst);
           } else {
             kd->reorth[sp] = 1;
           }
@@ -455,7 +518,7 @@ __global__ void __launch_bounds__(ORTH_TPB, 2) k_orth(Seg sg, int N, int nv, con
           kd->hinv[sp] = 0.0;
         }
       } else if (kd->reorth[sp]) {  // MODE 5
-        arnoldi_column(kd, sp, nv - 1, tot[sp]);
+        arnoldi_column(kd, sp, nv - 1, tot[sp], &cst);
         kd->reorth_count[sp] += 1;
       }
     }
