@@ -1291,26 +1291,83 @@ static void launch_spmv2(int tpr, const Csr<T>& A, const V2* x, V2* y, cudaStrea
   CH_TPR_DISPATCH(tpr, (launch_k(pdl, k_spmv2<T, V2, TPRC, ACC>, g, TPB, 0, st, A, x, y)));
 }
 
-// x = Ainv b, dense nc x nc, one warp per row
-template <typename T, typename V2>
-__global__ void k_dense_solve(int n, const T* inv, const V2* b, V2* x) {
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+// x = Ainv b, dense nc x nc.  WPR warps per row: lane l of the row's warp `sub` takes columns
+// sub * 32 + l + k * 32 WPR, with its first U entries of Ainv read before the dependency wait and
+// 8 loads in flight after it; the lanes' sums are added by a butterfly and the warps' in warp order.
+template <typename T, typename V2, int WPR>
+__global__ void __launch_bounds__(TPB) k_dense_solve(int n, const T* __restrict__ inv, const V2* __restrict__ b,
+                                                     V2* __restrict__ x) {
+  static_assert((TPB / 32) % WPR == 0, "a row's warps share a block");
+  constexpr int U = 8;  // the lane's first entries, read before the dependency wait
+  __shared__ T part[TPB / 32][2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int row = gw / WPR, sub = gw % WPR;
+  const bool on = row < n;
+  const int stride = 32 * WPR, j0 = sub * 32 + lane;
+  const T* __restrict__ a = inv + (size_t)(on ? row : 0) * n;
+  T pa[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    const int j = j0 + k * stride;
+    pa[k] = (on && j < n) ? a[j] : T(0);
+  }
   pdl_wait();
   pdl_trigger_t<T>();
-  if (row >= n) return;
   T s0 = 0, s1 = 0;
-  for (int j = lane; j < n; j += 32) {
-    const T a = inv[(size_t)row * n + j];
-    const V2 bj = b[j];
-    s0 = fma(a, bj.x, s0);
-    s1 = fma(a, bj.y, s1);
+  if (on) {
+    V2 bj[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int j = j0 + k * stride;
+      if (j < n) bj[k] = b[j];
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (j0 + k * stride < n) {
+        s0 = fma(pa[k], bj[k].x, s0);
+        s1 = fma(pa[k], bj[k].y, s1);
+      }
+    }
+#pragma unroll 8
+    for (int j = j0 + U * stride; j < n; j += stride) {
+      const T aj = a[j];
+      const V2 v = b[j];
+      s0 = fma(aj, v.x, s0);
+      s1 = fma(aj, v.y, s1);
+    }
   }
+#pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     s0 += __shfl_xor_sync(0xffffffffu, s0, o);
     s1 += __shfl_xor_sync(0xffffffffu, s1, o);
   }
-  if (lane == 0) x[row] = mk2<T, V2>(s0, s1);
+  if (WPR == 1) {
+    if (on && lane == 0) x[row] = mk2<T, V2>(s0, s1);
+    return;
+  }
+  if (lane == 0) {
+    part[w][0] = s0;
+    part[w][1] = s1;
+  }
+  __syncthreads();
+  if (on && sub == 0 && lane == 0) {
+    T t0 = s0, t1 = s1;
+#pragma unroll
+    for (int q = 1; q < WPR; ++q) {
+      t0 += part[w + q][0];
+      t1 += part[w + q][1];
+    }
+    x[row] = mk2<T, V2>(t0, t1);
+  }
+}
+
+// x = Ainv b on the dense coarsest level, two warps per row.  Measured alone with the inverse
+// flushed from L2 (us per solve, one / two / four warps per row): 3742 FP32 rows 26.2 / 22.5 / 24.8,
+// 2048 FP32 rows 14.3 / 9.8 / 10.5, 512 FP64 rows 11.1 / 7.8 / 9.8.
+template <typename T, typename V2>
+static void launch_dense_solve(bool pdl, int n, const T* cinv, const V2* b, V2* x, cudaStream_t st) {
+  launch_k(pdl, k_dense_solve<T, V2, 2>, blocks_for((int64_t)n * 64), TPB, 0, st, n, cinv, b, x);
 }
 
 // fine-level I/O: strided fp64 pairs <-> working precision pairs
@@ -1426,7 +1483,7 @@ static ch_status vcycle(Hierarchy* h, std::vector<LevelT<T>>& Ls, const T* cinv,
   const double Tb = sizeof(T);
   if (l == h->nlev - 1) {
     ProfScope ps(st, K_COARSE, sizeof(T) == 4, Tb * n * (double)n + 4.0 * Tb * n, 2.0 * n * (double)n);
-    launch_k(L.pdl, k_dense_solve<T, V2>, blocks_for((int64_t)n * 32), TPB, 0, st, n, cinv, L.b, L.x);
+    launch_dense_solve<T, V2>(L.pdl, n, cinv, L.b, L.x, st);
     CH_LAUNCHED();
     *xres = L.x;
     return CH_OK;
@@ -1677,7 +1734,7 @@ static ch_status vcycle_static(Hierarchy* h, LevelT<T>* Ls, const T* cinv, int l
   LevelT<T>& L = Ls[l];
   const int n = L.A.nrows;
   if (l == h->nlev - 1) {
-    launch_k(L.pdl, k_dense_solve<T, V2>, blocks_for((int64_t)n * 32), TPB, 0, st, n, cinv, L.b, L.x);
+    launch_dense_solve<T, V2>(L.pdl, n, cinv, L.b, L.x, st);
     CH_LAUNCHED();
     *xres = L.x;
     return CH_OK;
