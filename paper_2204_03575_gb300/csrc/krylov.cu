@@ -76,6 +76,8 @@ struct Seg {
   const int* lo;
   const int* hi;
   const int* first;
+  unsigned int* gticket;  // per block: the last-block counter of the reduction group it starts (else unused)
+  int nblocks;            // blocks of the grid; group sums are rows nblocks + (group's first block) of partials
 };
 
 // ---------------------------------------------------------------- block reductions
@@ -99,7 +101,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* [TPB/32
 }
 
 // After a block has written its partials, returns true in the last block of its run to finish,
-// which then reads the run's block partials (reduce_partials, a fixed order).
+// which then reads the run's block partials (reduce_run, a fixed order).
 __device__ __forceinline__ bool last_block_of_run(unsigned int* ticket, int nblocks) {
   __shared__ bool am_last;
   __threadfence();
@@ -113,15 +115,14 @@ __device__ __forceinline__ bool last_block_of_run(unsigned int* ticket, int nblo
   return am_last;
 }
 
-// out[v] = sum over the run's blocks b0..b1-1 of partials[b][v] for v < nv, in the last block of the
-// run (TPB threads).  Lanes take values and warps take blocks: warp w adds the rows b0 + w, b0 + w + 8,
-// ..., RP_ROWS of them loaded per round (independent loads: a round costs one L2 round trip), and
-// warp 0 then adds the 8 warp sums in warp order.  Every FP64 add is a warp instruction over up to 32
-// values (a warp-wide FP64 instruction holds the SM's FP64 pipe equally long whatever its active
-// lanes).  A thread walking the run's blocks in turn would wait for one L2 load per block (304 for a
-// single run) at the end of every pass.  The order is fixed, so the sums are reproducible.
-constexpr int RP_ROWS = 20;
-__device__ void reduce_partials(const double* partials, int b0, int b1, int nv, double* out) {
+// out[v] = sum over k < count of rows[r0 + k stride][v] (rows of MAXV values), v < nv, by the TPB
+// threads of one block.  Lanes take values and warps take rows: warp w adds the rows w, w + 8, ...,
+// RP_ROWS of them loaded per round (independent loads, past L1: other blocks wrote them), and warp 0
+// then adds the 8 warp sums in warp order, so the order is fixed and the sums reproducible.  Every
+// FP64 add is a warp instruction over up to 32 values: a warp-wide FP64 instruction holds the SM's
+// FP64 pipe equally long whatever its active lanes, so adds of absent rows are skipped.
+constexpr int RP_ROWS = 4;  // rows loaded per warp and round: 32 per round (a run's group rows fit one)
+__device__ void sum_rows(const double* rows, int r0, int count, int stride, int nv, double* out) {
   constexpr int NW = TPB / 32;
   __shared__ double wsum[NW][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -129,15 +130,18 @@ __device__ void reduce_partials(const double* partials, int b0, int b1, int nv, 
     const int v = v0 + lane;
     const bool on = v < nv;
     double s = 0.0;
-    for (int base = b0 + w; base < b1; base += NW * RP_ROWS) {
+    for (int base = w; base < count; base += NW * RP_ROWS) {
       double t[RP_ROWS];
 #pragma unroll
       for (int i = 0; i < RP_ROWS; ++i) {
-        const int b = base + NW * i;
-        t[i] = (on && b < b1) ? partials[(size_t)b * MAXV + v] : 0.0;
+        const int k = base + NW * i;
+        t[i] = (on && k < count) ? __ldcg(rows + (size_t)(r0 + k * stride) * MAXV + v) : 0.0;
       }
 #pragma unroll
-      for (int i = 0; i < RP_ROWS; ++i) s += t[i];
+      for (int i = 0; i < RP_ROWS; ++i) {
+        if (base + NW * i >= count) break;
+        s += t[i];
+      }
     }
     wsum[w][lane] = s;
     __syncthreads();
@@ -149,6 +153,35 @@ __device__ void reduce_partials(const double* partials, int b0, int b1, int nv, 
     }
     __syncthreads();
   }
+}
+
+// The run-wide sums of the nv values that each block of the run (blocks b0..b1-1) wrote to its row of
+// `partials`: returns true in one block of the run, with out[0..nv) (shared) holding them.  The blocks
+// form groups of RGS consecutive blocks of the run: the last block of a group to finish adds the
+// group's rows into a group row (row nblocks + the group's first block), and the last of the group
+// leaders adds the group rows (a run of at most RGS blocks: its last block adds the rows).  Each level
+// adds at most 19 rows for a single run, one round of loads.  Measured (512 x 512, ms per step FP64 /
+// mixed): two levels 11.62 / 4.82; one level for up to 32 values 11.75 / 4.98 (304 rows: ten rounds of
+// loads); one level with 20 rows per warp in flight 11.69 / 4.90.  Per-block timer stamps at basis
+// size 18: the last block's end to the dot sums ready 9.2 us with one level, 6.9 us with two.  The
+// grouping and the orders are fixed: reproducible sums.
+constexpr int RGS = 16;
+__device__ bool reduce_run(const Seg& sg, double* partials, unsigned int* run_ticket, int b0, int b1, int nv,
+                           double* out) {
+  const int nbr = b1 - b0, ng = (nbr + RGS - 1) / RGS;
+  if (ng == 1) {
+    if (!last_block_of_run(run_ticket, nbr)) return false;
+    sum_rows(partials, b0, nbr, 1, nv, out);
+    return true;
+  }
+  const int gb0 = b0 + ((int)blockIdx.x - b0) / RGS * RGS, gb1 = min(gb0 + RGS, b1);
+  if (!last_block_of_run(&sg.gticket[gb0], gb1 - gb0)) return false;
+  double* grows = partials + (size_t)sg.nblocks * MAXV;
+  sum_rows(partials, gb0, gb1 - gb0, 1, nv, grows + (size_t)gb0 * MAXV);
+  if (threadIdx.x == 0) sg.gticket[gb0] = 0;
+  if (!last_block_of_run(run_ticket, ng)) return false;
+  sum_rows(grows, b0, ng, RGS, nv, out);
+  return true;
 }
 
 // ---------------------------------------------------------------- residual / norms
@@ -192,9 +225,8 @@ __global__ void k_residual4(Seg sg, const int* rowptr, const int* col, const dou
   if (threadIdx.x < 4) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = sm[threadIdx.x];
   KrylovDev* kd = kds + run;
   const int b0 = sg.first[run], b1 = sg.first[run + 1];
-  if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
   __shared__ double tot[4];
-  reduce_partials(partials, b0, b1, 4, tot);
+  if (!reduce_run(sg, partials, &kd->ticket, b0, b1, 4, tot)) return;
   if (threadIdx.x < 2) {
     const int s = threadIdx.x;
     const double bn = sqrt(tot[s]), rn = sqrt(tot[2 + s]);
@@ -250,7 +282,7 @@ constexpr int ORTH_BLOCKS = 152 * 2;  // target grid of the segmented kernels (2
 // 64-run batch): 256 threads 14.1 / 6.75 / 37.3, 128 threads 14.1 / 6.71 / 38.5, 64 threads
 // 14.5 / 7.07 / 44.4 -- more nodes per thread halve the reduction's share but expose more latency
 constexpr int ORTH_TPB = 256;
-static_assert(ORTH_TPB == TPB, "reduce_partials assumes TPB threads in the reducing block");
+static_assert(ORTH_TPB == TPB, "sum_rows assumes TPB threads in the reducing block");
 
 // Sum V per-lane values (V a power of two, 2..32) over the warp by recursive halving: at each of the
 // log2 V steps a lane keeps half of its values and adds the partner's copy of that half; plain xor
@@ -365,14 +397,16 @@ __device__ __forceinline__ void orth_dots_dispatch(int kw, const double4_32a* __
 #undef CH_ORTH_CASE
 }
 
-// Column j's inputs for both species, staged in shared memory by the whole block (parallel loads,
-// instead of one dependent L2 load per previous rotation in the thread that applies them):
-// h_k = h1_k + h2_k (the two Gram-Schmidt passes' coefficients; h1 alone with only_h1) and the
-// previous rotations (cs_k, sn_k), k < j.
+// Column j's inputs for both species, staged in shared memory by the whole block in one round of
+// parallel loads, so that the thread applying the rotations issues no dependent global load (each
+// cost it about a microsecond): h_k = h1_k + h2_k (the two Gram-Schmidt passes' coefficients; h1
+// alone with only_h1), the previous rotations (cs_k, sn_k), k < j, and the species' scalars.
 struct ColumnStage {
   double h[2][MAXM + 1];
   double cs[2][MAXM];
   double sn[2][MAXM];
+  double g[2], tol[2];          // g_j and the tolerance of each species
+  int its[2], active[2], rcount[2];  // iterations, cycle_active, reorth_count
 };
 __device__ __forceinline__ void stage_columns(const KrylovDev* kd, int j, bool only_h1, ColumnStage* cst) {
   for (int t = threadIdx.x; t < 2 * (j + 1); t += blockDim.x) {
@@ -382,6 +416,14 @@ __device__ __forceinline__ void stage_columns(const KrylovDev* kd, int j, bool o
       cst->cs[sp][k] = kd->cs[sp][k];
       cst->sn[sp][k] = kd->sn[sp][k];
     }
+  }
+  if (threadIdx.x >= 32 && threadIdx.x < 34) {  // the species' scalars, in the same round of loads
+    const int sp = threadIdx.x - 32;
+    cst->g[sp] = kd->g[sp][j];
+    cst->tol[sp] = kd->tol[sp];
+    cst->its[sp] = kd->its[sp];
+    cst->active[sp] = kd->cycle_active[sp];
+    cst->rcount[sp] = kd->reorth_count[sp];
   }
   __syncthreads();
 }
@@ -408,15 +450,15 @@ __device__ __forceinline__ void arnoldi_column(KrylovDev* kd, int sp, int j, dou
   kd->sn[sp][j] = sn;
   h[j] = den;
   for (int k = 0; k <= j; ++k) kd->R[sp][k][j] = h[k];
-  const double gj = kd->g[sp][j];
-  kd->g[sp][j + 1] = -sn * gj;
+  const double gj = cst->g[sp], gj1 = -sn * gj;
+  kd->g[sp][j + 1] = gj1;
   kd->g[sp][j] = cs * gj;
   kd->k[sp] = j + 1;
-  kd->its[sp] += 1;
+  kd->its[sp] = cst->its[sp] + 1;
   if (!isfinite(hn) || !isfinite(den)) kd->nonfinite = 1;
   const bool breakdown = !(hn > 1e-300);
   kd->hinv[sp] = breakdown ? 0.0 : 1.0 / hn;
-  if (fabs(kd->g[sp][j + 1]) <= kd->tol[sp] || breakdown || den == 0.0) kd->cycle_active[sp] = 0;
+  if (fabs(gj1) <= cst->tol[sp] || breakdown || den == 0.0) kd->cycle_active[sp] = 0;
 }
 
 template <int MODE>
@@ -469,9 +511,8 @@ __global__ void __launch_bounds__(ORTH_TPB, 2) k_orth(Seg sg, int N, int nv, con
       const double bt = block_sum_v<ORTH_TPB, 2>(acc, sm);
       if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + 2 * nv + threadIdx.x] = bt;
     }
-    if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
     __shared__ double tot[MAXV];
-    reduce_partials(partials, b0, b1, 2 * nv + (norm ? 2 : 0), tot);
+    if (!reduce_run(sg, partials, &kd->ticket, b0, b1, 2 * nv + (norm ? 2 : 0), tot)) return;
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
       double* dst0 = MODE == 0 ? kd->h1[0] : kd->h2[0];
       double* dst1 = MODE == 0 ? kd->h1[1] : kd->h2[1];
@@ -491,17 +532,16 @@ __global__ void __launch_bounds__(ORTH_TPB, 2) k_orth(Seg sg, int N, int nv, con
     }
     const double bt = block_sum_v<ORTH_TPB, 2>(acc, sm);
     if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = bt;
-    if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
     __shared__ double tot[2];
-    reduce_partials(partials, b0, b1, 2, tot);
+    if (!reduce_run(sg, partials, &kd->ticket, b0, b1, 2, tot)) return;
     __shared__ ColumnStage cst;
     stage_columns(kd, nv - 1, MODE == 3, &cst);
     if (threadIdx.x < 2) {
       const int sp = threadIdx.x;
       if (MODE == 2) {
-        if (kd->cycle_active[sp]) {
+        if (cst.active[sp]) {
           arnoldi_column(kd, sp, nv - 1, tot[sp], &cst);
-          kd->reorth_count[sp] += 1;
+          kd->reorth_count[sp] = cst.rcount[sp] + 1;
         } else {
           kd->hinv[sp] = 0.0;
         }
@@ -797,9 +837,8 @@ __global__ void k_mass(Seg sg, const double* mlump, const double4_32a* x, double
   if (threadIdx.x < 2) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = sm[threadIdx.x];
   KrylovDev* kd = kds + run;
   const int b0 = sg.first[run], b1 = sg.first[run + 1];
-  if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
   __shared__ double tot[2];
-  reduce_partials(partials, b0, b1, 2, tot);
+  if (!reduce_run(sg, partials, &kd->ticket, b0, b1, 2, tot)) return;
   if (threadIdx.x < 2) kd->mass[threadIdx.x] = tot[threadIdx.x];
   if (threadIdx.x == 0) kd->ticket = 0;
 }
@@ -978,8 +1017,11 @@ static ch_status make_segments(ch_state_s* S, cudaStream_t st) {
   CH_CUDA(cudaMemcpyAsync(d_lo, lo.data(), sizeof(int) * lo.size(), cudaMemcpyHostToDevice, st));
   CH_CUDA(cudaMemcpyAsync(d_hi, hi.data(), sizeof(int) * hi.size(), cudaMemcpyHostToDevice, st));
   CH_CUDA(cudaMemcpyAsync(d_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, st));
+  unsigned int* d_gticket = nullptr;
+  CH_TRY(S->mem.get(&d_gticket, run.size()));
+  CH_CUDA(cudaMemsetAsync(d_gticket, 0, sizeof(unsigned int) * run.size(), st));
   CH_CUDA(cudaStreamSynchronize(st));
-  S->seg = Seg{d_run, d_lo, d_hi, d_first};
+  S->seg = Seg{d_run, d_lo, d_hi, d_first, d_gticket, S->nblocks};
   return CH_OK;
 }
 
@@ -1014,7 +1056,7 @@ ch_status state_create(const ch_system_s* s, ch_precond_s* pc, cudaStream_t st, 
   if (r == CH_OK) r = S->mem.get(&S->dstats, (size_t)S->R);
   if (r == CH_OK) r = S->mem.get(&S->dctl, 1);
   if (r == CH_OK) r = make_segments(S, st);
-  if (r == CH_OK) r = S->mem.get(&S->partials, (size_t)S->nblocks * MAXV);
+  if (r == CH_OK) r = S->mem.get(&S->partials, 2 * (size_t)S->nblocks * MAXV);  // block rows, group rows
   auto pinned = [&](void** ptr, size_t bytes) {
     if (r != CH_OK) return;
     if (cudaMallocHost(ptr, bytes) != cudaSuccess) {
@@ -1228,9 +1270,8 @@ __global__ void __launch_bounds__(TPB) k_mr_dot(Seg sg, const double4_32a* __res
   KrylovDev* kd = kds + run;
   MrDev* mr = mrs + run;
   const int b0 = sg.first[run], b1 = sg.first[run + 1];
-  if (!last_block_of_run(&kd->ticket, b1 - b0)) return;
   __shared__ double tot[2];
-  reduce_partials(partials, b0, b1, 2, tot);
+  if (!reduce_run(sg, partials, &kd->ticket, b0, b1, 2, tot)) return;
   if (threadIdx.x < 2) {
     const int sp = threadIdx.x;
     const double d = tot[sp];
