@@ -79,7 +79,7 @@ typedef struct ch_params {
   int32_t cheb_degree;       /* Chebyshev smoothing steps before and after coarse correction on the
                                 finest level; 0 (default): 5 */
   int32_t coarse_max;        /* AMG: coarsest level is solved densely at or below this size (<= 4096);
-                                0 (default): 512 rows for FP64 V-cycles, 4096 for FP32 */
+                                0 (default): 512 rows for FP64 V-cycles, 2048 for FP32 */
   double amg_theta;          /* AMG strength threshold, default 0.08 */
   int32_t vcycles_M;         /* V-cycles per application of M~^-1 (Algorithm 1, step 1), default 1 */
   int32_t vcycles_H;         /* V-cycles per application of H~^-1 (Algorithm 1, steps 2 and 4), default 2 */

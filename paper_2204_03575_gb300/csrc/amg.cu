@@ -464,11 +464,11 @@ static ch_status level_setup(Hierarchy* h, int l, const ch_params& p, cudaStream
   CH_TRY(power_estimate(A, dinv, st, &lam));
   if (lam > 0.0 && std::isfinite(lam)) rho = std::min(rho, 1.05 * lam);
   h->rho.push_back(rho);
-  // coarse_max 0: 512 rows for FP64 V-cycles, 4096 for FP32 (where the dense inverse is half the
-  // bytes); measured on 512 x 512: the dense solve beats the per-level launch chain up to there
-  // (FP32 with programmatic dependent launch: 6.85 / 6.77 / 6.78 / 6.78 ms per step at
-  // 4096 / 2048 / 1024 / 512 rows, but the 64-run batch 32.05 / 32.70 ms at 4096 / 2048)
-  const int cmax = p.coarse_max > 0 ? p.coarse_max : (h->precision == 0 ? 512 : 4096);
+  // coarse_max 0: 512 rows for FP64 V-cycles, 2048 for FP32 (where the dense inverse is half the
+  // bytes); measured on 512 x 512, the dense solve beating the per-level launch chain up to there
+  // (FP64: 512 and 1024 alike, 11.63 ms per step; FP32: 4.85-4.88 ms at 4096 rows, 4.75 at 2048;
+  // the 64-run batch 30.9-31.1 ms either way, the 3D 128 x 128 x 32 box 14.8 ms either way)
+  const int cmax = p.coarse_max > 0 ? p.coarse_max : (h->precision == 0 ? 512 : 2048);
   if (n <= cmax) {
     *last = true;
     return CH_OK;

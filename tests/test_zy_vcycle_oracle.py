@@ -16,7 +16,7 @@ the oracle's hierarchy must agree with ch_vcycle element by element:
     and the coarse corrections; measured at most 2.3e-7);
   * one cycle from a zero guess, and two cycles, the second continuing from the first's iterate.
 The coarsest level is capped at 256 rows so that every mesh here has several levels in both
-precisions (FP32 hierarchies otherwise stop at 4096 rows).
+precisions (FP32 hierarchies otherwise stop at 2048 rows).
 """
 import numpy as np
 import pytest
