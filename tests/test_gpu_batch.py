@@ -130,3 +130,34 @@ def test_batch_patterned_substrate_per_run(lib):
         op = o.Params(nx=g[0], ny=g[1], Lx=g[2] if len(g) > 2 else 1.0, Ly=g[3] if len(g) > 3 else 1.0, **kw)
         egp, egn = o.boundary_load(o.mesh(op), split(mesh, pp)[r], split(mesh, pn)[r], op)
         assert rel(gp[r], egp) < 1e-13 and rel(gn[r], egn) < 1e-13, r
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_run_spanning_reduction_groups(lib, precision):
+    """A run whose blocks start mid-grid and span several reduction groups.
+
+    Blocks own at least 256 nodes, and the run-wide sums of a run with more than 16 blocks go
+    through groups of 16 consecutive blocks of that run (group rows, per-group tickets).  Here
+    the 96 x 96 run (9409 nodes, 37 blocks) starts at block 1, after a one-block run, and a
+    one-block run follows it; every run must still match its own oracle step."""
+    geoms = [(8, 8), (96, 96), (10, 6)]
+    bases = [(0.33, 0.33), (0.28, 0.38), (0.40, 0.25)]
+    mesh, system, state = make_batch(lib, geoms, rtol=1e-14, max_iter=2000, precision=precision)
+    off = mesh.run_offsets
+    assert off[2] - off[1] == 97 * 97 and off[1] - off[0] <= 256
+    state.init_seeded_batch([b[0] for b in bases], [b[1] for b in bases], 0.01, seed=300)
+    solvers = [o.Solver(o.Params(nx=g[0], ny=g[1])) for g in geoms]
+    g0 = {k: split(mesh, v.cpu().numpy()) for k, v in state.get().items()}
+    prev = [o.initial(s.N, g0["phi_p"][r], g0["phi_nfa"][r]) for r, s in enumerate(solvers)]
+    for step in range(2):
+        state.step()
+        g = {k: split(mesh, v.cpu().numpy()) for k, v in state.get().items()}
+        for r, s in enumerate(solvers):
+            ref = s.step(prev[r])
+            for gk in ("phi_p", "phi_nfa", "mu_p", "mu_nfa"):
+                err = rel(g[gk][r], getattr(ref, gk))
+                assert err < 1e-10, (step, r, gk, err)
+            st = state.run_stats(r)
+            assert st["status"] == 0 and max(st["relres"]) <= 1e-14
+            assert abs(st["mass"][0] - o.mass(s.M, g["phi_p"][r])) <= 1e-12 * abs(st["mass"][0])
+            prev[r] = o.State(g["phi_p"][r], g["phi_nfa"][r], g["mu_p"][r], g["mu_nfa"][r])
