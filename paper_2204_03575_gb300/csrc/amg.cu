@@ -1380,6 +1380,24 @@ __global__ void k_load2(int n, const double* src, int ld, V2* dst) {
   const double2 v = *reinterpret_cast<const double2*>(src + (size_t)i * ld);
   dst[i] = mk2<T, V2>((T)v.x, (T)v.y);
 }
+// k_load2 fused with the finest level's first Chebyshev step from a zero guess (the arithmetic of
+// k_cheb_first on the converted values): b = (T) src, x = d = invtheta D^-1 b.  One launch instead
+// of two at the start of the first V-cycle of a solve.
+template <typename T, typename V2>
+__global__ void k_load2_first(int n, const double* src, int ld, const T* dinv, T invtheta, V2* b, V2* x, V2* d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const T di = i < n ? dinv[i] : T(0);  // set-up data: read before the dependency wait
+  pdl_wait();
+  pdl_trigger_t<T>();
+  if (i >= n) return;
+  const double2 v = *reinterpret_cast<const double2*>(src + (size_t)i * ld);
+  const V2 bi = mk2<T, V2>((T)v.x, (T)v.y);
+  b[i] = bi;
+  const T s = invtheta * di;
+  const V2 w = mk2<T, V2>(s * bi.x, s * bi.y);
+  x[i] = w;
+  d[i] = w;
+}
 template <typename T, typename V2>
 __global__ void k_store2(int n, const V2* src, double* dst, int ld) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1586,6 +1604,26 @@ ch_status hierarchy_solve(Hierarchy* h, const double* b, int ldb, double* x, int
 // v, w are N x 4 (phi_p, phi_n, mu_p, mu_n per node): block 1 at offset 0, block 2 at offset 2.
 static int semi_steps(const ch_params& p) { return p.cheb_M_steps > 0 ? p.cheb_M_steps : 5; }
 
+// The fine-level input of a solve: b = (T) v (strided FP64 pairs).  With AMG V-cycles on a
+// hierarchy of more than one level the first V-cycle's first smoothing step (from zero) is done in
+// the same launch (k_load2_first), and the V-cycle then starts at its second step (zero_guess 2).
+// Returns the zero_guess for the first V-cycle.
+template <typename T>
+static int load_input(Hierarchy* h, LevelT<T>& L, bool amg, const double* v, int ld, cudaStream_t st) {
+  using V2 = typename V2T<T>::t;
+  const int n = L.A.nrows;
+  if (amg && h->nlev > 1) {
+    const ChebCoef c = cheb_coef(h->rho[0], h->cheb_degree, h->cheb_lower);
+    ProfScope ps(st, K_VLOAD, sizeof(T) == 4, n * (16.0 + 7.0 * sizeof(T)), 2.0 * n);
+    launch_k(L.pdl, k_load2_first<T, V2>, blocks_for(n), TPB, 0, st, n, v, ld, L.dinv, (T)c.invtheta, L.b, L.x,
+             L.d);
+    return 2;
+  }
+  ProfScope ps(st, K_VLOAD, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
+  launch_k(L.pdl, k_load2<T, V2>, blocks_for(n), TPB, 0, st, n, v, ld, L.b);
+  return 1;
+}
+
 template <typename T>
 static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::vector<LevelT<T>>& LH,
                            const T* cinvM, const T* cinvH, const double* v, double* w,
@@ -1607,15 +1645,12 @@ static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::ve
   // step 1: M w_1 = v_1 (w_1 in columns 0-1 of w; steps 2-4 write columns 2-3)
   {
     LevelT<T>& L = LM[0];
-    {
-      ProfScope ps(sm, K_VLOAD, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
-      launch_k(L.pdl, k_load2<T, V2>, blocks_for(n), TPB, 0, sm, n, v, 4, L.b);
-    }
+    const int zg = load_input<T>(pc->hM, L, p.precond_M != 1, v, 4, sm);
     V2* xr = L.x;
     if (p.precond_M == 1) {
       CH_TRY(semi_iteration<T>(L, pc->sys->mesh->dim, semi_steps(p), &xr, sm));
     } else {
-      for (int c = 0; c < p.vcycles_M; ++c) CH_TRY(vcycle<T>(pc->hM, LM, cinvM, 0, c == 0, &xr, sm));
+      for (int c = 0; c < p.vcycles_M; ++c) CH_TRY(vcycle<T>(pc->hM, LM, cinvM, 0, c == 0 ? zg : 0, &xr, sm));
     }
     {
       ProfScope ps(sm, K_VSTORE, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
@@ -1627,12 +1662,9 @@ static ch_status precond_t(ch_precond_s* pc, std::vector<LevelT<T>>& LM, std::ve
   // steps 2-4: H w_2 = v_2; w_2 = M w_2; H w_2 = w_2
   {
     LevelT<T>& L = LH[0];
-    {
-      ProfScope ps(st, K_VLOAD, sizeof(T) == 4, n * (16.0 + 2.0 * sizeof(T)), 0.0);
-      launch_k(L.pdl, k_load2<T, V2>, blocks_for(n), TPB, 0, st, n, v + 2, 4, L.b);
-    }
+    const int zg = load_input<T>(pc->hH, L, true, v + 2, 4, st);
     V2* xr = L.x;
-    for (int c = 0; c < p.vcycles_H; ++c) CH_TRY(vcycle<T>(pc->hH, LH, cinvH, 0, c == 0, &xr, st));
+    for (int c = 0; c < p.vcycles_H; ++c) CH_TRY(vcycle<T>(pc->hH, LH, cinvH, 0, c == 0 ? zg : 0, &xr, st));
     // b <- M x (M's fine level in working precision); the V-cycle reads only L.b afterwards
     {
       const double Tb = sizeof(T), nnz = (double)LM[0].A.nnz;
