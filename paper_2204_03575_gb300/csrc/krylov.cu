@@ -194,32 +194,62 @@ __global__ void k_residual4(Seg sg, const int* rowptr, const int* col, const dou
   __shared__ double sm[(TPB / 32) * 4];
   const int run = sg.run[blockIdx.x];
   double acc[4] = {0, 0, 0, 0};  // ||b_p||^2, ||b_n||^2, ||r_p||^2, ||r_n||^2
-  for (int v = sg.lo[blockIdx.x] + threadIdx.x; v < sg.hi[blockIdx.x]; v += blockDim.x) {
-    double m1p = 0, m1n = 0, m2p = 0, m2n = 0, k1p = 0, k1n = 0, k2p = 0, k2n = 0;
-    for (int q = rowptr[v]; q < rowptr[v + 1]; ++q) {
-      const int j = col[q];
-      const double m = valM[q], k = valK[q];
-      const double4_32a z = x[j];
-      m1p = fma(m, z.x, m1p);
-      m1n = fma(m, z.y, m1n);
-      m2p = fma(m, z.z, m2p);
-      m2n = fma(m, z.w, m2n);
-      k1p = fma(k, z.x, k1p);
-      k1n = fma(k, z.y, k1n);
-      k2p = fma(k, z.z, k2p);
-      k2n = fma(k, z.w, k2n);
+  // Two nodes per iteration (v and v + blockDim.x, the order of the plain loop) with their rows
+  // walked in one loop, so that both rows' gathers are in flight together: the segmented grid has
+  // 16 warps per SM to hide them.  Each row's sums keep their order.
+  const int hi = sg.hi[blockIdx.x];
+  for (int v = sg.lo[blockIdx.x] + threadIdx.x; v < hi; v += 2 * blockDim.x) {
+    const int v2 = v + blockDim.x;
+    const bool two = v2 < hi;
+    const int q0 = rowptr[v], n0 = rowptr[v + 1] - q0;
+    const int p0 = two ? rowptr[v2] : 0, n1 = two ? rowptr[v2 + 1] - p0 : 0;
+    double u[8] = {0, 0, 0, 0, 0, 0, 0, 0}, t[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // M x, K x per node
+    const int len = n0 > n1 ? n0 : n1;
+    for (int e = 0; e < len; ++e) {
+      if (e < n0) {
+        const int q = q0 + e;
+        const double m = valM[q], k = valK[q];
+        const double4_32a z = x[col[q]];
+        u[0] = fma(m, z.x, u[0]);
+        u[1] = fma(m, z.y, u[1]);
+        u[2] = fma(m, z.z, u[2]);
+        u[3] = fma(m, z.w, u[3]);
+        u[4] = fma(k, z.x, u[4]);
+        u[5] = fma(k, z.y, u[5]);
+        u[6] = fma(k, z.z, u[6]);
+        u[7] = fma(k, z.w, u[7]);
+      }
+      if (e < n1) {
+        const int q = p0 + e;
+        const double m = valM[q], k = valK[q];
+        const double4_32a z = x[col[q]];
+        t[0] = fma(m, z.x, t[0]);
+        t[1] = fma(m, z.y, t[1]);
+        t[2] = fma(m, z.z, t[2]);
+        t[3] = fma(m, z.w, t[3]);
+        t[4] = fma(k, z.x, t[4]);
+        t[5] = fma(k, z.y, t[5]);
+        t[6] = fma(k, z.z, t[6]);
+        t[7] = fma(k, z.w, t[7]);
+      }
     }
-    const double4_32a bb = b[v];
-    double4_32a r;
-    r.x = bb.x - fma(a, k2p, m1p);
-    r.y = bb.y - fma(a, k2n, m1n);
-    r.z = bb.z - fma(a, k1p, -c * m2p);
-    r.w = bb.w - fma(a, k1n, -c * m2n);
-    W[v] = r;
-    acc[0] += bb.x * bb.x + bb.z * bb.z;
-    acc[1] += bb.y * bb.y + bb.w * bb.w;
-    acc[2] += r.x * r.x + r.z * r.z;
-    acc[3] += r.y * r.y + r.w * r.w;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !two) break;
+      const int w = h == 0 ? v : v2;
+      const double* s8 = h == 0 ? u : t;  // m1p, m1n, m2p, m2n, k1p, k1n, k2p, k2n
+      const double4_32a bb = b[w];
+      double4_32a r;
+      r.x = bb.x - fma(a, s8[6], s8[0]);
+      r.y = bb.y - fma(a, s8[7], s8[1]);
+      r.z = bb.z - fma(a, s8[4], -c * s8[2]);
+      r.w = bb.w - fma(a, s8[5], -c * s8[3]);
+      W[w] = r;
+      acc[0] += bb.x * bb.x + bb.z * bb.z;
+      acc[1] += bb.y * bb.y + bb.w * bb.w;
+      acc[2] += r.x * r.x + r.z * r.z;
+      acc[3] += r.y * r.y + r.w * r.w;
+    }
   }
   block_sum<4>(acc, sm);
   if (threadIdx.x < 4) partials[(size_t)blockIdx.x * MAXV + threadIdx.x] = sm[threadIdx.x];
@@ -570,44 +600,53 @@ __global__ void __launch_bounds__(ORTH_TPB, 2) k_orth(Seg sg, int N, int nv, con
   }
 }
 
-// y_s = R_s^-1 g_s (back substitution, k_s x k_s), one thread per (run, species)
-__global__ void k_cycle_solve(int nruns, KrylovDev* kds) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * nruns) return;
-  KrylovDev* kd = kds + t / 2;
-  const int s = t % 2;
+// y_s = R_s^-1 g_s (back substitution, k_s x k_s), one warp per (run, species): the warp stages the
+// triangle and g in shared memory (one round of independent loads), then for i = k-1 .. 0 the lanes
+// form the products R[i][q] y[q], q > i, a butterfly adds them and every lane takes
+// y[i] = (g[i] - sum) / R[i][i].  One thread walking the triangle in global memory waited on a
+// load at every entry it read after a store (47 us at k = 11 in a cold capture).
+__global__ void __launch_bounds__(32) k_cycle_solve(int nruns, KrylovDev* kds) {
+  __shared__ double Rs[MAXM][MAXM + 1];
+  __shared__ double gs[MAXM], ys[MAXM];
+  if ((int)blockIdx.x >= 2 * nruns) return;
+  KrylovDev* kd = kds + blockIdx.x / 2;
+  const int s = blockIdx.x % 2, lane = threadIdx.x;
   const int k = kd->k[s];
-  for (int i = k - 1; i >= 0; --i) {
-    double v = kd->g[s][i];
-    for (int q = i + 1; q < k; ++q) v -= kd->R[s][i][q] * kd->y[s][q];
-    kd->y[s][i] = kd->R[s][i][i] != 0.0 ? v / kd->R[s][i][i] : 0.0;
+  for (int e = lane; e < k * k; e += 32) {
+    const int i = e / k, q = e - i * k;
+    Rs[i][q] = kd->R[s][i][q];
   }
-  for (int i = k; i < MAXM; ++i) kd->y[s][i] = 0.0;
+  for (int i = lane; i < k; i += 32) gs[i] = kd->g[s][i];
+  __syncwarp();
+  for (int i = k - 1; i >= 0; --i) {
+    double p = 0.0;
+    for (int q = i + 1 + lane; q < k; q += 32) p = fma(Rs[i][q], ys[q], p);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    const double rii = Rs[i][i];
+    const double yi = rii != 0.0 ? (gs[i] - p) / rii : 0.0;
+    if (lane == 0) ys[i] = yi;
+    __syncwarp();
+  }
+  for (int i = lane; i < MAXM; i += 32) kd->y[s][i] = i < k ? ys[i] : 0.0;
 }
 
 // x += sum_k y_s[k] Z_k with the coefficients of the block's run, k < kmax (read from kmax_dev
 // when it is given: the device-side loop knows the cycle's length only on the device)
 __global__ void k_update_x(Seg sg, int N, int kmax_arg, const int* kmax_dev, const double4_32a* __restrict__ Z,
                            double4_32a* x, const KrylovDev* kds) {
-  __shared__ double y[2][MAXM];
+  __shared__ double ny[2][MAXM + 1];  // -y: x - sum(-y_k Z_k) is x + sum(y_k Z_k) exactly
   const int kmax = kmax_dev ? *kmax_dev : kmax_arg;
   const KrylovDev* kd = kds + sg.run[blockIdx.x];
   for (int k = threadIdx.x; k < kmax; k += blockDim.x) {
-    y[0][k] = kd->y[0][k];
-    y[1][k] = kd->y[1][k];
+    ny[0][k] = -kd->y[0][k];
+    ny[1][k] = -kd->y[1][k];
   }
   __syncthreads();
-  for (int v = sg.lo[blockIdx.x] + threadIdx.x; v < sg.hi[blockIdx.x]; v += blockDim.x) {
-    double4_32a a = x[v];
-    for (int k = 0; k < kmax; ++k) {
-      const double4_32a z = Z[(size_t)k * N + v];
-      a.x = fma(y[0][k], z.x, a.x);
-      a.z = fma(y[0][k], z.z, a.z);
-      a.y = fma(y[1][k], z.y, a.y);
-      a.w = fma(y[1][k], z.w, a.w);
-    }
-    x[v] = a;
-  }
+  // two partial sums (even / odd k) and the basis vectors loaded in pairs, as in the Gram-Schmidt
+  // update: a single FMA chain per component left the loads of one vector at a time in flight
+  for (int v = sg.lo[blockIdx.x] + threadIdx.x; v < sg.hi[blockIdx.x]; v += blockDim.x)
+    orth_update_node(Z, x, (size_t)N, kmax, ny, v);
 }
 
 // summary flags over all runs (one block)
@@ -1228,7 +1267,7 @@ static ch_status fgmres(ch_state_s* S, cudaStream_t st, int* restarts) {
     if (j > m) j = m;
     {
       ProfScope ps(st, K_CYCLE_SOLVE, 0, 0.0, 0.0);
-      k_cycle_solve<<<blocks_for(2 * S->R, 64), 64, 0, st>>>(S->R, S->kd);
+      k_cycle_solve<<<2 * S->R, 32, 0, st>>>(S->R, S->kd);
     }
     {
       ProfScope ps(st, K_UPDATE_X, 0, (j + 2) * 32.0 * N, 4.0 * j * N);
@@ -1579,7 +1618,7 @@ static ch_status loop_case(ch_state_s* S, int j, cudaStream_t st) {
   }
   {
     ProfScope ps(st, K_CYCLE_SOLVE, 0, 0.0, 0.0);
-    k_cycle_solve<<<blocks_for(2 * S->R, 64), 64, 0, st>>>(S->R, S->kd);
+    k_cycle_solve<<<2 * S->R, 32, 0, st>>>(S->R, S->kd);
   }
   {
     // bytes of the x update beyond x itself (32 N per Krylov vector) are added per cycle from
